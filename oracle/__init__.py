@@ -1,0 +1,14 @@
+"""CPU oracle for the lMBD hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py, never by the product package.
+"""
+from .lmbd_oracle import (BOHR_ANGSTROM, HARTREE_EV, Params, System, quadrature, frequencies,
+                          free_atom, fermi, cutoff_buffer, f_inner, f_scs, dipole_T,
+                          dipole_T_sr_bare, enumerate_sites, scs_local, t_lr, local_energy,
+                          blend, site_positions, with_params)
+
+__all__ = ["BOHR_ANGSTROM", "HARTREE_EV", "Params", "System", "quadrature", "frequencies",
+           "free_atom", "fermi", "cutoff_buffer", "f_inner", "f_scs", "dipole_T",
+           "dipole_T_sr_bare", "enumerate_sites", "scs_local", "t_lr", "local_energy", "blend",
+           "site_positions", "with_params"]

@@ -1,0 +1,446 @@
+"""Plain CPU oracle for the lMBD local-cluster problem (arXiv 2407.06409).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports, calls or runs
+this module: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` do.  It shares no code with the CUDA path.
+
+Everything is float64 PyTorch on the CPU and follows the paper's equations in
+the paper's order, one atom (one "central atom k") at a time:
+
+* free-atom polarisability, characteristic frequency, Gaussian width and
+  vdW radius (Sec. II.B, Eq. bar-alpha and the definitions after Eq. h-func);
+* the short-range dipole tensor T_SR = (1 - f) d_i d_j [erf(r/sigma)/r]
+  written as -T g + h (Eq. T_SR, Eqs. g-func / h-func) with the cutoff
+  functions f_SR and f_inner (Sec. III.B);
+* the local SCS system B_K alpha_K = d_K over the coupled set K1 = B(r_SCS)
+  with the uncoupled shell K2 = B(2 r_SCS) minus B(r_SCS) (Eq. local_pol),
+  solved with a library dense solve;
+* central polarisabilities alpha_I (each atom in its own sphere) and the
+  range-separated blend with f_SCS (Eq. full-pol);
+* SCS radii (Eq. scaled-rvdw), T_LR with f_LR and the primary/secondary radii
+  (Sec. III.A), G = sqrt(A) T_LR sqrt(A) (Eq. G_frequency);
+* the local energy as the truncated series Tr{g_k G^(n-2) g_k^T} with
+  c_n = -1/n (Eq. mbd-local / Eq. E_k) or, in "log mode", the k-block of
+  ln(1 - G) from a symmetric eigendecomposition (Eq. series-expansion);
+* the frequency integral by Gauss-Legendre quadrature mapped to [0, inf).
+
+Forces are -d(sum_k w_k E_k)/dR by PyTorch autograd (reverse mode), applied to
+the two phases separately so that memory stays bounded: first E_k with the
+other atoms' central polarisabilities as leaves, then those central
+polarisabilities with the accumulated seeds (exact chain rule).
+
+Readings where the paper is silent or inconsistent (the design notes list
+them): energy sign per Eq. E_MBD (c_n = -1/n, dispersion energy negative);
+MBD sphere radius r_sphere (default r_MBD,1 + r_MBD,2); every periodic image
+within a radius is a distinct site; set membership by strict r < r_c with r
+measured in Angstrom from the central atom; Gauss-Legendre nodes mapped by
+omega = L (1 + x)/(1 - x); positions in Angstrom, species parameters in
+atomic units, outputs in eV and eV/Angstrom with CODATA 2018 constants.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, replace
+
+import numpy as np
+import torch
+
+BOHR_ANGSTROM = 0.529177210903       # CODATA 2018
+HARTREE_EV = 27.211386245988         # CODATA 2018
+_DT = torch.float64
+
+
+@dataclass(frozen=True)
+class Params:
+    """Cutoffs in Angstrom; beta and d from Sec. II.B (beta = 0.83, d = 6)."""
+    r_scs: float = 5.0
+    r_mbd1: float = 7.0
+    r_mbd2: float = 7.0
+    r_sphere: float = 7.0          # <= 0 means r_mbd1 + r_mbd2 (the paper's B_{r_MBD})
+    r_buf: float = 0.5             # buffer width r_b of f_SR and f_LR (Sec. III.A)
+    r_inner: float = 2.0           # r_inner of f_inner (Sec. III.B: hard-coded 2 Angstrom)
+    beta: float = 0.83
+    d: float = 6.0
+    n_freq: int = 12
+    series_order: int | None = 6   # None = log mode (the n_max -> infinity limit)
+    omega_scale: float = 0.6       # L of the frequency mapping, Hartree
+
+    @property
+    def sphere(self) -> float:
+        return self.r_sphere if self.r_sphere > 0 else self.r_mbd1 + self.r_mbd2
+
+    @property
+    def r_list(self) -> float:
+        return max(2.0 * self.r_scs, self.sphere)
+
+
+# ----------------------------------------------------------------------------------------
+# frequency grid (Eq. E_MBD integral over imaginary frequency)
+# ----------------------------------------------------------------------------------------
+def quadrature(n_freq: int, omega_scale: float) -> tuple[np.ndarray, np.ndarray]:
+    """Gauss-Legendre nodes on [-1, 1] mapped to [0, inf): omega = L(1+x)/(1-x)."""
+    x, w = np.polynomial.legendre.leggauss(n_freq)
+    omega = omega_scale * (1.0 + x) / (1.0 - x)
+    weight = 2.0 * omega_scale * w / (1.0 - x) ** 2
+    return omega, weight
+
+
+def frequencies(p: Params) -> tuple[torch.Tensor, torch.Tensor]:
+    """Column 0 is omega = 0 (needed for the SCS radii), then the quadrature nodes."""
+    om, w = quadrature(p.n_freq, p.omega_scale)
+    omega = torch.tensor(np.concatenate([[0.0], om]), dtype=_DT)
+    weight = torch.tensor(np.concatenate([[0.0], w]), dtype=_DT)
+    return omega, weight
+
+
+# ----------------------------------------------------------------------------------------
+# free-atom quantities (Sec. II.B)
+# ----------------------------------------------------------------------------------------
+def free_atom(species, nu, table, omega):
+    """alpha_bar_i(omega) (Eq. bar-alpha), sigma_i(omega), R_vdW,i.
+
+    omega_i = 4 C6 / (3 alpha0^2); alpha_bar = alpha0 nu / (1 + (omega/omega_i)^2);
+    sigma_i = (sqrt(2/pi) alpha_bar / 3)^(1/3); R_vdW,i = R0 nu^(1/3).
+    """
+    tab = torch.as_tensor(table, dtype=_DT)
+    sp = torch.as_tensor(np.asarray(species), dtype=torch.long)
+    nu = torch.as_tensor(nu, dtype=_DT)
+    a0, c6, r0 = tab[sp, 0], tab[sp, 1], tab[sp, 2]
+    om_i = 4.0 * c6 / (3.0 * a0 * a0)
+    alpha_bar = (a0 * nu)[:, None] / (1.0 + (omega[None, :] / om_i[:, None]) ** 2)
+    sigma = (math.sqrt(2.0 / math.pi) * alpha_bar / 3.0) ** (1.0 / 3.0)
+    r_vdw = r0 * nu ** (1.0 / 3.0)
+    return alpha_bar, sigma, r_vdw, a0, r0
+
+
+# ----------------------------------------------------------------------------------------
+# pair functions (Sec. II.B and III)
+# ----------------------------------------------------------------------------------------
+def fermi(r, s, d):
+    """Damping f(r, S) = 1 / (1 + exp[-d (r/S - 1)]) (Eq. damping-function)."""
+    return 1.0 / (1.0 + torch.exp(-d * (r / s - 1.0)))
+
+
+def cutoff_buffer(r, rc, rb):
+    """f_SR / f_LR: 1 below rc - rb, 1 - 3t^2 + 2t^3 in the buffer, 0 beyond rc."""
+    t = (r - rc + rb) / rb
+    mid = 1.0 - 3.0 * t * t + 2.0 * t * t * t
+    return torch.where(r < rc - rb, torch.ones_like(r), torch.where(r < rc, mid, torch.zeros_like(r)))
+
+
+def f_inner(r, r_in):
+    """f_inner = 3 (r/r_in)^2 - 2 (r/r_in)^3 below r_in, else 1 (Sec. III.B)."""
+    u = r / r_in
+    return torch.where(r < r_in, 3.0 * u * u - 2.0 * u * u * u, torch.ones_like(r))
+
+
+def f_scs(r, r_scs):
+    """f_SCS = 3 (r/r_SCS)^2 - 2 (r/r_SCS)^3 (Eq. full-pol)."""
+    u = r / r_scs
+    return 3.0 * u * u - 2.0 * u * u * u
+
+
+def dipole_T(rvec):
+    """T_ij = d/dr d/dr (1/r) = (3 r r^T - delta r^2) / r^5, rvec = r_j - r_i (bohr)."""
+    r2 = (rvec * rvec).sum(-1)
+    r = torch.sqrt(r2)
+    outer = rvec[..., :, None] * rvec[..., None, :]
+    eye = torch.eye(3, dtype=_DT)
+    return (3.0 * outer - r2[..., None, None] * eye) / (r ** 5)[..., None, None]
+
+
+def dipole_T_sr_bare(rvec, sigma_ij):
+    """d/dr_i d/dr_j [erf(r/sigma)/r] = -T g + h (Eqs. T_SR, g-func, h-func), undamped."""
+    r2 = (rvec * rvec).sum(-1)
+    r = torch.sqrt(r2)
+    x = r / sigma_ij
+    ex = torch.exp(-x * x)
+    g = torch.special.erf(x) - 2.0 / math.sqrt(math.pi) * x * ex
+    hfac = 4.0 / math.sqrt(math.pi) * x ** 3 * ex
+    outer = rvec[..., :, None] * rvec[..., None, :]
+    h = hfac[..., None, None] * outer / (r ** 5)[..., None, None]
+    return -dipole_T(rvec) * g[..., None, None] + h
+
+
+# ----------------------------------------------------------------------------------------
+# sites: every periodic image within r_list of the central atom is its own site
+# ----------------------------------------------------------------------------------------
+@dataclass
+class Sites:
+    atom: torch.Tensor      # (n,) long
+    shift: torch.Tensor     # (n, 3) long lattice shift
+    r_ang: torch.Tensor     # (n,) distance to the centre, Angstrom (no grad)
+    n1: int                 # |K1| = #sites with r < r_SCS (prefix)
+    ns: int                 # #sites with r < r_sphere (prefix)
+    n12: int                # #sites with r < 2 r_SCS (prefix; K2 = [n1, n12))
+
+
+def enumerate_sites(positions: np.ndarray, cell: np.ndarray | None, k: int, p: Params) -> Sites:
+    """Brute force over all atoms and all lattice shifts; sorted by (r, atom, shift)."""
+    pos = np.asarray(positions, dtype=np.float64)
+    n = pos.shape[0]
+    rl = p.r_list
+    if cell is None:
+        shifts = np.zeros((1, 3), dtype=np.int64)
+    else:
+        cell = np.asarray(cell, dtype=np.float64)
+        inv = np.linalg.inv(cell)
+        frac = pos @ inv
+        dfrac = frac - frac[k]
+        vol = abs(np.linalg.det(cell))
+        width = np.array([vol / np.linalg.norm(np.cross(cell[(i + 1) % 3], cell[(i + 2) % 3]))
+                          for i in range(3)])
+        reach = rl / width
+        lo = np.floor(-reach - dfrac.max(axis=0)).astype(np.int64) - 1
+        hi = np.ceil(reach - dfrac.min(axis=0)).astype(np.int64) + 1
+        grids = np.meshgrid(*[np.arange(lo[i], hi[i] + 1) for i in range(3)], indexing="ij")
+        shifts = np.stack([g.ravel() for g in grids], axis=1)
+    atoms = np.repeat(np.arange(n), shifts.shape[0])
+    sh = np.tile(shifts, (n, 1))
+    if cell is None:
+        disp = pos[atoms] - pos[k]
+    else:
+        disp = pos[atoms] + sh @ cell - pos[k]
+    r2 = np.einsum("ij,ij->i", disp, disp)
+    keep = r2 < rl * rl
+    atoms, sh, r2 = atoms[keep], sh[keep], r2[keep]
+    order = np.lexsort((sh[:, 2], sh[:, 1], sh[:, 0], atoms, r2))
+    atoms, sh, r2 = atoms[order], sh[order], r2[order]
+    if atoms[0] != k or r2[0] != 0.0 or (len(r2) > 1 and r2[1] == 0.0):
+        raise ValueError("central atom must be the unique site at distance zero")
+    n1 = int(np.sum(r2 < p.r_scs ** 2))
+    ns = int(np.sum(r2 < p.sphere ** 2))
+    n12 = int(np.sum(r2 < (2.0 * p.r_scs) ** 2))
+    return Sites(torch.as_tensor(atoms), torch.as_tensor(sh), torch.as_tensor(np.sqrt(r2)), n1, ns, n12)
+
+
+def site_positions(P: torch.Tensor, cell, s: Sites, k: int) -> torch.Tensor:
+    """Site displacement from the central atom, in bohr (differentiable in P, Angstrom)."""
+    if cell is None:
+        disp = P[s.atom] - P[k]
+    else:
+        disp = P[s.atom] + s.shift.to(_DT) @ torch.as_tensor(cell, dtype=_DT) - P[k]
+    return disp / BOHR_ANGSTROM
+
+
+# ----------------------------------------------------------------------------------------
+# local SCS solve (Sec. III.B, Eq. local_pol)
+# ----------------------------------------------------------------------------------------
+def scs_local(x, s: Sites, alpha_bar, sigma, r_vdw, p: Params):
+    """Solve B_K alpha_K = d_K for all frequencies.
+
+    x: (n_sites, 3) bohr displacements of the sites.  Returns X with shape
+    (Q, 3 n1, 3) and alpha_K (Q, n1) = Tr(X_i)/3 (Eq. after Eq. polarizabilities).
+    """
+    n1, n12 = s.n1, s.n12
+    r_scs = p.r_scs / BOHR_ANGSTROM
+    r_b = p.r_buf / BOHR_ANGSTROM
+    r_in = p.r_inner / BOHR_ANGSTROM
+    Q = alpha_bar.shape[1]
+    a = alpha_bar[s.atom]          # (n_sites, Q)
+    sg = sigma[s.atom]
+    rv = r_vdw[s.atom]
+
+    # coupled pairs i != j inside K1
+    ii, jj = torch.meshgrid(torch.arange(n1), torch.arange(n1), indexing="ij")
+    off = ii != jj
+    ii, jj = ii[off], jj[off]
+    diag = 1.0 / a[:n1].T                                   # (Q, n1): 1/alpha_bar_i on the diagonal
+    eye3 = torch.eye(3, dtype=_DT)
+    B = torch.diag_embed(diag.repeat_interleave(3, dim=1))
+    if len(ii):
+        rvec = x[jj] - x[ii]
+        r = torch.sqrt((rvec * rvec).sum(-1))
+        s_ij = p.beta * (rv[ii] + rv[jj])
+        damp = (1.0 - fermi(r, s_ij, p.d)) * cutoff_buffer(r, r_scs, r_b)
+        sig_ij = torch.sqrt(sg[ii] ** 2 + sg[jj] ** 2)          # (npair, Q)
+        tsr = dipole_T_sr_bare(rvec[:, None, :].expand(-1, Q, -1), sig_ij) * damp[:, None, None, None]
+        blocks = torch.zeros(Q, n1, n1, 3, 3, dtype=_DT)
+        blocks = blocks.index_put((torch.arange(Q)[:, None], ii[None, :], jj[None, :]),
+                                  tsr.permute(1, 0, 2, 3))
+        B = B + blocks.permute(0, 1, 3, 2, 4).reshape(Q, 3 * n1, 3 * n1)
+
+    # right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j
+    d = eye3.repeat(n1, 1)[None].expand(Q, -1, -1).clone()
+    n2 = n12 - n1
+    if n2 > 0:
+        ii, jj = torch.meshgrid(torch.arange(n1), torch.arange(n1, n12), indexing="ij")
+        ii, jj = ii.reshape(-1), jj.reshape(-1)
+        rvec = x[jj] - x[ii]
+        r = torch.sqrt((rvec * rvec).sum(-1))
+        s_ij = p.beta * (rv[ii] + rv[jj])
+        damp = (1.0 - fermi(r, s_ij, p.d)) * cutoff_buffer(r, r_scs, r_b) * f_inner(r, r_in)
+        sig_ij = torch.sqrt(sg[ii] ** 2 + sg[jj] ** 2)
+        tsr = dipole_T_sr_bare(rvec[:, None, :].expand(-1, Q, -1), sig_ij) * damp[:, None, None, None]
+        contrib = tsr * a[jj][:, :, None, None]              # (npair, Q, 3, 3)
+        acc = torch.zeros(n1, Q, 3, 3, dtype=_DT).index_add(0, ii, contrib)
+        d = d - acc.permute(1, 0, 2, 3).reshape(Q, 3 * n1, 3)
+
+    X = torch.linalg.solve(B, d)
+    alpha_K = X.reshape(Q, n1, 3, 3).diagonal(dim1=-2, dim2=-1).sum(-1) / 3.0
+    return X, alpha_K, B, d
+
+
+# ----------------------------------------------------------------------------------------
+# local energy (Sec. III.A, Eq. E_k)
+# ----------------------------------------------------------------------------------------
+def blend(alpha_K, alpha_I_sites, r_bohr, p: Params):
+    """Eq. full-pol: (1 - f_SCS) alpha_K + f_SCS alpha_I inside r_SCS, alpha_I outside.
+
+    alpha_K: (Q, n1) for the K1 prefix; alpha_I_sites: (n, Q); r_bohr: (n,).
+    """
+    n = alpha_I_sites.shape[0]
+    n1 = alpha_K.shape[1]
+    r_scs = p.r_scs / BOHR_ANGSTROM
+    out = alpha_I_sites.clone()
+    m = min(n1, n)
+    fs = f_scs(r_bohr[:m], r_scs)[:, None]
+    out[:m] = (1.0 - fs) * alpha_K.T[:m] + fs * alpha_I_sites[:m]
+    return out
+
+
+def t_lr(x, alpha0_tilde, a0, r0, p: Params):
+    """T_LR,K (3n x 3n): f_LR(r; r_MBD,p) f(r, S~) T with p = 1 on the central row/column."""
+    n = x.shape[0]
+    r_b = p.r_buf / BOHR_ANGSTROM
+    r1 = p.r_mbd1 / BOHR_ANGSTROM
+    r2c = p.r_mbd2 / BOHR_ANGSTROM
+    r_t = r0 * (alpha0_tilde / a0) ** (1.0 / 3.0)            # Eq. scaled-rvdw
+    ii, jj = torch.meshgrid(torch.arange(n), torch.arange(n), indexing="ij")
+    off = ii != jj
+    ii, jj = ii[off], jj[off]
+    T = torch.zeros(n, n, 3, 3, dtype=_DT)
+    if len(ii):
+        rvec = x[jj] - x[ii]
+        r = torch.sqrt((rvec * rvec).sum(-1))
+        s_t = p.beta * (r_t[ii] + r_t[jj])
+        central = (ii == 0) | (jj == 0)
+        rc = torch.where(central, torch.full_like(r, r1), torch.full_like(r, r2c))
+        flr = cutoff_buffer(r, rc, r_b)
+        blk = dipole_T(rvec) * (flr * fermi(r, s_t, p.d))[:, None, None]
+        T = T.index_put((ii, jj), blk)
+    return T.permute(0, 2, 1, 3).reshape(3 * n, 3 * n)
+
+
+def local_energy(T, alpha_tilde, weight, p: Params):
+    """E_k in Hartree: sum_q w_q/(2 pi) sum_n c_n Tr{g_k G^(n-2) g_k^T}, c_n = -1/n.
+
+    The central site is site 0, so g_k is rows 0..2 of G = sqrt(A) T sqrt(A).
+    In log mode the k-block trace of ln(1 - G) from eigh replaces the series.
+    """
+    e = torch.zeros((), dtype=_DT)
+    for q in range(1, alpha_tilde.shape[1]):
+        dq = torch.sqrt(alpha_tilde[:, q]).repeat_interleave(3)
+        G = dq[:, None] * T * dq[None, :]
+        if p.series_order is None:
+            lam, V = torch.linalg.eigh(G)
+            term = (V[:3, :] ** 2 * torch.log1p(-lam)[None, :]).sum()
+        else:
+            gk = G[:3, :]
+            y = gk.T
+            term = torch.zeros((), dtype=_DT)
+            for n in range(2, p.series_order + 1):
+                term = term + (-1.0 / n) * torch.trace(gk @ y)
+                y = G @ y
+        e = e + weight[q] / (2.0 * math.pi) * term
+    return e
+
+
+# ----------------------------------------------------------------------------------------
+# drivers
+# ----------------------------------------------------------------------------------------
+class System:
+    """Holds the inputs and caches site lists."""
+
+    def __init__(self, positions, cell, species, hirshfeld, table, params: Params):
+        self.pos = np.asarray(positions, dtype=np.float64)
+        self.cell = None if cell is None else np.asarray(cell, dtype=np.float64)
+        self.species = np.asarray(species)
+        self.nu = np.asarray(hirshfeld, dtype=np.float64)
+        self.table = np.asarray(table, dtype=np.float64)
+        self.p = params
+        self.omega, self.weight = frequencies(params)
+        self._sites: dict[int, Sites] = {}
+
+    @property
+    def n(self) -> int:
+        return self.pos.shape[0]
+
+    def sites(self, k: int) -> Sites:
+        if k not in self._sites:
+            self._sites[k] = enumerate_sites(self.pos, self.cell, k, self.p)
+        return self._sites[k]
+
+    def free(self):
+        return free_atom(self.species, self.nu, self.table, self.omega)
+
+    def central_alpha(self, atoms, P=None) -> dict[int, torch.Tensor]:
+        """alpha_I,a(omega) for the listed atoms: the centre block of each atom's own solve."""
+        P = torch.as_tensor(self.pos) if P is None else P
+        ab, sg, rv, _, _ = self.free()
+        out = {}
+        for a in atoms:
+            s = self.sites(a)
+            x = site_positions(P, self.cell, s, a)
+            _, aK, _, _ = scs_local(x, s, ab, sg, rv, self.p)
+            out[a] = aK[:, 0]
+        return out
+
+    def energy_of_centre(self, k, P, alpha_I: dict[int, torch.Tensor]):
+        ab, sg, rv, a0, r0 = self.free()
+        s = self.sites(k)
+        x = site_positions(P, self.cell, s, k)
+        _, aK, _, _ = scs_local(x, s, ab, sg, rv, self.p)
+        ns = s.ns
+        aI = torch.stack([alpha_I[int(a)] for a in s.atom[:ns]])
+        # distance to the centre (site 0 sits at the origin; keep sqrt away from zero)
+        rb = torch.cat([torch.zeros(1, dtype=_DT), torch.sqrt((x[1:ns] * x[1:ns]).sum(-1))])
+        at = blend(aK, aI, rb, self.p)
+        T = t_lr(x[:ns], at[:, 0], a0[s.atom[:ns]], r0[s.atom[:ns]], self.p)
+        return local_energy(T, at, self.weight, self.p) * HARTREE_EV
+
+    def energies(self, centres=None) -> np.ndarray:
+        """Per-atom energies E_k in eV for the listed centres (default all)."""
+        centres = list(range(self.n)) if centres is None else [int(c) for c in centres]
+        need = sorted({int(a) for k in centres for a in self.sites(k).atom[: self.sites(k).ns]})
+        P = torch.as_tensor(self.pos)
+        with torch.no_grad():
+            aI = self.central_alpha(need, P)
+            return np.array([float(self.energy_of_centre(k, P, aI)) for k in centres])
+
+    def energies_forces(self, centres=None, weights=None):
+        """Energies (eV) of the centres and F = -d(sum_k w_k E_k)/dR (eV/Angstrom), all atoms."""
+        centres = list(range(self.n)) if centres is None else [int(c) for c in centres]
+        w = np.ones(len(centres)) if weights is None else np.asarray(weights, dtype=np.float64)
+        need = sorted({int(a) for k in centres for a in self.sites(k).atom[: self.sites(k).ns]})
+        P0 = torch.as_tensor(self.pos)
+        with torch.no_grad():
+            aI0 = self.central_alpha(need, P0)
+        grad = torch.zeros_like(P0)
+        seed = {a: torch.zeros_like(aI0[a]) for a in need}
+        energies = []
+        for k, wk in zip(centres, w):
+            P = P0.clone().requires_grad_(True)
+            leaves = {a: aI0[a].clone().requires_grad_(True) for a in
+                      {int(b) for b in self.sites(k).atom[: self.sites(k).ns]}}
+            e = self.energy_of_centre(k, P, leaves)
+            energies.append(float(e.detach()))
+            if wk == 0.0:
+                continue
+            (wk * e).backward()
+            grad += P.grad
+            for a, t in leaves.items():
+                if t.grad is not None:
+                    seed[a] += t.grad
+        for a in need:
+            if torch.count_nonzero(seed[a]) == 0:
+                continue
+            P = P0.clone().requires_grad_(True)
+            aI = self.central_alpha([a], P)[a]
+            (aI * seed[a]).sum().backward()
+            grad += P.grad
+        return np.array(energies), (-grad).numpy()
+
+
+def with_params(p: Params, **kw) -> Params:
+    return replace(p, **kw)

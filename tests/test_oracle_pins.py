@@ -1,0 +1,427 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test names what fixes the expected value: a closed form, a derivative
+identity checked by autograd, the full (non-local) MBD limit computed by a
+global solve and an eigendecomposition, an invariance, or finite differences.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import BOHR_ANGSTROM as BOHR, HARTREE_EV as HA
+from paper_2407_06409_gb300 import inputs
+
+DT = torch.float64
+
+
+def _double_factorial(n):
+    return 1 if n <= 0 else n * _double_factorial(n - 2)
+
+
+# ---------------------------------------------------------------------------------------
+# constants printed in the paper
+# ---------------------------------------------------------------------------------------
+def test_paper_constants_match_defaults():
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+    vals = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            vals[k.strip()] = float(v)
+    p = oracle.Params()
+    for k, v in vals.items():
+        assert getattr(p, k) == v, k
+
+
+# ---------------------------------------------------------------------------------------
+# quadrature: closed-form Lorentzian integrals (Casimir-Polder form of C6)
+# ---------------------------------------------------------------------------------------
+def test_quadrature_lorentzian_product():
+    a, b = 0.31, 1.7
+    exact = 0.5 * math.pi * a * b / (a + b)
+    for n, tol in ((80, 1e-12), (40, 1e-9)):
+        om, w = oracle.quadrature(n, 0.6)
+        val = np.sum(w / ((1 + (om / a) ** 2) * (1 + (om / b) ** 2)))
+        assert abs(val / exact - 1) < tol, (n, val, exact)
+    # nodes and weights agree with an independent Golub-Welsch construction
+    n = 12
+    k = np.arange(1, n)
+    beta = k / np.sqrt(4.0 * k * k - 1.0)
+    J = np.diag(beta, 1) + np.diag(beta, -1)
+    x, V = np.linalg.eigh(J)
+    wgl = 2.0 * V[0] ** 2
+    om, w = oracle.quadrature(n, 0.6)
+    assert np.allclose(om, 0.6 * (1 + x) / (1 - x), rtol=1e-13)
+    assert np.allclose(w, 1.2 * wgl / (1 - x) ** 2, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# pair tensors: derivative identities (autograd Hessians of the scalar potentials)
+# ---------------------------------------------------------------------------------------
+def test_dipole_tensor_is_hessian_of_inverse_distance():
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        r = torch.tensor(rng.normal(size=3) * 3.0, dtype=DT)
+        H = torch.autograd.functional.hessian(lambda v: 1.0 / torch.linalg.norm(v), r)
+        T = oracle.dipole_T(r)
+        assert torch.allclose(T, H, rtol=1e-12, atol=1e-14)
+
+
+def test_short_range_tensor_is_mixed_derivative_of_erf_potential():
+    rng = np.random.default_rng(2)
+    for _ in range(6):
+        ri = torch.tensor(rng.normal(size=3), dtype=DT)
+        rj = torch.tensor(rng.normal(size=3) * 2.5, dtype=DT)
+        sigma = float(rng.uniform(0.8, 2.5))
+
+        def phi(v):
+            d = v[3:] - v[:3]
+            r = torch.linalg.norm(d)
+            return torch.special.erf(r / sigma) / r
+
+        H = torch.autograd.functional.hessian(phi, torch.cat([ri, rj]))
+        mixed = H[:3, 3:]                      # d/dr_i d/dr_j
+        T = oracle.dipole_T_sr_bare(rj - ri, torch.tensor(sigma, dtype=DT))
+        assert torch.allclose(T, mixed, rtol=1e-11, atol=1e-13)
+
+
+def test_cutoff_functions_are_c1_switches():
+    rc, rb = 5.0, 0.5
+    r = torch.tensor([rc - rb, rc - 1e-12, rc + 0.1, 1.0], dtype=DT, requires_grad=True)
+    f = oracle.cutoff_buffer(r, rc, rb)
+    fv = f.detach()
+    assert abs(float(fv[0]) - 1) < 1e-15 and abs(float(fv[1])) < 1e-10 and float(fv[2]) == 0 and float(fv[3]) == 1
+    (g,) = torch.autograd.grad(f.sum(), r)
+    assert abs(float(g[0])) < 1e-12 and abs(float(g[1])) < 1e-9
+    # inside the buffer it decreases monotonically
+    rr = torch.linspace(rc - rb, rc, 101, dtype=DT)
+    ff = oracle.cutoff_buffer(rr, rc, rb)
+    assert torch.all(ff[1:] <= ff[:-1])
+    ri = torch.tensor([0.0, 2.0 - 1e-12, 2.5], dtype=DT, requires_grad=True)
+    fi = oracle.f_inner(ri, 2.0)
+    fiv = fi.detach()
+    assert float(fiv[0]) == 0 and abs(float(fiv[1]) - 1) < 1e-11 and float(fiv[2]) == 1
+    (gi,) = torch.autograd.grad(fi.sum(), ri)
+    assert abs(float(gi[1])) < 1e-9
+    rs = torch.tensor([0.0, 5.0], dtype=DT, requires_grad=True)
+    fs = oracle.f_scs(rs, 5.0)
+    assert float(fs.detach()[0]) == 0 and abs(float(fs.detach()[1]) - 1) < 1e-15
+    (gs,) = torch.autograd.grad(fs.sum(), rs)
+    assert abs(float(gs[0])) < 1e-15 and abs(float(gs[1])) < 1e-14
+
+
+# ---------------------------------------------------------------------------------------
+# dimer closed forms (screening switched off exactly: K1 = {k}, K2 empty)
+# ---------------------------------------------------------------------------------------
+def _dimer(r_ang, table, species, nu, p):
+    pos = np.array([[0.0, 0.0, 0.0], [0.3, -0.4, 1.0]])
+    pos[1] *= r_ang / np.linalg.norm(pos[1])
+    return oracle.System(pos, None, species, nu, table, p)
+
+
+def _lorentz(table, s, nu):
+    a0, c6, r0 = table[s]
+    return a0 * nu, 4 * c6 / (3 * a0 * a0), r0 * nu ** (1 / 3)
+
+
+def test_dimer_two_body_is_casimir_polder_c6():
+    table = np.array([[6.0, 20.0, 3.2], [10.0, 44.0, 3.8]])
+    nu = np.array([0.8, 0.93])
+    r_ang = 3.4
+    p = oracle.Params(r_scs=1.0, r_mbd1=10, r_mbd2=10, r_sphere=10, series_order=2, n_freq=120)
+    e = _dimer(r_ang, table, np.array([0, 1]), nu, p).energies()
+    a1, w1, R1 = _lorentz(table, 0, nu[0])
+    a2, w2, R2 = _lorentz(table, 1, nu[1])
+    c6 = 1.5 * a1 * a2 * w1 * w2 / (w1 + w2)
+    r = r_ang / BOHR
+    f = 1 / (1 + math.exp(-6 * (r / (0.83 * (R1 + R2)) - 1)))
+    exact = -f * f * c6 / r ** 6 * HA                 # London form, Eq. london-dispersion
+    assert abs(e.sum() / exact - 1) < 1e-10
+    assert abs(e[0] - e[1]) < 1e-14 * abs(exact)
+
+
+@pytest.mark.parametrize("nmax", [2, 3, 4, 6])
+def test_identical_dimer_series_closed_form(nmax):
+    table = np.array([[9.0, 30.0, 3.5]])
+    nu = np.array([0.9, 0.9])
+    r_ang = 2.3
+    p = oracle.Params(r_scs=1.0, r_mbd1=10, r_mbd2=10, r_sphere=10, series_order=nmax, n_freq=160)
+    e = _dimer(r_ang, table, np.array([0, 0]), nu, p).energies()
+    a, w0, R = _lorentz(table, 0, nu[0])
+    r = r_ang / BOHR
+    f = 1 / (1 + math.exp(-6 * (r / (0.83 * 2 * R) - 1)))
+    exact = 0.0
+    for n in range(2, nmax + 1, 2):
+        lor = 0.5 * math.pi * _double_factorial(2 * n - 3) / _double_factorial(2 * n - 2)
+        exact += (-1.0 / n) * (f * a) ** n * (2 ** n + 2) / r ** (3 * n) * w0 / (2 * math.pi) * lor
+    exact *= HA
+    assert abs(e[0] / exact - 1) < 1e-10, (e, exact)
+
+
+def test_identical_dimer_log_mode_is_coupled_oscillators():
+    table = np.array([[11.0, 25.0, 3.3]])
+    nu = np.array([1.0, 1.0])
+    r_ang = 2.0
+    p = oracle.Params(r_scs=0.9, r_mbd1=10, r_mbd2=10, r_sphere=10, series_order=None, n_freq=200)
+    e = _dimer(r_ang, table, np.array([0, 0]), nu, p).energies()
+    a, w0, R = _lorentz(table, 0, 1.0)
+    r = r_ang / BOHR
+    f = 1 / (1 + math.exp(-6 * (r / (0.83 * 2 * R) - 1)))
+    exact = 0.0
+    for tau in (2.0, -1.0, -1.0):
+        x = a * f * tau / r ** 3
+        exact += 0.5 * w0 * (math.sqrt(1 - x) + math.sqrt(1 + x) - 2)
+    exact *= HA
+    assert abs(e.sum() / exact - 1) < 1e-9, (e.sum(), exact)
+    # the log limit differs from the n_max = 6 series at the (a f tau)^8 level
+    p6 = oracle.with_params(p, series_order=6)
+    e6 = _dimer(r_ang, table, np.array([0, 0]), nu, p6).energies()
+    assert abs(e6.sum() / exact - 1) > 1e-9
+
+
+# ---------------------------------------------------------------------------------------
+# full-system limit: one sphere covers everything (Sec. III.A: "If the cutoff spans the
+# entire molecule ... the original MBD energy is retrieved exactly")
+# ---------------------------------------------------------------------------------------
+def _global_scs(pos_b, ab, sg, rv, p):
+    """Full SCS (Eq. polarizabilities) by a global solve, assembled pair by pair."""
+    n, Q = ab.shape
+    B = np.zeros((Q, 3 * n, 3 * n))
+    for q in range(Q):
+        for i in range(n):
+            B[q, 3 * i:3 * i + 3, 3 * i:3 * i + 3] = np.eye(3) / ab[i, q]
+            for j in range(n):
+                if i == j:
+                    continue
+                rv_ = torch.tensor(pos_b[j] - pos_b[i], dtype=DT)
+                r = float(torch.linalg.norm(rv_))
+                sig = math.sqrt(sg[i, q] ** 2 + sg[j, q] ** 2)
+                f = 1 / (1 + math.exp(-p.d * (r / (p.beta * (rv[i] + rv[j])) - 1)))
+                B[q, 3 * i:3 * i + 3, 3 * j:3 * j + 3] = (1 - f) * oracle.dipole_T_sr_bare(
+                    rv_, torch.tensor(sig, dtype=DT)).numpy()
+    d = np.tile(np.eye(3), (n, 1))
+    X = np.linalg.solve(B, np.broadcast_to(d, (Q, 3 * n, 3)))
+    return np.einsum("qiaa->qi", X.reshape(Q, n, 3, 3)) / 3.0
+
+
+def _global_g(pos_b, alpha, a0, r0, p):
+    """Full A_LR T_LR for every frequency (no cutoff function is active)."""
+    n, Q = alpha.shape
+    rt = r0 * (alpha[:, 0] / a0) ** (1 / 3)
+    T = np.zeros((3 * n, 3 * n))
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                d = pos_b[j] - pos_b[i]
+                r = np.linalg.norm(d)
+                f = 1 / (1 + math.exp(-p.d * (r / (p.beta * (rt[i] + rt[j])) - 1)))
+                T[3 * i:3 * i + 3, 3 * j:3 * j + 3] = f * (3 * np.outer(d, d) - r * r * np.eye(3)) / r ** 5
+    return [np.repeat(alpha[:, q], 3)[:, None] * T for q in range(Q)]
+
+
+@pytest.fixture(scope="module")
+def small_cluster():
+    s = inputs.cluster(9, radius=2.6, min_sep=1.2, n_species=3, seed=4)
+    return s
+
+
+def test_full_system_limit_scs_and_series(small_cluster):
+    s = small_cluster
+    p = oracle.Params(r_scs=20.0, r_mbd1=20.0, r_mbd2=20.0, r_sphere=20.0, series_order=6)
+    sysm = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table, p)
+    ab, sg, rv, a0, r0 = [t.numpy() for t in sysm.free()]
+    pos_b = s.positions / BOHR
+    alpha_full = _global_scs(pos_b, ab, sg, rv, p)           # (Q, n)
+    aI = sysm.central_alpha(range(s.n_atoms))
+    for a in range(s.n_atoms):
+        assert np.allclose(aI[a].numpy(), alpha_full[:, a], rtol=1e-12)
+    e = sysm.energies()
+    G = _global_g(pos_b, alpha_full.T, a0, r0, p)
+    w = sysm.weight.numpy()
+    tot = 0.0
+    for q in range(1, len(w)):
+        Gn = G[q].copy()
+        for n in range(2, 7):
+            Gn = Gn @ G[q]
+            tot += w[q] / (2 * math.pi) * (-1.0 / n) * np.trace(Gn)
+        assert abs(np.trace(G[q])) < 1e-14                # the n = 1 term vanishes
+    assert abs(e.sum() / (tot * HA) - 1) < 1e-11
+
+
+def test_full_system_limit_log_mode_is_full_mbd(small_cluster):
+    s = small_cluster
+    p = oracle.Params(r_scs=20.0, r_mbd1=20.0, r_mbd2=20.0, r_sphere=20.0, series_order=None)
+    sysm = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table, p)
+    ab, sg, rv, a0, r0 = [t.numpy() for t in sysm.free()]
+    pos_b = s.positions / BOHR
+    alpha_full = _global_scs(pos_b, ab, sg, rv, p)
+    G = _global_g(pos_b, alpha_full.T, a0, r0, p)
+    w = sysm.weight.numpy()
+    e_mbd = 0.0
+    for q in range(1, len(w)):
+        lam = np.linalg.eigvals(G[q])                         # non-symmetric A T (Eq. E_MBD)
+        e_mbd += w[q] / (2 * math.pi) * np.sum(np.log(1 - lam)).real
+    e = sysm.energies()
+    assert abs(e.sum() / (e_mbd * HA) - 1) < 1e-11
+
+
+# ---------------------------------------------------------------------------------------
+# local SCS: the matrix solution satisfies the paper's fixed-point form with the K2 shell
+# ---------------------------------------------------------------------------------------
+def test_local_scs_satisfies_fixed_point_equation():
+    s = inputs.box(60, seed=3)
+    p = oracle.Params(r_scs=3.5, r_mbd1=4.0, r_mbd2=4.0, r_sphere=4.0)
+    sysm = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p)
+    ab, sg, rv, _, _ = sysm.free()
+    k = 7
+    st = sysm.sites(k)
+    x = oracle.site_positions(torch.as_tensor(s.positions), s.cell, st, k).numpy()
+    X, aK, _, _ = oracle.scs_local(torch.as_tensor(x), st, ab, sg, rv, p)
+    assert st.n12 > st.n1 > 1
+    q = 3
+    a = ab[st.atom, q].numpy()
+    sgs = sg[st.atom, q].numpy()
+    rvs = rv[st.atom].numpy()
+    Xq = X[q].numpy().reshape(st.n1, 3, 3)
+    rsc, rb, rin = p.r_scs / BOHR, p.r_buf / BOHR, p.r_inner / BOHR
+    for i in range(st.n1):
+        acc = np.eye(3)
+        for j in range(st.n12):
+            if j == i:
+                continue
+            d = x[j] - x[i]
+            r = np.linalg.norm(d)
+            if r >= rsc:
+                continue
+            t = (r - rsc + rb) / rb
+            fsr = 1.0 if r < rsc - rb else 1 - 3 * t * t + 2 * t ** 3
+            fin = 1.0
+            if j >= st.n1 and r < rin:
+                fin = 3 * (r / rin) ** 2 - 2 * (r / rin) ** 3
+            f = 1 / (1 + math.exp(-p.d * (r / (p.beta * (rvs[i] + rvs[j])) - 1)))
+            Tij = fin * fsr * (1 - f) * oracle.dipole_T_sr_bare(
+                torch.tensor(d, dtype=DT), torch.tensor(math.hypot(sgs[i], sgs[j]), dtype=DT)).numpy()
+            other = Xq[j] if j < st.n1 else a[j] * np.eye(3)
+            acc = acc - Tij @ other
+        assert np.allclose(Xq[i], a[i] * acc, rtol=1e-11, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# symmetrisation conserves the k-block trace (Sec. III.A, after Eq. polynomial-fit)
+# ---------------------------------------------------------------------------------------
+def test_symmetrised_series_equals_unsymmetrised(small_cluster):
+    s = small_cluster
+    p = oracle.Params(r_scs=2.0, r_mbd1=4.0, r_mbd2=3.0, r_sphere=6.0, series_order=6)
+    sysm = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table, p)
+    ab, sg, rv, a0, r0 = sysm.free()
+    k = 2
+    st = sysm.sites(k)
+    P = torch.as_tensor(s.positions)
+    x = oracle.site_positions(P, None, st, k)
+    _, aK, _, _ = oracle.scs_local(x, st, ab, sg, rv, p)
+    aI = sysm.central_alpha([int(a) for a in st.atom[:st.ns]])
+    r = torch.cat([torch.zeros(1, dtype=DT), torch.linalg.norm(x[1:st.ns], dim=1)])
+    at = oracle.blend(aK, torch.stack([aI[int(a)] for a in st.atom[:st.ns]]), r, p)
+    T = oracle.t_lr(x[:st.ns], at[:, 0], a0[st.atom[:st.ns]], r0[st.atom[:st.ns]], p).numpy()
+    e = float(oracle.local_energy(torch.as_tensor(T), at, sysm.weight, p))
+    ref = 0.0
+    for q in range(1, at.shape[1]):
+        G = np.repeat(at[:, q].numpy(), 3)[:, None] * T            # A T, not symmetric
+        for n in range(2, 7):
+            ref += sysm.weight[q].item() / (2 * math.pi) * (-1.0 / n) * np.trace(
+                np.linalg.matrix_power(G, n)[:3, :3])
+    assert abs(e / ref - 1) < 1e-12
+    assert float(sysm.energies([k])[0]) == pytest.approx(e * HA, rel=1e-13)
+
+
+# ---------------------------------------------------------------------------------------
+# the two-body energy does not depend on the secondary radius (Sec. IV.E)
+# ---------------------------------------------------------------------------------------
+def test_two_body_energy_independent_of_secondary_radius():
+    s = inputs.box(50, seed=5)
+    ref = None
+    for r2 in (2.0, 3.0, 4.5):
+        p = oracle.Params(r_scs=3.0, r_mbd1=4.5, r_mbd2=r2, r_sphere=4.5, series_order=2)
+        e = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p).energies([0, 1, 2])
+        if ref is None:
+            ref = e
+        assert np.allclose(e, ref, rtol=1e-14, atol=0)
+    p3 = oracle.Params(r_scs=3.0, r_mbd1=4.5, r_mbd2=2.0, r_sphere=4.5, series_order=3)
+    e3 = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p3).energies([0, 1, 2])
+    p3b = oracle.with_params(p3, r_mbd2=4.0)
+    e3b = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p3b).energies([0, 1, 2])
+    assert not np.allclose(e3, e3b, rtol=1e-8)
+
+
+# ---------------------------------------------------------------------------------------
+# invariances and forces
+# ---------------------------------------------------------------------------------------
+_P_SMALL = oracle.Params(r_scs=3.0, r_mbd1=4.0, r_mbd2=3.5, r_sphere=4.0, series_order=6)
+
+
+def test_rotation_translation_permutation_invariance():
+    s = inputs.cluster(14, radius=3.5, seed=7)
+    base = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table, _P_SMALL)
+    e0, f0 = base.energies_forces()
+    rng = np.random.default_rng(0)
+    Qm, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    pos = s.positions @ Qm.T + np.array([1.3, -7.0, 2.2])
+    perm = rng.permutation(s.n_atoms)
+    sysr = oracle.System(pos[perm], None, s.species[perm], s.hirshfeld[perm], s.table, _P_SMALL)
+    e1, f1 = sysr.energies_forces()
+    assert np.allclose(e1, e0[perm], rtol=1e-11, atol=1e-15)
+    assert np.allclose(f1, (f0 @ Qm.T)[perm], rtol=1e-9, atol=1e-13)
+    assert np.abs(f0.sum(0)).max() < 1e-13
+
+
+def test_periodic_image_shift_invariance():
+    s = inputs.box(40, seed=2)
+    p = _P_SMALL
+    e0 = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p).energies([0, 5, 9])
+    pos = s.positions.copy()
+    pos[5] += s.cell[0] - 2 * s.cell[2]
+    e1 = oracle.System(pos, s.cell, s.species, s.hirshfeld, s.table, p).energies([0, 5, 9])
+    assert np.allclose(e0, e1, rtol=1e-12)
+
+
+def _site_sets(sysm, centres):
+    out = []
+    for k in centres:
+        st = sysm.sites(k)
+        out.append((st.n1, st.ns, st.n12, tuple(st.atom.tolist())))
+    return out
+
+
+def test_forces_match_central_finite_differences():
+    s = inputs.box(36, seed=11, jitter=0.05)
+    p = _P_SMALL
+    sysm = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p)
+    _, F = sysm.energies_forces()
+    assert np.abs(F.sum(0)).max() < 1e-12
+    h = 1e-4
+    rng = np.random.default_rng(3)
+    checked = 0
+    ref_sets = _site_sets(sysm, range(s.n_atoms))
+    for a in rng.choice(s.n_atoms, 8, replace=False):
+        for g in range(3):
+            es = []
+            ok = True
+            for sgn in (1, -1):
+                pos = s.positions.copy()
+                pos[a, g] += sgn * h
+                sp = oracle.System(pos, s.cell, s.species, s.hirshfeld, s.table, p)
+                if _site_sets(sp, range(s.n_atoms)) != ref_sets:
+                    ok = False
+                    break
+                es.append(sp.energies().sum())
+            if not ok:
+                continue
+            fd = -(es[0] - es[1]) / (2 * h)
+            assert abs(fd - F[a, g]) < 2e-8 + 1e-6 * abs(F[a, g]), (a, g, fd, F[a, g])
+            checked += 1
+    assert checked >= 10
