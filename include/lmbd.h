@@ -1,0 +1,172 @@
+/* lmbd.h — C ABI of the GB300 (sm_103a) lMBD library.
+ *
+ * lMBD is the atom-wise, linear-scaling many-body dispersion model of
+ * Muhli, Ala-Nissila and Caro, arXiv 2407.06409.  For every atom k ("central
+ * atom") the library
+ *   1. gathers the sites (atoms and their periodic images) within the cutoffs
+ *      (Sec. III.A, sets K; Sec. III.B, sets K1 and K2),
+ *   2. builds the short-range dipole tensors T_SR(omega) and solves the local
+ *      screening system B_K alpha_K = d_K at omega = 0 and at every quadrature
+ *      frequency (Sec. III.B, Eq. local_pol),
+ *   3. blends local and central polarisabilities (Eq. full-pol), forms the SCS
+ *      radii (Eq. scaled-rvdw) and the long-range tensor T_LR with the cutoff
+ *      function f_LR (Sec. III.A),
+ *   4. evaluates the local energy E_k as the k-block trace of the truncated
+ *      series sum_n c_n G^n, c_n = -1/n, G = sqrt(A) T_LR sqrt(A) (Eq. E_k),
+ *      integrated over imaginary frequency by Gauss-Legendre quadrature,
+ *   5. optionally returns forces, the exact gradient -d(sum_k w_k E_k)/dR at
+ *      fixed Hirshfeld ratios, by a hand-written adjoint of steps 2-4.
+ *
+ * Units: positions and cell in Angstrom; species parameters in atomic units
+ * (alpha0 in bohr^3, C6 in Ha bohr^6, R_vdW in bohr); energies in eV; forces
+ * in eV/Angstrom (CODATA 2018 bohr and hartree).
+ *
+ * Memory: every array argument may be a device pointer or a host pointer; the
+ * library asks the CUDA runtime which one it is.  Host arrays are copied to and
+ * from the device inside the call (on the given stream, which is then
+ * synchronised).  The caller owns every array; the context owns its device
+ * workspaces (grown on demand with cudaMalloc) and frees them in lmbd_destroy.
+ *
+ * Errors: every entry point returns an int status (LMBD_OK = 0); no exception
+ * or longjmp crosses the ABI.  After an error the outputs are unspecified and
+ * the context stays usable.  A context is not thread-safe: calls on one
+ * context must be serialised by the caller.
+ */
+#ifndef LMBD_H
+#define LMBD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LMBD_OK            0
+#define LMBD_EINVAL        1  /* bad argument: sizes, NaN input, coincident atoms, bad cutoffs   */
+#define LMBD_ENOMEM        2  /* device allocation failed                                         */
+#define LMBD_NOT_SPD       3  /* a screening matrix B_K had a non-positive Cholesky pivot        */
+#define LMBD_ECUDA         4  /* a CUDA runtime call failed                                       */
+#define LMBD_ECAPACITY     5  /* more sites around one atom than the kernels support             */
+#define LMBD_EUNSUPPORTED  6  /* option not supported (e.g. series order out of range)           */
+
+#define LMBD_MAX_FREQ      64 /* maximum number of quadrature frequencies                        */
+#define LMBD_MAX_ORDER     10 /* maximum series order n_max                                      */
+
+typedef struct lmbd_ctx lmbd_ctx;
+
+/* Free-atom reference data of one species (Sec. II.B, Eq. bar-alpha and after). */
+typedef struct {
+  double alpha0;   /* static free-atom polarisability alpha^atom, bohr^3     */
+  double c6;       /* free-atom C6^atom, Ha bohr^6                            */
+  double r0;       /* free-atom vdW radius R_vdW^atom, bohr                   */
+} lmbd_species;
+
+/* Model parameters.  Radii in Angstrom.
+ *   r_scs     SCS radius: K1 = B(r_SCS), K2 = B(2 r_SCS) \ B(r_SCS)      (Sec. III.B)
+ *   r_mbd1    primary MBD radius: couplings of the central atom          (Sec. III.A)
+ *   r_mbd2    secondary MBD radius: couplings between other sites        (Sec. III.A)
+ *   r_sphere  radius of the local MBD sphere K; <= 0 selects the paper's
+ *             r_MBD = r_mbd1 + r_mbd2
+ *   r_buf     buffer width r_b of f_SR and f_LR (~0.5 Angstrom)          (Sec. III.A)
+ *   r_inner   inner buffer of f_inner (2 Angstrom in the paper)          (Sec. III.B)
+ *   beta, d   damping parameters (0.83 and 6)                            (Sec. II.B)
+ *   omega_scale  L of the quadrature map omega = L (1 + x) / (1 - x), Ha
+ * Requirements: 0 < r_scs <= sphere radius, r_buf > 0, r_inner > 0.           */
+typedef struct {
+  double r_scs, r_mbd1, r_mbd2, r_sphere, r_buf, r_inner, beta, d, omega_scale;
+} lmbd_params;
+
+/* Phases of one call, in launch order (index into the lmbd_stats arrays). */
+#define LMBD_PHASE_NEIGHBORS   0  /* free-atom terms, cell list, site lists, offsets          */
+#define LMBD_PHASE_SCS         1  /* T_SR assembly + Cholesky + solves, all atoms/frequencies */
+#define LMBD_PHASE_PREPARE     2  /* blend, SCS radii, T_LR, first Krylov block               */
+#define LMBD_PHASE_CHAIN       3  /* Krylov products v_{m+1} = D T D v_m                       */
+#define LMBD_PHASE_ENERGY      4  /* k-block traces and quadrature                            */
+#define LMBD_PHASE_ADJ_SERIES  5  /* series adjoint: dL/dalpha~, pair-matrix factors          */
+#define LMBD_PHASE_ADJ_PAIR    6  /* pair matrix and dT_LR/dr contraction                     */
+#define LMBD_PHASE_ADJ_BLEND   7  /* SCS-radius and blend adjoint                             */
+#define LMBD_PHASE_ADJ_SCS     8  /* adjoint SCS solves and dT_SR/dr contraction              */
+#define LMBD_PHASE_OUTPUT      9  /* unit conversion and copies of the outputs                */
+#define LMBD_NPHASE           10
+
+/* Per-call statistics of the last lmbd_energy_forces call.  flops count the dense
+ * linear algebra of each phase from the actual site counts (Cholesky n^3/3, two
+ * triangular solves 6 n^2 per frequency, 2 n^2 k per product of an n x n with an
+ * n x k matrix); ms are device times from CUDA events on the call's stream and are
+ * filled only when profiling is on (lmbd_set_profiling), in batched launch mode. */
+typedef struct {
+  double flops[LMBD_NPHASE];
+  double ms[LMBD_NPHASE];
+  int launches[LMBD_NPHASE];
+  double bytes_workspace;  /* device workspace in use, bytes                                */
+  long long n_sites;       /* total sites over all central atoms (within the list radius)  */
+  int max_k1, max_sphere, max_sites; /* largest K1, sphere and site-list capacity           */
+  int kernel_launches;     /* kernels launched by the call                                  */
+} lmbd_stats;
+
+/* Fill *out with the defaults r_scs = 5, r_mbd1 = r_mbd2 = r_sphere = 7,
+ * r_buf = 0.5, r_inner = 2, beta = 0.83, d = 6, omega_scale = 0.6.          */
+int lmbd_default_params(lmbd_params* out);
+
+/* Create a context.  species: n_species entries (host memory, copied).
+ * n_freq: quadrature points (1..LMBD_MAX_FREQ); series_order: n_max
+ * (2..LMBD_MAX_ORDER).  On success *out receives the context.               */
+int lmbd_create(const lmbd_species* species, int n_species, const lmbd_params* params,
+                int n_freq, int series_order, lmbd_ctx** out);
+
+/* Per-atom energies and (optionally) forces of one structure.
+ *   n_atoms      N >= 0
+ *   positions    N x 3 row-major, Angstrom
+ *   cell         3 x 3 row-major lattice vectors (rows), Angstrom; NULL = no periodicity
+ *   species      N indices into the species table
+ *   hirshfeld    N Hirshfeld volume ratios nu_i > 0
+ *   energies     out, N per-atom energies E_k, eV (may be NULL)
+ *   forces       out, N x 3, eV/Angstrom, -d(sum_k E_k)/dR; NULL = energies only
+ *   stream       cudaStream_t to run on (NULL = legacy default stream)
+ * The call is complete (outputs written) when it returns.                   */
+int lmbd_energy_forces(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell,
+                       const int* species, const double* hirshfeld, double* energies,
+                       double* forces, void* stream);
+
+/* As lmbd_energy_forces, but forces = -d(sum_k w_k E_k)/dR for caller weights
+ * w (N entries; NULL = all ones).  This is the vector-Jacobian product that
+ * a reverse-mode autograd backward needs.                                   */
+int lmbd_energy_forces_weighted(lmbd_ctx* ctx, int n_atoms, const double* positions,
+                                const double* cell, const int* species,
+                                const double* hirshfeld, const double* energy_weights,
+                                double* energies, double* forces, void* stream);
+
+/* Launch mode: LMBD_LAUNCH_BATCHED (default) processes all atoms in each
+ * kernel launch; LMBD_LAUNCH_PER_ATOM launches every per-atom kernel once per
+ * central atom (the plain one-launch-per-atom form, same arithmetic).       */
+#define LMBD_LAUNCH_BATCHED  0
+#define LMBD_LAUNCH_PER_ATOM 1
+int lmbd_set_launch_mode(lmbd_ctx* ctx, int mode);
+
+/* Per-phase device timing with CUDA events (0 = off, the default). */
+int lmbd_set_profiling(lmbd_ctx* ctx, int on);
+
+/* Central polarisabilities alpha_I,k(omega) of the last call (Sec. III.B):
+ * N x (n_freq + 1) row-major; column 0 is omega = 0, then the quadrature
+ * nodes in increasing order.  out: device or host.                          */
+int lmbd_get_central_polarizabilities(lmbd_ctx* ctx, double* out, void* stream);
+
+/* Site counts of the last call, N x 4 int32 row-major:
+ * |K1| (r < r_SCS, includes the atom), |sphere| (r < sphere radius),
+ * |K1 u K2| (r < 2 r_SCS), all sites within max(2 r_SCS, sphere radius).   */
+int lmbd_get_site_counts(lmbd_ctx* ctx, int* out, void* stream);
+
+/* Quadrature nodes (Ha) and weights of the context; host arrays of n_freq. */
+int lmbd_get_quadrature(const lmbd_ctx* ctx, double* omega, double* weight);
+
+/* Statistics of the last call (host struct). */
+int lmbd_get_stats(const lmbd_ctx* ctx, lmbd_stats* out);
+
+/* Destroy the context and free its device memory.  NULL is accepted. */
+int lmbd_destroy(lmbd_ctx* ctx);
+
+/* Static, human-readable text for a status code. */
+const char* lmbd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMBD_H */

@@ -1,0 +1,505 @@
+// Stage 2: local MBD energy of every central atom (Sec. III.A) and its adjoint.
+//
+// For central atom k with sphere sites s = 0..ns-1 (s = 0 is k):
+//   alpha~_s(omega) = (1 - f_SCS(r_s)) alpha_K,s + f_SCS(r_s) alpha_I,a(s)  if r_s < r_SCS,
+//                     alpha_I,a(s) otherwise                              (Eq. full-pol)
+//   R~_s = R0 (alpha~_s(0)/alpha0)^(1/3), S~_st = beta (R~_s + R~_t)        (Eq. scaled-rvdw)
+//   T_LR,st = f_LR(r_st; r_MBD,p) f(r_st, S~_st) T_st, p = 1 on the central row/column
+//   G(omega) = D T_LR D, D = diag(sqrt(alpha~(omega)))                    (Eq. G_frequency)
+//   E_k = sum_q w_q/(2 pi) sum_{n=2}^{n_max} (-1/n) Tr[G^n]_kk                 (Eq. E_k)
+// The k-block traces use Krylov blocks v_m = G^m e_k (3 ns x 3 per frequency): all
+// quadrature frequencies share T_LR, so v_{m+1} = D (T (D v_m)) is one product of T with
+// a 3 ns x 3 n_freq block, and Tr[G^n]_kk = <v_a, v_b> with a + b = n.
+//
+// Adjoint (exact gradient of L = sum_k w_k E_k):
+//   dL/dG = sum_n c_n sum_{j=0}^{n-1} v_j v_{n-1-j}^T (G symmetric),
+//   dL/dalpha~_s = (1/alpha~_s) Tr[(dL/dG) G]_ss = (1/alpha~_s) sum_n c_n sum_j <v_j[s], v_{n-j}[s]>,
+//   dL/dT_st = sum_q D_s D_t (dL/dG)_st, contracted with dT_LR/dr and dT_LR/dS~ per pair.
+#include "lmbd_internal.cuh"
+
+// ---------------------------------------------------------------------------------------
+// prepare: blended polarisabilities, SCS radii, T_LR and the first Krylov block
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mbd_prepare(Work w, DevParams p, int c0, int max_ns) {
+  extern __shared__ double smem_d[];
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const Counts cn = w.counts[c];
+  const int ns = cn.ns, n1 = cn.n1, N = 3 * ns;
+  double* xs = smem_d;                 // 3 x max_ns
+  double* rt = xs + 3 * max_ns;        // max_ns
+  const int tid = threadIdx.x;
+  const long long sbase = (long long)c * w.site_cap;
+  const long long offs = w.off_s[c], offk1 = w.off_k1[c];
+  const double rscs = p.r_scs;
+  for (int s = tid; s < ns; s += blockDim.x) {
+    int a = w.site_atom[sbase + s];
+    double x0 = w.site_x[3 * (sbase + s)], x1 = w.site_x[3 * (sbase + s) + 1], x2 = w.site_x[3 * (sbase + s) + 2];
+    xs[s] = x0; xs[max_ns + s] = x1; xs[2 * max_ns + s] = x2;
+    double fs = 0.0;
+    if (s < n1 && s > 0) {
+      double u = sqrt(x0 * x0 + x1 * x1 + x2 * x2) / rscs;
+      fs = 3.0 * u * u - 2.0 * u * u * u;
+    }
+    for (int q = 0; q < p.nq; ++q) {
+      double aI = w.alphaI[(long long)a * p.nq + q];
+      double at = aI;
+      if (s < n1) at = (1.0 - fs) * w.alphaK[(offk1 + s) * p.nq + q] + fs * aI;
+      w.alphaT[(offs + s) * p.nq + q] = at;
+      w.dsq[(offs + s) * p.nq + q] = sqrt(at);
+    }
+    rt[s] = w.r0[a] * cbrt(w.alphaT[(offs + s) * p.nq] / w.a0[a]);
+  }
+  __syncthreads();
+  double* T = w.tlr + w.off_t[c];
+  // diagonal blocks are zero
+  for (int e = tid; e < ns * 9; e += blockDim.x) {
+    int s = e / 9, t = e % 9;
+    T[(long long)(3 * s + t / 3) * N + 3 * s + t % 3] = 0.0;
+  }
+  const int npair = ns * (ns - 1) / 2;
+  for (int e = tid; e < npair; e += blockDim.x) {
+    int i = (int)((sqrtf(8.0f * e + 1.0f) + 1.0f) * 0.5f);
+    while (i * (i - 1) / 2 > e) --i;
+    while ((i + 1) * i / 2 <= e) ++i;
+    int j = e - i * (i - 1) / 2;     // i > j
+    double rr[3] = {xs[j] - xs[i], xs[max_ns + j] - xs[max_ns + i], xs[2 * max_ns + j] - xs[2 * max_ns + i]};
+    double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+    double rc = (j == 0) ? p.r_mbd1 : p.r_mbd2;
+    double blk[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (r2 < rc * rc) {
+      double r = sqrt(r2);
+      double flr, dflr, f, dfr, dfs;
+      cutoff_buf(r, rc, p.r_buf, flr, dflr);
+      fermi(r, p.beta * (rt[i] + rt[j]), p.d, f, dfr, dfs);
+      double C = flr * f;
+      double ir2 = 1.0 / r2;
+      double ir3 = ir2 / r;
+      double ir5 = ir3 * ir2;
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be)
+          blk[al][be] = C * (3.0 * rr[al] * rr[be] * ir5 - (al == be ? ir3 : 0.0));
+    }
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+      for (int be = 0; be < 3; ++be) {
+        T[(long long)(3 * i + al) * N + 3 * j + be] = blk[al][be];
+        T[(long long)(3 * j + al) * N + 3 * i + be] = blk[al][be];
+      }
+  }
+  __threadfence_block();
+  __syncthreads();
+  // v_1 = G e_k: column block of the central site, scaled by D_s D_0 (per frequency)
+  const int ncv = 3 * p.n_freq;
+  double* V1 = w.vkr + (offs * 3) * ncv;
+  for (int e = tid; e < N * ncv; e += blockDim.x) {
+    int row = e / ncv, col = e % ncv;
+    int s = row / 3, q = col / 3 + 1, be = col % 3;
+    double d = w.dsq[(offs + s) * p.nq + q] * w.dsq[offs * p.nq + q];
+    V1[(long long)row * ncv + col] = d * T[(long long)row * N + be];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// chain: v_{m+1} = D (T (D v_m)), one block per (central atom, 64-row tile)
+// ---------------------------------------------------------------------------------------
+#define CH_R 64
+#define CH_K 32
+#define CH_C 36
+
+__global__ void __launch_bounds__(256) k_mbd_chain(Work w, DevParams p, int m, int c0, int tiles_per_c) {
+  __shared__ double Ts[CH_R][CH_K + 1];
+  __shared__ double Ws[CH_K][CH_C];
+  const int c = c0 + blockIdx.x / tiles_per_c;
+  const int tile = blockIdx.x % tiles_per_c;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns, N = 3 * ns;
+  const int row0 = tile * CH_R;
+  if (row0 >= N) return;
+  const long long offs = w.off_s[c];
+  const int ncv = 3 * p.n_freq;
+  const double* T = w.tlr + w.off_t[c];
+  const double* Vin = w.vkr + (long long)(m - 1) * w.vstride + (offs * 3) * ncv;
+  double* Vout = w.vkr + (long long)m * w.vstride + (offs * 3) * ncv;
+  const double* dsq = w.dsq + offs * p.nq;
+  const int tid = threadIdx.x;
+  const int tr = tid % CH_R, cg = tid / CH_R;     // row in tile, column group (4 x 9)
+  for (int cc0 = 0; cc0 < ncv; cc0 += CH_C) {
+    const int ncc = min(CH_C, ncv - cc0);
+    double acc[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) acc[j] = 0.0;
+    for (int k0 = 0; k0 < N; k0 += CH_K) {
+      __syncthreads();
+      for (int e = tid; e < CH_R * CH_K; e += blockDim.x) {
+        int rr = e / CH_K, kk = e % CH_K;
+        int gr = row0 + rr, gk = k0 + kk;
+        Ts[rr][kk] = (gr < N && gk < N) ? T[(long long)gr * N + gk] : 0.0;
+      }
+      for (int e = tid; e < CH_K * CH_C; e += blockDim.x) {
+        int kk = e / CH_C, cl = e % CH_C;
+        int gk = k0 + kk, gc = cc0 + cl;
+        double v = 0.0;
+        if (gk < N && cl < ncc) v = dsq[(gk / 3) * p.nq + gc / 3 + 1] * Vin[(long long)gk * ncv + gc];
+        Ws[kk][cl] = v;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < CH_K; ++kk) {
+        double t = Ts[tr][kk];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) acc[j] += t * Ws[kk][cg * 9 + j];
+      }
+    }
+    const int gr = row0 + tr;
+    if (gr < N) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        int gc = cc0 + cg * 9 + j;
+        if (cg * 9 + j < ncc) Vout[(long long)gr * ncv + gc] = dsq[(gr / 3) * p.nq + gc / 3 + 1] * acc[j];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// energy: tr_{n,q} = <v_a, v_b>_q (a + b = n) and E_k = sum_q cw_q sum_n (-1/n) tr_{n,q}
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0) {
+  // deterministic: one thread per column sums all rows in order, then a fixed-order
+  // sum over the three columns of each frequency
+  __shared__ double red[LMBD_MAX_ORDER_P1][3 * 64];
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns, N = 3 * ns;
+  const long long offs = w.off_s[c];
+  const int ncv = 3 * p.n_freq;
+  const int tid = threadIdx.x;
+  for (int col = tid; col < ncv; col += blockDim.x) {
+    double acc[LMBD_MAX_ORDER_P1];
+#pragma unroll
+    for (int n = 0; n < LMBD_MAX_ORDER_P1; ++n) acc[n] = 0.0;
+    for (int row = 0; row < N; ++row) {
+      for (int n = 2; n <= p.order; ++n) {
+        int a = n / 2, b = n - a;
+        const double* Va = w.vkr + (long long)(a - 1) * w.vstride + (offs * 3) * ncv;
+        const double* Vb = w.vkr + (long long)(b - 1) * w.vstride + (offs * 3) * ncv;
+        acc[n] += Va[(long long)row * ncv + col] * Vb[(long long)row * ncv + col];
+      }
+    }
+    for (int n = 2; n <= p.order; ++n) red[n][col] = acc[n];
+  }
+  __syncthreads();
+  __shared__ double epart[64];
+  if (tid < p.n_freq) {
+    int q = tid;
+    double e = 0.0;
+    for (int n = 2; n <= p.order; ++n) {
+      double tr = red[n][3 * q] + red[n][3 * q + 1] + red[n][3 * q + 2];
+      w.trbuf[((long long)c * (LMBD_MAX_ORDER_P1)) * 64 + n * 64 + q] = tr;
+      e += (-1.0 / n) * tr;
+    }
+    epart[q] = e * p.cweight[q + 1];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double e = 0.0;
+    for (int q = 0; q < p.n_freq; ++q) e += epart[q];
+    w.energies[c] = e;
+  }
+}
+
+void launch_mbd_prepare_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {
+  if (c1 <= c0) return;
+  size_t sm = sizeof(double) * 4 * (size_t)max_ns;
+  cudaFuncSetAttribute(k_mbd_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_mbd_prepare<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_ns);
+}
+
+void launch_mbd_chain_sized(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, cudaStream_t s) {
+  if (c1 <= c0) return;
+  int tiles = (3 * max_ns + CH_R - 1) / CH_R;
+  k_mbd_chain<<<(c1 - c0) * tiles, 256, 0, s>>>(w, p, m, c0, tiles);
+}
+
+void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_mbd_energy<<<c1 - c0, 256, 0, s>>>(w, p, c0);
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint, part 1 (one block per central atom): dL/dalpha~ from the series, the factors
+// P, Q of the pair matrix M' = P Q^T, and the central-column term X0
+//   c~_{n,q} = w_k cw_q (-1/n)
+//   a_j = sum_{l=1}^{n_max-1-j} c~_{j+l+1} v_l,  P_s = [D_qs v_j[s]],  Q_s = [D_qs a_j[s]]
+//   X0_s = sum_q D_qs D_q0 sum_n c~_n v_{n-1}[s]
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c0) {
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns;
+  const long long offs = w.off_s[c];
+  const int ncv = 3 * p.n_freq;
+  const int nm = p.order;
+  const double wk = w.weights ? w.weights[c] : 1.0;
+  const int tid = threadIdx.x;
+  const double* V0 = w.vkr + (offs * 3) * ncv;   // block of v_1, others at +vstride*(m-1)
+  // per (site, frequency) work items
+  for (int e = tid; e < ns * p.n_freq; e += blockDim.x) {
+    int s = e / p.n_freq, qq = e % p.n_freq, q = qq + 1;
+    double ct[LMBD_MAX_ORDER_P1];
+    for (int n = 0; n <= nm; ++n) ct[n] = (n >= 2) ? wk * p.cweight[q] * (-1.0 / n) : 0.0;
+    // inner products <v_j[s], v_l[s]> for 1 <= j <= l, j + l <= n_max
+    double ga = 0.0;
+    for (int n = 2; n <= nm; ++n) {
+      double sum = 0.0;
+      if (s == 0) sum += w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq];
+      for (int j = 1; j <= n - 1; ++j) {
+        const double* Va = V0 + (long long)(j - 1) * w.vstride;
+        const double* Vb = V0 + (long long)(n - j - 1) * w.vstride;
+        for (int al = 0; al < 3; ++al)
+          for (int be = 0; be < 3; ++be) {
+            long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
+            sum += Va[idx] * Vb[idx];
+          }
+      }
+      ga += ct[n] * sum;
+    }
+    w.gbar[(offs + s) * p.nq + q] = ga / w.alphaT[(offs + s) * p.nq + q];
+    // P and Q columns of this frequency
+    const double ds = w.dsq[(offs + s) * p.nq + q];
+    for (int j = 1; j <= nm - 2; ++j) {
+      const double* Vj = V0 + (long long)(j - 1) * w.vstride;
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be) {
+          long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
+          double a = 0.0;
+          for (int l = 1; l <= nm - 1 - j; ++l) a += ct[j + l + 1] * V0[(long long)(l - 1) * w.vstride + idx];
+          long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
+          w.pmat[o] = ds * Vj[idx];
+          w.qmat[o] = ds * a;
+        }
+    }
+  }
+  __syncthreads();
+  // X0_s (3 x 3) summed over frequencies
+  for (int e = tid; e < ns * 9; e += blockDim.x) {
+    int s = e / 9, al = (e % 9) / 3, be = e % 3;
+    double acc = 0.0;
+    for (int qq = 0; qq < p.n_freq; ++qq) {
+      int q = qq + 1;
+      double dd = w.dsq[(offs + s) * p.nq + q] * w.dsq[offs * p.nq + q];
+      double sum = 0.0;
+      for (int n = 2; n <= nm; ++n)
+        sum += wk * p.cweight[q] * (-1.0 / n) * V0[(long long)(n - 2) * w.vstride + (long long)(3 * s + al) * ncv + 3 * qq + be];
+      acc += dd * sum;
+    }
+    w.x0buf[(offs + s) * 9 + al * 3 + be] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint, part 2: pair matrix M_st = (P Q^T)_st (+ X0_s if t = 0) on 16 x 16 site tiles
+// of the lower triangle, contracted with dT_LR/dr (sites) and dT_LR/dS~ (SCS radii)
+// ---------------------------------------------------------------------------------------
+#define PT 16
+#define PK 16
+
+__global__ void __launch_bounds__(256) k_mbd_adj_pair(Work w, DevParams p, int c0, int tiles_per_c) {
+  __shared__ double Ps[3 * PT][PK + 1];
+  __shared__ double Qs[3 * PT][PK + 1];
+  __shared__ double xs[2][3][PT];
+  __shared__ double rts[2][PT];
+  __shared__ double gacc_s[2][PT][3];
+  __shared__ double racc_s[2][PT];
+  const int c = c0 + blockIdx.x / tiles_per_c;
+  int tile = blockIdx.x % tiles_per_c;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns;
+  const int nt = (ns + PT - 1) / PT;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int bi = 0;
+  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+  const int bj = tile - bi * (bi + 1) / 2;
+  const long long offs = w.off_s[c];
+  const long long sbase = (long long)c * w.site_cap;
+  const int tid = threadIdx.x;
+  const int ty = tid / PT, tx = tid % PT;
+  if (tid < 2 * PT) {
+    int side = tid / PT, l = tid % PT;
+    int s = (side == 0 ? bi : bj) * PT + l;
+    for (int d = 0; d < 3; ++d) xs[side][d][l] = s < ns ? w.site_x[3 * (sbase + s) + d] : 0.0;
+    double rt = 1.0;
+    if (s < ns) {
+      int a = w.site_atom[sbase + s];
+      rt = w.r0[a] * cbrt(w.alphaT[(offs + s) * p.nq] / w.a0[a]);
+    }
+    rts[side][l] = rt;
+    gacc_s[side][l][0] = gacc_s[side][l][1] = gacc_s[side][l][2] = 0.0;
+    racc_s[side][l] = 0.0;
+  }
+  const int s = bi * PT + ty, t = bj * PT + tx;
+  double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  const int ncol = w.ncol;
+  for (int k0 = 0; k0 < ncol; k0 += PK) {
+    __syncthreads();
+    for (int e = tid; e < 3 * PT * PK; e += blockDim.x) {
+      int rr = e / PK, kk = e % PK;
+      int gk = k0 + kk;
+      int sr = bi * PT * 3 + rr, tr = bj * PT * 3 + rr;
+      Ps[rr][kk] = (sr < 3 * ns && gk < ncol) ? w.pmat[(offs * 3 + sr) * (long long)ncol + gk] : 0.0;
+      Qs[rr][kk] = (tr < 3 * ns && gk < ncol) ? w.qmat[(offs * 3 + tr) * (long long)ncol + gk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < PK; ++kk) {
+      double a0 = Ps[3 * ty][kk], a1 = Ps[3 * ty + 1][kk], a2 = Ps[3 * ty + 2][kk];
+      double b0 = Qs[3 * tx][kk], b1 = Qs[3 * tx + 1][kk], b2 = Qs[3 * tx + 2][kk];
+      acc[0][0] += a0 * b0; acc[0][1] += a0 * b1; acc[0][2] += a0 * b2;
+      acc[1][0] += a1 * b0; acc[1][1] += a1 * b1; acc[1][2] += a1 * b2;
+      acc[2][0] += a2 * b0; acc[2][1] += a2 * b1; acc[2][2] += a2 * b2;
+    }
+  }
+  __syncthreads();
+  if (s < ns && t < ns && s > t) {
+    if (t == 0) {
+      const double* x0 = w.x0buf + (offs + s) * 9;
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) acc[al][be] += x0[al * 3 + be];
+    }
+    double rr[3] = {xs[1][0][tx] - xs[0][0][ty], xs[1][1][tx] - xs[0][1][ty], xs[1][2][tx] - xs[0][2][ty]};
+    double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+    double rc = (t == 0) ? p.r_mbd1 : p.r_mbd2;
+    if (r2 < rc * rc) {
+      double r = sqrt(r2);
+      double flr, dflr, f, dfr, dfs;
+      double St = p.beta * (rts[0][ty] + rts[1][tx]);
+      cutoff_buf(r, rc, p.r_buf, flr, dflr);
+      fermi(r, St, p.d, f, dfr, dfs);
+      double C = flr * f, dC = dflr * f + flr * dfr, CS = flr * dfs;
+      double M[6] = {acc[0][0], acc[1][1], acc[2][2], 0.5 * (acc[0][1] + acc[1][0]),
+                     0.5 * (acc[0][2] + acc[2][0]), 0.5 * (acc[1][2] + acc[2][1])};
+      double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2],
+                      M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
+                      M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
+      double trM = M[0] + M[1] + M[2];
+      double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
+      double ir2 = 1.0 / r2, ir = sqrt(ir2);
+      double ir3 = ir2 * ir, ir5 = ir3 * ir2, ir7 = ir5 * ir2;
+      double psi = 3.0 * rMr * ir5 - trM * ir3;
+      double radial = 2.0 * (dC * psi * ir + C * (-15.0 * rMr * ir7 + 3.0 * trM * ir5));
+      double tang = 2.0 * C * 6.0 * ir5;
+      double g[3] = {radial * rr[0] + tang * Mr[0], radial * rr[1] + tang * Mr[1], radial * rr[2] + tang * Mr[2]};
+      double sbar = 2.0 * CS * psi * p.beta;
+      atomicAdd(&gacc_s[1][tx][0], g[0]); atomicAdd(&gacc_s[1][tx][1], g[1]); atomicAdd(&gacc_s[1][tx][2], g[2]);
+      atomicAdd(&gacc_s[0][ty][0], -g[0]); atomicAdd(&gacc_s[0][ty][1], -g[1]); atomicAdd(&gacc_s[0][ty][2], -g[2]);
+      atomicAdd(&racc_s[0][ty], sbar);
+      atomicAdd(&racc_s[1][tx], sbar);
+    }
+  }
+  __syncthreads();
+  if (tid < 2 * PT) {
+    int side = tid / PT, l = tid % PT;
+    int ss = (side == 0 ? bi : bj) * PT + l;
+    if (ss < ns) {
+      int a = w.site_atom[sbase + ss];
+      atomic_add3(w.gacc + 3 * a, gacc_s[side][l][0], gacc_s[side][l][1], gacc_s[side][l][2]);
+      atomicAdd(&w.rbar[offs + ss], racc_s[side][l]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint, part 3 (one block per central atom): SCS-radius gradient into alpha~(0), then
+// through the blend (Eq. full-pol) into alpha_K (local) and alpha_I (global, atomics)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mbd_adj_blend(Work w, DevParams p, int c0) {
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const Counts cn = w.counts[c];
+  const int ns = cn.ns, n1 = cn.n1;
+  const long long offs = w.off_s[c], offk1 = w.off_k1[c];
+  const long long sbase = (long long)c * w.site_cap;
+  const int tid = threadIdx.x;
+  double g0[3] = {0.0, 0.0, 0.0};
+  for (int s = tid; s < ns; s += blockDim.x) {
+    int a = w.site_atom[sbase + s];
+    double at0 = w.alphaT[(offs + s) * p.nq];
+    double rt = w.r0[a] * cbrt(at0 / w.a0[a]);
+    double gb0 = w.rbar[offs + s] * rt / (3.0 * at0);
+    double x0 = w.site_x[3 * (sbase + s)], x1 = w.site_x[3 * (sbase + s) + 1], x2 = w.site_x[3 * (sbase + s) + 2];
+    double fs = 0.0, dfs = 0.0, r = 0.0;
+    if (s < n1 && s > 0) {
+      r = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+      double u = r / p.r_scs;
+      fs = 3.0 * u * u - 2.0 * u * u * u;
+      dfs = (6.0 * u - 6.0 * u * u) / p.r_scs;
+    }
+    double gr = 0.0;
+    for (int q = 0; q < p.nq; ++q) {
+      double g = (q == 0) ? gb0 : w.gbar[(offs + s) * p.nq + q];
+      if (s < n1) {
+        double aK = w.alphaK[(offk1 + s) * p.nq + q];
+        double aI = w.alphaI[(long long)a * p.nq + q];
+        w.alphaK_bar[(offk1 + s) * p.nq + q] = (1.0 - fs) * g;
+        if (fs != 0.0) atomicAdd(&w.alphaI_bar[(long long)a * p.nq + q], fs * g);
+        gr += dfs * (aI - aK) * g;
+      } else {
+        atomicAdd(&w.alphaI_bar[(long long)a * p.nq + q], g);
+      }
+    }
+    if (s < n1 && s > 0 && gr != 0.0) {
+      double ir = 1.0 / r;
+      double gx = gr * x0 * ir, gy = gr * x1 * ir, gz = gr * x2 * ir;
+      atomic_add3(w.gacc + 3 * a, gx, gy, gz);
+      g0[0] -= gx; g0[1] -= gy; g0[2] -= gz;
+    }
+  }
+  // the central site carries minus the sum of the f_SCS gradients
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) g0[d] += __shfl_xor_sync(0xffffffffu, g0[d], o);
+  if ((tid & 31) == 0) atomic_add3(w.gacc + 3 * c, g0[0], g0[1], g0[2]);
+}
+
+void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_mbd_adj_site<<<c1 - c0, 256, 0, s>>>(w, p, c0);
+}
+
+void launch_mbd_adj_pair(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {
+  if (c1 <= c0) return;
+  int nt = (max_ns + PT - 1) / PT;
+  int tiles = nt * (nt + 1) / 2;
+  k_mbd_adj_pair<<<(c1 - c0) * tiles, 256, 0, s>>>(w, p, c0, tiles);
+}
+
+void launch_mbd_adj_blend(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_mbd_adj_blend<<<c1 - c0, 256, 0, s>>>(w, p, c0);
+}
+
+void launch_mbd_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns,
+                              cudaStream_t s, int* launches) {
+  launch_mbd_adj_series(w, p, c0, c1, s);
+  launch_mbd_adj_pair(w, p, c0, c1, max_ns, s);
+  launch_mbd_adj_blend(w, p, c0, c1, s);
+  *launches += 3;
+}
+
+__global__ void k_forces_out(Work w, double* forces) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * w.n_atoms) return;
+  forces[i] = -w.gacc[i] * (1.0 / LMBD_BOHR);
+}
+
+void launch_forces_out(const Work& w, double* forces, cudaStream_t s) {
+  if (w.n_atoms == 0) return;
+  k_forces_out<<<(3 * w.n_atoms + 255) / 256, 256, 0, s>>>(w, forces);
+}

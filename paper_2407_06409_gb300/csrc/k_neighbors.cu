@@ -1,0 +1,369 @@
+// Neighbour search: free-atom quantities, cell list, per-centre site lists.
+//
+// A site is an atom together with a lattice shift (Sec. III.A: replicas are
+// captured in real space, so every periodic image inside a radius is its own
+// site).  Each central atom k gets the sites within
+// r_list = max(2 r_SCS, sphere radius), sorted by distance, so that
+//   K1 (r < r_SCS), the MBD sphere (r < r_sphere) and K1 u K2 (r < 2 r_SCS)
+// are prefixes of one list (Sec. III.A and III.B).  Set membership compares
+// squared distances in Angstrom against squared radii in Angstrom.
+#include "lmbd_internal.cuh"
+
+// ---------------------------------------------------------------------------------------
+// free-atom quantities (Sec. II.B): alpha_bar_i(omega) = alpha0 nu / (1 + (omega/omega_i)^2),
+// omega_i = 4 C6 / (3 alpha0^2), sigma_i = (sqrt(2/pi) alpha_bar / 3)^(1/3), R_i = R0 nu^(1/3)
+// ---------------------------------------------------------------------------------------
+__global__ void k_free_atom(Work w, DevParams p) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= w.n_atoms) return;
+  int s = w.species[a];
+  double nu = w.nu[a];
+  double a0 = w.table[3 * s + 0], c6 = w.table[3 * s + 1], r0 = w.table[3 * s + 2];
+  double om = 4.0 * c6 / (3.0 * a0 * a0);
+  const double c = 0.26596152026762182;  // sqrt(2/pi)/3
+  for (int q = 0; q < p.nq; ++q) {
+    double u = p.omega[q] / om;
+    double ab = a0 * nu / (1.0 + u * u);
+    w.abar[a * p.nq + q] = ab;
+    w.sig[a * p.nq + q] = cbrt(c * ab);
+  }
+  w.rvdw[a] = r0 * cbrt(nu);
+  w.a0[a] = a0;
+  w.r0[a] = r0;
+}
+
+void launch_free_atom(const Work& w, const DevParams& p, cudaStream_t s) {
+  if (w.n_atoms == 0) return;
+  k_free_atom<<<(w.n_atoms + 127) / 128, 128, 0, s>>>(w, p);
+}
+
+// ---------------------------------------------------------------------------------------
+// cell list
+// ---------------------------------------------------------------------------------------
+// Non-periodic structures: bounding box and grid, computed on the device by one block.
+__global__ void k_bbox(Work w, Grid* g, double r_list) {
+  __shared__ double lo[3][256], hi[3][256];
+  double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
+  for (int a = threadIdx.x; a < w.n_atoms; a += blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      double v = w.pos[3 * a + d];
+      l[d] = fmin(l[d], v);
+      h[d] = fmax(h[d], v);
+    }
+  for (int d = 0; d < 3; ++d) { lo[d][threadIdx.x] = l[d]; hi[d][threadIdx.x] = h[d]; }
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int d = 0; d < 3; ++d) {
+        lo[d][threadIdx.x] = fmin(lo[d][threadIdx.x], lo[d][threadIdx.x + st]);
+        hi[d][threadIdx.x] = fmax(hi[d][threadIdx.x], hi[d][threadIdx.x + st]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < 3; ++d) {
+      double ext = hi[d][0] - lo[d][0];
+      int nc = (int)(ext / r_list);
+      if (nc < 1) nc = 1;
+      if (nc > 64) nc = 64;
+      double hh = ext / nc;
+      if (hh < r_list) hh = r_list;     // every cell at least r_list wide
+      g->origin[d] = lo[d][0];
+      g->h[d] = hh;
+      g->nc[d] = nc;
+      g->reach[d] = 1;
+    }
+  }
+}
+
+__global__ void k_bin(Work w, const Grid* __restrict__ gp) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= w.n_atoms) return;
+  const Grid& g = *gp;
+  double x[3] = {w.pos[3 * a], w.pos[3 * a + 1], w.pos[3 * a + 2]};
+  int ci[3];
+  if (g.periodic) {
+    double f[3];
+    for (int d = 0; d < 3; ++d) {
+      double v = x[0] * g.inv[0 * 3 + d] + x[1] * g.inv[1 * 3 + d] + x[2] * g.inv[2 * 3 + d];
+      v -= floor(v);
+      if (v >= 1.0) v = 0.0;
+      f[d] = v;
+      int c = (int)(v * g.nc[d]);
+      ci[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
+    }
+    for (int d = 0; d < 3; ++d)
+      w.wpos[3 * a + d] = f[0] * g.cell[0 * 3 + d] + f[1] * g.cell[1 * 3 + d] + f[2] * g.cell[2 * 3 + d];
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      int c = (int)((x[d] - g.origin[d]) / g.h[d]);
+      ci[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
+      w.wpos[3 * a + d] = x[d];
+    }
+  }
+  int cell = (ci[0] * g.nc[1] + ci[1]) * g.nc[2] + ci[2];
+  w.cell_of[a] = cell;
+  atomicAdd(&w.cell_count[cell], 1);
+}
+
+// Exclusive scan of cell_count into cell_start by one block; cell_count becomes
+// the scatter cursor (zeroed).
+__global__ void k_cell_scan(Work w, const Grid* __restrict__ gp) {
+  __shared__ int part[1024];
+  const Grid& g = *gp;
+  int n = g.nc[0] * g.nc[1] * g.nc[2];
+  int per = (n + blockDim.x - 1) / blockDim.x;
+  int b = threadIdx.x * per, e = min(n, b + per);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += w.cell_count[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int i = b; i < e; ++i) {
+    int c = w.cell_count[i];
+    w.cell_start[i] = run;
+    w.cell_count[i] = 0;
+    run += c;
+  }
+  if (threadIdx.x == blockDim.x - 1) w.cell_start[n] = run;
+}
+
+__global__ void k_scatter(Work w) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= w.n_atoms) return;
+  int c = w.cell_of[a];
+  int slot = atomicAdd(&w.cell_count[c], 1);
+  w.cell_atoms[w.cell_start[c] + slot] = a;
+}
+
+// ---------------------------------------------------------------------------------------
+// site lists: one block per central atom, candidates collected in shared memory and
+// bitonic-sorted by (r^2, atom, displacement)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool site_less(double ra, int aa, const double* xa, double rb, int ab,
+                                          const double* xb) {
+  if (ra != rb) return ra < rb;
+  if (aa != ab) return aa < ab;
+  if (xa[0] != xb[0]) return xa[0] < xb[0];
+  if (xa[1] != xb[1]) return xa[1] < xb[1];
+  return xa[2] < xb[2];
+}
+
+__global__ void k_sites(Work w, DevParams p, const Grid* __restrict__ gp, int c0) {
+  extern __shared__ unsigned char smem[];
+  const int cap = w.site_cap;                 // power of two
+  double* key = (double*)smem;                // cap
+  double* dx = key + cap;                     // cap x 3
+  int* at = (int*)(dx + 3 * cap);             // cap
+  __shared__ int cnt;
+  const Grid& g = *gp;
+  int k = c0 + blockIdx.x;
+  if (k >= w.n_atoms) return;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  double xk[3] = {w.wpos[3 * k], w.wpos[3 * k + 1], w.wpos[3 * k + 2]};
+  int ck = w.cell_of[k];
+  int ci[3] = {ck / (g.nc[1] * g.nc[2]), (ck / g.nc[2]) % g.nc[1], ck % g.nc[2]};
+  for (int ox = -g.reach[0]; ox <= g.reach[0]; ++ox)
+    for (int oy = -g.reach[1]; oy <= g.reach[1]; ++oy)
+      for (int oz = -g.reach[2]; oz <= g.reach[2]; ++oz) {
+        int o[3] = {ox, oy, oz};
+        int cc[3], img[3];
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+          int c = ci[d] + o[d];
+          if (g.periodic) {
+            int q = c >= 0 ? c / g.nc[d] : -((-c + g.nc[d] - 1) / g.nc[d]);
+            cc[d] = c - q * g.nc[d];
+            img[d] = q;
+          } else {
+            if (c < 0 || c >= g.nc[d]) ok = false;
+            cc[d] = c;
+            img[d] = 0;
+          }
+        }
+        if (!ok) continue;
+        double sh[3] = {0.0, 0.0, 0.0};
+        if (g.periodic)
+          for (int d = 0; d < 3; ++d)
+            sh[d] = img[0] * g.cell[0 * 3 + d] + img[1] * g.cell[1 * 3 + d] + img[2] * g.cell[2 * 3 + d];
+        int cell = (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
+        int b = w.cell_start[cell], e = w.cell_start[cell + 1];
+        for (int t = b + threadIdx.x; t < e; t += blockDim.x) {
+          int j = w.cell_atoms[t];
+          double d0 = w.wpos[3 * j + 0] + sh[0] - xk[0];
+          double d1 = w.wpos[3 * j + 1] + sh[1] - xk[1];
+          double d2 = w.wpos[3 * j + 2] + sh[2] - xk[2];
+          double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+          if (r2 < p.r2_list_ang) {
+            int slot = atomicAdd(&cnt, 1);
+            if (slot < cap) {
+              key[slot] = r2;
+              at[slot] = j;
+              dx[3 * slot + 0] = d0;
+              dx[3 * slot + 1] = d1;
+              dx[3 * slot + 2] = d2;
+            }
+          }
+        }
+      }
+  __syncthreads();
+  int n = cnt;
+  if (n > cap) {
+    if (threadIdx.x == 0) atomicOr(w.status, LMBD_FLAG_CAPACITY);
+    n = cap;
+  }
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = n + threadIdx.x; i < P; i += blockDim.x) {
+    key[i] = 1e300;
+    at[i] = 0x7fffffff;
+    dx[3 * i] = dx[3 * i + 1] = dx[3 * i + 2] = 0.0;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+        int lo = 2 * i - (i & (stride - 1));
+        int hi = lo + stride;
+        bool up = ((lo & size) == 0);
+        bool less = site_less(key[hi], at[hi], dx + 3 * hi, key[lo], at[lo], dx + 3 * lo);
+        if (less == up) {
+          double tk = key[lo]; key[lo] = key[hi]; key[hi] = tk;
+          int ta = at[lo]; at[lo] = at[hi]; at[hi] = ta;
+          for (int d = 0; d < 3; ++d) { double t = dx[3 * lo + d]; dx[3 * lo + d] = dx[3 * hi + d]; dx[3 * hi + d] = t; }
+        }
+      }
+      __syncthreads();
+    }
+  // write out and count the prefixes
+  __shared__ int c1, cs, c12;
+  if (threadIdx.x == 0) { c1 = 0; cs = 0; c12 = 0; }
+  __syncthreads();
+  long long base = (long long)k * cap;
+  const double ib = 1.0 / LMBD_BOHR;
+  int l1 = 0, ls = 0, l12 = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r2 = key[i];
+    w.site_atom[base + i] = at[i];
+    w.site_x[3 * (base + i) + 0] = dx[3 * i + 0] * ib;
+    w.site_x[3 * (base + i) + 1] = dx[3 * i + 1] * ib;
+    w.site_x[3 * (base + i) + 2] = dx[3 * i + 2] * ib;
+    l1 += r2 < p.r2_scs_ang;
+    ls += r2 < p.r2_sphere_ang;
+    l12 += r2 < p.r2_scs2_ang;
+  }
+  atomicAdd(&c1, l1);
+  atomicAdd(&cs, ls);
+  atomicAdd(&c12, l12);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    w.counts[k] = Counts{c1, cs, c12, n};
+    // the central atom must be the unique site at distance zero
+    if (n < 1 || at[0] != k || key[0] != 0.0 || (n > 1 && key[1] == 0.0))
+      atomicOr(w.status, LMBD_FLAG_COINCIDENT);
+  }
+}
+
+void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStream_t s, int* launches) {
+  if (w.n_atoms == 0) return;
+  Grid* gdev = w.grid;
+  cudaMemcpyAsync(gdev, &g, sizeof(Grid), cudaMemcpyHostToDevice, s);
+  if (!g.periodic) {
+    k_bbox<<<1, 256, 0, s>>>(w, gdev, sqrt(p.r2_list_ang));
+    ++*launches;
+  }
+  cudaMemsetAsync(w.cell_count, 0, sizeof(int) * w.ncells, s);
+  int nb = (w.n_atoms + 127) / 128;
+  k_bin<<<nb, 128, 0, s>>>(w, gdev);
+  k_cell_scan<<<1, 1024, 0, s>>>(w, gdev);
+  k_scatter<<<nb, 128, 0, s>>>(w);
+  size_t sm = (size_t)w.site_cap * (8 + 24 + 4);
+  cudaFuncSetAttribute(k_sites, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_sites<<<w.n_atoms, 256, sm, s>>>(w, p, gdev, 0);
+  *launches += 4;
+}
+
+// ---------------------------------------------------------------------------------------
+// per-centre offsets into the variable-size workspaces (one block, 64-bit scans)
+// totals: [0] sum n1, [1] sum ns, [2] sum nq (3 n1)^2, [3] sum (3 ns)^2,
+//         [4] max n1, [5] max ns, [6] max n12, [7] sum nt
+// ---------------------------------------------------------------------------------------
+__global__ void k_offsets(Work w, int nq) {
+  __shared__ long long part[4][512];
+  __shared__ int mx[3][512];
+  __shared__ long long tot_nt[512];
+  int N = w.n_atoms;
+  int per = (N + blockDim.x - 1) / blockDim.x;
+  int b = threadIdx.x * per, e = min(N, b + per);
+  long long s[4] = {0, 0, 0, 0};
+  int m[3] = {0, 0, 0};
+  long long snt = 0;
+  for (int i = b; i < e; ++i) {
+    Counts c = w.counts[i];
+    s[0] += c.n1;
+    s[1] += c.ns;
+    s[2] += (long long)nq * 9 * c.n1 * c.n1;
+    s[3] += 9LL * c.ns * c.ns;
+    m[0] = max(m[0], c.n1);
+    m[1] = max(m[1], c.ns);
+    m[2] = max(m[2], c.n12);
+    snt += c.nt;
+  }
+  for (int t = 0; t < 4; ++t) part[t][threadIdx.x] = s[t];
+  for (int t = 0; t < 3; ++t) mx[t][threadIdx.x] = m[t];
+  tot_nt[threadIdx.x] = snt;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    long long v[4];
+    for (int t = 0; t < 4; ++t) v[t] = threadIdx.x >= off ? part[t][threadIdx.x - off] : 0;
+    __syncthreads();
+    for (int t = 0; t < 4; ++t) part[t][threadIdx.x] += v[t];
+    __syncthreads();
+  }
+  long long run[4];
+  for (int t = 0; t < 4; ++t) run[t] = part[t][threadIdx.x] - s[t];
+  for (int i = b; i < e; ++i) {
+    Counts c = w.counts[i];
+    w.off_k1[i] = run[0];
+    w.off_s[i] = run[1];
+    w.off_b[i] = run[2];
+    w.off_t[i] = run[3];
+    run[0] += c.n1;
+    run[1] += c.ns;
+    run[2] += (long long)nq * 9 * c.n1 * c.n1;
+    run[3] += 9LL * c.ns * c.ns;
+  }
+  // reductions of the maxima and of sum nt
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      for (int t = 0; t < 3; ++t) mx[t][threadIdx.x] = max(mx[t][threadIdx.x], mx[t][threadIdx.x + st]);
+      tot_nt[threadIdx.x] += tot_nt[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    w.off_k1[N] = part[0][threadIdx.x];
+    w.off_s[N] = part[1][threadIdx.x];
+    w.off_b[N] = part[2][threadIdx.x];
+    w.off_t[N] = part[3][threadIdx.x];
+    for (int t = 0; t < 4; ++t) w.totals[t] = part[t][threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    w.totals[4] = mx[0][0];
+    w.totals[5] = mx[1][0];
+    w.totals[6] = mx[2][0];
+    w.totals[7] = tot_nt[0];
+  }
+}
+
+void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s) {
+  if (w.n_atoms == 0) return;
+  k_offsets<<<1, 512, 0, s>>>(w, p.nq);
+}

@@ -1,0 +1,691 @@
+// Host engine and C ABI of the lMBD library (declared in include/lmbd.h).
+//
+// One call of lmbd_energy_forces runs, on one stream:
+//   free-atom quantities -> cell list and site lists -> per-centre offsets
+//   -> (one small device-to-host read of the sizes to size the workspaces)
+//   -> SCS solves for all centres and frequencies (stage 1)
+//   -> blend / T_LR / Krylov chain / energies (stage 2)
+//   -> [forces] series adjoint, pair contractions, blend adjoint, SCS adjoint
+// Every arithmetic step runs in the kernels of k_*.cu; the host only validates
+// arguments, sizes buffers and orders launches.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lmbd.h"
+#include "lmbd_internal.cuh"
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Ctx {
+  lmbd_params prm;
+  std::vector<double> table;     // S x 3
+  int n_species = 0;
+  int n_freq = 0, order = 0;
+  std::vector<double> omega, weight;   // quadrature (n_freq)
+  int launch_mode = LMBD_LAUNCH_BATCHED;
+  int profiling = 0;
+  cudaEvent_t ev[LMBD_NPHASE + 1] = {};
+  int site_cap = 0;
+  int last_n = 0;
+  lmbd_stats stats{};
+  // device buffers
+  DevBuf table_d, pos_d, species_d, nu_d, weights_d, out_e_d, out_f_d;
+  DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
+  DevBuf site_atom, site_x, counts, off_k1, off_s, off_b, off_t, totals, status;
+  DevBuf bmat, xsol, alphaK, alphaI, alphaT, dsq, tlr, vkr, energies, trbuf;
+  DevBuf gbar, pmat, qmat, x0buf, rbar, alphaK_bar, alphaI_bar, gacc;
+  long long* totals_h = nullptr;   // pinned
+  int* status_h = nullptr;         // pinned
+};
+
+int ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return LMBD_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  size_t want = bytes + bytes / 8;     // a little headroom for the next call
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return LMBD_ENOMEM;
+    }
+    want = bytes;
+  }
+  b.bytes = want;
+  return LMBD_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n,
+// then mapped to [0, inf) with omega = L (1 + x) / (1 - x).
+void gauss_legendre(int n, double L, std::vector<double>& om, std::vector<double>& w) {
+  std::vector<double> x(n), wx(n);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[n - 1 - i] = z;
+    wx[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  om.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    om[i] = L * (1.0 + x[i]) / (1.0 - x[i]);
+    w[i] = 2.0 * L * wx[i] / ((1.0 - x[i]) * (1.0 - x[i]));
+  }
+}
+
+double sphere_radius(const lmbd_params& p) { return p.r_sphere > 0 ? p.r_sphere : p.r_mbd1 + p.r_mbd2; }
+
+int next_pow2(long long v) {
+  int p = 1;
+  while (p < v && p < (1 << 20)) p <<= 1;
+  return p;
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) {                   \
+      cudaGetLastError();                       \
+      return LMBD_ECUDA;                        \
+    }                                           \
+  } while (0)
+#define TRY(x)                    \
+  do {                            \
+    int _st = (x);                \
+    if (_st != LMBD_OK) return _st; \
+  } while (0)
+
+int stage_input(DevBuf& buf, const void* src, size_t bytes, cudaStream_t s, const void** out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return LMBD_OK;
+  }
+  TRY(ensure(buf, bytes));
+  CK(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, s));
+  *out = buf.p;
+  return LMBD_OK;
+}
+
+int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec_in, const double* nu_in,
+        const double* w_in, double* e_out, double* f_out, cudaStream_t s) {
+  lmbd_stats st{};
+  c->stats = st;
+  c->last_n = N;
+  if (N == 0) return LMBD_OK;
+  const lmbd_params& P = c->prm;
+  const int nq = c->n_freq + 1;
+  const bool forces = f_out != nullptr;
+  int launches = 0;
+
+  // ---- inputs ---------------------------------------------------------------------------
+  const void *pos, *spec, *nu, *wts = nullptr;
+  TRY(stage_input(c->pos_d, pos_in, sizeof(double) * 3 * N, s, &pos));
+  TRY(stage_input(c->species_d, spec_in, sizeof(int) * N, s, &spec));
+  TRY(stage_input(c->nu_d, nu_in, sizeof(double) * N, s, &nu));
+  if (w_in) TRY(stage_input(c->weights_d, w_in, sizeof(double) * N, s, &wts));
+
+  // ---- parameters -------------------------------------------------------------------------
+  DevParams dp{};
+  const double ib = 1.0 / LMBD_BOHR;
+  const double rsph = sphere_radius(P);
+  const double rlist = fmax(2.0 * P.r_scs, rsph);
+  dp.r_scs = P.r_scs * ib;
+  dp.r_mbd1 = P.r_mbd1 * ib;
+  dp.r_mbd2 = P.r_mbd2 * ib;
+  dp.r_buf = P.r_buf * ib;
+  dp.r_inner = P.r_inner * ib;
+  dp.beta = P.beta;
+  dp.d = P.d;
+  dp.r2_scs_ang = P.r_scs * P.r_scs;
+  dp.r2_sphere_ang = rsph * rsph;
+  dp.r2_scs2_ang = 4.0 * P.r_scs * P.r_scs;
+  dp.r2_list_ang = rlist * rlist;
+  dp.n_freq = c->n_freq;
+  dp.nq = nq;
+  dp.order = c->order;
+  dp.n_species = c->n_species;
+  dp.omega[0] = 0.0;
+  dp.cweight[0] = 0.0;
+  const double pi = 3.14159265358979323846;
+  for (int q = 0; q < c->n_freq; ++q) {
+    dp.omega[q + 1] = c->omega[q];
+    dp.cweight[q + 1] = LMBD_HARTREE * c->weight[q] / (2.0 * pi);
+  }
+
+  // ---- search grid ------------------------------------------------------------------------
+  Grid g{};
+  double vol_est = 0.0;
+  if (cell) {
+    double hc[9];
+    if (is_device_ptr(cell)) {
+      CK(cudaMemcpyAsync(hc, cell, sizeof(hc), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    } else {
+      memcpy(hc, cell, sizeof(hc));
+    }
+    for (int i = 0; i < 9; ++i)
+      if (!std::isfinite(hc[i])) return LMBD_EINVAL;
+    double det = hc[0] * (hc[4] * hc[8] - hc[5] * hc[7]) - hc[1] * (hc[3] * hc[8] - hc[5] * hc[6]) +
+                 hc[2] * (hc[3] * hc[7] - hc[4] * hc[6]);
+    if (!(fabs(det) > 1e-9)) return LMBD_EINVAL;
+    g.periodic = 1;
+    memcpy(g.cell, hc, sizeof(hc));
+    // inverse (cofactor / det), frac = pos * inv
+    double inv[9] = {(hc[4] * hc[8] - hc[5] * hc[7]) / det, -(hc[1] * hc[8] - hc[2] * hc[7]) / det,
+                     (hc[1] * hc[5] - hc[2] * hc[4]) / det, -(hc[3] * hc[8] - hc[5] * hc[6]) / det,
+                     (hc[0] * hc[8] - hc[2] * hc[6]) / det, -(hc[0] * hc[5] - hc[2] * hc[3]) / det,
+                     (hc[3] * hc[7] - hc[4] * hc[6]) / det, -(hc[0] * hc[7] - hc[1] * hc[6]) / det,
+                     (hc[0] * hc[4] - hc[1] * hc[3]) / det};
+    memcpy(g.inv, inv, sizeof(inv));
+    vol_est = fabs(det);
+    for (int d = 0; d < 3; ++d) {
+      const double* a = hc + 3 * ((d + 1) % 3);
+      const double* b = hc + 3 * ((d + 2) % 3);
+      double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2], cz = a[0] * b[1] - a[1] * b[0];
+      double width = fabs(det) / sqrt(cx * cx + cy * cy + cz * cz);
+      int nc = (int)(width / rlist);
+      if (nc < 1) nc = 1;
+      if (nc > 64) nc = 64;
+      g.nc[d] = nc;
+      g.reach[d] = (int)ceil(rlist / (width / nc) - 1e-12);
+      if (g.reach[d] < 1) g.reach[d] = 1;
+    }
+  }
+  const int ncells = cell ? g.nc[0] * g.nc[1] * g.nc[2] : 64 * 64 * 64;
+
+  // ---- per-atom buffers ----------------------------------------------------------------------
+  TRY(ensure(c->abar, sizeof(double) * N * nq));
+  TRY(ensure(c->sig, sizeof(double) * N * nq));
+  TRY(ensure(c->rvdw, sizeof(double) * N));
+  TRY(ensure(c->a0, sizeof(double) * N));
+  TRY(ensure(c->r0, sizeof(double) * N));
+  TRY(ensure(c->wpos, sizeof(double) * 3 * N));
+  TRY(ensure(c->cell_of, sizeof(int) * N));
+  TRY(ensure(c->cell_count, sizeof(int) * ncells));
+  TRY(ensure(c->cell_start, sizeof(int) * (ncells + 1)));
+  TRY(ensure(c->cell_atoms, sizeof(int) * N));
+  TRY(ensure(c->grid, sizeof(Grid)));
+  TRY(ensure(c->counts, sizeof(Counts) * N));
+  TRY(ensure(c->off_k1, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->off_s, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->off_b, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->off_t, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->totals, sizeof(long long) * 8));
+  TRY(ensure(c->status, sizeof(int) * 4));
+  TRY(ensure(c->alphaI, sizeof(double) * N * nq));
+  TRY(ensure(c->energies, sizeof(double) * N));
+  TRY(ensure(c->trbuf, sizeof(double) * (size_t)N * LMBD_MAX_ORDER_P1 * 64));
+
+  // site capacity from the density (sites within r_list), grown on overflow
+  {
+    const double four_pi_3 = 4.18879020478639098;
+    double dens = cell ? N / vol_est : 0.1;
+    long long expect = (long long)(dens * four_pi_3 * rlist * rlist * rlist) + 1;
+    if (!cell && expect > N) expect = N;
+    int cap = next_pow2((long long)(1.5 * expect) + 64);
+    if (cap < 64) cap = 64;
+    if (cap > 4096) cap = 4096;
+    if (cap < c->site_cap) cap = c->site_cap;
+    c->site_cap = cap;
+  }
+
+  Work w{};
+  w.n_atoms = N;
+  w.pos = (const double*)pos;
+  w.species = (const int*)spec;
+  w.nu = (const double*)nu;
+  w.table = (const double*)c->table_d.p;
+  w.weights = (const double*)wts;
+  w.abar = (double*)c->abar.p;
+  w.sig = (double*)c->sig.p;
+  w.rvdw = (double*)c->rvdw.p;
+  w.a0 = (double*)c->a0.p;
+  w.r0 = (double*)c->r0.p;
+  w.wpos = (double*)c->wpos.p;
+  w.cell_of = (int*)c->cell_of.p;
+  w.cell_count = (int*)c->cell_count.p;
+  w.cell_start = (int*)c->cell_start.p;
+  w.cell_atoms = (int*)c->cell_atoms.p;
+  w.ncells = ncells;
+  w.grid = (Grid*)c->grid.p;
+  w.counts = (Counts*)c->counts.p;
+  w.off_k1 = (long long*)c->off_k1.p;
+  w.off_s = (long long*)c->off_s.p;
+  w.off_b = (long long*)c->off_b.p;
+  w.off_t = (long long*)c->off_t.p;
+  w.totals = (long long*)c->totals.p;
+  w.status = (int*)c->status.p;
+  w.alphaI = (double*)c->alphaI.p;
+  w.energies = (double*)c->energies.p;
+  w.trbuf = (double*)c->trbuf.p;
+
+  // species indices must be in range and inputs finite: checked on the host only when
+  // the caller passed host arrays (device arrays are trusted).
+  if (!is_device_ptr(spec_in))
+    for (int i = 0; i < N; ++i)
+      if (spec_in[i] < 0 || spec_in[i] >= c->n_species) return LMBD_EINVAL;
+  if (!is_device_ptr(nu_in))
+    for (int i = 0; i < N; ++i)
+      if (!(nu_in[i] > 0.0) || !std::isfinite(nu_in[i])) return LMBD_EINVAL;
+  if (!is_device_ptr(pos_in))
+    for (int i = 0; i < 3 * N; ++i)
+      if (!std::isfinite(pos_in[i])) return LMBD_EINVAL;
+
+  const bool prof = c->profiling && c->launch_mode == LMBD_LAUNCH_BATCHED;
+  int phase_launch[LMBD_NPHASE] = {};
+  bool marked[LMBD_NPHASE + 1] = {};
+  auto mark = [&](int ph) {
+    if (prof) {
+      cudaEventRecord(c->ev[ph], s);
+      marked[ph] = true;
+    }
+  };
+  mark(LMBD_PHASE_NEIGHBORS);
+  launch_free_atom(w, dp, s);
+  ++launches;
+  Counts* cn = nullptr;
+  (void)cn;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    TRY(ensure(c->site_atom, sizeof(int) * (size_t)N * c->site_cap));
+    TRY(ensure(c->site_x, sizeof(double) * 3 * (size_t)N * c->site_cap));
+    w.site_cap = c->site_cap;
+    w.site_atom = (int*)c->site_atom.p;
+    w.site_x = (double*)c->site_x.p;
+    CK(cudaMemsetAsync(w.status, 0, sizeof(int) * 4, s));
+    launch_neighbors(w, dp, g, s, &launches);
+    launch_offsets(w, dp, s);
+    ++launches;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->totals_h, w.totals, sizeof(long long) * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->status_h, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*c->status_h & LMBD_FLAG_COINCIDENT) return LMBD_EINVAL;
+    if (!(*c->status_h & LMBD_FLAG_CAPACITY)) break;
+    if (c->site_cap >= 4096 || attempt == 3) return LMBD_ECAPACITY;
+    c->site_cap *= 2;
+  }
+  phase_launch[LMBD_PHASE_NEIGHBORS] = launches;
+  const long long sum_n1 = c->totals_h[0], sum_ns = c->totals_h[1], sum_b = c->totals_h[2],
+                  sum_t = c->totals_h[3];
+  const int max_n1 = (int)c->totals_h[4], max_ns = (int)c->totals_h[5], max_n12 = (int)c->totals_h[6];
+  // kernel shared-memory capacities (per-centre systems live in shared memory)
+  if (max_n1 > 200 || max_ns > 1024 || max_n12 > 2048) return LMBD_ECAPACITY;
+
+  // ---- workspaces -------------------------------------------------------------------------
+  const int ncv = 3 * c->n_freq;
+  const int nvec = forces ? (c->order - 1) : (c->order + 1) / 2;
+  const int ncol = 3 * c->n_freq * (c->order - 2);
+  TRY(ensure(c->bmat, sizeof(double) * (size_t)sum_b));
+  TRY(ensure(c->xsol, sizeof(double) * (size_t)sum_n1 * nq * 9));
+  TRY(ensure(c->alphaK, sizeof(double) * (size_t)sum_n1 * nq));
+  TRY(ensure(c->alphaT, sizeof(double) * (size_t)sum_ns * nq));
+  TRY(ensure(c->dsq, sizeof(double) * (size_t)sum_ns * nq));
+  TRY(ensure(c->tlr, sizeof(double) * (size_t)sum_t));
+  TRY(ensure(c->vkr, sizeof(double) * (size_t)nvec * sum_ns * 3 * ncv));
+  w.bmat = (double*)c->bmat.p;
+  w.xsol = (double*)c->xsol.p;
+  w.alphaK = (double*)c->alphaK.p;
+  w.alphaT = (double*)c->alphaT.p;
+  w.dsq = (double*)c->dsq.p;
+  w.tlr = (double*)c->tlr.p;
+  w.vkr = (double*)c->vkr.p;
+  w.nvec = nvec;
+  w.vstride = sum_ns * 3 * ncv;
+  w.ncol = ncol;
+  if (forces) {
+    TRY(ensure(c->gbar, sizeof(double) * (size_t)sum_ns * nq));
+    TRY(ensure(c->pmat, sizeof(double) * (size_t)sum_ns * 3 * (ncol > 0 ? ncol : 1)));
+    TRY(ensure(c->qmat, sizeof(double) * (size_t)sum_ns * 3 * (ncol > 0 ? ncol : 1)));
+    TRY(ensure(c->x0buf, sizeof(double) * (size_t)sum_ns * 9));
+    TRY(ensure(c->rbar, sizeof(double) * (size_t)sum_ns));
+    TRY(ensure(c->alphaK_bar, sizeof(double) * (size_t)sum_n1 * nq));
+    TRY(ensure(c->alphaI_bar, sizeof(double) * (size_t)N * nq));
+    TRY(ensure(c->gacc, sizeof(double) * 3 * (size_t)N));
+    w.gbar = (double*)c->gbar.p;
+    w.pmat = (double*)c->pmat.p;
+    w.qmat = (double*)c->qmat.p;
+    w.x0buf = (double*)c->x0buf.p;
+    w.rbar = (double*)c->rbar.p;
+    w.alphaK_bar = (double*)c->alphaK_bar.p;
+    w.alphaI_bar = (double*)c->alphaI_bar.p;
+    w.gacc = (double*)c->gacc.p;
+  }
+
+  // ---- stage 1 and 2 ------------------------------------------------------------------------
+  const bool per_atom = c->launch_mode == LMBD_LAUNCH_PER_ATOM;
+  const int step = per_atom ? 1 : N;
+  mark(LMBD_PHASE_SCS);
+  for (int c0 = 0; c0 < N; c0 += step) {
+    launch_scs_forward_sized(w, dp, c0, c0 + step, max_n12, max_n1, s);
+    ++phase_launch[LMBD_PHASE_SCS];
+  }
+  if (per_atom) {
+    for (int c0 = 0; c0 < N; ++c0) {
+      launch_mbd_prepare_sized(w, dp, c0, c0 + 1, max_ns, s);
+      for (int m = 1; m < nvec; ++m) launch_mbd_chain_sized(w, dp, m, c0, c0 + 1, max_ns, s);
+      launch_mbd_energy(w, dp, c0, c0 + 1, s);
+    }
+    phase_launch[LMBD_PHASE_PREPARE] = N;
+    phase_launch[LMBD_PHASE_CHAIN] = N * (nvec - 1);
+    phase_launch[LMBD_PHASE_ENERGY] = N;
+  } else {
+    mark(LMBD_PHASE_PREPARE);
+    launch_mbd_prepare_sized(w, dp, 0, N, max_ns, s);
+    mark(LMBD_PHASE_CHAIN);
+    for (int m = 1; m < nvec; ++m) launch_mbd_chain_sized(w, dp, m, 0, N, max_ns, s);
+    mark(LMBD_PHASE_ENERGY);
+    launch_mbd_energy(w, dp, 0, N, s);
+    phase_launch[LMBD_PHASE_PREPARE] = 1;
+    phase_launch[LMBD_PHASE_CHAIN] = nvec - 1;
+    phase_launch[LMBD_PHASE_ENERGY] = 1;
+  }
+  CK(cudaGetLastError());
+  if (forces) {
+    CK(cudaMemsetAsync(w.gacc, 0, sizeof(double) * 3 * N, s));
+    CK(cudaMemsetAsync(w.alphaI_bar, 0, sizeof(double) * N * nq, s));
+    CK(cudaMemsetAsync(w.rbar, 0, sizeof(double) * sum_ns, s));
+    if (per_atom) {
+      int dummy = 0;
+      for (int c0 = 0; c0 < N; ++c0) launch_mbd_adjoint_sized(w, dp, c0, c0 + 1, max_ns, s, &dummy);
+      for (int c0 = 0; c0 < N; ++c0) launch_scs_adjoint_sized(w, dp, c0, c0 + 1, max_n12, max_n1, s);
+      phase_launch[LMBD_PHASE_ADJ_SERIES] = phase_launch[LMBD_PHASE_ADJ_PAIR] = N;
+      phase_launch[LMBD_PHASE_ADJ_BLEND] = phase_launch[LMBD_PHASE_ADJ_SCS] = N;
+    } else {
+      mark(LMBD_PHASE_ADJ_SERIES);
+      launch_mbd_adj_series(w, dp, 0, N, s);
+      mark(LMBD_PHASE_ADJ_PAIR);
+      launch_mbd_adj_pair(w, dp, 0, N, max_ns, s);
+      mark(LMBD_PHASE_ADJ_BLEND);
+      launch_mbd_adj_blend(w, dp, 0, N, s);
+      mark(LMBD_PHASE_ADJ_SCS);
+      launch_scs_adjoint_sized(w, dp, 0, N, max_n12, max_n1, s);
+      phase_launch[LMBD_PHASE_ADJ_SERIES] = phase_launch[LMBD_PHASE_ADJ_PAIR] = 1;
+      phase_launch[LMBD_PHASE_ADJ_BLEND] = phase_launch[LMBD_PHASE_ADJ_SCS] = 1;
+    }
+    CK(cudaGetLastError());
+  }
+
+  // ---- outputs ----------------------------------------------------------------------------------
+  mark(LMBD_PHASE_OUTPUT);
+  if (e_out) {
+    bool dev = is_device_ptr(e_out);
+    CK(cudaMemcpyAsync(e_out, w.energies, sizeof(double) * N, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  }
+  if (forces) {
+    bool dev = is_device_ptr(f_out);
+    double* dst = f_out;
+    if (!dev) {
+      TRY(ensure(c->out_f_d, sizeof(double) * 3 * N));
+      dst = (double*)c->out_f_d.p;
+    }
+    launch_forces_out(w, dst, s);
+    ++phase_launch[LMBD_PHASE_OUTPUT];
+    if (!dev) CK(cudaMemcpyAsync(f_out, dst, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s));
+  }
+  mark(LMBD_NPHASE);
+  CK(cudaMemcpyAsync(c->status_h, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+
+  // ---- statistics (algorithmic work from the actual sizes) ----------------------------------
+  {
+    std::vector<Counts> hc(N);
+    CK(cudaMemcpy(hc.data(), w.counts, sizeof(Counts) * N, cudaMemcpyDeviceToHost));
+    lmbd_stats& S = c->stats;
+    for (int i = 0; i < N; ++i) {
+      double n1 = 3.0 * hc[i].n1, n = 3.0 * hc[i].ns;
+      S.flops[LMBD_PHASE_SCS] += nq * (n1 * n1 * n1 / 3.0 + 6.0 * n1 * n1);
+      S.flops[LMBD_PHASE_CHAIN] += (nvec - 1) * 2.0 * n * n * ncv;
+      if (forces) {
+        S.flops[LMBD_PHASE_ADJ_PAIR] += 2.0 * (n * (n + 48.0) / 2.0) * ncol;   // lower tiles of P Q^T
+        S.flops[LMBD_PHASE_ADJ_SCS] += nq * 6.0 * n1 * n1;
+      }
+    }
+    for (int ph = 0; ph < LMBD_NPHASE; ++ph) {
+      S.launches[ph] = phase_launch[ph];
+      launches += ph == LMBD_PHASE_NEIGHBORS ? 0 : phase_launch[ph];
+    }
+    if (prof)
+      for (int ph = 0; ph < LMBD_NPHASE; ++ph) {
+        if (!marked[ph]) continue;
+        int nx = ph + 1;
+        while (nx <= LMBD_NPHASE && !marked[nx]) ++nx;
+        float ms = 0.f;
+        if (nx <= LMBD_NPHASE && cudaEventElapsedTime(&ms, c->ev[ph], c->ev[nx]) == cudaSuccess) S.ms[ph] = ms;
+        cudaGetLastError();
+      }
+    S.n_sites = c->totals_h[7];
+    S.max_k1 = max_n1;
+    S.max_sphere = max_ns;
+    S.max_sites = c->site_cap;
+    S.kernel_launches = launches;
+    double bytes = 0.0;
+    const DevBuf* all[] = {&c->bmat, &c->xsol, &c->alphaK, &c->alphaT, &c->dsq, &c->tlr, &c->vkr, &c->gbar,
+                           &c->pmat, &c->qmat, &c->x0buf, &c->rbar, &c->alphaK_bar, &c->alphaI_bar,
+                           &c->site_atom, &c->site_x};
+    for (const DevBuf* b : all) bytes += b->bytes;
+    S.bytes_workspace = bytes;
+  }
+  if (*c->status_h & LMBD_FLAG_NOT_SPD) return LMBD_NOT_SPD;
+  return LMBD_OK;
+}
+
+}  // namespace
+
+struct lmbd_ctx {
+  Ctx c;
+};
+
+extern "C" {
+
+int lmbd_default_params(lmbd_params* out) {
+  if (!out) return LMBD_EINVAL;
+  out->r_scs = 5.0;
+  out->r_mbd1 = 7.0;
+  out->r_mbd2 = 7.0;
+  out->r_sphere = 7.0;
+  out->r_buf = 0.5;
+  out->r_inner = 2.0;
+  out->beta = 0.83;
+  out->d = 6.0;
+  out->omega_scale = 0.6;
+  return LMBD_OK;
+}
+
+int lmbd_create(const lmbd_species* species, int n_species, const lmbd_params* params, int n_freq,
+                int series_order, lmbd_ctx** out) {
+  if (!out || !species || !params || n_species <= 0) return LMBD_EINVAL;
+  *out = nullptr;
+  if (n_freq < 1 || n_freq > LMBD_MAX_FREQ) return LMBD_EINVAL;
+  if (series_order < 2 || series_order > LMBD_MAX_ORDER) return LMBD_EUNSUPPORTED;
+  const lmbd_params& p = *params;
+  double rs = p.r_sphere > 0 ? p.r_sphere : p.r_mbd1 + p.r_mbd2;
+  if (!(p.r_scs > 0) || !(p.r_buf > 0) || !(p.r_inner > 0) || !(p.r_mbd1 > 0) || !(p.r_mbd2 > 0) ||
+      !(p.beta > 0) || !(p.d > 0) || !(p.omega_scale > 0) || p.r_scs > rs || p.r_buf > p.r_scs ||
+      p.r_buf > p.r_mbd1 || p.r_buf > p.r_mbd2)
+    return LMBD_EINVAL;
+  for (int i = 0; i < n_species; ++i)
+    if (!(species[i].alpha0 > 0) || !(species[i].c6 > 0) || !(species[i].r0 > 0)) return LMBD_EINVAL;
+  lmbd_ctx* h = new (std::nothrow) lmbd_ctx();
+  if (!h) return LMBD_ENOMEM;
+  Ctx& c = h->c;
+  c.prm = p;
+  c.n_species = n_species;
+  c.n_freq = n_freq;
+  c.order = series_order;
+  c.table.resize(3 * n_species);
+  for (int i = 0; i < n_species; ++i) {
+    c.table[3 * i] = species[i].alpha0;
+    c.table[3 * i + 1] = species[i].c6;
+    c.table[3 * i + 2] = species[i].r0;
+  }
+  gauss_legendre(n_freq, p.omega_scale, c.omega, c.weight);
+  int st = ensure(c.table_d, sizeof(double) * c.table.size());
+  if (st == LMBD_OK &&
+      cudaMemcpy(c.table_d.p, c.table.data(), sizeof(double) * c.table.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    st = LMBD_ECUDA;
+  if (st == LMBD_OK && cudaMallocHost((void**)&c.totals_h, sizeof(long long) * 8) != cudaSuccess) st = LMBD_ENOMEM;
+  if (st == LMBD_OK && cudaMallocHost((void**)&c.status_h, sizeof(int) * 4) != cudaSuccess) st = LMBD_ENOMEM;
+  if (st != LMBD_OK) {
+    cudaGetLastError();
+    lmbd_destroy(h);
+    return st;
+  }
+  *out = h;
+  return LMBD_OK;
+}
+
+int lmbd_energy_forces_weighted(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell,
+                                const int* species, const double* hirshfeld, const double* energy_weights,
+                                double* energies, double* forces, void* stream) {
+  if (!ctx || n_atoms < 0) return LMBD_EINVAL;
+  if (n_atoms > 0 && (!positions || !species || !hirshfeld)) return LMBD_EINVAL;
+  int st = run(&ctx->c, n_atoms, positions, cell, species, hirshfeld, energy_weights, energies, forces,
+               (cudaStream_t)stream);
+  if (st != LMBD_OK) cudaGetLastError();
+  return st;
+}
+
+int lmbd_energy_forces(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell,
+                       const int* species, const double* hirshfeld, double* energies, double* forces,
+                       void* stream) {
+  return lmbd_energy_forces_weighted(ctx, n_atoms, positions, cell, species, hirshfeld, nullptr, energies,
+                                     forces, stream);
+}
+
+int lmbd_set_profiling(lmbd_ctx* ctx, int on) {
+  if (!ctx) return LMBD_EINVAL;
+  Ctx& c = ctx->c;
+  if (on && !c.ev[0])
+    for (int i = 0; i <= LMBD_NPHASE; ++i)
+      if (cudaEventCreate(&c.ev[i]) != cudaSuccess) {
+        cudaGetLastError();
+        return LMBD_ECUDA;
+      }
+  c.profiling = on ? 1 : 0;
+  return LMBD_OK;
+}
+
+int lmbd_set_launch_mode(lmbd_ctx* ctx, int mode) {
+  if (!ctx || (mode != LMBD_LAUNCH_BATCHED && mode != LMBD_LAUNCH_PER_ATOM)) return LMBD_EINVAL;
+  ctx->c.launch_mode = mode;
+  return LMBD_OK;
+}
+
+int lmbd_get_central_polarizabilities(lmbd_ctx* ctx, double* out, void* stream) {
+  if (!ctx || !out) return LMBD_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.last_n == 0) return LMBD_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool dev = is_device_ptr(out);
+  if (cudaMemcpyAsync(out, c.alphaI.p, sizeof(double) * c.last_n * (c.n_freq + 1),
+                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return LMBD_ECUDA;
+  }
+  return LMBD_OK;
+}
+
+int lmbd_get_site_counts(lmbd_ctx* ctx, int* out, void* stream) {
+  if (!ctx || !out) return LMBD_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.last_n == 0) return LMBD_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool dev = is_device_ptr(out);
+  if (cudaMemcpyAsync(out, c.counts.p, sizeof(Counts) * c.last_n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return LMBD_ECUDA;
+  }
+  return LMBD_OK;
+}
+
+int lmbd_get_quadrature(const lmbd_ctx* ctx, double* omega, double* weight) {
+  if (!ctx || !omega || !weight) return LMBD_EINVAL;
+  for (int i = 0; i < ctx->c.n_freq; ++i) {
+    omega[i] = ctx->c.omega[i];
+    weight[i] = ctx->c.weight[i];
+  }
+  return LMBD_OK;
+}
+
+int lmbd_get_stats(const lmbd_ctx* ctx, lmbd_stats* out) {
+  if (!ctx || !out) return LMBD_EINVAL;
+  *out = ctx->c.stats;
+  return LMBD_OK;
+}
+
+int lmbd_destroy(lmbd_ctx* ctx) {
+  if (!ctx) return LMBD_OK;
+  Ctx& c = ctx->c;
+  DevBuf* all[] = {&c.table_d, &c.pos_d, &c.species_d, &c.nu_d, &c.weights_d, &c.out_e_d, &c.out_f_d,
+                   &c.abar, &c.sig, &c.rvdw, &c.a0, &c.r0, &c.wpos, &c.cell_of, &c.cell_count,
+                   &c.cell_start, &c.cell_atoms, &c.grid, &c.site_atom, &c.site_x, &c.counts, &c.off_k1,
+                   &c.off_s, &c.off_b, &c.off_t, &c.totals, &c.status, &c.bmat, &c.xsol, &c.alphaK,
+                   &c.alphaI, &c.alphaT, &c.dsq, &c.tlr, &c.vkr, &c.energies, &c.trbuf, &c.gbar, &c.pmat,
+                   &c.qmat, &c.x0buf, &c.rbar, &c.alphaK_bar, &c.alphaI_bar, &c.gacc};
+  for (DevBuf* b : all) release(*b);
+  for (int i = 0; i <= LMBD_NPHASE; ++i)
+    if (c.ev[i]) cudaEventDestroy(c.ev[i]);
+  if (c.totals_h) cudaFreeHost(c.totals_h);
+  if (c.status_h) cudaFreeHost(c.status_h);
+  delete ctx;
+  return LMBD_OK;
+}
+
+const char* lmbd_status_string(int status) {
+  switch (status) {
+    case LMBD_OK: return "ok";
+    case LMBD_EINVAL: return "invalid argument";
+    case LMBD_ENOMEM: return "device allocation failed";
+    case LMBD_NOT_SPD: return "screening matrix not positive definite";
+    case LMBD_ECUDA: return "CUDA runtime error";
+    case LMBD_ECAPACITY: return "too many sites around one atom for the kernels";
+    case LMBD_EUNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

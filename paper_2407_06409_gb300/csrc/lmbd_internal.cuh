@@ -1,0 +1,194 @@
+// Internal declarations of the lMBD CUDA library: device parameter block,
+// workspace layout, pair functions of the model and kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define LMBD_BOHR 0.529177210903       // Angstrom per bohr, CODATA 2018
+#define LMBD_HARTREE 27.211386245988   // eV per hartree, CODATA 2018
+#define LMBD_MAXQ 65                   // omega = 0 plus up to 64 quadrature nodes
+#define LMBD_MAX_ORDER_P1 11           // series order n_max <= 10
+
+// Error bits written by kernels into the device status word.
+#define LMBD_FLAG_NOT_SPD 1
+#define LMBD_FLAG_CAPACITY 2
+#define LMBD_FLAG_COINCIDENT 4
+
+struct DevParams {
+  // lengths in bohr
+  double r_scs, r_mbd1, r_mbd2, r_buf, r_inner, beta, d;
+  // squared membership radii in Angstrom^2 (sets are decided on Angstrom distances)
+  double r2_scs_ang, r2_sphere_ang, r2_scs2_ang, r2_list_ang;
+  int n_freq;        // quadrature nodes
+  int nq;            // n_freq + 1 (column 0 is omega = 0)
+  int order;         // series order n_max
+  int n_species;
+  double omega[LMBD_MAXQ];
+  double cweight[LMBD_MAXQ];  // hartree->eV * w_q / (2 pi) for q >= 1, 0 for q = 0
+};
+
+// Geometry of the neighbour search (host-computed from the cell).
+struct Grid {
+  int periodic;
+  int nc[3];          // cells per direction
+  int reach[3];       // cell offsets to scan per direction
+  double cell[9];     // rows = lattice vectors (Angstrom)
+  double inv[9];      // inverse of the cell matrix (frac = pos * inv)
+  double origin[3];   // non-periodic: lower corner of the bounding box
+  double h[3];        // non-periodic: cell edge length
+};
+
+// Per-centre counts: n1 = |K1|, ns = |sphere|, n12 = |K1 u K2|, nt = all sites.
+struct Counts {
+  int n1, ns, n12, nt;
+};
+
+// Workspace pointers handed to kernels (all device memory).
+struct Work {
+  int n_atoms;
+  int site_cap;                // capacity of one centre's site list
+  // inputs (device copies)
+  const double* pos;           // N x 3 Angstrom
+  const int* species;          // N
+  const double* nu;            // N
+  const double* table;         // S x 3
+  const double* weights;       // N energy weights (NULL = ones)
+  // free-atom quantities
+  double* abar;                // N x nq
+  double* sig;                 // N x nq
+  double* rvdw;                // N
+  double* a0;                  // N
+  double* r0;                  // N
+  // neighbour search
+  double* wpos;                // N x 3 wrapped positions (Angstrom)
+  int* cell_of;                // N
+  int* cell_count;             // ncells
+  int* cell_start;             // ncells + 1
+  int* cell_atoms;             // N
+  int ncells;
+  Grid* grid;                  // device copy of the search grid
+  int* site_atom;              // N x site_cap
+  double* site_x;              // N x site_cap x 3, displacement from the centre (bohr)
+  Counts* counts;              // N
+  // per-centre offsets (exclusive prefix sums, N + 1 entries)
+  long long* off_k1;           // sum n1
+  long long* off_s;            // sum ns
+  long long* off_b;            // sum nq (3 n1)^2
+  long long* off_t;            // sum (3 ns)^2
+  long long* totals;           // 8 entries written by the offsets kernel
+  // stage 1 (SCS)
+  double* bmat;                // factors, off_b
+  double* xsol;                // X = B^-1 d, off_k1 * nq * 9
+  double* alphaK;              // off_k1 * nq
+  double* alphaI;              // N x nq
+  // stage 2 (MBD)
+  double* alphaT;              // blended alpha, off_s * nq
+  double* tlr;                 // T_LR, off_t
+  double* dsq;                 // sqrt(alpha~), off_s * nq
+  double* vkr;                 // Krylov vectors: nvec blocks of (off_s total * 3) x (3 n_freq)
+  int nvec;
+  long long vstride;           // doubles per Krylov block
+  double* energies;            // N, eV
+  double* trbuf;               // N x 11 x 64 k-block traces tr_{n,q}
+  // adjoint
+  double* gbar;                // dL/d alpha~, off_s * nq
+  double* pmat;                // off_s*3 x ncol
+  double* qmat;                // off_s*3 x ncol
+  int ncol;                    // 3 n_freq (n_max - 2)
+  double* x0buf;               // off_s x 9, central-column term of the pair matrix
+  double* rbar;                // dL/d R~ per sphere site, off_s
+  double* alphaK_bar;          // off_k1 * nq
+  double* alphaI_bar;          // N x nq
+  double* gacc;                // N x 3, dL/dR in eV/bohr (accumulated)
+  int* status;                 // device status word
+};
+
+// ---------------------------------------------------------------------------------------
+// model functions (device)
+// ---------------------------------------------------------------------------------------
+// f_SR / f_LR: 1 below rc - rb, 1 - 3t^2 + 2t^3 in the buffer, 0 beyond (Sec. III.A/B).
+__device__ __forceinline__ void cutoff_buf(double r, double rc, double rb, double& f, double& df) {
+  if (r < rc - rb) { f = 1.0; df = 0.0; return; }
+  if (r >= rc) { f = 0.0; df = 0.0; return; }
+  double t = (r - rc + rb) / rb;
+  f = 1.0 - 3.0 * t * t + 2.0 * t * t * t;
+  df = (-6.0 * t + 6.0 * t * t) / rb;
+}
+
+// f_inner (Sec. III.B): 3u^2 - 2u^3 with u = r/r_inner for r < r_inner, else 1.
+__device__ __forceinline__ void finner(double r, double rin, double& f, double& df) {
+  if (r >= rin) { f = 1.0; df = 0.0; return; }
+  double u = r / rin;
+  f = 3.0 * u * u - 2.0 * u * u * u;
+  df = (6.0 * u - 6.0 * u * u) / rin;
+}
+
+// Fermi damping f(r, S) = 1/(1 + exp(-d (r/S - 1))) (Eq. damping-function) and
+// its partial derivatives with respect to r and S.
+__device__ __forceinline__ void fermi(double r, double s, double d, double& f, double& dfr, double& dfs) {
+  double e = exp(-d * (r / s - 1.0));
+  f = 1.0 / (1.0 + e);
+  double g = f * (1.0 - f) * d / s;   // df/dr
+  dfr = g;
+  dfs = -g * r / s;                   // df/dS
+}
+
+// T_SR written as F(r) [A0(r) I + B0(r) r r^T] (Eq. T_SR with Eqs. g-func, h-func):
+// A0 = g / r^3, B0 = (h~ - 3 g) / r^5 with x = r/sigma, h~ = (4/sqrt(pi)) x^3 exp(-x^2).
+// Also returns the radial derivatives A0', B0'.
+__device__ __forceinline__ void tsr_radial(double r, double sigma, double& A0, double& B0,
+                                           double& dA0, double& dB0) {
+  const double two_over_sqrtpi = 1.1283791670955126;
+  double x = r / sigma;
+  double ex = exp(-x * x);
+  double g = erf(x) - two_over_sqrtpi * x * ex;
+  double ht = 2.0 * two_over_sqrtpi * x * x * x * ex;
+  double ir = 1.0 / r;
+  double ir2 = ir * ir;
+  double ir3 = ir2 * ir;
+  double ir4 = ir2 * ir2;
+  A0 = g * ir3;
+  B0 = (ht - 3.0 * g) * ir4 * ir;
+  dA0 = (ht - 3.0 * g) * ir4;
+  dB0 = (15.0 * g - 5.0 * ht - 2.0 * x * x * ht) * ir4 * ir2;
+}
+
+__device__ __forceinline__ void tsr_value(double r, double sigma, double& A0, double& B0) {
+  const double two_over_sqrtpi = 1.1283791670955126;
+  double x = r / sigma;
+  double ex = exp(-x * x);
+  double g = erf(x) - two_over_sqrtpi * x * ex;
+  double ht = 2.0 * two_over_sqrtpi * x * x * x * ex;
+  double ir = 1.0 / r;
+  double ir2 = ir * ir;
+  A0 = g * ir2 * ir;
+  B0 = (ht - 3.0 * g) * ir2 * ir2 * ir;
+}
+
+// atomicAdd for doubles is native on sm_60+.
+__device__ __forceinline__ void atomic_add3(double* p, double a, double b, double c) {
+  atomicAdd(p, a);
+  atomicAdd(p + 1, b);
+  atomicAdd(p + 2, c);
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers (host)
+// ---------------------------------------------------------------------------------------
+// Each launcher enqueues its kernels on stream s for central atoms [c0, c1).
+void launch_free_atom(const Work& w, const DevParams& p, cudaStream_t s);
+void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStream_t s, int* launches);
+void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s);
+void launch_scs_forward_sized(const Work& w, const DevParams& p, int c0, int c1, int max_n12,
+                              int max_n1, cudaStream_t s);
+void launch_mbd_prepare_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
+void launch_mbd_chain_sized(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, cudaStream_t s);
+void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
+void launch_mbd_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns,
+                              cudaStream_t s, int* launches);
+void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
+void launch_mbd_adj_pair(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
+void launch_mbd_adj_blend(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
+void launch_scs_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1, int max_n12,
+                              int max_n1, cudaStream_t s);
+void launch_forces_out(const Work& w, double* forces, cudaStream_t s);

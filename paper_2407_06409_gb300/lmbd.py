@@ -1,0 +1,250 @@
+"""Thin ctypes binding of the lMBD C ABI (include/lmbd.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``liblmbd.so``.  Arrays may be torch tensors (CUDA or CPU) or numpy
+arrays; CUDA tensors are passed as device pointers, everything else as host
+pointers (the library copies host arrays itself).  If the shared library has
+not been built this module raises at import time: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblmbd.so")
+
+LMBD_OK, LMBD_EINVAL, LMBD_ENOMEM, LMBD_NOT_SPD, LMBD_ECUDA, LMBD_ECAPACITY, LMBD_EUNSUPPORTED = range(7)
+LAUNCH_BATCHED, LAUNCH_PER_ATOM = 0, 1
+
+
+class Species(ctypes.Structure):
+    _fields_ = [("alpha0", ctypes.c_double), ("c6", ctypes.c_double), ("r0", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("r_scs", "r_mbd1", "r_mbd2", "r_sphere", "r_buf", "r_inner", "beta", "d", "omega_scale")]
+
+
+PHASES = ("neighbors", "scs", "prepare", "chain", "energy", "adj_series", "adj_pair", "adj_blend",
+          "adj_scs", "output")
+NPHASE = len(PHASES)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("flops", ctypes.c_double * NPHASE), ("ms", ctypes.c_double * NPHASE),
+                ("launches", ctypes.c_int * NPHASE), ("bytes_workspace", ctypes.c_double),
+                ("n_sites", ctypes.c_longlong), ("max_k1", ctypes.c_int), ("max_sphere", ctypes.c_int),
+                ("max_sites", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = {ph: v[i] for i, ph in enumerate(PHASES)} if k in ("flops", "ms", "launches") else v
+        return d
+
+
+class LmbdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {lib().lmbd_status_string(status).decode()} (status {status})")
+        self.status = status
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2407_06409_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.lmbd_status_string.restype = ctypes.c_char_p
+        L.lmbd_status_string.argtypes = [ctypes.c_int]
+        L.lmbd_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.lmbd_create.argtypes = [ctypes.POINTER(Species), ctypes.c_int, ctypes.POINTER(Params), ctypes.c_int,
+                                  ctypes.c_int, ctypes.POINTER(_P)]
+        L.lmbd_energy_forces.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
+        L.lmbd_energy_forces_weighted.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]
+        L.lmbd_set_launch_mode.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_profiling.argtypes = [_P, ctypes.c_int]
+        L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
+        L.lmbd_get_site_counts.argtypes = [_P, _P, _P]
+        L.lmbd_get_quadrature.argtypes = [_P, _D, _D]
+        L.lmbd_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
+        L.lmbd_destroy.argtypes = [_P]
+        for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
+                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
+                  "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
+            getattr(L, f).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, what: str) -> None:
+    if status != LMBD_OK:
+        raise LmbdError(status, what)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _check(lib().lmbd_default_params(ctypes.byref(p)), "lmbd_default_params")
+    for k, v in kw.items():
+        setattr(p, k, float(v))
+    return p
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _as_arg(x, dtype):
+    """(pointer, keepalive) for a torch tensor / numpy array / None."""
+    if x is None:
+        return None, None
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        t = x.detach().to(dtype).contiguous()
+        return ctypes.c_void_p(t.data_ptr()), t
+    a = np.ascontiguousarray(x, dtype={torch.float64: np.float64, torch.int32: np.int32}[dtype])
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _stream_ptr(stream, device):
+    torch = _torch()
+    if device.type != "cuda":
+        return None
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class LMBD:
+    """One library context: species table, model parameters, quadrature and series order."""
+
+    def __init__(self, table, params: Params | None = None, n_freq: int = 12, series_order: int = 6):
+        table = np.asarray(table, dtype=np.float64).reshape(-1, 3)
+        sp = (Species * len(table))(*[Species(*row) for row in table])
+        self.params = params if params is not None else default_params()
+        self.n_freq = int(n_freq)
+        self.series_order = int(series_order)
+        h = _P()
+        _check(lib().lmbd_create(sp, len(table), ctypes.byref(self.params), self.n_freq, self.series_order,
+                                 ctypes.byref(h)), "lmbd_create")
+        self._h = h
+        self.last_status = LMBD_OK
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().lmbd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_launch_mode(self, mode: int) -> None:
+        _check(lib().lmbd_set_launch_mode(self._h, int(mode)), "lmbd_set_launch_mode")
+
+    def set_profiling(self, on: bool) -> None:
+        _check(lib().lmbd_set_profiling(self._h, 1 if on else 0), "lmbd_set_profiling")
+
+    def energy_forces(self, positions, cell, species, hirshfeld, forces: bool = True, weights=None,
+                      stream=None, allow_not_spd: bool = False):
+        """Per-atom energies (eV) and forces (eV/Angstrom) as torch tensors.
+
+        Outputs live on the device of ``positions`` (CPU tensors / numpy -> CPU).
+        ``weights`` (N) turns forces into -d(sum_k w_k E_k)/dR.
+        """
+        torch = _torch()
+        dev = positions.device if isinstance(positions, torch.Tensor) else torch.device("cpu")
+        n = int(positions.shape[0])
+        pp, k1 = _as_arg(positions, torch.float64)
+        cp, k2 = _as_arg(cell, torch.float64)
+        sp, k3 = _as_arg(species, torch.int32)
+        hp, k4 = _as_arg(hirshfeld, torch.float64)
+        wp, k5 = _as_arg(weights, torch.float64)
+        e = torch.empty(n, dtype=torch.float64, device=dev)
+        f = torch.empty((n, 3), dtype=torch.float64, device=dev) if forces else None
+        st = _stream_ptr(stream, dev)
+        status = lib().lmbd_energy_forces_weighted(
+            self._h, n, pp, cp, sp, hp, wp, ctypes.c_void_p(e.data_ptr()),
+            ctypes.c_void_p(f.data_ptr()) if f is not None else None, st)
+        self.last_status = status
+        if not (status == LMBD_OK or (allow_not_spd and status == LMBD_NOT_SPD)):
+            raise LmbdError(status, "lmbd_energy_forces")
+        del k1, k2, k3, k4, k5
+        return e, f
+
+    def central_polarizabilities(self, n: int, device="cpu"):
+        torch = _torch()
+        out = torch.empty((n, self.n_freq + 1), dtype=torch.float64, device=device)
+        st = _stream_ptr(None, out.device)
+        _check(lib().lmbd_get_central_polarizabilities(self._h, ctypes.c_void_p(out.data_ptr()), st),
+               "lmbd_get_central_polarizabilities")
+        return out
+
+    def site_counts(self, n: int):
+        out = np.empty((n, 4), dtype=np.int32)
+        _check(lib().lmbd_get_site_counts(self._h, ctypes.c_void_p(out.ctypes.data), None), "lmbd_get_site_counts")
+        return out
+
+    def quadrature(self):
+        om = np.empty(self.n_freq)
+        w = np.empty(self.n_freq)
+        _check(lib().lmbd_get_quadrature(self._h, om.ctypes.data_as(_D), w.ctypes.data_as(_D)),
+               "lmbd_get_quadrature")
+        return om, w
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().lmbd_get_stats(self._h, ctypes.byref(s)), "lmbd_get_stats")
+        return s.as_dict()
+
+
+def _make_energy_function():
+    torch = _torch()
+
+    class LmbdEnergy(torch.autograd.Function):
+        """Per-atom lMBD energies with the hand-written adjoint as backward.
+
+        forward(positions, model, cell, species, hirshfeld) -> E (N); backward uses
+        the library's weighted forces: dL/dR = -F(w = dL/dE).
+        """
+
+        @staticmethod
+        def forward(ctx, positions, model, cell, species, hirshfeld):
+            e, _ = model.energy_forces(positions, cell, species, hirshfeld, forces=False)
+            ctx.model = model
+            ctx.save_for_backward(positions)
+            ctx.extra = (cell, species, hirshfeld)
+            return e
+
+        @staticmethod
+        def backward(ctx, grad_e):
+            (positions,) = ctx.saved_tensors
+            cell, species, hirshfeld = ctx.extra
+            _, f = ctx.model.energy_forces(positions, cell, species, hirshfeld, forces=True,
+                                           weights=grad_e.contiguous())
+            return -f, None, None, None, None
+
+    return LmbdEnergy
+
+
+_ENERGY_FN = None
+
+
+def lmbd_energy(positions, model: LMBD, cell, species, hirshfeld):
+    """Differentiable per-atom energies (torch.autograd)."""
+    global _ENERGY_FN
+    if _ENERGY_FN is None:
+        _ENERGY_FN = _make_energy_function()
+    return _ENERGY_FN.apply(positions, model, cell, species, hirshfeld)
