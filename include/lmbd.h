@@ -46,6 +46,7 @@ extern "C" {
 #define LMBD_ECUDA         4  /* a CUDA runtime call failed                                       */
 #define LMBD_ECAPACITY     5  /* more sites around one atom than the kernels support             */
 #define LMBD_EUNSUPPORTED  6  /* option not supported (e.g. series order out of range)           */
+#define LMBD_ESCRATCH      7  /* problem larger than the allocation-free entry point's scratch   */
 
 #define LMBD_MAX_FREQ      64 /* maximum number of quadrature frequencies                        */
 #define LMBD_MAX_ORDER     10 /* maximum series order n_max                                      */
@@ -162,6 +163,40 @@ int lmbd_get_stats(const lmbd_ctx* ctx, lmbd_stats* out);
 
 /* Destroy the context and free its device memory.  NULL is accepted. */
 int lmbd_destroy(lmbd_ctx* ctx);
+
+/* Allocation-free central polarisabilities.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory — code running inside someone else's CUDA-graph capture or
+ * replay, plug-ins of an MD engine that owns the device memory pool, and embedded
+ * runtimes that forbid allocation after start-up.  It computes the same central
+ * polarisabilities alpha_I,k(omega) as lmbd_energy_forces (site search and one local
+ * SCS solve per atom and frequency, Sec. III.B), without a context and without
+ * calling cudaMalloc, cudaFree or any allocating routine: every scratch buffer is
+ * carved from one fixed array of LMBD_NOALLOC_SCRATCH_BYTES that is part of the
+ * library image, so every GPU that loads the library holds it until the process exits.
+ *   species_params/n_species  as lmbd_create (host, n_species <= 64)
+ *   params, n_freq            as lmbd_create
+ *   n_atoms ... hirshfeld     as lmbd_energy_forces (device or host pointers)
+ *   alpha_central             out, n_atoms x (n_freq + 1), column 0 is omega = 0
+ *   stream                    cudaStream_t (NULL = legacy default stream); the call
+ *                             synchronises it before returning
+ * Limits: n_atoms <= LMBD_NOALLOC_MAX_ATOMS, at most LMBD_NOALLOC_SITE_CAP sites within
+ * max(2 r_SCS, sphere radius) of any atom, at most LMBD_NOALLOC_MAX_K1 sites within
+ * r_SCS; larger problems return LMBD_ESCRATCH before any device work on them.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU (other streams or threads) race on it and must be serialised. */
+#define LMBD_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define LMBD_NOALLOC_MAX_ATOMS     256
+#define LMBD_NOALLOC_SITE_CAP      512
+#define LMBD_NOALLOC_MAX_K1        64
+int lmbd_central_polarizabilities_noalloc(const lmbd_species* species_params, int n_species,
+                                          const lmbd_params* params, int n_freq, int n_atoms,
+                                          const double* positions, const double* cell,
+                                          const int* species, const double* hirshfeld,
+                                          double* alpha_central, void* stream);
 
 /* Static, human-readable text for a status code. */
 const char* lmbd_status_string(int status);

@@ -496,3 +496,155 @@ void launch_scs_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1,
   k_scs_adjoint<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_n12, max_n1);
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the SCS forward kernel.
+//
+// Some callers cannot call cudaMalloc: code that runs inside a CUDA graph being captured
+// or replayed by someone else, plug-ins of an MD engine that owns the device memory pool,
+// and embedded runtimes that forbid allocation after start-up.  For them,
+// lmbd_central_polarizabilities_noalloc (lmbd.h) computes the central polarisabilities
+// with every scratch buffer carved from the fixed array below.  This array is part of the
+// library image: every GPU that loads the library holds these bytes until the process
+// exits.  All calls share it and it keeps the contents of the last call; calls whose
+// work overlaps on the GPU (two streams, two threads) race on it and must be serialised
+// by the caller.
+// ---------------------------------------------------------------------------------------
+#include <mutex>
+
+#include "../../include/lmbd.h"
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LMBD_NOALLOC_SCRATCH_BYTES];
+
+// Device address of the scratch array for the current device.  The first call on a
+// device looks the address up with cudaGetSymbolAddress (host code cannot use the
+// symbol itself: in host code it names a host-side stand-in, not device memory).
+// Returns 0 on success.
+int noalloc_scratch(void** ptr, size_t* bytes) {
+  static void* addr[64] = {};
+  static std::mutex mtx;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::lock_guard<std::mutex> lock(mtx);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return -1;
+    }
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  *bytes = sizeof(g_noalloc_scratch);
+  return 0;
+}
+
+// Same arithmetic as k_scs_forward (assembly, Cholesky, solves), but persistent over
+// central atoms with the matrix of the current (atom, frequency) in this block's slot of
+// the scratch array, and only alpha_I written out.
+__global__ void __launch_bounds__(256) k_scs_central_noalloc(Work w, DevParams p, double* bslots,
+                                                           long long slot_doubles, int max_n12, int max_n1) {
+  extern __shared__ double smem_d[];
+  ScsSmem sm = scs_carve(smem_d, max_n12, max_n1, false);
+  const int tid = threadIdx.x;
+  double* B = bslots + (long long)blockIdx.x * slot_doubles;
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  for (int c = blockIdx.x; c < w.n_atoms; c += gridDim.x) {
+    __syncthreads();
+    const Counts cn = w.counts[c];
+    const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
+    const long long sbase = (long long)c * w.site_cap;
+    for (int s = tid; s < n12; s += blockDim.x) {
+      int a = w.site_atom[sbase + s];
+      sm.x[s] = w.site_x[3 * (sbase + s) + 0];
+      sm.x[max_n12 + s] = w.site_x[3 * (sbase + s) + 1];
+      sm.x[2 * max_n12 + s] = w.site_x[3 * (sbase + s) + 2];
+      sm.rv[s] = w.rvdw[a];
+    }
+    const int npair = n1 * (n1 - 1) / 2;
+    for (int q = 0; q < p.nq; ++q) {
+      __syncthreads();
+      for (int s = tid; s < n12; s += blockDim.x) {
+        int a = w.site_atom[sbase + s];
+        sm.ab[s] = w.abar[a * p.nq + q];
+        sm.sg[s] = w.sig[a * p.nq + q];
+      }
+      __syncthreads();
+      for (int e = tid; e < n1 * 6; e += blockDim.x) {
+        int i = e / 6, t = e % 6;
+        int al = t < 3 ? t : (t == 3 ? 1 : 2), be = t < 3 ? t : (t == 3 ? 0 : (t == 4 ? 0 : 1));
+        B[(long long)(3 * i + al) * N1 + 3 * i + be] = (al == be) ? 1.0 / sm.ab[i] : 0.0;
+      }
+      for (int e = tid; e < npair; e += blockDim.x) {
+        int i = (int)((sqrtf(8.0f * e + 1.0f) + 1.0f) * 0.5f);
+        while (i * (i - 1) / 2 > e) --i;
+        while ((i + 1) * i / 2 <= e) ++i;
+        int j = e - i * (i - 1) / 2;
+        double rx = sm.x[j] - sm.x[i];
+        double ry = sm.x[max_n12 + j] - sm.x[max_n12 + i];
+        double rz = sm.x[2 * max_n12 + j] - sm.x[2 * max_n12 + i];
+        double r = sqrt(rx * rx + ry * ry + rz * rz);
+        double F = 0.0, A0 = 0.0, B0 = 0.0;
+        double sig = sqrt(sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j]);
+        if (!tsr_pair(p, r, p.beta * (sm.rv[i] + sm.rv[j]), sig, false, F, A0, B0)) F = 0.0;
+        double a = F * A0, b = F * B0;
+        double rr[3] = {rx, ry, rz};
+        double* blk = B + (long long)(3 * i) * N1 + 3 * j;
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+          for (int be = 0; be < 3; ++be)
+            blk[(long long)al * N1 + be] = b * rr[al] * rr[be] + (al == be ? a : 0.0);
+      }
+      const int warp = tid / 32, lane = tid % 32;
+      for (int i = warp; i < n1; i += blockDim.x / 32) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        double xi = sm.x[i], yi = sm.x[max_n12 + i], zi = sm.x[2 * max_n12 + i];
+        for (int j = n1 + lane; j < n12; j += 32) {
+          double rx = sm.x[j] - xi, ry = sm.x[max_n12 + j] - yi, rz = sm.x[2 * max_n12 + j] - zi;
+          double r2 = rx * rx + ry * ry + rz * rz;
+          if (r2 >= p.r_scs * p.r_scs) continue;
+          double r = sqrt(r2);
+          double F, A0, B0;
+          double sig = sqrt(sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j]);
+          if (!tsr_pair(p, r, p.beta * (sm.rv[i] + sm.rv[j]), sig, true, F, A0, B0)) continue;
+          double a = F * A0 * sm.ab[j], b = F * B0 * sm.ab[j];
+          acc[0] += a + b * rx * rx;
+          acc[1] += a + b * ry * ry;
+          acc[2] += a + b * rz * rz;
+          acc[3] += b * rx * ry;
+          acc[4] += b * rx * rz;
+          acc[5] += b * ry * rz;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int t = 0; t < 6; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+        if (lane == 0) {
+          double* y = sm.y + 9 * i;
+          y[0] = 1.0 - acc[0]; y[1] = -acc[3];      y[2] = -acc[4];
+          y[3] = -acc[3];      y[4] = 1.0 - acc[1]; y[5] = -acc[5];
+          y[6] = -acc[4];      y[7] = -acc[5];      y[8] = 1.0 - acc[2];
+        }
+      }
+      __threadfence_block();
+      __syncthreads();
+      block_cholesky(B, N1, sm.panel, sm.dg, sm.inv, &bad);
+      block_solve3(B, N1, sm.inv, sm.y, sm.red);
+      if (tid == 0) w.alphaI[(long long)c * p.nq + q] = (sm.y[0] + sm.y[4] + sm.y[8]) / 3.0;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && bad) atomicOr(w.status, LMBD_FLAG_NOT_SPD);
+}
+
+void launch_scs_central_noalloc(const Work& w, const DevParams& p, double* bslots, long long slot_doubles,
+                                int nslots, int max_n12, int max_n1, cudaStream_t s) {
+  size_t sm = scs_smem_bytes(max_n12, max_n1, false);
+  cudaFuncSetAttribute(k_scs_central_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_scs_central_noalloc<<<nslots, 256, sm, s>>>(w, p, bslots, slot_doubles, max_n12, max_n1);
+}

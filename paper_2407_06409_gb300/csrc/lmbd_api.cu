@@ -684,8 +684,237 @@ const char* lmbd_status_string(int status) {
     case LMBD_ECUDA: return "CUDA runtime error";
     case LMBD_ECAPACITY: return "too many sites around one atom for the kernels";
     case LMBD_EUNSUPPORTED: return "unsupported option";
+    case LMBD_ESCRATCH: return "problem exceeds the fixed scratch of the allocation-free entry point";
     default: return "unknown status";
   }
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free central polarisabilities (lmbd_central_polarizabilities_noalloc).
+// Every buffer is carved from the library's static device scratch array; the host side
+// uses fixed-size stack arrays only.  Nothing here allocates memory.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct Carve {
+  unsigned char* base;
+  size_t used, cap;
+  template <class T>
+  T* take(size_t n) {
+    size_t off = (used + 255) & ~size_t(255);
+    size_t bytes = n * sizeof(T);
+    if (off + bytes > cap) return nullptr;
+    used = off + bytes;
+    return reinterpret_cast<T*>(base + off);
+  }
+};
+
+// Gauss-Legendre nodes on [-1, 1] by Newton iteration on P_n, mapped to [0, inf);
+// fixed-size output arrays (n <= LMBD_MAX_FREQ).
+void gauss_legendre_fixed(int n, double L, double* om, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double x = z, wx = 2.0 / ((1.0 - z * z) * dp * dp);
+    om[n - 1 - i] = L * (1.0 + x) / (1.0 - x);
+    w[n - 1 - i] = 2.0 * L * wx / ((1.0 - x) * (1.0 - x));
+  }
+}
+
+int noalloc_central(const lmbd_species* species_params, int n_species, const lmbd_params* params, int n_freq,
+                    int N, const double* positions, const double* cell, const int* species,
+                    const double* hirshfeld, double* alpha_central, cudaStream_t s) {
+  const lmbd_params& P = *params;
+  double rsph = sphere_radius(P);
+  if (!(P.r_scs > 0) || !(P.r_buf > 0) || !(P.r_inner > 0) || !(P.r_mbd1 > 0) || !(P.r_mbd2 > 0) ||
+      !(P.beta > 0) || !(P.d > 0) || !(P.omega_scale > 0) || P.r_scs > rsph || P.r_buf > P.r_scs)
+    return LMBD_EINVAL;
+  for (int i = 0; i < n_species; ++i)
+    if (!(species_params[i].alpha0 > 0) || !(species_params[i].c6 > 0) || !(species_params[i].r0 > 0))
+      return LMBD_EINVAL;
+  if (!is_device_ptr(species))
+    for (int i = 0; i < N; ++i)
+      if (species[i] < 0 || species[i] >= n_species) return LMBD_EINVAL;
+  if (!is_device_ptr(hirshfeld))
+    for (int i = 0; i < N; ++i)
+      if (!(hirshfeld[i] > 0.0) || !std::isfinite(hirshfeld[i])) return LMBD_EINVAL;
+  if (!is_device_ptr(positions))
+    for (int i = 0; i < 3 * N; ++i)
+      if (!std::isfinite(positions[i])) return LMBD_EINVAL;
+
+  void* base = nullptr;
+  size_t cap = 0;
+  if (noalloc_scratch(&base, &cap) != 0) return LMBD_ECUDA;
+  const int nq = n_freq + 1;
+
+  // parameters (same definitions as lmbd_energy_forces)
+  DevParams dp{};
+  const double ib = 1.0 / LMBD_BOHR;
+  const double rlist = fmax(2.0 * P.r_scs, rsph);
+  dp.r_scs = P.r_scs * ib;
+  dp.r_mbd1 = P.r_mbd1 * ib;
+  dp.r_mbd2 = P.r_mbd2 * ib;
+  dp.r_buf = P.r_buf * ib;
+  dp.r_inner = P.r_inner * ib;
+  dp.beta = P.beta;
+  dp.d = P.d;
+  dp.r2_scs_ang = P.r_scs * P.r_scs;
+  dp.r2_sphere_ang = rsph * rsph;
+  dp.r2_scs2_ang = 4.0 * P.r_scs * P.r_scs;
+  dp.r2_list_ang = rlist * rlist;
+  dp.n_freq = n_freq;
+  dp.nq = nq;
+  dp.order = 2;
+  dp.n_species = n_species;
+  double om[LMBD_MAX_FREQ], wt[LMBD_MAX_FREQ];
+  gauss_legendre_fixed(n_freq, P.omega_scale, om, wt);
+  for (int q = 0; q < n_freq; ++q) dp.omega[q + 1] = om[q];
+
+  // search grid
+  Grid g{};
+  if (cell) {
+    double hc[9];
+    CK(cudaMemcpy(hc, cell, sizeof(hc), cudaMemcpyDefault));
+    for (int i = 0; i < 9; ++i)
+      if (!std::isfinite(hc[i])) return LMBD_EINVAL;
+    double det = hc[0] * (hc[4] * hc[8] - hc[5] * hc[7]) - hc[1] * (hc[3] * hc[8] - hc[5] * hc[6]) +
+                 hc[2] * (hc[3] * hc[7] - hc[4] * hc[6]);
+    if (!(fabs(det) > 1e-9)) return LMBD_EINVAL;
+    g.periodic = 1;
+    memcpy(g.cell, hc, sizeof(hc));
+    double inv[9] = {(hc[4] * hc[8] - hc[5] * hc[7]) / det, -(hc[1] * hc[8] - hc[2] * hc[7]) / det,
+                     (hc[1] * hc[5] - hc[2] * hc[4]) / det, -(hc[3] * hc[8] - hc[5] * hc[6]) / det,
+                     (hc[0] * hc[8] - hc[2] * hc[6]) / det, -(hc[0] * hc[5] - hc[2] * hc[3]) / det,
+                     (hc[3] * hc[7] - hc[4] * hc[6]) / det, -(hc[0] * hc[7] - hc[1] * hc[6]) / det,
+                     (hc[0] * hc[4] - hc[1] * hc[3]) / det};
+    memcpy(g.inv, inv, sizeof(inv));
+    for (int d = 0; d < 3; ++d) {
+      const double* a = hc + 3 * ((d + 1) % 3);
+      const double* b = hc + 3 * ((d + 2) % 3);
+      double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2], cz = a[0] * b[1] - a[1] * b[0];
+      double width = fabs(det) / sqrt(cx * cx + cy * cy + cz * cz);
+      int nc = (int)(width / rlist);
+      if (nc < 1) nc = 1;
+      if (nc > 64) nc = 64;
+      g.nc[d] = nc;
+      g.reach[d] = (int)ceil(rlist / (width / nc) - 1e-12);
+      if (g.reach[d] < 1) g.reach[d] = 1;
+    }
+  }
+  const int ncells = cell ? g.nc[0] * g.nc[1] * g.nc[2] : 64 * 64 * 64;
+  const int site_cap = LMBD_NOALLOC_SITE_CAP;
+
+  // carve the scratch array
+  Carve cv{static_cast<unsigned char*>(base), 0, cap};
+  double* table = cv.take<double>(3 * (size_t)n_species);
+  double* pos = cv.take<double>(3 * (size_t)N);
+  int* spec = cv.take<int>(N);
+  double* nu = cv.take<double>(N);
+  Work w{};
+  w.n_atoms = N;
+  w.site_cap = site_cap;
+  w.abar = cv.take<double>((size_t)N * nq);
+  w.sig = cv.take<double>((size_t)N * nq);
+  w.rvdw = cv.take<double>(N);
+  w.a0 = cv.take<double>(N);
+  w.r0 = cv.take<double>(N);
+  w.wpos = cv.take<double>(3 * (size_t)N);
+  w.cell_of = cv.take<int>(N);
+  w.cell_count = cv.take<int>(ncells);
+  w.cell_start = cv.take<int>(ncells + 1);
+  w.cell_atoms = cv.take<int>(N);
+  w.ncells = ncells;
+  w.grid = cv.take<Grid>(1);
+  w.site_atom = cv.take<int>((size_t)N * site_cap);
+  w.site_x = cv.take<double>(3 * (size_t)N * site_cap);
+  w.counts = cv.take<Counts>(N);
+  w.off_k1 = cv.take<long long>(N + 1);
+  w.off_s = cv.take<long long>(N + 1);
+  w.off_b = cv.take<long long>(N + 1);
+  w.off_t = cv.take<long long>(N + 1);
+  w.totals = cv.take<long long>(8);
+  w.status = cv.take<int>(4);
+  w.alphaI = cv.take<double>((size_t)N * nq);
+  const long long slot_doubles = 9LL * LMBD_NOALLOC_MAX_K1 * LMBD_NOALLOC_MAX_K1;
+  if (!table || !pos || !spec || !nu || !w.alphaI) return LMBD_ESCRATCH;
+  size_t used = (cv.used + 255) & ~size_t(255);
+  long long nslots = (long long)((cap - used) / (sizeof(double) * slot_doubles));
+  if (nslots > 128) nslots = 128;
+  if (nslots < 1) return LMBD_ESCRATCH;
+  double* slots = cv.take<double>((size_t)nslots * slot_doubles);
+  if (!slots) return LMBD_ESCRATCH;
+  w.pos = pos;
+  w.species = spec;
+  w.nu = nu;
+  w.table = table;
+
+  // inputs into the scratch (host or device sources)
+  double htab[3 * 64];
+  for (int i = 0; i < n_species; ++i) {
+    htab[3 * i] = species_params[i].alpha0;
+    htab[3 * i + 1] = species_params[i].c6;
+    htab[3 * i + 2] = species_params[i].r0;
+  }
+  CK(cudaMemcpyAsync(table, htab, sizeof(double) * 3 * n_species, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(pos, positions, sizeof(double) * 3 * N, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(spec, species, sizeof(int) * N, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(nu, hirshfeld, sizeof(double) * N, cudaMemcpyDefault, s));
+  CK(cudaMemsetAsync(w.status, 0, sizeof(int) * 4, s));   // flags must start at zero
+
+  int launches = 0;
+  launch_free_atom(w, dp, s);
+  launch_neighbors(w, dp, g, s, &launches);
+  launch_offsets(w, dp, s);
+  CK(cudaGetLastError());
+  long long tot[8];
+  int flags = 0;
+  CK(cudaMemcpyAsync(tot, w.totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&flags, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flags & LMBD_FLAG_COINCIDENT) return LMBD_EINVAL;
+  if (flags & LMBD_FLAG_CAPACITY) return LMBD_ESCRATCH;
+  const int max_n1 = (int)tot[4], max_n12 = (int)tot[6];
+  if (max_n1 > LMBD_NOALLOC_MAX_K1 || max_n12 > site_cap) return LMBD_ESCRATCH;
+  launch_scs_central_noalloc(w, dp, slots, slot_doubles, (int)nslots, max_n12, max_n1, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(alpha_central, w.alphaI, sizeof(double) * N * nq, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(&flags, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flags & LMBD_FLAG_NOT_SPD) return LMBD_NOT_SPD;
+  return LMBD_OK;
+}
+
+}  // namespace
+
+extern "C" int lmbd_central_polarizabilities_noalloc(const lmbd_species* species_params, int n_species,
+                                                     const lmbd_params* params, int n_freq, int n_atoms,
+                                                     const double* positions, const double* cell,
+                                                     const int* species, const double* hirshfeld,
+                                                     double* alpha_central, void* stream) {
+  if (!species_params || !params || n_species <= 0 || n_species > 64 || n_freq < 1 || n_freq > LMBD_MAX_FREQ ||
+      n_atoms < 0)
+    return LMBD_EINVAL;
+  if (n_atoms > LMBD_NOALLOC_MAX_ATOMS) return LMBD_ESCRATCH;
+  if (n_atoms == 0) return LMBD_OK;
+  if (!positions || !species || !hirshfeld || !alpha_central) return LMBD_EINVAL;
+  int st = noalloc_central(species_params, n_species, params, n_freq, n_atoms, positions, cell, species,
+                           hirshfeld, alpha_central, (cudaStream_t)stream);
+  if (st != LMBD_OK) cudaGetLastError();
+  return st;
+}

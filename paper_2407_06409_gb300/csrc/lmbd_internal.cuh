@@ -192,3 +192,9 @@ void launch_mbd_adj_blend(const Work& w, const DevParams& p, int c0, int c1, cud
 void launch_scs_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1, int max_n12,
                               int max_n1, cudaStream_t s);
 void launch_forces_out(const Work& w, double* forces, cudaStream_t s);
+
+// Allocation-free entry point (lmbd_central_polarizabilities_noalloc): scratch lookup and
+// the persistent SCS kernel variant, both in k_scs.cu next to the static scratch array.
+int noalloc_scratch(void** ptr, size_t* bytes);
+void launch_scs_central_noalloc(const Work& w, const DevParams& p, double* bslots, long long slot_doubles,
+                                int nslots, int max_n12, int max_n1, cudaStream_t s);
