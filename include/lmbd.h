@@ -142,6 +142,16 @@ int lmbd_energy_forces_weighted(lmbd_ctx* ctx, int n_atoms, const double* positi
 #define LMBD_LAUNCH_PER_ATOM 1
 int lmbd_set_launch_mode(lmbd_ctx* ctx, int mode);
 
+/* Arithmetic of the two large matrix products (the Krylov chain T_LR W and the adjoint pair
+ * matrix P Q^T).  LMBD_PREC_SLICED (default) evaluates them on the bf16 tensor cores from
+ * exact 7-bit integer slices of the FP64 operands, recombined in FP64 (6 slices for the
+ * products that feed the energies, 5 for those that feed only the forces; truncation error
+ * ~S 2^-7S relative to sum |a||b|); LMBD_PREC_FP64 uses FP64 FMA kernels.  Everything
+ * else is FP64 (the SCS factorisation is FP32 with FP64 iterative refinement).            */
+#define LMBD_PREC_FP64   0
+#define LMBD_PREC_SLICED 1
+int lmbd_set_precision(lmbd_ctx* ctx, int mode);
+
 /* Per-phase device timing with CUDA events (0 = off, the default). */
 int lmbd_set_profiling(lmbd_ctx* ctx, int on);
 

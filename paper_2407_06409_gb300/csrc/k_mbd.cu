@@ -16,6 +16,7 @@
 //   dL/dalpha~_s = (1/alpha~_s) Tr[(dL/dG) G]_ss = (1/alpha~_s) sum_n c_n sum_j <v_j[s], v_{n-j}[s]>,
 //   dL/dT_st = sum_q D_s D_t (dL/dG)_st, contracted with dT_LR/dr and dT_LR/dS~ per pair.
 #include "lmbd_internal.cuh"
+#include "ozaki.cuh"
 
 // ---------------------------------------------------------------------------------------
 // prepare: blended polarisabilities, SCS radii, T_LR and the first Krylov block
@@ -308,13 +309,97 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
 #define PT 16
 #define PK 16
 
+// Site positions and SCS radii of the row (bi) and column (bj) site blocks of a pair tile.
+__device__ __forceinline__ void pair_tile_sites(const Work& w, const DevParams& p, long long offs, long long sbase,
+                                                int ns, int bi, int bj, double (*xs)[PT][3], double (*rts)[PT]) {
+  const int tid = threadIdx.x;
+  if (tid < 2 * PT) {
+    int side = tid / PT, l = tid % PT;
+    int s = (side == 0 ? bi : bj) * PT + l;
+    for (int d = 0; d < 3; ++d) xs[side][l][d] = s < ns ? w.site_x[3 * (sbase + s) + d] : 0.0;
+    double rt = 1.0;
+    if (s < ns) {
+      int a = w.site_atom[sbase + s];
+      rt = w.r0[a] * cbrt(w.alphaT[(offs + s) * p.nq] / w.a0[a]);
+    }
+    rts[side][l] = rt;
+  }
+}
+
+// Contribution of the site pair (s, t), s > t, to dL/dr and dL/dR~ from its pair-matrix
+// block acc = M_st (3 x 3, before the central-column term): T_LR,st = f_LR f(r, S~) T(r).
+// Returns g = dL/dr_t (= -dL/dr_s) in out[0..2] and the SCS-radius seed beta dL/dS~ in out[3]
+// (zeros when the pair does not couple).
+__device__ __forceinline__ void pair_epilogue(const Work& w, const DevParams& p, long long offs, int s, int t,
+                                              int ns, const double* xsv, const double* xtv, double rts_s,
+                                              double rts_t, double (&acc)[3][3], double* out) {
+  out[0] = out[1] = out[2] = out[3] = 0.0;
+  if (!(s < ns && t < ns && s > t)) return;
+  if (t == 0) {
+    const double* x0 = w.x0buf + (offs + s) * 9;
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+      for (int be = 0; be < 3; ++be) acc[al][be] += x0[al * 3 + be];
+  }
+  double rr[3] = {xtv[0] - xsv[0], xtv[1] - xsv[1], xtv[2] - xsv[2]};
+  double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+  double rc = (t == 0) ? p.r_mbd1 : p.r_mbd2;
+  if (!(r2 < rc * rc)) return;
+  double r = sqrt(r2);
+  double flr, dflr, f, dfr, dfs;
+  double St = p.beta * (rts_s + rts_t);
+  cutoff_buf(r, rc, p.r_buf, flr, dflr);
+  fermi(r, St, p.d, f, dfr, dfs);
+  double C = flr * f, dC = dflr * f + flr * dfr, CS = flr * dfs;
+  double M[6] = {acc[0][0], acc[1][1], acc[2][2], 0.5 * (acc[0][1] + acc[1][0]),
+                 0.5 * (acc[0][2] + acc[2][0]), 0.5 * (acc[1][2] + acc[2][1])};
+  double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2], M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
+                  M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
+  double trM = M[0] + M[1] + M[2];
+  double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
+  double ir = 1.0 / r, ir2 = ir * ir;
+  double ir3 = ir2 * ir, ir5 = ir3 * ir2, ir7 = ir5 * ir2;
+  double psi = 3.0 * rMr * ir5 - trM * ir3;
+  double radial = 2.0 * (dC * psi * ir + C * (-15.0 * rMr * ir7 + 3.0 * trM * ir5));
+  double tang = 2.0 * C * 6.0 * ir5;
+  out[0] = radial * rr[0] + tang * Mr[0];
+  out[1] = radial * rr[1] + tang * Mr[1];
+  out[2] = radial * rr[2] + tang * Mr[2];
+  out[3] = 2.0 * CS * psi * p.beta;
+}
+
+// Deterministic reduction of the 16 x 16 pair results of a tile to its row sites (-g, seed)
+// and column sites (+g, seed), then one global atomic per site.
+__device__ __forceinline__ void pair_tile_reduce(const Work& w, long long offs, long long sbase, int ns, int bi,
+                                                 int bj, double (*gp)[PT][4]) {
+  const int tid = threadIdx.x;
+  if (tid < 2 * PT) {
+    const int side = tid / PT, l = tid % PT;
+    const int ss = (side == 0 ? bi : bj) * PT + l;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0, sb = 0.0;
+    for (int o = 0; o < PT; ++o) {
+      const double* v = side == 0 ? gp[l][o] : gp[o][l];
+      g0 += v[0];
+      g1 += v[1];
+      g2 += v[2];
+      sb += v[3];
+    }
+    if (ss < ns) {
+      const double sgn = side == 0 ? -1.0 : 1.0;
+      const int a = w.site_atom[sbase + ss];
+      if (g0 != 0.0 || g1 != 0.0 || g2 != 0.0) atomic_add3(w.gacc + 3 * a, sgn * g0, sgn * g1, sgn * g2);
+      if (sb != 0.0) atomicAdd(&w.rbar[offs + ss], sb);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_mbd_adj_pair(Work w, DevParams p, int c0, int tiles_per_c) {
   __shared__ double Ps[3 * PT][PK + 1];
   __shared__ double Qs[3 * PT][PK + 1];
-  __shared__ double xs[2][3][PT];
+  __shared__ double xs[2][PT][3];
   __shared__ double rts[2][PT];
-  __shared__ double gacc_s[2][PT][3];
-  __shared__ double racc_s[2][PT];
+  __shared__ double gp[PT][PT][4];
   const int c = c0 + blockIdx.x / tiles_per_c;
   int tile = blockIdx.x % tiles_per_c;
   if (c >= w.n_atoms) return;
@@ -328,19 +413,7 @@ __global__ void __launch_bounds__(256) k_mbd_adj_pair(Work w, DevParams p, int c
   const long long sbase = (long long)c * w.site_cap;
   const int tid = threadIdx.x;
   const int ty = tid / PT, tx = tid % PT;
-  if (tid < 2 * PT) {
-    int side = tid / PT, l = tid % PT;
-    int s = (side == 0 ? bi : bj) * PT + l;
-    for (int d = 0; d < 3; ++d) xs[side][d][l] = s < ns ? w.site_x[3 * (sbase + s) + d] : 0.0;
-    double rt = 1.0;
-    if (s < ns) {
-      int a = w.site_atom[sbase + s];
-      rt = w.r0[a] * cbrt(w.alphaT[(offs + s) * p.nq] / w.a0[a]);
-    }
-    rts[side][l] = rt;
-    gacc_s[side][l][0] = gacc_s[side][l][1] = gacc_s[side][l][2] = 0.0;
-    racc_s[side][l] = 0.0;
-  }
+  pair_tile_sites(w, p, offs, sbase, ns, bi, bj, xs, rts);
   const int s = bi * PT + ty, t = bj * PT + tx;
   double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   const int ncol = w.ncol;
@@ -363,55 +436,10 @@ __global__ void __launch_bounds__(256) k_mbd_adj_pair(Work w, DevParams p, int c
       acc[2][0] += a2 * b0; acc[2][1] += a2 * b1; acc[2][2] += a2 * b2;
     }
   }
+  __syncthreads();   // site data of the tile visible to all threads (also when ncol = 0)
+  pair_epilogue(w, p, offs, s, t, ns, xs[0][ty], xs[1][tx], rts[0][ty], rts[1][tx], acc, gp[ty][tx]);
   __syncthreads();
-  if (s < ns && t < ns && s > t) {
-    if (t == 0) {
-      const double* x0 = w.x0buf + (offs + s) * 9;
-#pragma unroll
-      for (int al = 0; al < 3; ++al)
-#pragma unroll
-        for (int be = 0; be < 3; ++be) acc[al][be] += x0[al * 3 + be];
-    }
-    double rr[3] = {xs[1][0][tx] - xs[0][0][ty], xs[1][1][tx] - xs[0][1][ty], xs[1][2][tx] - xs[0][2][ty]};
-    double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
-    double rc = (t == 0) ? p.r_mbd1 : p.r_mbd2;
-    if (r2 < rc * rc) {
-      double r = sqrt(r2);
-      double flr, dflr, f, dfr, dfs;
-      double St = p.beta * (rts[0][ty] + rts[1][tx]);
-      cutoff_buf(r, rc, p.r_buf, flr, dflr);
-      fermi(r, St, p.d, f, dfr, dfs);
-      double C = flr * f, dC = dflr * f + flr * dfr, CS = flr * dfs;
-      double M[6] = {acc[0][0], acc[1][1], acc[2][2], 0.5 * (acc[0][1] + acc[1][0]),
-                     0.5 * (acc[0][2] + acc[2][0]), 0.5 * (acc[1][2] + acc[2][1])};
-      double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2],
-                      M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
-                      M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
-      double trM = M[0] + M[1] + M[2];
-      double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
-      double ir2 = 1.0 / r2, ir = sqrt(ir2);
-      double ir3 = ir2 * ir, ir5 = ir3 * ir2, ir7 = ir5 * ir2;
-      double psi = 3.0 * rMr * ir5 - trM * ir3;
-      double radial = 2.0 * (dC * psi * ir + C * (-15.0 * rMr * ir7 + 3.0 * trM * ir5));
-      double tang = 2.0 * C * 6.0 * ir5;
-      double g[3] = {radial * rr[0] + tang * Mr[0], radial * rr[1] + tang * Mr[1], radial * rr[2] + tang * Mr[2]};
-      double sbar = 2.0 * CS * psi * p.beta;
-      atomicAdd(&gacc_s[1][tx][0], g[0]); atomicAdd(&gacc_s[1][tx][1], g[1]); atomicAdd(&gacc_s[1][tx][2], g[2]);
-      atomicAdd(&gacc_s[0][ty][0], -g[0]); atomicAdd(&gacc_s[0][ty][1], -g[1]); atomicAdd(&gacc_s[0][ty][2], -g[2]);
-      atomicAdd(&racc_s[0][ty], sbar);
-      atomicAdd(&racc_s[1][tx], sbar);
-    }
-  }
-  __syncthreads();
-  if (tid < 2 * PT) {
-    int side = tid / PT, l = tid % PT;
-    int ss = (side == 0 ? bi : bj) * PT + l;
-    if (ss < ns) {
-      int a = w.site_atom[sbase + ss];
-      atomic_add3(w.gacc + 3 * a, gacc_s[side][l][0], gacc_s[side][l][1], gacc_s[side][l][2]);
-      atomicAdd(&w.rbar[offs + ss], racc_s[side][l]);
-    }
-  }
+  pair_tile_reduce(w, offs, sbase, ns, bi, bj, gp);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -502,4 +530,229 @@ __global__ void k_forces_out(Work w, double* forces) {
 void launch_forces_out(const Work& w, double* forces, cudaStream_t s) {
   if (w.n_atoms == 0) return;
   k_forces_out<<<(3 * w.n_atoms + 255) / 256, 256, 0, s>>>(w, forces);
+}
+
+// =======================================================================================
+// Sliced tensor-core products (ozaki.cuh): the Krylov chain T W and the pair matrix P Q^T
+// evaluated from 7-bit digit planes on bf16 mma.sync, combined in FP64.
+// Per central atom (N = 3 ns): T digit planes [Mpad][Kpad] with Mpad = 64 ceil(N/64),
+// Kpad = 16 ceil(N/16); W^T digit planes [48][Kpad]; P and Q digit planes [3 ns16][Kp] with
+// ns16 = 16 ceil(ns/16) and Kp = 16 ceil(ncol/16).
+// =======================================================================================
+__device__ __forceinline__ int oz_mpad(int n) { return (n + 63) / 64 * 64; }
+__device__ __forceinline__ int oz_kpad(int n) { return (n + 15) / 16 * 16; }
+
+// T_LR digit planes and row exponents (one block per central atom, one warp per row).
+__global__ void __launch_bounds__(256) k_slice_t(Work w, int c0, int st) {
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const int N = 3 * w.counts[c].ns, Mpad = oz_mpad(N), Kpad = oz_kpad(N);
+  const double* T = w.tlr + w.off_t[c];
+  unsigned short* base = w.tdig + w.off_tq[c] * st;
+  const long long plane = (long long)Mpad * Kpad;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = warp; row < Mpad; row += nw) {
+    int mx = 0;
+    if (row < N)
+      for (int j = lane; j < N; j += 32) mx = max(mx, oz_biased_exp(T[(long long)row * N + j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = oz_scale_exp(mx);
+    if (lane == 0) w.texp[w.off_tr[c] + row] = e;
+    for (int j = lane; j < Kpad; j += 32) {
+      const double v = (row < N && j < N) ? T[(long long)row * N + j] : 0.0;
+      int d[OZ_MAXS];
+      oz_digits(v, e, st, d);
+      for (int k = 0; k < st; ++k) base[k * plane + (long long)row * Kpad + j] = oz_bf16_bits(d[k]);
+    }
+  }
+}
+
+// W = D v_m digit planes (stored by column) and column exponents (one block per atom).
+__global__ void __launch_bounds__(256) k_slice_w(Work w, DevParams p, int m, int c0, int sw) {
+  __shared__ int cmax[48];
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const int N = 3 * w.counts[c].ns, Kpad = oz_kpad(N);
+  const long long offs = w.off_s[c];
+  const int ncv = 3 * p.n_freq;
+  const double* Vin = w.vkr + (long long)(m - 1) * w.vstride + (offs * 3) * ncv;
+  const double* dsq = w.dsq + offs * p.nq;
+  unsigned short* base = w.wdig + w.off_kp[c] * 48 * sw;
+  const long long plane = 48LL * Kpad;
+  const int tid = threadIdx.x;
+  if (tid < 48) cmax[tid] = 0;
+  __syncthreads();
+  for (int e = tid; e < N * ncv; e += blockDim.x) {
+    const int j = e / ncv, col = e % ncv;
+    const double v = dsq[(j / 3) * p.nq + col / 3 + 1] * Vin[(long long)j * ncv + col];
+    atomicMax(&cmax[col], oz_biased_exp(v));
+  }
+  __syncthreads();
+  if (tid < 48) w.wexp[(long long)c * 48 + tid] = oz_scale_exp(cmax[tid]);
+  for (int e = tid; e < 48 * Kpad; e += blockDim.x) {
+    const int col = e / Kpad, j = e % Kpad;
+    double v = 0.0;
+    if (col < ncv && j < N) v = dsq[(j / 3) * p.nq + col / 3 + 1] * Vin[(long long)j * ncv + col];
+    int d[OZ_MAXS];
+    oz_digits(v, oz_scale_exp(cmax[col]), sw, d);
+    for (int k = 0; k < sw; ++k) base[k * plane + (long long)col * Kpad + j] = oz_bf16_bits(d[k]);
+  }
+}
+
+// v_{m+1} = D (T W): 64 output rows x 48 columns per block, 12 warps of 16 x 16.
+template <int S>
+__global__ void __launch_bounds__(384) k_chain_oz(Work w, DevParams p, int m, int c0, int tiles_per_c, int st) {
+  const int c = c0 + blockIdx.x / tiles_per_c;
+  const int tile = blockIdx.x % tiles_per_c;
+  if (c >= w.n_atoms) return;
+  const int N = 3 * w.counts[c].ns, Mpad = oz_mpad(N), Kpad = oz_kpad(N);
+  if (tile * 64 >= N) return;
+  const long long offs = w.off_s[c];
+  const int ncv = 3 * p.n_freq;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+  const int wr = warp / 3, wc = warp % 3;
+  const int r0 = tile * 64 + wr * 16, cb = wc * 16;
+  const unsigned short* A = w.tdig + w.off_tq[c] * st + (long long)r0 * Kpad;
+  const unsigned short* B = w.wdig + w.off_kp[c] * 48 * S + (long long)cb * Kpad;
+  double y[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  int er[2], ec[2][2];
+  er[0] = w.texp[w.off_tr[c] + r0 + g];
+  er[1] = w.texp[w.off_tr[c] + r0 + g + 8];
+  for (int nt = 0; nt < 2; ++nt)
+    for (int h = 0; h < 2; ++h) ec[nt][h] = w.wexp[(long long)c * 48 + cb + nt * 8 + 2 * tq + h];
+  for (int kb = 0; kb < Kpad; kb += OZ_KCHUNK) {
+    float acc[S][2][4];
+    oz_warp_tile<S>(A, Kpad, (long long)Mpad * Kpad, B, Kpad, 48LL * Kpad, kb, min(kb + OZ_KCHUNK, Kpad), acc);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) y[nt][v] += oz_combine<S>(acc, nt, v, er[v >> 1], ec[nt][v & 1]);
+  }
+  double* Vout = w.vkr + (long long)m * w.vstride + (offs * 3) * ncv;
+  const double* dsq = w.dsq + offs * p.nq;
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int row = r0 + g + (v >> 1) * 8, col = cb + nt * 8 + 2 * tq + (v & 1);
+      if (row < N && col < ncv) Vout[(long long)row * ncv + col] = dsq[(row / 3) * p.nq + col / 3 + 1] * y[nt][v];
+    }
+}
+
+// P and Q digit planes and row exponents (blockIdx.y = 0: P, 1: Q).
+__global__ void __launch_bounds__(256) k_slice_pq(Work w, int c0, int sp) {
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns, R = 3 * ((ns + 15) / 16 * 16), rows = 3 * ns;
+  const int ncol = w.ncol, Kp = oz_kpad(ncol);
+  const long long offs = w.off_s[c];
+  const double* src = (blockIdx.y == 0 ? w.pmat : w.qmat) + offs * 3 * (long long)ncol;
+  unsigned short* base = (blockIdx.y == 0 ? w.pdig : w.qdig) + w.off_sp[c] * 3 * (long long)Kp * sp;
+  int* ex = (blockIdx.y == 0 ? w.pexp : w.qexp) + w.off_sp[c] * 3;
+  const long long plane = (long long)R * Kp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = warp; row < R; row += nw) {
+    int mx = 0;
+    if (row < rows)
+      for (int j = lane; j < ncol; j += 32) mx = max(mx, oz_biased_exp(src[(long long)row * ncol + j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = oz_scale_exp(mx);
+    if (lane == 0) ex[row] = e;
+    for (int j = lane; j < Kp; j += 32) {
+      const double v = (row < rows && j < ncol) ? src[(long long)row * ncol + j] : 0.0;
+      int d[OZ_MAXS];
+      oz_digits(v, e, sp, d);
+      for (int k = 0; k < sp; ++k) base[k * plane + (long long)row * Kp + j] = oz_bf16_bits(d[k]);
+    }
+  }
+}
+
+// Pair matrix M' = P Q^T on one 16 x 16 site tile (48 x 48 values, 9 warps of 16 x 16) from
+// digit planes, then the same per-pair epilogue as the FP64 kernel.
+template <int S>
+__global__ void __launch_bounds__(288) k_mbd_adj_pair_oz(Work w, DevParams p, int c0, int tiles_per_c) {
+  __shared__ double Ms[3 * PT][3 * PT + 1];
+  __shared__ double xs[2][PT][3];
+  __shared__ double rts[2][PT];
+  __shared__ double gp[PT][PT][4];
+  const int c = c0 + blockIdx.x / tiles_per_c;
+  const int tile = blockIdx.x % tiles_per_c;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns;
+  const int nt = (ns + PT - 1) / PT;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int bi = 0;
+  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+  const int bj = tile - bi * (bi + 1) / 2;
+  const long long offs = w.off_s[c];
+  const long long sbase = (long long)c * w.site_cap;
+  const int tid = threadIdx.x;
+  pair_tile_sites(w, p, offs, sbase, ns, bi, bj, xs, rts);
+  const int R = 3 * nt * PT, Kp = oz_kpad(w.ncol);
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const int wr = warp / 3, wc = warp % 3;
+  const long long dbase = w.off_sp[c] * 3 * (long long)Kp * S;
+  const unsigned short* A = w.pdig + dbase + (long long)(bi * 48 + wr * 16) * Kp;
+  const unsigned short* B = w.qdig + dbase + (long long)(bj * 48 + wc * 16) * Kp;
+  const int* pe = w.pexp + w.off_sp[c] * 3;
+  const int* qe = w.qexp + w.off_sp[c] * 3;
+  const int ra = bi * 48 + wr * 16 + g, cbs = bj * 48 + wc * 16;
+  double y[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (int kb = 0; kb < Kp; kb += OZ_KCHUNK) {
+    float acc[S][2][4];
+    oz_warp_tile<S>(A, Kp, (long long)R * Kp, B, Kp, (long long)R * Kp, kb, min(kb + OZ_KCHUNK, Kp), acc);
+#pragma unroll
+    for (int n8 = 0; n8 < 2; ++n8)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        y[n8][v] += oz_combine<S>(acc, n8, v, pe[ra + (v >> 1) * 8], qe[cbs + n8 * 8 + 2 * tq + (v & 1)]);
+  }
+#pragma unroll
+  for (int n8 = 0; n8 < 2; ++n8)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Ms[wr * 16 + g + (v >> 1) * 8][wc * 16 + n8 * 8 + 2 * tq + (v & 1)] = y[n8][v];
+  __syncthreads();
+  if (tid < PT * PT) {
+    const int ty = tid / PT, tx = tid % PT;
+    const int s = bi * PT + ty, t = bj * PT + tx;
+    double acc[3][3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+      for (int be = 0; be < 3; ++be) acc[al][be] = Ms[3 * ty + al][3 * tx + be];
+    pair_epilogue(w, p, offs, s, t, ns, xs[0][ty], xs[1][tx], rts[0][ty], rts[1][tx], acc, gp[ty][tx]);
+  }
+  __syncthreads();
+  pair_tile_reduce(w, offs, sbase, ns, bi, bj, gp);
+}
+
+void launch_slice_t(const Work& w, int c0, int c1, int st, cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_slice_t<<<c1 - c0, 256, 0, s>>>(w, c0, st);
+}
+
+void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
+                     cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_slice_w<<<c1 - c0, 256, 0, s>>>(w, p, m, c0, digits);
+  const int tiles = (3 * max_ns + 63) / 64;
+  if (digits == 6)
+    k_chain_oz<6><<<(c1 - c0) * tiles, 384, 0, s>>>(w, p, m, c0, tiles, st);
+  else
+    k_chain_oz<5><<<(c1 - c0) * tiles, 384, 0, s>>>(w, p, m, c0, tiles, st);
+}
+
+void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
+                            cudaStream_t s) {
+  if (c1 <= c0) return;
+  dim3 g2(c1 - c0, 2);
+  k_slice_pq<<<g2, 256, 0, s>>>(w, c0, digits);
+  const int nt = (max_ns + PT - 1) / PT;
+  const int tiles = nt * (nt + 1) / 2;
+  if (digits == 6)
+    k_mbd_adj_pair_oz<6><<<(c1 - c0) * tiles, 288, 0, s>>>(w, p, c0, tiles);
+  else
+    k_mbd_adj_pair_oz<5><<<(c1 - c0) * tiles, 288, 0, s>>>(w, p, c0, tiles);
 }

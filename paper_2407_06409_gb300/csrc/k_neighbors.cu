@@ -292,58 +292,86 @@ void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStre
 
 // ---------------------------------------------------------------------------------------
 // per-centre offsets into the variable-size workspaces (one block, 64-bit scans)
-// totals: [0] sum n1, [1] sum ns, [2] sum nq (3 n1)^2, [3] sum (3 ns)^2,
-//         [4] max n1, [5] max ns, [6] max n12, [7] sum nt
+// totals: [0] sum n1, [1] sum ns, [2] sum nq N1(N1+1)/2 (packed factors, N1 = 3 n1),
+//         [3] sum (3 ns)^2, [4] max n1, [5] max ns, [6] max n12, [7] sum nt,
+//         [8] sum of SCS pairs, [9] sum of SCS adjacency entries, [10] max pairs,
+//         [12] sum Mpad Kpad, [13] sum Mpad, [14] sum Kpad, [15] sum ns16 (sliced products)
 // ---------------------------------------------------------------------------------------
+#define OFF_T 512
 __global__ void k_offsets(Work w, int nq) {
-  __shared__ long long part[4][512];
-  __shared__ int mx[3][512];
-  __shared__ long long tot_nt[512];
+  __shared__ long long part[10][OFF_T];
+  __shared__ int mx[4][OFF_T];
+  __shared__ long long tot_nt[OFF_T];
   int N = w.n_atoms;
   int per = (N + blockDim.x - 1) / blockDim.x;
   int b = threadIdx.x * per, e = min(N, b + per);
-  long long s[4] = {0, 0, 0, 0};
-  int m[3] = {0, 0, 0};
+  long long s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int m[4] = {0, 0, 0, 0};
   long long snt = 0;
   for (int i = b; i < e; ++i) {
     Counts c = w.counts[i];
+    long long N1 = 3LL * c.n1;
+    int np = w.pcount ? w.pcount[2 * i] : 0, na = w.pcount ? w.pcount[2 * i + 1] : 0;
     s[0] += c.n1;
     s[1] += c.ns;
-    s[2] += (long long)nq * 9 * c.n1 * c.n1;
+    s[2] += (long long)nq * N1 * (N1 + 1) / 2;
     s[3] += 9LL * c.ns * c.ns;
+    s[4] += np;
+    s[5] += na;
+    const long long Nn = 3LL * c.ns, Mp = (Nn + 63) / 64 * 64, Kp = (Nn + 15) / 16 * 16;
+    s[6] += Mp * Kp;
+    s[7] += Mp;
+    s[8] += Kp;
+    s[9] += (c.ns + 15) / 16 * 16;
     m[0] = max(m[0], c.n1);
     m[1] = max(m[1], c.ns);
     m[2] = max(m[2], c.n12);
+    m[3] = max(m[3], np);
     snt += c.nt;
   }
-  for (int t = 0; t < 4; ++t) part[t][threadIdx.x] = s[t];
-  for (int t = 0; t < 3; ++t) mx[t][threadIdx.x] = m[t];
+  for (int t = 0; t < 10; ++t) part[t][threadIdx.x] = s[t];
+  for (int t = 0; t < 4; ++t) mx[t][threadIdx.x] = m[t];
   tot_nt[threadIdx.x] = snt;
   __syncthreads();
   for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-    long long v[4];
-    for (int t = 0; t < 4; ++t) v[t] = threadIdx.x >= off ? part[t][threadIdx.x - off] : 0;
+    long long v[10];
+    for (int t = 0; t < 10; ++t) v[t] = threadIdx.x >= off ? part[t][threadIdx.x - off] : 0;
     __syncthreads();
-    for (int t = 0; t < 4; ++t) part[t][threadIdx.x] += v[t];
+    for (int t = 0; t < 10; ++t) part[t][threadIdx.x] += v[t];
     __syncthreads();
   }
-  long long run[4];
-  for (int t = 0; t < 4; ++t) run[t] = part[t][threadIdx.x] - s[t];
+  long long run[10];
+  for (int t = 0; t < 10; ++t) run[t] = part[t][threadIdx.x] - s[t];
   for (int i = b; i < e; ++i) {
     Counts c = w.counts[i];
+    long long N1 = 3LL * c.n1;
     w.off_k1[i] = run[0];
     w.off_s[i] = run[1];
     w.off_b[i] = run[2];
     w.off_t[i] = run[3];
+    if (w.off_p) w.off_p[i] = run[4];
+    if (w.off_a) w.off_a[i] = run[5];
+    if (w.off_tq) {
+      w.off_tq[i] = run[6];
+      w.off_tr[i] = run[7];
+      w.off_kp[i] = run[8];
+      w.off_sp[i] = run[9];
+    }
+    const long long Nn = 3LL * c.ns, Mp = (Nn + 63) / 64 * 64, Kp = (Nn + 15) / 16 * 16;
+    run[6] += Mp * Kp;
+    run[7] += Mp;
+    run[8] += Kp;
+    run[9] += (c.ns + 15) / 16 * 16;
     run[0] += c.n1;
     run[1] += c.ns;
-    run[2] += (long long)nq * 9 * c.n1 * c.n1;
+    run[2] += (long long)nq * N1 * (N1 + 1) / 2;
     run[3] += 9LL * c.ns * c.ns;
+    run[4] += w.pcount ? w.pcount[2 * i] : 0;
+    run[5] += w.pcount ? w.pcount[2 * i + 1] : 0;
   }
-  // reductions of the maxima and of sum nt
   for (int st = blockDim.x / 2; st > 0; st >>= 1) {
     if (threadIdx.x < st) {
-      for (int t = 0; t < 3; ++t) mx[t][threadIdx.x] = max(mx[t][threadIdx.x], mx[t][threadIdx.x + st]);
+      for (int t = 0; t < 4; ++t) mx[t][threadIdx.x] = max(mx[t][threadIdx.x], mx[t][threadIdx.x + st]);
       tot_nt[threadIdx.x] += tot_nt[threadIdx.x + st];
     }
     __syncthreads();
@@ -353,17 +381,30 @@ __global__ void k_offsets(Work w, int nq) {
     w.off_s[N] = part[1][threadIdx.x];
     w.off_b[N] = part[2][threadIdx.x];
     w.off_t[N] = part[3][threadIdx.x];
+    if (w.off_p) w.off_p[N] = part[4][threadIdx.x];
+    if (w.off_a) w.off_a[N] = part[5][threadIdx.x];
     for (int t = 0; t < 4; ++t) w.totals[t] = part[t][threadIdx.x];
+    w.totals[8] = part[4][threadIdx.x];
+    w.totals[9] = part[5][threadIdx.x];
+    for (int t = 6; t < 10; ++t) w.totals[6 + t] = part[t][threadIdx.x];
+    if (w.off_tq) {
+      w.off_tq[N] = part[6][threadIdx.x];
+      w.off_tr[N] = part[7][threadIdx.x];
+      w.off_kp[N] = part[8][threadIdx.x];
+      w.off_sp[N] = part[9][threadIdx.x];
+    }
   }
   if (threadIdx.x == 0) {
     w.totals[4] = mx[0][0];
     w.totals[5] = mx[1][0];
     w.totals[6] = mx[2][0];
     w.totals[7] = tot_nt[0];
+    w.totals[10] = mx[3][0];
+    w.totals[11] = 0;
   }
 }
 
 void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s) {
   if (w.n_atoms == 0) return;
-  k_offsets<<<1, 512, 0, s>>>(w, p.nq);
+  k_offsets<<<1, OFF_T, 0, s>>>(w, p.nq);
 }

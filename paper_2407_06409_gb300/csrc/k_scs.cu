@@ -1,13 +1,12 @@
-// Stage 1: local self-consistent screening (Sec. III.B, Eq. local_pol).
-//
-// For every central atom k and every frequency omega_q (q = 0 is omega = 0):
+// Stage 1 in FP64 for the allocation-free entry point (lmbd_central_polarizabilities_noalloc):
+// local self-consistent screening (Sec. III.B, Eq. local_pol) for every central atom k and
+// frequency omega_q (q = 0 is omega = 0):
 //   B_K = diag(1/alpha_bar_i) + T_SR,K,ij     (i, j in K1, Eq. local_pol)
 //   d_K,i = 1 - sum_{j in K2} T_SR,K,ij alpha_bar_j
 //   X = B_K^-1 d_K  (3 n1 x 3), alpha_K,i = Tr(X_i)/3, alpha_I,k = alpha_K,k
-// T_SR,K,ij = f_inner f_SR (1 - f(r, S_ij)) (-T g + h) (Eqs. T_SR, g-func, h-func).
-// B_K is factorised in place (Cholesky, lower) in the workspace and kept for
-// the adjoint, which solves B_K lambda = dL/dX with the same factor and
-// contracts dB/dr and dd/dr pair by pair (Sec. III.D: dalpha = B^-1 (dd - dB alpha)).
+// T_SR,K,ij = f_inner f_SR (1 - f(r, S_ij)) (-T g + h) (Eqs. T_SR, g-func, h-func), factorised
+// with an FP64 blocked Cholesky.  The main path (k_scs2.cu) solves the same systems in mixed
+// precision.
 #include "lmbd_internal.cuh"
 
 #define NB 16
@@ -230,272 +229,6 @@ __device__ __forceinline__ bool tsr_pair(const DevParams& p, double r, double s_
   tsr_value(r, sig_ij, A0, B0);
   return true;
 }
-
-// ---------------------------------------------------------------------------------------
-// forward: assemble, factor, solve; one block per central atom, loop over frequencies
-// ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scs_forward(Work w, DevParams p, int c0, int max_n12, int max_n1) {
-  extern __shared__ double smem_d[];
-  const int c = c0 + blockIdx.x;
-  if (c >= w.n_atoms) return;
-  const Counts cn = w.counts[c];
-  const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
-  ScsSmem sm = scs_carve(smem_d, max_n12, max_n1, false);
-  const int tid = threadIdx.x;
-  const long long sbase = (long long)c * w.site_cap;
-  for (int s = tid; s < n12; s += blockDim.x) {
-    int a = w.site_atom[sbase + s];
-    sm.x[s] = w.site_x[3 * (sbase + s) + 0];
-    sm.x[max_n12 + s] = w.site_x[3 * (sbase + s) + 1];
-    sm.x[2 * max_n12 + s] = w.site_x[3 * (sbase + s) + 2];
-    sm.rv[s] = w.rvdw[a];
-  }
-  __shared__ int bad;
-  if (tid == 0) bad = 0;
-  const long long offk1 = w.off_k1[c];
-  const int npair = n1 * (n1 - 1) / 2;
-  for (int q = 0; q < p.nq; ++q) {
-    __syncthreads();
-    for (int s = tid; s < n12; s += blockDim.x) {
-      int a = w.site_atom[sbase + s];
-      sm.ab[s] = w.abar[a * p.nq + q];
-      sm.sg[s] = w.sig[a * p.nq + q];
-    }
-    __syncthreads();
-    double* B = w.bmat + w.off_b[c] + (long long)q * N1 * N1;
-    // diagonal blocks: 1/alpha_bar on the diagonal
-    for (int e = tid; e < n1 * 6; e += blockDim.x) {
-      int i = e / 6, t = e % 6;
-      int al = t < 3 ? t : (t == 3 ? 1 : 2), be = t < 3 ? t : (t == 3 ? 0 : (t == 4 ? 0 : 1));
-      B[(long long)(3 * i + al) * N1 + 3 * i + be] = (al == be) ? 1.0 / sm.ab[i] : 0.0;
-    }
-    // coupled pairs i > j in K1
-    for (int e = tid; e < npair; e += blockDim.x) {
-      int i = (int)((sqrtf(8.0f * e + 1.0f) + 1.0f) * 0.5f);
-      while (i * (i - 1) / 2 > e) --i;
-      while ((i + 1) * i / 2 <= e) ++i;
-      int j = e - i * (i - 1) / 2;
-      double rx = sm.x[j] - sm.x[i];
-      double ry = sm.x[max_n12 + j] - sm.x[max_n12 + i];
-      double rz = sm.x[2 * max_n12 + j] - sm.x[2 * max_n12 + i];
-      double r = sqrt(rx * rx + ry * ry + rz * rz);
-      double F = 0.0, A0 = 0.0, B0 = 0.0;
-      double sig = sqrt(sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j]);
-      if (!tsr_pair(p, r, p.beta * (sm.rv[i] + sm.rv[j]), sig, false, F, A0, B0)) F = 0.0;
-      double a = F * A0, b = F * B0;
-      double rr[3] = {rx, ry, rz};
-      double* blk = B + (long long)(3 * i) * N1 + 3 * j;
-#pragma unroll
-      for (int al = 0; al < 3; ++al)
-#pragma unroll
-        for (int be = 0; be < 3; ++be)
-          blk[(long long)al * N1 + be] = b * rr[al] * rr[be] + (al == be ? a : 0.0);
-    }
-    // right-hand side: one warp per coupled site i, lanes over K2 partners
-    const int warp = tid / 32, lane = tid % 32;
-    for (int i = warp; i < n1; i += blockDim.x / 32) {
-      double acc[6] = {0, 0, 0, 0, 0, 0};
-      double xi = sm.x[i], yi = sm.x[max_n12 + i], zi = sm.x[2 * max_n12 + i];
-      for (int j = n1 + lane; j < n12; j += 32) {
-        double rx = sm.x[j] - xi, ry = sm.x[max_n12 + j] - yi, rz = sm.x[2 * max_n12 + j] - zi;
-        double r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 >= p.r_scs * p.r_scs) continue;
-        double r = sqrt(r2);
-        double F, A0, B0;
-        double sig = sqrt(sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j]);
-        if (!tsr_pair(p, r, p.beta * (sm.rv[i] + sm.rv[j]), sig, true, F, A0, B0)) continue;
-        double a = F * A0 * sm.ab[j], b = F * B0 * sm.ab[j];
-        acc[0] += a + b * rx * rx;
-        acc[1] += a + b * ry * ry;
-        acc[2] += a + b * rz * rz;
-        acc[3] += b * rx * ry;
-        acc[4] += b * rx * rz;
-        acc[5] += b * ry * rz;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int t = 0; t < 6; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-      if (lane == 0) {
-        double* y = sm.y + 9 * i;
-        y[0] = 1.0 - acc[0]; y[1] = -acc[3];      y[2] = -acc[4];
-        y[3] = -acc[3];      y[4] = 1.0 - acc[1]; y[5] = -acc[5];
-        y[6] = -acc[4];      y[7] = -acc[5];      y[8] = 1.0 - acc[2];
-      }
-    }
-    __threadfence_block();
-    __syncthreads();
-    block_cholesky(B, N1, sm.panel, sm.dg, sm.inv, &bad);
-    block_solve3(B, N1, sm.inv, sm.y, sm.red);
-    // outputs
-    double* X = w.xsol + offk1 * p.nq * 9 + (long long)q * N1 * 3;
-    for (int e = tid; e < N1 * 3; e += blockDim.x) X[e] = sm.y[e];
-    for (int i = tid; i < n1; i += blockDim.x) {
-      double a = (sm.y[9 * i + 0] + sm.y[9 * i + 4] + sm.y[9 * i + 8]) / 3.0;
-      w.alphaK[(offk1 + i) * p.nq + q] = a;
-      if (i == 0) w.alphaI[(long long)c * p.nq + q] = a;
-    }
-  }
-  __syncthreads();
-  if (tid == 0 && bad) atomicOr(w.status, LMBD_FLAG_NOT_SPD);
-}
-
-void launch_scs_forward_sized(const Work& w, const DevParams& p, int c0, int c1, int max_n12,
-                              int max_n1, cudaStream_t s) {
-  if (c1 <= c0) return;
-  size_t sm = scs_smem_bytes(max_n12, max_n1, false);
-  cudaFuncSetAttribute(k_scs_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_scs_forward<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_n12, max_n1);
-}
-
-// ---------------------------------------------------------------------------------------
-// adjoint: lambda = B^-1 dL/dX with the stored factor; pair contractions with dT_SR/dr
-// ---------------------------------------------------------------------------------------
-// Gradient of <M, T_SR(r)> (M symmetric, 6 entries xx yy zz xy xz yz) with respect to
-// the pair vector r = x_j - x_i.
-__device__ __forceinline__ void tsr_grad(const DevParams& p, const double rr[3], double r,
-                                         double s_ij, double sig_ij, bool k2, const double M[6],
-                                         double g[3]) {
-  double fsr, dfsr, fin = 1.0, dfin = 0.0, f, dfr, dfs;
-  cutoff_buf(r, p.r_scs, p.r_buf, fsr, dfsr);
-  if (k2) finner(r, p.r_inner, fin, dfin);
-  fermi(r, s_ij, p.d, f, dfr, dfs);
-  double F = fin * fsr * (1.0 - f);
-  double dF = dfin * fsr * (1.0 - f) + fin * dfsr * (1.0 - f) - fin * fsr * dfr;
-  double A0, B0, dA0, dB0;
-  tsr_radial(r, sig_ij, A0, B0, dA0, dB0);
-  double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2],
-                  M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
-                  M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
-  double trM = M[0] + M[1] + M[2];
-  double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
-  double phi = A0 * trM + B0 * rMr;
-  double radial = (dF * phi + F * (dA0 * trM + dB0 * rMr)) / r;
-  double tang = 2.0 * F * B0;
-  g[0] = radial * rr[0] + tang * Mr[0];
-  g[1] = radial * rr[1] + tang * Mr[1];
-  g[2] = radial * rr[2] + tang * Mr[2];
-}
-
-__global__ void __launch_bounds__(256) k_scs_adjoint(Work w, DevParams p, int c0, int max_n12, int max_n1) {
-  extern __shared__ double smem_d[];
-  const int c = c0 + blockIdx.x;
-  if (c >= w.n_atoms) return;
-  const Counts cn = w.counts[c];
-  const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
-  ScsSmem sm = scs_carve(smem_d, max_n12, max_n1, true);
-  const int tid = threadIdx.x;
-  const long long sbase = (long long)c * w.site_cap;
-  for (int s = tid; s < n12; s += blockDim.x) {
-    int a = w.site_atom[sbase + s];
-    sm.x[s] = w.site_x[3 * (sbase + s) + 0];
-    sm.x[max_n12 + s] = w.site_x[3 * (sbase + s) + 1];
-    sm.x[2 * max_n12 + s] = w.site_x[3 * (sbase + s) + 2];
-    sm.rv[s] = w.rvdw[a];
-    sm.gs[3 * s] = sm.gs[3 * s + 1] = sm.gs[3 * s + 2] = 0.0;
-  }
-  const long long offk1 = w.off_k1[c];
-  const int npair = n1 * (n1 - 1) / 2;
-  for (int q = 0; q < p.nq; ++q) {
-    __syncthreads();
-    for (int s = tid; s < n12; s += blockDim.x) {
-      int a = w.site_atom[sbase + s];
-      sm.ab[s] = w.abar[a * p.nq + q];
-      sm.sg[s] = w.sig[a * p.nq + q];
-    }
-    // seeds dL/dX_i = (dL/dalpha_K,i + [i = k] dL/dalpha_I,k) I / 3
-    for (int e = tid; e < N1 * 3; e += blockDim.x) {
-      int row = e / 3, col = e % 3, i = row / 3, al = row % 3;
-      double gval = 0.0;
-      if (al == col) {
-        gval = w.alphaK_bar[(offk1 + i) * p.nq + q];
-        if (i == 0) gval += w.alphaI_bar[(long long)c * p.nq + q];
-        gval *= (1.0 / 3.0);
-      }
-      sm.y[e] = gval;
-    }
-    const double* X = w.xsol + offk1 * p.nq * 9 + (long long)q * N1 * 3;
-    for (int e = tid; e < N1 * 3; e += blockDim.x) sm.z[e] = X[e];
-    const double* L = w.bmat + w.off_b[c] + (long long)q * N1 * N1;
-    for (int i = tid; i < N1; i += blockDim.x) sm.inv[i] = 1.0 / L[(long long)i * N1 + i];
-    __syncthreads();
-    block_solve3(L, N1, sm.inv, sm.y, sm.red);   // y <- lambda
-    __syncthreads();
-    // coupled pairs: M = -(lambda_i X_j^T + lambda_j X_i^T), symmetrised
-    for (int e = tid; e < npair; e += blockDim.x) {
-      int i = (int)((sqrtf(8.0f * e + 1.0f) + 1.0f) * 0.5f);
-      while (i * (i - 1) / 2 > e) --i;
-      while ((i + 1) * i / 2 <= e) ++i;
-      int j = e - i * (i - 1) / 2;
-      double rr[3] = {sm.x[j] - sm.x[i], sm.x[max_n12 + j] - sm.x[max_n12 + i],
-                      sm.x[2 * max_n12 + j] - sm.x[2 * max_n12 + i]};
-      double r = sqrt(rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2]);
-      if (r >= p.r_scs) continue;
-      const double* li = sm.y + 9 * i;
-      const double* lj = sm.y + 9 * j;
-      const double* xi = sm.z + 9 * i;
-      const double* xj = sm.z + 9 * j;
-      double Mf[3][3];
-#pragma unroll
-      for (int al = 0; al < 3; ++al)
-#pragma unroll
-        for (int be = 0; be < 3; ++be) {
-          double s = 0.0;
-#pragma unroll
-          for (int ga = 0; ga < 3; ++ga) s += li[3 * al + ga] * xj[3 * be + ga] + lj[3 * al + ga] * xi[3 * be + ga];
-          Mf[al][be] = -s;
-        }
-      double M[6] = {Mf[0][0], Mf[1][1], Mf[2][2], 0.5 * (Mf[0][1] + Mf[1][0]),
-                     0.5 * (Mf[0][2] + Mf[2][0]), 0.5 * (Mf[1][2] + Mf[2][1])};
-      double sig = sqrt(sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j]);
-      double g[3];
-      tsr_grad(p, rr, r, p.beta * (sm.rv[i] + sm.rv[j]), sig, false, M, g);
-      atomicAdd(&sm.gs[3 * j + 0], g[0]); atomicAdd(&sm.gs[3 * j + 1], g[1]); atomicAdd(&sm.gs[3 * j + 2], g[2]);
-      atomicAdd(&sm.gs[3 * i + 0], -g[0]); atomicAdd(&sm.gs[3 * i + 1], -g[1]); atomicAdd(&sm.gs[3 * i + 2], -g[2]);
-    }
-    // uncoupled shell: d_i = 1 - sum_j T_SR,ij alpha_bar_j, dL/dd_i = lambda_i
-    const int warp = tid / 32, lane = tid % 32;
-    for (int i = warp; i < n1; i += blockDim.x / 32) {
-      const double* li = sm.y + 9 * i;
-      double Ms[6] = {li[0], li[4], li[8], 0.5 * (li[1] + li[3]), 0.5 * (li[2] + li[6]), 0.5 * (li[5] + li[7])};
-      double gi[3] = {0.0, 0.0, 0.0};
-      double xi = sm.x[i], yi = sm.x[max_n12 + i], zi = sm.x[2 * max_n12 + i];
-      for (int j = n1 + lane; j < n12; j += 32) {
-        double rr[3] = {sm.x[j] - xi, sm.x[max_n12 + j] - yi, sm.x[2 * max_n12 + j] - zi};
-        double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
-        if (r2 >= p.r_scs * p.r_scs) continue;
-        double r = sqrt(r2);
-        double M[6];
-#pragma unroll
-        for (int t = 0; t < 6; ++t) M[t] = -sm.ab[j] * Ms[t];
-        double sig = sqrt(sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j]);
-        double g[3];
-        tsr_grad(p, rr, r, p.beta * (sm.rv[i] + sm.rv[j]), sig, true, M, g);
-        atomicAdd(&sm.gs[3 * j + 0], g[0]); atomicAdd(&sm.gs[3 * j + 1], g[1]); atomicAdd(&sm.gs[3 * j + 2], g[2]);
-        gi[0] -= g[0]; gi[1] -= g[1]; gi[2] -= g[2];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int t = 0; t < 3; ++t) gi[t] += __shfl_xor_sync(0xffffffffu, gi[t], o);
-      if (lane == 0) { atomicAdd(&sm.gs[3 * i], gi[0]); atomicAdd(&sm.gs[3 * i + 1], gi[1]); atomicAdd(&sm.gs[3 * i + 2], gi[2]); }
-    }
-  }
-  __syncthreads();
-  for (int s = tid; s < n12; s += blockDim.x) {
-    int a = w.site_atom[sbase + s];
-    atomic_add3(w.gacc + 3 * a, sm.gs[3 * s], sm.gs[3 * s + 1], sm.gs[3 * s + 2]);
-  }
-}
-
-void launch_scs_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1, int max_n12,
-                              int max_n1, cudaStream_t s) {
-  if (c1 <= c0) return;
-  size_t sm = scs_smem_bytes(max_n12, max_n1, true);
-  cudaFuncSetAttribute(k_scs_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_scs_adjoint<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_n12, max_n1);
-}
-
 
 // ---------------------------------------------------------------------------------------
 // Allocation-free variant of the SCS forward kernel.

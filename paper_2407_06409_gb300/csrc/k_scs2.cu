@@ -1,0 +1,804 @@
+// Stage 1, mixed precision: local SCS solves (Sec. III.B, Eq. local_pol) for every
+// central atom k and frequency omega_q, FP64 results.
+//
+//   B_K = diag(1/alpha_bar_i) + T_SR,K,ij (i, j in K1),  d_K,i = 1 - sum_{j in K2} T_SR,K,ij alpha_bar_j
+//   X = B_K^-1 d_K,  alpha_K,i = Tr(X_i)/3,  alpha_I,k = alpha_K,k
+//   T_SR,K,ij = F(r) [A0(r) I + B0(r) r r^T],  F = f_inner f_SR (1 - f(r, S_ij)),
+//   A0 = g/r^3, B0 = (h~ - 3 g)/r^5 (Eqs. T_SR, g-func, h-func, written out in lmbd_internal.cuh)
+//
+// Design for GB300, whose FP64 pipe runs at 1/70 of FP32:
+//  * the pairs (i in K1, j in K1 u K2) with r_ij < r_SCS are listed once per central atom
+//    with their frequency-independent geometry and damping F, dF/dr (k_scs_count/k_scs_fill);
+//  * per (atom, frequency) only erf and exp of r/sigma_ij are evaluated (FP64), and the radial
+//    terms A0, B0, A0', B0' are kept for the adjoint;
+//  * B_K is factorised in FP32 (Cholesky, packed lower triangle in shared memory) and the
+//    FP64 solution is recovered by iterative refinement: the residual d - B X is formed in
+//    FP64 from the sparse pair list, corrections come from the FP32 factor (classical mixed-
+//    precision refinement, Wilkinson/Moler; converges when cond(B) * eps_fp32 << 1);
+//  * the adjoint solve B lambda = dL/dX reuses the stored FP32 factor with the same refinement,
+//    and contracts dB/dr, dd/dr pair by pair from the stored radial terms.
+#include "lmbd_internal.cuh"
+
+// pair predicate shared by the counting and filling kernels (identical FP64 arithmetic)
+__device__ __forceinline__ bool scs_pair_in(const double* xs, int ld, int i, int j, double rc2, double& rx,
+                                            double& ry, double& rz, double& r2) {
+  rx = xs[j] - xs[i];
+  ry = xs[ld + j] - xs[ld + i];
+  rz = xs[2 * ld + j] - xs[2 * ld + i];
+  r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+  return r2 < rc2;
+}
+
+__device__ __forceinline__ long long packed_idx(int i, int k) { return (long long)i * (i + 1) / 2 + k; }
+
+// ---------------------------------------------------------------------------------------
+// pair lists: count (before the workspace is sized) and fill
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_scs_count(Work w, DevParams p, int max_n12) {
+  extern __shared__ double smem_d[];
+  double* xs = smem_d;                 // 3 x max_n12
+  __shared__ int cnt_k1k1, cnt_k2;
+  const int c = blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const Counts cn = w.counts[c];
+  const int n1 = cn.n1, n12 = cn.n12;
+  const long long sbase = (long long)c * w.site_cap;
+  const int tid = threadIdx.x;
+  for (int s = tid; s < n12; s += blockDim.x)
+    for (int d = 0; d < 3; ++d) xs[d * max_n12 + s] = w.site_x[3 * (sbase + s) + d];
+  if (tid == 0) { cnt_k1k1 = 0; cnt_k2 = 0; }
+  __syncthreads();
+  const double rc2 = p.r_scs * p.r_scs;
+  int a = 0, b = 0;
+  const int nkk = n1 * (n1 - 1) / 2;
+  for (int e = tid; e < nkk; e += blockDim.x) {
+    int i = (int)((sqrtf(8.0f * e + 1.0f) + 1.0f) * 0.5f);
+    while (i * (i - 1) / 2 > e) --i;
+    while ((i + 1) * i / 2 <= e) ++i;
+    int j = e - i * (i - 1) / 2;
+    double rx, ry, rz, r2;
+    a += scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+  }
+  const int n2 = n12 - n1;
+  for (int e = tid; e < n1 * n2; e += blockDim.x) {
+    int i = e / n2, j = n1 + e % n2;
+    double rx, ry, rz, r2;
+    b += scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+  }
+  atomicAdd(&cnt_k1k1, a);
+  atomicAdd(&cnt_k2, b);
+  __syncthreads();
+  if (tid == 0) {
+    w.pcount[2 * c] = cnt_k1k1 + cnt_k2;   // unique pairs
+    w.pcount[2 * c + 1] = 2 * cnt_k1k1;    // adjacency entries (both directions of K1-K1 pairs)
+  }
+}
+
+// One block per central atom.  Pairs are ordered by owner row i: first the K1 partners
+// j < i (ascending), then the K2 partners (ascending); adjacency rows list every K1
+// partner j != i (ascending) with the index of the shared pair.
+__global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int max_n12, int max_n1) {
+  extern __shared__ double smem_d[];
+  double* xs = smem_d;                             // 3 x max_n12
+  int* pid = (int*)(xs + 3 * max_n12);             // max_n1 x max_n1 (pair index, -1 = none)
+  int* rowk1 = pid + max_n1 * max_n1;              // max_n1
+  int* rowcnt = rowk1 + max_n1;                    // max_n1
+  int* rowstart = rowcnt + max_n1;                 // max_n1 + 1
+  int* adjcnt = rowstart + max_n1 + 1;             // max_n1
+  int* adjstart = adjcnt + max_n1;                 // max_n1 + 1
+  int* k2cnt = adjstart + max_n1 + 1;              // max_n12
+  const int c = blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const Counts cn = w.counts[c];
+  const int n1 = cn.n1, n12 = cn.n12;
+  const long long sbase = (long long)c * w.site_cap;
+  const long long offp = w.off_p[c], offa = w.off_a[c], rbase = w.off_k1[c] + c;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32, nw = blockDim.x / 32;
+  for (int s = tid; s < n12; s += blockDim.x)
+    for (int d = 0; d < 3; ++d) xs[d * max_n12 + s] = w.site_x[3 * (sbase + s) + d];
+  for (int e = tid; e < n1 * n1; e += blockDim.x) pid[(e / n1) * max_n1 + e % n1] = -1;
+  __syncthreads();
+  const double rc2 = p.r_scs * p.r_scs;
+  // phase 1: per-row counts
+  for (int i = warp; i < n1; i += nw) {
+    int k1 = 0, k2 = 0;
+    for (int j0 = 0; j0 < i; j0 += 32) {
+      int j = j0 + lane;
+      double rx, ry, rz, r2;
+      bool in = j < i && scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+      k1 += __popc(__ballot_sync(0xffffffffu, in));
+    }
+    for (int j0 = n1; j0 < n12; j0 += 32) {
+      int j = j0 + lane;
+      double rx, ry, rz, r2;
+      bool in = j < n12 && scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+      k2 += __popc(__ballot_sync(0xffffffffu, in));
+    }
+    if (lane == 0) { rowk1[i] = k1; rowcnt[i] = k1 + k2; }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int i = 0; i < n1; ++i) { rowstart[i] = run; run += rowcnt[i]; }
+    rowstart[n1] = run;
+  }
+  __syncthreads();
+  // phase 2: write pairs in order with their geometry and damping
+  for (int i = warp; i < n1; i += nw) {
+    int pos = rowstart[i];
+    for (int pass = 0; pass < 2; ++pass) {
+      int jb = pass == 0 ? 0 : n1, je = pass == 0 ? i : n12;
+      for (int j0 = jb; j0 < je; j0 += 32) {
+        int j = j0 + lane;
+        double rx = 0, ry = 0, rz = 0, r2 = 0;
+        bool in = j < je && scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+        unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          int slot = pos + __popc(m & ((1u << lane) - 1u));
+          long long q = offp + slot;
+          double r = sqrt(r2);
+          int ai = w.site_atom[sbase + i], aj = w.site_atom[sbase + j];
+          double fsr, dfsr, fin = 1.0, dfin = 0.0, f, dfr, dfs;
+          cutoff_buf(r, p.r_scs, p.r_buf, fsr, dfsr);
+          if (pass == 1) finner(r, p.r_inner, fin, dfin);
+          fermi(r, p.beta * (w.rvdw[ai] + w.rvdw[aj]), p.d, f, dfr, dfs);
+          double F = fin * fsr * (1.0 - f);
+          double dF = dfin * fsr * (1.0 - f) + fin * dfsr * (1.0 - f) - fin * fsr * dfr;
+          w.pr_ij[2 * q] = i;
+          w.pr_ij[2 * q + 1] = j;
+          double* g = w.pr_geo + 8 * q;
+          g[0] = rx; g[1] = ry; g[2] = rz; g[3] = r; g[4] = F; g[5] = dF; g[6] = 1.0 / r; g[7] = 0.0;
+          if (pass == 0) pid[i * max_n1 + j] = slot;
+        }
+        pos += __popc(m);
+      }
+    }
+    if (lane == 0) {
+      w.prow[rbase + i] = rowstart[i];
+      w.prow_k2[rbase + i] = rowstart[i] + rowk1[i];
+    }
+  }
+  if (tid == 0) w.prow[rbase + n1] = rowstart[n1];
+  __syncthreads();
+  // phase 3: adjacency rows (K1 partners of every coupled site, both directions)
+  for (int i = warp; i < n1; i += nw) {
+    int k = 0;
+    for (int j0 = 0; j0 < n1; j0 += 32) {
+      int j = j0 + lane;
+      bool in = j < n1 && j != i && (j < i ? pid[i * max_n1 + j] : pid[j * max_n1 + i]) >= 0;
+      k += __popc(__ballot_sync(0xffffffffu, in));
+    }
+    if (lane == 0) adjcnt[i] = k;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int i = 0; i < n1; ++i) { adjstart[i] = run; run += adjcnt[i]; }
+    adjstart[n1] = run;
+  }
+  __syncthreads();
+  for (int i = warp; i < n1; i += nw) {
+    int pos = adjstart[i];
+    for (int j0 = 0; j0 < n1; j0 += 32) {
+      int j = j0 + lane;
+      int pp = -1;
+      if (j < n1 && j != i) pp = j < i ? pid[i * max_n1 + j] : pid[j * max_n1 + i];
+      unsigned m = __ballot_sync(0xffffffffu, pp >= 0);
+      if (pp >= 0) {
+        long long q = offa + pos + __popc(m & ((1u << lane) - 1u));
+        w.adj[2 * q] = j;
+        w.adj[2 * q + 1] = pp;
+      }
+      pos += __popc(m);
+    }
+    if (lane == 0) w.arow[rbase + i] = adjstart[i];
+  }
+  if (tid == 0) w.arow[rbase + n1] = adjstart[n1];
+  // phase 4: for every K2 site the pairs in which it is the partner (rows ascending)
+  if (tid < 32) {
+    for (int j = n1 + lane; j < n12; j += 32) k2cnt[j] = 0;
+    __syncwarp();
+    for (int i = 0; i < n1; ++i) {
+      const int b = rowstart[i] + rowk1[i], e = rowstart[i + 1];
+      for (int t = b + lane; t < e; t += 32) ++k2cnt[w.pr_ij[2 * (offp + t) + 1]];
+      __syncwarp();
+    }
+    if (lane == 0) {
+      int run = 0;
+      for (int j = n1; j < n12; ++j) {
+        int cj = k2cnt[j];
+        w.k2ptr[sbase + j] = run;
+        k2cnt[j] = run;
+        run += cj;
+      }
+      w.k2ptr[sbase + n12] = run;
+    }
+    __syncwarp();
+    for (int i = 0; i < n1; ++i) {
+      const int b = rowstart[i] + rowk1[i], e = rowstart[i + 1];
+      for (int t = b + lane; t < e; t += 32) {
+        const int j = w.pr_ij[2 * (offp + t) + 1];
+        w.k2rev[offp + k2cnt[j]] = t;
+        ++k2cnt[j];
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP32 Cholesky and triangular solves on a packed lower triangle in shared memory
+// (whole thread block of 256 threads; 16-wide blocks; 3 right-hand sides)
+// ---------------------------------------------------------------------------------------
+#define CB 16
+
+// Right-looking blocked Cholesky: warp 0 factors each 16 x 16 diagonal block, every thread
+// then solves panel rows and updates the trailing lower triangle.  sinv[i] = 1/L_ii.
+__device__ void chol32_packed(float* A, int n, int* bad, float* sinv) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    const int kb = min(CB, n - k0);
+    if (tid < 32) {
+      for (int t = 0; t < kb; ++t) {
+        if (tid == 0) {
+          float a = A[packed_idx(k0 + t, k0 + t)];
+          if (!(a > 0.f)) { *bad = 1; a = 1.f; }
+          a = sqrtf(a);
+          A[packed_idx(k0 + t, k0 + t)] = a;
+          sinv[k0 + t] = 1.f / a;
+        }
+        __syncwarp();
+        const float it = sinv[k0 + t];
+        if (tid > t && tid < kb) A[packed_idx(k0 + tid, k0 + t)] *= it;
+        __syncwarp();
+        for (int e = tid; e < kb * kb; e += 32) {
+          int i = e / kb, j = e % kb;
+          if (j > t && j <= i) A[packed_idx(k0 + i, k0 + j)] -= A[packed_idx(k0 + i, k0 + t)] * A[packed_idx(k0 + j, k0 + t)];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    const int r0 = k0 + kb;
+    for (int i = r0 + tid; i < n; i += blockDim.x) {
+      float* row = A + packed_idx(i, k0);
+      float v[CB];
+#pragma unroll
+      for (int t = 0; t < CB; ++t) v[t] = t < kb ? row[t] : 0.f;
+#pragma unroll
+      for (int t = 0; t < CB; ++t) {
+        if (t < kb) {
+          const float* dt = A + packed_idx(k0 + t, k0);
+          float s = v[t];
+#pragma unroll
+          for (int u = 0; u < t; ++u) s -= v[u] * dt[u];
+          v[t] = s * sinv[k0 + t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < CB; ++t)
+        if (t < kb) row[t] = v[t];
+    }
+    __syncthreads();
+    for (int i = r0 + warp; i < n; i += nw) {
+      const float* li = A + packed_idx(i, k0);
+      float a[CB];
+#pragma unroll
+      for (int t = 0; t < CB; ++t) a[t] = t < kb ? li[t] : 0.f;
+      float* row = A + packed_idx(i, 0);
+      for (int j = r0 + lane; j <= i; j += 32) {
+        const float* lj = A + packed_idx(j, k0);
+        float s = 0.f;
+#pragma unroll
+        for (int t = 0; t < CB; ++t)
+          if (t < kb) s += a[t] * lj[t];
+        row[j] -= s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y (n x 3, FP32, shared) <- (L L^T)^-1 y; sinv[i] = 1/L_ii.  Off-diagonal blocks by
+// 16 rows x 16 partial sums, diagonal triangles by warp 0.
+__device__ void solve32_packed(const float* L, int n, const float* sinv, float* y) {
+  const int tid = threadIdx.x;
+  const int r = tid >> 4, s = tid & 15;
+  for (int b0 = 0; b0 < n; b0 += CB) {
+    const int bb = min(CB, n - b0);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (r < bb) {
+      const float* row = L + packed_idx(b0 + r, 0);
+      for (int k = s; k < b0; k += 16) {
+        const float l = row[k];
+        a0 += l * y[3 * k];
+        a1 += l * y[3 * k + 1];
+        a2 += l * y[3 * k + 2];
+      }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      a0 += __shfl_down_sync(0xffffffffu, a0, o, 16);
+      a1 += __shfl_down_sync(0xffffffffu, a1, o, 16);
+      a2 += __shfl_down_sync(0xffffffffu, a2, o, 16);
+    }
+    if (s == 0 && r < bb) {
+      y[3 * (b0 + r)] -= a0;
+      y[3 * (b0 + r) + 1] -= a1;
+      y[3 * (b0 + r) + 2] -= a2;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const int ii0 = tid / 3, c = tid % 3;
+      for (int t = 0; t < bb; ++t) {
+        if (tid < 3) y[3 * (b0 + t) + tid] *= sinv[b0 + t];
+        __syncwarp();
+        if (tid < 30)
+          for (int ii = t + 1 + ii0; ii < bb; ii += 10)
+            y[3 * (b0 + ii) + c] -= L[packed_idx(b0 + ii, b0 + t)] * y[3 * (b0 + t) + c];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  const int nblk = (n + CB - 1) / CB;
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int b0 = blk * CB, bb = min(CB, n - b0), b1 = b0 + bb;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (r < bb) {
+      for (int k = b1 + s; k < n; k += 16) {
+        const float l = L[packed_idx(k, b0 + r)];
+        a0 += l * y[3 * k];
+        a1 += l * y[3 * k + 1];
+        a2 += l * y[3 * k + 2];
+      }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      a0 += __shfl_down_sync(0xffffffffu, a0, o, 16);
+      a1 += __shfl_down_sync(0xffffffffu, a1, o, 16);
+      a2 += __shfl_down_sync(0xffffffffu, a2, o, 16);
+    }
+    if (s == 0 && r < bb) {
+      y[3 * (b0 + r)] -= a0;
+      y[3 * (b0 + r) + 1] -= a1;
+      y[3 * (b0 + r) + 2] -= a2;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const int ii0 = tid / 3, c = tid % 3;
+      for (int t = bb - 1; t >= 0; --t) {
+        if (tid < 3) y[3 * (b0 + t) + tid] *= sinv[b0 + t];
+        __syncwarp();
+        if (tid < 30)
+          for (int ii = ii0; ii < t; ii += 10)
+            y[3 * (b0 + ii) + c] -= L[packed_idx(b0 + t, b0 + ii)] * y[3 * (b0 + t) + c];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// shared memory of the per-(atom, frequency) kernels
+// ---------------------------------------------------------------------------------------
+struct Scs2Smem {
+  float* A;       // packed lower factor, N1 (N1 + 1) / 2
+  float* sinv;    // N1
+  float* y;       // N1 x 3 (FP32 right-hand side / correction)
+  double* rhs;    // N1 x 3 (FP64 right-hand side d or dL/dX)
+  double* x;      // N1 x 3 (FP64 solution X or lambda)
+  double* xs;     // N1 x 3 (adjoint: X of the forward solve)
+  double* ab;     // n12 (alpha_bar at this frequency)
+  double* sg;     // n12 (sigma at this frequency)
+  double* red;    // 64
+};
+
+__host__ __device__ inline size_t scs2_smem_bytes(int max_n1, int max_n12, bool adjoint) {
+  size_t N1 = 3 * (size_t)max_n1;
+  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1;
+  fl = (fl + 1) & ~size_t(1);
+  size_t dd = 2 * 3 * N1 + 2 * (size_t)max_n12 + 64;
+  if (adjoint) dd += 3 * N1;
+  return fl * sizeof(float) + dd * sizeof(double);
+}
+
+__device__ inline Scs2Smem scs2_carve(unsigned char* base, int max_n1, int max_n12, bool adjoint) {
+  Scs2Smem s;
+  size_t N1 = 3 * (size_t)max_n1;
+  s.A = (float*)base;
+  s.sinv = s.A + N1 * (N1 + 1) / 2;
+  s.y = s.sinv + N1;
+  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1;
+  fl = (fl + 1) & ~size_t(1);
+  double* d = (double*)(base + fl * sizeof(float));
+  s.rhs = d;
+  s.x = s.rhs + 3 * N1;
+  s.ab = s.x + 3 * N1;
+  s.sg = s.ab + max_n12;
+  s.red = s.sg + max_n12;
+  s.xs = adjoint ? s.red + 64 : nullptr;
+  return s;
+}
+
+// y = (float)(rhs - B x) with B = diag(1/alpha_bar) + sum over the K1 pairs of T_SR; the
+// residual is formed in FP64 (one warp per row, fixed reduction order), then rounded.
+__device__ void scs2_residual(const Work& w, const DevParams& p, int n1, long long offp, long long offa,
+                              long long rbase, int q, Scs2Smem& sm) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < n1; i += nw) {
+    double acc[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t] = 0.0;
+    const int b = w.arow[rbase + i], e = w.arow[rbase + i + 1];
+    for (int t = b + lane; t < e; t += 32) {
+      const int j = w.adj[2 * (offa + t)], pp = w.adj[2 * (offa + t) + 1];
+      const double* g = w.pr_geo + 8 * (offp + pp);
+      const double* rad = w.pr_rad + 4 * ((offp + pp) * p.nq + q);
+      const double F = g[4], a = F * rad[0], bb = F * rad[1];
+      const double rr[3] = {g[0], g[1], g[2]};
+      const double* xj = sm.x + 9 * j;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double u = rr[0] * xj[c] + rr[1] * xj[3 + c] + rr[2] * xj[6 + c];
+#pragma unroll
+        for (int al = 0; al < 3; ++al) acc[3 * al + c] += a * xj[3 * al + c] + bb * rr[al] * u;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int t = 0; t < 9; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    if (lane == 0) {
+      const double ia = 1.0 / sm.ab[i];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) sm.y[9 * i + t] = (float)(sm.rhs[9 * i + t] - ia * sm.x[9 * i + t] - acc[t]);
+    }
+  }
+}
+
+// x = B^-1 rhs: FP32 solve, then FP64 refinement until the predicted error is below
+// 2^-52 |x|.  Returns the number of residuals formed; *fail set if it does not converge.
+__device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long offp, long long offa,
+                           long long rbase, int q, Scs2Smem& sm, int* fail) {
+  const int N1 = 3 * n1, tid = threadIdx.x;
+  for (int e = tid; e < 3 * N1; e += blockDim.x) sm.y[e] = (float)sm.rhs[e];
+  __syncthreads();
+  solve32_packed(sm.A, N1, sm.sinv, sm.y);
+  for (int e = tid; e < 3 * N1; e += blockDim.x) sm.x[e] = (double)sm.y[e];
+  __syncthreads();
+  double prev = 0.0;
+  int it = 0;
+  for (; it < 12; ++it) {
+    scs2_residual(w, p, n1, offp, offa, rbase, q, sm);
+    __syncthreads();
+    solve32_packed(sm.A, N1, sm.sinv, sm.y);
+    double dmax = 0.0, xmax = 0.0;
+    for (int e = tid; e < 3 * N1; e += blockDim.x) {
+      double dlt = (double)sm.y[e];
+      double xn = sm.x[e] + dlt;
+      sm.x[e] = xn;
+      dmax = fmax(dmax, fabs(dlt));
+      xmax = fmax(xmax, fabs(xn));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if ((tid & 31) == 0) { sm.red[tid >> 5] = dmax; sm.red[32 + (tid >> 5)] = xmax; }
+    __syncthreads();
+    dmax = 0.0;
+    xmax = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      dmax = fmax(dmax, sm.red[k]);
+      xmax = fmax(xmax, sm.red[32 + k]);
+    }
+    __syncthreads();
+    // contraction estimate rho = |delta_k| / |delta_{k-1}|; stop when rho |delta_k| is negligible
+    const double tol = 2.220446049250313e-16 * xmax;
+    if (dmax <= tol) { ++it; break; }
+    if (it >= 1) {
+      double rho = prev > 0.0 ? dmax / prev : 1.0;
+      if (rho < 0.5 && rho * dmax <= tol) { ++it; break; }
+    }
+    prev = dmax;
+    if (it == 11 && tid == 0) *fail = 1;
+  }
+  return it;
+}
+
+// Radial terms of T_SR (see lmbd_internal.cuh): A0 = g/r^3, B0 = (h~ - 3g)/r^5 and their
+// r-derivatives, with x = r / sigma_ij.  For x >= 8, erf(x) = 1 and x^3 exp(-x^2) < 1e-25 in
+// double precision, so g = 1 and h~ = 0 exactly; the transcendental calls are skipped there.
+__device__ __forceinline__ void tsr_radial_fast(double r, double ir, double s2, double& A0, double& B0,
+                                                double& dA0, double& dB0) {
+  const double x = r * rsqrt(s2);
+  double g = 1.0, ht = 0.0;
+  if (x < 8.0) {
+    const double two_over_sqrtpi = 1.1283791670955126;
+    const double ex = exp(-x * x);
+    g = erf(x) - two_over_sqrtpi * x * ex;
+    ht = 2.0 * two_over_sqrtpi * x * x * x * ex;
+  }
+  const double ir2 = ir * ir, ir3 = ir2 * ir, ir4 = ir2 * ir2;
+  A0 = g * ir3;
+  B0 = (ht - 3.0 * g) * ir4 * ir;
+  dA0 = (ht - 3.0 * g) * ir4;
+  dB0 = (15.0 * g - 5.0 * ht - 2.0 * x * x * ht) * ir4 * ir2;
+}
+
+// ---------------------------------------------------------------------------------------
+// forward: one block per (central atom, frequency)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, int c0, int max_n1, int max_n12) {
+  extern __shared__ unsigned char smem_raw[];
+  const int c = c0 + blockIdx.x / p.nq;
+  const int q = blockIdx.x % p.nq;
+  if (c >= w.n_atoms) return;
+  const Counts cn = w.counts[c];
+  const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
+  Scs2Smem sm = scs2_carve(smem_raw, max_n1, max_n12, false);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const long long sbase = (long long)c * w.site_cap;
+  const long long offp = w.off_p[c], offa = w.off_a[c], rbase = w.off_k1[c] + c;
+  const int np = w.prow[rbase + n1];
+  __shared__ int bad, fail;
+  if (tid == 0) { bad = 0; fail = 0; }
+  for (int s = tid; s < n12; s += blockDim.x) {
+    int a = w.site_atom[sbase + s];
+    sm.ab[s] = w.abar[(long long)a * p.nq + q];
+    sm.sg[s] = w.sig[(long long)a * p.nq + q];
+  }
+  const long long nA = (long long)N1 * (N1 + 1) / 2;
+  for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = 0.f;
+  __syncthreads();
+  // radial terms of every pair at this frequency (FP64), and the K1 blocks of B in FP32
+  for (int t = tid; t < np; t += blockDim.x) {
+    const long long pq = offp + t;
+    const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
+    const double* g = w.pr_geo + 8 * pq;
+    double A0, B0, dA0, dB0;
+    tsr_radial_fast(g[3], g[6], sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j], A0, B0, dA0, dB0);
+    double* rad = w.pr_rad + 4 * (pq * p.nq + q);
+    rad[0] = A0; rad[1] = B0; rad[2] = dA0; rad[3] = dB0;
+    if (j < n1) {
+      const double a = g[4] * A0, b = g[4] * B0;
+      const double rr[3] = {g[0], g[1], g[2]};
+#pragma unroll
+      for (int al = 0; al < 3; ++al) {
+        float* row = sm.A + packed_idx(3 * i + al, 3 * j);
+#pragma unroll
+        for (int be = 0; be < 3; ++be) row[be] = (float)(b * rr[al] * rr[be] + (al == be ? a : 0.0));
+      }
+    }
+  }
+  for (int i = tid; i < n1; i += blockDim.x)
+#pragma unroll
+    for (int al = 0; al < 3; ++al) sm.A[packed_idx(3 * i + al, 3 * i + al)] = (float)(1.0 / sm.ab[i]);
+  __threadfence_block();
+  __syncthreads();
+  // right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j (FP64, fixed order)
+  for (int i = warp; i < n1; i += nw) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int b = w.prow_k2[rbase + i], e = w.prow[rbase + i + 1];
+    for (int t = b + lane; t < e; t += 32) {
+      const long long pq = offp + t;
+      const int j = w.pr_ij[2 * pq + 1];
+      const double* g = w.pr_geo + 8 * pq;
+      const double* rad = w.pr_rad + 4 * (pq * p.nq + q);
+      const double a = g[4] * rad[0] * sm.ab[j], bb = g[4] * rad[1] * sm.ab[j];
+      acc[0] += a + bb * g[0] * g[0];
+      acc[1] += a + bb * g[1] * g[1];
+      acc[2] += a + bb * g[2] * g[2];
+      acc[3] += bb * g[0] * g[1];
+      acc[4] += bb * g[0] * g[2];
+      acc[5] += bb * g[1] * g[2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int t = 0; t < 6; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    if (lane == 0) {
+      double* y = sm.rhs + 9 * i;
+      y[0] = 1.0 - acc[0]; y[1] = -acc[3];      y[2] = -acc[4];
+      y[3] = -acc[3];      y[4] = 1.0 - acc[1]; y[5] = -acc[5];
+      y[6] = -acc[4];      y[7] = -acc[5];      y[8] = 1.0 - acc[2];
+    }
+  }
+  __syncthreads();
+  chol32_packed(sm.A, N1, &bad, sm.sinv);
+  scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail);
+  // outputs: X, alpha_K, alpha_I and the FP32 factor for the adjoint
+  const long long offk1 = w.off_k1[c];
+  double* X = w.xsol + offk1 * p.nq * 9 + (long long)q * N1 * 3;
+  for (int e = tid; e < N1 * 3; e += blockDim.x) X[e] = sm.x[e];
+  for (int i = tid; i < n1; i += blockDim.x) {
+    double a = (sm.x[9 * i + 0] + sm.x[9 * i + 4] + sm.x[9 * i + 8]) / 3.0;
+    w.alphaK[(offk1 + i) * p.nq + q] = a;
+    if (i == 0) w.alphaI[(long long)c * p.nq + q] = a;
+  }
+  float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
+  for (long long e = tid; e < nA; e += blockDim.x) Lg[e] = sm.A[e];
+  if (tid == 0 && (bad || fail)) atomicOr(w.status, bad ? LMBD_FLAG_NOT_SPD : LMBD_FLAG_NOT_CONVERGED);
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint: one block per (central atom, frequency)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_scs_adjoint2(Work w, DevParams p, int c0, int max_n1, int max_n12) {
+  extern __shared__ unsigned char smem_raw[];
+  const int c = c0 + blockIdx.x / p.nq;
+  const int q = blockIdx.x % p.nq;
+  if (c >= w.n_atoms) return;
+  const Counts cn = w.counts[c];
+  const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
+  Scs2Smem sm = scs2_carve(smem_raw, max_n1, max_n12, true);
+  const int tid = threadIdx.x;
+  const long long sbase = (long long)c * w.site_cap;
+  const long long offp = w.off_p[c], offa = w.off_a[c], rbase = w.off_k1[c] + c, offk1 = w.off_k1[c];
+  const int np = w.prow[rbase + n1];
+  __shared__ int fail;
+  if (tid == 0) fail = 0;
+  for (int s = tid; s < n12; s += blockDim.x) {
+    int a = w.site_atom[sbase + s];
+    sm.ab[s] = w.abar[(long long)a * p.nq + q];
+  }
+  const long long nA = (long long)N1 * (N1 + 1) / 2;
+  const float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
+  for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = Lg[e];
+  for (int i = tid; i < N1; i += blockDim.x) sm.sinv[i] = 1.f / Lg[packed_idx(i, i)];
+  const double* X = w.xsol + offk1 * p.nq * 9 + (long long)q * N1 * 3;
+  for (int e = tid; e < N1 * 3; e += blockDim.x) {
+    sm.xs[e] = X[e];
+    int row = e / 3, col = e % 3, i = row / 3, al = row % 3;
+    double gval = 0.0;
+    if (al == col) {
+      gval = w.alphaK_bar[(offk1 + i) * p.nq + q];
+      if (i == 0) gval += w.alphaI_bar[(long long)c * p.nq + q];
+      gval *= (1.0 / 3.0);
+    }
+    sm.rhs[e] = gval;
+  }
+  __syncthreads();
+  scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail);    // sm.x <- lambda
+  __syncthreads();
+  // pair contractions: <M, dT_SR/dr> with M = -(lambda_i X_j^T + lambda_j X_i^T) (K1 pairs)
+  // or M = -alpha_bar_j lambda_i (K2 pairs), symmetrised; g = dL/dr_j = -dL/dr_i per pair,
+  // staged in the shared memory of the factor (not needed after the solve)
+  double* gst = reinterpret_cast<double*>(sm.A);
+  for (int t = tid; t < np; t += blockDim.x) {
+    const long long pq = offp + t;
+    const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
+    const double* g = w.pr_geo + 8 * pq;
+    const double* rad = w.pr_rad + 4 * (pq * p.nq + q);
+    const double* li = sm.x + 9 * i;
+    double M[6];
+    if (j < n1) {
+      const double* lj = sm.x + 9 * j;
+      const double* xi = sm.xs + 9 * i;
+      const double* xj = sm.xs + 9 * j;
+      double Mf[3][3];
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+          double s = 0.0;
+#pragma unroll
+          for (int ga = 0; ga < 3; ++ga) s += li[3 * al + ga] * xj[3 * be + ga] + lj[3 * al + ga] * xi[3 * be + ga];
+          Mf[al][be] = -s;
+        }
+      M[0] = Mf[0][0]; M[1] = Mf[1][1]; M[2] = Mf[2][2];
+      M[3] = 0.5 * (Mf[0][1] + Mf[1][0]); M[4] = 0.5 * (Mf[0][2] + Mf[2][0]); M[5] = 0.5 * (Mf[1][2] + Mf[2][1]);
+    } else {
+      const double aj = -sm.ab[j];
+      M[0] = aj * li[0]; M[1] = aj * li[4]; M[2] = aj * li[8];
+      M[3] = aj * 0.5 * (li[1] + li[3]); M[4] = aj * 0.5 * (li[2] + li[6]); M[5] = aj * 0.5 * (li[5] + li[7]);
+    }
+    const double rr[3] = {g[0], g[1], g[2]};
+    const double F = g[4], dF = g[5], ir = g[6];
+    const double A0 = rad[0], B0 = rad[1], dA0 = rad[2], dB0 = rad[3];
+    const double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2], M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
+                          M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
+    const double trM = M[0] + M[1] + M[2];
+    const double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
+    const double phi = A0 * trM + B0 * rMr;
+    const double radial = (dF * phi + F * (dA0 * trM + dB0 * rMr)) * ir;
+    const double tang = 2.0 * F * B0;
+    gst[3 * t] = radial * rr[0] + tang * Mr[0];
+    gst[3 * t + 1] = radial * rr[1] + tang * Mr[1];
+    gst[3 * t + 2] = radial * rr[2] + tang * Mr[2];
+  }
+  __syncthreads();
+  // per site (fixed order): owner of its row's pairs (-g), partner of K1 pairs owned by later
+  // rows (+g, from the adjacency row) and of K2 pairs (+g, from the reverse list)
+  double* sgq = w.sgq + (sbase * p.nq + q) * 3;
+  for (int s = tid; s < n12; s += blockDim.x) {
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    if (s < n1) {
+      for (int t = w.prow[rbase + s]; t < w.prow[rbase + s + 1]; ++t) {
+        gx -= gst[3 * t]; gy -= gst[3 * t + 1]; gz -= gst[3 * t + 2];
+      }
+      for (int t = w.arow[rbase + s]; t < w.arow[rbase + s + 1]; ++t) {
+        const int j = w.adj[2 * (offa + t)], pp = w.adj[2 * (offa + t) + 1];
+        if (j > s) { gx += gst[3 * pp]; gy += gst[3 * pp + 1]; gz += gst[3 * pp + 2]; }
+      }
+    } else {
+      for (int t = w.k2ptr[sbase + s]; t < w.k2ptr[sbase + s + 1]; ++t) {
+        const int pp = w.k2rev[offp + t];
+        gx += gst[3 * pp]; gy += gst[3 * pp + 1]; gz += gst[3 * pp + 2];
+      }
+    }
+    sgq[(long long)s * p.nq * 3] = gx;
+    sgq[(long long)s * p.nq * 3 + 1] = gy;
+    sgq[(long long)s * p.nq * 3 + 2] = gz;
+  }
+  if (tid == 0 && fail) atomicOr(w.status, LMBD_FLAG_NOT_CONVERGED);
+}
+
+// Sum of the per-frequency site gradients of the SCS adjoint, scattered to atoms.
+__global__ void __launch_bounds__(256) k_scs_site_reduce(Work w, DevParams p, int c0) {
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const int n12 = w.counts[c].n12;
+  const long long sbase = (long long)c * w.site_cap;
+  for (int s = threadIdx.x; s < n12; s += blockDim.x) {
+    const double* g = w.sgq + (sbase + s) * p.nq * 3;
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int q = 0; q < p.nq; ++q) {
+      gx += g[3 * q];
+      gy += g[3 * q + 1];
+      gz += g[3 * q + 2];
+    }
+    if (gx != 0.0 || gy != 0.0 || gz != 0.0) atomic_add3(w.gacc + 3 * w.site_atom[sbase + s], gx, gy, gz);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+// The adjoint stages 3 doubles per pair in the factor region; max_n1 is raised until that
+// region holds max_pairs of them.
+int scs2_adjoint_n1(int max_n1, int max_pairs) {
+  int n1 = max_n1;
+  while ((size_t)(3 * n1) * (3 * n1 + 1) / 2 * sizeof(float) < (size_t)max_pairs * 3 * sizeof(double)) ++n1;
+  return n1;
+}
+
+void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s) {
+  if (w.n_atoms == 0) return;
+  size_t sm = sizeof(double) * 3 * (size_t)max_n12;
+  cudaFuncSetAttribute(k_scs_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_scs_count<<<w.n_atoms, 256, sm, s>>>(w, p, max_n12);
+}
+
+void launch_scs_fill(const Work& w, const DevParams& p, int max_n12, int max_n1, cudaStream_t s) {
+  if (w.n_atoms == 0) return;
+  size_t sm = sizeof(double) * 3 * (size_t)max_n12 +
+              sizeof(int) * ((size_t)max_n1 * max_n1 + 6 * (size_t)max_n1 + 2 + (size_t)max_n12);
+  cudaFuncSetAttribute(k_scs_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_scs_fill<<<w.n_atoms, 256, sm, s>>>(w, p, max_n12, max_n1);
+}
+
+size_t scs2_forward_smem(int max_n1, int max_n12) { return scs2_smem_bytes(max_n1, max_n12, false); }
+size_t scs2_adjoint_smem(int max_n1, int max_n12, int max_pairs) {
+  return scs2_smem_bytes(scs2_adjoint_n1(max_n1, max_pairs), max_n12, true);
+}
+
+void launch_scs_factor(const Work& w, const DevParams& p, int c0, int c1, int max_n1, int max_n12, cudaStream_t s) {
+  if (c1 <= c0) return;
+  size_t sm = scs2_smem_bytes(max_n1, max_n12, false);
+  cudaFuncSetAttribute(k_scs_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_scs_factor<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, c0, max_n1, max_n12);
+}
+
+void launch_scs_adjoint2(const Work& w, const DevParams& p, int c0, int c1, int max_n1, int max_n12, int max_pairs,
+                         cudaStream_t s) {
+  if (c1 <= c0) return;
+  const int n1s = scs2_adjoint_n1(max_n1, max_pairs);
+  size_t sm = scs2_smem_bytes(n1s, max_n12, true);
+  cudaFuncSetAttribute(k_scs_adjoint2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_scs_adjoint2<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, c0, n1s, max_n12);
+  k_scs_site_reduce<<<c1 - c0, 256, 0, s>>>(w, p, c0);
+}

@@ -32,6 +32,7 @@ struct Ctx {
   std::vector<double> omega, weight;   // quadrature (n_freq)
   int launch_mode = LMBD_LAUNCH_BATCHED;
   int profiling = 0;
+  int precision = LMBD_PREC_SLICED;
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
   int site_cap = 0;
   int last_n = 0;
@@ -40,7 +41,10 @@ struct Ctx {
   DevBuf table_d, pos_d, species_d, nu_d, weights_d, out_e_d, out_f_d;
   DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
   DevBuf site_atom, site_x, counts, off_k1, off_s, off_b, off_t, totals, status;
-  DevBuf bmat, xsol, alphaK, alphaI, alphaT, dsq, tlr, vkr, energies, trbuf;
+  DevBuf xsol, alphaK, alphaI, alphaT, dsq, tlr, vkr, energies, trbuf;
+  DevBuf pcount, off_p, off_a, pr_ij, pr_geo, pr_rad, prow, prow_k2, arow, adj, lfac;
+  DevBuf k2ptr, k2rev, sgq;
+  DevBuf off_tq, off_tr, off_kp, off_sp, tdig, texp, wdig, wexp, pdig, qdig, pexp, qexp;
   DevBuf gbar, pmat, qmat, x0buf, rbar, alphaK_bar, alphaI_bar, gacc;
   long long* totals_h = nullptr;   // pinned
   int* status_h = nullptr;         // pinned
@@ -250,7 +254,14 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   TRY(ensure(c->off_s, sizeof(long long) * (N + 1)));
   TRY(ensure(c->off_b, sizeof(long long) * (N + 1)));
   TRY(ensure(c->off_t, sizeof(long long) * (N + 1)));
-  TRY(ensure(c->totals, sizeof(long long) * 8));
+  TRY(ensure(c->totals, sizeof(long long) * 16));
+  TRY(ensure(c->off_tq, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->off_tr, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->off_kp, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->off_sp, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->pcount, sizeof(int) * 2 * N));
+  TRY(ensure(c->off_p, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->off_a, sizeof(long long) * (N + 1)));
   TRY(ensure(c->status, sizeof(int) * 4));
   TRY(ensure(c->alphaI, sizeof(double) * N * nq));
   TRY(ensure(c->energies, sizeof(double) * N));
@@ -295,6 +306,13 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   w.off_t = (long long*)c->off_t.p;
   w.totals = (long long*)c->totals.p;
   w.status = (int*)c->status.p;
+  w.pcount = (int*)c->pcount.p;
+  w.off_p = (long long*)c->off_p.p;
+  w.off_a = (long long*)c->off_a.p;
+  w.off_tq = (long long*)c->off_tq.p;
+  w.off_tr = (long long*)c->off_tr.p;
+  w.off_kp = (long long*)c->off_kp.p;
+  w.off_sp = (long long*)c->off_sp.p;
   w.alphaI = (double*)c->alphaI.p;
   w.energies = (double*)c->energies.p;
   w.trbuf = (double*)c->trbuf.p;
@@ -333,10 +351,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     w.site_x = (double*)c->site_x.p;
     CK(cudaMemsetAsync(w.status, 0, sizeof(int) * 4, s));
     launch_neighbors(w, dp, g, s, &launches);
+    launch_scs_count(w, dp, w.site_cap, s);
     launch_offsets(w, dp, s);
-    ++launches;
+    launches += 2;
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->totals_h, w.totals, sizeof(long long) * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->totals_h, w.totals, sizeof(long long) * 16, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->status_h, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (*c->status_h & LMBD_FLAG_COINCIDENT) return LMBD_EINVAL;
@@ -348,21 +367,44 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   const long long sum_n1 = c->totals_h[0], sum_ns = c->totals_h[1], sum_b = c->totals_h[2],
                   sum_t = c->totals_h[3];
   const int max_n1 = (int)c->totals_h[4], max_ns = (int)c->totals_h[5], max_n12 = (int)c->totals_h[6];
+  const long long sum_pairs = c->totals_h[8], sum_adj = c->totals_h[9];
+  const long long sum_tq = c->totals_h[12], sum_tr = c->totals_h[13], sum_kp = c->totals_h[14],
+                  sum_sp = c->totals_h[15];
   // kernel shared-memory capacities (per-centre systems live in shared memory)
-  if (max_n1 > 200 || max_ns > 1024 || max_n12 > 2048) return LMBD_ECAPACITY;
+  if (max_n1 > 96 || max_ns > 1024 || max_n12 > 4096) return LMBD_ECAPACITY;
+  const int max_pairs = (int)c->totals_h[10];
+  if (scs2_adjoint_smem(max_n1, max_n12, max_pairs) > 227 * 1024) return LMBD_ECAPACITY;
 
   // ---- workspaces -------------------------------------------------------------------------
   const int ncv = 3 * c->n_freq;
   const int nvec = forces ? (c->order - 1) : (c->order + 1) / 2;
   const int ncol = 3 * c->n_freq * (c->order - 2);
-  TRY(ensure(c->bmat, sizeof(double) * (size_t)sum_b));
+  TRY(ensure(c->lfac, sizeof(float) * (size_t)sum_b));
+  TRY(ensure(c->pr_ij, sizeof(int) * 2 * (size_t)(sum_pairs + 1)));
+  TRY(ensure(c->pr_geo, sizeof(double) * 8 * (size_t)(sum_pairs + 1)));
+  TRY(ensure(c->k2ptr, sizeof(int) * ((size_t)N * c->site_cap + 1)));
+  TRY(ensure(c->k2rev, sizeof(int) * (size_t)(sum_pairs + 1)));
+  TRY(ensure(c->pr_rad, sizeof(double) * 4 * (size_t)nq * (sum_pairs + 1)));
+  TRY(ensure(c->prow, sizeof(int) * (size_t)(sum_n1 + N)));
+  TRY(ensure(c->prow_k2, sizeof(int) * (size_t)(sum_n1 + N)));
+  TRY(ensure(c->arow, sizeof(int) * (size_t)(sum_n1 + N)));
+  TRY(ensure(c->adj, sizeof(int) * 2 * (size_t)(sum_adj + 1)));
   TRY(ensure(c->xsol, sizeof(double) * (size_t)sum_n1 * nq * 9));
   TRY(ensure(c->alphaK, sizeof(double) * (size_t)sum_n1 * nq));
   TRY(ensure(c->alphaT, sizeof(double) * (size_t)sum_ns * nq));
   TRY(ensure(c->dsq, sizeof(double) * (size_t)sum_ns * nq));
   TRY(ensure(c->tlr, sizeof(double) * (size_t)sum_t));
   TRY(ensure(c->vkr, sizeof(double) * (size_t)nvec * sum_ns * 3 * ncv));
-  w.bmat = (double*)c->bmat.p;
+  w.lfac = (float*)c->lfac.p;
+  w.pr_ij = (int*)c->pr_ij.p;
+  w.pr_geo = (double*)c->pr_geo.p;
+  w.pr_rad = (double*)c->pr_rad.p;
+  w.prow = (int*)c->prow.p;
+  w.prow_k2 = (int*)c->prow_k2.p;
+  w.arow = (int*)c->arow.p;
+  w.adj = (int*)c->adj.p;
+  w.k2ptr = (int*)c->k2ptr.p;
+  w.k2rev = (int*)c->k2rev.p;
   w.xsol = (double*)c->xsol.p;
   w.alphaK = (double*)c->alphaK.p;
   w.alphaT = (double*)c->alphaT.p;
@@ -370,6 +412,21 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   w.tlr = (double*)c->tlr.p;
   w.vkr = (double*)c->vkr.p;
   w.nvec = nvec;
+  // sliced tensor-core products: digits per product (see ozaki.cuh and the design notes)
+  const bool sliced = c->precision == LMBD_PREC_SLICED;
+  const bool sliced_chain = sliced && ncv <= 48;
+  const int ST = 6, DIG_E = 6, DIG_A = 5, DIG_P = 5;
+  const int Kp_pair = (ncol + 15) / 16 * 16;
+  if (sliced_chain) {
+    TRY(ensure(c->tdig, sizeof(unsigned short) * (size_t)ST * sum_tq));
+    TRY(ensure(c->texp, sizeof(int) * (size_t)sum_tr));
+    TRY(ensure(c->wdig, sizeof(unsigned short) * (size_t)48 * ST * sum_kp));
+    TRY(ensure(c->wexp, sizeof(int) * (size_t)48 * N));
+    w.tdig = (unsigned short*)c->tdig.p;
+    w.texp = (int*)c->texp.p;
+    w.wdig = (unsigned short*)c->wdig.p;
+    w.wexp = (int*)c->wexp.p;
+  }
   w.vstride = sum_ns * 3 * ncv;
   w.ncol = ncol;
   if (forces) {
@@ -389,20 +446,40 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     w.alphaK_bar = (double*)c->alphaK_bar.p;
     w.alphaI_bar = (double*)c->alphaI_bar.p;
     w.gacc = (double*)c->gacc.p;
+    TRY(ensure(c->sgq, sizeof(double) * 3 * (size_t)nq * N * c->site_cap));
+    w.sgq = (double*)c->sgq.p;
+    if (sliced && ncol > 0) {
+      TRY(ensure(c->pdig, sizeof(unsigned short) * (size_t)sum_sp * 3 * Kp_pair * DIG_P));
+      TRY(ensure(c->qdig, sizeof(unsigned short) * (size_t)sum_sp * 3 * Kp_pair * DIG_P));
+      TRY(ensure(c->pexp, sizeof(int) * (size_t)sum_sp * 3));
+      TRY(ensure(c->qexp, sizeof(int) * (size_t)sum_sp * 3));
+      w.pdig = (unsigned short*)c->pdig.p;
+      w.qdig = (unsigned short*)c->qdig.p;
+      w.pexp = (int*)c->pexp.p;
+      w.qexp = (int*)c->qexp.p;
+    }
   }
 
   // ---- stage 1 and 2 ------------------------------------------------------------------------
   const bool per_atom = c->launch_mode == LMBD_LAUNCH_PER_ATOM;
   const int step = per_atom ? 1 : N;
   mark(LMBD_PHASE_SCS);
+  launch_scs_fill(w, dp, max_n12, max_n1, s);
+  ++phase_launch[LMBD_PHASE_SCS];
   for (int c0 = 0; c0 < N; c0 += step) {
-    launch_scs_forward_sized(w, dp, c0, c0 + step, max_n12, max_n1, s);
+    launch_scs_factor(w, dp, c0, c0 + step, max_n1, max_n12, s);
     ++phase_launch[LMBD_PHASE_SCS];
   }
   if (per_atom) {
     for (int c0 = 0; c0 < N; ++c0) {
       launch_mbd_prepare_sized(w, dp, c0, c0 + 1, max_ns, s);
-      for (int m = 1; m < nvec; ++m) launch_mbd_chain_sized(w, dp, m, c0, c0 + 1, max_ns, s);
+      if (sliced_chain) launch_slice_t(w, c0, c0 + 1, ST, s);
+      for (int m = 1; m < nvec; ++m) {
+        if (sliced_chain)
+          launch_chain_oz(w, dp, m, c0, c0 + 1, max_ns, m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A, ST, s);
+        else
+          launch_mbd_chain_sized(w, dp, m, c0, c0 + 1, max_ns, s);
+      }
       launch_mbd_energy(w, dp, c0, c0 + 1, s);
     }
     phase_launch[LMBD_PHASE_PREPARE] = N;
@@ -411,8 +488,14 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   } else {
     mark(LMBD_PHASE_PREPARE);
     launch_mbd_prepare_sized(w, dp, 0, N, max_ns, s);
+    if (sliced_chain) launch_slice_t(w, 0, N, ST, s);
     mark(LMBD_PHASE_CHAIN);
-    for (int m = 1; m < nvec; ++m) launch_mbd_chain_sized(w, dp, m, 0, N, max_ns, s);
+    for (int m = 1; m < nvec; ++m) {
+      if (sliced_chain)
+        launch_chain_oz(w, dp, m, 0, N, max_ns, m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A, ST, s);
+      else
+        launch_mbd_chain_sized(w, dp, m, 0, N, max_ns, s);
+    }
     mark(LMBD_PHASE_ENERGY);
     launch_mbd_energy(w, dp, 0, N, s);
     phase_launch[LMBD_PHASE_PREPARE] = 1;
@@ -426,19 +509,30 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     CK(cudaMemsetAsync(w.rbar, 0, sizeof(double) * sum_ns, s));
     if (per_atom) {
       int dummy = 0;
-      for (int c0 = 0; c0 < N; ++c0) launch_mbd_adjoint_sized(w, dp, c0, c0 + 1, max_ns, s, &dummy);
-      for (int c0 = 0; c0 < N; ++c0) launch_scs_adjoint_sized(w, dp, c0, c0 + 1, max_n12, max_n1, s);
+      for (int c0 = 0; c0 < N; ++c0) {
+        launch_mbd_adj_series(w, dp, c0, c0 + 1, s);
+        if (sliced && ncol > 0)
+          launch_mbd_adj_pair_oz(w, dp, c0, c0 + 1, max_ns, DIG_P, s);
+        else
+          launch_mbd_adj_pair(w, dp, c0, c0 + 1, max_ns, s);
+        launch_mbd_adj_blend(w, dp, c0, c0 + 1, s);
+      }
+      (void)dummy;
+      for (int c0 = 0; c0 < N; ++c0) launch_scs_adjoint2(w, dp, c0, c0 + 1, max_n1, max_n12, max_pairs, s);
       phase_launch[LMBD_PHASE_ADJ_SERIES] = phase_launch[LMBD_PHASE_ADJ_PAIR] = N;
       phase_launch[LMBD_PHASE_ADJ_BLEND] = phase_launch[LMBD_PHASE_ADJ_SCS] = N;
     } else {
       mark(LMBD_PHASE_ADJ_SERIES);
       launch_mbd_adj_series(w, dp, 0, N, s);
       mark(LMBD_PHASE_ADJ_PAIR);
-      launch_mbd_adj_pair(w, dp, 0, N, max_ns, s);
+      if (sliced && ncol > 0)
+        launch_mbd_adj_pair_oz(w, dp, 0, N, max_ns, DIG_P, s);
+      else
+        launch_mbd_adj_pair(w, dp, 0, N, max_ns, s);
       mark(LMBD_PHASE_ADJ_BLEND);
       launch_mbd_adj_blend(w, dp, 0, N, s);
       mark(LMBD_PHASE_ADJ_SCS);
-      launch_scs_adjoint_sized(w, dp, 0, N, max_n12, max_n1, s);
+      launch_scs_adjoint2(w, dp, 0, N, max_n1, max_n12, max_pairs, s);
       phase_launch[LMBD_PHASE_ADJ_SERIES] = phase_launch[LMBD_PHASE_ADJ_PAIR] = 1;
       phase_launch[LMBD_PHASE_ADJ_BLEND] = phase_launch[LMBD_PHASE_ADJ_SCS] = 1;
     }
@@ -500,13 +594,13 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     S.max_sites = c->site_cap;
     S.kernel_launches = launches;
     double bytes = 0.0;
-    const DevBuf* all[] = {&c->bmat, &c->xsol, &c->alphaK, &c->alphaT, &c->dsq, &c->tlr, &c->vkr, &c->gbar,
+    const DevBuf* all[] = {&c->lfac, &c->pr_geo, &c->pr_rad, &c->tdig, &c->wdig, &c->pdig, &c->qdig, &c->xsol, &c->alphaK, &c->alphaT, &c->dsq, &c->tlr, &c->vkr, &c->gbar,
                            &c->pmat, &c->qmat, &c->x0buf, &c->rbar, &c->alphaK_bar, &c->alphaI_bar,
                            &c->site_atom, &c->site_x};
     for (const DevBuf* b : all) bytes += b->bytes;
     S.bytes_workspace = bytes;
   }
-  if (*c->status_h & LMBD_FLAG_NOT_SPD) return LMBD_NOT_SPD;
+  if (*c->status_h & (LMBD_FLAG_NOT_SPD | LMBD_FLAG_NOT_CONVERGED)) return LMBD_NOT_SPD;
   return LMBD_OK;
 }
 
@@ -564,7 +658,7 @@ int lmbd_create(const lmbd_species* species, int n_species, const lmbd_params* p
   if (st == LMBD_OK &&
       cudaMemcpy(c.table_d.p, c.table.data(), sizeof(double) * c.table.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     st = LMBD_ECUDA;
-  if (st == LMBD_OK && cudaMallocHost((void**)&c.totals_h, sizeof(long long) * 8) != cudaSuccess) st = LMBD_ENOMEM;
+  if (st == LMBD_OK && cudaMallocHost((void**)&c.totals_h, sizeof(long long) * 16) != cudaSuccess) st = LMBD_ENOMEM;
   if (st == LMBD_OK && cudaMallocHost((void**)&c.status_h, sizeof(int) * 4) != cudaSuccess) st = LMBD_ENOMEM;
   if (st != LMBD_OK) {
     cudaGetLastError();
@@ -603,6 +697,12 @@ int lmbd_set_profiling(lmbd_ctx* ctx, int on) {
         return LMBD_ECUDA;
       }
   c.profiling = on ? 1 : 0;
+  return LMBD_OK;
+}
+
+int lmbd_set_precision(lmbd_ctx* ctx, int mode) {
+  if (!ctx || (mode != LMBD_PREC_FP64 && mode != LMBD_PREC_SLICED)) return LMBD_EINVAL;
+  ctx->c.precision = mode;
   return LMBD_OK;
 }
 
@@ -663,7 +763,10 @@ int lmbd_destroy(lmbd_ctx* ctx) {
   DevBuf* all[] = {&c.table_d, &c.pos_d, &c.species_d, &c.nu_d, &c.weights_d, &c.out_e_d, &c.out_f_d,
                    &c.abar, &c.sig, &c.rvdw, &c.a0, &c.r0, &c.wpos, &c.cell_of, &c.cell_count,
                    &c.cell_start, &c.cell_atoms, &c.grid, &c.site_atom, &c.site_x, &c.counts, &c.off_k1,
-                   &c.off_s, &c.off_b, &c.off_t, &c.totals, &c.status, &c.bmat, &c.xsol, &c.alphaK,
+                   &c.off_s, &c.off_b, &c.off_t, &c.totals, &c.status, &c.xsol, &c.alphaK, &c.pcount,
+                   &c.off_p, &c.off_a, &c.pr_ij, &c.pr_geo, &c.pr_rad, &c.prow, &c.prow_k2, &c.arow, &c.adj,
+                   &c.lfac, &c.off_tq, &c.off_tr, &c.off_kp, &c.off_sp, &c.tdig, &c.texp, &c.wdig, &c.wexp,
+                   &c.pdig, &c.qdig, &c.pexp, &c.qexp, &c.k2ptr, &c.k2rev, &c.sgq,
                    &c.alphaI, &c.alphaT, &c.dsq, &c.tlr, &c.vkr, &c.energies, &c.trbuf, &c.gbar, &c.pmat,
                    &c.qmat, &c.x0buf, &c.rbar, &c.alphaK_bar, &c.alphaI_bar, &c.gacc};
   for (DevBuf* b : all) release(*b);
@@ -848,7 +951,7 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   w.off_s = cv.take<long long>(N + 1);
   w.off_b = cv.take<long long>(N + 1);
   w.off_t = cv.take<long long>(N + 1);
-  w.totals = cv.take<long long>(8);
+  w.totals = cv.take<long long>(12);
   w.status = cv.take<int>(4);
   w.alphaI = cv.take<double>((size_t)N * nq);
   const long long slot_doubles = 9LL * LMBD_NOALLOC_MAX_K1 * LMBD_NOALLOC_MAX_K1;
@@ -882,7 +985,7 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   launch_neighbors(w, dp, g, s, &launches);
   launch_offsets(w, dp, s);
   CK(cudaGetLastError());
-  long long tot[8];
+  long long tot[12];
   int flags = 0;
   CK(cudaMemcpyAsync(tot, w.totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&flags, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -13,6 +13,7 @@
 #define LMBD_FLAG_NOT_SPD 1
 #define LMBD_FLAG_CAPACITY 2
 #define LMBD_FLAG_COINCIDENT 4
+#define LMBD_FLAG_NOT_CONVERGED 8
 
 struct DevParams {
   // lengths in bohr
@@ -75,9 +76,37 @@ struct Work {
   long long* off_s;            // sum ns
   long long* off_b;            // sum nq (3 n1)^2
   long long* off_t;            // sum (3 ns)^2
-  long long* totals;           // 8 entries written by the offsets kernel
+  long long* off_p;            // sum of SCS pairs per centre
+  long long* off_a;            // sum of SCS adjacency entries per centre
+  long long* totals;           // 12 entries written by the offsets kernel
+  // SCS pair lists (one list per central atom; rows = coupled sites of K1)
+  int* pcount;                 // N x 2: pairs, adjacency entries
+  int* pr_ij;                  // pairs x 2: owner row i (K1), partner j (K1 with j < i, or K2)
+  double* pr_geo;              // pairs x 8: r = x_j - x_i (3), |r|, F, dF/dr, 1/|r|, unused
+  double* pr_rad;              // pairs x nq x 4: A0, B0, A0', B0' per frequency
+  int* prow;                   // (sum n1 + N): first pair of each row, per centre n1 + 1 entries
+  int* prow_k2;                // (sum n1 + N): first K2 pair of each row
+  int* arow;                   // (sum n1 + N): first adjacency entry of each row
+  int* adj;                    // entries x 2: K1 partner j, pair index
+  int* k2ptr;                  // N x site_cap: first reverse-list entry of each K2 site
+  int* k2rev;                  // per centre (off_p): pair indices grouped by K2 partner
+  double* sgq;                 // N x site_cap x nq x 3: SCS-adjoint site gradients per frequency
+  float* lfac;                 // packed FP32 Cholesky factors, off_b
+  // sliced tensor-core products (ozaki.cuh)
+  long long* off_tq;           // sum Mpad Kpad (T digit plane sizes)
+  long long* off_tr;           // sum Mpad (T rows)
+  long long* off_kp;           // sum Kpad (W digit planes are 48 x Kpad)
+  long long* off_sp;           // sum ns16 (P, Q rows are 3 ns16)
+  unsigned short* tdig;        // T digit planes (bf16 bits)
+  int* texp;                   // T row scale exponents
+  unsigned short* wdig;        // W digit planes
+  int* wexp;                   // W column exponents, N x 48
+  unsigned short* pdig;        // P digit planes
+  unsigned short* qdig;        // Q digit planes
+  int* pexp;                   // P row exponents
+  int* qexp;                   // Q row exponents
   // stage 1 (SCS)
-  double* bmat;                // factors, off_b
+  double* bmat;                // FP64 matrices of the allocation-free variant
   double* xsol;                // X = B^-1 d, off_k1 * nq * 9
   double* alphaK;              // off_k1 * nq
   double* alphaI;              // N x nq
@@ -179,8 +208,13 @@ __device__ __forceinline__ void atomic_add3(double* p, double a, double b, doubl
 void launch_free_atom(const Work& w, const DevParams& p, cudaStream_t s);
 void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStream_t s, int* launches);
 void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s);
-void launch_scs_forward_sized(const Work& w, const DevParams& p, int c0, int c1, int max_n12,
-                              int max_n1, cudaStream_t s);
+void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s);
+void launch_scs_fill(const Work& w, const DevParams& p, int max_n12, int max_n1, cudaStream_t s);
+void launch_scs_factor(const Work& w, const DevParams& p, int c0, int c1, int max_n1, int max_n12, cudaStream_t s);
+void launch_scs_adjoint2(const Work& w, const DevParams& p, int c0, int c1, int max_n1, int max_n12, int max_pairs,
+                         cudaStream_t s);
+size_t scs2_forward_smem(int max_n1, int max_n12);
+size_t scs2_adjoint_smem(int max_n1, int max_n12, int max_pairs);
 void launch_mbd_prepare_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_chain_sized(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
@@ -189,9 +223,12 @@ void launch_mbd_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1,
 void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
 void launch_mbd_adj_pair(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_adj_blend(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
-void launch_scs_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1, int max_n12,
-                              int max_n1, cudaStream_t s);
 void launch_forces_out(const Work& w, double* forces, cudaStream_t s);
+void launch_slice_t(const Work& w, int c0, int c1, int st, cudaStream_t s);
+void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
+                     cudaStream_t s);
+void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
+                            cudaStream_t s);
 
 // Allocation-free entry point (lmbd_central_polarizabilities_noalloc): scratch lookup and
 // the persistent SCS kernel variant, both in k_scs.cu next to the static scratch array.

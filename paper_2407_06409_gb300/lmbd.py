@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblmbd.so")
 
 LMBD_OK, LMBD_EINVAL, LMBD_ENOMEM, LMBD_NOT_SPD, LMBD_ECUDA, LMBD_ECAPACITY, LMBD_EUNSUPPORTED = range(7)
 LAUNCH_BATCHED, LAUNCH_PER_ATOM = 0, 1
+PREC_FP64, PREC_SLICED = 0, 1
 
 
 class Species(ctypes.Structure):
@@ -74,13 +75,14 @@ def lib() -> ctypes.CDLL:
         L.lmbd_energy_forces_weighted.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]
         L.lmbd_set_launch_mode.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_profiling.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_precision.argtypes = [_P, ctypes.c_int]
         L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
         L.lmbd_get_site_counts.argtypes = [_P, _P, _P]
         L.lmbd_get_quadrature.argtypes = [_P, _D, _D]
         L.lmbd_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
-                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
+                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
@@ -153,6 +155,9 @@ class LMBD:
 
     def set_launch_mode(self, mode: int) -> None:
         _check(lib().lmbd_set_launch_mode(self._h, int(mode)), "lmbd_set_launch_mode")
+
+    def set_precision(self, mode: int) -> None:
+        _check(lib().lmbd_set_precision(self._h, int(mode)), "lmbd_set_precision")
 
     def set_profiling(self, on: bool) -> None:
         _check(lib().lmbd_set_profiling(self._h, 1 if on else 0), "lmbd_set_profiling")

@@ -266,3 +266,16 @@ def test_autograd_function(lm, box110):
     (g,) = torch.autograd.grad((e * w).sum(), pos)
     _, f = model.energy_forces(pos.detach(), cell, sp, nu, forces=True, weights=w)
     assert (g + f).abs().max().item() < 1e-13
+
+
+def test_fp64_product_mode_matches_oracle(lm, box110, box110_ref):
+    # the exact FP64 kernels for the two large products stay available and correct
+    s = box110
+    so, e_ref, f_ref = box110_ref
+    model = lm.LMBD(s.table, lm.default_params(), 12, 6)
+    model.set_precision(lm.PREC_FP64)
+    e, f = model.energy_forces(torch.tensor(s.positions, device="cuda"), torch.tensor(s.cell, device="cuda"),
+                               torch.tensor(s.species, dtype=torch.int32, device="cuda"),
+                               torch.tensor(s.hirshfeld, device="cuda"))
+    _check_e(e.cpu().numpy(), e_ref)
+    _check_f(f.cpu().numpy(), f_ref)
