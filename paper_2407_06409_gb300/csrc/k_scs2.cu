@@ -232,9 +232,10 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int max_n
 // ---------------------------------------------------------------------------------------
 #define CB 16
 
-// Right-looking blocked Cholesky: warp 0 factors each 16 x 16 diagonal block, every thread
-// then solves panel rows and updates the trailing lower triangle.  sinv[i] = 1/L_ii.
-__device__ void chol32_packed(float* A, int n, int* bad, float* sinv) {
+// Right-looking blocked Cholesky: warp 0 factors each 16 x 16 diagonal block (and stores the
+// inverse of that block in binv, 256 floats per block, for the triangular solves), every
+// thread then solves panel rows and updates the trailing lower triangle.  sinv[i] = 1/L_ii.
+__device__ void chol32_packed(float* A, int n, int* bad, float* sinv, float* binv) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   for (int k0 = 0; k0 < n; k0 += CB) {
     const int kb = min(CB, n - k0);
@@ -256,6 +257,20 @@ __device__ void chol32_packed(float* A, int n, int* bad, float* sinv) {
           if (j > t && j <= i) A[packed_idx(k0 + i, k0 + j)] -= A[packed_idx(k0 + i, k0 + t)] * A[packed_idx(k0 + j, k0 + t)];
         }
         __syncwarp();
+      }
+      // inverse of the diagonal block: lane c solves L_bb x = e_c (column c), rows in order
+      float* inv = binv + (k0 / CB) * CB * CB;
+      if (tid < CB) {
+        const int cc = tid;
+        for (int i = 0; i < CB; ++i) {
+          float v = 0.f;
+          if (i < kb && cc < kb && i >= cc) {
+            float s = (i == cc) ? 1.f : 0.f;
+            for (int u = cc; u < i; ++u) s -= A[packed_idx(k0 + i, k0 + u)] * inv[u * CB + cc];
+            v = s * sinv[k0 + i];
+          }
+          inv[i * CB + cc] = v;
+        }
       }
     }
     __syncthreads();
@@ -299,9 +314,33 @@ __device__ void chol32_packed(float* A, int n, int* bad, float* sinv) {
   }
 }
 
-// y (n x 3, FP32, shared) <- (L L^T)^-1 y; sinv[i] = 1/L_ii.  Off-diagonal blocks by
-// 16 rows x 16 partial sums, diagonal triangles by warp 0.
-__device__ void solve32_packed(const float* L, int n, const float* sinv, float* y) {
+// Inverses of the 16 x 16 diagonal blocks of a stored factor (one warp per block, one lane
+// per column), as chol32_packed produces them.
+__device__ void blockinv32(const float* A, int n, const float* sinv, float* binv) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nblk = (n + CB - 1) / CB;
+  for (int blk = warp; blk < nblk; blk += nw) {
+    const int k0 = blk * CB, kb = min(CB, n - k0);
+    float* inv = binv + blk * CB * CB;
+    if (lane < CB) {
+      const int cc = lane;
+      for (int i = 0; i < CB; ++i) {
+        float v = 0.f;
+        if (i < kb && cc < kb && i >= cc) {
+          float s = (i == cc) ? 1.f : 0.f;
+          for (int u = cc; u < i; ++u) s -= A[packed_idx(k0 + i, k0 + u)] * inv[u * CB + cc];
+          v = s * sinv[k0 + i];
+        }
+        inv[i * CB + cc] = v;
+      }
+    }
+  }
+}
+
+// y (n x 3, FP32, shared) <- (L L^T)^-1 y with binv the inverses of the 16 x 16 diagonal
+// blocks.  Off-diagonal blocks by 16 rows x 16 partial sums; each diagonal block is one
+// parallel product with its inverse.
+__device__ void solve32_packed(const float* L, int n, const float* binv, float* y) {
   const int tid = threadIdx.x;
   const int r = tid >> 4, s = tid & 15;
   for (int b0 = 0; b0 < n; b0 += CB) {
@@ -328,17 +367,14 @@ __device__ void solve32_packed(const float* L, int n, const float* sinv, float* 
       y[3 * (b0 + r) + 2] -= a2;
     }
     __syncthreads();
-    if (tid < 32) {
-      const int ii0 = tid / 3, c = tid % 3;
-      for (int t = 0; t < bb; ++t) {
-        if (tid < 3) y[3 * (b0 + t) + tid] *= sinv[b0 + t];
-        __syncwarp();
-        if (tid < 30)
-          for (int ii = t + 1 + ii0; ii < bb; ii += 10)
-            y[3 * (b0 + ii) + c] -= L[packed_idx(b0 + ii, b0 + t)] * y[3 * (b0 + t) + c];
-        __syncwarp();
-      }
+    float v = 0.f;
+    const float* inv = binv + (b0 / CB) * CB * CB;
+    if (tid < 3 * bb) {
+      const int i = tid / 3, c = tid % 3;
+      for (int u = 0; u <= i; ++u) v += inv[i * CB + u] * y[3 * (b0 + u) + c];
     }
+    __syncthreads();
+    if (tid < 3 * bb) y[3 * b0 + tid] = v;
     __syncthreads();
   }
   const int nblk = (n + CB - 1) / CB;
@@ -365,17 +401,14 @@ __device__ void solve32_packed(const float* L, int n, const float* sinv, float* 
       y[3 * (b0 + r) + 2] -= a2;
     }
     __syncthreads();
-    if (tid < 32) {
-      const int ii0 = tid / 3, c = tid % 3;
-      for (int t = bb - 1; t >= 0; --t) {
-        if (tid < 3) y[3 * (b0 + t) + tid] *= sinv[b0 + t];
-        __syncwarp();
-        if (tid < 30)
-          for (int ii = ii0; ii < t; ii += 10)
-            y[3 * (b0 + ii) + c] -= L[packed_idx(b0 + t, b0 + ii)] * y[3 * (b0 + t) + c];
-        __syncwarp();
-      }
+    float v = 0.f;
+    const float* inv = binv + blk * CB * CB;
+    if (tid < 3 * bb) {
+      const int i = tid / 3, c = tid % 3;
+      for (int u = i; u < bb; ++u) v += inv[u * CB + i] * y[3 * (b0 + u) + c];
     }
+    __syncthreads();
+    if (tid < 3 * bb) y[3 * b0 + tid] = v;
     __syncthreads();
   }
 }
@@ -386,20 +419,22 @@ __device__ void solve32_packed(const float* L, int n, const float* sinv, float* 
 struct Scs2Smem {
   float* A;       // packed lower factor, N1 (N1 + 1) / 2
   float* sinv;    // N1
+  float* binv;    // ceil(N1/16) x 256: inverses of the diagonal blocks
   float* y;       // N1 x 3 (FP32 right-hand side / correction)
   double* rhs;    // N1 x 3 (FP64 right-hand side d or dL/dX)
   double* x;      // N1 x 3 (FP64 solution X or lambda)
   double* xs;     // N1 x 3 (adjoint: X of the forward solve)
   double* ab;     // n12 (alpha_bar at this frequency)
+  double* iab;    // n12 (1 / alpha_bar)
   double* sg;     // n12 (sigma at this frequency)
   double* red;    // 64
 };
 
 __host__ __device__ inline size_t scs2_smem_bytes(int max_n1, int max_n12, bool adjoint) {
   size_t N1 = 3 * (size_t)max_n1;
-  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1;
+  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1 + (N1 + 15) / 16 * 256;
   fl = (fl + 1) & ~size_t(1);
-  size_t dd = 2 * 3 * N1 + 2 * (size_t)max_n12 + 64;
+  size_t dd = 2 * 3 * N1 + 3 * (size_t)max_n12 + 64;
   if (adjoint) dd += 3 * N1;
   return fl * sizeof(float) + dd * sizeof(double);
 }
@@ -410,51 +445,63 @@ __device__ inline Scs2Smem scs2_carve(unsigned char* base, int max_n1, int max_n
   s.A = (float*)base;
   s.sinv = s.A + N1 * (N1 + 1) / 2;
   s.y = s.sinv + N1;
-  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1;
+  s.binv = s.y + 3 * N1;
+  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1 + (N1 + 15) / 16 * 256;
   fl = (fl + 1) & ~size_t(1);
   double* d = (double*)(base + fl * sizeof(float));
   s.rhs = d;
   s.x = s.rhs + 3 * N1;
   s.ab = s.x + 3 * N1;
-  s.sg = s.ab + max_n12;
+  s.iab = s.ab + max_n12;
+  s.sg = s.iab + max_n12;
   s.red = s.sg + max_n12;
   s.xs = adjoint ? s.red + 64 : nullptr;
   return s;
 }
 
-// y = (float)(rhs - B x) with B = diag(1/alpha_bar) + sum over the K1 pairs of T_SR; the
-// residual is formed in FP64 (one warp per row, fixed reduction order), then rounded.
+// y = (float)(rhs - B x) with B = diag(1/alpha_bar) + sum over the K1 pairs of T_SR.  One
+// thread per (coupled site i, right-hand side c) sums its adjacency row in a fixed order in
+// FP64, T_p x_j = F A0 x_j + F B0 r (r . x_j), then rounds the residual to FP32.
 __device__ void scs2_residual(const Work& w, const DevParams& p, int n1, long long offp, long long offa,
                               long long rbase, int q, Scs2Smem& sm) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < n1; i += nw) {
-    double acc[9];
+  for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
+    const int i = e / 3, c = e % 3;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const int b = w.arow[rbase + i], en = w.arow[rbase + i + 1];
+    // four entries per step: all loads first (independent), then the arithmetic in order
+    for (int t = b; t < en; t += 4) {
+      int jj[4], pp[4];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc[t] = 0.0;
-    const int b = w.arow[rbase + i], e = w.arow[rbase + i + 1];
-    for (int t = b + lane; t < e; t += 32) {
-      const int j = w.adj[2 * (offa + t)], pp = w.adj[2 * (offa + t) + 1];
-      const double* g = w.pr_geo + 8 * (offp + pp);
-      const double* rad = w.pr_rad + 4 * ((offp + pp) * p.nq + q);
-      const double F = g[4], a = F * rad[0], bb = F * rad[1];
-      const double rr[3] = {g[0], g[1], g[2]};
-      const double* xj = sm.x + 9 * j;
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = t + u < en;
+        jj[u] = ok ? w.adj[2 * (offa + t + u)] : 0;
+        pp[u] = ok ? w.adj[2 * (offa + t + u) + 1] : -1;
+      }
+      double gx[4], gy[4], gz[4], fa[4], fb[4];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double u = rr[0] * xj[c] + rr[1] * xj[3 + c] + rr[2] * xj[6 + c];
+      for (int u = 0; u < 4; ++u) {
+        if (pp[u] >= 0) {
+          const double* g = w.pr_geo + 8 * (offp + pp[u]);
+          const double* rad = w.pr_rad + 6 * ((offp + pp[u]) * p.nq + q);
+          gx[u] = g[0]; gy[u] = g[1]; gz[u] = g[2]; fa[u] = rad[4]; fb[u] = rad[5];
+        } else {
+          gx[u] = gy[u] = gz[u] = fa[u] = fb[u] = 0.0;
+        }
+      }
 #pragma unroll
-        for (int al = 0; al < 3; ++al) acc[3 * al + c] += a * xj[3 * al + c] + bb * rr[al] * u;
+      for (int u = 0; u < 4; ++u) {
+        const double* xj = sm.x + 9 * jj[u];
+        const double x0 = xj[c], x1 = xj[3 + c], x2 = xj[6 + c];
+        const double bu = fb[u] * (gx[u] * x0 + gy[u] * x1 + gz[u] * x2);
+        a0 += fa[u] * x0 + bu * gx[u];
+        a1 += fa[u] * x1 + bu * gy[u];
+        a2 += fa[u] * x2 + bu * gz[u];
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int t = 0; t < 9; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-    if (lane == 0) {
-      const double ia = 1.0 / sm.ab[i];
-#pragma unroll
-      for (int t = 0; t < 9; ++t) sm.y[9 * i + t] = (float)(sm.rhs[9 * i + t] - ia * sm.x[9 * i + t] - acc[t]);
-    }
+    const double ia = sm.iab[i];
+    sm.y[9 * i + c] = (float)(sm.rhs[9 * i + c] - ia * sm.x[9 * i + c] - a0);
+    sm.y[9 * i + 3 + c] = (float)(sm.rhs[9 * i + 3 + c] - ia * sm.x[9 * i + 3 + c] - a1);
+    sm.y[9 * i + 6 + c] = (float)(sm.rhs[9 * i + 6 + c] - ia * sm.x[9 * i + 6 + c] - a2);
   }
 }
 
@@ -465,7 +512,7 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
   const int N1 = 3 * n1, tid = threadIdx.x;
   for (int e = tid; e < 3 * N1; e += blockDim.x) sm.y[e] = (float)sm.rhs[e];
   __syncthreads();
-  solve32_packed(sm.A, N1, sm.sinv, sm.y);
+  solve32_packed(sm.A, N1, sm.binv, sm.y);
   for (int e = tid; e < 3 * N1; e += blockDim.x) sm.x[e] = (double)sm.y[e];
   __syncthreads();
   double prev = 0.0;
@@ -473,7 +520,7 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
   for (; it < 12; ++it) {
     scs2_residual(w, p, n1, offp, offa, rbase, q, sm);
     __syncthreads();
-    solve32_packed(sm.A, N1, sm.sinv, sm.y);
+    solve32_packed(sm.A, N1, sm.binv, sm.y);
     double dmax = 0.0, xmax = 0.0;
     for (int e = tid; e < 3 * N1; e += blockDim.x) {
       double dlt = (double)sm.y[e];
@@ -532,9 +579,10 @@ __device__ __forceinline__ void tsr_radial_fast(double r, double ir, double s2, 
 // ---------------------------------------------------------------------------------------
 // forward: one block per (central atom, frequency)
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, int c0, int max_n1, int max_n12) {
+__global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, const int* order, int c0, int max_n1,
+                                                  int max_n12) {
   extern __shared__ unsigned char smem_raw[];
-  const int c = c0 + blockIdx.x / p.nq;
+  const int c = order ? order[c0 + blockIdx.x / p.nq] : c0 + blockIdx.x / p.nq;
   const int q = blockIdx.x % p.nq;
   if (c >= w.n_atoms) return;
   const Counts cn = w.counts[c];
@@ -548,7 +596,9 @@ __global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, int c0,
   if (tid == 0) { bad = 0; fail = 0; }
   for (int s = tid; s < n12; s += blockDim.x) {
     int a = w.site_atom[sbase + s];
-    sm.ab[s] = w.abar[(long long)a * p.nq + q];
+    const double ab = w.abar[(long long)a * p.nq + q];
+    sm.ab[s] = ab;
+    sm.iab[s] = 1.0 / ab;
     sm.sg[s] = w.sig[(long long)a * p.nq + q];
   }
   const long long nA = (long long)N1 * (N1 + 1) / 2;
@@ -561,8 +611,8 @@ __global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, int c0,
     const double* g = w.pr_geo + 8 * pq;
     double A0, B0, dA0, dB0;
     tsr_radial_fast(g[3], g[6], sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j], A0, B0, dA0, dB0);
-    double* rad = w.pr_rad + 4 * (pq * p.nq + q);
-    rad[0] = A0; rad[1] = B0; rad[2] = dA0; rad[3] = dB0;
+    double* rad = w.pr_rad + 6 * (pq * p.nq + q);
+    rad[0] = A0; rad[1] = B0; rad[2] = dA0; rad[3] = dB0; rad[4] = g[4] * A0; rad[5] = g[4] * B0;
     if (j < n1) {
       const double a = g[4] * A0, b = g[4] * B0;
       const double rr[3] = {g[0], g[1], g[2]};
@@ -579,36 +629,31 @@ __global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, int c0,
     for (int al = 0; al < 3; ++al) sm.A[packed_idx(3 * i + al, 3 * i + al)] = (float)(1.0 / sm.ab[i]);
   __threadfence_block();
   __syncthreads();
-  // right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j (FP64, fixed order)
-  for (int i = warp; i < n1; i += nw) {
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    const int b = w.prow_k2[rbase + i], e = w.prow[rbase + i + 1];
-    for (int t = b + lane; t < e; t += 32) {
+  // right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j (FP64, fixed order); one thread
+  // per (coupled site i, column c): column c of T_SR,ij is F A0 e_c + F B0 r r_c
+  for (int e = tid; e < 3 * n1; e += blockDim.x) {
+    const int i = e / 3, c = e % 3;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, ad = 0.0;
+    const int b = w.prow_k2[rbase + i], en = w.prow[rbase + i + 1];
+    for (int t = b; t < en; ++t) {
       const long long pq = offp + t;
       const int j = w.pr_ij[2 * pq + 1];
       const double* g = w.pr_geo + 8 * pq;
-      const double* rad = w.pr_rad + 4 * (pq * p.nq + q);
-      const double a = g[4] * rad[0] * sm.ab[j], bb = g[4] * rad[1] * sm.ab[j];
-      acc[0] += a + bb * g[0] * g[0];
-      acc[1] += a + bb * g[1] * g[1];
-      acc[2] += a + bb * g[2] * g[2];
-      acc[3] += bb * g[0] * g[1];
-      acc[4] += bb * g[0] * g[2];
-      acc[5] += bb * g[1] * g[2];
+      const double* rad = w.pr_rad + 6 * (pq * p.nq + q);
+      const double abj = sm.ab[j];
+      ad += abj * rad[4];
+      const double wb = abj * rad[5] * g[c];
+      a0 += wb * g[0];
+      a1 += wb * g[1];
+      a2 += wb * g[2];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int t = 0; t < 6; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-    if (lane == 0) {
-      double* y = sm.rhs + 9 * i;
-      y[0] = 1.0 - acc[0]; y[1] = -acc[3];      y[2] = -acc[4];
-      y[3] = -acc[3];      y[4] = 1.0 - acc[1]; y[5] = -acc[5];
-      y[6] = -acc[4];      y[7] = -acc[5];      y[8] = 1.0 - acc[2];
-    }
+    double* y = sm.rhs + 9 * i;
+    y[c] = (c == 0 ? 1.0 : 0.0) - a0 - (c == 0 ? ad : 0.0);
+    y[3 + c] = (c == 1 ? 1.0 : 0.0) - a1 - (c == 1 ? ad : 0.0);
+    y[6 + c] = (c == 2 ? 1.0 : 0.0) - a2 - (c == 2 ? ad : 0.0);
   }
   __syncthreads();
-  chol32_packed(sm.A, N1, &bad, sm.sinv);
+  chol32_packed(sm.A, N1, &bad, sm.sinv, sm.binv);
   scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail);
   // outputs: X, alpha_K, alpha_I and the FP32 factor for the adjoint
   const long long offk1 = w.off_k1[c];
@@ -627,9 +672,10 @@ __global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, int c0,
 // ---------------------------------------------------------------------------------------
 // adjoint: one block per (central atom, frequency)
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scs_adjoint2(Work w, DevParams p, int c0, int max_n1, int max_n12) {
+__global__ void __launch_bounds__(256) k_scs_adjoint2(Work w, DevParams p, const int* order, int c0, int max_n1,
+                                                  int max_n12) {
   extern __shared__ unsigned char smem_raw[];
-  const int c = c0 + blockIdx.x / p.nq;
+  const int c = order ? order[c0 + blockIdx.x / p.nq] : c0 + blockIdx.x / p.nq;
   const int q = blockIdx.x % p.nq;
   if (c >= w.n_atoms) return;
   const Counts cn = w.counts[c];
@@ -643,12 +689,16 @@ __global__ void __launch_bounds__(256) k_scs_adjoint2(Work w, DevParams p, int c
   if (tid == 0) fail = 0;
   for (int s = tid; s < n12; s += blockDim.x) {
     int a = w.site_atom[sbase + s];
-    sm.ab[s] = w.abar[(long long)a * p.nq + q];
+    const double ab = w.abar[(long long)a * p.nq + q];
+    sm.ab[s] = ab;
+    sm.iab[s] = 1.0 / ab;
   }
   const long long nA = (long long)N1 * (N1 + 1) / 2;
   const float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
   for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = Lg[e];
   for (int i = tid; i < N1; i += blockDim.x) sm.sinv[i] = 1.f / Lg[packed_idx(i, i)];
+  __syncthreads();
+  blockinv32(sm.A, N1, sm.sinv, sm.binv);
   const double* X = w.xsol + offk1 * p.nq * 9 + (long long)q * N1 * 3;
   for (int e = tid; e < N1 * 3; e += blockDim.x) {
     sm.xs[e] = X[e];
@@ -666,13 +716,13 @@ __global__ void __launch_bounds__(256) k_scs_adjoint2(Work w, DevParams p, int c
   __syncthreads();
   // pair contractions: <M, dT_SR/dr> with M = -(lambda_i X_j^T + lambda_j X_i^T) (K1 pairs)
   // or M = -alpha_bar_j lambda_i (K2 pairs), symmetrised; g = dL/dr_j = -dL/dr_i per pair,
-  // staged in the shared memory of the factor (not needed after the solve)
-  double* gst = reinterpret_cast<double*>(sm.A);
+  // staged in global scratch (L2-resident) for the per-site gather
+  double* gst = w.gstage + (offp * p.nq + (long long)q * np) * 3;
   for (int t = tid; t < np; t += blockDim.x) {
     const long long pq = offp + t;
     const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
     const double* g = w.pr_geo + 8 * pq;
-    const double* rad = w.pr_rad + 4 * (pq * p.nq + q);
+    const double* rad = w.pr_rad + 6 * (pq * p.nq + q);
     const double* li = sm.x + 9 * i;
     double M[6];
     if (j < n1) {
@@ -758,14 +808,6 @@ __global__ void __launch_bounds__(256) k_scs_site_reduce(Work w, DevParams p, in
 // ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
-// The adjoint stages 3 doubles per pair in the factor region; max_n1 is raised until that
-// region holds max_pairs of them.
-int scs2_adjoint_n1(int max_n1, int max_pairs) {
-  int n1 = max_n1;
-  while ((size_t)(3 * n1) * (3 * n1 + 1) / 2 * sizeof(float) < (size_t)max_pairs * 3 * sizeof(double)) ++n1;
-  return n1;
-}
-
 void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s) {
   if (w.n_atoms == 0) return;
   size_t sm = sizeof(double) * 3 * (size_t)max_n12;
@@ -782,23 +824,27 @@ void launch_scs_fill(const Work& w, const DevParams& p, int max_n12, int max_n1,
 }
 
 size_t scs2_forward_smem(int max_n1, int max_n12) { return scs2_smem_bytes(max_n1, max_n12, false); }
-size_t scs2_adjoint_smem(int max_n1, int max_n12, int max_pairs) {
-  return scs2_smem_bytes(scs2_adjoint_n1(max_n1, max_pairs), max_n12, true);
-}
+size_t scs2_adjoint_smem(int max_n1, int max_n12) { return scs2_smem_bytes(max_n1, max_n12, true); }
 
-void launch_scs_factor(const Work& w, const DevParams& p, int c0, int c1, int max_n1, int max_n12, cudaStream_t s) {
+// Centres order[c0..c1) (or c0..c1 when order is NULL), shared memory sized for the largest
+// K1 and K1 u K2 among them.
+void launch_scs_factor(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1, int max_n12,
+                       cudaStream_t s) {
   if (c1 <= c0) return;
   size_t sm = scs2_smem_bytes(max_n1, max_n12, false);
   cudaFuncSetAttribute(k_scs_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_scs_factor<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, c0, max_n1, max_n12);
+  k_scs_factor<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
 }
 
-void launch_scs_adjoint2(const Work& w, const DevParams& p, int c0, int c1, int max_n1, int max_n12, int max_pairs,
-                         cudaStream_t s) {
+void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1,
+                         int max_n12, cudaStream_t s) {
   if (c1 <= c0) return;
-  const int n1s = scs2_adjoint_n1(max_n1, max_pairs);
-  size_t sm = scs2_smem_bytes(n1s, max_n12, true);
+  size_t sm = scs2_smem_bytes(max_n1, max_n12, true);
   cudaFuncSetAttribute(k_scs_adjoint2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_scs_adjoint2<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, c0, n1s, max_n12);
+  k_scs_adjoint2<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
+}
+
+void launch_scs_site_reduce(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {
+  if (c1 <= c0) return;
   k_scs_site_reduce<<<c1 - c0, 256, 0, s>>>(w, p, c0);
 }

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -43,7 +44,9 @@ struct Ctx {
   DevBuf site_atom, site_x, counts, off_k1, off_s, off_b, off_t, totals, status;
   DevBuf xsol, alphaK, alphaI, alphaT, dsq, tlr, vkr, energies, trbuf;
   DevBuf pcount, off_p, off_a, pr_ij, pr_geo, pr_rad, prow, prow_k2, arow, adj, lfac;
-  DevBuf k2ptr, k2rev, sgq;
+  DevBuf k2ptr, k2rev, sgq, gstage, order_d;
+  std::vector<Counts> counts_h;
+  std::vector<int> order_h;
   DevBuf off_tq, off_tr, off_kp, off_sp, tdig, texp, wdig, wexp, pdig, qdig, pexp, qexp;
   DevBuf gbar, pmat, qmat, x0buf, rbar, alphaK_bar, alphaI_bar, gacc;
   long long* totals_h = nullptr;   // pinned
@@ -372,8 +375,34 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
                   sum_sp = c->totals_h[15];
   // kernel shared-memory capacities (per-centre systems live in shared memory)
   if (max_n1 > 96 || max_ns > 1024 || max_n12 > 4096) return LMBD_ECAPACITY;
-  const int max_pairs = (int)c->totals_h[10];
-  if (scs2_adjoint_smem(max_n1, max_n12, max_pairs) > 227 * 1024) return LMBD_ECAPACITY;
+  if (scs2_adjoint_smem(max_n1, max_n12) > 227 * 1024) return LMBD_ECAPACITY;
+  // size buckets for the SCS kernels: centres sorted by |K1|, one launch per bucket of width 6
+  // in |K1| with shared memory sized to the bucket (more blocks per SM for typical centres)
+  struct Bucket { int b0, b1, n1, n12; };
+  std::vector<Bucket> buckets;
+  {
+    c->counts_h.resize(N);
+    CK(cudaMemcpy(c->counts_h.data(), w.counts, sizeof(Counts) * N, cudaMemcpyDeviceToHost));
+    c->order_h.resize(N);
+    for (int i = 0; i < N; ++i) c->order_h[i] = i;
+    std::stable_sort(c->order_h.begin(), c->order_h.end(),
+                     [&](int x, int y) { return c->counts_h[x].n1 < c->counts_h[y].n1; });
+    int b0 = 0;
+    while (b0 < N) {
+      const int lo = c->counts_h[c->order_h[b0]].n1;
+      int b1 = b0, n1m = 0, n12m = 0;
+      while (b1 < N && c->counts_h[c->order_h[b1]].n1 < lo + 6) {
+        n1m = std::max(n1m, c->counts_h[c->order_h[b1]].n1);
+        n12m = std::max(n12m, c->counts_h[c->order_h[b1]].n12);
+        ++b1;
+      }
+      buckets.push_back({b0, b1, n1m, n12m});
+      b0 = b1;
+    }
+    TRY(ensure(c->order_d, sizeof(int) * N));
+    CK(cudaMemcpyAsync(c->order_d.p, c->order_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  }
+  const int* order_dev = (const int*)c->order_d.p;
 
   // ---- workspaces -------------------------------------------------------------------------
   const int ncv = 3 * c->n_freq;
@@ -384,7 +413,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   TRY(ensure(c->pr_geo, sizeof(double) * 8 * (size_t)(sum_pairs + 1)));
   TRY(ensure(c->k2ptr, sizeof(int) * ((size_t)N * c->site_cap + 1)));
   TRY(ensure(c->k2rev, sizeof(int) * (size_t)(sum_pairs + 1)));
-  TRY(ensure(c->pr_rad, sizeof(double) * 4 * (size_t)nq * (sum_pairs + 1)));
+  TRY(ensure(c->pr_rad, sizeof(double) * 6 * (size_t)nq * (sum_pairs + 1)));
   TRY(ensure(c->prow, sizeof(int) * (size_t)(sum_n1 + N)));
   TRY(ensure(c->prow_k2, sizeof(int) * (size_t)(sum_n1 + N)));
   TRY(ensure(c->arow, sizeof(int) * (size_t)(sum_n1 + N)));
@@ -447,7 +476,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     w.alphaI_bar = (double*)c->alphaI_bar.p;
     w.gacc = (double*)c->gacc.p;
     TRY(ensure(c->sgq, sizeof(double) * 3 * (size_t)nq * N * c->site_cap));
+    TRY(ensure(c->gstage, sizeof(double) * 3 * (size_t)nq * (sum_pairs + 1)));
     w.sgq = (double*)c->sgq.p;
+    w.gstage = (double*)c->gstage.p;
     if (sliced && ncol > 0) {
       TRY(ensure(c->pdig, sizeof(unsigned short) * (size_t)sum_sp * 3 * Kp_pair * DIG_P));
       TRY(ensure(c->qdig, sizeof(unsigned short) * (size_t)sum_sp * 3 * Kp_pair * DIG_P));
@@ -466,9 +497,16 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   mark(LMBD_PHASE_SCS);
   launch_scs_fill(w, dp, max_n12, max_n1, s);
   ++phase_launch[LMBD_PHASE_SCS];
-  for (int c0 = 0; c0 < N; c0 += step) {
-    launch_scs_factor(w, dp, c0, c0 + step, max_n1, max_n12, s);
-    ++phase_launch[LMBD_PHASE_SCS];
+  if (per_atom) {
+    for (int c0 = 0; c0 < N; ++c0) {
+      launch_scs_factor(w, dp, nullptr, c0, c0 + 1, c->counts_h[c0].n1, c->counts_h[c0].n12, s);
+      ++phase_launch[LMBD_PHASE_SCS];
+    }
+  } else {
+    for (const Bucket& b : buckets) {
+      launch_scs_factor(w, dp, order_dev, b.b0, b.b1, b.n1, b.n12, s);
+      ++phase_launch[LMBD_PHASE_SCS];
+    }
   }
   if (per_atom) {
     for (int c0 = 0; c0 < N; ++c0) {
@@ -518,9 +556,13 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         launch_mbd_adj_blend(w, dp, c0, c0 + 1, s);
       }
       (void)dummy;
-      for (int c0 = 0; c0 < N; ++c0) launch_scs_adjoint2(w, dp, c0, c0 + 1, max_n1, max_n12, max_pairs, s);
+      for (int c0 = 0; c0 < N; ++c0) {
+        launch_scs_adjoint2(w, dp, nullptr, c0, c0 + 1, c->counts_h[c0].n1, c->counts_h[c0].n12, s);
+        launch_scs_site_reduce(w, dp, c0, c0 + 1, s);
+      }
       phase_launch[LMBD_PHASE_ADJ_SERIES] = phase_launch[LMBD_PHASE_ADJ_PAIR] = N;
-      phase_launch[LMBD_PHASE_ADJ_BLEND] = phase_launch[LMBD_PHASE_ADJ_SCS] = N;
+      phase_launch[LMBD_PHASE_ADJ_BLEND] = N;
+      phase_launch[LMBD_PHASE_ADJ_SCS] = 2 * N;
     } else {
       mark(LMBD_PHASE_ADJ_SERIES);
       launch_mbd_adj_series(w, dp, 0, N, s);
@@ -532,9 +574,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       mark(LMBD_PHASE_ADJ_BLEND);
       launch_mbd_adj_blend(w, dp, 0, N, s);
       mark(LMBD_PHASE_ADJ_SCS);
-      launch_scs_adjoint2(w, dp, 0, N, max_n1, max_n12, max_pairs, s);
+      for (const Bucket& b : buckets) launch_scs_adjoint2(w, dp, order_dev, b.b0, b.b1, b.n1, b.n12, s);
+      launch_scs_site_reduce(w, dp, 0, N, s);
       phase_launch[LMBD_PHASE_ADJ_SERIES] = phase_launch[LMBD_PHASE_ADJ_PAIR] = 1;
-      phase_launch[LMBD_PHASE_ADJ_BLEND] = phase_launch[LMBD_PHASE_ADJ_SCS] = 1;
+      phase_launch[LMBD_PHASE_ADJ_BLEND] = 1;
+      phase_launch[LMBD_PHASE_ADJ_SCS] = (int)buckets.size() + 1;
     }
     CK(cudaGetLastError());
   }
@@ -563,8 +607,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
 
   // ---- statistics (algorithmic work from the actual sizes) ----------------------------------
   {
-    std::vector<Counts> hc(N);
-    CK(cudaMemcpy(hc.data(), w.counts, sizeof(Counts) * N, cudaMemcpyDeviceToHost));
+    const std::vector<Counts>& hc = c->counts_h;
     lmbd_stats& S = c->stats;
     for (int i = 0; i < N; ++i) {
       double n1 = 3.0 * hc[i].n1, n = 3.0 * hc[i].ns;
@@ -766,7 +809,7 @@ int lmbd_destroy(lmbd_ctx* ctx) {
                    &c.off_s, &c.off_b, &c.off_t, &c.totals, &c.status, &c.xsol, &c.alphaK, &c.pcount,
                    &c.off_p, &c.off_a, &c.pr_ij, &c.pr_geo, &c.pr_rad, &c.prow, &c.prow_k2, &c.arow, &c.adj,
                    &c.lfac, &c.off_tq, &c.off_tr, &c.off_kp, &c.off_sp, &c.tdig, &c.texp, &c.wdig, &c.wexp,
-                   &c.pdig, &c.qdig, &c.pexp, &c.qexp, &c.k2ptr, &c.k2rev, &c.sgq,
+                   &c.pdig, &c.qdig, &c.pexp, &c.qexp, &c.k2ptr, &c.k2rev, &c.sgq, &c.gstage, &c.order_d,
                    &c.alphaI, &c.alphaT, &c.dsq, &c.tlr, &c.vkr, &c.energies, &c.trbuf, &c.gbar, &c.pmat,
                    &c.qmat, &c.x0buf, &c.rbar, &c.alphaK_bar, &c.alphaI_bar, &c.gacc};
   for (DevBuf* b : all) release(*b);

@@ -83,7 +83,7 @@ struct Work {
   int* pcount;                 // N x 2: pairs, adjacency entries
   int* pr_ij;                  // pairs x 2: owner row i (K1), partner j (K1 with j < i, or K2)
   double* pr_geo;              // pairs x 8: r = x_j - x_i (3), |r|, F, dF/dr, 1/|r|, unused
-  double* pr_rad;              // pairs x nq x 4: A0, B0, A0', B0' per frequency
+  double* pr_rad;              // pairs x nq x 6: A0, B0, A0', B0', F A0, F B0 per frequency
   int* prow;                   // (sum n1 + N): first pair of each row, per centre n1 + 1 entries
   int* prow_k2;                // (sum n1 + N): first K2 pair of each row
   int* arow;                   // (sum n1 + N): first adjacency entry of each row
@@ -91,6 +91,7 @@ struct Work {
   int* k2ptr;                  // N x site_cap: first reverse-list entry of each K2 site
   int* k2rev;                  // per centre (off_p): pair indices grouped by K2 partner
   double* sgq;                 // N x site_cap x nq x 3: SCS-adjoint site gradients per frequency
+  double* gstage;              // sum pairs x nq x 3: SCS-adjoint pair gradients (scratch)
   float* lfac;                 // packed FP32 Cholesky factors, off_b
   // sliced tensor-core products (ozaki.cuh)
   long long* off_tq;           // sum Mpad Kpad (T digit plane sizes)
@@ -210,11 +211,13 @@ void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStre
 void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s);
 void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s);
 void launch_scs_fill(const Work& w, const DevParams& p, int max_n12, int max_n1, cudaStream_t s);
-void launch_scs_factor(const Work& w, const DevParams& p, int c0, int c1, int max_n1, int max_n12, cudaStream_t s);
-void launch_scs_adjoint2(const Work& w, const DevParams& p, int c0, int c1, int max_n1, int max_n12, int max_pairs,
-                         cudaStream_t s);
+void launch_scs_factor(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1, int max_n12,
+                       cudaStream_t s);
+void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1,
+                         int max_n12, cudaStream_t s);
+void launch_scs_site_reduce(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
 size_t scs2_forward_smem(int max_n1, int max_n12);
-size_t scs2_adjoint_smem(int max_n1, int max_n12, int max_pairs);
+size_t scs2_adjoint_smem(int max_n1, int max_n12);
 void launch_mbd_prepare_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_chain_sized(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
