@@ -68,20 +68,38 @@ __global__ void __launch_bounds__(256) k_mbd_prepare(Work w, DevParams p, int c0
     double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
     double rc = (j == 0) ? p.r_mbd1 : p.r_mbd2;
     double blk[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double kc[5] = {0, 0, 0, 0, 0};
     if (r2 < rc * rc) {
       double r = sqrt(r2);
       double flr, dflr, f, dfr, dfs;
       cutoff_buf(r, rc, p.r_buf, flr, dflr);
       fermi(r, p.beta * (rt[i] + rt[j]), p.d, f, dfr, dfs);
       double C = flr * f;
-      double ir2 = 1.0 / r2;
-      double ir3 = ir2 / r;
+      double ir = 1.0 / r;
+      double ir2 = ir * ir;
+      double ir3 = ir2 * ir;
       double ir5 = ir3 * ir2;
 #pragma unroll
       for (int al = 0; al < 3; ++al)
 #pragma unroll
         for (int be = 0; be < 3; ++be)
           blk[al][be] = C * (3.0 * rr[al] * rr[be] * ir5 - (al == be ? ir3 : 0.0));
+      if (w.pcoef) {
+        // d<M, T_LR>/dr = (k1 r.M.r + k2 Tr M) r + k3 M r, d<M, T_LR>/dS~ beta = k4 r.M.r + k5 Tr M
+        // (both pair blocks counted), with C = f_LR f, dC/dr, dC/dS~
+        const double dC = dflr * f + flr * dfr, CS = flr * dfs;
+        const double ir4 = ir2 * ir2, ir6 = ir4 * ir2, ir7 = ir6 * ir;
+        kc[0] = 2.0 * (3.0 * dC * ir6 - 15.0 * C * ir7);
+        kc[1] = 2.0 * (3.0 * C * ir5 - dC * ir4);
+        kc[2] = 12.0 * C * ir5;
+        kc[3] = 6.0 * p.beta * CS * ir5;
+        kc[4] = -2.0 * p.beta * CS * ir3;
+      }
+    }
+    if (w.pcoef) {
+      double* pc = w.pcoef + w.off_t[c] + 8LL * (i * (i - 1) / 2 + j);
+      pc[0] = rr[0]; pc[1] = rr[1]; pc[2] = rr[2];
+      pc[3] = kc[0]; pc[4] = kc[1]; pc[5] = kc[2]; pc[6] = kc[3]; pc[7] = kc[4];
     }
 #pragma unroll
     for (int al = 0; al < 3; ++al)
@@ -327,14 +345,17 @@ __device__ __forceinline__ void pair_tile_sites(const Work& w, const DevParams& 
 }
 
 // Contribution of the site pair (s, t), s > t, to dL/dr and dL/dR~ from its pair-matrix
-// block acc = M_st (3 x 3, before the central-column term): T_LR,st = f_LR f(r, S~) T(r).
-// Returns g = dL/dr_t (= -dL/dr_s) in out[0..2] and the SCS-radius seed beta dL/dS~ in out[3]
+// block acc = M_st (3 x 3, before the central-column term): T_LR,st = f_LR f(r, S~) T(r), with
+// the geometry and derivative coefficients of the pair stored by k_mbd_prepare.  Returns
+// g = dL/dr_t (= -dL/dr_s) in out[0..2] and the SCS-radius seed beta dL/dS~ in out[3]
 // (zeros when the pair does not couple).
-__device__ __forceinline__ void pair_epilogue(const Work& w, const DevParams& p, long long offs, int s, int t,
-                                              int ns, const double* xsv, const double* xtv, double rts_s,
-                                              double rts_t, double (&acc)[3][3], double* out) {
+__device__ __forceinline__ void pair_epilogue(const Work& w, long long offs, long long offt, int s, int t, int ns,
+                                              double (&acc)[3][3], double* out) {
   out[0] = out[1] = out[2] = out[3] = 0.0;
   if (!(s < ns && t < ns && s > t)) return;
+  const double* pc = w.pcoef + offt + 8LL * (s * (s - 1) / 2 + t);
+  const double k3 = pc[5];
+  if (k3 == 0.0 && pc[6] == 0.0) return;
   if (t == 0) {
     const double* x0 = w.x0buf + (offs + s) * 9;
 #pragma unroll
@@ -342,31 +363,18 @@ __device__ __forceinline__ void pair_epilogue(const Work& w, const DevParams& p,
 #pragma unroll
       for (int be = 0; be < 3; ++be) acc[al][be] += x0[al * 3 + be];
   }
-  double rr[3] = {xtv[0] - xsv[0], xtv[1] - xsv[1], xtv[2] - xsv[2]};
-  double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
-  double rc = (t == 0) ? p.r_mbd1 : p.r_mbd2;
-  if (!(r2 < rc * rc)) return;
-  double r = sqrt(r2);
-  double flr, dflr, f, dfr, dfs;
-  double St = p.beta * (rts_s + rts_t);
-  cutoff_buf(r, rc, p.r_buf, flr, dflr);
-  fermi(r, St, p.d, f, dfr, dfs);
-  double C = flr * f, dC = dflr * f + flr * dfr, CS = flr * dfs;
-  double M[6] = {acc[0][0], acc[1][1], acc[2][2], 0.5 * (acc[0][1] + acc[1][0]),
-                 0.5 * (acc[0][2] + acc[2][0]), 0.5 * (acc[1][2] + acc[2][1])};
-  double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2], M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
-                  M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
-  double trM = M[0] + M[1] + M[2];
-  double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
-  double ir = 1.0 / r, ir2 = ir * ir;
-  double ir3 = ir2 * ir, ir5 = ir3 * ir2, ir7 = ir5 * ir2;
-  double psi = 3.0 * rMr * ir5 - trM * ir3;
-  double radial = 2.0 * (dC * psi * ir + C * (-15.0 * rMr * ir7 + 3.0 * trM * ir5));
-  double tang = 2.0 * C * 6.0 * ir5;
-  out[0] = radial * rr[0] + tang * Mr[0];
-  out[1] = radial * rr[1] + tang * Mr[1];
-  out[2] = radial * rr[2] + tang * Mr[2];
-  out[3] = 2.0 * CS * psi * p.beta;
+  const double rr[3] = {pc[0], pc[1], pc[2]};
+  const double M[6] = {acc[0][0], acc[1][1], acc[2][2], 0.5 * (acc[0][1] + acc[1][0]),
+                       0.5 * (acc[0][2] + acc[2][0]), 0.5 * (acc[1][2] + acc[2][1])};
+  const double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2], M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
+                        M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
+  const double trM = M[0] + M[1] + M[2];
+  const double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
+  const double radial = pc[3] * rMr + pc[4] * trM;
+  out[0] = radial * rr[0] + k3 * Mr[0];
+  out[1] = radial * rr[1] + k3 * Mr[1];
+  out[2] = radial * rr[2] + k3 * Mr[2];
+  out[3] = pc[6] * rMr + pc[7] * trM;
 }
 
 // Deterministic reduction of the 16 x 16 pair results of a tile to its row sites (-g, seed)
@@ -437,7 +445,7 @@ __global__ void __launch_bounds__(256) k_mbd_adj_pair(Work w, DevParams p, int c
     }
   }
   __syncthreads();   // site data of the tile visible to all threads (also when ncol = 0)
-  pair_epilogue(w, p, offs, s, t, ns, xs[0][ty], xs[1][tx], rts[0][ty], rts[1][tx], acc, gp[ty][tx]);
+  pair_epilogue(w, offs, w.off_t[c], s, t, ns, acc, gp[ty][tx]);
   __syncthreads();
   pair_tile_reduce(w, offs, sbase, ns, bi, bj, gp);
 }
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(288) k_mbd_adj_pair_oz(Work w, DevParams p, in
     for (int al = 0; al < 3; ++al)
 #pragma unroll
       for (int be = 0; be < 3; ++be) acc[al][be] = Ms[3 * ty + al][3 * tx + be];
-    pair_epilogue(w, p, offs, s, t, ns, xs[0][ty], xs[1][tx], rts[0][ty], rts[1][tx], acc, gp[ty][tx]);
+    pair_epilogue(w, offs, w.off_t[c], s, t, ns, acc, gp[ty][tx]);
   }
   __syncthreads();
   pair_tile_reduce(w, offs, sbase, ns, bi, bj, gp);
@@ -755,4 +763,229 @@ void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, i
     k_mbd_adj_pair_oz<6><<<(c1 - c0) * tiles, 288, 0, s>>>(w, p, c0, tiles);
   else
     k_mbd_adj_pair_oz<5><<<(c1 - c0) * tiles, 288, 0, s>>>(w, p, c0, tiles);
+}
+
+// v_{m+1} = D (T W) with shared-memory staging (cp.async, two stages of 32 K), 64 x 48 outputs
+// per block, 12 warps of 16 x 16, integer recombination of the digit groups.
+#define OZ_KS 32
+#define OZ_LD 40
+template <int S>
+__global__ void __launch_bounds__(384, 1) k_chain_oz2(Work w, DevParams p, int m, int c0, int tiles_per_c, int st) {
+  extern __shared__ __align__(16) unsigned short oz_sm[];
+  const int c = c0 + blockIdx.x / tiles_per_c;
+  const int tile = blockIdx.x % tiles_per_c;
+  if (c >= w.n_atoms) return;
+  const int N = 3 * w.counts[c].ns, Mpad = oz_mpad(N), Kpad = oz_kpad(N);
+  if (tile * 64 >= N) return;
+  const long long offs = w.off_s[c];
+  const int ncv = 3 * p.n_freq;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const int wr = warp / 3, wc = warp % 3;
+  const int stA = S * 64 * OZ_LD, stB = S * 48 * OZ_LD;
+  unsigned short* sbuf[2] = {oz_sm, oz_sm + stA + stB};
+  const unsigned short* gA = w.tdig + w.off_tq[c] * st + (long long)(tile * 64) * Kpad;
+  const unsigned short* gB = w.wdig + w.off_kp[c] * 48 * S;
+  const long long pA = (long long)Mpad * Kpad, pB = 48LL * Kpad;
+  const int nstage = (Kpad + OZ_KS - 1) / OZ_KS;
+  auto load = [&](int stage, int buf) {
+    const int k0 = stage * OZ_KS;
+    unsigned short* sA = sbuf[buf];
+    unsigned short* sB = sA + stA;
+    for (int e = tid; e < S * 64 * 4 + S * 48 * 4; e += blockDim.x) {
+      const unsigned short* src;
+      unsigned short* dst;
+      int q;
+      if (e < S * 64 * 4) {
+        const int k = e / 256, r = (e >> 2) & 63;
+        q = e & 3;
+        src = gA + k * pA + (long long)r * Kpad + k0 + 8 * q;
+        dst = sA + (k * 64 + r) * OZ_LD + 8 * q;
+      } else {
+        const int e2 = e - S * 256, k = e2 / 192, r = (e2 >> 2) % 48;
+        q = e2 & 3;
+        src = gB + k * pB + (long long)r * Kpad + k0 + 8 * q;
+        dst = sB + (k * 48 + r) * OZ_LD + 8 * q;
+      }
+      const bool ok = k0 + 8 * q < Kpad;
+      oz_cp_async16(dst, ok ? src : gA, ok ? 16 : 0);
+    }
+    oz_cp_commit();
+  };
+  float acc[S][2][4];
+  long long Y[2][4];
+#pragma unroll
+  for (int a = 0; a < S; ++a)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[a][nt][v] = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Y[nt][v] = 0;
+  load(0, 0);
+  for (int sidx = 0; sidx < nstage; ++sidx) {
+    if (sidx + 1 < nstage) {
+      load(sidx + 1, (sidx + 1) & 1);
+      oz_cp_wait<1>();
+    } else {
+      oz_cp_wait<0>();
+    }
+    __syncthreads();
+    const unsigned short* sA = sbuf[sidx & 1];
+    const unsigned short* sB = sA + stA;
+#pragma unroll
+    for (int kk = 0; kk < OZ_KS; kk += 16)
+      oz_warp_k16_smem<S>(sA, 64 * OZ_LD, OZ_LD, wr * 16, sB, 48 * OZ_LD, OZ_LD, wc * 16, kk, acc);
+    __syncthreads();
+    if (((sidx + 1) * OZ_KS) % OZ_KCHUNK == 0 || sidx + 1 == nstage) oz_int_combine<S>(acc, Y);
+  }
+  double* Vout = w.vkr + (long long)m * w.vstride + (offs * 3) * ncv;
+  const double* dsq = w.dsq + offs * p.nq;
+  const int r0 = tile * 64 + wr * 16, cb = wc * 16;
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int row = r0 + g + (v >> 1) * 8, col = cb + nt * 8 + 2 * tq + (v & 1);
+      if (row < N && col < ncv) {
+        const int er = w.texp[w.off_tr[c] + row], ec = w.wexp[(long long)c * 48 + col];
+        const double y = (double)Y[nt][v] * oz_pow2(er + ec - 7 * (S + 1));
+        Vout[(long long)row * ncv + col] = dsq[(row / 3) * p.nq + col / 3 + 1] * y;
+      }
+    }
+}
+
+void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
+                      cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_slice_w<<<c1 - c0, 256, 0, s>>>(w, p, m, c0, digits);
+  const int tiles = (3 * max_ns + 63) / 64;
+  if (digits == 6) {
+    const size_t sm = 2 * sizeof(unsigned short) * (6 * 64 + 6 * 48) * OZ_LD;
+    cudaFuncSetAttribute(k_chain_oz2<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_chain_oz2<6><<<(c1 - c0) * tiles, 384, sm, s>>>(w, p, m, c0, tiles, st);
+  } else {
+    const size_t sm = 2 * sizeof(unsigned short) * (5 * 64 + 5 * 48) * OZ_LD;
+    cudaFuncSetAttribute(k_chain_oz2<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_chain_oz2<5><<<(c1 - c0) * tiles, 384, sm, s>>>(w, p, m, c0, tiles, st);
+  }
+}
+
+// Pair matrix M' = P Q^T on one 16 x 16 site tile with staged digit tiles (cp.async, two
+// stages of 32 K) and integer recombination; 9 warps of 16 x 16 outputs, then the per-pair
+// epilogue of the FP64 kernel.
+template <int S>
+__global__ void __launch_bounds__(288) k_mbd_adj_pair_oz2(Work w, DevParams p, int c0, int tiles_per_c) {
+  extern __shared__ __align__(16) unsigned short oz_sm[];
+  __shared__ double xs[2][PT][3];
+  __shared__ double rts[2][PT];
+  __shared__ double gp[PT][PT][4];
+  const int c = c0 + blockIdx.x / tiles_per_c;
+  const int tile = blockIdx.x % tiles_per_c;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns;
+  const int nt = (ns + PT - 1) / PT;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int bi = 0;
+  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+  const int bj = tile - bi * (bi + 1) / 2;
+  const long long offs = w.off_s[c];
+  const long long sbase = (long long)c * w.site_cap;
+  const int tid = threadIdx.x;
+  pair_tile_sites(w, p, offs, sbase, ns, bi, bj, xs, rts);
+  const int R = 3 * nt * PT, Kp = oz_kpad(w.ncol);
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const int wr = warp / 3, wc = warp % 3;
+  const long long dbase = w.off_sp[c] * 3 * (long long)Kp * S;
+  const unsigned short* gA = w.pdig + dbase + (long long)(bi * 48) * Kp;
+  const unsigned short* gB = w.qdig + dbase + (long long)(bj * 48) * Kp;
+  const long long pl = (long long)R * Kp;
+  const int st = S * 48 * OZ_LD;
+  unsigned short* sbuf[2] = {oz_sm, oz_sm + 2 * st};
+  const int nstage = (Kp + OZ_KS - 1) / OZ_KS;
+  auto load = [&](int stage, int buf) {
+    const int k0 = stage * OZ_KS;
+    unsigned short* sA = sbuf[buf];
+    unsigned short* sB = sA + st;
+    for (int e = tid; e < 2 * S * 48 * 4; e += blockDim.x) {
+      const int side = e / (S * 192), e2 = e % (S * 192), k = e2 / 192, r = (e2 >> 2) % 48, q = e2 & 3;
+      const unsigned short* src = (side == 0 ? gA : gB) + k * pl + (long long)r * Kp + k0 + 8 * q;
+      unsigned short* dst = (side == 0 ? sA : sB) + (k * 48 + r) * OZ_LD + 8 * q;
+      const bool ok = k0 + 8 * q < Kp;
+      oz_cp_async16(dst, ok ? src : gA, ok ? 16 : 0);
+    }
+    oz_cp_commit();
+  };
+  float acc[S][2][4];
+  long long Y[2][4];
+#pragma unroll
+  for (int a = 0; a < S; ++a)
+#pragma unroll
+    for (int n8 = 0; n8 < 2; ++n8)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[a][n8][v] = 0.f;
+#pragma unroll
+  for (int n8 = 0; n8 < 2; ++n8)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Y[n8][v] = 0;
+  load(0, 0);
+  for (int sidx = 0; sidx < nstage; ++sidx) {
+    if (sidx + 1 < nstage) {
+      load(sidx + 1, (sidx + 1) & 1);
+      oz_cp_wait<1>();
+    } else {
+      oz_cp_wait<0>();
+    }
+    __syncthreads();
+    const unsigned short* sA = sbuf[sidx & 1];
+    const unsigned short* sB = sA + st;
+#pragma unroll
+    for (int kk = 0; kk < OZ_KS; kk += 16)
+      oz_warp_k16_smem<S>(sA, 48 * OZ_LD, OZ_LD, wr * 16, sB, 48 * OZ_LD, OZ_LD, wc * 16, kk, acc);
+    __syncthreads();
+    if (((sidx + 1) * OZ_KS) % OZ_KCHUNK == 0 || sidx + 1 == nstage) oz_int_combine<S>(acc, Y);
+  }
+  // FP64 pair matrix of the tile in shared memory (reuses the staging buffer)
+  double* Ms = reinterpret_cast<double*>(oz_sm);
+  const int* pe = w.pexp + w.off_sp[c] * 3;
+  const int* qe = w.qexp + w.off_sp[c] * 3;
+#pragma unroll
+  for (int n8 = 0; n8 < 2; ++n8)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int rr = wr * 16 + g + (v >> 1) * 8, cc = wc * 16 + n8 * 8 + 2 * tq + (v & 1);
+      Ms[rr * 49 + cc] = (double)Y[n8][v] * oz_pow2(pe[bi * 48 + rr] + qe[bj * 48 + cc] - 7 * (S + 1));
+    }
+  __syncthreads();
+  if (tid < PT * PT) {
+    const int ty = tid / PT, tx = tid % PT;
+    const int s = bi * PT + ty, t = bj * PT + tx;
+    double a3[3][3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+      for (int be = 0; be < 3; ++be) a3[al][be] = Ms[(3 * ty + al) * 49 + 3 * tx + be];
+    pair_epilogue(w, offs, w.off_t[c], s, t, ns, a3, gp[ty][tx]);
+  }
+  __syncthreads();
+  pair_tile_reduce(w, offs, sbase, ns, bi, bj, gp);
+}
+
+void launch_mbd_adj_pair_oz2(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
+                             cudaStream_t s) {
+  if (c1 <= c0) return;
+  dim3 g2(c1 - c0, 2);
+  k_slice_pq<<<g2, 256, 0, s>>>(w, c0, digits);
+  const int nt = (max_ns + PT - 1) / PT;
+  const int tiles = nt * (nt + 1) / 2;
+  if (digits == 6) {
+    const size_t sm = 2 * 2 * sizeof(unsigned short) * 6 * 48 * OZ_LD;
+    cudaFuncSetAttribute(k_mbd_adj_pair_oz2<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_mbd_adj_pair_oz2<6><<<(c1 - c0) * tiles, 288, sm, s>>>(w, p, c0, tiles);
+  } else {
+    const size_t sm = 2 * 2 * sizeof(unsigned short) * 5 * 48 * OZ_LD;
+    cudaFuncSetAttribute(k_mbd_adj_pair_oz2<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_mbd_adj_pair_oz2<5><<<(c1 - c0) * tiles, 288, sm, s>>>(w, p, c0, tiles);
+  }
 }

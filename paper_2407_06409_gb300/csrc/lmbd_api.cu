@@ -44,7 +44,7 @@ struct Ctx {
   DevBuf site_atom, site_x, counts, off_k1, off_s, off_b, off_t, totals, status;
   DevBuf xsol, alphaK, alphaI, alphaT, dsq, tlr, vkr, energies, trbuf;
   DevBuf pcount, off_p, off_a, pr_ij, pr_geo, pr_rad, prow, prow_k2, arow, adj, lfac;
-  DevBuf k2ptr, k2rev, sgq, gstage, order_d;
+  DevBuf k2ptr, k2rev, sgq, gstage, order_d, pcoef;
   std::vector<Counts> counts_h;
   std::vector<int> order_h;
   DevBuf off_tq, off_tr, off_kp, off_sp, tdig, texp, wdig, wexp, pdig, qdig, pexp, qexp;
@@ -463,6 +463,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     TRY(ensure(c->pmat, sizeof(double) * (size_t)sum_ns * 3 * (ncol > 0 ? ncol : 1)));
     TRY(ensure(c->qmat, sizeof(double) * (size_t)sum_ns * 3 * (ncol > 0 ? ncol : 1)));
     TRY(ensure(c->x0buf, sizeof(double) * (size_t)sum_ns * 9));
+    TRY(ensure(c->pcoef, sizeof(double) * (size_t)sum_t));
     TRY(ensure(c->rbar, sizeof(double) * (size_t)sum_ns));
     TRY(ensure(c->alphaK_bar, sizeof(double) * (size_t)sum_n1 * nq));
     TRY(ensure(c->alphaI_bar, sizeof(double) * (size_t)N * nq));
@@ -471,6 +472,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     w.pmat = (double*)c->pmat.p;
     w.qmat = (double*)c->qmat.p;
     w.x0buf = (double*)c->x0buf.p;
+    w.pcoef = (double*)c->pcoef.p;
     w.rbar = (double*)c->rbar.p;
     w.alphaK_bar = (double*)c->alphaK_bar.p;
     w.alphaI_bar = (double*)c->alphaI_bar.p;
@@ -514,7 +516,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       if (sliced_chain) launch_slice_t(w, c0, c0 + 1, ST, s);
       for (int m = 1; m < nvec; ++m) {
         if (sliced_chain)
-          launch_chain_oz(w, dp, m, c0, c0 + 1, max_ns, m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A, ST, s);
+          launch_chain_oz2(w, dp, m, c0, c0 + 1, max_ns, m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A, ST, s);
         else
           launch_mbd_chain_sized(w, dp, m, c0, c0 + 1, max_ns, s);
       }
@@ -530,7 +532,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     mark(LMBD_PHASE_CHAIN);
     for (int m = 1; m < nvec; ++m) {
       if (sliced_chain)
-        launch_chain_oz(w, dp, m, 0, N, max_ns, m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A, ST, s);
+        launch_chain_oz2(w, dp, m, 0, N, max_ns, m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A, ST, s);
       else
         launch_mbd_chain_sized(w, dp, m, 0, N, max_ns, s);
     }
@@ -550,7 +552,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       for (int c0 = 0; c0 < N; ++c0) {
         launch_mbd_adj_series(w, dp, c0, c0 + 1, s);
         if (sliced && ncol > 0)
-          launch_mbd_adj_pair_oz(w, dp, c0, c0 + 1, max_ns, DIG_P, s);
+          launch_mbd_adj_pair_oz2(w, dp, c0, c0 + 1, max_ns, DIG_P, s);
         else
           launch_mbd_adj_pair(w, dp, c0, c0 + 1, max_ns, s);
         launch_mbd_adj_blend(w, dp, c0, c0 + 1, s);
@@ -568,7 +570,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       launch_mbd_adj_series(w, dp, 0, N, s);
       mark(LMBD_PHASE_ADJ_PAIR);
       if (sliced && ncol > 0)
-        launch_mbd_adj_pair_oz(w, dp, 0, N, max_ns, DIG_P, s);
+        launch_mbd_adj_pair_oz2(w, dp, 0, N, max_ns, DIG_P, s);
       else
         launch_mbd_adj_pair(w, dp, 0, N, max_ns, s);
       mark(LMBD_PHASE_ADJ_BLEND);
@@ -809,7 +811,7 @@ int lmbd_destroy(lmbd_ctx* ctx) {
                    &c.off_s, &c.off_b, &c.off_t, &c.totals, &c.status, &c.xsol, &c.alphaK, &c.pcount,
                    &c.off_p, &c.off_a, &c.pr_ij, &c.pr_geo, &c.pr_rad, &c.prow, &c.prow_k2, &c.arow, &c.adj,
                    &c.lfac, &c.off_tq, &c.off_tr, &c.off_kp, &c.off_sp, &c.tdig, &c.texp, &c.wdig, &c.wexp,
-                   &c.pdig, &c.qdig, &c.pexp, &c.qexp, &c.k2ptr, &c.k2rev, &c.sgq, &c.gstage, &c.order_d,
+                   &c.pdig, &c.qdig, &c.pexp, &c.qexp, &c.k2ptr, &c.k2rev, &c.sgq, &c.gstage, &c.order_d, &c.pcoef,
                    &c.alphaI, &c.alphaT, &c.dsq, &c.tlr, &c.vkr, &c.energies, &c.trbuf, &c.gbar, &c.pmat,
                    &c.qmat, &c.x0buf, &c.rbar, &c.alphaK_bar, &c.alphaI_bar, &c.gacc};
   for (DevBuf* b : all) release(*b);

@@ -126,6 +126,7 @@ struct Work {
   double* qmat;                // off_s*3 x ncol
   int ncol;                    // 3 n_freq (n_max - 2)
   double* x0buf;               // off_s x 9, central-column term of the pair matrix
+  double* pcoef;               // off_t: per site pair (s > t) r (3) and 5 derivative coefficients
   double* rbar;                // dL/d R~ per sphere site, off_s
   double* alphaK_bar;          // off_k1 * nq
   double* alphaI_bar;          // N x nq
@@ -230,6 +231,10 @@ void launch_forces_out(const Work& w, double* forces, cudaStream_t s);
 void launch_slice_t(const Work& w, int c0, int c1, int st, cudaStream_t s);
 void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
                      cudaStream_t s);
+void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
+                      cudaStream_t s);
+void launch_mbd_adj_pair_oz2(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
+                             cudaStream_t s);
 void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
                             cudaStream_t s);
 

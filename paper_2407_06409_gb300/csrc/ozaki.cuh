@@ -121,3 +121,64 @@ __device__ __forceinline__ double oz_combine(const float (&acc)[S][2][4], int nt
   for (int m = S - 1; m >= 0; --m) y += (double)acc[m][nt][v] * oz_pow2(er + ec - 7 * (m + 2));
   return y;
 }
+
+// ---------------------------------------------------------------------------------------
+// shared-memory staged variant
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void oz_cp_async16(void* smem_dst, const void* gsrc, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(bytes));
+}
+__device__ __forceinline__ void oz_cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void oz_cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ uint32_t oz_lds32(const unsigned short* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// One warp, one k16 step from shared-memory tiles: A digit planes [S][*][lda] at rows ar..ar+15,
+// B digit planes [S][*][ldb] at rows br..br+15 (two n8 tiles).
+template <int S>
+__device__ __forceinline__ void oz_warp_k16_smem(const unsigned short* sA, int pa, int lda, int ar,
+                                                 const unsigned short* sB, int pb, int ldb, int br, int kk,
+                                                 float (&acc)[S][2][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t b[S][2][2];
+#pragma unroll
+  for (int l = 0; l < S; ++l)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const unsigned short* q = sB + l * pb + (br + nt * 8 + g) * ldb + kk + 2 * t;
+      b[l][nt][0] = oz_lds32(q);
+      b[l][nt][1] = oz_lds32(q + 8);
+    }
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const unsigned short* q = sA + k * pa + (ar + g) * lda + kk + 2 * t;
+    uint32_t a[4];
+    a[0] = oz_lds32(q);
+    a[1] = oz_lds32(q + 8 * lda);
+    a[2] = oz_lds32(q + 8);
+    a[3] = oz_lds32(q + 8 * lda + 8);
+#pragma unroll
+    for (int l = 0; l < S - k; ++l)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) oz_mma(acc[k + l][nt], a, b[l][nt]);
+  }
+}
+
+// Exact integer recombination of the digit-order groups: Y += sum_m acc_m 2^{7 (S - 1 - m)}
+// (every group value is an integer held exactly by the FP32 accumulator or rounded to one).
+template <int S>
+__device__ __forceinline__ void oz_int_combine(float (&acc)[S][2][4], long long (&Y)[2][4]) {
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      long long s = 0;
+#pragma unroll
+      for (int m = 0; m < S; ++m) s += (long long)__float2int_rn(acc[m][nt][v]) << (7 * (S - 1 - m));
+      Y[nt][v] += s;
+#pragma unroll
+      for (int m = 0; m < S; ++m) acc[m][nt][v] = 0.f;
+    }
+}
