@@ -259,8 +259,8 @@ def run_ours(args, world, rank, local):
     avg_ms = phase_ms[dom] / max(1, phase_launch[dom])
     flops_launch = phase_flops[dom] / max(1, phase_launch[dom])
     achieved = flops_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
-    kernel_names = {"scs": "k_scs_forward", "chain": "k_mbd_chain", "adj_pair": "k_mbd_adj_pair",
-                    "adj_scs": "k_scs_adjoint"}
+    kernel_names = {"scs": "k_scs_factor", "chain": "k_chain_oz2", "adj_pair": "k_mbd_adj_pair_oz2",
+                    "adj_scs": "k_scs_adjoint2"}
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kernel_names[dom],
                 "peak_note": "nominal FP64 (DFMA/DMMA) of GB300 from the profiling recipe; a DFMA-chain "
