@@ -35,6 +35,8 @@
 #ifndef LMBD_H
 #define LMBD_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -101,6 +103,10 @@ typedef struct {
   long long n_sites;       /* total sites over all central atoms (within the list radius)  */
   int max_k1, max_sphere, max_sites; /* largest K1, sphere and site-list capacity           */
   int kernel_launches;     /* kernels launched by the call                                  */
+  double bytes_arena;      /* of bytes_workspace: the arena holding the per-wave arrays       */
+  int waves_scs;           /* waves of central atoms in the forward SCS stage                 */
+  int waves_mbd;           /* waves of central atoms in the MBD stage (energy and adjoint)    */
+  int scs_recomputed;      /* 1 when the SCS stage was evaluated again before its adjoint     */
 } lmbd_stats;
 
 /* Fill *out with the defaults r_scs = 5, r_mbd1 = r_mbd2 = r_sphere = 7,
@@ -152,7 +158,19 @@ int lmbd_set_launch_mode(lmbd_ctx* ctx, int mode);
 #define LMBD_PREC_SLICED 1
 int lmbd_set_precision(lmbd_ctx* ctx, int mode);
 
-/* Per-phase device timing with CUDA events (0 = off, the default). */
+/* Device memory budget of the context in bytes (0 = the default: the device's free
+ * memory at each call less 1 GiB).  Central atoms are processed in contiguous waves whose
+ * per-centre arrays fit the budget: the SCS stage of every centre first (its central
+ * polarisabilities feed every sphere that contains the atom), then the MBD energy and its
+ * adjoint wave by wave, then the SCS adjoint wave by wave.  When the SCS arrays of all
+ * centres do not fit beside one MBD wave, each SCS adjoint wave first evaluates its SCS
+ * stage again (same arithmetic, same results).  Results do not depend on the waves up to
+ * the order of floating-point atomic additions in the forces.  A budget too small for one
+ * central atom gives LMBD_ENOMEM.                                                          */
+int lmbd_set_memory_budget(lmbd_ctx* ctx, size_t bytes);
+
+/* Per-phase device timing with CUDA events (0 = off, the default; reported only when
+ * every stage ran as a single wave). */
 int lmbd_set_profiling(lmbd_ctx* ctx, int on);
 
 /* Central polarisabilities alpha_I,k(omega) of the last call (Sec. III.B):

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) k_scs_count(Work w, DevParams p, int max_
 // One block per central atom.  Pairs are ordered by owner row i: first the K1 partners
 // j < i (ascending), then the K2 partners (ascending); adjacency rows list every K1
 // partner j != i (ascending) with the index of the shared pair.
-__global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int max_n12, int max_n1) {
+__global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, int max_n12, int max_n1) {
   extern __shared__ double smem_d[];
   double* xs = smem_d;                             // 3 x max_n12
   int* pid = (int*)(xs + 3 * max_n12);             // max_n1 x max_n1 (pair index, -1 = none)
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int max_n
   int* adjcnt = rowstart + max_n1 + 1;             // max_n1
   int* adjstart = adjcnt + max_n1;                 // max_n1 + 1
   int* k2cnt = adjstart + max_n1 + 1;              // max_n12
-  const int c = blockIdx.x;
+  const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
   const Counts cn = w.counts[c];
   const int n1 = cn.n1, n12 = cn.n12;
@@ -815,12 +815,12 @@ void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream
   k_scs_count<<<w.n_atoms, 256, sm, s>>>(w, p, max_n12);
 }
 
-void launch_scs_fill(const Work& w, const DevParams& p, int max_n12, int max_n1, cudaStream_t s) {
-  if (w.n_atoms == 0) return;
+void launch_scs_fill(const Work& w, const DevParams& p, int c0, int c1, int max_n12, int max_n1, cudaStream_t s) {
+  if (c1 <= c0) return;
   size_t sm = sizeof(double) * 3 * (size_t)max_n12 +
               sizeof(int) * ((size_t)max_n1 * max_n1 + 6 * (size_t)max_n1 + 2 + (size_t)max_n12);
   cudaFuncSetAttribute(k_scs_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_scs_fill<<<w.n_atoms, 256, sm, s>>>(w, p, max_n12, max_n1);
+  k_scs_fill<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_n12, max_n1);
 }
 
 size_t scs2_forward_smem(int max_n1, int max_n12) { return scs2_smem_bytes(max_n1, max_n12, false); }

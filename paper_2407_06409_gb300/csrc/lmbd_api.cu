@@ -38,17 +38,31 @@ struct Ctx {
   int site_cap = 0;
   int last_n = 0;
   lmbd_stats stats{};
-  // device buffers
+  size_t mem_budget = 0;          // bytes the context may hold on the device (0 = free memory)
+  // device buffers: whole-structure arrays, then one arena for the per-wave workspaces
   DevBuf table_d, pos_d, species_d, nu_d, weights_d, out_e_d, out_f_d;
   DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
-  DevBuf site_atom, site_x, counts, off_k1, off_s, off_b, off_t, totals, status;
-  DevBuf xsol, alphaK, alphaI, alphaT, dsq, tlr, vkr, energies, trbuf;
-  DevBuf pcount, off_p, off_a, pr_ij, pr_geo, pr_rad, prow, prow_k2, arow, adj, lfac;
-  DevBuf k2ptr, k2rev, sgq, gstage, order_d, pcoef;
+  DevBuf site_atom, site_x, counts, offs, totals, status, pcount;
+  DevBuf alphaK, alphaI, energies, trbuf, wexp, alphaK_bar, alphaI_bar, gacc;
+  DevBuf order1_d, order3_d;
+  DevBuf arena;
   std::vector<Counts> counts_h;
-  std::vector<int> order_h;
-  DevBuf off_tq, off_tr, off_kp, off_sp, tdig, texp, wdig, wexp, pdig, qdig, pexp, qexp;
-  DevBuf gbar, pmat, qmat, x0buf, rbar, alphaK_bar, alphaI_bar, gacc;
+  std::vector<long long> offs_h;
+  std::vector<int> order1_h, order3_h;
+  DevBuf* whole_bufs[36] = {};
+  int n_whole = 0;
+  Ctx() {
+    DevBuf* l[] = {&table_d, &pos_d, &species_d, &nu_d, &weights_d, &out_e_d, &out_f_d, &abar, &sig, &rvdw,
+                   &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
+                   &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
+                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d};
+    for (DevBuf* b : l) whole_bufs[n_whole++] = b;
+  }
+  size_t whole_bytes() const {
+    size_t t = 0;
+    for (int i = 0; i < n_whole; ++i) t += whole_bufs[i]->bytes;
+    return t;
+  }
   long long* totals_h = nullptr;   // pinned
   int* status_h = nullptr;         // pinned
 };
@@ -153,6 +167,193 @@ int stage_input(DevBuf& buf, const void* src, size_t bytes, cudaStream_t s, cons
   return LMBD_OK;
 }
 
+// ---- per-wave workspaces ------------------------------------------------------------------
+// Central atoms are processed in contiguous waves [c0, c1) whose per-centre arrays fit the
+// memory budget.  The arrays of a wave live in one arena; every pointer is rebased by the
+// wave's first offset, so kernels index them with the whole-structure offsets unchanged.
+enum { O_K1, O_S, O_B, O_T, O_P, O_A, O_TQ, O_TR, O_KP, O_SP, O_COUNT };
+
+struct Offs {
+  const long long* h;
+  int N;
+  long long at(int k, int i) const { return h[(size_t)k * (N + 1) + i]; }
+  long long span(int k, int c0, int c1) const { return at(k, c1) - at(k, c0); }
+};
+
+struct Carver {
+  char* base;   // NULL: sizing only
+  size_t used;
+  // n elements of T; the returned pointer is shifted down by `shift` elements
+  template <class T>
+  T* take(long long n, long long shift) {
+    used = (used + 255) & ~(size_t)255;
+    T* p = nullptr;
+    if (base) p = reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(base + used) - (uintptr_t)shift * sizeof(T));
+    used += (size_t)(n > 0 ? n : 1) * sizeof(T);
+    return p;
+  }
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+  int nq, ncv, nvec, ncol, kp_pair, st, dig_p, site_cap;
+  bool forces, sliced_chain, sliced_pair;
+
+  // stage 1 (SCS): pair lists, FP32 factors and solutions of centres [c0, c1)
+  size_t stage1(const Offs& o, int c0, int c1, char* base, Work* w) const {
+    Carver cv{base, 0};
+    const long long p0 = o.at(O_P, c0), np = o.span(O_P, c0, c1);
+    const long long a0 = o.at(O_A, c0), na = o.span(O_A, c0, c1);
+    const long long k0 = o.at(O_K1, c0), nk = o.span(O_K1, c0, c1);
+    const long long n = c1 - c0;
+    float* lfac = cv.take<float>(o.span(O_B, c0, c1), o.at(O_B, c0));
+    int* pr_ij = cv.take<int>(2 * (np + 1), 2 * p0);
+    double* pr_geo = cv.take<double>(8 * (np + 1), 8 * p0);
+    double* pr_rad = cv.take<double>(6LL * nq * (np + 1), 6LL * nq * p0);
+    int* k2rev = cv.take<int>(np + 1, p0);
+    int* prow = cv.take<int>(nk + n, k0 + c0);
+    int* prow_k2 = cv.take<int>(nk + n, k0 + c0);
+    int* arow = cv.take<int>(nk + n, k0 + c0);
+    int* adj = cv.take<int>(2 * (na + 1), 2 * a0);
+    int* k2ptr = cv.take<int>(n * site_cap + 1, (long long)c0 * site_cap);
+    double* xsol = cv.take<double>(9LL * nq * nk, 9LL * nq * k0);
+    if (w) {
+      w->lfac = lfac;
+      w->pr_ij = pr_ij;
+      w->pr_geo = pr_geo;
+      w->pr_rad = pr_rad;
+      w->k2rev = k2rev;
+      w->prow = prow;
+      w->prow_k2 = prow_k2;
+      w->arow = arow;
+      w->adj = adj;
+      w->k2ptr = k2ptr;
+      w->xsol = xsol;
+    }
+    return align256(cv.used);
+  }
+
+  // scratch of the SCS adjoint: pair and site gradients of centres [c0, c1)
+  size_t scs_adjoint(const Offs& o, int c0, int c1, char* base, Work* w) const {
+    Carver cv{base, 0};
+    const long long p0 = o.at(O_P, c0), np = o.span(O_P, c0, c1);
+    double* gstage = cv.take<double>(3LL * nq * (np + 1), 3LL * nq * p0);
+    double* sgq = cv.take<double>(3LL * nq * (c1 - c0) * site_cap, 3LL * nq * c0 * site_cap);
+    if (w) {
+      w->gstage = gstage;
+      w->sgq = sgq;
+    }
+    return align256(cv.used);
+  }
+
+  // stage 2 (MBD): blended polarisabilities, T_LR, Krylov blocks, slices and adjoint arrays
+  size_t stage2(const Offs& o, int c0, int c1, char* base, Work* w, unsigned short** wdig_raw) const {
+    Carver cv{base, 0};
+    const long long s0 = o.at(O_S, c0), ns = o.span(O_S, c0, c1);
+    const long long t0 = o.at(O_T, c0), nt = o.span(O_T, c0, c1);
+    double* alphaT = cv.take<double>((long long)nq * ns, (long long)nq * s0);
+    double* dsq = cv.take<double>((long long)nq * ns, (long long)nq * s0);
+    double* tlr = cv.take<double>(nt, t0);
+    double* vkr = cv.take<double>((long long)nvec * ns * 3 * ncv, s0 * 3 * ncv);
+    if (w) {
+      w->alphaT = alphaT;
+      w->dsq = dsq;
+      w->tlr = tlr;
+      w->vkr = vkr;
+      w->vstride = ns * 3 * ncv;
+    }
+    if (sliced_chain) {
+      unsigned short* tdig = cv.take<unsigned short>((long long)st * o.span(O_TQ, c0, c1), (long long)st * o.at(O_TQ, c0));
+      int* texp = cv.take<int>(o.span(O_TR, c0, c1), o.at(O_TR, c0));
+      // W planes: the digit count varies per chain step, so the pointer is rebased per launch
+      unsigned short* wdig = cv.take<unsigned short>(48LL * st * o.span(O_KP, c0, c1), 0);
+      if (w) {
+        w->tdig = tdig;
+        w->texp = texp;
+        *wdig_raw = wdig;
+      }
+    }
+    if (forces) {
+      const long long nc = ncol > 0 ? ncol : 1;
+      double* gbar = cv.take<double>((long long)nq * ns, (long long)nq * s0);
+      double* pmat = cv.take<double>(3 * ns * nc, 3 * s0 * nc);
+      double* qmat = cv.take<double>(3 * ns * nc, 3 * s0 * nc);
+      double* x0buf = cv.take<double>(9 * ns, 9 * s0);
+      double* pcoef = cv.take<double>(nt, t0);
+      double* rbar = cv.take<double>(ns, s0);
+      if (w) {
+        w->gbar = gbar;
+        w->pmat = pmat;
+        w->qmat = qmat;
+        w->x0buf = x0buf;
+        w->pcoef = pcoef;
+        w->rbar = rbar;
+      }
+      if (sliced_pair) {
+        const long long sp0 = o.at(O_SP, c0), nsp = o.span(O_SP, c0, c1);
+        const long long per = 3LL * kp_pair * dig_p;
+        unsigned short* pdig = cv.take<unsigned short>(per * nsp, per * sp0);
+        unsigned short* qdig = cv.take<unsigned short>(per * nsp, per * sp0);
+        int* pexp = cv.take<int>(3 * nsp, 3 * sp0);
+        int* qexp = cv.take<int>(3 * nsp, 3 * sp0);
+        if (w) {
+          w->pdig = pdig;
+          w->qdig = qdig;
+          w->pexp = pexp;
+          w->qexp = qexp;
+        }
+      }
+    }
+    return align256(cv.used);
+  }
+};
+
+// Contiguous waves [cuts[i], cuts[i+1]) with size(c0, c1) <= cap; false when one centre alone
+// does not fit.
+template <class F>
+bool partition(int N, size_t cap, F size, std::vector<int>& cuts) {
+  cuts.assign(1, 0);
+  int c0 = 0;
+  while (c0 < N) {
+    if (size(c0, c0 + 1) > cap) return false;
+    int c1 = c0 + 1;
+    while (c1 < N && size(c0, c1 + 1) <= cap) ++c1;
+    cuts.push_back(c1);
+    c0 = c1;
+  }
+  return true;
+}
+
+// Size buckets for the SCS kernels: within each wave, centres sorted by |K1|, one launch per
+// bucket of width 6 in |K1| with shared memory sized to the bucket.
+struct Bucket {
+  int b0, b1, n1, n12;
+};
+void make_buckets(const std::vector<Counts>& cnt, const std::vector<int>& cuts, std::vector<int>& order,
+                  std::vector<std::vector<Bucket>>& buckets) {
+  const int N = (int)cnt.size();
+  order.resize(N);
+  for (int i = 0; i < N; ++i) order[i] = i;
+  buckets.assign(cuts.size() - 1, {});
+  for (size_t wv = 0; wv + 1 < cuts.size(); ++wv) {
+    const int c0 = cuts[wv], c1 = cuts[wv + 1];
+    std::stable_sort(order.begin() + c0, order.begin() + c1, [&](int x, int y) { return cnt[x].n1 < cnt[y].n1; });
+    int b0 = c0;
+    while (b0 < c1) {
+      const int lo = cnt[order[b0]].n1;
+      int b1 = b0, n1m = 0, n12m = 0;
+      while (b1 < c1 && cnt[order[b1]].n1 < lo + 6) {
+        n1m = std::max(n1m, cnt[order[b1]].n1);
+        n12m = std::max(n12m, cnt[order[b1]].n12);
+        ++b1;
+      }
+      buckets[wv].push_back({b0, b1, n1m, n12m});
+      b0 = b1;
+    }
+  }
+}
+
 int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec_in, const double* nu_in,
         const double* w_in, double* e_out, double* f_out, cudaStream_t s) {
   lmbd_stats st{};
@@ -253,18 +454,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   TRY(ensure(c->cell_atoms, sizeof(int) * N));
   TRY(ensure(c->grid, sizeof(Grid)));
   TRY(ensure(c->counts, sizeof(Counts) * N));
-  TRY(ensure(c->off_k1, sizeof(long long) * (N + 1)));
-  TRY(ensure(c->off_s, sizeof(long long) * (N + 1)));
-  TRY(ensure(c->off_b, sizeof(long long) * (N + 1)));
-  TRY(ensure(c->off_t, sizeof(long long) * (N + 1)));
+  TRY(ensure(c->offs, sizeof(long long) * O_COUNT * (size_t)(N + 1)));
   TRY(ensure(c->totals, sizeof(long long) * 16));
-  TRY(ensure(c->off_tq, sizeof(long long) * (N + 1)));
-  TRY(ensure(c->off_tr, sizeof(long long) * (N + 1)));
-  TRY(ensure(c->off_kp, sizeof(long long) * (N + 1)));
-  TRY(ensure(c->off_sp, sizeof(long long) * (N + 1)));
   TRY(ensure(c->pcount, sizeof(int) * 2 * N));
-  TRY(ensure(c->off_p, sizeof(long long) * (N + 1)));
-  TRY(ensure(c->off_a, sizeof(long long) * (N + 1)));
   TRY(ensure(c->status, sizeof(int) * 4));
   TRY(ensure(c->alphaI, sizeof(double) * N * nq));
   TRY(ensure(c->energies, sizeof(double) * N));
@@ -303,19 +495,20 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   w.ncells = ncells;
   w.grid = (Grid*)c->grid.p;
   w.counts = (Counts*)c->counts.p;
-  w.off_k1 = (long long*)c->off_k1.p;
-  w.off_s = (long long*)c->off_s.p;
-  w.off_b = (long long*)c->off_b.p;
-  w.off_t = (long long*)c->off_t.p;
+  long long* const ob = (long long*)c->offs.p;
+  w.off_k1 = ob + (size_t)O_K1 * (N + 1);
+  w.off_s = ob + (size_t)O_S * (N + 1);
+  w.off_b = ob + (size_t)O_B * (N + 1);
+  w.off_t = ob + (size_t)O_T * (N + 1);
+  w.off_p = ob + (size_t)O_P * (N + 1);
+  w.off_a = ob + (size_t)O_A * (N + 1);
+  w.off_tq = ob + (size_t)O_TQ * (N + 1);
+  w.off_tr = ob + (size_t)O_TR * (N + 1);
+  w.off_kp = ob + (size_t)O_KP * (N + 1);
+  w.off_sp = ob + (size_t)O_SP * (N + 1);
   w.totals = (long long*)c->totals.p;
   w.status = (int*)c->status.p;
   w.pcount = (int*)c->pcount.p;
-  w.off_p = (long long*)c->off_p.p;
-  w.off_a = (long long*)c->off_a.p;
-  w.off_tq = (long long*)c->off_tq.p;
-  w.off_tr = (long long*)c->off_tr.p;
-  w.off_kp = (long long*)c->off_kp.p;
-  w.off_sp = (long long*)c->off_sp.p;
   w.alphaI = (double*)c->alphaI.p;
   w.energies = (double*)c->energies.p;
   w.trbuf = (double*)c->trbuf.p;
@@ -332,7 +525,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     for (int i = 0; i < 3 * N; ++i)
       if (!std::isfinite(pos_in[i])) return LMBD_EINVAL;
 
-  const bool prof = c->profiling && c->launch_mode == LMBD_LAUNCH_BATCHED;
+  const bool prof_req = c->profiling && c->launch_mode == LMBD_LAUNCH_BATCHED;
+  bool prof = prof_req;   // per-phase events only when every stage runs as one wave
   int phase_launch[LMBD_NPHASE] = {};
   bool marked[LMBD_NPHASE + 1] = {};
   auto mark = [&](int ph) {
@@ -344,8 +538,6 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   mark(LMBD_PHASE_NEIGHBORS);
   launch_free_atom(w, dp, s);
   ++launches;
-  Counts* cn = nullptr;
-  (void)cn;
   for (int attempt = 0; attempt < 4; ++attempt) {
     TRY(ensure(c->site_atom, sizeof(int) * (size_t)N * c->site_cap));
     TRY(ensure(c->site_x, sizeof(double) * 3 * (size_t)N * c->site_cap));
@@ -367,223 +559,264 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     c->site_cap *= 2;
   }
   phase_launch[LMBD_PHASE_NEIGHBORS] = launches;
-  const long long sum_n1 = c->totals_h[0], sum_ns = c->totals_h[1], sum_b = c->totals_h[2],
-                  sum_t = c->totals_h[3];
+  const long long sum_n1 = c->totals_h[0];
   const int max_n1 = (int)c->totals_h[4], max_ns = (int)c->totals_h[5], max_n12 = (int)c->totals_h[6];
-  const long long sum_pairs = c->totals_h[8], sum_adj = c->totals_h[9];
-  const long long sum_tq = c->totals_h[12], sum_tr = c->totals_h[13], sum_kp = c->totals_h[14],
-                  sum_sp = c->totals_h[15];
   // kernel shared-memory capacities (per-centre systems live in shared memory)
   if (max_n1 > 96 || max_ns > 1024 || max_n12 > 4096) return LMBD_ECAPACITY;
   if (scs2_adjoint_smem(max_n1, max_n12) > 227 * 1024) return LMBD_ECAPACITY;
-  // size buckets for the SCS kernels: centres sorted by |K1|, one launch per bucket of width 6
-  // in |K1| with shared memory sized to the bucket (more blocks per SM for typical centres)
-  struct Bucket { int b0, b1, n1, n12; };
-  std::vector<Bucket> buckets;
-  {
-    c->counts_h.resize(N);
-    CK(cudaMemcpy(c->counts_h.data(), w.counts, sizeof(Counts) * N, cudaMemcpyDeviceToHost));
-    c->order_h.resize(N);
-    for (int i = 0; i < N; ++i) c->order_h[i] = i;
-    std::stable_sort(c->order_h.begin(), c->order_h.end(),
-                     [&](int x, int y) { return c->counts_h[x].n1 < c->counts_h[y].n1; });
-    int b0 = 0;
-    while (b0 < N) {
-      const int lo = c->counts_h[c->order_h[b0]].n1;
-      int b1 = b0, n1m = 0, n12m = 0;
-      while (b1 < N && c->counts_h[c->order_h[b1]].n1 < lo + 6) {
-        n1m = std::max(n1m, c->counts_h[c->order_h[b1]].n1);
-        n12m = std::max(n12m, c->counts_h[c->order_h[b1]].n12);
-        ++b1;
-      }
-      buckets.push_back({b0, b1, n1m, n12m});
-      b0 = b1;
-    }
-    TRY(ensure(c->order_d, sizeof(int) * N));
-    CK(cudaMemcpyAsync(c->order_d.p, c->order_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
-  }
-  const int* order_dev = (const int*)c->order_d.p;
+  c->counts_h.resize(N);
+  c->offs_h.resize((size_t)O_COUNT * (N + 1));
+  CK(cudaMemcpyAsync(c->counts_h.data(), w.counts, sizeof(Counts) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->offs_h.data(), ob, sizeof(long long) * O_COUNT * (N + 1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const Offs o{c->offs_h.data(), N};
 
-  // ---- workspaces -------------------------------------------------------------------------
+  // ---- whole-structure arrays -------------------------------------------------------------
   const int ncv = 3 * c->n_freq;
   const int nvec = forces ? (c->order - 1) : (c->order + 1) / 2;
   const int ncol = 3 * c->n_freq * (c->order - 2);
-  TRY(ensure(c->lfac, sizeof(float) * (size_t)sum_b));
-  TRY(ensure(c->pr_ij, sizeof(int) * 2 * (size_t)(sum_pairs + 1)));
-  TRY(ensure(c->pr_geo, sizeof(double) * 8 * (size_t)(sum_pairs + 1)));
-  TRY(ensure(c->k2ptr, sizeof(int) * ((size_t)N * c->site_cap + 1)));
-  TRY(ensure(c->k2rev, sizeof(int) * (size_t)(sum_pairs + 1)));
-  TRY(ensure(c->pr_rad, sizeof(double) * 6 * (size_t)nq * (sum_pairs + 1)));
-  TRY(ensure(c->prow, sizeof(int) * (size_t)(sum_n1 + N)));
-  TRY(ensure(c->prow_k2, sizeof(int) * (size_t)(sum_n1 + N)));
-  TRY(ensure(c->arow, sizeof(int) * (size_t)(sum_n1 + N)));
-  TRY(ensure(c->adj, sizeof(int) * 2 * (size_t)(sum_adj + 1)));
-  TRY(ensure(c->xsol, sizeof(double) * (size_t)sum_n1 * nq * 9));
-  TRY(ensure(c->alphaK, sizeof(double) * (size_t)sum_n1 * nq));
-  TRY(ensure(c->alphaT, sizeof(double) * (size_t)sum_ns * nq));
-  TRY(ensure(c->dsq, sizeof(double) * (size_t)sum_ns * nq));
-  TRY(ensure(c->tlr, sizeof(double) * (size_t)sum_t));
-  TRY(ensure(c->vkr, sizeof(double) * (size_t)nvec * sum_ns * 3 * ncv));
-  w.lfac = (float*)c->lfac.p;
-  w.pr_ij = (int*)c->pr_ij.p;
-  w.pr_geo = (double*)c->pr_geo.p;
-  w.pr_rad = (double*)c->pr_rad.p;
-  w.prow = (int*)c->prow.p;
-  w.prow_k2 = (int*)c->prow_k2.p;
-  w.arow = (int*)c->arow.p;
-  w.adj = (int*)c->adj.p;
-  w.k2ptr = (int*)c->k2ptr.p;
-  w.k2rev = (int*)c->k2rev.p;
-  w.xsol = (double*)c->xsol.p;
-  w.alphaK = (double*)c->alphaK.p;
-  w.alphaT = (double*)c->alphaT.p;
-  w.dsq = (double*)c->dsq.p;
-  w.tlr = (double*)c->tlr.p;
-  w.vkr = (double*)c->vkr.p;
-  w.nvec = nvec;
   // sliced tensor-core products: digits per product (see ozaki.cuh and the design notes)
   const bool sliced = c->precision == LMBD_PREC_SLICED;
   const bool sliced_chain = sliced && ncv <= 48;
   const int ST = 6, DIG_E = 6, DIG_A = 5, DIG_P = 5;
-  const int Kp_pair = (ncol + 15) / 16 * 16;
+  TRY(ensure(c->alphaK, sizeof(double) * (size_t)sum_n1 * nq));
+  w.alphaK = (double*)c->alphaK.p;
+  w.nvec = nvec;
+  w.ncol = ncol;
   if (sliced_chain) {
-    TRY(ensure(c->tdig, sizeof(unsigned short) * (size_t)ST * sum_tq));
-    TRY(ensure(c->texp, sizeof(int) * (size_t)sum_tr));
-    TRY(ensure(c->wdig, sizeof(unsigned short) * (size_t)48 * ST * sum_kp));
     TRY(ensure(c->wexp, sizeof(int) * (size_t)48 * N));
-    w.tdig = (unsigned short*)c->tdig.p;
-    w.texp = (int*)c->texp.p;
-    w.wdig = (unsigned short*)c->wdig.p;
     w.wexp = (int*)c->wexp.p;
   }
-  w.vstride = sum_ns * 3 * ncv;
-  w.ncol = ncol;
   if (forces) {
-    TRY(ensure(c->gbar, sizeof(double) * (size_t)sum_ns * nq));
-    TRY(ensure(c->pmat, sizeof(double) * (size_t)sum_ns * 3 * (ncol > 0 ? ncol : 1)));
-    TRY(ensure(c->qmat, sizeof(double) * (size_t)sum_ns * 3 * (ncol > 0 ? ncol : 1)));
-    TRY(ensure(c->x0buf, sizeof(double) * (size_t)sum_ns * 9));
-    TRY(ensure(c->pcoef, sizeof(double) * (size_t)sum_t));
-    TRY(ensure(c->rbar, sizeof(double) * (size_t)sum_ns));
     TRY(ensure(c->alphaK_bar, sizeof(double) * (size_t)sum_n1 * nq));
     TRY(ensure(c->alphaI_bar, sizeof(double) * (size_t)N * nq));
     TRY(ensure(c->gacc, sizeof(double) * 3 * (size_t)N));
-    w.gbar = (double*)c->gbar.p;
-    w.pmat = (double*)c->pmat.p;
-    w.qmat = (double*)c->qmat.p;
-    w.x0buf = (double*)c->x0buf.p;
-    w.pcoef = (double*)c->pcoef.p;
-    w.rbar = (double*)c->rbar.p;
     w.alphaK_bar = (double*)c->alphaK_bar.p;
     w.alphaI_bar = (double*)c->alphaI_bar.p;
     w.gacc = (double*)c->gacc.p;
-    TRY(ensure(c->sgq, sizeof(double) * 3 * (size_t)nq * N * c->site_cap));
-    TRY(ensure(c->gstage, sizeof(double) * 3 * (size_t)nq * (sum_pairs + 1)));
-    w.sgq = (double*)c->sgq.p;
-    w.gstage = (double*)c->gstage.p;
-    if (sliced && ncol > 0) {
-      TRY(ensure(c->pdig, sizeof(unsigned short) * (size_t)sum_sp * 3 * Kp_pair * DIG_P));
-      TRY(ensure(c->qdig, sizeof(unsigned short) * (size_t)sum_sp * 3 * Kp_pair * DIG_P));
-      TRY(ensure(c->pexp, sizeof(int) * (size_t)sum_sp * 3));
-      TRY(ensure(c->qexp, sizeof(int) * (size_t)sum_sp * 3));
-      w.pdig = (unsigned short*)c->pdig.p;
-      w.qdig = (unsigned short*)c->qdig.p;
-      w.pexp = (int*)c->pexp.p;
-      w.qexp = (int*)c->qexp.p;
-    }
+    if (!is_device_ptr(f_out)) TRY(ensure(c->out_f_d, sizeof(double) * 3 * N));
   }
+  TRY(ensure(c->order1_d, sizeof(int) * N));
+  TRY(ensure(c->order3_d, sizeof(int) * N));
 
-  // ---- stage 1 and 2 ------------------------------------------------------------------------
-  const bool per_atom = c->launch_mode == LMBD_LAUNCH_PER_ATOM;
-  const int step = per_atom ? 1 : N;
-  mark(LMBD_PHASE_SCS);
-  launch_scs_fill(w, dp, max_n12, max_n1, s);
-  ++phase_launch[LMBD_PHASE_SCS];
-  if (per_atom) {
-    for (int c0 = 0; c0 < N; ++c0) {
-      launch_scs_factor(w, dp, nullptr, c0, c0 + 1, c->counts_h[c0].n1, c->counts_h[c0].n12, s);
-      ++phase_launch[LMBD_PHASE_SCS];
-    }
-  } else {
-    for (const Bucket& b : buckets) {
-      launch_scs_factor(w, dp, order_dev, b.b0, b.b1, b.n1, b.n12, s);
-      ++phase_launch[LMBD_PHASE_SCS];
+  // ---- waves under the memory budget --------------------------------------------------------
+  const Layout L{nq, ncv, nvec, ncol, (ncol + 15) / 16 * 16, ST, DIG_P, c->site_cap, forces, sliced_chain,
+                 sliced && ncol > 0};
+  auto s1 = [&](int a, int b) { return L.stage1(o, a, b, nullptr, nullptr); };
+  auto s1x = [&](int a, int b) { return forces ? L.scs_adjoint(o, a, b, nullptr, nullptr) : (size_t)0; };
+  auto s2 = [&](int a, int b) { return L.stage2(o, a, b, nullptr, nullptr, nullptr); };
+  auto s1_and_x = [&](int a, int b) { return s1(a, b) + s1x(a, b); };
+  size_t avail;
+  {
+    const size_t whole = c->whole_bytes();
+    if (c->mem_budget) {
+      avail = c->mem_budget > whole ? c->mem_budget - whole : 0;
+    } else {
+      size_t fr = 0, tot = 0;
+      CK(cudaMemGetInfo(&fr, &tot));
+      const size_t reserve = (size_t)1 << 30;
+      avail = fr + c->arena.bytes;
+      avail = avail > reserve ? avail - reserve : 0;
     }
   }
-  if (per_atom) {
-    for (int c0 = 0; c0 < N; ++c0) {
-      launch_mbd_prepare_sized(w, dp, c0, c0 + 1, max_ns, s);
-      if (sliced_chain) launch_slice_t(w, c0, c0 + 1, ST, s);
-      for (int m = 1; m < nvec; ++m) {
-        if (sliced_chain)
-          launch_chain_oz2(w, dp, m, c0, c0 + 1, max_ns, m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A, ST, s);
-        else
-          launch_mbd_chain_sized(w, dp, m, c0, c0 + 1, max_ns, s);
+  // cutA: waves of the forward SCS; cutC: waves of the SCS adjoint; cut2: waves of stage 2.
+  // persist: the stage-1 arrays of all centres stay resident from the forward SCS to its
+  // adjoint; otherwise stage 1 of each adjoint wave is computed again before its adjoint.
+  std::vector<int> cutA, cutC, cut2;
+  bool persist = true;
+  size_t R1 = 0, arena_need = 0;
+  {
+    const size_t S1all = s1(0, N), S2all = s2(0, N), X1all = s1x(0, N);
+    auto maxw = [](const std::vector<int>& cuts, auto f) {
+      size_t m = 0;
+      for (size_t i = 0; i + 1 < cuts.size(); ++i) m = std::max(m, (size_t)f(cuts[i], cuts[i + 1]));
+      return m;
+    };
+    if (S1all + std::max(S2all, X1all) <= avail) {
+      cutA = cutC = cut2 = {0, N};
+      R1 = S1all;
+      arena_need = S1all + std::max(S2all, X1all);
+    } else if (!forces) {
+      persist = false;
+      if (!partition(N, avail, s1, cutA) || !partition(N, avail, s2, cut2)) return LMBD_ENOMEM;
+      cutC = cutA;
+      arena_need = std::max(maxw(cutA, s1), maxw(cut2, s2));
+    } else if (S1all <= avail / 2) {
+      cutA = {0, N};
+      R1 = S1all;
+      if (!partition(N, avail - R1, s2, cut2) || !partition(N, avail - R1, s1x, cutC)) return LMBD_ENOMEM;
+      arena_need = R1 + std::max(maxw(cut2, s2), maxw(cutC, s1x));
+    } else {
+      persist = false;
+      if (!partition(N, avail, s1_and_x, cutA) || !partition(N, avail, s2, cut2)) return LMBD_ENOMEM;
+      cutC = cutA;
+      arena_need = std::max(maxw(cutA, s1_and_x), maxw(cut2, s2));
+    }
+    if (c->arena.bytes < arena_need || (c->mem_budget && c->arena.bytes > avail)) {
+      release(c->arena);
+      size_t want = std::min(arena_need + arena_need / 8, std::max(avail, arena_need));
+      if (cudaMalloc(&c->arena.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        c->arena.p = nullptr;
+        return LMBD_ENOMEM;
       }
-      launch_mbd_energy(w, dp, c0, c0 + 1, s);
+      c->arena.bytes = want;
     }
-    phase_launch[LMBD_PHASE_PREPARE] = N;
-    phase_launch[LMBD_PHASE_CHAIN] = N * (nvec - 1);
-    phase_launch[LMBD_PHASE_ENERGY] = N;
-  } else {
-    mark(LMBD_PHASE_PREPARE);
-    launch_mbd_prepare_sized(w, dp, 0, N, max_ns, s);
-    if (sliced_chain) launch_slice_t(w, 0, N, ST, s);
-    mark(LMBD_PHASE_CHAIN);
-    for (int m = 1; m < nvec; ++m) {
-      if (sliced_chain)
-        launch_chain_oz2(w, dp, m, 0, N, max_ns, m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A, ST, s);
-      else
-        launch_mbd_chain_sized(w, dp, m, 0, N, max_ns, s);
-    }
-    mark(LMBD_PHASE_ENERGY);
-    launch_mbd_energy(w, dp, 0, N, s);
-    phase_launch[LMBD_PHASE_PREPARE] = 1;
-    phase_launch[LMBD_PHASE_CHAIN] = nvec - 1;
-    phase_launch[LMBD_PHASE_ENERGY] = 1;
   }
-  CK(cudaGetLastError());
+  char* const arena = (char*)c->arena.p;
+  std::vector<std::vector<Bucket>> bucketsA, bucketsC;
+  make_buckets(c->counts_h, cutA, c->order1_h, bucketsA);
+  CK(cudaMemcpyAsync(c->order1_d.p, c->order1_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  const int* orderA = (const int*)c->order1_d.p;
+  const int* orderC = orderA;
+  if (forces && cutC != cutA) {
+    make_buckets(c->counts_h, cutC, c->order3_h, bucketsC);
+    CK(cudaMemcpyAsync(c->order3_d.p, c->order3_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    orderC = (const int*)c->order3_d.p;
+  } else {
+    bucketsC = bucketsA;
+  }
+  const int nwA = (int)cutA.size() - 1, nw2 = (int)cut2.size() - 1, nwC = (int)cutC.size() - 1;
+  const bool one_wave = nwA == 1 && nw2 == 1 && nwC == 1;
+  const bool per_atom = c->launch_mode == LMBD_LAUNCH_PER_ATOM;
+
+  // stage-1 forward of one wave: pair lists, FP32 factorisation, refined solutions, alpha_K
+  auto stage1_forward = [&](int wv, const std::vector<int>& cuts, const std::vector<std::vector<Bucket>>& bk,
+                            const int* order) -> int {
+    const int c0 = cuts[wv], c1 = cuts[wv + 1];
+    L.stage1(o, c0, c1, arena, &w);
+    launch_scs_fill(w, dp, c0, c1, max_n12, max_n1, s);
+    ++phase_launch[LMBD_PHASE_SCS];
+    if (per_atom) {
+      for (int cc = c0; cc < c1; ++cc)
+        launch_scs_factor(w, dp, nullptr, cc, cc + 1, c->counts_h[cc].n1, c->counts_h[cc].n12, s);
+      phase_launch[LMBD_PHASE_SCS] += c1 - c0;
+    } else {
+      for (const Bucket& b : bk[wv]) launch_scs_factor(w, dp, order, b.b0, b.b1, b.n1, b.n12, s);
+      phase_launch[LMBD_PHASE_SCS] += (int)bk[wv].size();
+    }
+    CK(cudaGetLastError());
+    return LMBD_OK;
+  };
+
+  // ---- pass A: stage 1 (SCS) of all centres --------------------------------------------------
+  prof = prof_req && one_wave;
+  mark(LMBD_PHASE_SCS);
+  for (int wv = 0; wv < nwA; ++wv) TRY(stage1_forward(wv, cutA, bucketsA, orderA));
+
+  // ---- pass B: stage 2 (MBD energy) and its adjoint, per wave --------------------------------
   if (forces) {
     CK(cudaMemsetAsync(w.gacc, 0, sizeof(double) * 3 * N, s));
     CK(cudaMemsetAsync(w.alphaI_bar, 0, sizeof(double) * N * nq, s));
-    CK(cudaMemsetAsync(w.rbar, 0, sizeof(double) * sum_ns, s));
+  }
+  char* const base2 = arena + (persist ? R1 : 0);
+  for (int wv = 0; wv < nw2; ++wv) {
+    const int c0 = cut2[wv], c1 = cut2[wv + 1];
+    unsigned short* wdig_raw = nullptr;
+    L.stage2(o, c0, c1, base2, &w, &wdig_raw);
+    // W digit planes at the wave's start for the digit count of each chain step
+    auto chain_work = [&](int digits) {
+      Work wm = w;
+      if (wdig_raw)
+        wm.wdig = reinterpret_cast<unsigned short*>(reinterpret_cast<uintptr_t>(wdig_raw) -
+                                                    (uintptr_t)(o.at(O_KP, c0) * 48 * digits) * sizeof(unsigned short));
+      return wm;
+    };
     if (per_atom) {
-      int dummy = 0;
-      for (int c0 = 0; c0 < N; ++c0) {
-        launch_mbd_adj_series(w, dp, c0, c0 + 1, s);
-        if (sliced && ncol > 0)
-          launch_mbd_adj_pair_oz2(w, dp, c0, c0 + 1, max_ns, DIG_P, s);
+      for (int cc = c0; cc < c1; ++cc) {
+        launch_mbd_prepare_sized(w, dp, cc, cc + 1, max_ns, s);
+        if (sliced_chain) launch_slice_t(w, cc, cc + 1, ST, s);
+        for (int m = 1; m < nvec; ++m) {
+          const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
+          if (sliced_chain)
+            launch_chain_oz2(chain_work(dg), dp, m, cc, cc + 1, max_ns, dg, ST, s);
+          else
+            launch_mbd_chain_sized(w, dp, m, cc, cc + 1, max_ns, s);
+        }
+        launch_mbd_energy(w, dp, cc, cc + 1, s);
+      }
+      phase_launch[LMBD_PHASE_PREPARE] += c1 - c0;
+      phase_launch[LMBD_PHASE_CHAIN] += (c1 - c0) * (nvec - 1);
+      phase_launch[LMBD_PHASE_ENERGY] += c1 - c0;
+    } else {
+      mark(LMBD_PHASE_PREPARE);
+      launch_mbd_prepare_sized(w, dp, c0, c1, max_ns, s);
+      if (sliced_chain) launch_slice_t(w, c0, c1, ST, s);
+      mark(LMBD_PHASE_CHAIN);
+      for (int m = 1; m < nvec; ++m) {
+        const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
+        if (sliced_chain)
+          launch_chain_oz2(chain_work(dg), dp, m, c0, c1, max_ns, dg, ST, s);
         else
-          launch_mbd_adj_pair(w, dp, c0, c0 + 1, max_ns, s);
-        launch_mbd_adj_blend(w, dp, c0, c0 + 1, s);
+          launch_mbd_chain_sized(w, dp, m, c0, c1, max_ns, s);
       }
-      (void)dummy;
-      for (int c0 = 0; c0 < N; ++c0) {
-        launch_scs_adjoint2(w, dp, nullptr, c0, c0 + 1, c->counts_h[c0].n1, c->counts_h[c0].n12, s);
-        launch_scs_site_reduce(w, dp, c0, c0 + 1, s);
+      mark(LMBD_PHASE_ENERGY);
+      launch_mbd_energy(w, dp, c0, c1, s);
+      phase_launch[LMBD_PHASE_PREPARE] += 1;
+      phase_launch[LMBD_PHASE_CHAIN] += nvec - 1;
+      phase_launch[LMBD_PHASE_ENERGY] += 1;
+    }
+    CK(cudaGetLastError());
+    if (!forces) continue;
+    CK(cudaMemsetAsync(w.rbar + o.at(O_S, c0), 0, sizeof(double) * o.span(O_S, c0, c1), s));
+    if (per_atom) {
+      for (int cc = c0; cc < c1; ++cc) {
+        launch_mbd_adj_series(w, dp, cc, cc + 1, s);
+        if (sliced && ncol > 0)
+          launch_mbd_adj_pair_oz2(w, dp, cc, cc + 1, max_ns, DIG_P, s);
+        else
+          launch_mbd_adj_pair(w, dp, cc, cc + 1, max_ns, s);
+        launch_mbd_adj_blend(w, dp, cc, cc + 1, s);
       }
-      phase_launch[LMBD_PHASE_ADJ_SERIES] = phase_launch[LMBD_PHASE_ADJ_PAIR] = N;
-      phase_launch[LMBD_PHASE_ADJ_BLEND] = N;
-      phase_launch[LMBD_PHASE_ADJ_SCS] = 2 * N;
+      phase_launch[LMBD_PHASE_ADJ_SERIES] += c1 - c0;
+      phase_launch[LMBD_PHASE_ADJ_PAIR] += c1 - c0;
+      phase_launch[LMBD_PHASE_ADJ_BLEND] += c1 - c0;
     } else {
       mark(LMBD_PHASE_ADJ_SERIES);
-      launch_mbd_adj_series(w, dp, 0, N, s);
+      launch_mbd_adj_series(w, dp, c0, c1, s);
       mark(LMBD_PHASE_ADJ_PAIR);
       if (sliced && ncol > 0)
-        launch_mbd_adj_pair_oz2(w, dp, 0, N, max_ns, DIG_P, s);
+        launch_mbd_adj_pair_oz2(w, dp, c0, c1, max_ns, DIG_P, s);
       else
-        launch_mbd_adj_pair(w, dp, 0, N, max_ns, s);
+        launch_mbd_adj_pair(w, dp, c0, c1, max_ns, s);
       mark(LMBD_PHASE_ADJ_BLEND);
-      launch_mbd_adj_blend(w, dp, 0, N, s);
-      mark(LMBD_PHASE_ADJ_SCS);
-      for (const Bucket& b : buckets) launch_scs_adjoint2(w, dp, order_dev, b.b0, b.b1, b.n1, b.n12, s);
-      launch_scs_site_reduce(w, dp, 0, N, s);
-      phase_launch[LMBD_PHASE_ADJ_SERIES] = phase_launch[LMBD_PHASE_ADJ_PAIR] = 1;
-      phase_launch[LMBD_PHASE_ADJ_BLEND] = 1;
-      phase_launch[LMBD_PHASE_ADJ_SCS] = (int)buckets.size() + 1;
+      launch_mbd_adj_blend(w, dp, c0, c1, s);
+      phase_launch[LMBD_PHASE_ADJ_SERIES] += 1;
+      phase_launch[LMBD_PHASE_ADJ_PAIR] += 1;
+      phase_launch[LMBD_PHASE_ADJ_BLEND] += 1;
     }
     CK(cudaGetLastError());
   }
+
+  // ---- pass C: SCS adjoint (needs dL/d alpha_I of every centre, complete after pass B) --------
+  if (forces) {
+    mark(LMBD_PHASE_ADJ_SCS);
+    for (int wv = 0; wv < nwC; ++wv) {
+      const int c0 = cutC[wv], c1 = cutC[wv + 1];
+      size_t x_at = R1;
+      if (!persist) {
+        TRY(stage1_forward(wv, cutC, bucketsC, orderC));
+        x_at = s1(c0, c1);
+      }
+      L.scs_adjoint(o, c0, c1, arena + x_at, &w);
+      if (per_atom) {
+        for (int cc = c0; cc < c1; ++cc) {
+          launch_scs_adjoint2(w, dp, nullptr, cc, cc + 1, c->counts_h[cc].n1, c->counts_h[cc].n12, s);
+          launch_scs_site_reduce(w, dp, cc, cc + 1, s);
+        }
+        phase_launch[LMBD_PHASE_ADJ_SCS] += 2 * (c1 - c0);
+      } else {
+        for (const Bucket& b : bucketsC[wv]) launch_scs_adjoint2(w, dp, orderC, b.b0, b.b1, b.n1, b.n12, s);
+        launch_scs_site_reduce(w, dp, c0, c1, s);
+        phase_launch[LMBD_PHASE_ADJ_SCS] += (int)bucketsC[wv].size() + 1;
+      }
+      CK(cudaGetLastError());
+    }
+  }
+  c->stats.waves_scs = nwA;
+  c->stats.waves_mbd = nw2;
+  c->stats.scs_recomputed = (forces && !persist) ? 1 : 0;
+  c->stats.bytes_arena = (double)c->arena.bytes;
 
   // ---- outputs ----------------------------------------------------------------------------------
   mark(LMBD_PHASE_OUTPUT);
@@ -638,12 +871,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     S.max_sphere = max_ns;
     S.max_sites = c->site_cap;
     S.kernel_launches = launches;
-    double bytes = 0.0;
-    const DevBuf* all[] = {&c->lfac, &c->pr_geo, &c->pr_rad, &c->tdig, &c->wdig, &c->pdig, &c->qdig, &c->xsol, &c->alphaK, &c->alphaT, &c->dsq, &c->tlr, &c->vkr, &c->gbar,
-                           &c->pmat, &c->qmat, &c->x0buf, &c->rbar, &c->alphaK_bar, &c->alphaI_bar,
-                           &c->site_atom, &c->site_x};
-    for (const DevBuf* b : all) bytes += b->bytes;
-    S.bytes_workspace = bytes;
+    S.bytes_workspace = (double)(c->whole_bytes() + c->arena.bytes);
   }
   if (*c->status_h & (LMBD_FLAG_NOT_SPD | LMBD_FLAG_NOT_CONVERGED)) return LMBD_NOT_SPD;
   return LMBD_OK;
@@ -751,6 +979,12 @@ int lmbd_set_precision(lmbd_ctx* ctx, int mode) {
   return LMBD_OK;
 }
 
+int lmbd_set_memory_budget(lmbd_ctx* ctx, size_t bytes) {
+  if (!ctx) return LMBD_EINVAL;
+  ctx->c.mem_budget = bytes;
+  return LMBD_OK;
+}
+
 int lmbd_set_launch_mode(lmbd_ctx* ctx, int mode) {
   if (!ctx || (mode != LMBD_LAUNCH_BATCHED && mode != LMBD_LAUNCH_PER_ATOM)) return LMBD_EINVAL;
   ctx->c.launch_mode = mode;
@@ -805,16 +1039,8 @@ int lmbd_get_stats(const lmbd_ctx* ctx, lmbd_stats* out) {
 int lmbd_destroy(lmbd_ctx* ctx) {
   if (!ctx) return LMBD_OK;
   Ctx& c = ctx->c;
-  DevBuf* all[] = {&c.table_d, &c.pos_d, &c.species_d, &c.nu_d, &c.weights_d, &c.out_e_d, &c.out_f_d,
-                   &c.abar, &c.sig, &c.rvdw, &c.a0, &c.r0, &c.wpos, &c.cell_of, &c.cell_count,
-                   &c.cell_start, &c.cell_atoms, &c.grid, &c.site_atom, &c.site_x, &c.counts, &c.off_k1,
-                   &c.off_s, &c.off_b, &c.off_t, &c.totals, &c.status, &c.xsol, &c.alphaK, &c.pcount,
-                   &c.off_p, &c.off_a, &c.pr_ij, &c.pr_geo, &c.pr_rad, &c.prow, &c.prow_k2, &c.arow, &c.adj,
-                   &c.lfac, &c.off_tq, &c.off_tr, &c.off_kp, &c.off_sp, &c.tdig, &c.texp, &c.wdig, &c.wexp,
-                   &c.pdig, &c.qdig, &c.pexp, &c.qexp, &c.k2ptr, &c.k2rev, &c.sgq, &c.gstage, &c.order_d, &c.pcoef,
-                   &c.alphaI, &c.alphaT, &c.dsq, &c.tlr, &c.vkr, &c.energies, &c.trbuf, &c.gbar, &c.pmat,
-                   &c.qmat, &c.x0buf, &c.rbar, &c.alphaK_bar, &c.alphaI_bar, &c.gacc};
-  for (DevBuf* b : all) release(*b);
+  for (int i = 0; i < c.n_whole; ++i) release(*c.whole_bufs[i]);
+  release(c.arena);
   for (int i = 0; i <= LMBD_NPHASE; ++i)
     if (c.ev[i]) cudaEventDestroy(c.ev[i]);
   if (c.totals_h) cudaFreeHost(c.totals_h);

@@ -211,7 +211,7 @@ void launch_free_atom(const Work& w, const DevParams& p, cudaStream_t s);
 void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStream_t s, int* launches);
 void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s);
 void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s);
-void launch_scs_fill(const Work& w, const DevParams& p, int max_n12, int max_n1, cudaStream_t s);
+void launch_scs_fill(const Work& w, const DevParams& p, int c0, int c1, int max_n12, int max_n1, cudaStream_t s);
 void launch_scs_factor(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1, int max_n12,
                        cudaStream_t s);
 void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1,

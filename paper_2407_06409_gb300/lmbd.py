@@ -39,7 +39,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("flops", ctypes.c_double * NPHASE), ("ms", ctypes.c_double * NPHASE),
                 ("launches", ctypes.c_int * NPHASE), ("bytes_workspace", ctypes.c_double),
                 ("n_sites", ctypes.c_longlong), ("max_k1", ctypes.c_int), ("max_sphere", ctypes.c_int),
-                ("max_sites", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+                ("max_sites", ctypes.c_int), ("kernel_launches", ctypes.c_int), ("bytes_arena", ctypes.c_double),
+                ("waves_scs", ctypes.c_int), ("waves_mbd", ctypes.c_int), ("scs_recomputed", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -76,13 +77,15 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_launch_mode.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_profiling.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_precision.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_memory_budget.argtypes = [_P, ctypes.c_size_t]
         L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
         L.lmbd_get_site_counts.argtypes = [_P, _P, _P]
         L.lmbd_get_quadrature.argtypes = [_P, _D, _D]
         L.lmbd_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
-                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
+                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget",
+                  "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
@@ -158,6 +161,10 @@ class LMBD:
 
     def set_precision(self, mode: int) -> None:
         _check(lib().lmbd_set_precision(self._h, int(mode)), "lmbd_set_precision")
+
+    def set_memory_budget(self, nbytes: int) -> None:
+        """Device bytes this context may hold (0 = free memory less 1 GiB); larger inputs run in waves."""
+        _check(lib().lmbd_set_memory_budget(self._h, int(nbytes)), "lmbd_set_memory_budget")
 
     def set_profiling(self, on: bool) -> None:
         _check(lib().lmbd_set_profiling(self._h, 1 if on else 0), "lmbd_set_profiling")

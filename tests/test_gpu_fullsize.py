@@ -144,3 +144,21 @@ def test_box512_weighted_forces_match_oracle(lm, box512):
     rel = np.abs(e.cpu().numpy()[centres] - e_ref) / np.abs(e_ref)
     assert np.all(rel < E_RTOL)
     assert np.abs(f.cpu().numpy() - f_ref).max() < F_ATOL
+
+
+def test_box4096_waves_under_budget_match_single_wave(lm, box4096):
+    s = box4096
+    p = lm.default_params()
+    model = lm.LMBD(s.table, p, 12, 6)
+    e0, f0 = model.energy_forces(*_dev(s))
+    st = model.stats()
+    whole = st["bytes_workspace"] - st["bytes_arena"]
+    for frac, recompute in ((0.5, 0), (0.12, 1)):
+        mb = lm.LMBD(s.table, p, 12, 6)
+        mb.set_memory_budget(int(whole + frac * st["bytes_arena"]))
+        e, f = mb.energy_forces(*_dev(s))
+        sb = mb.stats()
+        assert sb["waves_mbd"] > 1 and sb["scs_recomputed"] == recompute
+        assert sb["bytes_workspace"] <= whole + frac * st["bytes_arena"]
+        assert torch.equal(e, e0)
+        assert (f - f0).abs().max().item() < 1e-12
