@@ -41,6 +41,16 @@ def parse():
     ap.add_argument("--per-atom-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--sweep", default=None,
+                    help="comma-separated atom counts: atoms/s and HBM footprint per size (one JSON line each)")
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="device memory budget of the context for --sweep (0 = free memory less 1 GiB)")
+    ap.add_argument("--serve", action="store_true", help="serving run: Poisson arrivals, continuous batching")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--hbm-gb", type=float, default=150.0)
+    ap.add_argument("--max-atoms", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -292,11 +302,134 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------------------------------
+# linear-scaling sweep: atoms/s and device footprint against N
+# ----------------------------------------------------------------------------------------
+def run_sweep(args):
+    import torch
+    from paper_2407_06409_gb300 import build, lmbd
+
+    if not os.path.exists(lmbd.LIB_PATH):
+        build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    for n in [int(x) for x in args.sweep.split(",") if x]:
+        s = structure(n, args.seed)
+        model = lmbd.LMBD(s.table, lmbd.default_params(), 12, 6)
+        if args.budget_gb > 0:
+            model.set_memory_budget(int(args.budget_gb * 1e9))
+        pos = torch.tensor(s.positions, device=dev)
+        cell = torch.tensor(s.cell, device=dev)
+        sp = torch.tensor(s.species, dtype=torch.int32, device=dev)
+        nu = torch.tensor(s.hirshfeld, device=dev)
+        torch.cuda.synchronize(dev)
+        free0, total = torch.cuda.mem_get_info(dev)
+        model.energy_forces(pos, cell, sp, nu, forces=True)
+        torch.cuda.synchronize(dev)
+        free1, _ = torch.cuda.mem_get_info(dev)
+        steps = max(1, args.steps)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            model.energy_forces(pos, cell, sp, nu, forces=True)
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / steps
+        st = model.stats()
+        line = {"mode": "sweep", "atoms": n, "atoms_per_s": n / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
+                "warmup": 1, "device_bytes": st["bytes_workspace"], "arena_bytes": st["bytes_arena"],
+                "device_used_delta": int(free0 - free1), "bytes_per_atom": st["bytes_workspace"] / n,
+                "waves_scs": st["waves_scs"], "waves_mbd": st["waves_mbd"],
+                "scs_recomputed": st["scs_recomputed"], "budget_gb": args.budget_gb or None,
+                "device_total": int(total), "sites_per_atom": st["n_sites"] / n}
+        print(json.dumps(line), flush=True)
+        model.close()
+        del pos, cell, sp, nu
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# serving: Poisson arrivals, continuous batching over several contexts
+# ----------------------------------------------------------------------------------------
+class MemSampler:
+    """Device memory in use (cudaMemGetInfo) sampled from a host thread."""
+
+    def __init__(self, dev, period=0.1):
+        import threading
+        self.dev, self.period = dev, period
+        self.peak = 0
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        import torch
+        while not self._stop.is_set():
+            free, total = torch.cuda.mem_get_info(self.dev)
+            self.peak = max(self.peak, total - free)
+            self._stop.wait(self.period)
+
+    def start(self):
+        self._t.start()
+
+    def stop(self):
+        self._stop.set()
+        self._t.join()
+        return self.peak
+
+
+def run_serve(args):
+    import torch
+    from paper_2407_06409_gb300 import build, inputs, lmbd, serve
+
+    if not os.path.exists(lmbd.LIB_PATH):
+        build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t_gen = time.perf_counter()
+    table, items = inputs.serving_workload(args.requests, rate=args.rate, lo=50, hi=args.max_atoms,
+                                           seed=args.seed)
+    t_gen = time.perf_counter() - t_gen
+    engines = [serve.LmbdEngine(table) for _ in range(args.slots)]
+    warm = inputs.box(200, seed=12345, table=table)
+    for e in engines:
+        e.run(warm, 50e9)
+        e.release()
+    torch.cuda.synchronize(dev)
+    free0, total = torch.cuda.mem_get_info(dev)
+    srv = serve.Server(engines, hbm_bytes=args.hbm_gb * 1e9)
+    mem = MemSampler(dev)
+    clocks = ClockSampler(0)
+    mem.start()
+    clocks.start()
+    res = srv.serve(items, realtime=True)
+    clk = clocks.stop()
+    peak_used = mem.stop()
+    summ = serve.summarize(res)
+    sizes = [r.n_atoms for r in res]
+    line = {"mode": "serve", "metric": "lMBD serving (energies + forces): p50/p99 latency and atoms/s",
+            **summ, "rate_req_per_s": args.rate, "slots": args.slots, "hbm_cap_gb": args.hbm_gb,
+            "peak_reserved_gb": srv.peak_accounted / 1e9,
+            "peak_device_used_gb_above_idle": (peak_used - (total - free0)) / 1e9,
+            "idle_slot_releases": srv.releases, "md_frames": sum(1 for it in items if it.frame > 0),
+            "size_range": [int(min(sizes)), int(max(sizes))], "mean_atoms": float(sum(sizes) / len(sizes)),
+            "workload_gen_s": t_gen, "dtype": "f64", "data": "synthetic", "clocks": clk}
+    if summ["errors"]:
+        line["first_error"] = next(r.error for r in res if r.error)
+    print(json.dumps(line), flush=True)
+    for e in engines:
+        e.close()
+    return 0 if summ["errors"] == 0 else 1
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.sweep:
+        return run_sweep(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args, world, rank, local)
 
 

@@ -169,6 +169,14 @@ int lmbd_set_precision(lmbd_ctx* ctx, int mode);
  * central atom gives LMBD_ENOMEM.                                                          */
 int lmbd_set_memory_budget(lmbd_ctx* ctx, size_t bytes);
 
+/* Free every device workspace of the context except its species table (the next call
+ * allocates again); results of the last call are no longer available.  For a server that
+ * must return memory held by an idle context.                                          */
+int lmbd_release_workspace(lmbd_ctx* ctx);
+
+/* Device bytes the context holds now (*out, host). */
+int lmbd_held_bytes(const lmbd_ctx* ctx, size_t* out);
+
 /* Per-phase device timing with CUDA events (0 = off, the default; reported only when
  * every stage ran as a single wave). */
 int lmbd_set_profiling(lmbd_ctx* ctx, int on);

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0)
 void launch_mbd_prepare_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {
   if (c1 <= c0) return;
   size_t sm = sizeof(double) * 4 * (size_t)max_ns;
-  cudaFuncSetAttribute(k_mbd_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_mbd_prepare, sm);
   k_mbd_prepare<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_ns);
 }
 
@@ -863,11 +863,11 @@ void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, 
   const int tiles = (3 * max_ns + 63) / 64;
   if (digits == 6) {
     const size_t sm = 2 * sizeof(unsigned short) * (6 * 64 + 6 * 48) * OZ_LD;
-    cudaFuncSetAttribute(k_chain_oz2<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_chain_oz2<6>, sm);
     k_chain_oz2<6><<<(c1 - c0) * tiles, 384, sm, s>>>(w, p, m, c0, tiles, st);
   } else {
     const size_t sm = 2 * sizeof(unsigned short) * (5 * 64 + 5 * 48) * OZ_LD;
-    cudaFuncSetAttribute(k_chain_oz2<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_chain_oz2<5>, sm);
     k_chain_oz2<5><<<(c1 - c0) * tiles, 384, sm, s>>>(w, p, m, c0, tiles, st);
   }
 }
@@ -981,11 +981,11 @@ void launch_mbd_adj_pair_oz2(const Work& w, const DevParams& p, int c0, int c1, 
   const int tiles = nt * (nt + 1) / 2;
   if (digits == 6) {
     const size_t sm = 2 * 2 * sizeof(unsigned short) * 6 * 48 * OZ_LD;
-    cudaFuncSetAttribute(k_mbd_adj_pair_oz2<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_mbd_adj_pair_oz2<6>, sm);
     k_mbd_adj_pair_oz2<6><<<(c1 - c0) * tiles, 288, sm, s>>>(w, p, c0, tiles);
   } else {
     const size_t sm = 2 * 2 * sizeof(unsigned short) * 5 * 48 * OZ_LD;
-    cudaFuncSetAttribute(k_mbd_adj_pair_oz2<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_mbd_adj_pair_oz2<5>, sm);
     k_mbd_adj_pair_oz2<5><<<(c1 - c0) * tiles, 288, sm, s>>>(w, p, c0, tiles);
   }
 }

@@ -285,7 +285,7 @@ void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStre
   k_cell_scan<<<1, 1024, 0, s>>>(w, gdev);
   k_scatter<<<nb, 128, 0, s>>>(w);
   size_t sm = (size_t)w.site_cap * (8 + 24 + 4);
-  cudaFuncSetAttribute(k_sites, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_sites, sm);
   k_sites<<<w.n_atoms, 256, sm, s>>>(w, p, gdev, 0);
   *launches += 4;
 }

@@ -378,6 +378,6 @@ __global__ void __launch_bounds__(256) k_scs_central_noalloc(Work w, DevParams p
 void launch_scs_central_noalloc(const Work& w, const DevParams& p, double* bslots, long long slot_doubles,
                                 int nslots, int max_n12, int max_n1, cudaStream_t s) {
   size_t sm = scs_smem_bytes(max_n12, max_n1, false);
-  cudaFuncSetAttribute(k_scs_central_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_scs_central_noalloc, sm);
   k_scs_central_noalloc<<<nslots, 256, sm, s>>>(w, p, bslots, slot_doubles, max_n12, max_n1);
 }

@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(256) k_scs_site_reduce(Work w, DevParams p, in
 void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s) {
   if (w.n_atoms == 0) return;
   size_t sm = sizeof(double) * 3 * (size_t)max_n12;
-  cudaFuncSetAttribute(k_scs_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_scs_count, sm);
   k_scs_count<<<w.n_atoms, 256, sm, s>>>(w, p, max_n12);
 }
 
@@ -819,7 +819,7 @@ void launch_scs_fill(const Work& w, const DevParams& p, int c0, int c1, int max_
   if (c1 <= c0) return;
   size_t sm = sizeof(double) * 3 * (size_t)max_n12 +
               sizeof(int) * ((size_t)max_n1 * max_n1 + 6 * (size_t)max_n1 + 2 + (size_t)max_n12);
-  cudaFuncSetAttribute(k_scs_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_scs_fill, sm);
   k_scs_fill<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_n12, max_n1);
 }
 
@@ -832,7 +832,7 @@ void launch_scs_factor(const Work& w, const DevParams& p, const int* order, int 
                        cudaStream_t s) {
   if (c1 <= c0) return;
   size_t sm = scs2_smem_bytes(max_n1, max_n12, false);
-  cudaFuncSetAttribute(k_scs_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_scs_factor, sm);
   k_scs_factor<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
 }
 
@@ -840,7 +840,7 @@ void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, in
                          int max_n12, cudaStream_t s) {
   if (c1 <= c0) return;
   size_t sm = scs2_smem_bytes(max_n1, max_n12, true);
-  cudaFuncSetAttribute(k_scs_adjoint2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_scs_adjoint2, sm);
   k_scs_adjoint2<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
 }
 

@@ -13,10 +13,23 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/lmbd.h"
 #include "lmbd_internal.cuh"
+
+void raise_smem_limit(const void* func, size_t bytes) {
+  static std::mutex mtx;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mtx);
+  size_t& cur = limit[{dev, func}];
+  if (bytes > cur && cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    cur = bytes;
+}
 
 namespace {
 
@@ -819,6 +832,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   c->stats.bytes_arena = (double)c->arena.bytes;
 
   // ---- outputs ----------------------------------------------------------------------------------
+  CK(cudaGetLastError());   // before is_device_ptr, which clears the error state of a failed query
   mark(LMBD_PHASE_OUTPUT);
   if (e_out) {
     bool dev = is_device_ptr(e_out);
@@ -982,6 +996,22 @@ int lmbd_set_precision(lmbd_ctx* ctx, int mode) {
 int lmbd_set_memory_budget(lmbd_ctx* ctx, size_t bytes) {
   if (!ctx) return LMBD_EINVAL;
   ctx->c.mem_budget = bytes;
+  return LMBD_OK;
+}
+
+int lmbd_release_workspace(lmbd_ctx* ctx) {
+  if (!ctx) return LMBD_EINVAL;
+  Ctx& c = ctx->c;
+  for (int i = 0; i < c.n_whole; ++i)
+    if (c.whole_bufs[i] != &c.table_d) release(*c.whole_bufs[i]);
+  release(c.arena);
+  c.last_n = 0;
+  return LMBD_OK;
+}
+
+int lmbd_held_bytes(const lmbd_ctx* ctx, size_t* out) {
+  if (!ctx || !out) return LMBD_EINVAL;
+  *out = ctx->c.whole_bytes() + ctx->c.arena.bytes;
   return LMBD_OK;
 }
 

@@ -238,6 +238,11 @@ void launch_mbd_adj_pair_oz2(const Work& w, const DevParams& p, int c0, int c1, 
 void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
                             cudaStream_t s);
 
+// Raise the dynamic shared-memory limit of a kernel to at least `bytes` (never lowers it: the
+// limit is process-wide, and lowering it while another host thread launches the same kernel
+// with more shared memory would make that launch fail).
+void raise_smem_limit(const void* func, size_t bytes);
+
 // Allocation-free entry point (lmbd_central_polarizabilities_noalloc): scratch lookup and
 // the persistent SCS kernel variant, both in k_scs.cu next to the static scratch array.
 int noalloc_scratch(void** ptr, size_t* bytes);

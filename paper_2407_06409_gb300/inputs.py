@@ -100,6 +100,25 @@ def _rsa_box(n: int, box: float, min_sep: float, rng: np.random.Generator) -> np
     return pts
 
 
+def _resample_box(n: int, box: float, min_sep: float, rng: np.random.Generator) -> np.ndarray:
+    """Uniform points in a periodic cube; every point closer than min_sep (minimum image) to a
+    point of lower index is drawn again until no such pair is left.  Vectorised with a k-d
+    tree, for the large structures of the serving workload."""
+    from scipy.spatial import cKDTree
+    pts = rng.uniform(0.0, box, (n, 3))
+    pairs = cKDTree(pts, boxsize=box).query_pairs(min_sep, output_type="ndarray")
+    bad = np.unique(np.max(pairs, axis=1)) if len(pairs) else np.zeros(0, dtype=np.int64)
+    # the points outside `bad` have no close pair among themselves; redraw the others until
+    # each of them is clear of every point
+    for _ in range(1000):
+        if len(bad) == 0:
+            return pts
+        pts[bad] = rng.uniform(0.0, box, (len(bad), 3))
+        cnt = cKDTree(pts, boxsize=box).query_ball_point(pts[bad], min_sep, return_length=True)
+        bad = bad[cnt > 1]
+    raise RuntimeError("resampling did not remove every close pair")
+
+
 def cluster(n_atoms: int = 24, radius: float = 6.0, min_sep: float = 1.0,
             n_species: int = 3, seed: int = 0) -> Structure:
     rng = np.random.default_rng(seed)
@@ -111,11 +130,22 @@ def cluster(n_atoms: int = 24, radius: float = 6.0, min_sep: float = 1.0,
 
 
 def box(n_atoms: int, density: float = 0.1, min_sep: float = 1.1, n_species: int = 4,
-        seed: int = 0, jitter: float = 0.0) -> Structure:
+        seed: int = 0, jitter: float = 0.0, table: np.ndarray | None = None,
+        method: str = "rsa") -> Structure:
+    """Periodic cube at the given density.  method "rsa": random sequential addition;
+    "resample": draw all points, then redraw those in close pairs (same minimum separation,
+    much faster for large N).  table: species parameters to use instead of drawn ones."""
     rng = np.random.default_rng(seed)
-    table = species_table(n_species, rng)
+    drawn = species_table(n_species, rng)
+    if table is None:
+        table = drawn
     side = (n_atoms / density) ** (1.0 / 3.0)
-    pos = _rsa_box(n_atoms, side, min_sep, rng)
+    if method == "rsa":
+        pos = _rsa_box(n_atoms, side, min_sep, rng)
+    elif method == "resample":
+        pos = _resample_box(n_atoms, side, min_sep, rng)
+    else:
+        raise ValueError(method)
     species = rng.integers(0, n_species, n_atoms).astype(np.int32)
     nu = rng.uniform(0.6, 1.0, n_atoms)
     if jitter > 0.0:
@@ -136,3 +166,45 @@ def serving_sizes(n_requests: int, lo: int = 50, hi: int = 20000, seed: int = 0)
     """Log-uniform structure sizes for the serving workload."""
     rng = np.random.default_rng(seed)
     return np.exp(rng.uniform(math.log(lo), math.log(hi), n_requests)).astype(np.int64)
+
+
+@dataclass
+class ServeItem:
+    """One request of the serving workload."""
+    rid: int
+    arrival: float                 # seconds after the start
+    structure: Structure
+    trajectory: int                # id of the base structure; MD frames share their base's id
+    frame: int                     # 0 for a base structure, 1, 2, ... for its MD frames
+
+
+def serving_workload(n_requests: int = 2000, rate: float = 50.0, lo: int = 50, hi: int = 20000,
+                     md_fraction: float = 0.3, jitter: float = 0.02, seed: int = 0,
+                     density: float = 0.1) -> tuple[np.ndarray, list[ServeItem]]:
+    """Poisson arrivals at `rate` per second; a fraction `md_fraction` of the requests (never
+    the first) are MD frames (Gaussian jitter) of an earlier base structure chosen uniformly;
+    base structures are periodic boxes with log-uniform sizes in [lo, hi].  One species table
+    (4 species) is shared by every request, as one model serves them all."""
+    rng = np.random.default_rng(seed)
+    table = species_table(4, rng)
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    sizes = serving_sizes(n_requests, lo, hi, seed=seed + 1)
+    is_md = rng.uniform(size=n_requests) < md_fraction
+    is_md[0] = False
+    items: list[ServeItem] = []
+    bases: list[int] = []
+    frames: dict[int, int] = {}
+    for r in range(n_requests):
+        if is_md[r]:
+            b = bases[int(rng.integers(len(bases)))]
+            frames[b] += 1
+            s = md_frame(items[b].structure, jitter, seed=int(rng.integers(1 << 31)))
+            items.append(ServeItem(r, float(arrivals[r]), s, items[b].trajectory, frames[b]))
+        else:
+            s = box(int(sizes[r]), density=density, seed=int(rng.integers(1 << 31)), table=table,
+                    method="resample")
+            bases.append(r)
+            frames[r] = 0
+            items.append(ServeItem(r, float(arrivals[r]), s, r, 0))
+    return table, items

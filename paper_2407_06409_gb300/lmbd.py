@@ -78,6 +78,8 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_profiling.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_precision.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_memory_budget.argtypes = [_P, ctypes.c_size_t]
+        L.lmbd_release_workspace.argtypes = [_P]
+        L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
         L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
         L.lmbd_get_site_counts.argtypes = [_P, _P, _P]
         L.lmbd_get_quadrature.argtypes = [_P, _D, _D]
@@ -85,6 +87,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget",
+                  "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
             getattr(L, f).restype = ctypes.c_int
@@ -123,11 +126,13 @@ def _as_arg(x, dtype):
 
 
 def _stream_ptr(stream, device):
+    """The given stream; else the current stream of a CUDA device; else the legacy stream."""
     torch = _torch()
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream)
     if device.type != "cuda":
         return None
-    s = stream if stream is not None else torch.cuda.current_stream(device)
-    return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
 class LMBD:
@@ -165,6 +170,15 @@ class LMBD:
     def set_memory_budget(self, nbytes: int) -> None:
         """Device bytes this context may hold (0 = free memory less 1 GiB); larger inputs run in waves."""
         _check(lib().lmbd_set_memory_budget(self._h, int(nbytes)), "lmbd_set_memory_budget")
+
+    def release_workspace(self) -> None:
+        """Free the context's device workspaces (the next call allocates again)."""
+        _check(lib().lmbd_release_workspace(self._h), "lmbd_release_workspace")
+
+    def held_bytes(self) -> int:
+        out = ctypes.c_size_t(0)
+        _check(lib().lmbd_held_bytes(self._h, ctypes.byref(out)), "lmbd_held_bytes")
+        return int(out.value)
 
     def set_profiling(self, on: bool) -> None:
         _check(lib().lmbd_set_profiling(self._h, 1 if on else 0), "lmbd_set_profiling")
