@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--hbm-gb", type=float, default=150.0)
     ap.add_argument("--max-atoms", type=int, default=20000)
+    ap.add_argument("--large-slots", type=int, default=1,
+                    help="slots of the large-request lane (normal-priority streams); 0 = no lanes")
+    ap.add_argument("--large-atoms", type=int, default=2048)
     return ap.parse_args()
 
 
@@ -389,14 +392,15 @@ def run_serve(args):
     table, items = inputs.serving_workload(args.requests, rate=args.rate, lo=50, hi=args.max_atoms,
                                            seed=args.seed)
     t_gen = time.perf_counter() - t_gen
-    engines = [serve.LmbdEngine(table) for _ in range(args.slots)]
+    engines = serve.make_engines(table, args.slots, args.large_slots)
     warm = inputs.box(200, seed=12345, table=table)
     for e in engines:
         e.run(warm, 50e9)
         e.release()
     torch.cuda.synchronize(dev)
     free0, total = torch.cuda.mem_get_info(dev)
-    srv = serve.Server(engines, hbm_bytes=args.hbm_gb * 1e9)
+    srv = serve.Server(engines, hbm_bytes=args.hbm_gb * 1e9, large_atoms=args.large_atoms,
+                       large_slots=args.large_slots)
     mem = MemSampler(dev)
     clocks = ClockSampler(0)
     mem.start()
@@ -404,10 +408,11 @@ def run_serve(args):
     res = srv.serve(items, realtime=True)
     clk = clocks.stop()
     peak_used = mem.stop()
-    summ = serve.summarize(res)
+    summ = serve.summarize(res, large_atoms=args.large_atoms)
     sizes = [r.n_atoms for r in res]
     line = {"mode": "serve", "metric": "lMBD serving (energies + forces): p50/p99 latency and atoms/s",
             **summ, "rate_req_per_s": args.rate, "slots": args.slots, "hbm_cap_gb": args.hbm_gb,
+            "lanes": {"large_slots": srv.large_slots, "large_atoms": args.large_atoms},
             "peak_reserved_gb": srv.peak_accounted / 1e9,
             "peak_device_used_gb_above_idle": (peak_used - (total - free0)) / 1e9,
             "idle_slot_releases": srv.releases, "md_frames": sum(1 for it in items if it.frame > 0),

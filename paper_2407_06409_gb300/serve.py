@@ -73,13 +73,14 @@ class Result:
 
 
 class LmbdEngine:
-    """One library context on its own CUDA stream."""
+    """One library context on its own CUDA stream (lower number = higher priority)."""
 
-    def __init__(self, table, params=None, n_freq: int = 12, series_order: int = 6, forces: bool = True):
+    def __init__(self, table, params=None, n_freq: int = 12, series_order: int = 6, forces: bool = True,
+                 priority: int = 0):
         import torch
         from . import lmbd
         self.model = lmbd.LMBD(table, params, n_freq, series_order)
-        self.stream = torch.cuda.Stream()
+        self.stream = torch.cuda.Stream(priority=priority)
         self.forces = forces
 
     def run(self, structure, budget: float):
@@ -101,6 +102,13 @@ class LmbdEngine:
         self.model.close()
 
 
+def make_engines(table, n_slots: int, large_slots: int = 1, **kw) -> list:
+    """Engines for a Server: the first `large_slots` on normal-priority streams (the large-request
+    lane), the others on the highest-priority streams, so that the blocks of small requests are
+    scheduled ahead of those of a large request running beside them."""
+    return [LmbdEngine(table, priority=0 if i < large_slots else -8, **kw) for i in range(n_slots)]
+
+
 @dataclass
 class _Slot:
     index: int
@@ -120,10 +128,18 @@ _RELEASE = object()   # job: free the slot's device memory
 
 class Server:
     def __init__(self, engines: list, hbm_bytes: float = 150e9, footprint: Footprint | None = None,
-                 window: int = 16, clock=time.perf_counter):
+                 window: int = 16, clock=time.perf_counter, large_atoms: int = 2048, large_slots: int = 1):
+        """engines[:large_slots] form the lane for requests of at least `large_atoms` atoms (they
+        fill the GPU on their own, so running two at once only splits memory); the other slots
+        serve smaller requests, which may borrow an idle large-lane slot while no large request
+        waits.  large_slots = 0 (or >= the number of engines) disables lanes."""
         if not engines:
             raise ValueError("at least one engine")
         self.slots = [_Slot(i, e) for i, e in enumerate(engines)]
+        self.large_atoms = int(large_atoms)
+        self.lanes = 0 < large_slots < len(engines)
+        self.large_slots = int(large_slots) if self.lanes else 0
+        self._large_waiting = False
         self.hbm = float(hbm_bytes)
         self.fp = footprint if footprint is not None else Footprint()
         self.window = int(window)
@@ -138,11 +154,19 @@ class Server:
 
     def _pick_slot(self, item) -> _Slot | None:
         idle = [s for s in self.slots if not s.busy]
+        large = item.structure.n_atoms >= self.large_atoms
+        if self.lanes:
+            lane = [s for s in idle if (s.index < self.large_slots) == large]
+            if not lane and not large and not self._large_waiting:
+                lane = [s for s in idle if s.index < self.large_slots]
+            idle = lane
         if not idle:
             return None
         for s in idle:
             if s.trajectory == item.trajectory:
                 return s
+        if large:   # reuse the largest resident workspace
+            return max(idle, key=lambda s: s.held)
         fresh = [s for s in idle if s.trajectory is None]
         if fresh:
             return fresh[0]
@@ -158,12 +182,16 @@ class Server:
         return free - need, free
 
     def _admit(self, pending: list, t0: float) -> None:
+        self._large_waiting = any(it.structure.n_atoms >= self.large_atoms for it in pending[:self.window])
         i = 0
         while i < min(len(pending), self.window):
             item = pending[i]
             slot = self._pick_slot(item)
             if slot is None:
-                return
+                if not self.lanes:
+                    return
+                i += 1   # the other lane may still have a free slot
+                continue
             n = item.structure.n_atoms
             lo, hi = self.fp.minimum(n), self.fp.full(n)
             avail, free = self._avail(slot)
@@ -271,12 +299,24 @@ class Server:
         return [results[it.rid] for it in items]
 
 
-def summarize(results: list[Result]) -> dict:
+def _percentiles(results: list[Result]) -> dict:
+    if not results:
+        return {"requests": 0}
+    lat = np.array([r.latency for r in results])
+    return {"requests": len(results), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean())}
+
+
+def summarize(results: list[Result], large_atoms: int | None = None) -> dict:
     lat = np.array([r.latency for r in results])
     atoms = sum(r.n_atoms for r in results)
     span = max(r.done for r in results) - min(r.arrival for r in results)
     frames = [r for r in results if r.affinity]
-    return {
+    extra = {}
+    if large_atoms is not None:
+        extra = {f"below_{large_atoms}_atoms": _percentiles([r for r in results if r.n_atoms < large_atoms]),
+                 f"from_{large_atoms}_atoms": _percentiles([r for r in results if r.n_atoms >= large_atoms])}
+    return {**extra, 
         "requests": len(results),
         "errors": sum(r.error is not None for r in results),
         "atoms": int(atoms),

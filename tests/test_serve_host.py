@@ -66,12 +66,12 @@ class FakeEngine:
         self._held = 0.0
 
 
-def _server(n_slots, hbm, fail_on=None, window=16):
+def _server(n_slots, hbm, fail_on=None, window=16, **kw):
     fp = serve.Footprint(per_centre=1e6, per_atom_whole=1e3, fixed=1e6, min_wave=64)
     FakeEngine.running_bytes[0] = 0.0
     FakeEngine.peak_bytes[0] = 0.0
     return serve.Server([FakeEngine(fp, fail_on) for _ in range(n_slots)], hbm_bytes=hbm, footprint=fp,
-                        window=window)
+                        window=window, **kw)
 
 
 def test_all_served_and_memory_never_exceeds_cap():
@@ -161,3 +161,21 @@ def test_serving_workload_shape():
             assert 0 < np.abs(d).max() < 0.2
             assert np.array_equal(it.structure.species, base.structure.species)
     assert any(it.frame > 0 for it in items)
+
+
+def test_size_lanes():
+    # large requests (>= 500 atoms) use slot 0 only and never overlap; small ones run beside them
+    rng = np.random.default_rng(1)
+    sizes = [800, 20, 900, 30, 40, 700, 25, 35, 600, 15, 45, 50]
+    items = [_Item(i, 0.0, _S(n), i) for i, n in enumerate(sizes)]
+    srv = _server(3, hbm=5e9, large_atoms=500, large_slots=1)
+    res = srv.serve(items, realtime=False)
+    assert all(r.error is None for r in res)
+    large = sorted((r for r in res if r.n_atoms >= 500), key=lambda r: r.admitted)
+    assert all(r.slot == 0 for r in large)
+    for a, b in zip(large, large[1:]):
+        assert b.admitted >= a.done - 1e-6
+    small = [r for r in res if r.n_atoms < 500]
+    assert any(r.admitted < large[0].done for r in small)
+    s = serve.summarize(res, large_atoms=500)
+    assert s["below_500_atoms"]["requests"] == 8 and s["from_500_atoms"]["requests"] == 4
