@@ -22,7 +22,10 @@ the paper's order, one atom (one "central atom k") at a time:
 * the local energy as the truncated series Tr{g_k G^(n-2) g_k^T} with
   c_n = -1/n (Eq. mbd-local / Eq. E_k) or, in "log mode", the k-block of
   ln(1 - G) from a symmetric eigendecomposition (Eq. series-expansion);
-* the frequency integral by Gauss-Legendre quadrature mapped to [0, inf).
+* the frequency integral by Gauss-Legendre quadrature mapped to [0, inf);
+* optionally (omega_ref set) the Lorentzian frequency model of Sec. III.C: SCS solves at
+  omega = 0 and omega_ref only, alpha~(omega) at the nodes from Eqs. char-freq and
+  alpha_SCS_freq applied to the blended polarisabilities.
 
 Forces are -d(sum_k w_k E_k)/dR by PyTorch autograd (reverse mode), applied to
 the two phases separately so that memory stays bounded: first E_k with the
@@ -64,6 +67,11 @@ class Params:
     n_freq: int = 12
     series_order: int | None = 6   # None = log mode (the n_max -> infinity limit)
     omega_scale: float = 0.6       # L of the frequency mapping, Hartree
+    # None: SCS solved at omega = 0 and at every quadrature node.  A value (Hartree): the
+    # Lorentzian model of Sec. III.C -- SCS at omega = 0 and omega_ref only, then
+    # alpha~_i(omega) = alpha~_i(0) / (1 + (omega / omega~_i)^2) (Eq. alpha_SCS_freq) with
+    # omega~_i from the two solves (Eq. char-freq)
+    omega_ref: float | None = None
 
     @property
     def sphere(self) -> float:
@@ -91,6 +99,23 @@ def frequencies(p: Params) -> tuple[torch.Tensor, torch.Tensor]:
     omega = torch.tensor(np.concatenate([[0.0], om]), dtype=_DT)
     weight = torch.tensor(np.concatenate([[0.0], w]), dtype=_DT)
     return omega, weight
+
+
+def scs_frequencies(p: Params) -> torch.Tensor:
+    """Frequencies of the SCS solves: every column of `frequencies`, or 0 and omega_ref."""
+    if p.omega_ref is None:
+        return frequencies(p)[0]
+    return torch.tensor([0.0, p.omega_ref], dtype=_DT)
+
+
+def lorentzian(alpha0, alpha_ref, omega_ref, omega):
+    """Sec. III.C: omega~ = omega_ref / sqrt(alpha~(0)/alpha~(omega_ref) - 1) (Eq. char-freq),
+    alpha~(omega) = alpha~(0) / (1 + (omega/omega~)^2) (Eq. alpha_SCS_freq).
+
+    alpha0, alpha_ref: (n,); omega: (Q,).  Returns (n, Q).
+    """
+    omega_t = omega_ref / torch.sqrt(alpha0 / alpha_ref - 1.0)
+    return alpha0[:, None] / (1.0 + (omega[None, :] / omega_t[:, None]) ** 2)
 
 
 # ----------------------------------------------------------------------------------------
@@ -360,6 +385,7 @@ class System:
         self.table = np.asarray(table, dtype=np.float64)
         self.p = params
         self.omega, self.weight = frequencies(params)
+        self.omega_s = scs_frequencies(params)
         self._sites: dict[int, Sites] = {}
 
     @property
@@ -372,7 +398,8 @@ class System:
         return self._sites[k]
 
     def free(self):
-        return free_atom(self.species, self.nu, self.table, self.omega)
+        """Free-atom quantities at the SCS frequencies."""
+        return free_atom(self.species, self.nu, self.table, self.omega_s)
 
     def central_alpha(self, atoms, P=None) -> dict[int, torch.Tensor]:
         """alpha_I,a(omega) for the listed atoms: the centre block of each atom's own solve."""
@@ -397,6 +424,9 @@ class System:
         rb = torch.cat([torch.zeros(1, dtype=_DT), torch.sqrt((x[1:ns] * x[1:ns]).sum(-1))])
         at = blend(aK, aI, rb, self.p)
         T = t_lr(x[:ns], at[:, 0], a0[s.atom[:ns]], r0[s.atom[:ns]], self.p)
+        if self.p.omega_ref is not None:
+            # Lorentzian model: alpha~ at the quadrature nodes from its values at 0 and omega_ref
+            at = lorentzian(at[:, 0], at[:, 1], self.p.omega_ref, self.omega)
         return local_energy(T, at, self.weight, self.p) * HARTREE_EV
 
     def energies(self, centres=None) -> np.ndarray:

@@ -9,8 +9,8 @@
 // Design for GB300, whose FP64 pipe runs at 1/70 of FP32:
 //  * the pairs (i in K1, j in K1 u K2) with r_ij < r_SCS are listed once per central atom
 //    with their frequency-independent geometry and damping F, dF/dr (k_scs_count/k_scs_fill);
-//  * per (atom, frequency) only erf and exp of r/sigma_ij are evaluated (FP64), and the radial
-//    terms A0, B0, A0', B0' are kept for the adjoint;
+//  * erf and exp of r/sigma_ij are evaluated once per atom pair and frequency (k_pair_radial,
+//    FP64), not once per local system holding the pair; the local systems read the table;
 //  * B_K is factorised in FP32 (Cholesky, packed lower triangle in shared memory) and the
 //    FP64 solution is recovered by iterative refinement: the residual d - B X is formed in
 //    FP64 from the sparse pair list, corrections come from the FP32 factor (classical mixed-
@@ -18,6 +18,7 @@
 //  * the adjoint solve B lambda = dL/dX reuses the stored FP32 factor with the same refinement,
 //    and contracts dB/dr, dd/dr pair by pair from the stored radial terms.
 #include "lmbd_internal.cuh"
+#include "ff.cuh"
 
 // pair predicate shared by the counting and filling kernels (identical FP64 arithmetic)
 __device__ __forceinline__ bool scs_pair_in(const double* xs, int ld, int i, int j, double rc2, double& rx,
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
   int* adjcnt = rowstart + max_n1 + 1;             // max_n1
   int* adjstart = adjcnt + max_n1;                 // max_n1 + 1
   int* k2cnt = adjstart + max_n1 + 1;              // max_n12
+  int* klist = k2cnt + max_n12;                    // per warp max_n1: atoms of one K1 list
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
   const Counts cn = w.counts[c];
@@ -124,8 +126,16 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
   }
   __syncthreads();
   // phase 2: write pairs in order with their geometry and damping
+  int* lst = klist + warp * max_n1;
   for (int i = warp; i < n1; i += nw) {
     int pos = rowstart[i];
+    // atoms of the K1 list of site i's atom, for the radial-table lookup below
+    const int ai = w.site_atom[sbase + i];
+    const int na = w.counts[ai].n1;
+    const long long ab = (long long)ai * w.site_cap;
+    __syncwarp();
+    for (int t = lane; t < na; t += 32) lst[t] = w.site_atom[ab + t];
+    __syncwarp();
     for (int pass = 0; pass < 2; ++pass) {
       int jb = pass == 0 ? 0 : n1, je = pass == 0 ? i : n12;
       for (int j0 = jb; j0 < je; j0 += 32) {
@@ -137,7 +147,7 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
           int slot = pos + __popc(m & ((1u << lane) - 1u));
           long long q = offp + slot;
           double r = sqrt(r2);
-          int ai = w.site_atom[sbase + i], aj = w.site_atom[sbase + j];
+          const int aj = w.site_atom[sbase + j];
           double fsr, dfsr, fin = 1.0, dfin = 0.0, f, dfr, dfs;
           cutoff_buf(r, p.r_scs, p.r_buf, fsr, dfsr);
           if (pass == 1) finner(r, p.r_inner, fin, dfin);
@@ -148,6 +158,28 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
           w.pr_ij[2 * q + 1] = j;
           double* g = w.pr_geo + 8 * q;
           g[0] = rx; g[1] = ry; g[2] = rz; g[3] = r; g[4] = F; g[5] = dF; g[6] = 1.0 / r; g[7] = 0.0;
+          float2* gf = w.pr_gff + 6 * q;
+#pragma unroll
+          for (int u = 0; u < 7; ++u) {
+            if (u == 3) continue;
+            const ff v = ff_from_double(g[u]);
+            gf[u < 3 ? u : u - 1] = make_float2(v.hi, v.lo);
+          }
+          // the same atom pair in the radial table: the site of atom aj at displacement r in
+          // atom ai's own K1 list (none only if r ties r_SCS to rounding; then computed inline)
+          int gi = -1;
+          {
+            for (int t = 1; t < na; ++t) {
+              if (lst[t] != aj) continue;
+              const double* xt = w.site_x + 3 * (ab + t);
+              const double dx = xt[0] - rx, dy = xt[1] - ry, dz = xt[2] - rz;
+              if (dx * dx + dy * dy + dz * dz < 1e-12) {
+                gi = (int)(w.off_k1[ai] + t);
+                break;
+              }
+            }
+          }
+          w.pr_g[q] = gi;
           if (pass == 0) pid[i * max_n1 + j] = slot;
         }
         pos += __popc(m);
@@ -231,9 +263,11 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
 // (whole thread block of 256 threads; 16-wide blocks; 3 right-hand sides)
 // ---------------------------------------------------------------------------------------
 #define CB 16
+#define CBP (CB * (CB + 1) / 2)   // packed lower triangle of one diagonal-block inverse
+__device__ __forceinline__ int pidx16(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // Right-looking blocked Cholesky: warp 0 factors each 16 x 16 diagonal block (and stores the
-// inverse of that block in binv, 256 floats per block, for the triangular solves), every
+// inverse of that block in binv, packed lower triangle, for the triangular solves), every
 // thread then solves panel rows and updates the trailing lower triangle.  sinv[i] = 1/L_ii.
 __device__ void chol32_packed(float* A, int n, int* bad, float* sinv, float* binv) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
@@ -259,17 +293,17 @@ __device__ void chol32_packed(float* A, int n, int* bad, float* sinv, float* bin
         __syncwarp();
       }
       // inverse of the diagonal block: lane c solves L_bb x = e_c (column c), rows in order
-      float* inv = binv + (k0 / CB) * CB * CB;
+      float* inv = binv + (k0 / CB) * CBP;
       if (tid < CB) {
         const int cc = tid;
-        for (int i = 0; i < CB; ++i) {
+        for (int i = cc; i < CB; ++i) {
           float v = 0.f;
-          if (i < kb && cc < kb && i >= cc) {
+          if (i < kb && cc < kb) {
             float s = (i == cc) ? 1.f : 0.f;
-            for (int u = cc; u < i; ++u) s -= A[packed_idx(k0 + i, k0 + u)] * inv[u * CB + cc];
+            for (int u = cc; u < i; ++u) s -= A[packed_idx(k0 + i, k0 + u)] * inv[pidx16(u, cc)];
             v = s * sinv[k0 + i];
           }
-          inv[i * CB + cc] = v;
+          inv[pidx16(i, cc)] = v;
         }
       }
     }
@@ -321,17 +355,17 @@ __device__ void blockinv32(const float* A, int n, const float* sinv, float* binv
   const int nblk = (n + CB - 1) / CB;
   for (int blk = warp; blk < nblk; blk += nw) {
     const int k0 = blk * CB, kb = min(CB, n - k0);
-    float* inv = binv + blk * CB * CB;
+    float* inv = binv + blk * CBP;
     if (lane < CB) {
       const int cc = lane;
-      for (int i = 0; i < CB; ++i) {
+      for (int i = cc; i < CB; ++i) {
         float v = 0.f;
-        if (i < kb && cc < kb && i >= cc) {
+        if (i < kb && cc < kb) {
           float s = (i == cc) ? 1.f : 0.f;
-          for (int u = cc; u < i; ++u) s -= A[packed_idx(k0 + i, k0 + u)] * inv[u * CB + cc];
+          for (int u = cc; u < i; ++u) s -= A[packed_idx(k0 + i, k0 + u)] * inv[pidx16(u, cc)];
           v = s * sinv[k0 + i];
         }
-        inv[i * CB + cc] = v;
+        inv[pidx16(i, cc)] = v;
       }
     }
   }
@@ -368,10 +402,10 @@ __device__ void solve32_packed(const float* L, int n, const float* binv, float* 
     }
     __syncthreads();
     float v = 0.f;
-    const float* inv = binv + (b0 / CB) * CB * CB;
+    const float* inv = binv + (b0 / CB) * CBP;
     if (tid < 3 * bb) {
       const int i = tid / 3, c = tid % 3;
-      for (int u = 0; u <= i; ++u) v += inv[i * CB + u] * y[3 * (b0 + u) + c];
+      for (int u = 0; u <= i; ++u) v += inv[pidx16(i, u)] * y[3 * (b0 + u) + c];
     }
     __syncthreads();
     if (tid < 3 * bb) y[3 * b0 + tid] = v;
@@ -402,10 +436,10 @@ __device__ void solve32_packed(const float* L, int n, const float* binv, float* 
     }
     __syncthreads();
     float v = 0.f;
-    const float* inv = binv + blk * CB * CB;
+    const float* inv = binv + blk * CBP;
     if (tid < 3 * bb) {
       const int i = tid / 3, c = tid % 3;
-      for (int u = i; u < bb; ++u) v += inv[u * CB + i] * y[3 * (b0 + u) + c];
+      for (int u = i; u < bb; ++u) v += inv[pidx16(u, i)] * y[3 * (b0 + u) + c];
     }
     __syncthreads();
     if (tid < 3 * bb) y[3 * b0 + tid] = v;
@@ -419,22 +453,21 @@ __device__ void solve32_packed(const float* L, int n, const float* binv, float* 
 struct Scs2Smem {
   float* A;       // packed lower factor, N1 (N1 + 1) / 2
   float* sinv;    // N1
-  float* binv;    // ceil(N1/16) x 256: inverses of the diagonal blocks
+  float* binv;    // ceil(N1/16) x 136: inverses of the diagonal blocks (packed lower)
   float* y;       // N1 x 3 (FP32 right-hand side / correction)
   double* rhs;    // N1 x 3 (FP64 right-hand side d or dL/dX)
   double* x;      // N1 x 3 (FP64 solution X or lambda)
   double* xs;     // N1 x 3 (adjoint: X of the forward solve)
   double* ab;     // n12 (alpha_bar at this frequency)
-  double* iab;    // n12 (1 / alpha_bar)
-  double* sg;     // n12 (sigma at this frequency)
+  double* iab;    // n1 (1 / alpha_bar of the coupled sites)
   double* red;    // 64
 };
 
 __host__ __device__ inline size_t scs2_smem_bytes(int max_n1, int max_n12, bool adjoint) {
   size_t N1 = 3 * (size_t)max_n1;
-  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1 + (N1 + 15) / 16 * 256;
+  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1 + (N1 + 15) / 16 * CBP;
   fl = (fl + 1) & ~size_t(1);
-  size_t dd = 2 * 3 * N1 + 3 * (size_t)max_n12 + 64;
+  size_t dd = 2 * 3 * N1 + (size_t)max_n12 + (size_t)max_n1 + 64;
   if (adjoint) dd += 3 * N1;
   return fl * sizeof(float) + dd * sizeof(double);
 }
@@ -446,15 +479,14 @@ __device__ inline Scs2Smem scs2_carve(unsigned char* base, int max_n1, int max_n
   s.sinv = s.A + N1 * (N1 + 1) / 2;
   s.y = s.sinv + N1;
   s.binv = s.y + 3 * N1;
-  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1 + (N1 + 15) / 16 * 256;
+  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1 + (N1 + 15) / 16 * CBP;
   fl = (fl + 1) & ~size_t(1);
   double* d = (double*)(base + fl * sizeof(float));
   s.rhs = d;
   s.x = s.rhs + 3 * N1;
   s.ab = s.x + 3 * N1;
   s.iab = s.ab + max_n12;
-  s.sg = s.iab + max_n12;
-  s.red = s.sg + max_n12;
+  s.red = s.iab + max_n1;
   s.xs = adjoint ? s.red + 64 : nullptr;
   return s;
 }
@@ -482,8 +514,8 @@ __device__ void scs2_residual(const Work& w, const DevParams& p, int n1, long lo
       for (int u = 0; u < 4; ++u) {
         if (pp[u] >= 0) {
           const double* g = w.pr_geo + 8 * (offp + pp[u]);
-          const double* rad = w.pr_rad + 6 * ((offp + pp[u]) * p.nq + q);
-          gx[u] = g[0]; gy[u] = g[1]; gz[u] = g[2]; fa[u] = rad[4]; fb[u] = rad[5];
+          const double* rad = w.pr_rad + 2 * ((offp + pp[u]) * p.nq + q);
+          gx[u] = g[0]; gy[u] = g[1]; gz[u] = g[2]; fa[u] = rad[0]; fb[u] = rad[1];
         } else {
           gx[u] = gy[u] = gz[u] = fa[u] = fb[u] = 0.0;
         }
@@ -576,10 +608,41 @@ __device__ __forceinline__ void tsr_radial_fast(double r, double ir, double s2, 
   dB0 = (15.0 * g - 5.0 * ht - 2.0 * x * x * ht) * ir4 * ir2;
 }
 
+// Radial terms per atom pair and frequency: for atom a and every site s (1 <= s < n1) of its
+// own K1 list, A0, B0 and their r-derivatives at sigma_ab(omega_q).  They depend on |r_ab|
+// and sigma_a, sigma_b only, so every central atom whose local system holds the pair reads
+// them instead of evaluating erf and exp again (about 50 local systems share each pair).
+__global__ void __launch_bounds__(128) k_pair_radial(Work w, DevParams p) {
+  const int a = blockIdx.x;
+  if (a >= w.n_atoms) return;
+  const int n1 = w.counts[a].n1;
+  const long long ab = (long long)a * w.site_cap, base = w.off_k1[a];
+  for (int e = threadIdx.x; e < n1 * p.nq; e += blockDim.x) {
+    const int s = e / p.nq, q = e % p.nq;
+    if (s == 0) continue;
+    const double* x = w.site_x + 3 * (ab + s);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x[0], x[0]), __dmul_rn(x[1], x[1])), __dmul_rn(x[2], x[2]));
+    const double r = sqrt(r2);
+    const int b = w.site_atom[ab + s];
+    const double sa = w.sig[(long long)a * p.nq + q], sb = w.sig[(long long)b * p.nq + q];
+    double A0, B0, dA0, dB0;
+    tsr_radial_fast(r, 1.0 / r, sa * sa + sb * sb, A0, B0, dA0, dB0);
+    const long long o = (base + s) * p.nq + q;
+    w.rad_ab[2 * o] = A0;
+    w.rad_ab[2 * o + 1] = B0;
+    const double v[4] = {A0, B0, dA0, dB0};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const ff t = ff_from_double(v[u]);
+      w.rad_ff[4 * o + u] = make_float2(t.hi, t.lo);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // forward: one block per (central atom, frequency)
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, const int* order, int c0, int max_n1,
+__global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, const int* order, int c0, int max_n1,
                                                   int max_n12) {
   extern __shared__ unsigned char smem_raw[];
   const int c = order ? order[c0 + blockIdx.x / p.nq] : c0 + blockIdx.x / p.nq;
@@ -598,21 +661,32 @@ __global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, const i
     int a = w.site_atom[sbase + s];
     const double ab = w.abar[(long long)a * p.nq + q];
     sm.ab[s] = ab;
-    sm.iab[s] = 1.0 / ab;
-    sm.sg[s] = w.sig[(long long)a * p.nq + q];
+    if (s < n1) sm.iab[s] = 1.0 / ab;
   }
   const long long nA = (long long)N1 * (N1 + 1) / 2;
   for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = 0.f;
   __syncthreads();
-  // radial terms of every pair at this frequency (FP64), and the K1 blocks of B in FP32
+  // damped radial terms F A0, F B0 of every pair at this frequency (FP64, from the atom-pair
+  // table), and the K1 blocks of B in FP32
   for (int t = tid; t < np; t += blockDim.x) {
     const long long pq = offp + t;
     const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
     const double* g = w.pr_geo + 8 * pq;
-    double A0, B0, dA0, dB0;
-    tsr_radial_fast(g[3], g[6], sm.sg[i] * sm.sg[i] + sm.sg[j] * sm.sg[j], A0, B0, dA0, dB0);
-    double* rad = w.pr_rad + 6 * (pq * p.nq + q);
-    rad[0] = A0; rad[1] = B0; rad[2] = dA0; rad[3] = dB0; rad[4] = g[4] * A0; rad[5] = g[4] * B0;
+    const int gi = w.pr_g[pq];
+    double A0, B0;
+    if (gi >= 0) {
+      const double* ra = w.rad_ab + 2 * ((long long)gi * p.nq + q);
+      A0 = ra[0];
+      B0 = ra[1];
+    } else {
+      double dA0, dB0;
+      const double si = w.sig[(long long)w.site_atom[sbase + i] * p.nq + q];
+      const double sj = w.sig[(long long)w.site_atom[sbase + j] * p.nq + q];
+      tsr_radial_fast(g[3], g[6], si * si + sj * sj, A0, B0, dA0, dB0);
+    }
+    double* rad = w.pr_rad + 2 * (pq * p.nq + q);
+    rad[0] = g[4] * A0;
+    rad[1] = g[4] * B0;
     if (j < n1) {
       const double a = g[4] * A0, b = g[4] * B0;
       const double rr[3] = {g[0], g[1], g[2]};
@@ -626,7 +700,7 @@ __global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, const i
   }
   for (int i = tid; i < n1; i += blockDim.x)
 #pragma unroll
-    for (int al = 0; al < 3; ++al) sm.A[packed_idx(3 * i + al, 3 * i + al)] = (float)(1.0 / sm.ab[i]);
+    for (int al = 0; al < 3; ++al) sm.A[packed_idx(3 * i + al, 3 * i + al)] = (float)sm.iab[i];
   __threadfence_block();
   __syncthreads();
   // right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j (FP64, fixed order); one thread
@@ -639,10 +713,10 @@ __global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, const i
       const long long pq = offp + t;
       const int j = w.pr_ij[2 * pq + 1];
       const double* g = w.pr_geo + 8 * pq;
-      const double* rad = w.pr_rad + 6 * (pq * p.nq + q);
+      const double* rad = w.pr_rad + 2 * (pq * p.nq + q);
       const double abj = sm.ab[j];
-      ad += abj * rad[4];
-      const double wb = abj * rad[5] * g[c];
+      ad += abj * rad[0];
+      const double wb = abj * rad[1] * g[c];
       a0 += wb * g[0];
       a1 += wb * g[1];
       a2 += wb * g[2];
@@ -672,7 +746,7 @@ __global__ void __launch_bounds__(256) k_scs_factor(Work w, DevParams p, const i
 // ---------------------------------------------------------------------------------------
 // adjoint: one block per (central atom, frequency)
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scs_adjoint2(Work w, DevParams p, const int* order, int c0, int max_n1,
+__global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, const int* order, int c0, int max_n1,
                                                   int max_n12) {
   extern __shared__ unsigned char smem_raw[];
   const int c = order ? order[c0 + blockIdx.x / p.nq] : c0 + blockIdx.x / p.nq;
@@ -691,7 +765,7 @@ __global__ void __launch_bounds__(256) k_scs_adjoint2(Work w, DevParams p, const
     int a = w.site_atom[sbase + s];
     const double ab = w.abar[(long long)a * p.nq + q];
     sm.ab[s] = ab;
-    sm.iab[s] = 1.0 / ab;
+    if (s < n1) sm.iab[s] = 1.0 / ab;
   }
   const long long nA = (long long)N1 * (N1 + 1) / 2;
   const float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
@@ -716,49 +790,81 @@ __global__ void __launch_bounds__(256) k_scs_adjoint2(Work w, DevParams p, const
   __syncthreads();
   // pair contractions: <M, dT_SR/dr> with M = -(lambda_i X_j^T + lambda_j X_i^T) (K1 pairs)
   // or M = -alpha_bar_j lambda_i (K2 pairs), symmetrised; g = dL/dr_j = -dL/dr_i per pair,
-  // staged in global scratch (L2-resident) for the per-site gather
+  // staged in global scratch (L2-resident) for the per-site gather.  The contraction runs in
+  // float-float arithmetic (ff.cuh, ~2^-46 relative) on the FP32 pipe: lambda and X are
+  // converted once per site, geometry and radial terms come converted from the tables.
+  ff* lf = reinterpret_cast<ff*>(sm.rhs);   // lambda, 9 n1 (rhs is no longer needed)
+  ff* xf = reinterpret_cast<ff*>(sm.xs);    // X, 9 n1 (in place: one element per thread)
+  for (int e = tid; e < N1 * 3; e += blockDim.x) {
+    const double xv = sm.xs[e];
+    lf[e] = ff_from_double(sm.x[e]);
+    xf[e] = ff_from_double(xv);
+  }
+  __syncthreads();
   double* gst = w.gstage + (offp * p.nq + (long long)q * np) * 3;
   for (int t = tid; t < np; t += blockDim.x) {
     const long long pq = offp + t;
     const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
-    const double* g = w.pr_geo + 8 * pq;
-    const double* rad = w.pr_rad + 6 * (pq * p.nq + q);
-    const double* li = sm.x + 9 * i;
-    double M[6];
+    const int gi = w.pr_g[pq];
+    const ff* li = lf + 9 * i;
+    ff M[6];
     if (j < n1) {
-      const double* lj = sm.x + 9 * j;
-      const double* xi = sm.xs + 9 * i;
-      const double* xj = sm.xs + 9 * j;
-      double Mf[3][3];
+      const ff* lj = lf + 9 * j;
+      const ff* xi = xf + 9 * i;
+      const ff* xj = xf + 9 * j;
+      ff Mf[3][3];
 #pragma unroll
       for (int al = 0; al < 3; ++al)
 #pragma unroll
         for (int be = 0; be < 3; ++be) {
-          double s = 0.0;
+          ff s = ff_mul(li[3 * al], xj[3 * be]);
+          s = ff_fma(lj[3 * al], xi[3 * be], s);
 #pragma unroll
-          for (int ga = 0; ga < 3; ++ga) s += li[3 * al + ga] * xj[3 * be + ga] + lj[3 * al + ga] * xi[3 * be + ga];
-          Mf[al][be] = -s;
+          for (int ga = 1; ga < 3; ++ga) {
+            s = ff_fma(li[3 * al + ga], xj[3 * be + ga], s);
+            s = ff_fma(lj[3 * al + ga], xi[3 * be + ga], s);
+          }
+          Mf[al][be] = ff_neg(s);
         }
       M[0] = Mf[0][0]; M[1] = Mf[1][1]; M[2] = Mf[2][2];
-      M[3] = 0.5 * (Mf[0][1] + Mf[1][0]); M[4] = 0.5 * (Mf[0][2] + Mf[2][0]); M[5] = 0.5 * (Mf[1][2] + Mf[2][1]);
+      M[3] = ff_scale(ff_add(Mf[0][1], Mf[1][0]), 0.5f);
+      M[4] = ff_scale(ff_add(Mf[0][2], Mf[2][0]), 0.5f);
+      M[5] = ff_scale(ff_add(Mf[1][2], Mf[2][1]), 0.5f);
     } else {
-      const double aj = -sm.ab[j];
-      M[0] = aj * li[0]; M[1] = aj * li[4]; M[2] = aj * li[8];
-      M[3] = aj * 0.5 * (li[1] + li[3]); M[4] = aj * 0.5 * (li[2] + li[6]); M[5] = aj * 0.5 * (li[5] + li[7]);
+      const ff aj = ff_neg(ff_from_double(sm.ab[j]));
+      M[0] = ff_mul(aj, li[0]); M[1] = ff_mul(aj, li[4]); M[2] = ff_mul(aj, li[8]);
+      M[3] = ff_scale(ff_mul(aj, ff_add(li[1], li[3])), 0.5f);
+      M[4] = ff_scale(ff_mul(aj, ff_add(li[2], li[6])), 0.5f);
+      M[5] = ff_scale(ff_mul(aj, ff_add(li[5], li[7])), 0.5f);
     }
-    const double rr[3] = {g[0], g[1], g[2]};
-    const double F = g[4], dF = g[5], ir = g[6];
-    const double A0 = rad[0], B0 = rad[1], dA0 = rad[2], dB0 = rad[3];
-    const double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2], M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
-                          M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
-    const double trM = M[0] + M[1] + M[2];
-    const double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
-    const double phi = A0 * trM + B0 * rMr;
-    const double radial = (dF * phi + F * (dA0 * trM + dB0 * rMr)) * ir;
-    const double tang = 2.0 * F * B0;
-    gst[3 * t] = radial * rr[0] + tang * Mr[0];
-    gst[3 * t + 1] = radial * rr[1] + tang * Mr[1];
-    gst[3 * t + 2] = radial * rr[2] + tang * Mr[2];
+    const float2* gf = w.pr_gff + 6 * pq;
+    const ff rr[3] = {ff_make(gf[0].x, gf[0].y), ff_make(gf[1].x, gf[1].y), ff_make(gf[2].x, gf[2].y)};
+    const ff F = ff_make(gf[3].x, gf[3].y), dF = ff_make(gf[4].x, gf[4].y), ir = ff_make(gf[5].x, gf[5].y);
+    ff A0, B0, dA0, dB0;
+    if (gi >= 0) {
+      const float2* ra = w.rad_ff + 4 * ((long long)gi * p.nq + q);
+      A0 = ff_make(ra[0].x, ra[0].y); B0 = ff_make(ra[1].x, ra[1].y);
+      dA0 = ff_make(ra[2].x, ra[2].y); dB0 = ff_make(ra[3].x, ra[3].y);
+    } else {
+      const double* g = w.pr_geo + 8 * pq;
+      const double si = w.sig[(long long)w.site_atom[sbase + i] * p.nq + q];
+      const double sj = w.sig[(long long)w.site_atom[sbase + j] * p.nq + q];
+      double a0d, b0d, da0d, db0d;
+      tsr_radial_fast(g[3], g[6], si * si + sj * sj, a0d, b0d, da0d, db0d);
+      A0 = ff_from_double(a0d); B0 = ff_from_double(b0d); dA0 = ff_from_double(da0d); dB0 = ff_from_double(db0d);
+    }
+    const ff Mr[3] = {ff_fma(M[4], rr[2], ff_fma(M[3], rr[1], ff_mul(M[0], rr[0]))),
+                      ff_fma(M[5], rr[2], ff_fma(M[1], rr[1], ff_mul(M[3], rr[0]))),
+                      ff_fma(M[2], rr[2], ff_fma(M[5], rr[1], ff_mul(M[4], rr[0])))};
+    const ff trM = ff_add(ff_add(M[0], M[1]), M[2]);
+    const ff rMr = ff_fma(rr[2], Mr[2], ff_fma(rr[1], Mr[1], ff_mul(rr[0], Mr[0])));
+    const ff phi = ff_fma(B0, rMr, ff_mul(A0, trM));
+    const ff inner = ff_fma(dB0, rMr, ff_mul(dA0, trM));
+    const ff radial = ff_mul(ff_fma(F, inner, ff_mul(dF, phi)), ir);
+    const ff tang = ff_scale(ff_mul(F, B0), 2.0f);
+    gst[3 * t] = ff_to_double(ff_fma(tang, Mr[0], ff_mul(radial, rr[0])));
+    gst[3 * t + 1] = ff_to_double(ff_fma(tang, Mr[1], ff_mul(radial, rr[1])));
+    gst[3 * t + 2] = ff_to_double(ff_fma(tang, Mr[2], ff_mul(radial, rr[2])));
   }
   __syncthreads();
   // per site (fixed order): owner of its row's pairs (-g), partner of K1 pairs owned by later
@@ -818,9 +924,14 @@ void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream
 void launch_scs_fill(const Work& w, const DevParams& p, int c0, int c1, int max_n12, int max_n1, cudaStream_t s) {
   if (c1 <= c0) return;
   size_t sm = sizeof(double) * 3 * (size_t)max_n12 +
-              sizeof(int) * ((size_t)max_n1 * max_n1 + 6 * (size_t)max_n1 + 2 + (size_t)max_n12);
+              sizeof(int) * ((size_t)max_n1 * max_n1 + 6 * (size_t)max_n1 + 2 + (size_t)max_n12 + 8 * (size_t)max_n1);
   raise_smem_limit((const void*)k_scs_fill, sm);
   k_scs_fill<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_n12, max_n1);
+}
+
+void launch_pair_radial(const Work& w, const DevParams& p, cudaStream_t s) {
+  if (w.n_atoms == 0) return;
+  k_pair_radial<<<w.n_atoms, 128, 0, s>>>(w, p);
 }
 
 size_t scs2_forward_smem(int max_n1, int max_n12) { return scs2_smem_bytes(max_n1, max_n12, false); }

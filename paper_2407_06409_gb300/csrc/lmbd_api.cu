@@ -56,19 +56,19 @@ struct Ctx {
   DevBuf table_d, pos_d, species_d, nu_d, weights_d, out_e_d, out_f_d;
   DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
   DevBuf site_atom, site_x, counts, offs, totals, status, pcount;
-  DevBuf alphaK, alphaI, energies, trbuf, wexp, alphaK_bar, alphaI_bar, gacc;
+  DevBuf alphaK, alphaI, energies, trbuf, wexp, alphaK_bar, alphaI_bar, gacc, rad_ab, rad_ff;
   DevBuf order1_d, order3_d;
   DevBuf arena;
   std::vector<Counts> counts_h;
   std::vector<long long> offs_h;
   std::vector<int> order1_h, order3_h;
-  DevBuf* whole_bufs[36] = {};
+  DevBuf* whole_bufs[48] = {};
   int n_whole = 0;
   Ctx() {
     DevBuf* l[] = {&table_d, &pos_d, &species_d, &nu_d, &weights_d, &out_e_d, &out_f_d, &abar, &sig, &rvdw,
                    &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
-                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d};
+                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff};
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
   size_t whole_bytes() const {
@@ -223,7 +223,9 @@ struct Layout {
     float* lfac = cv.take<float>(o.span(O_B, c0, c1), o.at(O_B, c0));
     int* pr_ij = cv.take<int>(2 * (np + 1), 2 * p0);
     double* pr_geo = cv.take<double>(8 * (np + 1), 8 * p0);
-    double* pr_rad = cv.take<double>(6LL * nq * (np + 1), 6LL * nq * p0);
+    double* pr_rad = cv.take<double>(2LL * nq * (np + 1), 2LL * nq * p0);
+    int* pr_g = cv.take<int>(np + 1, p0);
+    float2* pr_gff = cv.take<float2>(6 * (np + 1), 6 * p0);
     int* k2rev = cv.take<int>(np + 1, p0);
     int* prow = cv.take<int>(nk + n, k0 + c0);
     int* prow_k2 = cv.take<int>(nk + n, k0 + c0);
@@ -236,6 +238,8 @@ struct Layout {
       w->pr_ij = pr_ij;
       w->pr_geo = pr_geo;
       w->pr_rad = pr_rad;
+      w->pr_g = pr_g;
+      w->pr_gff = pr_gff;
       w->k2rev = k2rev;
       w->prow = prow;
       w->prow_k2 = prow_k2;
@@ -593,7 +597,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   const bool sliced_chain = sliced && ncv <= 48;
   const int ST = 6, DIG_E = 6, DIG_A = 5, DIG_P = 5;
   TRY(ensure(c->alphaK, sizeof(double) * (size_t)sum_n1 * nq));
+  TRY(ensure(c->rad_ab, sizeof(double) * 2 * (size_t)sum_n1 * nq));
+  TRY(ensure(c->rad_ff, sizeof(float2) * 4 * (size_t)sum_n1 * nq));
   w.alphaK = (double*)c->alphaK.p;
+  w.rad_ab = (double*)c->rad_ab.p;
+  w.rad_ff = (float2*)c->rad_ff.p;
   w.nvec = nvec;
   w.ncol = ncol;
   if (sliced_chain) {
@@ -715,6 +723,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   // ---- pass A: stage 1 (SCS) of all centres --------------------------------------------------
   prof = prof_req && one_wave;
   mark(LMBD_PHASE_SCS);
+  launch_pair_radial(w, dp, s);
+  ++phase_launch[LMBD_PHASE_SCS];
   for (int wv = 0; wv < nwA; ++wv) TRY(stage1_forward(wv, cutA, bucketsA, orderA));
 
   // ---- pass B: stage 2 (MBD energy) and its adjoint, per wave --------------------------------

@@ -83,7 +83,13 @@ struct Work {
   int* pcount;                 // N x 2: pairs, adjacency entries
   int* pr_ij;                  // pairs x 2: owner row i (K1), partner j (K1 with j < i, or K2)
   double* pr_geo;              // pairs x 8: r = x_j - x_i (3), |r|, F, dF/dr, 1/|r|, unused
-  double* pr_rad;              // pairs x nq x 6: A0, B0, A0', B0', F A0, F B0 per frequency
+  double* pr_rad;              // pairs x nq x 2: F A0, F B0 per frequency (written by the factor kernel)
+  int* pr_g;                   // pairs: index of the pair in the atom-pair radial table, -1 = none
+  // radial terms of T_SR per atom pair and frequency, independent of the central atom: entry
+  // off_k1[a] + s is atom a with site s (1 <= s < n1) of its own K1 list
+  double* rad_ab;              // sum n1 x nq x 2: A0, B0
+  float2* rad_ff;              // sum n1 x nq x 4: A0, B0, dA0/dr, dB0/dr as float-float (hi, lo)
+  float2* pr_gff;              // pairs x 6: r (3), F, dF/dr, 1/|r| as float-float (SCS adjoint)
   int* prow;                   // (sum n1 + N): first pair of each row, per centre n1 + 1 entries
   int* prow_k2;                // (sum n1 + N): first K2 pair of each row
   int* arow;                   // (sum n1 + N): first adjacency entry of each row
@@ -212,6 +218,7 @@ void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStre
 void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s);
 void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s);
 void launch_scs_fill(const Work& w, const DevParams& p, int c0, int c1, int max_n12, int max_n1, cudaStream_t s);
+void launch_pair_radial(const Work& w, const DevParams& p, cudaStream_t s);
 void launch_scs_factor(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1, int max_n12,
                        cudaStream_t s);
 void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1,

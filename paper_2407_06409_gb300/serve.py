@@ -182,10 +182,20 @@ class Server:
         return free - need, free
 
     def _admit(self, pending: list, t0: float) -> None:
-        self._large_waiting = any(it.structure.n_atoms >= self.large_atoms for it in pending[:self.window])
+        # with lanes each lane has its own arrival-order queue and window, so that a backlog of
+        # large requests does not hold back small ones (and the other way round)
+        self._large_waiting = self.lanes and any(it.structure.n_atoms >= self.large_atoms for it in pending)
+        seen = {False: 0, True: 0}
         i = 0
-        while i < min(len(pending), self.window):
+        while i < len(pending):
             item = pending[i]
+            cls = self.lanes and item.structure.n_atoms >= self.large_atoms
+            if seen[cls] >= self.window:
+                if not self.lanes or seen[not cls] >= self.window:
+                    return
+                i += 1
+                continue
+            seen[cls] += 1
             slot = self._pick_slot(item)
             if slot is None:
                 if not self.lanes:

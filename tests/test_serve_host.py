@@ -179,3 +179,15 @@ def test_size_lanes():
     assert any(r.admitted < large[0].done for r in small)
     s = serve.summarize(res, large_atoms=500)
     assert s["below_500_atoms"]["requests"] == 8 and s["from_500_atoms"]["requests"] == 4
+
+
+def test_lanes_keep_small_requests_out_of_a_large_backlog():
+    # a backlog of large requests longer than the admission window; small requests arriving
+    # later are served from their own queue while the backlog drains
+    items = [_Item(i, 0.0, _S(600), i) for i in range(24)]
+    items += [_Item(24 + k, 0.02, _S(30), 24 + k) for k in range(5)]
+    srv = _server(3, hbm=5e9, window=4, large_atoms=500, large_slots=1)
+    res = {r.rid: r for r in srv.serve(items, realtime=True)}
+    assert all(r.error is None for r in res.values())
+    last_large = max(res[i].done for i in range(24))
+    assert max(res[24 + k].done for k in range(5)) < 0.5 * last_large
