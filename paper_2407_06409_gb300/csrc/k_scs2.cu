@@ -274,37 +274,58 @@ __device__ void chol32_packed(float* A, int n, int* bad, float* sinv, float* bin
   for (int k0 = 0; k0 < n; k0 += CB) {
     const int kb = min(CB, n - k0);
     if (tid < 32) {
-      for (int t = 0; t < kb; ++t) {
-        if (tid == 0) {
-          float a = A[packed_idx(k0 + t, k0 + t)];
-          if (!(a > 0.f)) { *bad = 1; a = 1.f; }
-          a = sqrtf(a);
-          A[packed_idx(k0 + t, k0 + t)] = a;
-          sinv[k0 + t] = 1.f / a;
+      // the 16 x 16 diagonal block in registers, one row per lane (rows beyond kb hold the
+      // identity): right-looking Cholesky with shuffles, then the inverse of the factor, one
+      // column per lane
+      const bool act = lane < kb;
+      float a[CB];
+#pragma unroll
+      for (int u = 0; u < CB; ++u)
+        a[u] = act ? (u <= lane ? A[packed_idx(k0 + lane, k0 + u)] : 0.f) : (u == lane ? 1.f : 0.f);
+      bool fail = false;
+#pragma unroll
+      for (int t = 0; t < CB; ++t) {
+        float d = __shfl_sync(0xffffffffu, a[t], t);
+        if (t < kb && !(d > 0.f)) {
+          fail = true;
+          d = 1.f;
         }
-        __syncwarp();
-        const float it = sinv[k0 + t];
-        if (tid > t && tid < kb) A[packed_idx(k0 + tid, k0 + t)] *= it;
-        __syncwarp();
-        for (int e = tid; e < kb * kb; e += 32) {
-          int i = e / kb, j = e % kb;
-          if (j > t && j <= i) A[packed_idx(k0 + i, k0 + j)] -= A[packed_idx(k0 + i, k0 + t)] * A[packed_idx(k0 + j, k0 + t)];
-        }
-        __syncwarp();
-      }
-      // inverse of the diagonal block: lane c solves L_bb x = e_c (column c), rows in order
-      float* inv = binv + (k0 / CB) * CBP;
-      if (tid < CB) {
-        const int cc = tid;
-        for (int i = cc; i < CB; ++i) {
-          float v = 0.f;
-          if (i < kb && cc < kb) {
-            float s = (i == cc) ? 1.f : 0.f;
-            for (int u = cc; u < i; ++u) s -= A[packed_idx(k0 + i, k0 + u)] * inv[pidx16(u, cc)];
-            v = s * sinv[k0 + i];
+        const float l = sqrtf(d), il = 1.f / l;
+        if (lane == t) a[t] = l;
+        else if (lane > t) a[t] *= il;
+#pragma unroll
+        for (int j = 1; j < CB; ++j) {
+          if (j > t) {
+            const float ljt = __shfl_sync(0xffffffffu, a[t], j);
+            if (lane >= j) a[j] -= a[t] * ljt;
           }
-          inv[pidx16(i, cc)] = v;
         }
+      }
+      if (fail && lane == 0) *bad = 1;
+      float dl = 1.f;
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        if (act && u <= lane) A[packed_idx(k0 + lane, k0 + u)] = a[u];
+        if (u == lane) dl = a[u];
+      }
+      if (act) sinv[k0 + lane] = 1.f / dl;
+      __syncwarp();
+      // inverse of the factor block: lane c solves L x = e_c, reading L from shared memory
+      // (every lane reads the same element: broadcast)
+      float* inv = binv + (k0 / CB) * CBP;
+      float x[CB];
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        float v = 0.f;
+        if (i < kb) {
+          const float* Li = A + packed_idx(k0 + i, k0);
+          float s = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+          for (int u = 0; u < i; ++u) s -= Li[u] * x[u];
+          v = (i >= lane && act) ? s * sinv[k0 + i] : 0.f;
+        }
+        x[i] = v;
+        if (lane < CB && i >= lane) inv[pidx16(i, lane)] = v;
       }
     }
     __syncthreads();
@@ -372,11 +393,13 @@ __device__ void blockinv32(const float* A, int n, const float* sinv, float* binv
 }
 
 // y (n x 3, FP32, shared) <- (L L^T)^-1 y with binv the inverses of the 16 x 16 diagonal
-// blocks.  Off-diagonal blocks by 16 rows x 16 partial sums; each diagonal block is one
-// parallel product with its inverse.
-__device__ void solve32_packed(const float* L, int n, const float* binv, float* y) {
+// blocks; z (n x 3) is scratch.  Per block row: the off-diagonal part as 16 rows x 16 partial
+// sums (it updates only this block's right-hand side), then one parallel product with the
+// block inverse written to the other buffer, so two barriers per block row suffice.
+__device__ void solve32_packed(const float* L, int n, const float* binv, float* y, float* z) {
   const int tid = threadIdx.x;
   const int r = tid >> 4, s = tid & 15;
+  // forward: z = L^-1 y
   for (int b0 = 0; b0 < n; b0 += CB) {
     const int bb = min(CB, n - b0);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
@@ -384,9 +407,9 @@ __device__ void solve32_packed(const float* L, int n, const float* binv, float* 
       const float* row = L + packed_idx(b0 + r, 0);
       for (int k = s; k < b0; k += 16) {
         const float l = row[k];
-        a0 += l * y[3 * k];
-        a1 += l * y[3 * k + 1];
-        a2 += l * y[3 * k + 2];
+        a0 += l * z[3 * k];
+        a1 += l * z[3 * k + 1];
+        a2 += l * z[3 * k + 2];
       }
     }
 #pragma unroll
@@ -401,16 +424,16 @@ __device__ void solve32_packed(const float* L, int n, const float* binv, float* 
       y[3 * (b0 + r) + 2] -= a2;
     }
     __syncthreads();
-    float v = 0.f;
     const float* inv = binv + (b0 / CB) * CBP;
     if (tid < 3 * bb) {
       const int i = tid / 3, c = tid % 3;
+      float v = 0.f;
       for (int u = 0; u <= i; ++u) v += inv[pidx16(i, u)] * y[3 * (b0 + u) + c];
+      z[3 * b0 + tid] = v;
     }
     __syncthreads();
-    if (tid < 3 * bb) y[3 * b0 + tid] = v;
-    __syncthreads();
   }
+  // backward: y = L^-T z
   const int nblk = (n + CB - 1) / CB;
   for (int blk = nblk - 1; blk >= 0; --blk) {
     const int b0 = blk * CB, bb = min(CB, n - b0), b1 = b0 + bb;
@@ -430,19 +453,18 @@ __device__ void solve32_packed(const float* L, int n, const float* binv, float* 
       a2 += __shfl_down_sync(0xffffffffu, a2, o, 16);
     }
     if (s == 0 && r < bb) {
-      y[3 * (b0 + r)] -= a0;
-      y[3 * (b0 + r) + 1] -= a1;
-      y[3 * (b0 + r) + 2] -= a2;
+      z[3 * (b0 + r)] -= a0;
+      z[3 * (b0 + r) + 1] -= a1;
+      z[3 * (b0 + r) + 2] -= a2;
     }
     __syncthreads();
-    float v = 0.f;
     const float* inv = binv + blk * CBP;
     if (tid < 3 * bb) {
       const int i = tid / 3, c = tid % 3;
-      for (int u = i; u < bb; ++u) v += inv[pidx16(u, i)] * y[3 * (b0 + u) + c];
+      float v = 0.f;
+      for (int u = i; u < bb; ++u) v += inv[pidx16(u, i)] * z[3 * (b0 + u) + c];
+      y[3 * b0 + tid] = v;
     }
-    __syncthreads();
-    if (tid < 3 * bb) y[3 * b0 + tid] = v;
     __syncthreads();
   }
 }
@@ -455,6 +477,7 @@ struct Scs2Smem {
   float* sinv;    // N1
   float* binv;    // ceil(N1/16) x 136: inverses of the diagonal blocks (packed lower)
   float* y;       // N1 x 3 (FP32 right-hand side / correction)
+  float* z;       // N1 x 3 (FP32 scratch of the triangular solves)
   double* rhs;    // N1 x 3 (FP64 right-hand side d or dL/dX)
   double* x;      // N1 x 3 (FP64 solution X or lambda)
   double* xs;     // N1 x 3 (adjoint: X of the forward solve)
@@ -465,7 +488,7 @@ struct Scs2Smem {
 
 __host__ __device__ inline size_t scs2_smem_bytes(int max_n1, int max_n12, bool adjoint) {
   size_t N1 = 3 * (size_t)max_n1;
-  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1 + (N1 + 15) / 16 * CBP;
+  size_t fl = N1 * (N1 + 1) / 2 + N1 + 6 * N1 + (N1 + 15) / 16 * CBP;
   fl = (fl + 1) & ~size_t(1);
   size_t dd = 2 * 3 * N1 + (size_t)max_n12 + (size_t)max_n1 + 64;
   if (adjoint) dd += 3 * N1;
@@ -478,8 +501,9 @@ __device__ inline Scs2Smem scs2_carve(unsigned char* base, int max_n1, int max_n
   s.A = (float*)base;
   s.sinv = s.A + N1 * (N1 + 1) / 2;
   s.y = s.sinv + N1;
-  s.binv = s.y + 3 * N1;
-  size_t fl = N1 * (N1 + 1) / 2 + N1 + 3 * N1 + (N1 + 15) / 16 * CBP;
+  s.z = s.y + 3 * N1;
+  s.binv = s.z + 3 * N1;
+  size_t fl = N1 * (N1 + 1) / 2 + N1 + 6 * N1 + (N1 + 15) / 16 * CBP;
   fl = (fl + 1) & ~size_t(1);
   double* d = (double*)(base + fl * sizeof(float));
   s.rhs = d;
@@ -544,7 +568,7 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
   const int N1 = 3 * n1, tid = threadIdx.x;
   for (int e = tid; e < 3 * N1; e += blockDim.x) sm.y[e] = (float)sm.rhs[e];
   __syncthreads();
-  solve32_packed(sm.A, N1, sm.binv, sm.y);
+  solve32_packed(sm.A, N1, sm.binv, sm.y, sm.z);
   for (int e = tid; e < 3 * N1; e += blockDim.x) sm.x[e] = (double)sm.y[e];
   __syncthreads();
   double prev = 0.0;
@@ -552,7 +576,7 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
   for (; it < 12; ++it) {
     scs2_residual(w, p, n1, offp, offa, rbase, q, sm);
     __syncthreads();
-    solve32_packed(sm.A, N1, sm.binv, sm.y);
+    solve32_packed(sm.A, N1, sm.binv, sm.y, sm.z);
     double dmax = 0.0, xmax = 0.0;
     for (int e = tid; e < 3 * N1; e += blockDim.x) {
       double dlt = (double)sm.y[e];
