@@ -555,14 +555,51 @@ __device__ void scs2_residual(const Work& w, const DevParams& p, int n1, long lo
       }
     }
     const double ia = sm.iab[i];
-    sm.y[9 * i + c] = (float)(sm.rhs[9 * i + c] - ia * sm.x[9 * i + c] - a0);
-    sm.y[9 * i + 3 + c] = (float)(sm.rhs[9 * i + 3 + c] - ia * sm.x[9 * i + 3 + c] - a1);
-    sm.y[9 * i + 6 + c] = (float)(sm.rhs[9 * i + 6 + c] - ia * sm.x[9 * i + 6 + c] - a2);
+    const double r0 = sm.rhs[9 * i + c] - ia * sm.x[9 * i + c] - a0;
+    const double r1 = sm.rhs[9 * i + 3 + c] - ia * sm.x[9 * i + 3 + c] - a1;
+    const double r2 = sm.rhs[9 * i + 6 + c] - ia * sm.x[9 * i + 6 + c] - a2;
+    sm.rhs[9 * i + c] = r0;
+    sm.rhs[9 * i + 3 + c] = r1;
+    sm.rhs[9 * i + 6 + c] = r2;
+    sm.y[9 * i + c] = (float)r0;
+    sm.y[9 * i + 3 + c] = (float)r1;
+    sm.y[9 * i + 6 + c] = (float)r2;
+  }
+}
+
+// rhs <- rhs - B delta for the FP32 correction delta in y, in float-float arithmetic: the
+// residual of x + delta without forming B x again in FP64 (delta is ~1e-7 of x, so 2^-46
+// relative accuracy in B delta keeps the residual exact to FP64 rounding).
+__device__ void scs2_residual_update(const Work& w, const DevParams& p, int n1, long long offp, long long offa,
+                                     long long rbase, int q, Scs2Smem& sm) {
+  for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
+    const int i = e / 3, c = e % 3;
+    const ff ia = ff_from_double(sm.iab[i]);
+    ff a0 = ff_scale(ia, sm.y[9 * i + c]), a1 = ff_scale(ia, sm.y[9 * i + 3 + c]),
+       a2 = ff_scale(ia, sm.y[9 * i + 6 + c]);
+    const int b = w.arow[rbase + i], en = w.arow[rbase + i + 1];
+    for (int t = b; t < en; ++t) {
+      const int j = w.adj[2 * (offa + t)];
+      const long long pq = offp + w.adj[2 * (offa + t) + 1];
+      const float2* gf = w.pr_gff + 6 * pq;
+      const float2* rf = w.pr_rad_ff + 2 * (pq * p.nq + q);
+      const ff rx = ff_make(gf[0].x, gf[0].y), ry = ff_make(gf[1].x, gf[1].y), rz = ff_make(gf[2].x, gf[2].y);
+      const ff fa = ff_make(rf[0].x, rf[0].y), fb = ff_make(rf[1].x, rf[1].y);
+      const float d0 = sm.y[9 * j + c], d1 = sm.y[9 * j + 3 + c], d2 = sm.y[9 * j + 6 + c];
+      const ff bu = ff_mul(fb, ff_add(ff_add(ff_scale(rx, d0), ff_scale(ry, d1)), ff_scale(rz, d2)));
+      a0 = ff_add(a0, ff_add(ff_scale(fa, d0), ff_mul(bu, rx)));
+      a1 = ff_add(a1, ff_add(ff_scale(fa, d1), ff_mul(bu, ry)));
+      a2 = ff_add(a2, ff_add(ff_scale(fa, d2), ff_mul(bu, rz)));
+    }
+    sm.rhs[9 * i + c] -= ff_to_double(a0);
+    sm.rhs[9 * i + 3 + c] -= ff_to_double(a1);
+    sm.rhs[9 * i + 6 + c] -= ff_to_double(a2);
   }
 }
 
 // x = B^-1 rhs: FP32 solve, then FP64 refinement until the predicted error is below
-// 2^-52 |x|.  Returns the number of residuals formed; *fail set if it does not converge.
+// 2^-52 |x|: the residual is formed once in FP64 and then updated by the corrections (rhs is
+// overwritten).  Returns the number of corrections; *fail set if it does not converge.
 __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long offp, long long offa,
                            long long rbase, int q, Scs2Smem& sm, int* fail) {
   const int N1 = 3 * n1, tid = threadIdx.x;
@@ -571,11 +608,12 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
   solve32_packed(sm.A, N1, sm.binv, sm.y, sm.z);
   for (int e = tid; e < 3 * N1; e += blockDim.x) sm.x[e] = (double)sm.y[e];
   __syncthreads();
+  // the residual d - B x once in FP64 (kept in rhs), then updated by -B delta per correction
+  scs2_residual(w, p, n1, offp, offa, rbase, q, sm);
+  __syncthreads();
   double prev = 0.0;
   int it = 0;
   for (; it < 12; ++it) {
-    scs2_residual(w, p, n1, offp, offa, rbase, q, sm);
-    __syncthreads();
     solve32_packed(sm.A, N1, sm.binv, sm.y, sm.z);
     double dmax = 0.0, xmax = 0.0;
     for (int e = tid; e < 3 * N1; e += blockDim.x) {
@@ -608,6 +646,10 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
     }
     prev = dmax;
     if (it == 11 && tid == 0) *fail = 1;
+    scs2_residual_update(w, p, n1, offp, offa, rbase, q, sm);
+    __syncthreads();
+    for (int e = tid; e < 3 * N1; e += blockDim.x) sm.y[e] = (float)sm.rhs[e];
+    __syncthreads();
   }
   return it;
 }
@@ -711,6 +753,22 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
     double* rad = w.pr_rad + 2 * (pq * p.nq + q);
     rad[0] = g[4] * A0;
     rad[1] = g[4] * B0;
+    {
+      float2* rf = w.pr_rad_ff + 2 * (pq * p.nq + q);
+      ff fa, fb;
+      if (gi >= 0) {   // from the float-float tables, on the FP32 pipe
+        const float2* ra = w.rad_ff + 4 * ((long long)gi * p.nq + q);
+        const float2 Fg = w.pr_gff[6 * pq + 3];
+        const ff F = ff_make(Fg.x, Fg.y);
+        fa = ff_mul(F, ff_make(ra[0].x, ra[0].y));
+        fb = ff_mul(F, ff_make(ra[1].x, ra[1].y));
+      } else {
+        fa = ff_from_double(rad[0]);
+        fb = ff_from_double(rad[1]);
+      }
+      rf[0] = make_float2(fa.hi, fa.lo);
+      rf[1] = make_float2(fb.hi, fb.lo);
+    }
     if (j < n1) {
       const double a = g[4] * A0, b = g[4] * B0;
       const double rr[3] = {g[0], g[1], g[2]};

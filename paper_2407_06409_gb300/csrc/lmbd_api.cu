@@ -224,6 +224,7 @@ struct Layout {
     int* pr_ij = cv.take<int>(2 * (np + 1), 2 * p0);
     double* pr_geo = cv.take<double>(8 * (np + 1), 8 * p0);
     double* pr_rad = cv.take<double>(2LL * nq * (np + 1), 2LL * nq * p0);
+    float2* pr_rad_ff = cv.take<float2>(2LL * nq * (np + 1), 2LL * nq * p0);
     int* pr_g = cv.take<int>(np + 1, p0);
     float2* pr_gff = cv.take<float2>(6 * (np + 1), 6 * p0);
     int* k2rev = cv.take<int>(np + 1, p0);
@@ -238,6 +239,7 @@ struct Layout {
       w->pr_ij = pr_ij;
       w->pr_geo = pr_geo;
       w->pr_rad = pr_rad;
+      w->pr_rad_ff = pr_rad_ff;
       w->pr_g = pr_g;
       w->pr_gff = pr_gff;
       w->k2rev = k2rev;
