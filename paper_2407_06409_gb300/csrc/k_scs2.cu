@@ -30,6 +30,19 @@ __device__ __forceinline__ bool scs_pair_in(const double* xs, int ld, int i, int
   return r2 < rc2;
 }
 
+// FP32 screen of the same predicate: pairs farther than a relative 1e-4 from the radius are
+// decided in FP32 (the FP32 error of r^2 is below 1e-5 r_SCS^2 for sites within 27 r_SCS of
+// the centre); the others take the FP64 test, so the decision is always the FP64 one.
+__device__ __forceinline__ bool scs_pair_in_screened(const float* xf, const double* xs, int ld, int i, int j,
+                                                     float lo2, float hi2, double rc2) {
+  const float dx = xf[j] - xf[i], dy = xf[ld + j] - xf[ld + i], dz = xf[2 * ld + j] - xf[2 * ld + i];
+  const float r2f = dx * dx + dy * dy + dz * dz;
+  if (r2f < lo2) return true;
+  if (r2f > hi2) return false;
+  double rx, ry, rz, r2;
+  return scs_pair_in(xs, ld, i, j, rc2, rx, ry, rz, r2);
+}
+
 __device__ __forceinline__ long long packed_idx(int i, int k) { return (long long)i * (i + 1) / 2 + k; }
 
 // ---------------------------------------------------------------------------------------
@@ -38,6 +51,7 @@ __device__ __forceinline__ long long packed_idx(int i, int k) { return (long lon
 __global__ void __launch_bounds__(256) k_scs_count(Work w, DevParams p, int max_n12) {
   extern __shared__ double smem_d[];
   double* xs = smem_d;                 // 3 x max_n12
+  float* xf = (float*)(xs + 3 * max_n12);   // 3 x max_n12, FP32 copies
   __shared__ int cnt_k1k1, cnt_k2;
   const int c = blockIdx.x;
   if (c >= w.n_atoms) return;
@@ -46,10 +60,15 @@ __global__ void __launch_bounds__(256) k_scs_count(Work w, DevParams p, int max_
   const long long sbase = (long long)c * w.site_cap;
   const int tid = threadIdx.x;
   for (int s = tid; s < n12; s += blockDim.x)
-    for (int d = 0; d < 3; ++d) xs[d * max_n12 + s] = w.site_x[3 * (sbase + s) + d];
+    for (int d = 0; d < 3; ++d) {
+      const double v = w.site_x[3 * (sbase + s) + d];
+      xs[d * max_n12 + s] = v;
+      xf[d * max_n12 + s] = (float)v;
+    }
   if (tid == 0) { cnt_k1k1 = 0; cnt_k2 = 0; }
   __syncthreads();
   const double rc2 = p.r_scs * p.r_scs;
+  const float lo2 = (float)(rc2 * (1.0 - 1e-4)), hi2 = (float)(rc2 * (1.0 + 1e-4));
   int a = 0, b = 0;
   const int nkk = n1 * (n1 - 1) / 2;
   for (int e = tid; e < nkk; e += blockDim.x) {
@@ -57,14 +76,12 @@ __global__ void __launch_bounds__(256) k_scs_count(Work w, DevParams p, int max_
     while (i * (i - 1) / 2 > e) --i;
     while ((i + 1) * i / 2 <= e) ++i;
     int j = e - i * (i - 1) / 2;
-    double rx, ry, rz, r2;
-    a += scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+    a += scs_pair_in_screened(xf, xs, max_n12, i, j, lo2, hi2, rc2);
   }
   const int n2 = n12 - n1;
   for (int e = tid; e < n1 * n2; e += blockDim.x) {
     int i = e / n2, j = n1 + e % n2;
-    double rx, ry, rz, r2;
-    b += scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+    b += scs_pair_in_screened(xf, xs, max_n12, i, j, lo2, hi2, rc2);
   }
   atomicAdd(&cnt_k1k1, a);
   atomicAdd(&cnt_k2, b);
@@ -89,6 +106,7 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
   int* adjstart = adjcnt + max_n1;                 // max_n1 + 1
   int* k2cnt = adjstart + max_n1 + 1;              // max_n12
   int* klist = k2cnt + max_n12;                    // per warp max_n1: atoms of one K1 list
+  float* xf = (float*)(klist + 8 * max_n1);        // 3 x max_n12, FP32 copies of xs
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
   const Counts cn = w.counts[c];
@@ -97,23 +115,26 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
   const long long offp = w.off_p[c], offa = w.off_a[c], rbase = w.off_k1[c] + c;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32, nw = blockDim.x / 32;
   for (int s = tid; s < n12; s += blockDim.x)
-    for (int d = 0; d < 3; ++d) xs[d * max_n12 + s] = w.site_x[3 * (sbase + s) + d];
+    for (int d = 0; d < 3; ++d) {
+      const double v = w.site_x[3 * (sbase + s) + d];
+      xs[d * max_n12 + s] = v;
+      xf[d * max_n12 + s] = (float)v;
+    }
   for (int e = tid; e < n1 * n1; e += blockDim.x) pid[(e / n1) * max_n1 + e % n1] = -1;
   __syncthreads();
   const double rc2 = p.r_scs * p.r_scs;
+  const float lo2 = (float)(rc2 * (1.0 - 1e-4)), hi2 = (float)(rc2 * (1.0 + 1e-4));
   // phase 1: per-row counts
   for (int i = warp; i < n1; i += nw) {
     int k1 = 0, k2 = 0;
     for (int j0 = 0; j0 < i; j0 += 32) {
       int j = j0 + lane;
-      double rx, ry, rz, r2;
-      bool in = j < i && scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+      bool in = j < i && scs_pair_in_screened(xf, xs, max_n12, i, j, lo2, hi2, rc2);
       k1 += __popc(__ballot_sync(0xffffffffu, in));
     }
     for (int j0 = n1; j0 < n12; j0 += 32) {
       int j = j0 + lane;
-      double rx, ry, rz, r2;
-      bool in = j < n12 && scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+      bool in = j < n12 && scs_pair_in_screened(xf, xs, max_n12, i, j, lo2, hi2, rc2);
       k2 += __popc(__ballot_sync(0xffffffffu, in));
     }
     if (lane == 0) { rowk1[i] = k1; rowcnt[i] = k1 + k2; }
@@ -125,7 +146,7 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
     rowstart[n1] = run;
   }
   __syncthreads();
-  // phase 2: write pairs in order with their geometry and damping
+  // phase 2a: pairs in order (row, partner) and their entry in the atom-pair radial table
   int* lst = klist + warp * max_n1;
   for (int i = warp; i < n1; i += nw) {
     int pos = rowstart[i];
@@ -140,43 +161,27 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
       int jb = pass == 0 ? 0 : n1, je = pass == 0 ? i : n12;
       for (int j0 = jb; j0 < je; j0 += 32) {
         int j = j0 + lane;
-        double rx = 0, ry = 0, rz = 0, r2 = 0;
-        bool in = j < je && scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+        bool in = j < je && scs_pair_in_screened(xf, xs, max_n12, i, j, lo2, hi2, rc2);
         unsigned m = __ballot_sync(0xffffffffu, in);
         if (in) {
           int slot = pos + __popc(m & ((1u << lane) - 1u));
           long long q = offp + slot;
-          double r = sqrt(r2);
-          const int aj = w.site_atom[sbase + j];
-          double fsr, dfsr, fin = 1.0, dfin = 0.0, f, dfr, dfs;
-          cutoff_buf(r, p.r_scs, p.r_buf, fsr, dfsr);
-          if (pass == 1) finner(r, p.r_inner, fin, dfin);
-          fermi(r, p.beta * (w.rvdw[ai] + w.rvdw[aj]), p.d, f, dfr, dfs);
-          double F = fin * fsr * (1.0 - f);
-          double dF = dfin * fsr * (1.0 - f) + fin * dfsr * (1.0 - f) - fin * fsr * dfr;
           w.pr_ij[2 * q] = i;
           w.pr_ij[2 * q + 1] = j;
-          double* g = w.pr_geo + 8 * q;
-          g[0] = rx; g[1] = ry; g[2] = rz; g[3] = r; g[4] = F; g[5] = dF; g[6] = 1.0 / r; g[7] = 0.0;
-          float2* gf = w.pr_gff + 6 * q;
-#pragma unroll
-          for (int u = 0; u < 7; ++u) {
-            if (u == 3) continue;
-            const ff v = ff_from_double(g[u]);
-            gf[u < 3 ? u : u - 1] = make_float2(v.hi, v.lo);
-          }
-          // the same atom pair in the radial table: the site of atom aj at displacement r in
-          // atom ai's own K1 list (none only if r ties r_SCS to rounding; then computed inline)
+          // the same atom pair in the radial table: the site of atom aj at displacement
+          // r = x_j - x_i in atom ai's own K1 list (periodic images of one atom are far apart,
+          // so an FP32 match is unambiguous; none only if r ties r_SCS to rounding)
+          const int aj = w.site_atom[sbase + j];
+          const float rxf = xf[j] - xf[i], ryf = xf[max_n12 + j] - xf[max_n12 + i],
+                      rzf = xf[2 * max_n12 + j] - xf[2 * max_n12 + i];
           int gi = -1;
-          {
-            for (int t = 1; t < na; ++t) {
-              if (lst[t] != aj) continue;
-              const double* xt = w.site_x + 3 * (ab + t);
-              const double dx = xt[0] - rx, dy = xt[1] - ry, dz = xt[2] - rz;
-              if (dx * dx + dy * dy + dz * dz < 1e-12) {
-                gi = (int)(w.off_k1[ai] + t);
-                break;
-              }
+          for (int t = 1; t < na; ++t) {
+            if (lst[t] != aj) continue;
+            const double* xt = w.site_x + 3 * (ab + t);
+            const float dx = (float)xt[0] - rxf, dy = (float)xt[1] - ryf, dz = (float)xt[2] - rzf;
+            if (dx * dx + dy * dy + dz * dz < 1e-4f) {
+              gi = (int)(w.off_k1[ai] + t);
+              break;
             }
           }
           w.pr_g[q] = gi;
@@ -191,6 +196,31 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
     }
   }
   if (tid == 0) w.prow[rbase + n1] = rowstart[n1];
+  __syncthreads();
+  // phase 2b: FP64 geometry and damping of every pair, one thread per pair
+  for (int t = tid; t < rowstart[n1]; t += blockDim.x) {
+    const long long q = offp + t;
+    const int i = w.pr_ij[2 * q], j = w.pr_ij[2 * q + 1];
+    double rx, ry, rz, r2;
+    scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
+    const double r = sqrt(r2);
+    const int ai = w.site_atom[sbase + i], aj = w.site_atom[sbase + j];
+    double fsr, dfsr, fin = 1.0, dfin = 0.0, f, dfr, dfs;
+    cutoff_buf(r, p.r_scs, p.r_buf, fsr, dfsr);
+    if (j >= n1) finner(r, p.r_inner, fin, dfin);
+    fermi(r, p.beta * (w.rvdw[ai] + w.rvdw[aj]), p.d, f, dfr, dfs);
+    const double F = fin * fsr * (1.0 - f);
+    const double dF = dfin * fsr * (1.0 - f) + fin * dfsr * (1.0 - f) - fin * fsr * dfr;
+    double* g = w.pr_geo + 8 * q;
+    g[0] = rx; g[1] = ry; g[2] = rz; g[3] = r; g[4] = F; g[5] = dF; g[6] = 1.0 / r; g[7] = 0.0;
+    float2* gf = w.pr_gff + 6 * q;
+#pragma unroll
+    for (int u = 0; u < 7; ++u) {
+      if (u == 3) continue;
+      const ff v = ff_from_double(g[u]);
+      gf[u < 3 ? u : u - 1] = make_float2(v.hi, v.lo);
+    }
+  }
   __syncthreads();
   // phase 3: adjacency rows (K1 partners of every coupled site, both directions)
   for (int i = warp; i < n1; i += nw) {
@@ -998,7 +1028,7 @@ __global__ void __launch_bounds__(256) k_scs_site_reduce(Work w, DevParams p, in
 // ---------------------------------------------------------------------------------------
 void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s) {
   if (w.n_atoms == 0) return;
-  size_t sm = sizeof(double) * 3 * (size_t)max_n12;
+  size_t sm = (sizeof(double) + sizeof(float)) * 3 * (size_t)max_n12;
   raise_smem_limit((const void*)k_scs_count, sm);
   k_scs_count<<<w.n_atoms, 256, sm, s>>>(w, p, max_n12);
 }
@@ -1006,7 +1036,8 @@ void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream
 void launch_scs_fill(const Work& w, const DevParams& p, int c0, int c1, int max_n12, int max_n1, cudaStream_t s) {
   if (c1 <= c0) return;
   size_t sm = sizeof(double) * 3 * (size_t)max_n12 +
-              sizeof(int) * ((size_t)max_n1 * max_n1 + 6 * (size_t)max_n1 + 2 + (size_t)max_n12 + 8 * (size_t)max_n1);
+              sizeof(int) * ((size_t)max_n1 * max_n1 + 6 * (size_t)max_n1 + 2 + (size_t)max_n12 + 8 * (size_t)max_n1) +
+              sizeof(float) * 3 * (size_t)max_n12;
   raise_smem_limit((const void*)k_scs_fill, sm);
   k_scs_fill<<<c1 - c0, 256, sm, s>>>(w, p, c0, max_n12, max_n1);
 }
