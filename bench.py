@@ -26,6 +26,10 @@ if ROOT not in sys.path:
 
 METRIC = "atoms/s for lMBD energy+forces on 1 GB300 (batched vs per-atom launch); serve p50/p99"
 FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (DFMA and DMMA), profiling recipe table
+FP32_PEAK_TFLOPS = 80.5          # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (unit counts and clock)
+# DRAM bytes (read + write) of the SCS phase (k_pair_radial, k_scs_fill, k_scs_factor) per atom:
+# ncu on the 512-atom box, profiles/scs_traffic_box512.md; scaled to a launch by atoms/launches
+SCS_DRAM_BYTES_PER_ATOM = 1.830e6
 WORKLOAD = ("periodic random box, 4096 atoms, 0.1 atoms/A^3, 4 species; r_SCS 5 A, MBD sphere 7 A "
             "(r_MBD,1 = r_MBD,2 = 7 A), 12 omega, n_max 6; FP64 energies + forces")
 SAMPLE_ATOMS = 64                # oracle sample: same density and cutoffs, same local problem sizes
@@ -270,14 +274,35 @@ def run_ours(args, world, rank, local):
     fp64 = ("scs", "chain", "adj_pair", "adj_scs")
     dom = max(fp64, key=lambda ph: phase_ms.get(ph, 0.0))
     avg_ms = phase_ms[dom] / max(1, phase_launch[dom])
-    flops_launch = phase_flops[dom] / max(1, phase_launch[dom])
-    achieved = flops_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
     kernel_names = {"scs": "k_scs_factor", "chain": "k_chain_oz2", "adj_pair": "k_mbd_adj_pair_oz2",
                     "adj_scs": "k_scs_adjoint2"}
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kernel_names[dom],
-                "peak_note": "nominal FP64 (DFMA/DMMA) of GB300 from the profiling recipe; a DFMA-chain "
-                             "probe measured 1.01 TFLOP/s at 1995 MHz"}
+    st_last = model.stats()
+    if dom == "scs":
+        # mixed-precision SCS: FP32 Cholesky and solves, FP64 residual and right-hand side.  The
+        # roofline is the sum of the two pipe-bound times: t* = W32 / P32 + W64 / P64.
+        nq = 13
+        n1 = model.site_counts(args.atoms)[:, 0].astype(float)
+        N1 = 3.0 * n1
+        w32 = nq * float(np.sum(N1 ** 3 / 3.0 + 18.0 * N1 ** 2))
+        pairs, adj = float(st_last["scs_pairs"]), float(st_last["scs_adjacency"])
+        w64 = nq * (60.0 * adj + 36.0 * (pairs - adj / 2.0) + 2.0 * pairs)
+        t_launch = avg_ms * 1e-3
+        t_star = (w32 / (FP32_PEAK_TFLOPS * 1e12) + w64 / (FP64_PEAK_TFLOPS * 1e12)) / phase_launch[dom] * args.steps
+        work = (w32 + w64) / phase_launch[dom] * args.steps
+        roofline = {"bound": "alu", "achieved": work / t_launch / 1e12, "peak": work / t_star / 1e12,
+                    "unit": "TFLOP/s", "frac": t_star / t_launch,
+                    "traffic": SCS_DRAM_BYTES_PER_ATOM * args.atoms * args.steps / phase_launch[dom],
+                    "kernel": kernel_names[dom],
+                    "peak_note": "composite of this phase's FP32 work (Cholesky, solves) at the nominal FP32 "
+                                 "peak (152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s) and its FP64 work "
+                                 "(residual, right-hand side) at the nominal FP64 peak 1.25 TFLOP/s",
+                    "work_fp32": w32, "work_fp64": w64}
+    else:
+        flops_launch = phase_flops[dom] / max(1, phase_launch[dom])
+        achieved = flops_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kernel_names[dom],
+                    "peak_note": "FP64-equivalent rate against the nominal FP64 peak"}
     phases = {ph: {"ms_per_step": phase_ms[ph] / args.steps, "launches_per_step": phase_launch[ph] // args.steps,
                    "tflops": (phase_flops[ph] / (phase_ms[ph] * 1e-3) / 1e12) if phase_ms[ph] > 0 and phase_flops[ph] > 0 else None}
               for ph in lmbd.PHASES}

@@ -107,6 +107,8 @@ typedef struct {
   int waves_scs;           /* waves of central atoms in the forward SCS stage                 */
   int waves_mbd;           /* waves of central atoms in the MBD stage (energy and adjoint)    */
   int scs_recomputed;      /* 1 when the SCS stage was evaluated again before its adjoint     */
+  long long scs_pairs;     /* SCS site pairs over all central atoms (r < r_SCS, K1 x (K1 u K2)) */
+  long long scs_adjacency; /* directed K1-K1 pair entries (two per K1-K1 pair)                 */
 } lmbd_stats;
 
 /* Fill *out with the defaults r_scs = 5, r_mbd1 = r_mbd2 = r_sphere = 7,

@@ -893,6 +893,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         cudaGetLastError();
       }
     S.n_sites = c->totals_h[7];
+    S.scs_pairs = c->totals_h[8];
+    S.scs_adjacency = c->totals_h[9];
     S.max_k1 = max_n1;
     S.max_sphere = max_ns;
     S.max_sites = c->site_cap;

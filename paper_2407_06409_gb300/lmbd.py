@@ -40,7 +40,8 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int * NPHASE), ("bytes_workspace", ctypes.c_double),
                 ("n_sites", ctypes.c_longlong), ("max_k1", ctypes.c_int), ("max_sphere", ctypes.c_int),
                 ("max_sites", ctypes.c_int), ("kernel_launches", ctypes.c_int), ("bytes_arena", ctypes.c_double),
-                ("waves_scs", ctypes.c_int), ("waves_mbd", ctypes.c_int), ("scs_recomputed", ctypes.c_int)]
+                ("waves_scs", ctypes.c_int), ("waves_mbd", ctypes.c_int), ("scs_recomputed", ctypes.c_int),
+                ("scs_pairs", ctypes.c_longlong), ("scs_adjacency", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         d = {}
