@@ -49,6 +49,7 @@ extern "C" {
 #define LMBD_ECAPACITY     5  /* more sites around one atom than the kernels support             */
 #define LMBD_EUNSUPPORTED  6  /* option not supported (e.g. series order out of range)           */
 #define LMBD_ESCRATCH      7  /* problem larger than the allocation-free entry point's scratch   */
+#define LMBD_EMODEL        8  /* Lorentzian frequency model not applicable (see below)           */
 
 #define LMBD_MAX_FREQ      64 /* maximum number of quadrature frequencies                        */
 #define LMBD_MAX_ORDER     10 /* maximum series order n_max                                      */
@@ -160,6 +161,22 @@ int lmbd_set_launch_mode(lmbd_ctx* ctx, int mode);
 #define LMBD_PREC_SLICED 1
 int lmbd_set_precision(lmbd_ctx* ctx, int mode);
 
+/* Frequency model of the screened polarisabilities.
+ * LMBD_FREQ_QUADRATURE (default): the SCS system is solved at omega = 0 and at every
+ *   quadrature node.
+ * LMBD_FREQ_LORENTZIAN: the paper's Lorentzian model (Sec. III.C, Eqs. alpha_SCS_freq and
+ *   char-freq): the SCS system is solved at omega = 0 and omega_ref (Hartree, > 0) only; for
+ *   every site the blended polarisability (Eq. full-pol) at the two frequencies defines
+ *   omega~_i = omega_ref / sqrt(alpha~(0)/alpha~(omega_ref) - 1), and
+ *   alpha~_i(omega) = alpha~_i(0) / (1 + (omega/omega~_i)^2) at the quadrature nodes.  Forces
+ *   are the exact gradient of that model.  A call in which some blended polarisability is
+ *   larger at omega_ref than at 0 (no real omega~) returns LMBD_EMODEL.  The paper treats
+ *   omega_ref as an empirical, element-dependent parameter.
+ * lmbd_get_central_polarizabilities then returns N x 2 columns (omega = 0, omega_ref).      */
+#define LMBD_FREQ_QUADRATURE 0
+#define LMBD_FREQ_LORENTZIAN 1
+int lmbd_set_frequency_model(lmbd_ctx* ctx, int model, double omega_ref);
+
 /* Device memory budget of the context in bytes (0 = the default: the device's free
  * memory at each call less 1 GiB).  Central atoms are processed in contiguous waves whose
  * per-centre arrays fit the budget: the SCS stage of every centre first (its central
@@ -185,7 +202,8 @@ int lmbd_set_profiling(lmbd_ctx* ctx, int on);
 
 /* Central polarisabilities alpha_I,k(omega) of the last call (Sec. III.B):
  * N x (n_freq + 1) row-major; column 0 is omega = 0, then the quadrature
- * nodes in increasing order.  out: device or host.                          */
+ * nodes in increasing order (N x 2: omega = 0, omega_ref with the Lorentzian
+ * frequency model).  out: device or host.                                   */
 int lmbd_get_central_polarizabilities(lmbd_ctx* ctx, double* out, void* stream);
 
 /* Site counts of the last call, N x 4 int32 row-major:

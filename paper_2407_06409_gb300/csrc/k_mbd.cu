@@ -42,12 +42,34 @@ __global__ void __launch_bounds__(256) k_mbd_prepare(Work w, DevParams p, int c0
       double u = sqrt(x0 * x0 + x1 * x1 + x2 * x2) / rscs;
       fs = 3.0 * u * u - 2.0 * u * u * u;
     }
-    for (int q = 0; q < p.nq; ++q) {
-      double aI = w.alphaI[(long long)a * p.nq + q];
-      double at = aI;
-      if (s < n1) at = (1.0 - fs) * w.alphaK[(offk1 + s) * p.nq + q] + fs * aI;
-      w.alphaT[(offs + s) * p.nq + q] = at;
-      w.dsq[(offs + s) * p.nq + q] = sqrt(at);
+    if (!p.lorentz) {
+      for (int q = 0; q < p.nq; ++q) {
+        double aI = w.alphaI[(long long)a * p.nqs + q];
+        double at = aI;
+        if (s < n1) at = (1.0 - fs) * w.alphaK[(offk1 + s) * p.nqs + q] + fs * aI;
+        w.alphaT[(offs + s) * p.nq + q] = at;
+        w.dsq[(offs + s) * p.nq + q] = sqrt(at);
+      }
+    } else {
+      // Lorentzian model (Sec. III.C): the blend at omega = 0 and omega_ref, then
+      // alpha~(omega) = alpha~(0) / (1 + (omega/omega~)^2) with
+      // (omega/omega~)^2 = (omega/omega_ref)^2 (alpha~(0)/alpha~(omega_ref) - 1) (Eq. char-freq)
+      double ab[2];
+      for (int qs = 0; qs < 2; ++qs) {
+        const double aI = w.alphaI[(long long)a * 2 + qs];
+        ab[qs] = (s < n1) ? (1.0 - fs) * w.alphaK[(offk1 + s) * 2 + qs] + fs * aI : aI;
+      }
+      double ratio = ab[0] / ab[1];
+      if (!(ratio >= 1.0)) {   // alpha~ rises with frequency: Eq. char-freq has no real solution
+        atomicOr(w.status, LMBD_FLAG_MODEL);
+        ratio = 1.0;
+      }
+      for (int q = 0; q < p.nq; ++q) {
+        const double u = p.omega[q] / p.omega_ref;
+        const double at = ab[0] / (1.0 + u * u * (ratio - 1.0));
+        w.alphaT[(offs + s) * p.nq + q] = at;
+        w.dsq[(offs + s) * p.nq + q] = sqrt(at);
+      }
     }
     rt[s] = w.r0[a] * cbrt(w.alphaT[(offs + s) * p.nq] / w.a0[a]);
   }
@@ -476,17 +498,42 @@ __global__ void __launch_bounds__(256) k_mbd_adj_blend(Work w, DevParams p, int 
       fs = 3.0 * u * u - 2.0 * u * u * u;
       dfs = (6.0 * u - 6.0 * u * u) / p.r_scs;
     }
+    // dL/d alpha~ at the frequencies of the SCS solves
+    double gs[LMBD_MAXQ];
+    if (!p.lorentz) {
+      for (int q = 0; q < p.nq; ++q) gs[q] = (q == 0) ? gb0 : w.gbar[(offs + s) * p.nq + q];
+    } else {
+      // reverse of the Lorentzian model: alpha~_q = a0 / D_q, D_q = 1 + u_q (a0/ar - 1),
+      // d alpha~_q / d a0 = 1/D_q - a0 u_q / (ar D_q^2), d alpha~_q / d ar = a0^2 u_q / (ar^2 D_q^2)
+      double ab[2];
+      for (int qs = 0; qs < 2; ++qs) {
+        const double aI = w.alphaI[(long long)a * 2 + qs];
+        ab[qs] = (s < n1) ? (1.0 - fs) * w.alphaK[(offk1 + s) * 2 + qs] + fs * aI : aI;
+      }
+      const double a0 = ab[0], ar = ab[1];
+      const double ratio = fmax(a0 / ar, 1.0);
+      double g0 = gb0, g1 = 0.0;
+      for (int q = 1; q < p.nq; ++q) {
+        const double g = w.gbar[(offs + s) * p.nq + q];
+        const double u = (p.omega[q] / p.omega_ref) * (p.omega[q] / p.omega_ref);
+        const double D = 1.0 + u * (ratio - 1.0);
+        g0 += g * (1.0 / D - a0 * u / (ar * D * D));
+        g1 += g * (a0 * a0 * u / (ar * ar * D * D));
+      }
+      gs[0] = g0;
+      gs[1] = g1;
+    }
     double gr = 0.0;
-    for (int q = 0; q < p.nq; ++q) {
-      double g = (q == 0) ? gb0 : w.gbar[(offs + s) * p.nq + q];
+    for (int q = 0; q < p.nqs; ++q) {
+      const double g = gs[q];
       if (s < n1) {
-        double aK = w.alphaK[(offk1 + s) * p.nq + q];
-        double aI = w.alphaI[(long long)a * p.nq + q];
-        w.alphaK_bar[(offk1 + s) * p.nq + q] = (1.0 - fs) * g;
-        if (fs != 0.0) atomicAdd(&w.alphaI_bar[(long long)a * p.nq + q], fs * g);
+        double aK = w.alphaK[(offk1 + s) * p.nqs + q];
+        double aI = w.alphaI[(long long)a * p.nqs + q];
+        w.alphaK_bar[(offk1 + s) * p.nqs + q] = (1.0 - fs) * g;
+        if (fs != 0.0) atomicAdd(&w.alphaI_bar[(long long)a * p.nqs + q], fs * g);
         gr += dfs * (aI - aK) * g;
       } else {
-        atomicAdd(&w.alphaI_bar[(long long)a * p.nq + q], g);
+        atomicAdd(&w.alphaI_bar[(long long)a * p.nqs + q], g);
       }
     }
     if (s < n1 && s > 0 && gr != 0.0) {

@@ -21,11 +21,11 @@ __global__ void k_free_atom(Work w, DevParams p) {
   double a0 = w.table[3 * s + 0], c6 = w.table[3 * s + 1], r0 = w.table[3 * s + 2];
   double om = 4.0 * c6 / (3.0 * a0 * a0);
   const double c = 0.26596152026762182;  // sqrt(2/pi)/3
-  for (int q = 0; q < p.nq; ++q) {
-    double u = p.omega[q] / om;
+  for (int q = 0; q < p.nqs; ++q) {   // at the frequencies of the SCS solves
+    double u = p.omega_s[q] / om;
     double ab = a0 * nu / (1.0 + u * u);
-    w.abar[a * p.nq + q] = ab;
-    w.sig[a * p.nq + q] = cbrt(c * ab);
+    w.abar[a * p.nqs + q] = ab;
+    w.sig[a * p.nqs + q] = cbrt(c * ab);
   }
   w.rvdw[a] = r0 * cbrt(nu);
   w.a0[a] = a0;
@@ -406,5 +406,5 @@ __global__ void k_offsets(Work w, int nq) {
 
 void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s) {
   if (w.n_atoms == 0) return;
-  k_offsets<<<1, OFF_T, 0, s>>>(w, p.nq);
+  k_offsets<<<1, OFF_T, 0, s>>>(w, p.nqs);
 }

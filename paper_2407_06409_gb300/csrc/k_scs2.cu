@@ -568,7 +568,7 @@ __device__ void scs2_residual(const Work& w, const DevParams& p, int n1, long lo
       for (int u = 0; u < 4; ++u) {
         if (pp[u] >= 0) {
           const double* g = w.pr_geo + 8 * (offp + pp[u]);
-          const double* rad = w.pr_rad + 2 * ((offp + pp[u]) * p.nq + q);
+          const double* rad = w.pr_rad + 2 * ((offp + pp[u]) * p.nqs + q);
           gx[u] = g[0]; gy[u] = g[1]; gz[u] = g[2]; fa[u] = rad[0]; fb[u] = rad[1];
         } else {
           gx[u] = gy[u] = gz[u] = fa[u] = fb[u] = 0.0;
@@ -612,7 +612,7 @@ __device__ void scs2_residual_update(const Work& w, const DevParams& p, int n1, 
       const int j = w.adj[2 * (offa + t)];
       const long long pq = offp + w.adj[2 * (offa + t) + 1];
       const float2* gf = w.pr_gff + 6 * pq;
-      const float2* rf = w.pr_rad_ff + 2 * (pq * p.nq + q);
+      const float2* rf = w.pr_rad_ff + 2 * (pq * p.nqs + q);
       const ff rx = ff_make(gf[0].x, gf[0].y), ry = ff_make(gf[1].x, gf[1].y), rz = ff_make(gf[2].x, gf[2].y);
       const ff fa = ff_make(rf[0].x, rf[0].y), fb = ff_make(rf[1].x, rf[1].y);
       const float d0 = sm.y[9 * j + c], d1 = sm.y[9 * j + 3 + c], d2 = sm.y[9 * j + 6 + c];
@@ -713,17 +713,17 @@ __global__ void __launch_bounds__(128) k_pair_radial(Work w, DevParams p) {
   if (a >= w.n_atoms) return;
   const int n1 = w.counts[a].n1;
   const long long ab = (long long)a * w.site_cap, base = w.off_k1[a];
-  for (int e = threadIdx.x; e < n1 * p.nq; e += blockDim.x) {
-    const int s = e / p.nq, q = e % p.nq;
+  for (int e = threadIdx.x; e < n1 * p.nqs; e += blockDim.x) {
+    const int s = e / p.nqs, q = e % p.nqs;
     if (s == 0) continue;
     const double* x = w.site_x + 3 * (ab + s);
     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x[0], x[0]), __dmul_rn(x[1], x[1])), __dmul_rn(x[2], x[2]));
     const double r = sqrt(r2);
     const int b = w.site_atom[ab + s];
-    const double sa = w.sig[(long long)a * p.nq + q], sb = w.sig[(long long)b * p.nq + q];
+    const double sa = w.sig[(long long)a * p.nqs + q], sb = w.sig[(long long)b * p.nqs + q];
     double A0, B0, dA0, dB0;
     tsr_radial_fast(r, 1.0 / r, sa * sa + sb * sb, A0, B0, dA0, dB0);
-    const long long o = (base + s) * p.nq + q;
+    const long long o = (base + s) * p.nqs + q;
     w.rad_ab[2 * o] = A0;
     w.rad_ab[2 * o + 1] = B0;
     const double v[4] = {A0, B0, dA0, dB0};
@@ -741,8 +741,8 @@ __global__ void __launch_bounds__(128) k_pair_radial(Work w, DevParams p) {
 __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, const int* order, int c0, int max_n1,
                                                   int max_n12) {
   extern __shared__ unsigned char smem_raw[];
-  const int c = order ? order[c0 + blockIdx.x / p.nq] : c0 + blockIdx.x / p.nq;
-  const int q = blockIdx.x % p.nq;
+  const int c = order ? order[c0 + blockIdx.x / p.nqs] : c0 + blockIdx.x / p.nqs;
+  const int q = blockIdx.x % p.nqs;
   if (c >= w.n_atoms) return;
   const Counts cn = w.counts[c];
   const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
@@ -755,7 +755,7 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
   if (tid == 0) { bad = 0; fail = 0; }
   for (int s = tid; s < n12; s += blockDim.x) {
     int a = w.site_atom[sbase + s];
-    const double ab = w.abar[(long long)a * p.nq + q];
+    const double ab = w.abar[(long long)a * p.nqs + q];
     sm.ab[s] = ab;
     if (s < n1) sm.iab[s] = 1.0 / ab;
   }
@@ -771,23 +771,23 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
     const int gi = w.pr_g[pq];
     double A0, B0;
     if (gi >= 0) {
-      const double* ra = w.rad_ab + 2 * ((long long)gi * p.nq + q);
+      const double* ra = w.rad_ab + 2 * ((long long)gi * p.nqs + q);
       A0 = ra[0];
       B0 = ra[1];
     } else {
       double dA0, dB0;
-      const double si = w.sig[(long long)w.site_atom[sbase + i] * p.nq + q];
-      const double sj = w.sig[(long long)w.site_atom[sbase + j] * p.nq + q];
+      const double si = w.sig[(long long)w.site_atom[sbase + i] * p.nqs + q];
+      const double sj = w.sig[(long long)w.site_atom[sbase + j] * p.nqs + q];
       tsr_radial_fast(g[3], g[6], si * si + sj * sj, A0, B0, dA0, dB0);
     }
-    double* rad = w.pr_rad + 2 * (pq * p.nq + q);
+    double* rad = w.pr_rad + 2 * (pq * p.nqs + q);
     rad[0] = g[4] * A0;
     rad[1] = g[4] * B0;
     {
-      float2* rf = w.pr_rad_ff + 2 * (pq * p.nq + q);
+      float2* rf = w.pr_rad_ff + 2 * (pq * p.nqs + q);
       ff fa, fb;
       if (gi >= 0) {   // from the float-float tables, on the FP32 pipe
-        const float2* ra = w.rad_ff + 4 * ((long long)gi * p.nq + q);
+        const float2* ra = w.rad_ff + 4 * ((long long)gi * p.nqs + q);
         const float2 Fg = w.pr_gff[6 * pq + 3];
         const ff F = ff_make(Fg.x, Fg.y);
         fa = ff_mul(F, ff_make(ra[0].x, ra[0].y));
@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
       const long long pq = offp + t;
       const int j = w.pr_ij[2 * pq + 1];
       const double* g = w.pr_geo + 8 * pq;
-      const double* rad = w.pr_rad + 2 * (pq * p.nq + q);
+      const double* rad = w.pr_rad + 2 * (pq * p.nqs + q);
       const double abj = sm.ab[j];
       ad += abj * rad[0];
       const double wb = abj * rad[1] * g[c];
@@ -843,12 +843,12 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
   scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail);
   // outputs: X, alpha_K, alpha_I and the FP32 factor for the adjoint
   const long long offk1 = w.off_k1[c];
-  double* X = w.xsol + offk1 * p.nq * 9 + (long long)q * N1 * 3;
+  double* X = w.xsol + offk1 * p.nqs * 9 + (long long)q * N1 * 3;
   for (int e = tid; e < N1 * 3; e += blockDim.x) X[e] = sm.x[e];
   for (int i = tid; i < n1; i += blockDim.x) {
     double a = (sm.x[9 * i + 0] + sm.x[9 * i + 4] + sm.x[9 * i + 8]) / 3.0;
-    w.alphaK[(offk1 + i) * p.nq + q] = a;
-    if (i == 0) w.alphaI[(long long)c * p.nq + q] = a;
+    w.alphaK[(offk1 + i) * p.nqs + q] = a;
+    if (i == 0) w.alphaI[(long long)c * p.nqs + q] = a;
   }
   float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
   for (long long e = tid; e < nA; e += blockDim.x) Lg[e] = sm.A[e];
@@ -861,8 +861,8 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
 __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, const int* order, int c0, int max_n1,
                                                   int max_n12) {
   extern __shared__ unsigned char smem_raw[];
-  const int c = order ? order[c0 + blockIdx.x / p.nq] : c0 + blockIdx.x / p.nq;
-  const int q = blockIdx.x % p.nq;
+  const int c = order ? order[c0 + blockIdx.x / p.nqs] : c0 + blockIdx.x / p.nqs;
+  const int q = blockIdx.x % p.nqs;
   if (c >= w.n_atoms) return;
   const Counts cn = w.counts[c];
   const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
   if (tid == 0) fail = 0;
   for (int s = tid; s < n12; s += blockDim.x) {
     int a = w.site_atom[sbase + s];
-    const double ab = w.abar[(long long)a * p.nq + q];
+    const double ab = w.abar[(long long)a * p.nqs + q];
     sm.ab[s] = ab;
     if (s < n1) sm.iab[s] = 1.0 / ab;
   }
@@ -885,14 +885,14 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
   for (int i = tid; i < N1; i += blockDim.x) sm.sinv[i] = 1.f / Lg[packed_idx(i, i)];
   __syncthreads();
   blockinv32(sm.A, N1, sm.sinv, sm.binv);
-  const double* X = w.xsol + offk1 * p.nq * 9 + (long long)q * N1 * 3;
+  const double* X = w.xsol + offk1 * p.nqs * 9 + (long long)q * N1 * 3;
   for (int e = tid; e < N1 * 3; e += blockDim.x) {
     sm.xs[e] = X[e];
     int row = e / 3, col = e % 3, i = row / 3, al = row % 3;
     double gval = 0.0;
     if (al == col) {
-      gval = w.alphaK_bar[(offk1 + i) * p.nq + q];
-      if (i == 0) gval += w.alphaI_bar[(long long)c * p.nq + q];
+      gval = w.alphaK_bar[(offk1 + i) * p.nqs + q];
+      if (i == 0) gval += w.alphaI_bar[(long long)c * p.nqs + q];
       gval *= (1.0 / 3.0);
     }
     sm.rhs[e] = gval;
@@ -913,7 +913,7 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
     xf[e] = ff_from_double(xv);
   }
   __syncthreads();
-  double* gst = w.gstage + (offp * p.nq + (long long)q * np) * 3;
+  double* gst = w.gstage + (offp * p.nqs + (long long)q * np) * 3;
   for (int t = tid; t < np; t += blockDim.x) {
     const long long pq = offp + t;
     const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
@@ -954,13 +954,13 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
     const ff F = ff_make(gf[3].x, gf[3].y), dF = ff_make(gf[4].x, gf[4].y), ir = ff_make(gf[5].x, gf[5].y);
     ff A0, B0, dA0, dB0;
     if (gi >= 0) {
-      const float2* ra = w.rad_ff + 4 * ((long long)gi * p.nq + q);
+      const float2* ra = w.rad_ff + 4 * ((long long)gi * p.nqs + q);
       A0 = ff_make(ra[0].x, ra[0].y); B0 = ff_make(ra[1].x, ra[1].y);
       dA0 = ff_make(ra[2].x, ra[2].y); dB0 = ff_make(ra[3].x, ra[3].y);
     } else {
       const double* g = w.pr_geo + 8 * pq;
-      const double si = w.sig[(long long)w.site_atom[sbase + i] * p.nq + q];
-      const double sj = w.sig[(long long)w.site_atom[sbase + j] * p.nq + q];
+      const double si = w.sig[(long long)w.site_atom[sbase + i] * p.nqs + q];
+      const double sj = w.sig[(long long)w.site_atom[sbase + j] * p.nqs + q];
       double a0d, b0d, da0d, db0d;
       tsr_radial_fast(g[3], g[6], si * si + sj * sj, a0d, b0d, da0d, db0d);
       A0 = ff_from_double(a0d); B0 = ff_from_double(b0d); dA0 = ff_from_double(da0d); dB0 = ff_from_double(db0d);
@@ -981,7 +981,7 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
   __syncthreads();
   // per site (fixed order): owner of its row's pairs (-g), partner of K1 pairs owned by later
   // rows (+g, from the adjacency row) and of K2 pairs (+g, from the reverse list)
-  double* sgq = w.sgq + (sbase * p.nq + q) * 3;
+  double* sgq = w.sgq + (sbase * p.nqs + q) * 3;
   for (int s = tid; s < n12; s += blockDim.x) {
     double gx = 0.0, gy = 0.0, gz = 0.0;
     if (s < n1) {
@@ -998,9 +998,9 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
         gx += gst[3 * pp]; gy += gst[3 * pp + 1]; gz += gst[3 * pp + 2];
       }
     }
-    sgq[(long long)s * p.nq * 3] = gx;
-    sgq[(long long)s * p.nq * 3 + 1] = gy;
-    sgq[(long long)s * p.nq * 3 + 2] = gz;
+    sgq[(long long)s * p.nqs * 3] = gx;
+    sgq[(long long)s * p.nqs * 3 + 1] = gy;
+    sgq[(long long)s * p.nqs * 3 + 2] = gz;
   }
   if (tid == 0 && fail) atomicOr(w.status, LMBD_FLAG_NOT_CONVERGED);
 }
@@ -1012,9 +1012,9 @@ __global__ void __launch_bounds__(256) k_scs_site_reduce(Work w, DevParams p, in
   const int n12 = w.counts[c].n12;
   const long long sbase = (long long)c * w.site_cap;
   for (int s = threadIdx.x; s < n12; s += blockDim.x) {
-    const double* g = w.sgq + (sbase + s) * p.nq * 3;
+    const double* g = w.sgq + (sbase + s) * p.nqs * 3;
     double gx = 0.0, gy = 0.0, gz = 0.0;
-    for (int q = 0; q < p.nq; ++q) {
+    for (int q = 0; q < p.nqs; ++q) {
       gx += g[3 * q];
       gy += g[3 * q + 1];
       gz += g[3 * q + 2];
@@ -1057,7 +1057,7 @@ void launch_scs_factor(const Work& w, const DevParams& p, const int* order, int 
   if (c1 <= c0) return;
   size_t sm = scs2_smem_bytes(max_n1, max_n12, false);
   raise_smem_limit((const void*)k_scs_factor, sm);
-  k_scs_factor<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
+  k_scs_factor<<<(c1 - c0) * p.nqs, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
 }
 
 void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1,
@@ -1065,7 +1065,7 @@ void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, in
   if (c1 <= c0) return;
   size_t sm = scs2_smem_bytes(max_n1, max_n12, true);
   raise_smem_limit((const void*)k_scs_adjoint2, sm);
-  k_scs_adjoint2<<<(c1 - c0) * p.nq, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
+  k_scs_adjoint2<<<(c1 - c0) * p.nqs, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
 }
 
 void launch_scs_site_reduce(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {

@@ -47,6 +47,9 @@ struct Ctx {
   int launch_mode = LMBD_LAUNCH_BATCHED;
   int profiling = 0;
   int precision = LMBD_PREC_SLICED;
+  int lorentz = 0;                 // frequency model (lmbd_set_frequency_model)
+  double omega_ref = 0.0;
+  int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
   int site_cap = 0;
   int last_n = 0;
@@ -212,6 +215,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 struct Layout {
   int nq, ncv, nvec, ncol, kp_pair, st, dig_p, site_cap;
   bool forces, sliced_chain, sliced_pair;
+  int nqs;   // frequencies of the SCS solves (stage-1 arrays)
 
   // stage 1 (SCS): pair lists, FP32 factors and solutions of centres [c0, c1)
   size_t stage1(const Offs& o, int c0, int c1, char* base, Work* w) const {
@@ -223,8 +227,8 @@ struct Layout {
     float* lfac = cv.take<float>(o.span(O_B, c0, c1), o.at(O_B, c0));
     int* pr_ij = cv.take<int>(2 * (np + 1), 2 * p0);
     double* pr_geo = cv.take<double>(8 * (np + 1), 8 * p0);
-    double* pr_rad = cv.take<double>(2LL * nq * (np + 1), 2LL * nq * p0);
-    float2* pr_rad_ff = cv.take<float2>(2LL * nq * (np + 1), 2LL * nq * p0);
+    double* pr_rad = cv.take<double>(2LL * nqs * (np + 1), 2LL * nqs * p0);
+    float2* pr_rad_ff = cv.take<float2>(2LL * nqs * (np + 1), 2LL * nqs * p0);
     int* pr_g = cv.take<int>(np + 1, p0);
     float2* pr_gff = cv.take<float2>(6 * (np + 1), 6 * p0);
     int* k2rev = cv.take<int>(np + 1, p0);
@@ -233,7 +237,7 @@ struct Layout {
     int* arow = cv.take<int>(nk + n, k0 + c0);
     int* adj = cv.take<int>(2 * (na + 1), 2 * a0);
     int* k2ptr = cv.take<int>(n * site_cap + 1, (long long)c0 * site_cap);
-    double* xsol = cv.take<double>(9LL * nq * nk, 9LL * nq * k0);
+    double* xsol = cv.take<double>(9LL * nqs * nk, 9LL * nqs * k0);
     if (w) {
       w->lfac = lfac;
       w->pr_ij = pr_ij;
@@ -257,8 +261,8 @@ struct Layout {
   size_t scs_adjoint(const Offs& o, int c0, int c1, char* base, Work* w) const {
     Carver cv{base, 0};
     const long long p0 = o.at(O_P, c0), np = o.span(O_P, c0, c1);
-    double* gstage = cv.take<double>(3LL * nq * (np + 1), 3LL * nq * p0);
-    double* sgq = cv.take<double>(3LL * nq * (c1 - c0) * site_cap, 3LL * nq * c0 * site_cap);
+    double* gstage = cv.take<double>(3LL * nqs * (np + 1), 3LL * nqs * p0);
+    double* sgq = cv.take<double>(3LL * nqs * (c1 - c0) * site_cap, 3LL * nqs * c0 * site_cap);
     if (w) {
       w->gstage = gstage;
       w->sgq = sgq;
@@ -418,6 +422,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     dp.omega[q + 1] = c->omega[q];
     dp.cweight[q + 1] = LMBD_HARTREE * c->weight[q] / (2.0 * pi);
   }
+  dp.lorentz = c->lorentz;
+  dp.omega_ref = c->omega_ref;
+  dp.nqs = c->lorentz ? 2 : nq;
+  for (int q = 0; q < dp.nqs; ++q) dp.omega_s[q] = c->lorentz ? (q == 0 ? 0.0 : c->omega_ref) : dp.omega[q];
+  c->last_nqs = dp.nqs;
 
   // ---- search grid ------------------------------------------------------------------------
   Grid g{};
@@ -624,7 +633,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
 
   // ---- waves under the memory budget --------------------------------------------------------
   const Layout L{nq, ncv, nvec, ncol, (ncol + 15) / 16 * 16, ST, DIG_P, c->site_cap, forces, sliced_chain,
-                 sliced && ncol > 0};
+                 sliced && ncol > 0, dp.nqs};
   auto s1 = [&](int a, int b) { return L.stage1(o, a, b, nullptr, nullptr); };
   auto s1x = [&](int a, int b) { return forces ? L.scs_adjoint(o, a, b, nullptr, nullptr) : (size_t)0; };
   auto s2 = [&](int a, int b) { return L.stage2(o, a, b, nullptr, nullptr, nullptr); };
@@ -872,11 +881,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     lmbd_stats& S = c->stats;
     for (int i = 0; i < N; ++i) {
       double n1 = 3.0 * hc[i].n1, n = 3.0 * hc[i].ns;
-      S.flops[LMBD_PHASE_SCS] += nq * (n1 * n1 * n1 / 3.0 + 6.0 * n1 * n1);
+      S.flops[LMBD_PHASE_SCS] += dp.nqs * (n1 * n1 * n1 / 3.0 + 6.0 * n1 * n1);
       S.flops[LMBD_PHASE_CHAIN] += (nvec - 1) * 2.0 * n * n * ncv;
       if (forces) {
         S.flops[LMBD_PHASE_ADJ_PAIR] += 2.0 * (n * (n + 48.0) / 2.0) * ncol;   // lower tiles of P Q^T
-        S.flops[LMBD_PHASE_ADJ_SCS] += nq * 6.0 * n1 * n1;
+        S.flops[LMBD_PHASE_ADJ_SCS] += dp.nqs * 6.0 * n1 * n1;
       }
     }
     for (int ph = 0; ph < LMBD_NPHASE; ++ph) {
@@ -902,6 +911,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     S.bytes_workspace = (double)(c->whole_bytes() + c->arena.bytes);
   }
   if (*c->status_h & (LMBD_FLAG_NOT_SPD | LMBD_FLAG_NOT_CONVERGED)) return LMBD_NOT_SPD;
+  if (*c->status_h & LMBD_FLAG_MODEL) return LMBD_EMODEL;
   return LMBD_OK;
 }
 
@@ -1007,6 +1017,19 @@ int lmbd_set_precision(lmbd_ctx* ctx, int mode) {
   return LMBD_OK;
 }
 
+int lmbd_set_frequency_model(lmbd_ctx* ctx, int model, double omega_ref) {
+  if (!ctx) return LMBD_EINVAL;
+  if (model == LMBD_FREQ_QUADRATURE) {
+    ctx->c.lorentz = 0;
+    ctx->c.omega_ref = 0.0;
+    return LMBD_OK;
+  }
+  if (model != LMBD_FREQ_LORENTZIAN || !(omega_ref > 0.0) || !std::isfinite(omega_ref)) return LMBD_EINVAL;
+  ctx->c.lorentz = 1;
+  ctx->c.omega_ref = omega_ref;
+  return LMBD_OK;
+}
+
 int lmbd_set_memory_budget(lmbd_ctx* ctx, size_t bytes) {
   if (!ctx) return LMBD_EINVAL;
   ctx->c.mem_budget = bytes;
@@ -1041,7 +1064,7 @@ int lmbd_get_central_polarizabilities(lmbd_ctx* ctx, double* out, void* stream) 
   if (c.last_n == 0) return LMBD_OK;
   cudaStream_t s = (cudaStream_t)stream;
   bool dev = is_device_ptr(out);
-  if (cudaMemcpyAsync(out, c.alphaI.p, sizeof(double) * c.last_n * (c.n_freq + 1),
+  if (cudaMemcpyAsync(out, c.alphaI.p, sizeof(double) * c.last_n * c.last_nqs,
                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
@@ -1103,6 +1126,7 @@ const char* lmbd_status_string(int status) {
     case LMBD_ECAPACITY: return "too many sites around one atom for the kernels";
     case LMBD_EUNSUPPORTED: return "unsupported option";
     case LMBD_ESCRATCH: return "problem exceeds the fixed scratch of the allocation-free entry point";
+    case LMBD_EMODEL: return "Lorentzian frequency model not applicable: a polarisability rises between 0 and omega_ref";
     default: return "unknown status";
   }
 }
@@ -1198,11 +1222,14 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   dp.r2_list_ang = rlist * rlist;
   dp.n_freq = n_freq;
   dp.nq = nq;
+  dp.nqs = nq;
+  dp.lorentz = 0;
   dp.order = 2;
   dp.n_species = n_species;
   double om[LMBD_MAX_FREQ], wt[LMBD_MAX_FREQ];
   gauss_legendre_fixed(n_freq, P.omega_scale, om, wt);
   for (int q = 0; q < n_freq; ++q) dp.omega[q + 1] = om[q];
+  for (int q = 0; q < nq; ++q) dp.omega_s[q] = dp.omega[q];
 
   // search grid
   Grid g{};

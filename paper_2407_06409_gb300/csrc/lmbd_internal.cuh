@@ -14,6 +14,7 @@
 #define LMBD_FLAG_CAPACITY 2
 #define LMBD_FLAG_COINCIDENT 4
 #define LMBD_FLAG_NOT_CONVERGED 8
+#define LMBD_FLAG_MODEL 16          // Lorentzian model not applicable: alpha~(0) < alpha~(omega_ref)
 
 struct DevParams {
   // lengths in bohr
@@ -26,6 +27,12 @@ struct DevParams {
   int n_species;
   double omega[LMBD_MAXQ];
   double cweight[LMBD_MAXQ];  // hartree->eV * w_q / (2 pi) for q >= 1, 0 for q = 0
+  // frequencies of the SCS solves: every omega[q] (nqs = nq), or with the Lorentzian model of
+  // Sec. III.C (lorentz = 1) only 0 and omega_ref (nqs = 2)
+  int nqs;
+  int lorentz;
+  double omega_ref;
+  double omega_s[LMBD_MAXQ];
 };
 
 // Geometry of the neighbour search (host-computed from the cell).

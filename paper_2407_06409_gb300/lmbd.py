@@ -17,6 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblmbd.so")
 
 LMBD_OK, LMBD_EINVAL, LMBD_ENOMEM, LMBD_NOT_SPD, LMBD_ECUDA, LMBD_ECAPACITY, LMBD_EUNSUPPORTED = range(7)
+LMBD_ESCRATCH, LMBD_EMODEL = 7, 8
+FREQ_QUADRATURE, FREQ_LORENTZIAN = 0, 1
 LAUNCH_BATCHED, LAUNCH_PER_ATOM = 0, 1
 PREC_FP64, PREC_SLICED = 0, 1
 
@@ -79,6 +81,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_profiling.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_precision.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_memory_budget.argtypes = [_P, ctypes.c_size_t]
+        L.lmbd_set_frequency_model.argtypes = [_P, ctypes.c_int, ctypes.c_double]
         L.lmbd_release_workspace.argtypes = [_P]
         L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
         L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
@@ -87,7 +90,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
-                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget",
+                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
@@ -172,6 +175,11 @@ class LMBD:
         """Device bytes this context may hold (0 = free memory less 1 GiB); larger inputs run in waves."""
         _check(lib().lmbd_set_memory_budget(self._h, int(nbytes)), "lmbd_set_memory_budget")
 
+    def set_frequency_model(self, model: int, omega_ref: float = 0.0) -> None:
+        """FREQ_QUADRATURE (SCS at every node) or FREQ_LORENTZIAN (SCS at 0 and omega_ref, Ha)."""
+        _check(lib().lmbd_set_frequency_model(self._h, int(model), float(omega_ref)), "lmbd_set_frequency_model")
+        self._scs_columns = 2 if model == FREQ_LORENTZIAN else self.n_freq + 1
+
     def release_workspace(self) -> None:
         """Free the context's device workspaces (the next call allocates again)."""
         _check(lib().lmbd_release_workspace(self._h), "lmbd_release_workspace")
@@ -213,7 +221,7 @@ class LMBD:
 
     def central_polarizabilities(self, n: int, device="cpu"):
         torch = _torch()
-        out = torch.empty((n, self.n_freq + 1), dtype=torch.float64, device=device)
+        out = torch.empty((n, getattr(self, "_scs_columns", self.n_freq + 1)), dtype=torch.float64, device=device)
         st = _stream_ptr(None, out.device)
         _check(lib().lmbd_get_central_polarizabilities(self._h, ctypes.c_void_p(out.data_ptr()), st),
                "lmbd_get_central_polarizabilities")
