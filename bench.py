@@ -226,12 +226,10 @@ def run_ours(args, world, rank, local):
     barrier()
     ms_total = ev0.elapsed_time(ev1)
     model.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    from paper_2407_06409_gb300.replicas import job_throughput
+    sec, value = job_throughput(ms_total * 1e-3, args.atoms * args.steps, device=dev)
+    ms_total = sec * 1e3
     ms_step = ms_total / args.steps
-    value = world * args.atoms * args.steps / (ms_total * 1e-3)
 
     # ---- end to end: pinned host buffers, copies inside the timed region ------------------
     pos_h = torch.tensor(s.positions).pin_memory()
@@ -247,11 +245,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * args.atoms * args.steps / e2e_s, "unit": "atoms/s",
+    e2e_s, e2e_value = job_throughput(e2e_s, args.atoms * args.steps, device=dev)
+    e2e = {"value": e2e_value, "unit": "atoms/s",
            "h2d_bytes_per_step": int(pos_h.numel() * 8 + cell_h.numel() * 8 + sp_h.numel() * 4 + nu_h.numel() * 8),
            "d2h_bytes_per_step": int(e_h.numel() * 8 + f_h.numel() * 8)}
 
