@@ -6,9 +6,11 @@ CPU-baseline leg of bench.py, never by the product package.
 from .lmbd_oracle import (BOHR_ANGSTROM, HARTREE_EV, Params, System, quadrature, frequencies,
                           free_atom, fermi, cutoff_buffer, f_inner, f_scs, dipole_T,
                           dipole_T_sr_bare, enumerate_sites, scs_local, t_lr, local_energy,
-                          blend, site_positions, with_params)
+                          blend, site_positions, with_params, fit_node_frequencies, nnls_passive,
+                          phi_fit, phi_integral, lorentzian)
 
 __all__ = ["BOHR_ANGSTROM", "HARTREE_EV", "Params", "System", "quadrature", "frequencies",
            "free_atom", "fermi", "cutoff_buffer", "f_inner", "f_scs", "dipole_T",
            "dipole_T_sr_bare", "enumerate_sites", "scs_local", "t_lr", "local_energy", "blend",
-           "site_positions", "with_params"]
+           "site_positions", "with_params", "fit_node_frequencies", "nnls_passive", "phi_fit",
+           "phi_integral", "lorentzian"]

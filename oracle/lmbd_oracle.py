@@ -25,7 +25,11 @@ the paper's order, one atom (one "central atom k") at a time:
 * the frequency integral by Gauss-Legendre quadrature mapped to [0, inf);
 * optionally (omega_ref set) the Lorentzian frequency model of Sec. III.C: SCS solves at
   omega = 0 and omega_ref only, alpha~(omega) at the nodes from Eqs. char-freq and
-  alpha_SCS_freq applied to the blended polarisabilities.
+  alpha_SCS_freq applied to the blended polarisabilities;
+* optionally (fit_nodes set) the fitted integrand of Sec. III.C: the integrand I(omega) of
+  Eq. integrand at omega = 0 and a few fit nodes, the rational phi(omega) = a / (1 + sum_n
+  b_n omega^(2n)) with a, b_n >= 0 from non-negative least squares (Lawson-Hanson active set)
+  on the linearised equations, and E_k = I(0) times the integral of phi (Eq. E_MBD_k).
 
 Forces are -d(sum_k w_k E_k)/dR by PyTorch autograd (reverse mode), applied to
 the two phases separately so that memory stays bounded: first E_k with the
@@ -72,6 +76,11 @@ class Params:
     # alpha~_i(omega) = alpha~_i(0) / (1 + (omega / omega~_i)^2) (Eq. alpha_SCS_freq) with
     # omega~_i from the two solves (Eq. char-freq)
     omega_ref: float | None = None
+    # None: the integrand is evaluated at every quadrature node.  m > 0: the fitted integrand
+    # of Sec. III.C -- I(omega) at omega = 0 and m fit nodes (m >= series_order, so at least
+    # n_max + 1 values), phi fitted by NNLS, E_k = I(0) * integral of phi, the integral by the
+    # n_freq-point quadrature
+    fit_nodes: int | None = None
 
     @property
     def sphere(self) -> float:
@@ -93,8 +102,22 @@ def quadrature(n_freq: int, omega_scale: float) -> tuple[np.ndarray, np.ndarray]
     return omega, weight
 
 
+def fit_node_frequencies(m: int, omega_scale: float) -> np.ndarray:
+    """Frequencies at which the fitted integrand is sampled: omega = 0, then the m-point
+    Gauss-Legendre nodes under the same mapping as the quadrature (the paper leaves the
+    sample frequencies open)."""
+    x, _ = np.polynomial.legendre.leggauss(m)
+    return np.concatenate([[0.0], omega_scale * (1.0 + x) / (1.0 - x)])
+
+
 def frequencies(p: Params) -> tuple[torch.Tensor, torch.Tensor]:
-    """Column 0 is omega = 0 (needed for the SCS radii), then the quadrature nodes."""
+    """Column 0 is omega = 0 (needed for the SCS radii), then the nodes at which the
+    integrand is evaluated: the quadrature nodes with their weights, or with fit_nodes set the
+    fit frequencies (weights unused, zero)."""
+    if p.fit_nodes:
+        nodes = fit_node_frequencies(p.fit_nodes, p.omega_scale)
+        omega = torch.tensor(np.concatenate([[0.0], nodes]), dtype=_DT)
+        return omega, torch.zeros_like(omega)
     om, w = quadrature(p.n_freq, p.omega_scale)
     omega = torch.tensor(np.concatenate([[0.0], om]), dtype=_DT)
     weight = torch.tensor(np.concatenate([[0.0], w]), dtype=_DT)
@@ -116,6 +139,94 @@ def lorentzian(alpha0, alpha_ref, omega_ref, omega):
     """
     omega_t = omega_ref / torch.sqrt(alpha0 / alpha_ref - 1.0)
     return alpha0[:, None] / (1.0 + (omega[None, :] / omega_t[:, None]) ** 2)
+
+
+# ----------------------------------------------------------------------------------------
+# fitted integrand (Sec. III.C, Eq. integrand and the phi(omega) fit, Eq. E_MBD_k)
+# ----------------------------------------------------------------------------------------
+def nnls_passive(A: np.ndarray, y: np.ndarray) -> tuple[list[int], np.ndarray]:
+    """Non-negative least squares min |A x - y|, x >= 0, by the Lawson-Hanson active-set
+    method (Lawson and Hanson, Solving Least Squares Problems, 1974, ch. 23), the method the
+    paper names for its fits.
+
+    A has unit-norm columns (the caller scales them).  Returns the passive set (sorted column
+    indices with x > 0) and x.  Tolerance: a column enters only if its gradient component
+    exceeds 1e-13 |y|; at most 3 C outer steps.
+    """
+    R, C = A.shape
+    x = np.zeros(C)
+    passive = np.zeros(C, dtype=bool)
+    ny = float(np.sqrt((y * y).sum()))
+    if ny == 0.0:
+        return [], x
+    tol = 1e-13 * ny
+    for _ in range(3 * C):
+        grad = A.T @ (y - A @ x)
+        cand = [c for c in range(C) if not passive[c]]
+        if not cand:
+            break
+        t = max(cand, key=lambda c: (grad[c], -c))
+        if grad[t] <= tol:
+            break
+        passive[t] = True
+        while True:
+            idx = np.nonzero(passive)[0]
+            z = np.zeros(C)
+            z[idx] = np.linalg.lstsq(A[:, idx], y, rcond=None)[0]
+            if np.all(z[idx] > 0.0):
+                x = z
+                break
+            # step from x towards z until the first passive component reaches zero
+            neg = [c for c in idx if z[c] <= 0.0]
+            steps = [x[c] / (x[c] - z[c]) for c in neg]
+            j = int(np.argmin(steps))
+            x = x + steps[j] * (z - x)
+            x[neg[j]] = 0.0
+            for c in idx:
+                if x[c] <= 0.0:
+                    x[c] = 0.0
+                    passive[c] = False
+            if not passive.any():
+                break
+    return [int(c) for c in np.nonzero(passive)[0]], x
+
+
+def phi_fit(I: torch.Tensor, nodes: np.ndarray, order: int) -> tuple[torch.Tensor, torch.Tensor]:
+    """Coefficients of phi(omega) = a / (1 + sum_{n=1}^{order} b_n omega^(2n)) with a, b >= 0.
+
+    I: integrand values at `nodes` (nodes[0] = 0).  The fit of Sec. III.C, I(omega) ~ phi(omega)
+    I(0), is made linear by multiplying out the denominator: for every node
+    a I(0) - sum_n b_n omega^(2n) I(omega) = I(omega), solved in the least-squares sense under
+    a, b >= 0.  The active set is chosen on unit-norm columns; the returned coefficients are
+    the plain least-squares solution on that set (differentiable through I).
+    """
+    J = I.shape[0]
+    nu = torch.as_tensor(nodes, dtype=_DT)
+    cols = [I[0] * torch.ones(J, dtype=_DT)] + [-(nu ** (2 * n)) * I for n in range(1, order + 1)]
+    A = torch.stack(cols, dim=1)
+    An = A.detach().numpy()
+    sc = np.sqrt((An * An).sum(0))
+    sc[sc == 0.0] = 1.0
+    passive, _ = nnls_passive(An / sc, I.detach().numpy())
+    x = torch.zeros(order + 1, dtype=_DT)
+    if passive:
+        sP = torch.as_tensor(sc[passive], dtype=_DT)
+        Q, R = torch.linalg.qr(A[:, passive] / sP)
+        zP = torch.linalg.solve_triangular(R, (Q.T @ I)[:, None], upper=True)[:, 0]
+        x = x.index_put((torch.tensor(passive),), zP / sP)
+    a, b = x[0], x[1:]
+    if float(a.detach()) > 0.0 and not bool((b.detach() > 0).any()):
+        raise ValueError("fitted integrand has no decaying term: phi is not integrable")
+    return a, b
+
+
+def phi_integral(a, b, omega: np.ndarray, weight: np.ndarray) -> torch.Tensor:
+    """Integral over [0, inf) of phi(omega) / (2 pi) by the given quadrature."""
+    om = torch.as_tensor(omega, dtype=_DT)
+    den = torch.ones_like(om)
+    for n in range(1, b.shape[0] + 1):
+        den = den + b[n - 1] * om ** (2 * n)
+    return (torch.as_tensor(weight, dtype=_DT) * a / den).sum() / (2.0 * math.pi)
 
 
 # ----------------------------------------------------------------------------------------
@@ -352,8 +463,10 @@ def local_energy(T, alpha_tilde, weight, p: Params):
 
     The central site is site 0, so g_k is rows 0..2 of G = sqrt(A) T sqrt(A).
     In log mode the k-block trace of ln(1 - G) from eigh replaces the series.
+    With fit_nodes set, the values at the nodes are the integrand I(omega_j) of the fit and
+    E_k = I(0) * integral of phi (Sec. III.C).
     """
-    e = torch.zeros((), dtype=_DT)
+    terms = []
     for q in range(1, alpha_tilde.shape[1]):
         dq = torch.sqrt(alpha_tilde[:, q]).repeat_interleave(3)
         G = dq[:, None] * T * dq[None, :]
@@ -367,6 +480,14 @@ def local_energy(T, alpha_tilde, weight, p: Params):
             for n in range(2, p.series_order + 1):
                 term = term + (-1.0 / n) * torch.trace(gk @ y)
                 y = G @ y
+        terms.append(term)
+    if p.fit_nodes:
+        I = torch.stack(terms)
+        a, b = phi_fit(I, fit_node_frequencies(p.fit_nodes, p.omega_scale), p.series_order)
+        om, w = quadrature(p.n_freq, p.omega_scale)
+        return I[0] * phi_integral(a, b, om, w)
+    e = torch.zeros((), dtype=_DT)
+    for q, term in enumerate(terms, start=1):
         e = e + weight[q] / (2.0 * math.pi) * term
     return e
 

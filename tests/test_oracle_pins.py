@@ -507,3 +507,121 @@ def test_lorentz_model_forces_match_central_finite_differences():
             assert abs(fd - F[a, g]) < 2e-8 + 1e-6 * abs(F[a, g]), (a, g, fd, F[a, g])
             checked += 1
     assert checked >= 6
+
+
+# ---------------------------------------------------------------------------------------
+# fitted integrand of Sec. III.C: I(omega) sampled at omega = 0 and fit nodes, phi(omega) =
+# a / (1 + sum_n b_n omega^(2n)) by non-negative least squares, E_k = I(0) * integral of phi
+# ---------------------------------------------------------------------------------------
+def test_nnls_matches_library_and_optimality_conditions():
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(3)
+    for trial in range(40):
+        R, C = int(rng.integers(4, 14)), int(rng.integers(2, 9))
+        A = rng.normal(size=(R, C))
+        A /= np.sqrt((A * A).sum(0))
+        y = rng.normal(size=R)
+        passive, x = oracle.nnls_passive(A, y)
+        x_ref, _ = scipy_opt.nnls(A, y)
+        assert np.allclose(x, x_ref, atol=1e-12, rtol=0), trial
+        # Karush-Kuhn-Tucker conditions of the constrained problem
+        g = A.T @ (y - A @ x)
+        assert np.all(x >= 0)
+        assert passive == [c for c in range(C) if x[c] > 0]
+        assert np.all(np.abs(g[passive]) < 1e-12)
+        assert np.all(g[[c for c in range(C) if c not in passive]] < 1e-12)
+
+
+def test_phi_fit_recovers_a_rational_integrand_and_its_integral():
+    # I(omega) = I0 / ((1 + omega^2/w1^2)(1 + omega^2/w2^2)) has exactly the form of phi, with
+    # b1 = 1/w1^2 + 1/w2^2, b2 = 1/(w1 w2)^2 and b3 = 0; its integral over [0, inf) is
+    # pi w1 w2 / (2 (w1 + w2))
+    w1, w2, i0 = 0.37, 1.9, -0.0123
+    nodes = oracle.fit_node_frequencies(3, 0.6)
+    I = torch.tensor(i0 / ((1 + nodes ** 2 / w1 ** 2) * (1 + nodes ** 2 / w2 ** 2)), dtype=torch.float64)
+    a, b = oracle.phi_fit(I, nodes, 3)
+    assert abs(float(a) - 1.0) < 1e-12
+    assert np.allclose(b.numpy(), [1 / w1 ** 2 + 1 / w2 ** 2, 1 / (w1 * w2) ** 2, 0.0], rtol=1e-11, atol=1e-12)
+    om, w = oracle.quadrature(200, 0.6)
+    phi_int = float(oracle.phi_integral(a, b, om, w))
+    assert abs(phi_int / (w1 * w2 / (4 * (w1 + w2))) - 1) < 1e-10
+
+
+def test_phi_fit_clamps_rising_terms():
+    # an integrand that first rises cannot be matched with a, b >= 0; the fit keeps every
+    # coefficient non-negative and the result is integrable
+    nodes = oracle.fit_node_frequencies(4, 0.6)
+    I = torch.tensor(-(1 + 0.5 * nodes ** 2) / (1 + nodes ** 2) ** 3, dtype=torch.float64)
+    a, b = oracle.phi_fit(I, nodes, 4)
+    assert float(a) > 0 and bool((b >= 0).all()) and bool((b > 0).any())
+    assert (b == 0).any()
+
+
+@pytest.mark.parametrize("omega_ref", [None, 0.7])
+def test_fitted_integrand_dimer_is_casimir_polder_c6(omega_ref):
+    # two atoms outside each other's SCS sphere: with n_max = 2 the integrand is a product of
+    # the two free Lorentzians, which the fit reproduces exactly, so the energy is the London
+    # closed form (also through the Lorentzian model, exact without screening)
+    table = np.array([[6.0, 20.0, 3.2], [10.0, 44.0, 3.8]])
+    nu = np.array([0.8, 0.93])
+    r_ang = 3.4
+    p = oracle.Params(r_scs=1.0, r_mbd1=10, r_mbd2=10, r_sphere=10, series_order=2, n_freq=200,
+                      fit_nodes=2, omega_ref=omega_ref)
+    e = _dimer(r_ang, table, np.array([0, 1]), nu, p).energies()
+    a1, w1, R1 = _lorentz(table, 0, nu[0])
+    a2, w2, R2 = _lorentz(table, 1, nu[1])
+    c6 = 1.5 * a1 * a2 * w1 * w2 / (w1 + w2)
+    r = r_ang / BOHR
+    f = 1 / (1 + math.exp(-6 * (r / (0.83 * (R1 + R2)) - 1)))
+    exact = -f * f * c6 / r ** 6 * HA
+    assert abs(e.sum() / exact - 1) < 1e-10
+
+
+@pytest.mark.parametrize("omega_ref", [None, 2.0])
+def test_fitted_integrand_close_to_quadrature(omega_ref):
+    # the paper's premise: for one chemical species the integrand keeps close to the rational
+    # form and the fit reproduces the quadrature of the same model to well below 1 %; with three
+    # species whose characteristic frequencies span 0.09-3.3 Ha the integrand is a mixture the
+    # form cannot follow, and the fit is off by up to tens of per cent per atom
+    s = inputs.cluster(24, seed=0)
+    p = oracle.Params(r_scs=5.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0, omega_ref=omega_ref)
+
+    def rel(species):
+        ex = oracle.System(s.positions, None, species, s.hirshfeld, s.table, p).energies()
+        ft = oracle.System(s.positions, None, species, s.hirshfeld, s.table,
+                           oracle.with_params(p, fit_nodes=6)).energies()
+        return np.abs(ft - ex) / np.abs(ex)
+
+    one = rel(np.full_like(s.species, 1))
+    assert 1e-9 < one.max() < (1e-2 if omega_ref is None else 1e-3)
+    mixed = rel(s.species)
+    assert 0.05 < mixed.max() < 0.5
+
+
+@pytest.mark.parametrize("omega_ref", [None, 0.5])
+def test_fitted_integrand_forces_match_central_finite_differences(omega_ref):
+    s = inputs.box(36, seed=11, jitter=0.05)
+    p = oracle.with_params(_P_SMALL, omega_ref=omega_ref, fit_nodes=6)
+    sysm = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p)
+    _, F = sysm.energies_forces()
+    assert np.abs(F.sum(0)).max() < 1e-12
+    h = 1e-4
+    rng = np.random.default_rng(6)
+    checked = 0
+    ref_sets = _site_sets(sysm, range(s.n_atoms))
+    for a in rng.choice(s.n_atoms, 4, replace=False):
+        for g in range(3):
+            es = []
+            for sgn in (1, -1):
+                pos = s.positions.copy()
+                pos[a, g] += sgn * h
+                sp = oracle.System(pos, s.cell, s.species, s.hirshfeld, s.table, p)
+                if _site_sets(sp, range(s.n_atoms)) != ref_sets:
+                    break
+                es.append(sp.energies().sum())
+            if len(es) < 2:
+                continue
+            fd = -(es[0] - es[1]) / (2 * h)
+            assert abs(fd - F[a, g]) < 2e-8 + 1e-6 * abs(F[a, g]), (a, g, fd, F[a, g])
+            checked += 1
+    assert checked >= 6
