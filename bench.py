@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--large-atoms", type=int, default=2048)
     ap.add_argument("--omega-ref", type=float, default=0.0,
                     help="> 0: the paper's Lorentzian frequency model with this reference frequency (Ha)")
+    ap.add_argument("--fit-nodes", type=int, default=0,
+                    help="> 0: the paper's fitted integrand phi(omega) from omega = 0 and this many fit nodes")
     return ap.parse_args()
 
 
@@ -192,6 +194,8 @@ def run_ours(args, world, rank, local):
     model = lmbd.LMBD(s.table, lmbd.default_params(), 12, 6)
     if args.omega_ref > 0:
         model.set_frequency_model(lmbd.FREQ_LORENTZIAN, args.omega_ref)
+    if args.fit_nodes > 0:
+        model.set_integrand_fit(args.fit_nodes)
     pos = torch.tensor(s.positions, device=dev)
     cell = torch.tensor(s.cell, device=dev)
     sp = torch.tensor(s.species, dtype=torch.int32, device=dev)
@@ -279,7 +283,8 @@ def run_ours(args, world, rank, local):
     if dom == "scs":
         # mixed-precision SCS: FP32 Cholesky and solves, FP64 residual and right-hand side.  The
         # roofline is the sum of the two pipe-bound times: t* = W32 / P32 + W64 / P64.
-        nq = 2 if args.omega_ref > 0 else 13   # frequencies of the SCS solves
+        # frequencies of the SCS solves
+        nq = 2 if args.omega_ref > 0 else (args.fit_nodes + 2 if args.fit_nodes > 0 else 13)
         n1 = model.site_counts(args.atoms)[:, 0].astype(float)
         N1 = 3.0 * n1
         w32 = nq * float(np.sum(N1 ** 3 / 3.0 + 18.0 * N1 ** 2))
@@ -320,7 +325,8 @@ def run_ours(args, world, rank, local):
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD + (f"; Lorentzian frequency model, omega_ref {args.omega_ref} Ha"
-                                               if args.omega_ref > 0 else ""),
+                                               if args.omega_ref > 0 else "")
+                       + (f"; fitted integrand, {args.fit_nodes} fit nodes" if args.fit_nodes > 0 else ""),
                        "atoms": args.atoms, "parallelism": f"replicas x{world}",
                        "l2": f"inputs resident; per-step working set {st['bytes_workspace'] / 1e9:.1f} GB > 129 MB L2",
                        "sites_per_atom": st["n_sites"] / args.atoms, "max_k1": st["max_k1"],

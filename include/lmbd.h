@@ -49,7 +49,7 @@ extern "C" {
 #define LMBD_ECAPACITY     5  /* more sites around one atom than the kernels support             */
 #define LMBD_EUNSUPPORTED  6  /* option not supported (e.g. series order out of range)           */
 #define LMBD_ESCRATCH      7  /* problem larger than the allocation-free entry point's scratch   */
-#define LMBD_EMODEL        8  /* Lorentzian frequency model not applicable (see below)           */
+#define LMBD_EMODEL        8  /* frequency or integrand model not applicable (see below)        */
 
 #define LMBD_MAX_FREQ      64 /* maximum number of quadrature frequencies                        */
 #define LMBD_MAX_ORDER     10 /* maximum series order n_max                                      */
@@ -176,6 +176,22 @@ int lmbd_set_precision(lmbd_ctx* ctx, int mode);
 #define LMBD_FREQ_QUADRATURE 0
 #define LMBD_FREQ_LORENTZIAN 1
 int lmbd_set_frequency_model(lmbd_ctx* ctx, int model, double omega_ref);
+
+/* Integrand model (Sec. III.C, Eq. integrand and Eq. E_MBD_k).
+ * n_fit_nodes = 0 (default): the integrand I(omega) = sum_n c_n Tr{g_k G^(n-2) g_k^T} is
+ *   evaluated at every quadrature node and integrated by the quadrature.
+ * n_fit_nodes = m, series_order <= m <= LMBD_MAX_FIT_NODES: I is evaluated at omega = 0 and at
+ *   m fit nodes omega_j = L (1 + x_j) / (1 - x_j), x_j the m-point Gauss-Legendre nodes and
+ *   L = omega_scale (so at n_max + 1 frequencies at least, as the paper asks).  For every
+ *   centre, phi(omega) = a / (1 + sum_{n=1}^{n_max} b_n omega^(2n)) is fitted with a, b_n >= 0
+ *   to the linearised equations a I(0) - sum_n b_n omega_j^(2n) I(omega_j) = I(omega_j) by
+ *   non-negative least squares (Lawson-Hanson active set, chosen on unit-norm columns), and
+ *   E_k = I(0) (1/2pi) sum_i w_i phi(omega_i) with the n_freq-point quadrature.  Forces are the
+ *   exact gradient of that E_k (the active set is locally constant).  Combines with either
+ *   frequency model.  A call in which some centre's fit has a > 0 and every b_n = 0 (phi not
+ *   integrable) returns LMBD_EMODEL.  m outside the range returns LMBD_EINVAL. */
+#define LMBD_MAX_FIT_NODES 24
+int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes);
 
 /* Device memory budget of the context in bytes (0 = the default: the device's free
  * memory at each call less 1 GiB).  Central atoms are processed in contiguous waves whose

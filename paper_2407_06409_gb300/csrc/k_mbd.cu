@@ -207,6 +207,239 @@ __global__ void __launch_bounds__(256) k_mbd_chain(Work w, DevParams p, int m, i
 }
 
 // ---------------------------------------------------------------------------------------
+// fitted integrand (Sec. III.C, Eq. integrand and Eq. E_MBD_k): with I_j = I(nu_j) at
+// nu_0 = 0 and the fit nodes, phi(omega) = a / (1 + sum_{n=1}^{n_max} b_n omega^(2n)) with
+// a, b_n >= 0 minimises sum_j [a I_0 - sum_n b_n nu_j^(2n) I_j - I_j]^2 (Lawson-Hanson
+// active set on unit-norm columns), and E_k = H I_0 sum_i wt_i phi(Omega_i).
+// One thread per centre; the systems are at most 25 x 11.
+// ---------------------------------------------------------------------------------------
+struct FitScratch {
+  double A[LMBD_MAX_ORDER_P1][LMBD_FIT_ROWS];   // columns scaled to unit norm
+  double W[LMBD_MAX_ORDER_P1][LMBD_FIT_ROWS];   // Householder vectors / R of the passive columns
+  double y[LMBD_FIT_ROWS];
+  double qy[LMBD_FIT_ROWS];
+  double sc[LMBD_MAX_ORDER_P1];                 // column norms
+  double rdiag[LMBD_MAX_ORDER_P1];
+};
+
+// QR of the k passive columns idx[] (Householder); R[i][l] (i < l) is W[l][i], R[i][i] rdiag[i].
+// Solves min |A_P z - y|.  Returns 0 if a column is numerically dependent on the others.
+__device__ int fit_qr_solve(FitScratch& S, int J, const int* idx, int k, double* z) {
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < J; ++j) S.W[i][j] = S.A[idx[i]][j];
+  for (int j = 0; j < J; ++j) S.qy[j] = S.y[j];
+  for (int i = 0; i < k; ++i) {
+    double nrm = 0.0;
+    for (int j = i; j < J; ++j) nrm += S.W[i][j] * S.W[i][j];
+    nrm = sqrt(nrm);
+    if (!(nrm > 1e-14)) return 0;
+    const double alpha = S.W[i][i] > 0.0 ? -nrm : nrm;
+    S.W[i][i] -= alpha;
+    double vv = 0.0;
+    for (int j = i; j < J; ++j) vv += S.W[i][j] * S.W[i][j];
+    S.rdiag[i] = alpha;
+    for (int l = i + 1; l < k; ++l) {
+      double d = 0.0;
+      for (int j = i; j < J; ++j) d += S.W[i][j] * S.W[l][j];
+      d *= 2.0 / vv;
+      for (int j = i; j < J; ++j) S.W[l][j] -= d * S.W[i][j];
+    }
+    double d = 0.0;
+    for (int j = i; j < J; ++j) d += S.W[i][j] * S.qy[j];
+    d *= 2.0 / vv;
+    for (int j = i; j < J; ++j) S.qy[j] -= d * S.W[i][j];
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double t = S.qy[i];
+    for (int l = i + 1; l < k; ++l) t -= S.W[l][i] * z[l];
+    z[i] = t / S.rdiag[i];
+  }
+  return 1;
+}
+
+// Lawson-Hanson NNLS on S.A (J x C, unit-norm columns), S.y.  Writes the passive flags and x.
+__device__ void fit_nnls(FitScratch& S, int J, int C, int* passive, double* x) {
+  for (int c = 0; c < C; ++c) {
+    passive[c] = 0;
+    x[c] = 0.0;
+  }
+  double ny = 0.0;
+  for (int j = 0; j < J; ++j) ny += S.y[j] * S.y[j];
+  ny = sqrt(ny);
+  if (ny == 0.0) return;
+  const double tol = 1e-13 * ny;
+  int idx[LMBD_MAX_ORDER_P1];
+  double z[LMBD_MAX_ORDER_P1], zf[LMBD_MAX_ORDER_P1];
+  for (int outer = 0; outer < 3 * C; ++outer) {
+    double r[LMBD_FIT_ROWS];
+    for (int j = 0; j < J; ++j) {
+      double t = S.y[j];
+      for (int c = 0; c < C; ++c) t -= S.A[c][j] * x[c];
+      r[j] = t;
+    }
+    int best = -1;
+    double gbest = 0.0;
+    for (int c = 0; c < C; ++c) {
+      if (passive[c]) continue;
+      double g = 0.0;
+      for (int j = 0; j < J; ++j) g += S.A[c][j] * r[j];
+      if (best < 0 || g > gbest) {
+        best = c;
+        gbest = g;
+      }
+    }
+    if (best < 0 || !(gbest > tol)) break;
+    passive[best] = 1;
+    for (int inner = 0; inner <= C; ++inner) {
+      int k = 0;
+      for (int c = 0; c < C; ++c)
+        if (passive[c]) idx[k++] = c;
+      if (!fit_qr_solve(S, J, idx, k, z))
+        for (int i = 0; i < k; ++i) z[i] = 0.0;     // dependent column: step back to x
+      for (int c = 0; c < C; ++c) zf[c] = 0.0;
+      bool all_pos = true;
+      for (int i = 0; i < k; ++i) {
+        zf[idx[i]] = z[i];
+        if (!(z[i] > 0.0)) all_pos = false;
+      }
+      if (all_pos) {
+        for (int c = 0; c < C; ++c) x[c] = zf[c];
+        break;
+      }
+      // step from x towards z until the first passive component reaches zero
+      int jmin = -1;
+      double smin = 0.0;
+      for (int i = 0; i < k; ++i) {
+        const int c = idx[i];
+        if (zf[c] <= 0.0) {
+          const double st = x[c] / (x[c] - zf[c]);
+          if (jmin < 0 || st < smin) {
+            jmin = c;
+            smin = st;
+          }
+        }
+      }
+      for (int c = 0; c < C; ++c) x[c] += smin * (zf[c] - x[c]);
+      x[jmin] = 0.0;
+      bool any = false;
+      for (int i = 0; i < k; ++i) {
+        const int c = idx[i];
+        if (x[c] <= 0.0) {
+          x[c] = 0.0;
+          passive[c] = 0;
+        } else {
+          any = true;
+        }
+      }
+      if (!any) break;
+    }
+  }
+}
+
+// Energy of one centre from its integrand values I[0..J-1] (Hartree), and dE/dI_j into dI.
+__device__ double fit_energy(FitScratch& S, const double* I, const DevParams& p, double* dI, int* status) {
+  const int J = p.n_freq, C = p.order + 1;
+  for (int j = 0; j < J; ++j) {
+    const double nu2 = p.omega[j + 1] * p.omega[j + 1];
+    S.A[0][j] = I[0];
+    double pw = 1.0;
+    for (int n = 1; n < C; ++n) {
+      pw *= nu2;
+      S.A[n][j] = -pw * I[j];
+    }
+    S.y[j] = I[j];
+  }
+  for (int c = 0; c < C; ++c) {
+    double t = 0.0;
+    for (int j = 0; j < J; ++j) t += S.A[c][j] * S.A[c][j];
+    t = sqrt(t);
+    S.sc[c] = t > 0.0 ? t : 1.0;
+    for (int j = 0; j < J; ++j) S.A[c][j] /= S.sc[c];
+  }
+  int passive[LMBD_MAX_ORDER_P1];
+  double xs[LMBD_MAX_ORDER_P1];
+  fit_nnls(S, J, C, passive, xs);
+  double x[LMBD_MAX_ORDER_P1];
+  bool decays = false;
+  for (int c = 0; c < C; ++c) {
+    x[c] = xs[c] / S.sc[c];           // coefficients of the unscaled columns
+    if (c > 0 && x[c] > 0.0) decays = true;
+  }
+  if (x[0] > 0.0 && !decays) atomicOr(status, LMBD_FLAG_MODEL);
+  // E = H I_0 Phi, Phi = sum_i wt_i a / den_i
+  double phi = 0.0, abar = 0.0;
+  double bbar[LMBD_MAX_ORDER_P1];
+  for (int n = 0; n < C; ++n) bbar[n] = 0.0;
+  for (int i = 0; i < p.n_phi; ++i) {
+    const double om2 = p.phi_omega[i] * p.phi_omega[i];
+    double den = 1.0, pw = 1.0;
+    for (int n = 1; n < C; ++n) {
+      pw *= om2;
+      den += x[n] * pw;
+    }
+    const double wt = p.phi_wt[i];
+    phi += wt * x[0] / den;
+    abar += wt / den;
+    pw = 1.0;
+    for (int n = 1; n < C; ++n) {
+      pw *= om2;
+      bbar[n] -= wt * x[0] * pw / (den * den);
+    }
+  }
+  const double H = LMBD_HARTREE;
+  const double E = H * I[0] * phi;
+  if (dI) {
+    for (int j = 0; j < J; ++j) dI[j] = 0.0;
+    dI[0] = H * phi;
+    int idx[LMBD_MAX_ORDER_P1];
+    int k = 0;
+    for (int c = 0; c < C; ++c)
+      if (passive[c]) idx[k++] = c;
+    double z[LMBD_MAX_ORDER_P1];
+    if (k > 0 && fit_qr_solve(S, J, idx, k, z)) {
+      // xbar of the passive columns (unscaled), then z = (A_P^T A_P)^-1 xbar through R
+      double u[LMBD_MAX_ORDER_P1], v[LMBD_MAX_ORDER_P1], zh[LMBD_MAX_ORDER_P1];
+      for (int i = 0; i < k; ++i) {
+        const int c = idx[i];
+        const double xb = (c == 0 ? abar : bbar[c]) * H * I[0];
+        u[i] = xb / S.sc[c];
+      }
+      for (int i = 0; i < k; ++i) {          // R^T v = u
+        double t = u[i];
+        for (int l = 0; l < i; ++l) t -= S.W[i][l] * v[l];
+        v[i] = t / S.rdiag[i];
+      }
+      for (int i = k - 1; i >= 0; --i) {     // R zh = v
+        double t = v[i];
+        for (int l = i + 1; l < k; ++l) t -= S.W[l][i] * zh[l];
+        zh[i] = t / S.rdiag[i];
+      }
+      for (int j = 0; j < J; ++j) {
+        double Az = 0.0, r = S.y[j];
+        for (int i = 0; i < k; ++i) {
+          Az += S.A[idx[i]][j] * zh[i];
+          r -= S.A[idx[i]][j] * S.sc[idx[i]] * x[idx[i]];
+        }
+        dI[j] += Az;                                  // through y_j = I_j
+        const double nu2 = p.omega[j + 1] * p.omega[j + 1];
+        for (int i = 0; i < k; ++i) {
+          const int c = idx[i];
+          const double Abar = r * (zh[i] / S.sc[c]) - Az * x[c];
+          if (c == 0) {
+            dI[0] += Abar;                            // A_j0 = I_0
+          } else {
+            double pw = 1.0;
+            for (int n = 0; n < c; ++n) pw *= nu2;
+            dI[j] -= pw * Abar;                       // A_jc = -nu_j^(2c) I_j
+          }
+        }
+      }
+    }
+  }
+  return E;
+}
+
+// ---------------------------------------------------------------------------------------
 // energy: tr_{n,q} = <v_a, v_b>_q (a + b = n) and E_k = sum_q cw_q sum_n (-1/n) tr_{n,q}
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0) {
@@ -235,6 +468,7 @@ __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0)
   }
   __syncthreads();
   __shared__ double epart[64];
+  __shared__ double ival[64];
   if (tid < p.n_freq) {
     int q = tid;
     double e = 0.0;
@@ -243,13 +477,19 @@ __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0)
       w.trbuf[((long long)c * (LMBD_MAX_ORDER_P1)) * 64 + n * 64 + q] = tr;
       e += (-1.0 / n) * tr;
     }
+    ival[q] = e;
     epart[q] = e * p.cweight[q + 1];
   }
   __syncthreads();
   if (tid == 0) {
-    double e = 0.0;
-    for (int q = 0; q < p.n_freq; ++q) e += epart[q];
-    w.energies[c] = e;
+    if (p.fit) {
+      __shared__ FitScratch fs;
+      w.energies[c] = fit_energy(fs, ival, p, w.fitw + (long long)c * LMBD_FITW, w.status);
+    } else {
+      double e = 0.0;
+      for (int q = 0; q < p.n_freq; ++q) e += epart[q];
+      w.energies[c] = e;
+    }
   }
 }
 
@@ -292,38 +532,46 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
   for (int e = tid; e < ns * p.n_freq; e += blockDim.x) {
     int s = e / p.n_freq, qq = e % p.n_freq, q = qq + 1;
     double ct[LMBD_MAX_ORDER_P1];
-    for (int n = 0; n <= nm; ++n) ct[n] = (n >= 2) ? wk * p.cweight[q] * (-1.0 / n) : 0.0;
-    // inner products <v_j[s], v_l[s]> for 1 <= j <= l, j + l <= n_max
-    double ga = 0.0;
-    for (int n = 2; n <= nm; ++n) {
-      double sum = 0.0;
-      if (s == 0) sum += w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq];
-      for (int j = 1; j <= n - 1; ++j) {
-        const double* Va = V0 + (long long)(j - 1) * w.vstride;
-        const double* Vb = V0 + (long long)(n - j - 1) * w.vstride;
-        for (int al = 0; al < 3; ++al)
-          for (int be = 0; be < 3; ++be) {
-            long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
-            sum += Va[idx] * Vb[idx];
-          }
-      }
-      ga += ct[n] * sum;
-    }
-    w.gbar[(offs + s) * p.nq + q] = ga / w.alphaT[(offs + s) * p.nq + q];
-    // P and Q columns of this frequency
+#pragma unroll
+    const double cwq = p.fit ? w.fitw[(long long)c * LMBD_FITW + qq] : p.cweight[q];
+    for (int n = 0; n < LMBD_MAX_ORDER_P1; ++n) ct[n] = (n >= 2 && n <= nm) ? wk * cwq * (-1.0 / n) : 0.0;
+    // one pass over the 9 components of this site-frequency block: the Krylov entries
+    // v_1..v_{n_max-1} are loaded once, then the inner products <v_j, v_{n-j}> and the
+    // P, Q columns are formed from registers
+    double sums[LMBD_MAX_ORDER_P1];
+#pragma unroll
+    for (int n = 0; n < LMBD_MAX_ORDER_P1; ++n)
+      sums[n] = (s == 0 && n >= 2 && n <= nm) ? w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq] : 0.0;
     const double ds = w.dsq[(offs + s) * p.nq + q];
-    for (int j = 1; j <= nm - 2; ++j) {
-      const double* Vj = V0 + (long long)(j - 1) * w.vstride;
-      for (int al = 0; al < 3; ++al)
-        for (int be = 0; be < 3; ++be) {
-          long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
+    for (int comp = 0; comp < 9; ++comp) {
+      const int al = comp / 3, be = comp % 3;
+      const long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
+      double v[(LMBD_MAX_ORDER_P1 - 1)];
+#pragma unroll
+      for (int m = 0; m < (LMBD_MAX_ORDER_P1 - 1); ++m) v[m] = (m < nm - 1) ? V0[(long long)m * w.vstride + idx] : 0.0;
+#pragma unroll
+      for (int n = 2; n < LMBD_MAX_ORDER_P1; ++n)
+        if (n <= nm) {
+#pragma unroll
+          for (int j = 1; j < n; ++j) sums[n] += v[j - 1] * v[n - j - 1];
+        }
+#pragma unroll
+      for (int j = 1; j < (LMBD_MAX_ORDER_P1 - 1) - 1; ++j)
+        if (j <= nm - 2) {
           double a = 0.0;
-          for (int l = 1; l <= nm - 1 - j; ++l) a += ct[j + l + 1] * V0[(long long)(l - 1) * w.vstride + idx];
-          long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
-          w.pmat[o] = ds * Vj[idx];
+#pragma unroll
+          for (int l = 1; l < (LMBD_MAX_ORDER_P1 - 1); ++l)
+            if (l <= nm - 1 - j) a += ct[j + l + 1] * v[l - 1];
+          const long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
+          w.pmat[o] = ds * v[j - 1];
           w.qmat[o] = ds * a;
         }
     }
+    double ga = 0.0;
+#pragma unroll
+    for (int n = 2; n < LMBD_MAX_ORDER_P1; ++n)
+      if (n <= nm) ga += ct[n] * sums[n];
+    w.gbar[(offs + s) * p.nq + q] = ga / w.alphaT[(offs + s) * p.nq + q];
   }
   __syncthreads();
   // X0_s (3 x 3) summed over frequencies
@@ -333,9 +581,10 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
     for (int qq = 0; qq < p.n_freq; ++qq) {
       int q = qq + 1;
       double dd = w.dsq[(offs + s) * p.nq + q] * w.dsq[offs * p.nq + q];
+      const double cwq = p.fit ? w.fitw[(long long)c * LMBD_FITW + qq] : p.cweight[q];
       double sum = 0.0;
       for (int n = 2; n <= nm; ++n)
-        sum += wk * p.cweight[q] * (-1.0 / n) * V0[(long long)(n - 2) * w.vstride + (long long)(3 * s + al) * ncv + 3 * qq + be];
+        sum += wk * cwq * (-1.0 / n) * V0[(long long)(n - 2) * w.vstride + (long long)(3 * s + al) * ncv + 3 * qq + be];
       acc += dd * sum;
     }
     w.x0buf[(offs + s) * 9 + al * 3 + be] = acc;

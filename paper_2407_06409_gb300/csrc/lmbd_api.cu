@@ -49,6 +49,8 @@ struct Ctx {
   int precision = LMBD_PREC_SLICED;
   int lorentz = 0;                 // frequency model (lmbd_set_frequency_model)
   double omega_ref = 0.0;
+  int fit_nodes = 0;               // integrand model (lmbd_set_integrand_fit): 0 = quadrature
+  std::vector<double> fit_omega;   // omega = 0, then the fit nodes
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
   int site_cap = 0;
@@ -60,7 +62,7 @@ struct Ctx {
   DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
   DevBuf site_atom, site_x, counts, offs, totals, status, pcount;
   DevBuf alphaK, alphaI, energies, trbuf, wexp, alphaK_bar, alphaI_bar, gacc, rad_ab, rad_ff;
-  DevBuf order1_d, order3_d;
+  DevBuf order1_d, order3_d, fitw;
   DevBuf arena;
   std::vector<Counts> counts_h;
   std::vector<long long> offs_h;
@@ -71,7 +73,7 @@ struct Ctx {
     DevBuf* l[] = {&table_d, &pos_d, &species_d, &nu_d, &weights_d, &out_e_d, &out_f_d, &abar, &sig, &rvdw,
                    &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
-                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff};
+                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw};
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
   size_t whole_bytes() const {
@@ -384,7 +386,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   c->last_n = N;
   if (N == 0) return LMBD_OK;
   const lmbd_params& P = c->prm;
-  const int nq = c->n_freq + 1;
+  // frequencies at which the integrand is evaluated: the quadrature nodes, or omega = 0 and
+  // the fit nodes of the fitted integrand
+  const int nf = c->fit_nodes ? c->fit_nodes + 1 : c->n_freq;
+  const int nq = nf + 1;
   const bool forces = f_out != nullptr;
   int launches = 0;
 
@@ -411,16 +416,29 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   dp.r2_sphere_ang = rsph * rsph;
   dp.r2_scs2_ang = 4.0 * P.r_scs * P.r_scs;
   dp.r2_list_ang = rlist * rlist;
-  dp.n_freq = c->n_freq;
+  dp.n_freq = nf;
   dp.nq = nq;
   dp.order = c->order;
   dp.n_species = c->n_species;
   dp.omega[0] = 0.0;
   dp.cweight[0] = 0.0;
   const double pi = 3.14159265358979323846;
-  for (int q = 0; q < c->n_freq; ++q) {
-    dp.omega[q + 1] = c->omega[q];
-    dp.cweight[q + 1] = LMBD_HARTREE * c->weight[q] / (2.0 * pi);
+  if (c->fit_nodes) {
+    dp.fit = 1;
+    for (int q = 0; q < nf; ++q) {
+      dp.omega[q + 1] = c->fit_omega[q];
+      dp.cweight[q + 1] = 0.0;
+    }
+    dp.n_phi = c->n_freq;
+    for (int i = 0; i < c->n_freq; ++i) {
+      dp.phi_omega[i] = c->omega[i];
+      dp.phi_wt[i] = c->weight[i] / (2.0 * pi);
+    }
+  } else {
+    for (int q = 0; q < c->n_freq; ++q) {
+      dp.omega[q + 1] = c->omega[q];
+      dp.cweight[q + 1] = LMBD_HARTREE * c->weight[q] / (2.0 * pi);
+    }
   }
   dp.lorentz = c->lorentz;
   dp.omega_ref = c->omega_ref;
@@ -600,9 +618,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   const Offs o{c->offs_h.data(), N};
 
   // ---- whole-structure arrays -------------------------------------------------------------
-  const int ncv = 3 * c->n_freq;
+  const int ncv = 3 * nf;
   const int nvec = forces ? (c->order - 1) : (c->order + 1) / 2;
-  const int ncol = 3 * c->n_freq * (c->order - 2);
+  const int ncol = 3 * nf * (c->order - 2);
   // sliced tensor-core products: digits per product (see ozaki.cuh and the design notes)
   const bool sliced = c->precision == LMBD_PREC_SLICED;
   const bool sliced_chain = sliced && ncv <= 48;
@@ -630,6 +648,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   }
   TRY(ensure(c->order1_d, sizeof(int) * N));
   TRY(ensure(c->order3_d, sizeof(int) * N));
+  if (c->fit_nodes) {
+    TRY(ensure(c->fitw, sizeof(double) * LMBD_FITW * (size_t)N));
+    w.fitw = (double*)c->fitw.p;
+  }
 
   // ---- waves under the memory budget --------------------------------------------------------
   const Layout L{nq, ncv, nvec, ncol, (ncol + 15) / 16 * 16, ST, DIG_P, c->site_cap, forces, sliced_chain,
@@ -1027,6 +1049,26 @@ int lmbd_set_frequency_model(lmbd_ctx* ctx, int model, double omega_ref) {
   if (model != LMBD_FREQ_LORENTZIAN || !(omega_ref > 0.0) || !std::isfinite(omega_ref)) return LMBD_EINVAL;
   ctx->c.lorentz = 1;
   ctx->c.omega_ref = omega_ref;
+  return LMBD_OK;
+}
+
+static_assert(LMBD_FIT_ROWS == LMBD_MAX_FIT_NODES + 1 && LMBD_FITW >= LMBD_FIT_ROWS,
+              "fit scratch sizes follow the public node limit");
+
+int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes) {
+  if (!ctx) return LMBD_EINVAL;
+  Ctx& c = ctx->c;
+  if (n_fit_nodes == 0) {
+    c.fit_nodes = 0;
+    c.fit_omega.clear();
+    return LMBD_OK;
+  }
+  if (n_fit_nodes < c.order || n_fit_nodes > LMBD_MAX_FIT_NODES) return LMBD_EINVAL;
+  std::vector<double> om, wt;
+  gauss_legendre(n_fit_nodes, c.prm.omega_scale, om, wt);
+  c.fit_omega.assign(1, 0.0);
+  c.fit_omega.insert(c.fit_omega.end(), om.begin(), om.end());
+  c.fit_nodes = n_fit_nodes;
   return LMBD_OK;
 }
 

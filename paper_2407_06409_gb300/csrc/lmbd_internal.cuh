@@ -14,7 +14,10 @@
 #define LMBD_FLAG_CAPACITY 2
 #define LMBD_FLAG_COINCIDENT 4
 #define LMBD_FLAG_NOT_CONVERGED 8
-#define LMBD_FLAG_MODEL 16          // Lorentzian model not applicable: alpha~(0) < alpha~(omega_ref)
+#define LMBD_FLAG_MODEL 16          // Lorentzian model not applicable: alpha~(0) < alpha~(omega_ref),
+                                    // or a fitted phi without decaying term
+#define LMBD_FITW 32                // stride of the per-centre integrand weights dE/dI(omega_j)
+#define LMBD_FIT_ROWS 25            // omega = 0 plus at most 24 fit nodes
 
 struct DevParams {
   // lengths in bohr
@@ -33,6 +36,12 @@ struct DevParams {
   int lorentz;
   double omega_ref;
   double omega_s[LMBD_MAXQ];
+  // fitted integrand of Sec. III.C (fit = 1): omega[1..n_freq] are omega = 0 and the fit
+  // nodes; the integral of phi uses the n_phi-point quadrature (phi_omega, phi_wt = w / 2 pi)
+  int fit;
+  int n_phi;
+  double phi_omega[LMBD_MAXQ - 1];
+  double phi_wt[LMBD_MAXQ - 1];
 };
 
 // Geometry of the neighbour search (host-computed from the cell).
@@ -136,6 +145,7 @@ struct Work {
   double* trbuf;               // N x 11 x 64 k-block traces tr_{n,q}
   // adjoint
   double* gbar;                // dL/d alpha~, off_s * nq
+  double* fitw;                // N x LMBD_FITW: dE_k/dI_k(omega_j) of the fitted integrand
   double* pmat;                // off_s*3 x ncol
   double* qmat;                // off_s*3 x ncol
   int ncol;                    // 3 n_freq (n_max - 2)

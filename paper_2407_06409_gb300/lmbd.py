@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_precision.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_memory_budget.argtypes = [_P, ctypes.c_size_t]
         L.lmbd_set_frequency_model.argtypes = [_P, ctypes.c_int, ctypes.c_double]
+        L.lmbd_set_integrand_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_release_workspace.argtypes = [_P]
         L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
         L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
@@ -91,6 +92,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
+                  "lmbd_set_integrand_fit",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
@@ -178,7 +180,23 @@ class LMBD:
     def set_frequency_model(self, model: int, omega_ref: float = 0.0) -> None:
         """FREQ_QUADRATURE (SCS at every node) or FREQ_LORENTZIAN (SCS at 0 and omega_ref, Ha)."""
         _check(lib().lmbd_set_frequency_model(self._h, int(model), float(omega_ref)), "lmbd_set_frequency_model")
-        self._scs_columns = 2 if model == FREQ_LORENTZIAN else self.n_freq + 1
+        self._lorentz = model == FREQ_LORENTZIAN
+        self._update_scs_columns()
+
+    def set_integrand_fit(self, n_fit_nodes: int) -> None:
+        """0: integrand at every quadrature node.  m >= series_order: the fitted integrand of
+        Sec. III.C -- I(omega) at 0 and m fit nodes, phi(omega) by non-negative least squares,
+        E_k = I(0) times the quadrature of phi."""
+        _check(lib().lmbd_set_integrand_fit(self._h, int(n_fit_nodes)), "lmbd_set_integrand_fit")
+        self._fit_nodes = int(n_fit_nodes)
+        self._update_scs_columns()
+
+    def _update_scs_columns(self) -> None:
+        # SCS solves: 0 and omega_ref, or omega = 0 and every frequency at which the integrand
+        # is evaluated (the quadrature nodes, or 0 and the fit nodes)
+        fit = getattr(self, "_fit_nodes", 0)
+        nodes = fit + 1 if fit else self.n_freq
+        self._scs_columns = 2 if getattr(self, "_lorentz", False) else nodes + 1
 
     def release_workspace(self) -> None:
         """Free the context's device workspaces (the next call allocates again)."""
