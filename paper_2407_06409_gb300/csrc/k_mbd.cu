@@ -531,47 +531,40 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
   // per (site, frequency) work items
   for (int e = tid; e < ns * p.n_freq; e += blockDim.x) {
     int s = e / p.n_freq, qq = e % p.n_freq, q = qq + 1;
-    double ct[LMBD_MAX_ORDER_P1];
-#pragma unroll
     const double cwq = p.fit ? w.fitw[(long long)c * LMBD_FITW + qq] : p.cweight[q];
-    for (int n = 0; n < LMBD_MAX_ORDER_P1; ++n) ct[n] = (n >= 2 && n <= nm) ? wk * cwq * (-1.0 / n) : 0.0;
-    // one pass over the 9 components of this site-frequency block: the Krylov entries
-    // v_1..v_{n_max-1} are loaded once, then the inner products <v_j, v_{n-j}> and the
-    // P, Q columns are formed from registers
-    double sums[LMBD_MAX_ORDER_P1];
-#pragma unroll
-    for (int n = 0; n < LMBD_MAX_ORDER_P1; ++n)
-      sums[n] = (s == 0 && n >= 2 && n <= nm) ? w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq] : 0.0;
+    double ct[LMBD_MAX_ORDER_P1];
+    for (int n = 0; n <= nm; ++n) ct[n] = (n >= 2) ? wk * cwq * (-1.0 / n) : 0.0;
+    // inner products <v_j[s], v_l[s]> for 1 <= j <= l, j + l <= n_max
+    double ga = 0.0;
+    for (int n = 2; n <= nm; ++n) {
+      double sum = 0.0;
+      if (s == 0) sum += w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq];
+      for (int j = 1; j <= n - 1; ++j) {
+        const double* Va = V0 + (long long)(j - 1) * w.vstride;
+        const double* Vb = V0 + (long long)(n - j - 1) * w.vstride;
+        for (int al = 0; al < 3; ++al)
+          for (int be = 0; be < 3; ++be) {
+            long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
+            sum += Va[idx] * Vb[idx];
+          }
+      }
+      ga += ct[n] * sum;
+    }
+    w.gbar[(offs + s) * p.nq + q] = ga / w.alphaT[(offs + s) * p.nq + q];
+    // P and Q columns of this frequency
     const double ds = w.dsq[(offs + s) * p.nq + q];
-    for (int comp = 0; comp < 9; ++comp) {
-      const int al = comp / 3, be = comp % 3;
-      const long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
-      double v[(LMBD_MAX_ORDER_P1 - 1)];
-#pragma unroll
-      for (int m = 0; m < (LMBD_MAX_ORDER_P1 - 1); ++m) v[m] = (m < nm - 1) ? V0[(long long)m * w.vstride + idx] : 0.0;
-#pragma unroll
-      for (int n = 2; n < LMBD_MAX_ORDER_P1; ++n)
-        if (n <= nm) {
-#pragma unroll
-          for (int j = 1; j < n; ++j) sums[n] += v[j - 1] * v[n - j - 1];
-        }
-#pragma unroll
-      for (int j = 1; j < (LMBD_MAX_ORDER_P1 - 1) - 1; ++j)
-        if (j <= nm - 2) {
+    for (int j = 1; j <= nm - 2; ++j) {
+      const double* Vj = V0 + (long long)(j - 1) * w.vstride;
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be) {
+          long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
           double a = 0.0;
-#pragma unroll
-          for (int l = 1; l < (LMBD_MAX_ORDER_P1 - 1); ++l)
-            if (l <= nm - 1 - j) a += ct[j + l + 1] * v[l - 1];
-          const long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
-          w.pmat[o] = ds * v[j - 1];
+          for (int l = 1; l <= nm - 1 - j; ++l) a += ct[j + l + 1] * V0[(long long)(l - 1) * w.vstride + idx];
+          long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
+          w.pmat[o] = ds * Vj[idx];
           w.qmat[o] = ds * a;
         }
     }
-    double ga = 0.0;
-#pragma unroll
-    for (int n = 2; n < LMBD_MAX_ORDER_P1; ++n)
-      if (n <= nm) ga += ct[n] * sums[n];
-    w.gbar[(offs + s) * p.nq + q] = ga / w.alphaT[(offs + s) * p.nq + q];
   }
   __syncthreads();
   // X0_s (3 x 3) summed over frequencies
