@@ -29,7 +29,12 @@ the paper's order, one atom (one "central atom k") at a time:
 * optionally (fit_nodes set) the fitted integrand of Sec. III.C: the integrand I(omega) of
   Eq. integrand at omega = 0 and a few fit nodes, the rational phi(omega) = a / (1 + sum_n
   b_n omega^(2n)) with a, b_n >= 0 from non-negative least squares (Lawson-Hanson active set)
-  on the linearised equations, and E_k = I(0) times the integral of phi (Eq. E_MBD_k).
+  on the linearised equations, and E_k = I(0) times the integral of phi (Eq. E_MBD_k);
+* optionally (lanczos_steps set) the polynomial-fit coefficients of Sec. III.A: per centre and
+  frequency, lambda_min and lambda_max of G from m Lanczos steps (Ritz values of the tridiagonal
+  matrix), c_n from the least-squares fit of ln(1 - lambda) by sum_{n=1}^{n_max} c_n lambda^n on
+  [lambda_min, lambda_max] (Eq. diagonal_appr), used in place of -1/n (Eq. polynomial-fit) and
+  held fixed in the forces.
 
 Forces are -d(sum_k w_k E_k)/dR by PyTorch autograd (reverse mode), applied to
 the two phases separately so that memory stays bounded: first E_k with the
@@ -81,6 +86,10 @@ class Params:
     # n_max + 1 values), phi fitted by NNLS, E_k = I(0) * integral of phi, the integral by the
     # n_freq-point quadrature
     fit_nodes: int | None = None
+    # None: c_n = -1/n.  m > 0: c_n per centre and frequency from the polynomial fit of
+    # ln(1 - lambda) on the Lanczos estimate (m steps) of G's spectral interval (Sec. III.A);
+    # forces hold the c_n fixed, as the force expressions of Sec. III.D do
+    lanczos_steps: int | None = None
 
     @property
     def sphere(self) -> float:
@@ -227,6 +236,73 @@ def phi_integral(a, b, omega: np.ndarray, weight: np.ndarray) -> torch.Tensor:
     for n in range(1, b.shape[0] + 1):
         den = den + b[n - 1] * om ** (2 * n)
     return (torch.as_tensor(weight, dtype=_DT) * a / den).sum() / (2.0 * math.pi)
+
+
+# ----------------------------------------------------------------------------------------
+# polynomial-fit series coefficients (Sec. III.A, Eqs. diagonal_appr, eigendecomp,
+# polynomial-fit)
+# ----------------------------------------------------------------------------------------
+def splitmix64_unit(count: int) -> np.ndarray:
+    """Start vector of the Lanczos iteration: entries in [-1, 1) from the SplitMix64 generator
+    (Steele, Lea and Flood 2014; Vigna's reference constants), counter 0, 1, 2, ..."""
+    out = np.empty(count)
+    m64 = (1 << 64) - 1
+    for i in range(count):
+        z = ((i + 1) * 0x9E3779B97F4A7C15) & m64
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m64
+        z ^= z >> 31
+        out[i] = (z >> 11) * 2.0 ** -52 - 1.0
+    return out
+
+
+def lanczos_interval(G: np.ndarray, steps: int) -> tuple[float, float]:
+    """Smallest and largest Ritz value after min(steps, dim) Lanczos steps on the symmetric G
+    (Lanczos 1950; three-term recurrence, no reorthogonalisation), started from the SplitMix64
+    vector.  An exhausted Krylov space (beta = 0) ends the iteration early."""
+    n = G.shape[0]
+    m = min(steps, n)
+    v = splitmix64_unit(n)
+    v = v / np.sqrt(v @ v)
+    v_prev = np.zeros(n)
+    beta = 0.0
+    alphas, betas = [], []
+    for j in range(m):
+        w = G @ v
+        a = float(v @ w)
+        w = w - a * v - beta * v_prev
+        alphas.append(a)
+        b = float(np.sqrt(w @ w))
+        if j == m - 1 or b == 0.0:
+            break
+        betas.append(b)
+        v_prev, v, beta = v, w / b, b
+    Tm = np.diag(alphas) + np.diag(betas, 1) + np.diag(betas, -1)
+    ev = np.linalg.eigvalsh(Tm)
+    return float(ev[0]), float(ev[-1])
+
+
+def log_fit_coefficients(lo: float, hi: float, order: int, target=None) -> np.ndarray:
+    """c_1..c_order of the least-squares polynomial sum_n c_n lambda^n (no constant term, since
+    ln(1 - 0) = 0) closest to target(lambda) = ln(1 - lambda) in L2 on [lo, hi], the integral
+    taken by 64-point Gauss-Legendre quadrature.  Returns c_0..c_order (c_0 = 0).  A degenerate
+    interval gives the Taylor coefficients -1/n."""
+    c = np.zeros(order + 1)
+    if not hi - lo > 1e-12:
+        c[1:] = [-1.0 / n for n in range(1, order + 1)]
+        return c
+    if target is None:
+        if hi >= 1.0:
+            raise ValueError("spectral interval reaches 1: ln(1 - lambda) is not defined")
+        target = lambda lam: np.log1p(-lam)
+    x, w = np.polynomial.legendre.leggauss(64)
+    lam = 0.5 * (hi - lo) * x + 0.5 * (hi + lo)
+    sw = np.sqrt(0.5 * (hi - lo) * w)
+    rho = max(abs(lo), abs(hi))                   # columns in lambda / rho for conditioning
+    V = np.stack([(lam / rho) ** n for n in range(1, order + 1)], axis=1) * sw[:, None]
+    d = np.linalg.lstsq(V, target(lam) * sw, rcond=None)[0]
+    c[1:] = d / rho ** np.arange(1, order + 1)
+    return c
 
 
 # ----------------------------------------------------------------------------------------
@@ -463,6 +539,7 @@ def local_energy(T, alpha_tilde, weight, p: Params):
 
     The central site is site 0, so g_k is rows 0..2 of G = sqrt(A) T sqrt(A).
     In log mode the k-block trace of ln(1 - G) from eigh replaces the series.
+    With lanczos_steps set, c_n of this centre and frequency come from the polynomial fit.
     With fit_nodes set, the values at the nodes are the integrand I(omega_j) of the fit and
     E_k = I(0) * integral of phi (Sec. III.C).
     """
@@ -474,11 +551,16 @@ def local_energy(T, alpha_tilde, weight, p: Params):
             lam, V = torch.linalg.eigh(G)
             term = (V[:3, :] ** 2 * torch.log1p(-lam)[None, :]).sum()
         else:
+            if p.lanczos_steps:
+                lo, hi = lanczos_interval(G.detach().numpy(), p.lanczos_steps)
+                cn = log_fit_coefficients(lo, hi, p.series_order)
+            else:
+                cn = [0.0, 0.0] + [-1.0 / n for n in range(2, p.series_order + 1)]
             gk = G[:3, :]
             y = gk.T
             term = torch.zeros((), dtype=_DT)
             for n in range(2, p.series_order + 1):
-                term = term + (-1.0 / n) * torch.trace(gk @ y)
+                term = term + float(cn[n]) * torch.trace(gk @ y)
                 y = G @ y
         terms.append(term)
     if p.fit_nodes:

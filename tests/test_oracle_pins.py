@@ -625,3 +625,117 @@ def test_fitted_integrand_forces_match_central_finite_differences(omega_ref):
             assert abs(fd - F[a, g]) < 2e-8 + 1e-6 * abs(F[a, g]), (a, g, fd, F[a, g])
             checked += 1
     assert checked >= 6
+
+
+# ---------------------------------------------------------------------------------------
+# polynomial-fit coefficients of Sec. III.A: spectral interval of G from Lanczos, c_n from the
+# least-squares fit of ln(1 - lambda) on it (Eqs. diagonal_appr, polynomial-fit)
+# ---------------------------------------------------------------------------------------
+def test_splitmix64_matches_the_reference_sequence():
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "splitmix64_seed0.txt")) as f:
+        ref = [int(line, 16) for line in f if line.strip() and not line.startswith("#")]
+    u = oracle.splitmix64_unit(len(ref))
+    assert np.array_equal(u, np.array([(z >> 11) * 2.0 ** -52 - 1.0 for z in ref]))
+
+
+def test_lanczos_interval_interlaces_and_converges():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(40, 40))
+    G = 0.1 * (X + X.T)
+    ev = np.linalg.eigvalsh(G)
+    lo, hi = oracle.lanczos_interval(G, 40)          # full Krylov space: the exact extremes
+    assert abs(lo - ev[0]) < 1e-12 and abs(hi - ev[-1]) < 1e-12
+    for m in (2, 5, 12):                              # Ritz values lie inside the spectrum
+        lo, hi = oracle.lanczos_interval(G, m)
+        assert ev[0] - 1e-14 <= lo <= hi <= ev[-1] + 1e-14
+    lo5, hi5 = oracle.lanczos_interval(G, 5)
+    lo12, hi12 = oracle.lanczos_interval(G, 12)
+    assert lo12 <= lo5 and hi12 >= hi5                # more steps widen the estimate
+    # a zero matrix ends the iteration at once
+    assert oracle.lanczos_interval(np.zeros((6, 6)), 10) == (0.0, 0.0)
+
+
+def test_log_fit_is_the_continuous_least_squares_fit():
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+    lo, hi, order = -0.55, 0.72, 6
+    c = oracle.log_fit_coefficients(lo, hi, order)
+    assert c[0] == 0.0
+    # normal equations of the L2 problem with exact moments and adaptive quadrature of the
+    # right-hand side
+    Gm = np.array([[(hi ** (m + n + 1) - lo ** (m + n + 1)) / (m + n + 1) for n in range(1, order + 1)]
+                   for m in range(1, order + 1)])
+    b = np.array([scipy_integrate.quad(lambda x, m=m: x ** m * np.log1p(-x), lo, hi, epsabs=1e-14)[0]
+                  for m in range(1, order + 1)])
+    assert np.allclose(c[1:], np.linalg.solve(Gm, b), rtol=1e-7, atol=1e-9)
+    # a target that is itself such a polynomial is reproduced
+    poly = lambda x: 0.3 * x - 1.7 * x ** 3 + 0.25 * x ** 6
+    cp = oracle.log_fit_coefficients(lo, hi, order, target=poly)
+    assert np.allclose(cp, [0, 0.3, 0, -1.7, 0, 0, 0.25], atol=1e-11)
+    # a point interval gives the Taylor coefficients; an interval reaching 1 is rejected
+    assert np.allclose(oracle.log_fit_coefficients(0.1, 0.1, 4), [0, -1, -0.5, -1 / 3, -0.25])
+    with pytest.raises(ValueError):
+        oracle.log_fit_coefficients(-0.2, 1.01, 4)
+
+
+def test_polynomial_fit_is_closer_to_the_logarithm_than_the_series():
+    # the paper's accuracy fix: in the full-system limit the fitted coefficients bring the
+    # truncated series closer to the log-mode (n_max -> infinity) energy
+    s = inputs.cluster(24, seed=0)
+    pos = s.positions * 0.85
+    base = dict(r_scs=20.0, r_mbd1=20.0, r_mbd2=20.0, r_sphere=20.0, n_freq=12)
+
+    def total(**kw):
+        p = oracle.Params(**{**base, **kw})
+        return oracle.System(pos, None, s.species, s.hirshfeld, s.table, p).energies().sum()
+
+    e_log = total(series_order=None)
+    err_series = abs(total(series_order=6) - e_log)
+    err_fit = abs(total(series_order=6, lanczos_steps=20) - e_log)
+    assert err_fit < err_series / 5
+
+
+def test_polynomial_fit_forces_hold_the_coefficients_fixed(monkeypatch):
+    # forces are -dE/dR with every c_n held at its value (Sec. III.D treats them as constants):
+    # central differences with the coefficients replayed from the unmoved structure
+    from oracle import lmbd_oracle as L
+    s = inputs.box(36, seed=11, jitter=0.05)
+    p = oracle.with_params(_P_SMALL, lanczos_steps=12)
+    sysm = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p)
+    recorded = []
+    real = L.log_fit_coefficients
+    monkeypatch.setattr(L, "log_fit_coefficients", lambda *a, **k: recorded.append(real(*a, **k)) or recorded[-1])
+    e0 = sysm.energies()
+    seq = list(recorded)
+    _, F = sysm.energies_forces()
+    it = {"i": 0}
+
+    def replay(*a, **k):
+        c = seq[it["i"] % len(seq)]
+        it["i"] += 1
+        return c
+    monkeypatch.setattr(L, "log_fit_coefficients", replay)
+    h = 1e-4
+    rng = np.random.default_rng(8)
+    checked = 0
+    ref_sets = _site_sets(sysm, range(s.n_atoms))
+    for a in rng.choice(s.n_atoms, 4, replace=False):
+        for g in range(3):
+            es = []
+            for sgn in (1, -1):
+                pos = s.positions.copy()
+                pos[a, g] += sgn * h
+                sp = oracle.System(pos, s.cell, s.species, s.hirshfeld, s.table, p)
+                if _site_sets(sp, range(s.n_atoms)) != ref_sets:
+                    break
+                it["i"] = 0
+                es.append(sp.energies().sum())
+            if len(es) < 2:
+                continue
+            fd = -(es[0] - es[1]) / (2 * h)
+            assert abs(fd - F[a, g]) < 2e-8 + 1e-6 * abs(F[a, g]), (a, g, fd, F[a, g])
+            checked += 1
+    assert checked >= 6
+    # the coefficients differ from -1/n, so the mode is not the plain series
+    ser = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, _P_SMALL).energies()
+    assert np.max(np.abs(e0 - ser) / np.abs(ser)) > 1e-9
