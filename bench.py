@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--large-atoms", type=int, default=2048)
     ap.add_argument("--omega-ref", type=float, default=0.0,
                     help="> 0: the paper's Lorentzian frequency model with this reference frequency (Ha)")
+    ap.add_argument("--lanczos", type=int, default=0,
+                    help="> 0: the paper's polynomial-fit series coefficients from this many Lanczos steps")
     ap.add_argument("--fit-nodes", type=int, default=0,
                     help="> 0: the paper's fitted integrand phi(omega) from omega = 0 and this many fit nodes")
     return ap.parse_args()
@@ -208,6 +210,8 @@ def run_ours(args, world, rank, local):
         model.set_frequency_model(lmbd.FREQ_LORENTZIAN, args.omega_ref)
     if args.fit_nodes > 0:
         model.set_integrand_fit(args.fit_nodes)
+    if args.lanczos > 0:
+        model.set_series_fit(args.lanczos)
     pos = torch.tensor(s.positions, device=dev)
     cell = torch.tensor(s.cell, device=dev)
     sp = torch.tensor(s.species, dtype=torch.int32, device=dev)
@@ -358,7 +362,8 @@ def run_ours(args, world, rank, local):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD + (f"; Lorentzian frequency model, omega_ref {args.omega_ref} Ha"
                                                if args.omega_ref > 0 else "")
-                       + (f"; fitted integrand, {args.fit_nodes} fit nodes" if args.fit_nodes > 0 else ""),
+                       + (f"; fitted integrand, {args.fit_nodes} fit nodes" if args.fit_nodes > 0 else "")
+                       + (f"; polynomial-fit c_n, {args.lanczos} Lanczos steps" if args.lanczos > 0 else ""),
                        "atoms": args.atoms, "parallelism": f"replicas x{world}",
                        "l2": f"inputs resident; per-step working set {st['bytes_workspace'] / 1e9:.1f} GB > 129 MB L2",
                        "sites_per_atom": st["n_sites"] / args.atoms, "max_k1": st["max_k1"],

@@ -193,6 +193,22 @@ int lmbd_set_frequency_model(lmbd_ctx* ctx, int model, double omega_ref);
 #define LMBD_MAX_FIT_NODES 24
 int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes);
 
+/* Series coefficients (Sec. III.A, Eqs. diagonal_appr, eigendecomp and polynomial-fit).
+ * lanczos_steps = 0 (default): c_n = -1/n, the Taylor coefficients of ln(1 - lambda).
+ * lanczos_steps = m (1..LMBD_MAX_LANCZOS): for every central atom and every frequency of the
+ *   integrand, the spectral interval [lambda_min, lambda_max] of the symmetric G = D T_LR D is
+ *   estimated by the extreme Ritz values of min(m, 3 n_sphere) Lanczos steps (three-term
+ *   recurrence without reorthogonalisation, FP64, start vector u_i = SplitMix64 output i mapped
+ *   to [-1, 1) and normalised), and c_1..c_n_max minimise the L2 distance between
+ *   sum_n c_n lambda^n and ln(1 - lambda) on that interval (64-point Gauss-Legendre quadrature);
+ *   these c_n replace -1/n in the energy.  Forces hold the c_n fixed, as the force expressions of
+ *   Sec. III.D do, so they are not the gradient of the c_n's own position dependence.  A call in
+ *   which some interval reaches lambda = 1 (ln(1 - lambda) undefined, a polarisation
+ *   catastrophe) returns LMBD_EMODEL; one whose sphere exceeds 341 sites returns
+ *   LMBD_ECAPACITY in this mode.  Returns LMBD_EINVAL for m outside 0..LMBD_MAX_LANCZOS. */
+#define LMBD_MAX_LANCZOS 64
+int lmbd_set_series_fit(lmbd_ctx* ctx, int lanczos_steps);
+
 /* Device memory budget of the context in bytes (0 = the default: the device's free
  * memory at each call less 1 GiB).  Central atoms are processed in contiguous waves whose
  * per-centre arrays fit the budget: the SCS stage of every centre first (its central

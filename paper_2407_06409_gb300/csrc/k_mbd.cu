@@ -15,6 +15,8 @@
 //   dL/dG = sum_n c_n sum_{j=0}^{n-1} v_j v_{n-1-j}^T (G symmetric),
 //   dL/dalpha~_s = (1/alpha~_s) Tr[(dL/dG) G]_ss = (1/alpha~_s) sum_n c_n sum_j <v_j[s], v_{n-j}[s]>,
 //   dL/dT_st = sum_q D_s D_t (dL/dG)_st, contracted with dT_LR/dr and dT_LR/dS~ per pair.
+#include <algorithm>
+
 #include "lmbd_internal.cuh"
 #include "ozaki.cuh"
 
@@ -204,6 +206,308 @@ __global__ void __launch_bounds__(256) k_mbd_chain(Work w, DevParams p, int m, i
       }
     }
   }
+}
+
+// Series coefficient c_n of centre c at frequency column qq: -1/n (Eq. E_k), or the fitted one.
+__device__ __forceinline__ double series_c(const Work& w, const DevParams& p, int c, int qq, int n) {
+  return p.lanczos ? w.cfit[((long long)c * p.n_freq + qq) * LMBD_MAX_ORDER_P1 + n] : -1.0 / n;
+}
+
+// ---------------------------------------------------------------------------------------
+// polynomial-fit series coefficients (Sec. III.A, Eqs. diagonal_appr and polynomial-fit):
+// per centre and frequency, the spectral interval [lambda_min, lambda_max] of the symmetric
+// G = D T_LR D from m Lanczos steps (three-term recurrence, no reorthogonalisation, start
+// vector from SplitMix64), then c_n, n = 1..n_max, of the L2 fit of ln(1 - lambda) on it.
+// ---------------------------------------------------------------------------------------
+#define LZ_THREADS 256
+#define LZ_RPT 4          // rows per thread: 3 ns <= 1024
+#define LZ_QC 12          // frequencies per pass
+
+// SplitMix64 output for counter i (state 0 advanced i + 1 times), mapped to [-1, 1).
+__device__ __forceinline__ double splitmix_unit(unsigned long long i) {
+  unsigned long long z = (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1p-52 - 1.0;
+}
+
+// Sums the qc per-thread partials v[q] over the block; every thread gets the totals in out[].
+__device__ __forceinline__ void lz_block_sum(const double* v, int qc, double* red, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < qc; ++q) {
+    double t = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[q * (LZ_THREADS / 32) + warp] = t;
+  }
+  __syncthreads();
+  for (int q = 0; q < qc; ++q) {
+    double t = 0.0;
+    for (int k = 0; k < LZ_THREADS / 32; ++k) t += red[q * (LZ_THREADS / 32) + k];
+    out[q] = t;
+  }
+  __syncthreads();
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal (a, b) of order m (Sturm count).
+__device__ int lz_sturm(const double* a, const double* b, int m, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; ++i) {
+    const double off = i > 0 ? b[i - 1] * b[i - 1] / d : 0.0;
+    d = a[i] - x - off;
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Eigenvalue number `which` (0 = smallest, m - 1 = largest) by bisection on the Sturm count.
+__device__ double lz_eig(const double* a, const double* b, int m, int which) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (lz_sturm(a, b, m, mid) > which) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+__global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int c0, int q0, int qc, int L3) {
+  extern __shared__ double lzs[];
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns, N = 3 * ns;
+  double* V = lzs;                                // L3 x qc, row-major
+  double* Vp = V + (size_t)L3 * qc;
+  double* X = Vp + (size_t)L3 * qc;
+  double* al = X + (size_t)L3 * qc;               // qc x LMBD_MAX_LANCZOS
+  double* be = al + qc * LMBD_MAX_LANCZOS;
+  double* red = be + qc * LMBD_MAX_LANCZOS;       // qc x (threads / 32)
+  __shared__ int mq[LZ_QC];                       // steps taken per frequency
+  __shared__ double bprev[LZ_QC];
+  const int tid = threadIdx.x;
+  const double* T = w.tlr + w.off_t[c];
+  const long long offs = w.off_s[c];
+  const int m = min(p.lanczos, N);
+  // start vector u / |u| for every frequency
+  double part[LZ_QC];
+  double tot[LZ_QC];
+  for (int q = 0; q < LZ_QC; ++q) part[q] = 0.0;
+  for (int r = 0; r < LZ_RPT; ++r) {
+    const int i = tid + r * LZ_THREADS;
+    if (i < N) {
+      const double u = splitmix_unit((unsigned long long)i);
+      part[0] += u * u;
+    }
+  }
+  lz_block_sum(part, 1, red, tot);
+  const double inv = 1.0 / sqrt(tot[0]);
+  for (int r = 0; r < LZ_RPT; ++r) {
+    const int i = tid + r * LZ_THREADS;
+    if (i < N) {
+      const double u = splitmix_unit((unsigned long long)i) * inv;
+      for (int q = 0; q < qc; ++q) {
+        V[i * qc + q] = u;
+        Vp[i * qc + q] = 0.0;
+      }
+    }
+  }
+  if (tid < qc) {
+    mq[tid] = 0;
+    bprev[tid] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    // X = D V
+    for (int e = tid; e < N * qc; e += LZ_THREADS) {
+      const int i = e / qc, q = e % qc;
+      X[e] = w.dsq[(offs + i / 3) * p.nq + q0 + q + 1] * V[e];
+    }
+    __syncthreads();
+    // Y = D (T X): T symmetric, so thread i reads column i of row k (coalesced)
+    double y[LZ_RPT][LZ_QC];
+#pragma unroll
+    for (int r = 0; r < LZ_RPT; ++r)
+#pragma unroll
+      for (int q = 0; q < LZ_QC; ++q) y[r][q] = 0.0;
+    for (int k = 0; k < N; ++k) {
+      const double* Tk = T + (long long)k * N;
+      const double* xk = X + k * qc;
+#pragma unroll
+      for (int r = 0; r < LZ_RPT; ++r) {
+        const int i = tid + r * LZ_THREADS;
+        if (i < N) {
+          const double t = Tk[i];
+#pragma unroll
+          for (int q = 0; q < LZ_QC; ++q)
+            if (q < qc) y[r][q] += t * xk[q];
+        }
+      }
+    }
+    // alpha_q = <v_q, y_q>
+    for (int q = 0; q < LZ_QC; ++q) part[q] = 0.0;
+#pragma unroll
+    for (int r = 0; r < LZ_RPT; ++r) {
+      const int i = tid + r * LZ_THREADS;
+      if (i < N) {
+#pragma unroll
+        for (int q = 0; q < LZ_QC; ++q)
+          if (q < qc) {
+            y[r][q] *= w.dsq[(offs + i / 3) * p.nq + q0 + q + 1];
+            part[q] += V[i * qc + q] * y[r][q];
+          }
+      }
+    }
+    double alpha[LZ_QC];
+    lz_block_sum(part, qc, red, alpha);
+    // w = y - alpha v - beta v_prev, beta = |w|
+    for (int q = 0; q < LZ_QC; ++q) part[q] = 0.0;
+#pragma unroll
+    for (int r = 0; r < LZ_RPT; ++r) {
+      const int i = tid + r * LZ_THREADS;
+      if (i < N) {
+#pragma unroll
+        for (int q = 0; q < LZ_QC; ++q)
+          if (q < qc) {
+            y[r][q] = y[r][q] - alpha[q] * V[i * qc + q] - bprev[q] * Vp[i * qc + q];
+            part[q] += y[r][q] * y[r][q];
+          }
+      }
+    }
+    double beta[LZ_QC];
+    lz_block_sum(part, qc, red, beta);
+    for (int q = 0; q < LZ_QC; ++q)
+      if (q < qc) beta[q] = sqrt(beta[q]);
+    if (tid < qc && mq[tid] == j) {           // frequency still running: record step j
+      al[tid * LMBD_MAX_LANCZOS + j] = alpha[tid];
+      mq[tid] = j + 1;
+      if (j < m - 1 && beta[tid] != 0.0) {
+        be[tid * LMBD_MAX_LANCZOS + j] = beta[tid];
+      } else {
+        mq[tid] = -(j + 1);                   // finished with j + 1 steps
+      }
+    }
+    __syncthreads();
+    // v_prev = v, v = w / beta for the frequencies still running
+#pragma unroll
+    for (int r = 0; r < LZ_RPT; ++r) {
+      const int i = tid + r * LZ_THREADS;
+      if (i < N) {
+#pragma unroll
+        for (int q = 0; q < LZ_QC; ++q)
+          if (q < qc && mq[q] > 0) {
+            Vp[i * qc + q] = V[i * qc + q];
+            V[i * qc + q] = y[r][q] / beta[q];
+          }
+      }
+    }
+    if (tid < qc && mq[tid] > 0) bprev[tid] = beta[tid];
+    __syncthreads();
+    bool running = false;
+    for (int q = 0; q < qc; ++q) running |= mq[q] > 0;
+    if (!running) break;
+  }
+  // extremes of the tridiagonal matrices
+  if (tid < qc) {
+    const int mm = mq[tid] < 0 ? -mq[tid] : mq[tid];
+    const double* a = al + tid * LMBD_MAX_LANCZOS;
+    const double* b = be + tid * LMBD_MAX_LANCZOS;
+    double* out = w.lam + ((long long)c * p.n_freq + q0 + tid) * 2;
+    out[0] = lz_eig(a, b, mm, 0);
+    out[1] = lz_eig(a, b, mm, mm - 1);
+  }
+}
+
+// c_0..c_n_max of the L2 fit of ln(1 - lambda) by sum_{n>=1} c_n lambda^n on [lo, hi] (64-point
+// Gauss-Legendre quadrature, columns in lambda / rho, Householder least squares); one thread
+// per (centre, frequency).
+__global__ void __launch_bounds__(128) k_series_fit(Work w, DevParams p, int c0, int c1) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nf = p.n_freq, order = p.order;
+  if (e >= (long long)(c1 - c0) * nf) return;
+  const int c = c0 + (int)(e / nf), q = (int)(e % nf);
+  const double lo = w.lam[((long long)c * nf + q) * 2], hi = w.lam[((long long)c * nf + q) * 2 + 1];
+  double* cf = w.cfit + ((long long)c * nf + q) * LMBD_MAX_ORDER_P1;
+  cf[0] = 0.0;
+  const bool degenerate = !(hi - lo > 1e-12);
+  if (degenerate || !(hi < 1.0)) {            // point interval: Taylor coefficients
+    if (!degenerate) atomicOr(w.status, LMBD_FLAG_MODEL);   // ln(1 - lambda) undefined
+    for (int n = 1; n <= order; ++n) cf[n] = -1.0 / n;
+    return;
+  }
+  const double rho = fmax(fabs(lo), fabs(hi));
+  double A[LMBD_MAX_ORDER_P1 - 1][64];
+  double y[64];
+  for (int i = 0; i < 64; ++i) {
+    const double lam = 0.5 * (hi - lo) * w.gl64[i] + 0.5 * (hi + lo);
+    const double sw = sqrt(0.5 * (hi - lo) * w.gl64[64 + i]);
+    const double t = lam / rho;
+    double pw = 1.0;
+    for (int n = 0; n < order; ++n) {
+      pw *= t;
+      A[n][i] = pw * sw;
+    }
+    y[i] = log1p(-lam) * sw;
+  }
+  double rd[LMBD_MAX_ORDER_P1 - 1];
+  for (int k = 0; k < order; ++k) {
+    double nrm = 0.0;
+    for (int i = k; i < 64; ++i) nrm += A[k][i] * A[k][i];
+    nrm = sqrt(nrm);
+    const double alpha = A[k][k] > 0.0 ? -nrm : nrm;
+    A[k][k] -= alpha;
+    double vv = 0.0;
+    for (int i = k; i < 64; ++i) vv += A[k][i] * A[k][i];
+    rd[k] = alpha;
+    if (vv == 0.0) continue;
+    for (int l = k + 1; l < order; ++l) {
+      double d = 0.0;
+      for (int i = k; i < 64; ++i) d += A[k][i] * A[l][i];
+      d *= 2.0 / vv;
+      for (int i = k; i < 64; ++i) A[l][i] -= d * A[k][i];
+    }
+    double d = 0.0;
+    for (int i = k; i < 64; ++i) d += A[k][i] * y[i];
+    d *= 2.0 / vv;
+    for (int i = k; i < 64; ++i) y[i] -= d * A[k][i];
+  }
+  double dcoef[LMBD_MAX_ORDER_P1 - 1];
+  for (int k = order - 1; k >= 0; --k) {
+    double t = y[k];
+    for (int l = k + 1; l < order; ++l) t -= A[l][k] * dcoef[l];
+    dcoef[k] = t / rd[k];
+  }
+  double rp = 1.0;
+  for (int n = 1; n <= order; ++n) {
+    rp *= rho;
+    cf[n] = dcoef[n - 1] / rp;
+  }
+}
+
+bool launch_series_coefficients(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {
+  if (c1 <= c0) return true;
+  const int L3 = 3 * max_ns;
+  if (L3 > LZ_THREADS * LZ_RPT) return false;
+  // frequencies per pass: three L3 x qc vectors in shared memory next to the recurrence
+  const size_t per_q = sizeof(double) * (3 * (size_t)L3 + 2 * LMBD_MAX_LANCZOS + LZ_THREADS / 32);
+  int qc = (int)((200 * 1024) / per_q);
+  qc = std::max(1, std::min(std::min(qc, LZ_QC), p.n_freq));
+  for (int q0 = 0; q0 < p.n_freq; q0 += qc) {
+    const int n = std::min(qc, p.n_freq - q0);
+    const size_t sm = per_q * n;
+    raise_smem_limit((const void*)k_lanczos, sm);
+    k_lanczos<<<c1 - c0, LZ_THREADS, sm, s>>>(w, p, c0, q0, n, L3);
+  }
+  const long long items = (long long)(c1 - c0) * p.n_freq;
+  k_series_fit<<<(unsigned)((items + 127) / 128), 128, 0, s>>>(w, p, c0, c1);
+  return true;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -475,7 +779,7 @@ __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0)
     for (int n = 2; n <= p.order; ++n) {
       double tr = red[n][3 * q] + red[n][3 * q + 1] + red[n][3 * q + 2];
       w.trbuf[((long long)c * (LMBD_MAX_ORDER_P1)) * 64 + n * 64 + q] = tr;
-      e += (-1.0 / n) * tr;
+      e += series_c(w, p, c, q, n) * tr;
     }
     ival[q] = e;
     epart[q] = e * p.cweight[q + 1];
@@ -533,7 +837,7 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
     int s = e / p.n_freq, qq = e % p.n_freq, q = qq + 1;
     const double cwq = p.fit ? w.fitw[(long long)c * LMBD_FITW + qq] : p.cweight[q];
     double ct[LMBD_MAX_ORDER_P1];
-    for (int n = 0; n <= nm; ++n) ct[n] = (n >= 2) ? wk * cwq * (-1.0 / n) : 0.0;
+    for (int n = 0; n <= nm; ++n) ct[n] = (n >= 2) ? wk * cwq * series_c(w, p, c, qq, n) : 0.0;
     // inner products <v_j[s], v_l[s]> for 1 <= j <= l, j + l <= n_max
     double ga = 0.0;
     for (int n = 2; n <= nm; ++n) {
@@ -577,7 +881,7 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
       const double cwq = p.fit ? w.fitw[(long long)c * LMBD_FITW + qq] : p.cweight[q];
       double sum = 0.0;
       for (int n = 2; n <= nm; ++n)
-        sum += wk * cwq * (-1.0 / n) * V0[(long long)(n - 2) * w.vstride + (long long)(3 * s + al) * ncv + 3 * qq + be];
+        sum += wk * cwq * series_c(w, p, c, qq, n) * V0[(long long)(n - 2) * w.vstride + (long long)(3 * s + al) * ncv + 3 * qq + be];
       acc += dd * sum;
     }
     w.x0buf[(offs + s) * 9 + al * 3 + be] = acc;

@@ -51,6 +51,7 @@ struct Ctx {
   double omega_ref = 0.0;
   int fit_nodes = 0;               // integrand model (lmbd_set_integrand_fit): 0 = quadrature
   std::vector<double> fit_omega;   // omega = 0, then the fit nodes
+  int lanczos = 0;                 // polynomial-fit coefficients (lmbd_set_series_fit): steps
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
   int site_cap = 0;
@@ -62,7 +63,7 @@ struct Ctx {
   DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
   DevBuf site_atom, site_x, counts, offs, totals, status, pcount;
   DevBuf alphaK, alphaI, energies, trbuf, wexp, alphaK_bar, alphaI_bar, gacc, rad_ab, rad_ff;
-  DevBuf order1_d, order3_d, fitw;
+  DevBuf order1_d, order3_d, fitw, cfit, lam, gl64;
   DevBuf arena;
   std::vector<Counts> counts_h;
   std::vector<long long> offs_h;
@@ -73,7 +74,7 @@ struct Ctx {
     DevBuf* l[] = {&table_d, &pos_d, &species_d, &nu_d, &weights_d, &out_e_d, &out_f_d, &abar, &sig, &rvdw,
                    &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
-                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw};
+                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw, &cfit, &lam, &gl64};
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
   size_t whole_bytes() const {
@@ -121,10 +122,10 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n,
-// then mapped to [0, inf) with omega = L (1 + x) / (1 - x).
-void gauss_legendre(int n, double L, std::vector<double>& om, std::vector<double>& w) {
-  std::vector<double> x(n), wx(n);
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre_unit(int n, std::vector<double>& x, std::vector<double>& wx) {
+  x.assign(n, 0.0);
+  wx.assign(n, 0.0);
   const double pi = 3.14159265358979323846;
   for (int i = 0; i < n; ++i) {
     double z = cos(pi * (i + 0.75) / (n + 0.5));
@@ -145,6 +146,12 @@ void gauss_legendre(int n, double L, std::vector<double>& om, std::vector<double
     x[n - 1 - i] = z;
     wx[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
   }
+}
+
+// Gauss-Legendre nodes and weights mapped to [0, inf) with omega = L (1 + x) / (1 - x).
+void gauss_legendre(int n, double L, std::vector<double>& om, std::vector<double>& w) {
+  std::vector<double> x, wx;
+  gauss_legendre_unit(n, x, wx);
   om.resize(n);
   w.resize(n);
   for (int i = 0; i < n; ++i) {
@@ -441,6 +448,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     }
   }
   dp.lorentz = c->lorentz;
+  dp.lanczos = c->lanczos;
   dp.omega_ref = c->omega_ref;
   dp.nqs = c->lorentz ? 2 : nq;
   for (int q = 0; q < dp.nqs; ++q) dp.omega_s[q] = c->lorentz ? (q == 0 ? 0.0 : c->omega_ref) : dp.omega[q];
@@ -652,6 +660,25 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     TRY(ensure(c->fitw, sizeof(double) * LMBD_FITW * (size_t)N));
     w.fitw = (double*)c->fitw.p;
   }
+  if (c->lanczos) {
+    TRY(ensure(c->cfit, sizeof(double) * LMBD_MAX_ORDER_P1 * (size_t)nf * N));
+    TRY(ensure(c->lam, sizeof(double) * 2 * (size_t)nf * N));
+    TRY(ensure(c->gl64, sizeof(double) * 128));
+    static double gl_h[128];
+    static std::once_flag gl_once;
+    std::call_once(gl_once, [] {
+      std::vector<double> x, wx;
+      gauss_legendre_unit(64, x, wx);
+      for (int i = 0; i < 64; ++i) {
+        gl_h[i] = x[i];
+        gl_h[64 + i] = wx[i];
+      }
+    });
+    CK(cudaMemcpyAsync(c->gl64.p, gl_h, sizeof(gl_h), cudaMemcpyHostToDevice, s));
+    w.cfit = (double*)c->cfit.p;
+    w.lam = (double*)c->lam.p;
+    w.gl64 = (const double*)c->gl64.p;
+  }
 
   // ---- waves under the memory budget --------------------------------------------------------
   const Layout L{nq, ncv, nvec, ncol, (ncol + 15) / 16 * 16, ST, DIG_P, c->site_cap, forces, sliced_chain,
@@ -782,6 +809,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       for (int cc = c0; cc < c1; ++cc) {
         launch_mbd_prepare_sized(w, dp, cc, cc + 1, max_ns, s);
         if (sliced_chain) launch_slice_t(w, cc, cc + 1, ST, s);
+        if (dp.lanczos) {
+          if (!launch_series_coefficients(w, dp, cc, cc + 1, max_ns, s)) return LMBD_ECAPACITY;
+          phase_launch[LMBD_PHASE_PREPARE] += 2;
+        }
         for (int m = 1; m < nvec; ++m) {
           const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
           if (sliced_chain)
@@ -798,6 +829,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       mark(LMBD_PHASE_PREPARE);
       launch_mbd_prepare_sized(w, dp, c0, c1, max_ns, s);
       if (sliced_chain) launch_slice_t(w, c0, c1, ST, s);
+      if (dp.lanczos) {
+        if (!launch_series_coefficients(w, dp, c0, c1, max_ns, s)) return LMBD_ECAPACITY;
+        phase_launch[LMBD_PHASE_PREPARE] += 2;
+      }
       mark(LMBD_PHASE_CHAIN);
       for (int m = 1; m < nvec; ++m) {
         const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
@@ -1069,6 +1104,12 @@ int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes) {
   c.fit_omega.assign(1, 0.0);
   c.fit_omega.insert(c.fit_omega.end(), om.begin(), om.end());
   c.fit_nodes = n_fit_nodes;
+  return LMBD_OK;
+}
+
+int lmbd_set_series_fit(lmbd_ctx* ctx, int lanczos_steps) {
+  if (!ctx || lanczos_steps < 0 || lanczos_steps > LMBD_MAX_LANCZOS) return LMBD_EINVAL;
+  ctx->c.lanczos = lanczos_steps;
   return LMBD_OK;
 }
 

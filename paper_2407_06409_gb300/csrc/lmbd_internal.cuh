@@ -18,6 +18,7 @@
                                     // or a fitted phi without decaying term
 #define LMBD_FITW 32                // stride of the per-centre integrand weights dE/dI(omega_j)
 #define LMBD_FIT_ROWS 25            // omega = 0 plus at most 24 fit nodes
+#define LMBD_MAX_LANCZOS 64         // Lanczos steps of the polynomial-fit coefficients
 
 struct DevParams {
   // lengths in bohr
@@ -40,6 +41,8 @@ struct DevParams {
   // nodes; the integral of phi uses the n_phi-point quadrature (phi_omega, phi_wt = w / 2 pi)
   int fit;
   int n_phi;
+  // polynomial-fit series coefficients (Sec. III.A): Lanczos steps, 0 = c_n = -1/n
+  int lanczos;
   double phi_omega[LMBD_MAXQ - 1];
   double phi_wt[LMBD_MAXQ - 1];
 };
@@ -146,6 +149,9 @@ struct Work {
   // adjoint
   double* gbar;                // dL/d alpha~, off_s * nq
   double* fitw;                // N x LMBD_FITW: dE_k/dI_k(omega_j) of the fitted integrand
+  double* cfit;                // N x n_freq x LMBD_MAX_ORDER_P1: fitted c_n per centre and frequency
+  double* lam;                 // N x n_freq x 2: Lanczos estimate of G's spectral interval
+  const double* gl64;          // 64 Gauss-Legendre nodes on [-1, 1], then their weights
   double* pmat;                // off_s*3 x ncol
   double* qmat;                // off_s*3 x ncol
   int ncol;                    // 3 n_freq (n_max - 2)
@@ -247,6 +253,9 @@ size_t scs2_adjoint_smem(int max_n1, int max_n12);
 void launch_mbd_prepare_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_chain_sized(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
+// polynomial-fit coefficients: Lanczos interval of every (centre, frequency), then the fit;
+// returns false when the sphere is too large for the kernel (3 max_ns > 1024)
+bool launch_series_coefficients(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns,
                               cudaStream_t s, int* launches);
 void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);

@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_memory_budget.argtypes = [_P, ctypes.c_size_t]
         L.lmbd_set_frequency_model.argtypes = [_P, ctypes.c_int, ctypes.c_double]
         L.lmbd_set_integrand_fit.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_series_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_release_workspace.argtypes = [_P]
         L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
         L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
@@ -92,7 +93,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
-                  "lmbd_set_integrand_fit",
+                  "lmbd_set_integrand_fit", "lmbd_set_series_fit",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
@@ -190,6 +191,11 @@ class LMBD:
         _check(lib().lmbd_set_integrand_fit(self._h, int(n_fit_nodes)), "lmbd_set_integrand_fit")
         self._fit_nodes = int(n_fit_nodes)
         self._update_scs_columns()
+
+    def set_series_fit(self, lanczos_steps: int) -> None:
+        """0: c_n = -1/n.  m > 0: c_n per centre and frequency from the least-squares fit of
+        ln(1 - lambda) on the m-step Lanczos estimate of G's spectral interval (Sec. III.A)."""
+        _check(lib().lmbd_set_series_fit(self._h, int(lanczos_steps)), "lmbd_set_series_fit")
 
     def _update_scs_columns(self) -> None:
         # SCS solves: 0 and omega_ref, or omega = 0 and every frequency at which the integrand
