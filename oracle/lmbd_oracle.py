@@ -36,6 +36,11 @@ the paper's order, one atom (one "central atom k") at a time:
   [lambda_min, lambda_max] (Eq. diagonal_appr), used in place of -1/n (Eq. polynomial-fit) and
   held fixed in the forces.
 
+The paper's approximate forces (Sec. III.D) are a separate driver, ``System.paper_forces``:
+F_k = -dE^{k,tot}/dr_k of the total energy of atom k's own sphere (Eq. E_k_tot, full trace)
+with dalpha_I/dr = 0 (Eq. full-pol-grad), the full dG/dr_k in the n = 2 term and, for n >= 3,
+dG/dr_k kept only in the row and column of the central atom (Eqs. mbd-forces, cent-appr).
+
 Forces are -d(sum_k w_k E_k)/dR by PyTorch autograd (reverse mode), applied to
 the two phases separately so that memory stays bounded: first E_k with the
 other atoms' central polarisabilities as leaves, then those central
@@ -641,6 +646,10 @@ class System:
             aI = self.central_alpha(need, P)
             return np.array([float(self.energy_of_centre(k, P, aI)) for k in centres])
 
+    def paper_forces(self, centres=None) -> np.ndarray:
+        """The paper's approximate forces (Sec. III.D); see the module function."""
+        return paper_forces(self, centres)
+
     def energies_forces(self, centres=None, weights=None):
         """Energies (eV) of the centres and F = -d(sum_k w_k E_k)/dR (eV/Angstrom), all atoms."""
         centres = list(range(self.n)) if centres is None else [int(c) for c in centres]
@@ -670,9 +679,72 @@ class System:
                 continue
             P = P0.clone().requires_grad_(True)
             aI = self.central_alpha([a], P)[a]
+            if not aI.requires_grad:       # no SCS neighbours: alpha_I does not move
+                continue
             (aI * seed[a]).sum().backward()
             grad += P.grad
         return np.array(energies), (-grad).numpy()
+
+
+def _paper_total(T, alpha_tilde, weight, p: Params):
+    """E^{k,tot} of Eq. E_k_tot in Hartree with the central-atom approximation of Sec. III.D
+    built into its derivative: the n = 2 term sees every block of G, the n >= 3 terms only the
+    blocks in the row and column of the central site (the others enter as constants)."""
+    n3 = T.shape[0]
+    central = torch.zeros(n3, n3, dtype=torch.bool)
+    central[:3, :] = True
+    central[:, :3] = True
+    e = torch.zeros((), dtype=_DT)
+    for q in range(1, alpha_tilde.shape[1]):
+        dq = torch.sqrt(alpha_tilde[:, q]).repeat_interleave(3)
+        G = dq[:, None] * T * dq[None, :]
+        if p.lanczos_steps:
+            lo, hi = lanczos_interval(G.detach().numpy(), p.lanczos_steps)
+            cn = log_fit_coefficients(lo, hi, p.series_order)
+        else:
+            cn = [0.0, 0.0] + [-1.0 / n for n in range(2, p.series_order + 1)]
+        term = float(cn[2]) * torch.trace(G @ G)
+        Gm = torch.where(central, G, G.detach())
+        Y = Gm @ Gm
+        for n in range(3, p.series_order + 1):
+            Y = Y @ Gm
+            term = term + float(cn[n]) * torch.trace(Y)
+        e = e + weight[q] / (2.0 * math.pi) * term
+    return e
+
+
+def paper_forces(sysm: "System", centres=None) -> np.ndarray:
+    """The paper's approximate forces (Sec. III.D) in eV/Angstrom: for every atom k,
+    F_k = -dE^{k,tot}/dr_k of its own sphere (every image of k in the sphere moves with it),
+    with alpha_I held fixed (Eq. full-pol-grad) and the central-atom approximation for n >= 3
+    (Eq. cent-appr).  The frequency integral is the quadrature (the paper's fitted force
+    integrand theta(omega) is not used)."""
+    p = sysm.p
+    if p.series_order is None or p.fit_nodes:
+        raise ValueError("paper forces need the truncated series and the quadrature integral")
+    centres = list(range(sysm.n)) if centres is None else [int(c) for c in centres]
+    need = sorted({int(a) for k in centres for a in sysm.sites(k).atom[: sysm.sites(k).ns]})
+    P0 = torch.as_tensor(sysm.pos)
+    with torch.no_grad():
+        aI0 = sysm.central_alpha(need, P0)
+    ab, sg, rv, a0, r0 = sysm.free()
+    F = np.zeros((sysm.n, 3))
+    for k in centres:
+        P = P0.clone().requires_grad_(True)
+        s = sysm.sites(k)
+        x = site_positions(P, sysm.cell, s, k)
+        _, aK, _, _ = scs_local(x, s, ab, sg, rv, p)
+        ns = s.ns
+        aI = torch.stack([aI0[int(a)] for a in s.atom[:ns]])
+        rb = torch.cat([torch.zeros(1, dtype=_DT), torch.sqrt((x[1:ns] * x[1:ns]).sum(-1))])
+        at = blend(aK, aI, rb, p)
+        T = t_lr(x[:ns], at[:, 0], a0[s.atom[:ns]], r0[s.atom[:ns]], p)
+        if p.omega_ref is not None:
+            at = lorentzian(at[:, 0], at[:, 1], p.omega_ref, sysm.omega)
+        e = _paper_total(T, at, sysm.weight, p) * HARTREE_EV
+        g = torch.autograd.grad(e, P)[0]
+        F[k] = -g[k].numpy()
+    return F
 
 
 def with_params(p: Params, **kw) -> Params:

@@ -739,3 +739,109 @@ def test_polynomial_fit_forces_hold_the_coefficients_fixed(monkeypatch):
     # the coefficients differ from -1/n, so the mode is not the plain series
     ser = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, _P_SMALL).energies()
     assert np.max(np.abs(e0 - ser) / np.abs(ser)) > 1e-9
+
+
+# ---------------------------------------------------------------------------------------
+# the paper's approximate forces (Sec. III.D): F_k = -dE^{k,tot}/dr_k with dalpha_I/dr = 0
+# and the central-atom approximation for n >= 3 (Eqs. full-pol-grad, mbd-forces, cent-appr)
+# ---------------------------------------------------------------------------------------
+def test_paper_forces_are_exact_for_a_dimer():
+    # two atoms outside each other's SCS sphere: E^{k,tot} is the total energy and nothing is
+    # approximated, so the paper's force equals the exact one (and the London-form gradient)
+    table = np.array([[6.0, 20.0, 3.2], [10.0, 44.0, 3.8]])
+    nu = np.array([0.8, 0.93])
+    p = oracle.Params(r_scs=1.0, r_mbd1=10, r_mbd2=10, r_sphere=10, series_order=2, n_freq=120)
+    sysm = _dimer(3.4, table, np.array([0, 1]), nu, p)
+    _, F = sysm.energies_forces()
+    Fp = sysm.paper_forces()
+    assert np.abs(Fp - F).max() < 1e-15 + 1e-12 * np.abs(F).max()
+    # closed form: E = -f(r)^2 C6 / r^6 along the bond
+    a1, w1, R1 = _lorentz(table, 0, nu[0])
+    a2, w2, R2 = _lorentz(table, 1, nu[1])
+    c6 = 1.5 * a1 * a2 * w1 * w2 / (w1 + w2)
+    S = 0.83 * (R1 + R2)
+    x = sysm.pos[1] - sysm.pos[0]
+    r_ang = np.linalg.norm(x)
+
+    def energy(r_ang):
+        r = r_ang / BOHR
+        f = 1 / (1 + math.exp(-6 * (r / S - 1)))
+        return -f * f * c6 / r ** 6 * HA
+
+    h = 1e-5
+    dEdr = (energy(r_ang + h) - energy(r_ang - h)) / (2 * h)
+    assert np.allclose(Fp[1], -dEdr * x / r_ang, rtol=1e-7, atol=0)
+    assert np.allclose(Fp[0], dEdr * x / r_ang, rtol=1e-7, atol=0)
+
+
+def test_paper_forces_are_exact_without_screening_in_the_full_sphere():
+    # no SCS coupling (free polarisabilities) and a sphere holding the whole cluster: every
+    # E^{k,tot} is the total series energy, the rows away from the centre do not move with it,
+    # so the approximation is exact
+    s = inputs.cluster(12, seed=2)
+    p = oracle.Params(r_scs=0.5, r_mbd1=20, r_mbd2=20, r_sphere=20, series_order=6, n_freq=12)
+    sysm = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table, p)
+    _, F = sysm.energies_forces()
+    Fp = sysm.paper_forces()
+    assert np.abs(Fp - F).max() < 1e-12 * np.abs(F).max()
+
+
+def test_paper_forces_two_body_term_by_finite_differences():
+    # n_max = 2: the paper's force is the full derivative of Tr G^2 of the centre's own sphere at
+    # fixed alpha_I; central differences move atom k alone and keep alpha_I at its base value
+    from oracle import lmbd_oracle as L
+    s = inputs.box(36, seed=11, jitter=0.05)
+    p = oracle.with_params(_P_SMALL, series_order=2)
+    sysm = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p)
+    Fp = sysm.paper_forces()
+    ab, sg, rv, a0, r0 = sysm.free()
+    P0 = torch.as_tensor(sysm.pos)
+    with torch.no_grad():
+        aI0 = sysm.central_alpha(range(s.n_atoms), P0)
+
+    def e_tot(k, P):
+        st = sysm.sites(k)
+        x = L.site_positions(P, sysm.cell, st, k)
+        _, aK, _, _ = L.scs_local(x, st, ab, sg, rv, p)
+        aI = torch.stack([aI0[int(a)] for a in st.atom[:st.ns]])
+        rb = torch.cat([torch.zeros(1, dtype=torch.float64), torch.sqrt((x[1:st.ns] ** 2).sum(-1))])
+        at = L.blend(aK, aI, rb, p)
+        T = L.t_lr(x[:st.ns], at[:, 0], a0[st.atom[:st.ns]], r0[st.atom[:st.ns]], p)
+        e = 0.0
+        for q in range(1, at.shape[1]):
+            dq = torch.sqrt(at[:, q]).repeat_interleave(3)
+            G = dq[:, None] * T * dq[None, :]
+            e += float(sysm.weight[q]) / (2 * math.pi) * (-0.5) * float(torch.trace(G @ G))
+        return e * HA
+
+    h = 1e-4
+    ref_sets = _site_sets(sysm, range(s.n_atoms))
+    checked = 0
+    with torch.no_grad():
+        for k in (0, 7, 19, 30, 12, 25):
+            for g in range(3):
+                es = []
+                for sgn in (1, -1):
+                    P = P0.clone()
+                    P[k, g] += sgn * h
+                    sp = oracle.System(P.numpy(), s.cell, s.species, s.hirshfeld, s.table, p)
+                    if _site_sets(sp, range(s.n_atoms)) != ref_sets:
+                        break
+                    es.append(e_tot(k, P))
+                if len(es) < 2:
+                    continue
+                fd = -(es[0] - es[1]) / (2 * h)
+                assert abs(fd - Fp[k, g]) < 2e-9 + 1e-6 * abs(Fp[k, g]), (k, g, fd, Fp[k, g])
+                checked += 1
+    assert checked >= 8
+
+
+def test_paper_forces_differ_from_the_exact_ones_with_screening():
+    # with SCS coupling the approximations (dalpha_I = 0, central rows only for n >= 3) change
+    # the forces, by tens of per cent of the RMS force on this small box
+    s = inputs.box(36, seed=11, jitter=0.05)
+    sysm = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, _P_SMALL)
+    _, F = sysm.energies_forces()
+    Fp = sysm.paper_forces()
+    rel = np.sqrt(((Fp - F) ** 2).mean() / (F ** 2).mean())
+    assert 0.01 < rel < 0.5
