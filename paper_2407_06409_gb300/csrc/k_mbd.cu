@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) k_mbd_chain(Work w, DevParams p, int m, i
 
 // Series coefficient c_n of centre c at frequency column qq: -1/n (Eq. E_k), or the fitted one.
 __device__ __forceinline__ double series_c(const Work& w, const DevParams& p, int c, int qq, int n) {
-  return p.lanczos ? w.cfit[((long long)c * p.n_freq + qq) * LMBD_MAX_ORDER_P1 + n] : -1.0 / n;
+  return p.lanczos ? w.cfit[((long long)c * p.n_freq + qq) * LMBD_MAX_ORDER_P1 + n] : p.cn[n];
 }
 
 // ---------------------------------------------------------------------------------------

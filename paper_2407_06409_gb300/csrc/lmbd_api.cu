@@ -449,6 +449,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   }
   dp.lorentz = c->lorentz;
   dp.lanczos = c->lanczos;
+  for (int n = 1; n < LMBD_MAX_ORDER_P1; ++n) dp.cn[n] = -1.0 / n;
   dp.omega_ref = c->omega_ref;
   dp.nqs = c->lorentz ? 2 : nq;
   for (int q = 0; q < dp.nqs; ++q) dp.omega_s[q] = c->lorentz ? (q == 0 ? 0.0 : c->omega_ref) : dp.omega[q];

@@ -43,6 +43,7 @@ struct DevParams {
   int n_phi;
   // polynomial-fit series coefficients (Sec. III.A): Lanczos steps, 0 = c_n = -1/n
   int lanczos;
+  double cn[LMBD_MAX_ORDER_P1];   // -1/n (Eq. E_k), so that kernels need no FP64 division
   double phi_omega[LMBD_MAXQ - 1];
   double phi_wt[LMBD_MAXQ - 1];
 };

@@ -90,5 +90,6 @@ def test_series_fit_settings_are_checked(lm):
     ref = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table,
                         _op(lm.default_params(r_scs=4.0, r_mbd1=4.0, r_mbd2=4.0, r_sphere=4.0),
                             lanczos_steps=64)).energies()
-    assert np.max(np.abs(e.cpu().numpy() - ref) / np.abs(ref)) < 1e-10
+    # (an atom without neighbours inside the 4 Angstrom sphere has E_k = 0 on both sides)
+    assert np.all(np.abs(e.cpu().numpy() - ref) <= 1e-10 * np.abs(ref))
     assert torch.isfinite(f).all()
