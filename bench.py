@@ -74,6 +74,8 @@ def parse():
                     help="> 0: the paper's Lorentzian frequency model with this reference frequency (Ha)")
     ap.add_argument("--lanczos", type=int, default=0,
                     help="> 0: the paper's polynomial-fit series coefficients from this many Lanczos steps")
+    ap.add_argument("--paper-forces", action="store_true",
+                    help="the paper's approximate forces (Sec. III.D) instead of the exact gradient")
     ap.add_argument("--fit-nodes", type=int, default=0,
                     help="> 0: the paper's fitted integrand phi(omega) from omega = 0 and this many fit nodes")
     return ap.parse_args()
@@ -212,6 +214,8 @@ def run_ours(args, world, rank, local):
         model.set_integrand_fit(args.fit_nodes)
     if args.lanczos > 0:
         model.set_series_fit(args.lanczos)
+    if args.paper_forces:
+        model.set_force_model(lmbd.FORCES_PAPER)
     pos = torch.tensor(s.positions, device=dev)
     cell = torch.tensor(s.cell, device=dev)
     sp = torch.tensor(s.species, dtype=torch.int32, device=dev)
@@ -363,7 +367,8 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD + (f"; Lorentzian frequency model, omega_ref {args.omega_ref} Ha"
                                                if args.omega_ref > 0 else "")
                        + (f"; fitted integrand, {args.fit_nodes} fit nodes" if args.fit_nodes > 0 else "")
-                       + (f"; polynomial-fit c_n, {args.lanczos} Lanczos steps" if args.lanczos > 0 else ""),
+                       + (f"; polynomial-fit c_n, {args.lanczos} Lanczos steps" if args.lanczos > 0 else "")
+                       + ("; the paper's approximate forces" if args.paper_forces else ""),
                        "atoms": args.atoms, "parallelism": f"replicas x{world}",
                        "l2": f"inputs resident; per-step working set {st['bytes_workspace'] / 1e9:.1f} GB > 129 MB L2",
                        "sites_per_atom": st["n_sites"] / args.atoms, "max_k1": st["max_k1"],

@@ -209,6 +209,21 @@ int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes);
 #define LMBD_MAX_LANCZOS 64
 int lmbd_set_series_fit(lmbd_ctx* ctx, int lanczos_steps);
 
+/* Force model (Sec. III.D).
+ * LMBD_FORCES_EXACT (default): forces = -d(sum_k w_k E_k)/dR, the exact gradient of the
+ *   returned energies at fixed Hirshfeld ratios.
+ * LMBD_FORCES_PAPER: the paper's approximate forces, F_k = -dE^{k,tot}/dr_k of the total
+ *   energy of atom k's own sphere (Eq. E_k_tot, full traces, every image of k in the sphere
+ *   moving with it), with the central polarisabilities held fixed (Eq. full-pol-grad), the full
+ *   derivative in the n = 2 term and, for n >= 3, the derivative of G kept only in the row and
+ *   column of the central atom (Eq. cent-appr).  The frequency integral is the quadrature (the
+ *   paper's fitted force integrand theta(omega) is not used), so the mode cannot be combined
+ *   with lmbd_set_integrand_fit (LMBD_EINVAL at the call).  Energies are unchanged; with
+ *   per-atom weights (lmbd_energy_forces_weighted) E^{k,tot} is multiplied by w_k. */
+#define LMBD_FORCES_EXACT 0
+#define LMBD_FORCES_PAPER 1
+int lmbd_set_force_model(lmbd_ctx* ctx, int model);
+
 /* Device memory budget of the context in bytes (0 = the default: the device's free
  * memory at each call less 1 GiB).  Central atoms are processed in contiguous waves whose
  * per-centre arrays fit the budget: the SCS stage of every centre first (its central

@@ -948,7 +948,7 @@ __device__ __forceinline__ void pair_epilogue(const Work& w, long long offs, lon
 // Deterministic reduction of the 16 x 16 pair results of a tile to its row sites (-g, seed)
 // and column sites (+g, seed), then one global atomic per site.
 __device__ __forceinline__ void pair_tile_reduce(const Work& w, long long offs, long long sbase, int ns, int bi,
-                                                 int bj, double (*gp)[PT][4]) {
+                                                 int bj, double (*gp)[PT][4], int only_atom = -1) {
   const int tid = threadIdx.x;
   if (tid < 2 * PT) {
     const int side = tid / PT, l = tid % PT;
@@ -964,7 +964,8 @@ __device__ __forceinline__ void pair_tile_reduce(const Work& w, long long offs, 
     if (ss < ns) {
       const double sgn = side == 0 ? -1.0 : 1.0;
       const int a = w.site_atom[sbase + ss];
-      if (g0 != 0.0 || g1 != 0.0 || g2 != 0.0) atomic_add3(w.gacc + 3 * a, sgn * g0, sgn * g1, sgn * g2);
+      if ((g0 != 0.0 || g1 != 0.0 || g2 != 0.0) && (only_atom < 0 || a == only_atom))
+        atomic_add3(w.gacc + 3 * a, sgn * g0, sgn * g1, sgn * g2);
       if (sb != 0.0) atomicAdd(&w.rbar[offs + ss], sb);
     }
   }
@@ -1076,16 +1077,16 @@ __global__ void __launch_bounds__(256) k_mbd_adj_blend(Work w, DevParams p, int 
         double aK = w.alphaK[(offk1 + s) * p.nqs + q];
         double aI = w.alphaI[(long long)a * p.nqs + q];
         w.alphaK_bar[(offk1 + s) * p.nqs + q] = (1.0 - fs) * g;
-        if (fs != 0.0) atomicAdd(&w.alphaI_bar[(long long)a * p.nqs + q], fs * g);
+        if (fs != 0.0 && !p.paper) atomicAdd(&w.alphaI_bar[(long long)a * p.nqs + q], fs * g);
         gr += dfs * (aI - aK) * g;
-      } else {
+      } else if (!p.paper) {             // the paper's forces hold alpha_I (Eq. full-pol-grad)
         atomicAdd(&w.alphaI_bar[(long long)a * p.nqs + q], g);
       }
     }
     if (s < n1 && s > 0 && gr != 0.0) {
       double ir = 1.0 / r;
       double gx = gr * x0 * ir, gy = gr * x1 * ir, gz = gr * x2 * ir;
-      atomic_add3(w.gacc + 3 * a, gx, gy, gz);
+      if (!p.paper || a == c) atomic_add3(w.gacc + 3 * a, gx, gy, gz);
       g0[0] -= gx; g0[1] -= gy; g0[2] -= gz;
     }
   }
@@ -1095,6 +1096,150 @@ __global__ void __launch_bounds__(256) k_mbd_adj_blend(Work w, DevParams p, int 
 #pragma unroll
     for (int d = 0; d < 3; ++d) g0[d] += __shfl_xor_sync(0xffffffffu, g0[d], o);
   if ((tid & 31) == 0) atomic_add3(w.gacc + 3 * c, g0[0], g0[1], g0[2]);
+}
+
+// ---------------------------------------------------------------------------------------
+// the paper's approximate forces (Sec. III.D, Eqs. mbd-forces and cent-appr): seeds of
+//   L_k = w_k sum_q cw_q [ c_2 Tr G^2 + sum_{n>=3} c_n Tr G~^n ]   (Eq. E_k_tot, full traces)
+// where G~ moves only in the row and column of the central site and alpha_I is held.  The
+// reverse pass is the exact one from here on; position gradients are kept for the images of
+// atom k only (F_k = -dL_k/dr_k).
+//   two-body term:  dL/dalpha~_s = 2 c_2 cw sum_t alpha~_t |T_st|^2,
+//                   pair block M_st = 2 c_2 cw alpha~_s alpha~_t T_st (one block of the pair);
+//   central column: Z_s = sum_{n>=3} n c_n cw v_{n-1}[s], M_s0 += D_s D_0 Z_s,
+//                   dL/dalpha~_s = <Z_s, v_1[s]> / alpha~_s (s > 0),
+//                   dL/dalpha~_0 = sum_{n>=3} n c_n cw tr_n / alpha~_0.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_f3_site(Work w, DevParams p, int c0) {
+  const int c = c0 + blockIdx.x;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns, N = 3 * ns;
+  const long long offs = w.off_s[c];
+  const int ncv = 3 * p.n_freq, nm = p.order, nf = p.n_freq;
+  const double wk = w.weights ? w.weights[c] : 1.0;
+  const int tid = threadIdx.x;
+  const double* T = w.tlr + w.off_t[c];
+  const double* V0 = w.vkr + (offs * 3) * ncv;   // v_1, then v_m at +vstride (m - 1)
+  // two-body term, eight frequencies per pass over the rows of T
+  for (int s = tid; s < ns; s += blockDim.x) {
+    for (int q0 = 0; q0 < nf; q0 += 8) {
+      double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int t = 0; t < ns; ++t) {
+        if (t == s) continue;
+        double n2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const double v = T[(long long)(3 * s + a) * N + 3 * t + b];
+            n2 += v * v;
+          }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (q0 + j < nf) acc[j] += w.alphaT[(offs + t) * p.nq + q0 + j + 1] * n2;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (q0 + j < nf) {
+          const int qq = q0 + j, q = qq + 1;
+          w.gbar[(offs + s) * p.nq + q] = 2.0 * series_c(w, p, c, qq, 2) * wk * p.cweight[q] * acc[j];
+        }
+    }
+  }
+  __syncthreads();
+  // central row and column, n >= 3
+  for (int e = tid; e < ns * nf; e += blockDim.x) {
+    const int s = e / nf, qq = e % nf, q = qq + 1;
+    const double cwq = wk * p.cweight[q];
+    double g = 0.0;
+    if (s == 0) {
+      for (int n = 3; n <= nm; ++n)
+        g += n * series_c(w, p, c, qq, n) * cwq * w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq];
+    } else {
+      for (int n = 3; n <= nm; ++n) {
+        const double* Va = V0 + (long long)(n - 2) * w.vstride;
+        double d = 0.0;
+        for (int al = 0; al < 3; ++al)
+          for (int be = 0; be < 3; ++be) {
+            const long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
+            d += Va[idx] * V0[idx];
+          }
+        g += n * series_c(w, p, c, qq, n) * cwq * d;
+      }
+    }
+    w.gbar[(offs + s) * p.nq + q] += g / w.alphaT[(offs + s) * p.nq + q];
+  }
+  // X0_s = sum_q D_qs D_q0 Z_s, the central-column block of the pair matrix
+  for (int e = tid; e < ns * 9; e += blockDim.x) {
+    const int s = e / 9, al = (e % 9) / 3, be = e % 3;
+    double acc = 0.0;
+    for (int qq = 0; qq < nf; ++qq) {
+      const int q = qq + 1;
+      const double dd = w.dsq[(offs + s) * p.nq + q] * w.dsq[offs * p.nq + q];
+      const double cwq = wk * p.cweight[q];
+      double z = 0.0;
+      for (int n = 3; n <= nm; ++n)
+        z += n * series_c(w, p, c, qq, n) * cwq *
+             V0[(long long)(n - 2) * w.vstride + (long long)(3 * s + al) * ncv + 3 * qq + be];
+      acc += dd * z;
+    }
+    w.x0buf[(offs + s) * 9 + al * 3 + be] = acc;
+  }
+}
+
+// Two-body pair blocks M_st = gamma_st T_LR,st, gamma_st = sum_q 2 c_2 cw_q alpha~_qs alpha~_qt,
+// plus the central column, contracted with the stored pair coefficients (pair_epilogue).
+__global__ void __launch_bounds__(256) k_f3_pair(Work w, DevParams p, int c0, int tiles_per_c) {
+  __shared__ double alt[2][PT][LMBD_MAXQ - 1];
+  __shared__ double cq[LMBD_MAXQ - 1];
+  __shared__ double gp[PT][PT][4];
+  const int c = c0 + blockIdx.x / tiles_per_c;
+  int tile = blockIdx.x % tiles_per_c;
+  if (c >= w.n_atoms) return;
+  const int ns = w.counts[c].ns;
+  const int nt = (ns + PT - 1) / PT;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int bi = 0;
+  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+  const int bj = tile - bi * (bi + 1) / 2;
+  const long long offs = w.off_s[c];
+  const long long sbase = (long long)c * w.site_cap;
+  const int tid = threadIdx.x;
+  const int ty = tid / PT, tx = tid % PT;
+  const int nf = p.n_freq;
+  const double wk = w.weights ? w.weights[c] : 1.0;
+  for (int e = tid; e < 2 * PT * nf; e += blockDim.x) {
+    const int side = e / (PT * nf), l = (e / nf) % PT, qq = e % nf;
+    const int site = (side == 0 ? bi : bj) * PT + l;
+    alt[side][l][qq] = site < ns ? w.alphaT[(offs + site) * p.nq + qq + 1] : 0.0;
+  }
+  for (int qq = tid; qq < nf; qq += blockDim.x) cq[qq] = 2.0 * series_c(w, p, c, qq, 2) * wk * p.cweight[qq + 1];
+  __syncthreads();
+  const int s = bi * PT + ty, t = bj * PT + tx;
+  double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  if (s < ns && t < ns && s > t) {
+    double gamma = 0.0;
+    for (int qq = 0; qq < nf; ++qq) gamma += cq[qq] * alt[0][ty][qq] * alt[1][tx][qq];
+    const double* pc = w.pcoef + w.off_t[c] + 8LL * (s * (s - 1) / 2 + t);
+    const double rr[3] = {pc[0], pc[1], pc[2]};
+    const double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+    const double cg = gamma * pc[5] / 12.0;      // pc[5] = 12 f_LR f / r^5
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc[a][b] = cg * (3.0 * rr[a] * rr[b] - (a == b ? r2 : 0.0));
+  }
+  pair_epilogue(w, offs, w.off_t[c], s, t, ns, acc, gp[ty][tx]);
+  __syncthreads();
+  pair_tile_reduce(w, offs, sbase, ns, bi, bj, gp, c);
+}
+
+void launch_paper_force_seeds(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_f3_site<<<c1 - c0, 256, 0, s>>>(w, p, c0);
+  const int nt = (max_ns + PT - 1) / PT;
+  const int tiles = nt * (nt + 1) / 2;
+  k_f3_pair<<<(c1 - c0) * tiles, 256, 0, s>>>(w, p, c0, tiles);
 }
 
 void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {

@@ -1019,7 +1019,9 @@ __global__ void __launch_bounds__(256) k_scs_site_reduce(Work w, DevParams p, in
       gy += g[3 * q + 1];
       gz += g[3 * q + 2];
     }
-    if (gx != 0.0 || gy != 0.0 || gz != 0.0) atomic_add3(w.gacc + 3 * w.site_atom[sbase + s], gx, gy, gz);
+    const int a = w.site_atom[sbase + s];
+    if (p.paper && a != c) continue;     // the paper's forces: only atom c's own gradient
+    if (gx != 0.0 || gy != 0.0 || gz != 0.0) atomic_add3(w.gacc + 3 * a, gx, gy, gz);
   }
 }
 

@@ -52,6 +52,7 @@ struct Ctx {
   int fit_nodes = 0;               // integrand model (lmbd_set_integrand_fit): 0 = quadrature
   std::vector<double> fit_omega;   // omega = 0, then the fit nodes
   int lanczos = 0;                 // polynomial-fit coefficients (lmbd_set_series_fit): steps
+  int paper_forces = 0;            // force model (lmbd_set_force_model)
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
   int site_cap = 0;
@@ -450,6 +451,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   dp.lorentz = c->lorentz;
   dp.lanczos = c->lanczos;
   for (int n = 1; n < LMBD_MAX_ORDER_P1; ++n) dp.cn[n] = -1.0 / n;
+  dp.paper = c->paper_forces && forces;
+  if (dp.paper && c->fit_nodes) return LMBD_EINVAL;   // the paper fits its force integrand separately
   dp.omega_ref = c->omega_ref;
   dp.nqs = c->lorentz ? 2 : nq;
   for (int q = 0; q < dp.nqs; ++q) dp.omega_s[q] = c->lorentz ? (q == 0 ? 0.0 : c->omega_ref) : dp.omega[q];
@@ -853,11 +856,15 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     CK(cudaMemsetAsync(w.rbar + o.at(O_S, c0), 0, sizeof(double) * o.span(O_S, c0, c1), s));
     if (per_atom) {
       for (int cc = c0; cc < c1; ++cc) {
-        launch_mbd_adj_series(w, dp, cc, cc + 1, s);
-        if (sliced && ncol > 0)
-          launch_mbd_adj_pair_oz2(w, dp, cc, cc + 1, max_ns, DIG_P, s);
-        else
-          launch_mbd_adj_pair(w, dp, cc, cc + 1, max_ns, s);
+        if (dp.paper) {
+          launch_paper_force_seeds(w, dp, cc, cc + 1, max_ns, s);
+        } else {
+          launch_mbd_adj_series(w, dp, cc, cc + 1, s);
+          if (sliced && ncol > 0)
+            launch_mbd_adj_pair_oz2(w, dp, cc, cc + 1, max_ns, DIG_P, s);
+          else
+            launch_mbd_adj_pair(w, dp, cc, cc + 1, max_ns, s);
+        }
         launch_mbd_adj_blend(w, dp, cc, cc + 1, s);
       }
       phase_launch[LMBD_PHASE_ADJ_SERIES] += c1 - c0;
@@ -865,12 +872,17 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       phase_launch[LMBD_PHASE_ADJ_BLEND] += c1 - c0;
     } else {
       mark(LMBD_PHASE_ADJ_SERIES);
-      launch_mbd_adj_series(w, dp, c0, c1, s);
-      mark(LMBD_PHASE_ADJ_PAIR);
-      if (sliced && ncol > 0)
-        launch_mbd_adj_pair_oz2(w, dp, c0, c1, max_ns, DIG_P, s);
-      else
-        launch_mbd_adj_pair(w, dp, c0, c1, max_ns, s);
+      if (dp.paper) {
+        launch_paper_force_seeds(w, dp, c0, c1, max_ns, s);
+        mark(LMBD_PHASE_ADJ_PAIR);
+      } else {
+        launch_mbd_adj_series(w, dp, c0, c1, s);
+        mark(LMBD_PHASE_ADJ_PAIR);
+        if (sliced && ncol > 0)
+          launch_mbd_adj_pair_oz2(w, dp, c0, c1, max_ns, DIG_P, s);
+        else
+          launch_mbd_adj_pair(w, dp, c0, c1, max_ns, s);
+      }
       mark(LMBD_PHASE_ADJ_BLEND);
       launch_mbd_adj_blend(w, dp, c0, c1, s);
       phase_launch[LMBD_PHASE_ADJ_SERIES] += 1;
@@ -1105,6 +1117,12 @@ int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes) {
   c.fit_omega.assign(1, 0.0);
   c.fit_omega.insert(c.fit_omega.end(), om.begin(), om.end());
   c.fit_nodes = n_fit_nodes;
+  return LMBD_OK;
+}
+
+int lmbd_set_force_model(lmbd_ctx* ctx, int model) {
+  if (!ctx || (model != LMBD_FORCES_EXACT && model != LMBD_FORCES_PAPER)) return LMBD_EINVAL;
+  ctx->c.paper_forces = model == LMBD_FORCES_PAPER;
   return LMBD_OK;
 }
 

@@ -44,6 +44,9 @@ struct DevParams {
   // polynomial-fit series coefficients (Sec. III.A): Lanczos steps, 0 = c_n = -1/n
   int lanczos;
   double cn[LMBD_MAX_ORDER_P1];   // -1/n (Eq. E_k), so that kernels need no FP64 division
+  // force model: 0 = exact gradient of sum_k w_k E_k, 1 = the paper's approximate forces
+  // (Sec. III.D: F_k = -dE^{k,tot}/dr_k, alpha_I held, central row and column only for n >= 3)
+  int paper;
   double phi_omega[LMBD_MAXQ - 1];
   double phi_wt[LMBD_MAXQ - 1];
 };
@@ -257,6 +260,8 @@ void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaSt
 // polynomial-fit coefficients: Lanczos interval of every (centre, frequency), then the fit;
 // returns false when the sphere is too large for the kernel (3 max_ns > 1024)
 bool launch_series_coefficients(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
+// seeds of the paper's approximate forces (replace the series and pair-matrix adjoint)
+void launch_paper_force_seeds(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns,
                               cudaStream_t s, int* launches);
 void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblmbd.so")
 LMBD_OK, LMBD_EINVAL, LMBD_ENOMEM, LMBD_NOT_SPD, LMBD_ECUDA, LMBD_ECAPACITY, LMBD_EUNSUPPORTED = range(7)
 LMBD_ESCRATCH, LMBD_EMODEL = 7, 8
 FREQ_QUADRATURE, FREQ_LORENTZIAN = 0, 1
+FORCES_EXACT, FORCES_PAPER = 0, 1
 LAUNCH_BATCHED, LAUNCH_PER_ATOM = 0, 1
 PREC_FP64, PREC_SLICED = 0, 1
 
@@ -84,6 +85,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_frequency_model.argtypes = [_P, ctypes.c_int, ctypes.c_double]
         L.lmbd_set_integrand_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_series_fit.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_force_model.argtypes = [_P, ctypes.c_int]
         L.lmbd_release_workspace.argtypes = [_P]
         L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
         L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
@@ -93,7 +95,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
-                  "lmbd_set_integrand_fit", "lmbd_set_series_fit",
+                  "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
@@ -196,6 +198,10 @@ class LMBD:
         """0: c_n = -1/n.  m > 0: c_n per centre and frequency from the least-squares fit of
         ln(1 - lambda) on the m-step Lanczos estimate of G's spectral interval (Sec. III.A)."""
         _check(lib().lmbd_set_series_fit(self._h, int(lanczos_steps)), "lmbd_set_series_fit")
+
+    def set_force_model(self, model: int) -> None:
+        """FORCES_EXACT (gradient of the energies) or FORCES_PAPER (Sec. III.D approximations)."""
+        _check(lib().lmbd_set_force_model(self._h, int(model)), "lmbd_set_force_model")
 
     def _update_scs_columns(self) -> None:
         # SCS solves: 0 and omega_ref, or omega = 0 and every frequency at which the integrand
