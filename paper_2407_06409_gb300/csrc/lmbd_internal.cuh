@@ -175,9 +175,10 @@ struct Work {
 __device__ __forceinline__ void cutoff_buf(double r, double rc, double rb, double& f, double& df) {
   if (r < rc - rb) { f = 1.0; df = 0.0; return; }
   if (r >= rc) { f = 0.0; df = 0.0; return; }
-  double t = (r - rc + rb) / rb;
+  const double irb = 1.0 / rb;
+  double t = (r - rc + rb) * irb;
   f = 1.0 - 3.0 * t * t + 2.0 * t * t * t;
-  df = (-6.0 * t + 6.0 * t * t) / rb;
+  df = (-6.0 * t + 6.0 * t * t) * irb;
 }
 
 // f_inner (Sec. III.B): 3u^2 - 2u^3 with u = r/r_inner for r < r_inner, else 1.
@@ -191,11 +192,13 @@ __device__ __forceinline__ void finner(double r, double rin, double& f, double& 
 // Fermi damping f(r, S) = 1/(1 + exp(-d (r/S - 1))) (Eq. damping-function) and
 // its partial derivatives with respect to r and S.
 __device__ __forceinline__ void fermi(double r, double s, double d, double& f, double& dfr, double& dfs) {
-  double e = exp(-d * (r / s - 1.0));
+  const double is = 1.0 / s;
+  const double x = r * is;
+  double e = exp(-d * (x - 1.0));
   f = 1.0 / (1.0 + e);
-  double g = f * (1.0 - f) * d / s;   // df/dr
+  double g = f * (1.0 - f) * d * is;  // df/dr
   dfr = g;
-  dfs = -g * r / s;                   // df/dS
+  dfs = -g * x;                       // df/dS
 }
 
 // T_SR written as F(r) [A0(r) I + B0(r) r r^T] (Eq. T_SR with Eqs. g-func, h-func):
