@@ -198,14 +198,13 @@ int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes);
  * lanczos_steps = m (1..LMBD_MAX_LANCZOS): for every central atom and every frequency of the
  *   integrand, the spectral interval [lambda_min, lambda_max] of the symmetric G = D T_LR D is
  *   estimated by the extreme Ritz values of min(m, 3 n_sphere) Lanczos steps (three-term
- *   recurrence without reorthogonalisation, FP64 vectors, products with T_LR summed in
- *   float-float arithmetic (~2^-44 relative), start vector u_i = SplitMix64 output i mapped
+ *   recurrence without reorthogonalisation, FP64, start vector u_i = SplitMix64 output i mapped
  *   to [-1, 1) and normalised), and c_1..c_n_max minimise the L2 distance between
  *   sum_n c_n lambda^n and ln(1 - lambda) on that interval (64-point Gauss-Legendre quadrature);
  *   these c_n replace -1/n in the energy.  Forces hold the c_n fixed, as the force expressions of
  *   Sec. III.D do, so they are not the gradient of the c_n's own position dependence.  A call in
  *   which some interval reaches lambda = 1 (ln(1 - lambda) undefined, a polarisation
- *   catastrophe) returns LMBD_EMODEL; one whose sphere exceeds 256 sites returns
+ *   catastrophe) returns LMBD_EMODEL; one whose sphere exceeds 341 sites returns
  *   LMBD_ECAPACITY in this mode.  Returns LMBD_EINVAL for m outside 0..LMBD_MAX_LANCZOS. */
 #define LMBD_MAX_LANCZOS 64
 int lmbd_set_series_fit(lmbd_ctx* ctx, int lanczos_steps);

@@ -219,8 +219,8 @@ __device__ __forceinline__ double series_c(const Work& w, const DevParams& p, in
 // G = D T_LR D from m Lanczos steps (three-term recurrence, no reorthogonalisation, start
 // vector from SplitMix64), then c_n, n = 1..n_max, of the L2 fit of ln(1 - lambda) on it.
 // ---------------------------------------------------------------------------------------
-#define LZ_THREADS 384
-#define LZ_RPT 2          // rows per thread: 3 ns <= 768
+#define LZ_THREADS 256
+#define LZ_RPT 4          // rows per thread: 3 ns <= 1024
 #define LZ_QC 12          // frequencies per pass
 
 // SplitMix64 output for counter i (state 0 advanced i + 1 times), mapped to [-1, 1).
@@ -324,55 +324,33 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int
     bprev[tid] = 0.0;
   }
   __syncthreads();
-  float2* Xf = reinterpret_cast<float2*>(X);      // D V split into float hi + lo
   for (int j = 0; j < m; ++j) {
-    // X = D V as a float-float pair per entry
+    // X = D V
     for (int e = tid; e < N * qc; e += LZ_THREADS) {
       const int i = e / qc, q = e % qc;
-      const double x = w.dsq[(offs + i / 3) * p.nq + q0 + q + 1] * V[e];
-      const float hi = __double2float_rn(x);
-      Xf[e] = make_float2(hi, __double2float_rn(x - (double)hi));
+      X[e] = w.dsq[(offs + i / 3) * p.nq + q0 + q + 1] * V[e];
     }
     __syncthreads();
-    // Y = D (T X): T symmetric, so thread i reads column i of row k (coalesced).  Each T entry
-    // is split once into float hi + lo and serves every frequency; the products are summed in
-    // float-float arithmetic on the FP32 pipe (t_hi x_hi exact by FMA and two-sum, the cross
-    // terms t_hi x_lo + t_lo x_hi into the low word): relative error ~2^-44 of sum |t x|.
-    float ah[LZ_RPT][LZ_QC], alo[LZ_RPT][LZ_QC];
+    // Y = D (T X): T symmetric, so thread i reads column i of row k (coalesced)
+    double y[LZ_RPT][LZ_QC];
 #pragma unroll
     for (int r = 0; r < LZ_RPT; ++r)
 #pragma unroll
-      for (int q = 0; q < LZ_QC; ++q) ah[r][q] = alo[r][q] = 0.f;
+      for (int q = 0; q < LZ_QC; ++q) y[r][q] = 0.0;
     for (int k = 0; k < N; ++k) {
       const double* Tk = T + (long long)k * N;
-      const float2* xk = Xf + k * qc;
+      const double* xk = X + k * qc;
 #pragma unroll
       for (int r = 0; r < LZ_RPT; ++r) {
         const int i = tid + r * LZ_THREADS;
         if (i < N) {
           const double t = Tk[i];
-          const float th = __double2float_rn(t);
-          const float tl = __double2float_rn(t - (double)th);
 #pragma unroll
           for (int q = 0; q < LZ_QC; ++q)
-            if (q < qc) {
-              const float2 x = xk[q];
-              const float pr = th * x.x;
-              const float pe = fmaf(th, x.x, -pr);
-              const float sm = ah[r][q] + pr;
-              const float bp = sm - ah[r][q];
-              const float er = (ah[r][q] - (sm - bp)) + (pr - bp);
-              ah[r][q] = sm;
-              alo[r][q] += fmaf(th, x.y, fmaf(tl, x.x, er + pe));
-            }
+            if (q < qc) y[r][q] += t * xk[q];
         }
       }
     }
-    double y[LZ_RPT][LZ_QC];
-#pragma unroll
-    for (int r = 0; r < LZ_RPT; ++r)
-#pragma unroll
-      for (int q = 0; q < LZ_QC; ++q) y[r][q] = (double)ah[r][q] + (double)alo[r][q];
     // alpha_q = <v_q, y_q>
     for (int q = 0; q < LZ_QC; ++q) part[q] = 0.0;
 #pragma unroll
