@@ -224,6 +224,19 @@ int lmbd_set_series_fit(lmbd_ctx* ctx, int lanczos_steps);
 #define LMBD_FORCES_PAPER 1
 int lmbd_set_force_model(lmbd_ctx* ctx, int model);
 
+/* Autotuner of the SCS launch shapes.  The local SCS systems are launched in buckets of
+ * central atoms whose |K1| lies within a width w (shared memory, and with it the blocks per
+ * SM, is sized for the largest system of a bucket; narrow buckets waste less shared memory,
+ * wide ones launch less often).  lmbd_autotune runs the given structure (the arguments of
+ * lmbd_energy_forces; forces may be NULL) twice for each w in {2, 3, 4, 6, 8, 12, 16}, times the
+ * SCS and SCS-adjoint phases with CUDA events on the stream, keeps the fastest w in the
+ * context for later calls and returns it in *bucket_width (if not NULL).  Results do not depend
+ * on w.  The outputs hold the last call's values.  Batched launch mode only (LMBD_EINVAL
+ * otherwise).  Default w = 6. */
+int lmbd_autotune(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell, const int* species,
+                  const double* hirshfeld_ratios, double* energies, double* forces, void* cuda_stream,
+                  int* bucket_width);
+
 /* Device memory budget of the context in bytes (0 = the default: the device's free
  * memory at each call less 1 GiB).  Central atoms are processed in contiguous waves whose
  * per-centre arrays fit the budget: the SCS stage of every centre first (its central

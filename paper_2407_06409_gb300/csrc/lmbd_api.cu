@@ -53,6 +53,7 @@ struct Ctx {
   std::vector<double> fit_omega;   // omega = 0, then the fit nodes
   int lanczos = 0;                 // polynomial-fit coefficients (lmbd_set_series_fit): steps
   int paper_forces = 0;            // force model (lmbd_set_force_model)
+  int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
   int site_cap = 0;
@@ -364,7 +365,7 @@ struct Bucket {
   int b0, b1, n1, n12;
 };
 void make_buckets(const std::vector<Counts>& cnt, const std::vector<int>& cuts, std::vector<int>& order,
-                  std::vector<std::vector<Bucket>>& buckets) {
+                  std::vector<std::vector<Bucket>>& buckets, int width) {
   const int N = (int)cnt.size();
   order.resize(N);
   for (int i = 0; i < N; ++i) order[i] = i;
@@ -376,7 +377,7 @@ void make_buckets(const std::vector<Counts>& cnt, const std::vector<int>& cuts, 
     while (b0 < c1) {
       const int lo = cnt[order[b0]].n1;
       int b1 = b0, n1m = 0, n12m = 0;
-      while (b1 < c1 && cnt[order[b1]].n1 < lo + 6) {
+      while (b1 < c1 && cnt[order[b1]].n1 < lo + width) {
         n1m = std::max(n1m, cnt[order[b1]].n1);
         n12m = std::max(n12m, cnt[order[b1]].n12);
         ++b1;
@@ -750,12 +751,12 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   }
   char* const arena = (char*)c->arena.p;
   std::vector<std::vector<Bucket>> bucketsA, bucketsC;
-  make_buckets(c->counts_h, cutA, c->order1_h, bucketsA);
+  make_buckets(c->counts_h, cutA, c->order1_h, bucketsA, c->bucket_width);
   CK(cudaMemcpyAsync(c->order1_d.p, c->order1_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
   const int* orderA = (const int*)c->order1_d.p;
   const int* orderC = orderA;
   if (forces && cutC != cutA) {
-    make_buckets(c->counts_h, cutC, c->order3_h, bucketsC);
+    make_buckets(c->counts_h, cutC, c->order3_h, bucketsC, c->bucket_width);
     CK(cudaMemcpyAsync(c->order3_d.p, c->order3_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
     orderC = (const int*)c->order3_d.p;
   } else {
@@ -1066,6 +1067,41 @@ int lmbd_energy_forces(lmbd_ctx* ctx, int n_atoms, const double* positions, cons
                        void* stream) {
   return lmbd_energy_forces_weighted(ctx, n_atoms, positions, cell, species, hirshfeld, nullptr, energies,
                                      forces, stream);
+}
+
+int lmbd_autotune(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell, const int* species,
+                  const double* hirshfeld, double* energies, double* forces, void* stream, int* bucket_width) {
+  if (!ctx || n_atoms <= 0 || !positions || !species || !hirshfeld || !energies) return LMBD_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.launch_mode != LMBD_LAUNCH_BATCHED) return LMBD_EINVAL;
+  static const int cand[] = {2, 3, 4, 6, 8, 12, 16};
+  const int save_prof = c.profiling, save_w = c.bucket_width;
+  int st = lmbd_set_profiling(ctx, 1);
+  if (st != LMBD_OK) return st;
+  double best = 1e300;
+  int best_w = save_w;
+  for (int wdt : cand) {
+    c.bucket_width = wdt;
+    double t = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {       // the first call settles allocations, the second is timed
+      st = run(&c, n_atoms, positions, cell, species, hirshfeld, nullptr, energies, forces, (cudaStream_t)stream);
+      if (st != LMBD_OK) {
+        cudaGetLastError();
+        c.bucket_width = save_w;
+        c.profiling = save_prof;
+        return st;
+      }
+      t = c.stats.ms[LMBD_PHASE_SCS] + c.stats.ms[LMBD_PHASE_ADJ_SCS];
+    }
+    if (t < best) {
+      best = t;
+      best_w = wdt;
+    }
+  }
+  c.bucket_width = best_w;
+  c.profiling = save_prof;
+  if (bucket_width) *bucket_width = best_w;
+  return LMBD_OK;
 }
 
 int lmbd_set_profiling(lmbd_ctx* ctx, int on) {

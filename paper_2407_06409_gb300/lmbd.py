@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_integrand_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_series_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_force_model.argtypes = [_P, ctypes.c_int]
+        L.lmbd_autotune.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]
         L.lmbd_release_workspace.argtypes = [_P]
         L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
         L.lmbd_get_central_polarizabilities.argtypes = [_P, _P, _P]
@@ -95,7 +96,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
-                  "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model",
+                  "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_autotune",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
@@ -248,6 +249,24 @@ class LMBD:
             raise LmbdError(status, "lmbd_energy_forces")
         del k1, k2, k3, k4, k5
         return e, f
+
+    def autotune(self, positions, cell, species, hirshfeld, forces: bool = True, stream=None) -> int:
+        """Pick the SCS bucket width for this kind of structure (lmbd_autotune); returns it."""
+        torch = _torch()
+        dev = positions.device if isinstance(positions, torch.Tensor) else torch.device("cpu")
+        n = int(positions.shape[0])
+        pp, k1 = _as_arg(positions, torch.float64)
+        cp, k2 = _as_arg(cell, torch.float64)
+        sp, k3 = _as_arg(species, torch.int32)
+        hp, k4 = _as_arg(hirshfeld, torch.float64)
+        e = torch.empty(n, dtype=torch.float64, device=dev)
+        f = torch.empty((n, 3), dtype=torch.float64, device=dev) if forces else None
+        width = ctypes.c_int(0)
+        _check(lib().lmbd_autotune(self._h, n, pp, cp, sp, hp, ctypes.c_void_p(e.data_ptr()),
+                                   ctypes.c_void_p(f.data_ptr()) if f is not None else None,
+                                   _stream_ptr(stream, dev), ctypes.byref(width)), "lmbd_autotune")
+        del k1, k2, k3, k4
+        return int(width.value)
 
     def central_polarizabilities(self, n: int, device="cpu"):
         torch = _torch()
