@@ -56,6 +56,11 @@ struct Ctx {
   int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
+  // side streams for independent bucket launches (same priority as the caller's stream)
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+  int side_prio = 0;
   int site_cap = 0;
   int last_n = 0;
   lmbd_stats stats{};
@@ -388,12 +393,49 @@ void make_buckets(const std::vector<Counts>& cnt, const std::vector<int>& cuts, 
   }
 }
 
+// Side streams with the priority of s, created on first use (or again when the priority changes).
+int side_streams(Ctx* c, cudaStream_t s) {
+  int prio = 0;
+  if (cudaStreamGetPriority(s, &prio) != cudaSuccess) prio = 0;
+  if (c->side[0] && prio == c->side_prio) return LMBD_OK;
+  for (int i = 0; i < Ctx::kSide; ++i) {
+    if (c->side[i]) cudaStreamDestroy(c->side[i]);
+    c->side[i] = nullptr;
+    if (cudaStreamCreateWithPriority(&c->side[i], cudaStreamNonBlocking, prio) != cudaSuccess) return LMBD_ECUDA;
+    if (!c->join_ev[i] && cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      return LMBD_ECUDA;
+  }
+  if (!c->fork_ev && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess) return LMBD_ECUDA;
+  c->side_prio = prio;
+  return LMBD_OK;
+}
+
+// Launches of independent buckets spread over s and the side streams: fork after the work
+// already queued on s, join back into s at the end.
+struct Fork {
+  Ctx* c;
+  cudaStream_t s;
+  int n;
+  Fork(Ctx* c_, cudaStream_t s_, int buckets) : c(c_), s(s_), n(std::min(buckets, Ctx::kSide + 1)) {
+    cudaEventRecord(c->fork_ev, s);
+    for (int i = 0; i + 1 < n; ++i) cudaStreamWaitEvent(c->side[i], c->fork_ev, 0);
+  }
+  cudaStream_t stream(int b) const { return b % n == 0 ? s : c->side[b % n - 1]; }
+  void join() {
+    for (int i = 0; i + 1 < n; ++i) {
+      cudaEventRecord(c->join_ev[i], c->side[i]);
+      cudaStreamWaitEvent(s, c->join_ev[i], 0);
+    }
+  }
+};
+
 int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec_in, const double* nu_in,
         const double* w_in, double* e_out, double* f_out, cudaStream_t s) {
   lmbd_stats st{};
   c->stats = st;
   c->last_n = N;
   if (N == 0) return LMBD_OK;
+  TRY(side_streams(c, s));
   const lmbd_params& P = c->prm;
   // frequencies at which the integrand is evaluated: the quadrature nodes, or omega = 0 and
   // the fit nodes of the fitted integrand
@@ -778,7 +820,12 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         launch_scs_factor(w, dp, nullptr, cc, cc + 1, c->counts_h[cc].n1, c->counts_h[cc].n12, s);
       phase_launch[LMBD_PHASE_SCS] += c1 - c0;
     } else {
-      for (const Bucket& b : bk[wv]) launch_scs_factor(w, dp, order, b.b0, b.b1, b.n1, b.n12, s);
+      Fork fk(c, s, (int)bk[wv].size());
+      for (size_t i = 0; i < bk[wv].size(); ++i) {
+        const Bucket& b = bk[wv][i];
+        launch_scs_factor(w, dp, order, b.b0, b.b1, b.n1, b.n12, fk.stream((int)i));
+      }
+      fk.join();
       phase_launch[LMBD_PHASE_SCS] += (int)bk[wv].size();
     }
     CK(cudaGetLastError());
@@ -911,7 +958,12 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         }
         phase_launch[LMBD_PHASE_ADJ_SCS] += 2 * (c1 - c0);
       } else {
-        for (const Bucket& b : bucketsC[wv]) launch_scs_adjoint2(w, dp, orderC, b.b0, b.b1, b.n1, b.n12, s);
+        Fork fk(c, s, (int)bucketsC[wv].size());
+        for (size_t i = 0; i < bucketsC[wv].size(); ++i) {
+          const Bucket& b = bucketsC[wv][i];
+          launch_scs_adjoint2(w, dp, orderC, b.b0, b.b1, b.n1, b.n12, fk.stream((int)i));
+        }
+        fk.join();
         launch_scs_site_reduce(w, dp, c0, c1, s);
         phase_launch[LMBD_PHASE_ADJ_SCS] += (int)bucketsC[wv].size() + 1;
       }
@@ -1248,6 +1300,11 @@ int lmbd_destroy(lmbd_ctx* ctx) {
   release(c.arena);
   for (int i = 0; i <= LMBD_NPHASE; ++i)
     if (c.ev[i]) cudaEventDestroy(c.ev[i]);
+  for (int i = 0; i < Ctx::kSide; ++i) {
+    if (c.side[i]) cudaStreamDestroy(c.side[i]);
+    if (c.join_ev[i]) cudaEventDestroy(c.join_ev[i]);
+  }
+  if (c.fork_ev) cudaEventDestroy(c.fork_ev);
   if (c.totals_h) cudaFreeHost(c.totals_h);
   if (c.status_h) cudaFreeHost(c.status_h);
   delete ctx;
