@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default SCS bucket width")
     ap.add_argument("--paper-forces", action="store_true",
                     help="the paper's approximate forces (Sec. III.D) instead of the exact gradient")
+    ap.add_argument("--mma", default="warp", choices=["warp", "tc05"],
+                    help="tensor-core path of the sliced chain product: warp-level mma.sync or tcgen05")
     ap.add_argument("--fit-nodes", type=int, default=0,
                     help="> 0: the paper's fitted integrand phi(omega) from omega = 0 and this many fit nodes")
     return ap.parse_args()
@@ -217,6 +219,7 @@ def run_ours(args, world, rank, local):
         model.set_series_fit(args.lanczos)
     if args.paper_forces:
         model.set_force_model(lmbd.FORCES_PAPER)
+    model.set_mma_path(lmbd.MMA_TC05 if args.mma == "tc05" else lmbd.MMA_WARP)
     pos = torch.tensor(s.positions, device=dev)
     cell = torch.tensor(s.cell, device=dev)
     sp = torch.tensor(s.species, dtype=torch.int32, device=dev)
@@ -300,7 +303,8 @@ def run_ours(args, world, rank, local):
     fp64 = ("scs", "chain", "adj_pair", "adj_scs")
     dom = max(fp64, key=lambda ph: phase_ms.get(ph, 0.0))
     avg_ms = phase_ms[dom] / max(1, phase_launch[dom])
-    kernel_names = {"scs": "k_scs_factor", "chain": "k_chain_oz2", "adj_pair": "k_mbd_adj_pair_oz2",
+    kernel_names = {"scs": "k_scs_factor", "chain": "k_chain_tc" if args.mma == "tc05" else "k_chain_oz2",
+                    "adj_pair": "k_pair_tc" if args.mma == "tc05" else "k_mbd_adj_pair_oz2",
                     "adj_scs": "k_scs_adjoint2"}
     st_last = model.stats()
     if dom == "scs":
@@ -375,7 +379,7 @@ def run_ours(args, world, rank, local):
                        "atoms": args.atoms, "parallelism": f"replicas x{world}",
                        "l2": f"inputs resident; per-step working set {st['bytes_workspace'] / 1e9:.1f} GB > 129 MB L2",
                        "sites_per_atom": st["n_sites"] / args.atoms, "max_k1": st["max_k1"],
-                       "scs_bucket_width": bucket_width,
+                       "scs_bucket_width": bucket_width, "chain_mma": args.mma,
                        "max_sphere": st["max_sphere"]},
             "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "per_atom_launch": per_atom, "clocks": clocks}

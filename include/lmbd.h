@@ -50,6 +50,8 @@ extern "C" {
 #define LMBD_EUNSUPPORTED  6  /* option not supported (e.g. series order out of range)           */
 #define LMBD_ESCRATCH      7  /* problem larger than the allocation-free entry point's scratch   */
 #define LMBD_EMODEL        8  /* frequency or integrand model not applicable (see below)        */
+#define LMBD_ETIMEOUT      9  /* a bounded wait inside a tensor-core kernel ran out; the kernel
+                                 drained its own copies, freed its tensor memory and returned   */
 
 #define LMBD_MAX_FREQ      64 /* maximum number of quadrature frequencies                        */
 #define LMBD_MAX_ORDER     10 /* maximum series order n_max                                      */
@@ -160,6 +162,22 @@ int lmbd_set_launch_mode(lmbd_ctx* ctx, int mode);
 #define LMBD_PREC_FP64   0
 #define LMBD_PREC_SLICED 1
 int lmbd_set_precision(lmbd_ctx* ctx, int mode);
+
+/* Tensor-core instruction path of the two sliced products: the Krylov chain T_LR W (Eq. E_k;
+ * the matrix-vector products of the series, all frequencies at once) and the adjoint pair
+ * matrix P Q^T (the derivative pieces of Sec. III.D).  Same digit slices, same exact integer
+ * recombination, so results agree to the last bits (the FP32 accumulation of the
+ * lowest-order digit groups may round in another order).
+ * LMBD_MMA_WARP (default): warp-level mma.sync, 64 x 48 chain tiles, 48 x 48 pair tiles.
+ * LMBD_MMA_TC05: fifth-generation tensor cores, tcgen05.mma issued by one thread per CTA,
+ * FP32 accumulators in tensor memory (one per digit order), operands staged in 64-byte
+ * swizzled shared memory; 128 x 48 chain tiles, 126 x 96 pair tiles (42 x 32 sites); needs
+ * sm_100a/sm_103a.  A device wait that runs out returns LMBD_ETIMEOUT.
+ * Ignored under LMBD_PREC_FP64.
+ * Returns LMBD_EINVAL for another value.                                                      */
+#define LMBD_MMA_WARP 0
+#define LMBD_MMA_TC05 1
+int lmbd_set_mma_path(lmbd_ctx* ctx, int path);
 
 /* Frequency model of the screened polarisabilities.
  * LMBD_FREQ_QUADRATURE (default): the SCS system is solved at omega = 0 and at every

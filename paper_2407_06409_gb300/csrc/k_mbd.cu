@@ -19,6 +19,7 @@
 
 #include "lmbd_internal.cuh"
 #include "ozaki.cuh"
+#include "pair_epilogue.cuh"
 
 // ---------------------------------------------------------------------------------------
 // prepare: blended polarisabilities, SCS radii, T_LR and the first Krylov block
@@ -912,39 +913,6 @@ __device__ __forceinline__ void pair_tile_sites(const Work& w, const DevParams& 
   }
 }
 
-// Contribution of the site pair (s, t), s > t, to dL/dr and dL/dR~ from its pair-matrix
-// block acc = M_st (3 x 3, before the central-column term): T_LR,st = f_LR f(r, S~) T(r), with
-// the geometry and derivative coefficients of the pair stored by k_mbd_prepare.  Returns
-// g = dL/dr_t (= -dL/dr_s) in out[0..2] and the SCS-radius seed beta dL/dS~ in out[3]
-// (zeros when the pair does not couple).
-__device__ __forceinline__ void pair_epilogue(const Work& w, long long offs, long long offt, int s, int t, int ns,
-                                              double (&acc)[3][3], double* out) {
-  out[0] = out[1] = out[2] = out[3] = 0.0;
-  if (!(s < ns && t < ns && s > t)) return;
-  const double* pc = w.pcoef + offt + 8LL * (s * (s - 1) / 2 + t);
-  const double k3 = pc[5];
-  if (k3 == 0.0 && pc[6] == 0.0) return;
-  if (t == 0) {
-    const double* x0 = w.x0buf + (offs + s) * 9;
-#pragma unroll
-    for (int al = 0; al < 3; ++al)
-#pragma unroll
-      for (int be = 0; be < 3; ++be) acc[al][be] += x0[al * 3 + be];
-  }
-  const double rr[3] = {pc[0], pc[1], pc[2]};
-  const double M[6] = {acc[0][0], acc[1][1], acc[2][2], 0.5 * (acc[0][1] + acc[1][0]),
-                       0.5 * (acc[0][2] + acc[2][0]), 0.5 * (acc[1][2] + acc[2][1])};
-  const double Mr[3] = {M[0] * rr[0] + M[3] * rr[1] + M[4] * rr[2], M[3] * rr[0] + M[1] * rr[1] + M[5] * rr[2],
-                        M[4] * rr[0] + M[5] * rr[1] + M[2] * rr[2]};
-  const double trM = M[0] + M[1] + M[2];
-  const double rMr = rr[0] * Mr[0] + rr[1] * Mr[1] + rr[2] * Mr[2];
-  const double radial = pc[3] * rMr + pc[4] * trM;
-  out[0] = radial * rr[0] + k3 * Mr[0];
-  out[1] = radial * rr[1] + k3 * Mr[1];
-  out[2] = radial * rr[2] + k3 * Mr[2];
-  out[3] = pc[6] * rMr + pc[7] * trM;
-}
-
 // Deterministic reduction of the 16 x 16 pair results of a tile to its row sites (-g, seed)
 // and column sites (+g, seed), then one global atomic per site.
 __device__ __forceinline__ void pair_tile_reduce(const Work& w, long long offs, long long sbase, int ns, int bi,
@@ -1477,6 +1445,17 @@ __global__ void __launch_bounds__(288) k_mbd_adj_pair_oz(Work w, DevParams p, in
 void launch_slice_t(const Work& w, int c0, int c1, int st, cudaStream_t s) {
   if (c1 <= c0) return;
   k_slice_t<<<c1 - c0, 256, 0, s>>>(w, c0, st);
+}
+
+void launch_slice_pq(const Work& w, int c0, int c1, int digits, cudaStream_t s) {
+  if (c1 <= c0) return;
+  dim3 g2(c1 - c0, 2);
+  k_slice_pq<<<g2, 256, 0, s>>>(w, c0, digits);
+}
+
+void launch_slice_w(const Work& w, const DevParams& p, int m, int c0, int c1, int digits, cudaStream_t s) {
+  if (c1 <= c0) return;
+  k_slice_w<<<c1 - c0, 256, 0, s>>>(w, p, m, c0, digits);
 }
 
 void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,

@@ -47,6 +47,7 @@ struct Ctx {
   int launch_mode = LMBD_LAUNCH_BATCHED;
   int profiling = 0;
   int precision = LMBD_PREC_SLICED;
+  int mma_path = LMBD_MMA_WARP;
   int lorentz = 0;                 // frequency model (lmbd_set_frequency_model)
   double omega_ref = 0.0;
   int fit_nodes = 0;               // integrand model (lmbd_set_integrand_fit): 0 = quadrature
@@ -679,6 +680,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   // sliced tensor-core products: digits per product (see ozaki.cuh and the design notes)
   const bool sliced = c->precision == LMBD_PREC_SLICED;
   const bool sliced_chain = sliced && ncv <= 48;
+  const bool tc05 = c->mma_path == LMBD_MMA_TC05;
   const int ST = 6, DIG_E = 6, DIG_A = 5, DIG_P = 5;
   TRY(ensure(c->alphaK, sizeof(double) * (size_t)sum_n1 * nq));
   TRY(ensure(c->rad_ab, sizeof(double) * 2 * (size_t)sum_n1 * nq));
@@ -867,7 +869,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         }
         for (int m = 1; m < nvec; ++m) {
           const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
-          if (sliced_chain)
+          if (sliced_chain && tc05)
+            launch_chain_tc(chain_work(dg), dp, m, cc, cc + 1, max_ns, dg, ST, s);
+          else if (sliced_chain)
             launch_chain_oz2(chain_work(dg), dp, m, cc, cc + 1, max_ns, dg, ST, s);
           else
             launch_mbd_chain_sized(w, dp, m, cc, cc + 1, max_ns, s);
@@ -888,7 +892,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       mark(LMBD_PHASE_CHAIN);
       for (int m = 1; m < nvec; ++m) {
         const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
-        if (sliced_chain)
+        if (sliced_chain && tc05)
+          launch_chain_tc(chain_work(dg), dp, m, c0, c1, max_ns, dg, ST, s);
+        else if (sliced_chain)
           launch_chain_oz2(chain_work(dg), dp, m, c0, c1, max_ns, dg, ST, s);
         else
           launch_mbd_chain_sized(w, dp, m, c0, c1, max_ns, s);
@@ -908,7 +914,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
           launch_paper_force_seeds(w, dp, cc, cc + 1, max_ns, s);
         } else {
           launch_mbd_adj_series(w, dp, cc, cc + 1, s);
-          if (sliced && ncol > 0)
+          if (sliced && ncol > 0 && tc05)
+            launch_pair_tc(w, dp, cc, cc + 1, max_ns, DIG_P, s);
+          else if (sliced && ncol > 0)
             launch_mbd_adj_pair_oz2(w, dp, cc, cc + 1, max_ns, DIG_P, s);
           else
             launch_mbd_adj_pair(w, dp, cc, cc + 1, max_ns, s);
@@ -926,7 +934,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       } else {
         launch_mbd_adj_series(w, dp, c0, c1, s);
         mark(LMBD_PHASE_ADJ_PAIR);
-        if (sliced && ncol > 0)
+        if (sliced && ncol > 0 && tc05)
+          launch_pair_tc(w, dp, c0, c1, max_ns, DIG_P, s);
+        else if (sliced && ncol > 0)
           launch_mbd_adj_pair_oz2(w, dp, c0, c1, max_ns, DIG_P, s);
         else
           launch_mbd_adj_pair(w, dp, c0, c1, max_ns, s);
@@ -1035,6 +1045,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   }
   if (*c->status_h & (LMBD_FLAG_NOT_SPD | LMBD_FLAG_NOT_CONVERGED)) return LMBD_NOT_SPD;
   if (*c->status_h & LMBD_FLAG_MODEL) return LMBD_EMODEL;
+  if (*c->status_h & LMBD_FLAG_TIMEOUT) return LMBD_ETIMEOUT;
   return LMBD_OK;
 }
 
@@ -1172,6 +1183,12 @@ int lmbd_set_profiling(lmbd_ctx* ctx, int on) {
 int lmbd_set_precision(lmbd_ctx* ctx, int mode) {
   if (!ctx || (mode != LMBD_PREC_FP64 && mode != LMBD_PREC_SLICED)) return LMBD_EINVAL;
   ctx->c.precision = mode;
+  return LMBD_OK;
+}
+
+int lmbd_set_mma_path(lmbd_ctx* ctx, int path) {
+  if (!ctx || (path != LMBD_MMA_WARP && path != LMBD_MMA_TC05)) return LMBD_EINVAL;
+  ctx->c.mma_path = path;
   return LMBD_OK;
 }
 
@@ -1322,6 +1339,7 @@ const char* lmbd_status_string(int status) {
     case LMBD_EUNSUPPORTED: return "unsupported option";
     case LMBD_ESCRATCH: return "problem exceeds the fixed scratch of the allocation-free entry point";
     case LMBD_EMODEL: return "Lorentzian frequency model not applicable: a polarisability rises between 0 and omega_ref";
+    case LMBD_ETIMEOUT: return "a bounded device wait in a tensor-core kernel ran out";
     default: return "unknown status";
   }
 }

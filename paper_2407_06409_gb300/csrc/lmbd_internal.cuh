@@ -16,6 +16,7 @@
 #define LMBD_FLAG_NOT_CONVERGED 8
 #define LMBD_FLAG_MODEL 16          // Lorentzian model not applicable: alpha~(0) < alpha~(omega_ref),
                                     // or a fitted phi without decaying term
+#define LMBD_FLAG_TIMEOUT 32        // a bounded device wait (tensor-core pipeline) ran out
 #define LMBD_FITW 32                // stride of the per-centre integrand weights dE/dI(omega_j)
 #define LMBD_FIT_ROWS 25            // omega = 0 plus at most 24 fit nodes
 #define LMBD_MAX_LANCZOS 64         // Lanczos steps of the polynomial-fit coefficients
@@ -276,6 +277,17 @@ void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, i
                      cudaStream_t s);
 void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
                       cudaStream_t s);
+// W = D v_m digit planes for chain step m (one block per central atom)
+void launch_slice_w(const Work& w, const DevParams& p, int m, int c0, int c1, int digits, cudaStream_t s);
+// chain step on the fifth-generation tensor cores (tcgen05, TMEM accumulators), digits 5 or 6
+void launch_chain_tc(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
+                     cudaStream_t s);
+size_t chain_tc_smem(int digits);
+// P and Q digit planes (blockIdx.y = 0: P, 1: Q)
+void launch_slice_pq(const Work& w, int c0, int c1, int digits, cudaStream_t s);
+// adjoint pair matrix and its per-pair contraction on the tcgen05 tensor cores (digits 5 only;
+// returns false for another digit count)
+bool launch_pair_tc(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits, cudaStream_t s);
 void launch_mbd_adj_pair_oz2(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
                              cudaStream_t s);
 void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,

@@ -17,11 +17,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblmbd.so")
 
 LMBD_OK, LMBD_EINVAL, LMBD_ENOMEM, LMBD_NOT_SPD, LMBD_ECUDA, LMBD_ECAPACITY, LMBD_EUNSUPPORTED = range(7)
-LMBD_ESCRATCH, LMBD_EMODEL = 7, 8
+LMBD_ESCRATCH, LMBD_EMODEL, LMBD_ETIMEOUT = 7, 8, 9
 FREQ_QUADRATURE, FREQ_LORENTZIAN = 0, 1
 FORCES_EXACT, FORCES_PAPER = 0, 1
 LAUNCH_BATCHED, LAUNCH_PER_ATOM = 0, 1
 PREC_FP64, PREC_SLICED = 0, 1
+MMA_WARP, MMA_TC05 = 0, 1
 
 
 class Species(ctypes.Structure):
@@ -81,6 +82,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_launch_mode.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_profiling.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_precision.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_mma_path.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_memory_budget.argtypes = [_P, ctypes.c_size_t]
         L.lmbd_set_frequency_model.argtypes = [_P, ctypes.c_int, ctypes.c_double]
         L.lmbd_set_integrand_fit.argtypes = [_P, ctypes.c_int]
@@ -95,7 +97,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
-                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
+                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_mma_path", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
                   "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_autotune",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
@@ -176,6 +178,10 @@ class LMBD:
 
     def set_precision(self, mode: int) -> None:
         _check(lib().lmbd_set_precision(self._h, int(mode)), "lmbd_set_precision")
+
+    def set_mma_path(self, path: int) -> None:
+        """Tensor-core path of the sliced products: MMA_TC05 (tcgen05, default) or MMA_WARP (mma.sync)."""
+        _check(lib().lmbd_set_mma_path(self._h, int(path)), "lmbd_set_mma_path")
 
     def set_memory_budget(self, nbytes: int) -> None:
         """Device bytes this context may hold (0 = free memory less 1 GiB); larger inputs run in waves."""
