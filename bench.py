@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default SCS bucket width")
     ap.add_argument("--paper-forces", action="store_true",
                     help="the paper's approximate forces (Sec. III.D) instead of the exact gradient")
-    ap.add_argument("--mma", default="warp", choices=["warp", "tc05"],
+    ap.add_argument("--mma", default="tc05", choices=["warp", "tc05"],
                     help="tensor-core path of the sliced chain product: warp-level mma.sync or tcgen05")
     ap.add_argument("--fit-nodes", type=int, default=0,
                     help="> 0: the paper's fitted integrand phi(omega) from omega = 0 and this many fit nodes")

@@ -168,11 +168,11 @@ int lmbd_set_precision(lmbd_ctx* ctx, int mode);
  * matrix P Q^T (the derivative pieces of Sec. III.D).  Same digit slices, same exact integer
  * recombination, so results agree to the last bits (the FP32 accumulation of the
  * lowest-order digit groups may round in another order).
- * LMBD_MMA_WARP (default): warp-level mma.sync, 64 x 48 chain tiles, 48 x 48 pair tiles.
- * LMBD_MMA_TC05: fifth-generation tensor cores, tcgen05.mma issued by one thread per CTA,
- * FP32 accumulators in tensor memory (one per digit order), operands staged in 64-byte
- * swizzled shared memory; 128 x 48 chain tiles, 126 x 96 pair tiles (42 x 32 sites); needs
- * sm_100a/sm_103a.  A device wait that runs out returns LMBD_ETIMEOUT.
+ * LMBD_MMA_TC05 (default): fifth-generation tensor cores, tcgen05.mma issued by one thread
+ * per CTA, FP32 accumulators in tensor memory (one per digit order), operands staged in
+ * 64-byte swizzled shared memory; 128 x 48 chain tiles, 126 x 96 pair tiles (42 x 32 sites);
+ * needs sm_100a/sm_103a.  A device wait that runs out returns LMBD_ETIMEOUT.
+ * LMBD_MMA_WARP: warp-level mma.sync, 64 x 48 chain tiles, 48 x 48 pair tiles.
  * Ignored under LMBD_PREC_FP64.
  * Returns LMBD_EINVAL for another value.                                                      */
 #define LMBD_MMA_WARP 0

@@ -47,7 +47,7 @@ struct Ctx {
   int launch_mode = LMBD_LAUNCH_BATCHED;
   int profiling = 0;
   int precision = LMBD_PREC_SLICED;
-  int mma_path = LMBD_MMA_WARP;
+  int mma_path = LMBD_MMA_TC05;
   int lorentz = 0;                 // frequency model (lmbd_set_frequency_model)
   double omega_ref = 0.0;
   int fit_nodes = 0;               // integrand model (lmbd_set_integrand_fit): 0 = quadrature
