@@ -1262,8 +1262,10 @@ __global__ void __launch_bounds__(256) k_slice_t(Work w, int c0, int st) {
   if (c >= w.n_atoms) return;
   const int N = 3 * w.counts[c].ns, Mpad = oz_mpad(N), Kpad = oz_kpad(N);
   const double* T = w.tlr + w.off_t[c];
-  unsigned short* base = w.tdig + w.off_tq[c] * st;
-  const long long plane = (long long)Mpad * Kpad;
+  // row pitch: the centre's Kpad, or the common pitch tk of the tcgen05 path (zeros past N)
+  const int ld = w.tk > 0 ? w.tk : Kpad;
+  unsigned short* base = w.tk > 0 ? w.tdig + w.off_tr[c] * st * w.tk : w.tdig + w.off_tq[c] * st;
+  const long long plane = (long long)Mpad * ld;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int row = warp; row < Mpad; row += nw) {
     int mx = 0;
@@ -1273,11 +1275,11 @@ __global__ void __launch_bounds__(256) k_slice_t(Work w, int c0, int st) {
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = oz_scale_exp(mx);
     if (lane == 0) w.texp[w.off_tr[c] + row] = e;
-    for (int j = lane; j < Kpad; j += 32) {
+    for (int j = lane; j < ld; j += 32) {
       const double v = (row < N && j < N) ? T[(long long)row * N + j] : 0.0;
       int d[OZ_MAXS];
       oz_digits(v, e, st, d);
-      for (int k = 0; k < st; ++k) base[k * plane + (long long)row * Kpad + j] = oz_bf16_bits(d[k]);
+      for (int k = 0; k < st; ++k) base[k * plane + (long long)row * ld + j] = oz_bf16_bits(d[k]);
     }
   }
 }
@@ -1292,8 +1294,9 @@ __global__ void __launch_bounds__(256) k_slice_w(Work w, DevParams p, int m, int
   const int ncv = 3 * p.n_freq;
   const double* Vin = w.vkr + (long long)(m - 1) * w.vstride + (offs * 3) * ncv;
   const double* dsq = w.dsq + offs * p.nq;
-  unsigned short* base = w.wdig + w.off_kp[c] * 48 * sw;
-  const long long plane = 48LL * Kpad;
+  const int ld = w.tk > 0 ? w.tk : Kpad;
+  unsigned short* base = w.tk > 0 ? w.wdig + (long long)c * 48 * sw * w.tk : w.wdig + w.off_kp[c] * 48 * sw;
+  const long long plane = 48LL * ld;
   const int tid = threadIdx.x;
   if (tid < 48) cmax[tid] = 0;
   __syncthreads();
@@ -1304,13 +1307,13 @@ __global__ void __launch_bounds__(256) k_slice_w(Work w, DevParams p, int m, int
   }
   __syncthreads();
   if (tid < 48) w.wexp[(long long)c * 48 + tid] = oz_scale_exp(cmax[tid]);
-  for (int e = tid; e < 48 * Kpad; e += blockDim.x) {
-    const int col = e / Kpad, j = e % Kpad;
+  for (int e = tid; e < 48 * ld; e += blockDim.x) {
+    const int col = e / ld, j = e % ld;
     double v = 0.0;
     if (col < ncv && j < N) v = dsq[(j / 3) * p.nq + col / 3 + 1] * Vin[(long long)j * ncv + col];
     int d[OZ_MAXS];
     oz_digits(v, oz_scale_exp(cmax[col]), sw, d);
-    for (int k = 0; k < sw; ++k) base[k * plane + (long long)col * Kpad + j] = oz_bf16_bits(d[k]);
+    for (int k = 0; k < sw; ++k) base[k * plane + (long long)col * ld + j] = oz_bf16_bits(d[k]);
   }
 }
 

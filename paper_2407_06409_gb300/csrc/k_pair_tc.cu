@@ -19,13 +19,15 @@
 namespace {
 
 __device__ __forceinline__ int ptc_kpad(int n) { return (n + 15) / 16 * 16; }
+inline long long ptc_kpad_host(int n) { return (n + 15) / 16 * 16; }
 
 template <int S>
-__global__ void __launch_bounds__(256, 1) k_pair_tc(Work w, DevParams p, int c0, int nb_max, int tiles_per_c) {
+__global__ void __launch_bounds__(256, 1)
+    k_pair_tc(Work w, DevParams p, int c0, int nb_max, int tiles_per_c, const __grid_constant__ CUtensorMap tmP,
+              const __grid_constant__ CUtensorMap tmQ) {
   using Sh = TcsShape<S, PTC_NB>;
   extern __shared__ unsigned char tc_dyn[];
-  __shared__ uint64_t mbar[TCS_NBUF];
-  __shared__ uint32_t tmem_holder;
+  __shared__ TcsBarriers bar;
   const int c = c0 + blockIdx.x / tiles_per_c;
   const int tile = blockIdx.x % tiles_per_c;
   if (c >= w.n_atoms) return;
@@ -34,19 +36,20 @@ __global__ void __launch_bounds__(256, 1) k_pair_tc(Work w, DevParams p, int c0,
   // tiles without a site pair s > t inside the sphere have nothing to do
   if (s0 >= ns || t0 >= ns || min(s0 + PTC_SA, ns) - 1 <= t0) return;
   const int R = 3 * ((ns + 15) / 16 * 16), Kp = ptc_kpad(w.ncol);
-  const long long dbase = w.off_sp[c] * 3 * (long long)Kp * S;
-  const TcsOperand A{w.pdig + dbase + (long long)(3 * s0) * Kp, (long long)R * Kp, Kp, min(3 * PTC_SA, R - 3 * s0)};
-  const TcsOperand B{w.qdig + dbase + (long long)(3 * t0) * Kp, (long long)R * Kp, Kp, min(3 * PTC_SB, R - 3 * t0)};
+  // P and Q digit planes of this centre: rows off_sp[c] 3 S + k R + r of the wave's maps (pitch Kp)
+  const int prow = (int)(w.off_sp[c] * 3 * S - w.prow0);
+  const TcsTile A{&tmP, prow + 3 * s0, R};
+  const TcsTile B{&tmQ, prow + 3 * t0, R};
   const uint32_t sraw = tc_smem_u32(tc_dyn);
   const uint32_t sbase = (sraw + 1023u) & ~1023u;
-  const uint32_t tmem = tcs_setup(&tmem_holder, mbar);
+  const uint32_t tmem = tcs_setup(bar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cb = (warp >> 2) * 48;
   long long Y[48];
 #pragma unroll
   for (int j = 0; j < 48; ++j) Y[j] = 0;
-  int committed = -1;
-  const bool ok = tcs_mainloop<S, PTC_NB>(A, B, Kp, sbase, tmem, mbar, committed, [&]() {
+  int issued = -1, committed = -1;
+  const bool ok = tcs_mainloop<S, PTC_NB>(A, B, Kp, sbase, bar, issued, committed, [&]() {
 #pragma unroll
     for (int g = 0; g < S; ++g)
 #pragma unroll
@@ -57,7 +60,7 @@ __global__ void __launch_bounds__(256, 1) k_pair_tc(Work w, DevParams p, int c0,
         for (int i = 0; i < 8; ++i) Y[j8 * 8 + i] += (long long)__float2int_rn(v[i]) << (7 * (S - 1 - g));
       }
   });
-  tcs_teardown(tmem, !ok, committed, mbar, w.status);
+  tcs_teardown(bar, !ok, issued, committed, w.status);
   if (!ok) return;
 
   // FP64 tile (126 x 96) and per-pair results (42 x 32 x 4) in the drained staging ring
@@ -125,8 +128,13 @@ bool launch_pair_tc(const Work& w, const DevParams& p, int c0, int c1, int max_n
   if (digits != 5) return false;
   launch_slice_pq(w, c0, c1, digits, s);
   const int na = (max_ns + PTC_SA - 1) / PTC_SA, nb = (max_ns + PTC_SB - 1) / PTC_SB;
+  const long long Kp = ptc_kpad_host(w.ncol);
+  CUtensorMap tmP, tmQ;
+  if (!tc_encode_map(&tmP, w.pdig + w.prow0 * Kp, Kp, Kp, w.prows, TCS_M) ||
+      !tc_encode_map(&tmQ, w.qdig + w.prow0 * Kp, Kp, Kp, w.prows, PTC_NB))
+    return false;
   using Sh = TcsShape<5, PTC_NB>;
   raise_smem_limit((const void*)k_pair_tc<5>, Sh::kBytes);
-  k_pair_tc<5><<<(c1 - c0) * na * nb, 256, Sh::kBytes, s>>>(w, p, c0, nb, na * nb);
+  k_pair_tc<5><<<(c1 - c0) * na * nb, 256, Sh::kBytes, s>>>(w, p, c0, nb, na * nb, tmP, tmQ);
   return true;
 }

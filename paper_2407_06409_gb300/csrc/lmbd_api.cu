@@ -233,6 +233,7 @@ struct Layout {
   int nq, ncv, nvec, ncol, kp_pair, st, dig_p, site_cap;
   bool forces, sliced_chain, sliced_pair;
   int nqs;   // frequencies of the SCS solves (stage-1 arrays)
+  int tk;    // tcgen05 path: row pitch of the T and W digit planes (0: per-centre Kpad)
 
   // stage 1 (SCS): pair lists, FP32 factors and solutions of centres [c0, c1)
   size_t stage1(const Offs& o, int c0, int c1, char* base, Work* w) const {
@@ -304,14 +305,24 @@ struct Layout {
       w->vstride = ns * 3 * ncv;
     }
     if (sliced_chain) {
-      unsigned short* tdig = cv.take<unsigned short>((long long)st * o.span(O_TQ, c0, c1), (long long)st * o.at(O_TQ, c0));
+      // T planes: per centre st planes of Mpad rows, row pitch Kpad (warp-level path) or the
+      // common pitch tk (tcgen05 path: one tensor map covers the wave)
+      unsigned short* tdig =
+          tk > 0 ? cv.take<unsigned short>((long long)st * o.span(O_TR, c0, c1) * tk, (long long)st * o.at(O_TR, c0) * tk)
+                 : cv.take<unsigned short>((long long)st * o.span(O_TQ, c0, c1), (long long)st * o.at(O_TQ, c0));
       int* texp = cv.take<int>(o.span(O_TR, c0, c1), o.at(O_TR, c0));
       // W planes: the digit count varies per chain step, so the pointer is rebased per launch
-      unsigned short* wdig = cv.take<unsigned short>(48LL * st * o.span(O_KP, c0, c1), 0);
+      unsigned short* wdig = tk > 0 ? cv.take<unsigned short>(48LL * st * (c1 - c0) * tk, 0)
+                                    : cv.take<unsigned short>(48LL * st * o.span(O_KP, c0, c1), 0);
       if (w) {
         w->tdig = tdig;
         w->texp = texp;
         *wdig_raw = wdig;
+        w->tk = tk;
+        w->trow0 = (long long)st * o.at(O_TR, c0);
+        w->trows = (long long)st * o.span(O_TR, c0, c1);
+        w->wc0 = c0;
+        w->wcn = c1 - c0;
       }
     }
     if (forces) {
@@ -342,6 +353,8 @@ struct Layout {
           w->qdig = qdig;
           w->pexp = pexp;
           w->qexp = qexp;
+          w->prow0 = 3LL * dig_p * sp0;
+          w->prows = 3LL * dig_p * nsp;
         }
       }
     }
@@ -731,7 +744,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
 
   // ---- waves under the memory budget --------------------------------------------------------
   const Layout L{nq, ncv, nvec, ncol, (ncol + 15) / 16 * 16, ST, DIG_P, c->site_cap, forces, sliced_chain,
-                 sliced && ncol > 0, dp.nqs};
+                 sliced && ncol > 0, dp.nqs, tc05 ? (3 * max_ns + 15) / 16 * 16 : 0};
   auto s1 = [&](int a, int b) { return L.stage1(o, a, b, nullptr, nullptr); };
   auto s1x = [&](int a, int b) { return forces ? L.scs_adjoint(o, a, b, nullptr, nullptr) : (size_t)0; };
   auto s2 = [&](int a, int b) { return L.stage2(o, a, b, nullptr, nullptr, nullptr); };
@@ -854,9 +867,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     // W digit planes at the wave's start for the digit count of each chain step
     auto chain_work = [&](int digits) {
       Work wm = w;
+      const long long shift = L.tk > 0 ? (long long)c0 * 48 * digits * L.tk : o.at(O_KP, c0) * 48 * digits;
       if (wdig_raw)
         wm.wdig = reinterpret_cast<unsigned short*>(reinterpret_cast<uintptr_t>(wdig_raw) -
-                                                    (uintptr_t)(o.at(O_KP, c0) * 48 * digits) * sizeof(unsigned short));
+                                                    (uintptr_t)shift * sizeof(unsigned short));
       return wm;
     };
     if (per_atom) {
@@ -869,8 +883,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         }
         for (int m = 1; m < nvec; ++m) {
           const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
-          if (sliced_chain && tc05)
-            launch_chain_tc(chain_work(dg), dp, m, cc, cc + 1, max_ns, dg, ST, s);
+          if (sliced_chain && tc05) {
+            if (!launch_chain_tc(chain_work(dg), dp, m, cc, cc + 1, max_ns, dg, ST, s)) return LMBD_ECUDA;
+          }
           else if (sliced_chain)
             launch_chain_oz2(chain_work(dg), dp, m, cc, cc + 1, max_ns, dg, ST, s);
           else
@@ -892,8 +907,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       mark(LMBD_PHASE_CHAIN);
       for (int m = 1; m < nvec; ++m) {
         const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
-        if (sliced_chain && tc05)
-          launch_chain_tc(chain_work(dg), dp, m, c0, c1, max_ns, dg, ST, s);
+        if (sliced_chain && tc05) {
+          if (!launch_chain_tc(chain_work(dg), dp, m, c0, c1, max_ns, dg, ST, s)) return LMBD_ECUDA;
+        }
         else if (sliced_chain)
           launch_chain_oz2(chain_work(dg), dp, m, c0, c1, max_ns, dg, ST, s);
         else
@@ -914,8 +930,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
           launch_paper_force_seeds(w, dp, cc, cc + 1, max_ns, s);
         } else {
           launch_mbd_adj_series(w, dp, cc, cc + 1, s);
-          if (sliced && ncol > 0 && tc05)
-            launch_pair_tc(w, dp, cc, cc + 1, max_ns, DIG_P, s);
+          if (sliced && ncol > 0 && tc05) {
+            if (!launch_pair_tc(w, dp, cc, cc + 1, max_ns, DIG_P, s)) return LMBD_ECUDA;
+          }
           else if (sliced && ncol > 0)
             launch_mbd_adj_pair_oz2(w, dp, cc, cc + 1, max_ns, DIG_P, s);
           else
@@ -934,8 +951,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       } else {
         launch_mbd_adj_series(w, dp, c0, c1, s);
         mark(LMBD_PHASE_ADJ_PAIR);
-        if (sliced && ncol > 0 && tc05)
-          launch_pair_tc(w, dp, c0, c1, max_ns, DIG_P, s);
+        if (sliced && ncol > 0 && tc05) {
+          if (!launch_pair_tc(w, dp, c0, c1, max_ns, DIG_P, s)) return LMBD_ECUDA;
+        }
         else if (sliced && ncol > 0)
           launch_mbd_adj_pair_oz2(w, dp, c0, c1, max_ns, DIG_P, s);
         else

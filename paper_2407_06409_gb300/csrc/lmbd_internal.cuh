@@ -129,6 +129,14 @@ struct Work {
   long long* off_tr;           // sum Mpad (T rows)
   long long* off_kp;           // sum Kpad (W digit planes are 48 x Kpad)
   long long* off_sp;           // sum ns16 (P, Q rows are 3 ns16)
+  // tcgen05 path: T and W digit planes with one row pitch tk for all centres (0 on the warp-level
+  // path, which uses each centre's Kpad), addressed through tensor maps over the current wave:
+  // T rows [trow0, trow0 + trows) of the rebased pointer, W planes of centres [wc0, wc0 + wcn),
+  // P and Q rows [prow0, prow0 + prows) (pitch Kp)
+  int tk;
+  long long trow0, trows;
+  int wc0, wcn;
+  long long prow0, prows;
   unsigned short* tdig;        // T digit planes (bf16 bits)
   int* texp;                   // T row scale exponents
   unsigned short* wdig;        // W digit planes
@@ -280,13 +288,14 @@ void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, 
 // W = D v_m digit planes for chain step m (one block per central atom)
 void launch_slice_w(const Work& w, const DevParams& p, int m, int c0, int c1, int digits, cudaStream_t s);
 // chain step on the fifth-generation tensor cores (tcgen05, TMEM accumulators), digits 5 or 6
-void launch_chain_tc(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
+// (returns false when a tensor map cannot be encoded)
+bool launch_chain_tc(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
                      cudaStream_t s);
 size_t chain_tc_smem(int digits);
 // P and Q digit planes (blockIdx.y = 0: P, 1: Q)
 void launch_slice_pq(const Work& w, int c0, int c1, int digits, cudaStream_t s);
 // adjoint pair matrix and its per-pair contraction on the tcgen05 tensor cores (digits 5 only;
-// returns false for another digit count)
+// returns false for another digit count or when a tensor map cannot be encoded)
 bool launch_pair_tc(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits, cudaStream_t s);
 void launch_mbd_adj_pair_oz2(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
                              cudaStream_t s);

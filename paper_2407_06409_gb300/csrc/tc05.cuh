@@ -8,6 +8,7 @@
 //   * the accumulator of an M = 128 MMA (cta_group::1) holds row i in TMEM lane i and column j
 //     in TMEM column (base + j); warp w of a warpgroup reads lanes 32 (w % 4) .. 32 (w % 4) + 31.
 #pragma once
+#include <cuda.h>
 #include <stdint.h>
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -117,3 +118,19 @@ __device__ __forceinline__ void tc_cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void tc_cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Arrive once on the mbarrier and add `bytes` to the transaction count it waits for.
+__device__ __forceinline__ void tc_mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+
+// Bulk tensor copy (TMA) of the box at (x, y) of a 2-D tensor map into shared memory; completion is
+// counted in bytes on the mbarrier.  The map is a __grid_constant__ kernel parameter.
+__device__ __forceinline__ void tc_tma_load_2d(uint32_t sdst, const CUtensorMap* map, int x, int y, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          sdst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(tc_smem_u32(mbar))
+      : "memory");
+}
