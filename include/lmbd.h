@@ -179,6 +179,14 @@ int lmbd_set_precision(lmbd_ctx* ctx, int mode);
 #define LMBD_MMA_TC05 1
 int lmbd_set_mma_path(lmbd_ctx* ctx, int path);
 
+/* Bound, in SM clock cycles, of every mbarrier wait in the main loop of the tcgen05 kernels
+ * (copies landed, MMAs done, accumulators complete); 0 (default) = 2^32 cycles, about two
+ * seconds.  A wait that runs out ends that kernel's tile early: the kernel waits (with the
+ * default bound) for its own copies and MMAs in flight, frees its tensor memory and returns,
+ * and the call returns LMBD_ETIMEOUT with its outputs undefined; the context stays usable.
+ * Small budgets exist to exercise that path.  Returns LMBD_EINVAL for a negative value.     */
+int lmbd_set_wait_budget(lmbd_ctx* ctx, long long cycles);
+
 /* Frequency model of the screened polarisabilities.
  * LMBD_FREQ_QUADRATURE (default): the SCS system is solved at omega = 0 and at every
  *   quadrature node.

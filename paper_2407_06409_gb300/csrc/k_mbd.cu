@@ -1257,7 +1257,8 @@ __device__ __forceinline__ int oz_mpad(int n) { return (n + 63) / 64 * 64; }
 __device__ __forceinline__ int oz_kpad(int n) { return (n + 15) / 16 * 16; }
 
 // T_LR digit planes and row exponents (one block per central atom, one warp per row).
-__global__ void __launch_bounds__(256) k_slice_t(Work w, int c0, int st) {
+template <int st>
+__global__ void __launch_bounds__(256) k_slice_t(Work w, int c0) {
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
   const int N = 3 * w.counts[c].ns, Mpad = oz_mpad(N), Kpad = oz_kpad(N);
@@ -1277,15 +1278,14 @@ __global__ void __launch_bounds__(256) k_slice_t(Work w, int c0, int st) {
     if (lane == 0) w.texp[w.off_tr[c] + row] = e;
     for (int j = lane; j < ld; j += 32) {
       const double v = (row < N && j < N) ? T[(long long)row * N + j] : 0.0;
-      int d[OZ_MAXS];
-      oz_digits(v, e, st, d);
-      for (int k = 0; k < st; ++k) base[k * plane + (long long)row * ld + j] = oz_bf16_bits(d[k]);
+      oz_store_digits<st>(base + (long long)row * ld + j, plane, v, e);
     }
   }
 }
 
 // W = D v_m digit planes (stored by column) and column exponents (one block per atom).
-__global__ void __launch_bounds__(256) k_slice_w(Work w, DevParams p, int m, int c0, int sw) {
+template <int sw>
+__global__ void __launch_bounds__(256) k_slice_w(Work w, DevParams p, int m, int c0) {
   __shared__ int cmax[48];
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
@@ -1311,9 +1311,7 @@ __global__ void __launch_bounds__(256) k_slice_w(Work w, DevParams p, int m, int
     const int col = e / ld, j = e % ld;
     double v = 0.0;
     if (col < ncv && j < N) v = dsq[(j / 3) * p.nq + col / 3 + 1] * Vin[(long long)j * ncv + col];
-    int d[OZ_MAXS];
-    oz_digits(v, oz_scale_exp(cmax[col]), sw, d);
-    for (int k = 0; k < sw; ++k) base[k * plane + (long long)col * ld + j] = oz_bf16_bits(d[k]);
+    oz_store_digits<sw>(base + (long long)col * ld + j, plane, v, oz_scale_exp(cmax[col]));
   }
 }
 
@@ -1358,7 +1356,8 @@ __global__ void __launch_bounds__(384) k_chain_oz(Work w, DevParams p, int m, in
 }
 
 // P and Q digit planes and row exponents (blockIdx.y = 0: P, 1: Q).
-__global__ void __launch_bounds__(256) k_slice_pq(Work w, int c0, int sp) {
+template <int sp>
+__global__ void __launch_bounds__(256) k_slice_pq(Work w, int c0) {
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
   const int ns = w.counts[c].ns, R = 3 * ((ns + 15) / 16 * 16), rows = 3 * ns;
@@ -1379,9 +1378,7 @@ __global__ void __launch_bounds__(256) k_slice_pq(Work w, int c0, int sp) {
     if (lane == 0) ex[row] = e;
     for (int j = lane; j < Kp; j += 32) {
       const double v = (row < rows && j < ncol) ? src[(long long)row * ncol + j] : 0.0;
-      int d[OZ_MAXS];
-      oz_digits(v, e, sp, d);
-      for (int k = 0; k < sp; ++k) base[k * plane + (long long)row * Kp + j] = oz_bf16_bits(d[k]);
+      oz_store_digits<sp>(base + (long long)row * Kp + j, plane, v, e);
     }
   }
 }
@@ -1445,26 +1442,52 @@ __global__ void __launch_bounds__(288) k_mbd_adj_pair_oz(Work w, DevParams p, in
   pair_tile_reduce(w, offs, sbase, ns, bi, bj, gp);
 }
 
+// Slicing launches for the digit counts in use (4 to 7; the products use 5 and 6).
+static void run_slice_t(const Work& w, int c0, int n, int st, cudaStream_t s) {
+  switch (st) {
+    case 4: k_slice_t<4><<<n, 256, 0, s>>>(w, c0); break;
+    case 5: k_slice_t<5><<<n, 256, 0, s>>>(w, c0); break;
+    case 6: k_slice_t<6><<<n, 256, 0, s>>>(w, c0); break;
+    default: k_slice_t<7><<<n, 256, 0, s>>>(w, c0); break;
+  }
+}
+static void run_slice_w(const Work& w, const DevParams& p, int m, int c0, int n, int sw, cudaStream_t s) {
+  switch (sw) {
+    case 4: k_slice_w<4><<<n, 256, 0, s>>>(w, p, m, c0); break;
+    case 5: k_slice_w<5><<<n, 256, 0, s>>>(w, p, m, c0); break;
+    case 6: k_slice_w<6><<<n, 256, 0, s>>>(w, p, m, c0); break;
+    default: k_slice_w<7><<<n, 256, 0, s>>>(w, p, m, c0); break;
+  }
+}
+static void run_slice_pq(const Work& w, int c0, int n, int sp, cudaStream_t s) {
+  const dim3 g2(n, 2);
+  switch (sp) {
+    case 4: k_slice_pq<4><<<g2, 256, 0, s>>>(w, c0); break;
+    case 5: k_slice_pq<5><<<g2, 256, 0, s>>>(w, c0); break;
+    case 6: k_slice_pq<6><<<g2, 256, 0, s>>>(w, c0); break;
+    default: k_slice_pq<7><<<g2, 256, 0, s>>>(w, c0); break;
+  }
+}
+
 void launch_slice_t(const Work& w, int c0, int c1, int st, cudaStream_t s) {
   if (c1 <= c0) return;
-  k_slice_t<<<c1 - c0, 256, 0, s>>>(w, c0, st);
+  run_slice_t(w, c0, c1 - c0, st, s);
 }
 
 void launch_slice_pq(const Work& w, int c0, int c1, int digits, cudaStream_t s) {
   if (c1 <= c0) return;
-  dim3 g2(c1 - c0, 2);
-  k_slice_pq<<<g2, 256, 0, s>>>(w, c0, digits);
+  run_slice_pq(w, c0, c1 - c0, digits, s);
 }
 
 void launch_slice_w(const Work& w, const DevParams& p, int m, int c0, int c1, int digits, cudaStream_t s) {
   if (c1 <= c0) return;
-  k_slice_w<<<c1 - c0, 256, 0, s>>>(w, p, m, c0, digits);
+  run_slice_w(w, p, m, c0, c1 - c0, digits, s);
 }
 
 void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
                      cudaStream_t s) {
   if (c1 <= c0) return;
-  k_slice_w<<<c1 - c0, 256, 0, s>>>(w, p, m, c0, digits);
+  run_slice_w(w, p, m, c0, c1 - c0, digits, s);
   const int tiles = (3 * max_ns + 63) / 64;
   if (digits == 6)
     k_chain_oz<6><<<(c1 - c0) * tiles, 384, 0, s>>>(w, p, m, c0, tiles, st);
@@ -1475,8 +1498,7 @@ void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, i
 void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
                             cudaStream_t s) {
   if (c1 <= c0) return;
-  dim3 g2(c1 - c0, 2);
-  k_slice_pq<<<g2, 256, 0, s>>>(w, c0, digits);
+  run_slice_pq(w, c0, c1 - c0, digits, s);
   const int nt = (max_ns + PT - 1) / PT;
   const int tiles = nt * (nt + 1) / 2;
   if (digits == 6)
@@ -1579,7 +1601,7 @@ __global__ void __launch_bounds__(384, 1) k_chain_oz2(Work w, DevParams p, int m
 void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
                       cudaStream_t s) {
   if (c1 <= c0) return;
-  k_slice_w<<<c1 - c0, 256, 0, s>>>(w, p, m, c0, digits);
+  run_slice_w(w, p, m, c0, c1 - c0, digits, s);
   const int tiles = (3 * max_ns + 63) / 64;
   if (digits == 6) {
     const size_t sm = 2 * sizeof(unsigned short) * (6 * 64 + 6 * 48) * OZ_LD;
@@ -1695,8 +1717,7 @@ __global__ void __launch_bounds__(288) k_mbd_adj_pair_oz2(Work w, DevParams p, i
 void launch_mbd_adj_pair_oz2(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
                              cudaStream_t s) {
   if (c1 <= c0) return;
-  dim3 g2(c1 - c0, 2);
-  k_slice_pq<<<g2, 256, 0, s>>>(w, c0, digits);
+  run_slice_pq(w, c0, c1 - c0, digits, s);
   const int nt = (max_ns + PT - 1) / PT;
   const int tiles = nt * (nt + 1) / 2;
   if (digits == 6) {

@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(256, 1)
   long long Y[48];
 #pragma unroll
   for (int j = 0; j < 48; ++j) Y[j] = 0;
-  int issued = -1, committed = -1;
-  const bool ok = tcs_mainloop<S, PTC_NB>(A, B, Kp, sbase, bar, issued, committed, [&]() {
+  TcsProgress pr;
+  const bool ok = tcs_mainloop<S, PTC_NB>(A, B, Kp, sbase, bar, p.tc_wait, pr, [&]() {
 #pragma unroll
     for (int g = 0; g < S; ++g)
 #pragma unroll
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256, 1)
         for (int i = 0; i < 8; ++i) Y[j8 * 8 + i] += (long long)__float2int_rn(v[i]) << (7 * (S - 1 - g));
       }
   });
-  tcs_teardown(bar, !ok, issued, committed, w.status);
+  tcs_teardown(bar, !ok, pr, w.status);
   if (!ok) return;
 
   // FP64 tile (126 x 96) and per-pair results (42 x 32 x 4) in the drained staging ring

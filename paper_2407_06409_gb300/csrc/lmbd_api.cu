@@ -48,6 +48,7 @@ struct Ctx {
   int profiling = 0;
   int precision = LMBD_PREC_SLICED;
   int mma_path = LMBD_MMA_TC05;
+  long long tc_wait = 0;           // main-loop wait bound of the tcgen05 kernels (0: 2^32 cycles)
   int lorentz = 0;                 // frequency model (lmbd_set_frequency_model)
   double omega_ref = 0.0;
   int fit_nodes = 0;               // integrand model (lmbd_set_integrand_fit): 0 = quadrature
@@ -509,6 +510,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   dp.lanczos = c->lanczos;
   for (int n = 1; n < LMBD_MAX_ORDER_P1; ++n) dp.cn[n] = -1.0 / n;
   dp.paper = c->paper_forces && forces;
+  dp.tc_wait = c->tc_wait > 0 ? c->tc_wait : (1LL << 32);
   if (dp.paper && c->fit_nodes) return LMBD_EINVAL;   // the paper fits its force integrand separately
   dp.omega_ref = c->omega_ref;
   dp.nqs = c->lorentz ? 2 : nq;
@@ -1061,9 +1063,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     S.kernel_launches = launches;
     S.bytes_workspace = (double)(c->whole_bytes() + c->arena.bytes);
   }
+  // a tensor-core kernel that gave up leaves its outputs undefined, which later stages may
+  // report as failures of their own: the timeout is the cause
+  if (*c->status_h & LMBD_FLAG_TIMEOUT) return LMBD_ETIMEOUT;
   if (*c->status_h & (LMBD_FLAG_NOT_SPD | LMBD_FLAG_NOT_CONVERGED)) return LMBD_NOT_SPD;
   if (*c->status_h & LMBD_FLAG_MODEL) return LMBD_EMODEL;
-  if (*c->status_h & LMBD_FLAG_TIMEOUT) return LMBD_ETIMEOUT;
   return LMBD_OK;
 }
 
@@ -1207,6 +1211,12 @@ int lmbd_set_precision(lmbd_ctx* ctx, int mode) {
 int lmbd_set_mma_path(lmbd_ctx* ctx, int path) {
   if (!ctx || (path != LMBD_MMA_WARP && path != LMBD_MMA_TC05)) return LMBD_EINVAL;
   ctx->c.mma_path = path;
+  return LMBD_OK;
+}
+
+int lmbd_set_wait_budget(lmbd_ctx* ctx, long long cycles) {
+  if (!ctx || cycles < 0) return LMBD_EINVAL;
+  ctx->c.tc_wait = cycles;
   return LMBD_OK;
 }
 

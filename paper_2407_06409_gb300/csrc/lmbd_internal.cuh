@@ -48,6 +48,8 @@ struct DevParams {
   // force model: 0 = exact gradient of sum_k w_k E_k, 1 = the paper's approximate forces
   // (Sec. III.D: F_k = -dE^{k,tot}/dr_k, alpha_I held, central row and column only for n >= 3)
   int paper;
+  // bound of each mbarrier wait in the main loop of the tcgen05 kernels (SM clock cycles)
+  long long tc_wait;
   double phi_omega[LMBD_MAXQ - 1];
   double phi_wt[LMBD_MAXQ - 1];
 };

@@ -21,7 +21,6 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
-#define OZ_MAXS 7
 
 // Exponent e with |v| < 2^e for the largest |v| (biased exponent of v, 0 for zero).
 __device__ __forceinline__ int oz_biased_exp(double v) {
@@ -31,27 +30,28 @@ __device__ __forceinline__ int oz_biased_exp(double v) {
 // Scale exponent from the largest biased exponent of a row/column: |v| < 2^(ex - 1022).
 __device__ __forceinline__ int oz_scale_exp(int max_biased) { return max_biased == 0 ? -1022 : max_biased - 1022; }
 
-// Signed 7-bit digits of v relative to 2^e (|v| < 2^e): v ~= 2^e sum_{k=1..S} d_k 2^{-7k},
-// truncated toward zero.  Integer operations only.
-__device__ __forceinline__ void oz_digits(double v, int e, int S, int* d) {
-  const long long bits = __double_as_longlong(v);
-  const int ex = (int)((bits >> 52) & 0x7ff);
-  if (ex == 0) {
-    for (int k = 0; k < S; ++k) d[k] = 0;
-    return;
-  }
-  const unsigned long long mant = (unsigned long long)(bits & 0xFFFFFFFFFFFFFLL) | (1ULL << 52);
-  const int sh = (ex - 1075) + 7 * S - e;
-  unsigned long long U = 0;
-  if (sh >= 0) U = mant << sh;
-  else if (sh > -64) U = mant >> (-sh);
-  const int sg = bits < 0 ? -1 : 1;
-  for (int k = 0; k < S; ++k) d[k] = sg * (int)((U >> (7 * (S - 1 - k))) & 127ULL);
-}
-
 __device__ __forceinline__ unsigned short oz_bf16_bits(int d) {
   __nv_bfloat16 h = __float2bfloat16_rn((float)d);
   return *reinterpret_cast<unsigned short*>(&h);
+}
+
+// Signed 7-bit digits of v relative to 2^e (|v| < 2^e): v ~= 2^e sum_{k=1..S} d_k 2^{-7k},
+// truncated toward zero (integer operations only), stored as bf16 bits at dst[(k - 1) plane].
+// S is a compile-time constant so the digits stay in registers.
+template <int S>
+__device__ __forceinline__ void oz_store_digits(unsigned short* dst, long long plane, double v, int e) {
+  const long long bits = __double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  unsigned long long U = 0;
+  if (ex != 0) {
+    const unsigned long long mant = (unsigned long long)(bits & 0xFFFFFFFFFFFFFLL) | (1ULL << 52);
+    const int sh = (ex - 1075) + 7 * S - e;
+    if (sh >= 0) U = mant << sh;
+    else if (sh > -64) U = mant >> (-sh);
+  }
+  const int sg = bits < 0 ? -1 : 1;
+#pragma unroll
+  for (int k = 0; k < S; ++k) dst[k * plane] = oz_bf16_bits(sg * (int)((U >> (7 * (S - 1 - k))) & 127ULL));
 }
 
 // 2^E as a double (E clamped to the normal range; tiny scales flush to zero).

@@ -57,21 +57,23 @@ __device__ __forceinline__ void tc_mbar_init(uint64_t* mbar, uint32_t count) {
 __device__ __forceinline__ void tc_mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ bool tc_mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+// Non-blocking test of the phase of the given parity.
+__device__ __forceinline__ bool tc_mbar_test_wait(uint64_t* mbar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
       : "r"(tc_smem_u32(mbar)), "r"(parity)
       : "memory");
   return ok != 0;
 }
-// Wait for the phase of the given parity to complete, giving up after `budget` clock cycles.
+// Wait for the phase of the given parity to complete, giving up after `budget` clock cycles
+// (a spin on the non-blocking test, so that a small budget runs out deterministically).
 __device__ __forceinline__ bool tc_mbar_wait(uint64_t* mbar, uint32_t parity, long long budget) {
   const long long t0 = clock64();
-  while (!tc_mbar_try_wait(mbar, parity))
+  while (!tc_mbar_test_wait(mbar, parity))
     if (clock64() - t0 > budget) return false;
   return true;
 }

@@ -19,12 +19,14 @@
 //     then) with the stage three ahead, so copies and MMAs overlap;
 //   * at the end of every K chunk of OZ_KCHUNK (every partial sum of the low digit orders is an
 //     integer below 2^24 and therefore exact in FP32) the thread commits an "accumulators"
-//     mbarrier, and all 256 threads hand the accumulators to `consume`, which reads them with
-//     tcgen05.ld and adds them up as integers; the next chunk restarts them.
+//     mbarrier and waits for it, a block barrier publishes the result, and all 256 threads hand
+//     the accumulators to `consume`, which reads them with tcgen05.ld and adds them up as
+//     integers; the next chunk restarts them.
 // Rows of a box past a plane's end read the next plane or centre: they only reach output rows
-// (A) or columns (B) that the callers discard.  Every mbarrier wait is bounded
-// (TCS_WAIT_CYCLES); if one runs out the loop stops, and the teardown waits (bounded again) for
-// the block's copies and MMAs in flight, frees tensor memory and sets LMBD_FLAG_TIMEOUT.
+// (A) or columns (B) that the callers discard.  Every mbarrier wait of the loop is bounded (a
+// cycle budget, 2^32 by default); if one runs out the loop stops, and the teardown waits for the
+// block's copies and MMAs in flight (bounded by TCS_WAIT_CYCLES), frees tensor memory and sets
+// LMBD_FLAG_TIMEOUT.
 #pragma once
 #include "lmbd_internal.cuh"
 #include "ozaki.cuh"
@@ -91,14 +93,23 @@ __device__ __forceinline__ uint32_t tcs_setup(TcsBarriers& bar) {
   return bar.tmem;
 }
 
-// Block-wide tear-down.  After an abort, thread 0 waits (bounded) for the copies it issued and
-// the MMAs it committed; then tensor memory is freed.
-__device__ __forceinline__ void tcs_teardown(TcsBarriers& bar, bool abort, int issued, int committed, int* status) {
+// What thread 0 has in flight: the last stage copied, the last stage whose MMAs were committed,
+// and the K chunk whose accumulator commit was not yet seen complete (-1: none).
+struct TcsProgress {
+  int issued = -1, committed = -1, acc = -1;
+};
+
+// Block-wide tear-down.  After an abort, thread 0 waits (bounded) for the copies it issued, the
+// MMAs it committed and their commits' arrivals, so nothing lands in shared or tensor memory
+// after the block is gone; then tensor memory is freed.
+__device__ __forceinline__ void tcs_teardown(TcsBarriers& bar, bool abort, const TcsProgress& pr, int* status) {
   if (abort && threadIdx.x == 0) {
     atomicOr(status, LMBD_FLAG_TIMEOUT);
-    for (int s = committed + 1; s <= issued; ++s)
+    for (int s = pr.committed + 1; s <= pr.issued; ++s)
       tc_mbar_wait(&bar.full[s % TCS_NBUF], (s / TCS_NBUF) & 1, TCS_WAIT_CYCLES);
-    if (committed >= 0) tc_mbar_wait(&bar.empty[committed % TCS_NBUF], (committed / TCS_NBUF) & 1, TCS_WAIT_CYCLES);
+    if (pr.committed >= 0)
+      tc_mbar_wait(&bar.empty[pr.committed % TCS_NBUF], (pr.committed / TCS_NBUF) & 1, TCS_WAIT_CYCLES);
+    if (pr.acc >= 0) tc_mbar_wait(&bar.acc, pr.acc & 1, TCS_WAIT_CYCLES);
   }
   tc_fence_before();
   __syncthreads();
@@ -113,12 +124,13 @@ __device__ __forceinline__ uint32_t tcs_lane_addr(uint32_t tmem, int col) {
   return tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + (uint32_t)col;
 }
 
-// The main loop (all 256 threads; thread 0 issues copies and MMAs).  consume() runs block-wide
-// at the end of every K chunk with the accumulators complete in TMEM.  Returns false if a wait
-// ran out; `issued` and `committed` (thread 0) are the last stage copied and multiplied.
+// The main loop (all 256 threads; thread 0 issues copies and MMAs and waits for them).
+// consume() runs block-wide at the end of every K chunk with the accumulators complete in TMEM.
+// Every wait is bounded by `budget` cycles; returns false if one ran out.  `pr` (thread 0) keeps
+// what is in flight, for the tear-down.
 template <int S, int NB, class Consume>
 __device__ __forceinline__ bool tcs_mainloop(const TcsTile& A, const TcsTile& B, int K, uint32_t sbase,
-                                             TcsBarriers& bar, int& issued, int& committed, Consume&& consume) {
+                                             TcsBarriers& bar, long long budget, TcsProgress& pr, Consume&& consume) {
   using Sh = TcsShape<S, NB>;
   const int tid = threadIdx.x;
   const int nst = (K + TCS_KS - 1) / TCS_KS;
@@ -133,7 +145,7 @@ __device__ __forceinline__ bool tcs_mainloop(const TcsTile& A, const TcsTile& B,
     for (int k = 0; k < S; ++k) tc_tma_load_2d(sA + k * Sh::kAPlane, A.map, s * TCS_KS, A.y0 + k * A.plane_rows, &bar.full[slot]);
 #pragma unroll
     for (int k = 0; k < S; ++k) tc_tma_load_2d(sB + k * Sh::kBPlane, B.map, s * TCS_KS, B.y0 + k * B.plane_rows, &bar.full[slot]);
-    issued = s;
+    pr.issued = s;
   };
   if (tid == 0)
     for (int s = 0; s < TCS_NBUF && s < nst; ++s) load(s);
@@ -144,7 +156,7 @@ __device__ __forceinline__ bool tcs_mainloop(const TcsTile& A, const TcsTile& B,
     if (tid == 0) {
       for (int s = s0; s < s1; ++s) {
         const int slot = s % TCS_NBUF;
-        if (!tc_mbar_wait(&bar.full[slot], (s / TCS_NBUF) & 1, TCS_WAIT_CYCLES)) {
+        if (!tc_mbar_wait(&bar.full[slot], (s / TCS_NBUF) & 1, budget)) {
           to = true;
           break;
         }
@@ -166,21 +178,25 @@ __device__ __forceinline__ bool tcs_mainloop(const TcsTile& A, const TcsTile& B,
             }
           }
         tc_commit(&bar.empty[slot]);
-        committed = s;
+        pr.committed = s;
         // refill the slot of stage s - 1 with stage s - 1 + TCS_NBUF once its MMAs are done
         const int r = s - 1 + TCS_NBUF;
         if (s >= 1 && r < nst) {
-          if (!tc_mbar_wait(&bar.empty[(s - 1) % TCS_NBUF], ((s - 1) / TCS_NBUF) & 1, TCS_WAIT_CYCLES)) {
+          if (!tc_mbar_wait(&bar.empty[(s - 1) % TCS_NBUF], ((s - 1) / TCS_NBUF) & 1, budget)) {
             to = true;
             break;
           }
           load(r);
         }
       }
-      if (!to) tc_commit(&bar.acc);
+      if (!to) {
+        // accumulators of this chunk complete: seen by thread 0, published by the barrier
+        tc_commit(&bar.acc);
+        pr.acc = ch;
+        if (tc_mbar_wait(&bar.acc, ch & 1, budget)) pr.acc = -1;
+        else to = true;
+      }
     }
-    if (__syncthreads_or(to)) return false;
-    to = !tc_mbar_wait(&bar.acc, ch & 1, TCS_WAIT_CYCLES);
     if (__syncthreads_or(to)) return false;
     tc_fence_after();
     consume();

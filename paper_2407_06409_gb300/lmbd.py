@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_profiling.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_precision.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_mma_path.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_wait_budget.argtypes = [_P, ctypes.c_longlong]
         L.lmbd_set_memory_budget.argtypes = [_P, ctypes.c_size_t]
         L.lmbd_set_frequency_model.argtypes = [_P, ctypes.c_int, ctypes.c_double]
         L.lmbd_set_integrand_fit.argtypes = [_P, ctypes.c_int]
@@ -97,7 +98,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
-                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_mma_path", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
+                  "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_mma_path", "lmbd_set_wait_budget", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
                   "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_autotune",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
@@ -182,6 +183,10 @@ class LMBD:
     def set_mma_path(self, path: int) -> None:
         """Tensor-core path of the sliced products: MMA_TC05 (tcgen05, default) or MMA_WARP (mma.sync)."""
         _check(lib().lmbd_set_mma_path(self._h, int(path)), "lmbd_set_mma_path")
+
+    def set_wait_budget(self, cycles: int) -> None:
+        """Bound (SM cycles) of each wait in the tcgen05 kernels' main loop; 0 = default (~2 s)."""
+        _check(lib().lmbd_set_wait_budget(self._h, int(cycles)), "lmbd_set_wait_budget")
 
     def set_memory_budget(self, nbytes: int) -> None:
         """Device bytes this context may hold (0 = free memory less 1 GiB); larger inputs run in waves."""

@@ -126,3 +126,25 @@ def test_tc05_box4096_matches_warp_path(lm):
     warp, tc = _both(lm, s, p)
     assert 3 * tc[2]["max_sphere"] > 384
     _same(warp, tc)
+
+
+def test_tc05_wait_that_runs_out_is_reported_and_the_context_recovers(lm):
+    # A one-cycle budget makes the first wait for a slot's copies run out (the bulk copies were
+    # issued just before it).  The kernels then wait for their own copies and MMAs in flight,
+    # free tensor memory and return; the call reports LMBD_ETIMEOUT.  With the default budget the
+    # same context gives the results of a fresh one, bit for bit.
+    s = inputs.box(110, seed=1, jitter=0.05)
+    p = lm.default_params()
+    ref = lm.LMBD(s.table, p, 12, 6)
+    e0, f0 = ref.energy_forces(*_args(s))
+    model = lm.LMBD(s.table, p, 12, 6)
+    model.set_wait_budget(1)
+    with pytest.raises(lm.LmbdError) as err:
+        model.energy_forces(*_args(s))
+    assert err.value.status == lm.LMBD_ETIMEOUT
+    model.set_wait_budget(0)
+    e1, f1 = model.energy_forces(*_args(s))
+    assert torch.equal(e1, e0)
+    assert (f1 - f0).abs().max().item() < F_PATH_ATOL
+    with pytest.raises(lm.LmbdError):
+        model.set_wait_budget(-1)
