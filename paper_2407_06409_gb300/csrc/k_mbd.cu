@@ -1315,46 +1315,6 @@ __global__ void __launch_bounds__(256) k_slice_w(Work w, DevParams p, int m, int
   }
 }
 
-// v_{m+1} = D (T W): 64 output rows x 48 columns per block, 12 warps of 16 x 16.
-template <int S>
-__global__ void __launch_bounds__(384) k_chain_oz(Work w, DevParams p, int m, int c0, int tiles_per_c, int st) {
-  const int c = c0 + blockIdx.x / tiles_per_c;
-  const int tile = blockIdx.x % tiles_per_c;
-  if (c >= w.n_atoms) return;
-  const int N = 3 * w.counts[c].ns, Mpad = oz_mpad(N), Kpad = oz_kpad(N);
-  if (tile * 64 >= N) return;
-  const long long offs = w.off_s[c];
-  const int ncv = 3 * p.n_freq;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-  const int wr = warp / 3, wc = warp % 3;
-  const int r0 = tile * 64 + wr * 16, cb = wc * 16;
-  const unsigned short* A = w.tdig + w.off_tq[c] * st + (long long)r0 * Kpad;
-  const unsigned short* B = w.wdig + w.off_kp[c] * 48 * S + (long long)cb * Kpad;
-  double y[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-  int er[2], ec[2][2];
-  er[0] = w.texp[w.off_tr[c] + r0 + g];
-  er[1] = w.texp[w.off_tr[c] + r0 + g + 8];
-  for (int nt = 0; nt < 2; ++nt)
-    for (int h = 0; h < 2; ++h) ec[nt][h] = w.wexp[(long long)c * 48 + cb + nt * 8 + 2 * tq + h];
-  for (int kb = 0; kb < Kpad; kb += OZ_KCHUNK) {
-    float acc[S][2][4];
-    oz_warp_tile<S>(A, Kpad, (long long)Mpad * Kpad, B, Kpad, 48LL * Kpad, kb, min(kb + OZ_KCHUNK, Kpad), acc);
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) y[nt][v] += oz_combine<S>(acc, nt, v, er[v >> 1], ec[nt][v & 1]);
-  }
-  double* Vout = w.vkr + (long long)m * w.vstride + (offs * 3) * ncv;
-  const double* dsq = w.dsq + offs * p.nq;
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int row = r0 + g + (v >> 1) * 8, col = cb + nt * 8 + 2 * tq + (v & 1);
-      if (row < N && col < ncv) Vout[(long long)row * ncv + col] = dsq[(row / 3) * p.nq + col / 3 + 1] * y[nt][v];
-    }
-}
-
 // P and Q digit planes and row exponents (blockIdx.y = 0: P, 1: Q).
 template <int sp>
 __global__ void __launch_bounds__(256) k_slice_pq(Work w, int c0) {
@@ -1381,65 +1341,6 @@ __global__ void __launch_bounds__(256) k_slice_pq(Work w, int c0) {
       oz_store_digits<sp>(base + (long long)row * Kp + j, plane, v, e);
     }
   }
-}
-
-// Pair matrix M' = P Q^T on one 16 x 16 site tile (48 x 48 values, 9 warps of 16 x 16) from
-// digit planes, then the same per-pair epilogue as the FP64 kernel.
-template <int S>
-__global__ void __launch_bounds__(288) k_mbd_adj_pair_oz(Work w, DevParams p, int c0, int tiles_per_c) {
-  __shared__ double Ms[3 * PT][3 * PT + 1];
-  __shared__ double xs[2][PT][3];
-  __shared__ double rts[2][PT];
-  __shared__ double gp[PT][PT][4];
-  const int c = c0 + blockIdx.x / tiles_per_c;
-  const int tile = blockIdx.x % tiles_per_c;
-  if (c >= w.n_atoms) return;
-  const int ns = w.counts[c].ns;
-  const int nt = (ns + PT - 1) / PT;
-  if (tile >= nt * (nt + 1) / 2) return;
-  int bi = 0;
-  while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
-  const int bj = tile - bi * (bi + 1) / 2;
-  const long long offs = w.off_s[c];
-  const long long sbase = (long long)c * w.site_cap;
-  const int tid = threadIdx.x;
-  pair_tile_sites(w, p, offs, sbase, ns, bi, bj, xs, rts);
-  const int R = 3 * nt * PT, Kp = oz_kpad(w.ncol);
-  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
-  const int wr = warp / 3, wc = warp % 3;
-  const long long dbase = w.off_sp[c] * 3 * (long long)Kp * S;
-  const unsigned short* A = w.pdig + dbase + (long long)(bi * 48 + wr * 16) * Kp;
-  const unsigned short* B = w.qdig + dbase + (long long)(bj * 48 + wc * 16) * Kp;
-  const int* pe = w.pexp + w.off_sp[c] * 3;
-  const int* qe = w.qexp + w.off_sp[c] * 3;
-  const int ra = bi * 48 + wr * 16 + g, cbs = bj * 48 + wc * 16;
-  double y[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-  for (int kb = 0; kb < Kp; kb += OZ_KCHUNK) {
-    float acc[S][2][4];
-    oz_warp_tile<S>(A, Kp, (long long)R * Kp, B, Kp, (long long)R * Kp, kb, min(kb + OZ_KCHUNK, Kp), acc);
-#pragma unroll
-    for (int n8 = 0; n8 < 2; ++n8)
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        y[n8][v] += oz_combine<S>(acc, n8, v, pe[ra + (v >> 1) * 8], qe[cbs + n8 * 8 + 2 * tq + (v & 1)]);
-  }
-#pragma unroll
-  for (int n8 = 0; n8 < 2; ++n8)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) Ms[wr * 16 + g + (v >> 1) * 8][wc * 16 + n8 * 8 + 2 * tq + (v & 1)] = y[n8][v];
-  __syncthreads();
-  if (tid < PT * PT) {
-    const int ty = tid / PT, tx = tid % PT;
-    const int s = bi * PT + ty, t = bj * PT + tx;
-    double acc[3][3];
-#pragma unroll
-    for (int al = 0; al < 3; ++al)
-#pragma unroll
-      for (int be = 0; be < 3; ++be) acc[al][be] = Ms[3 * ty + al][3 * tx + be];
-    pair_epilogue(w, offs, w.off_t[c], s, t, ns, acc, gp[ty][tx]);
-  }
-  __syncthreads();
-  pair_tile_reduce(w, offs, sbase, ns, bi, bj, gp);
 }
 
 // Slicing launches for the digit counts in use (4 to 7; the products use 5 and 6).
@@ -1482,29 +1383,6 @@ void launch_slice_pq(const Work& w, int c0, int c1, int digits, cudaStream_t s) 
 void launch_slice_w(const Work& w, const DevParams& p, int m, int c0, int c1, int digits, cudaStream_t s) {
   if (c1 <= c0) return;
   run_slice_w(w, p, m, c0, c1 - c0, digits, s);
-}
-
-void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
-                     cudaStream_t s) {
-  if (c1 <= c0) return;
-  run_slice_w(w, p, m, c0, c1 - c0, digits, s);
-  const int tiles = (3 * max_ns + 63) / 64;
-  if (digits == 6)
-    k_chain_oz<6><<<(c1 - c0) * tiles, 384, 0, s>>>(w, p, m, c0, tiles, st);
-  else
-    k_chain_oz<5><<<(c1 - c0) * tiles, 384, 0, s>>>(w, p, m, c0, tiles, st);
-}
-
-void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
-                            cudaStream_t s) {
-  if (c1 <= c0) return;
-  run_slice_pq(w, c0, c1 - c0, digits, s);
-  const int nt = (max_ns + PT - 1) / PT;
-  const int tiles = nt * (nt + 1) / 2;
-  if (digits == 6)
-    k_mbd_adj_pair_oz<6><<<(c1 - c0) * tiles, 288, 0, s>>>(w, p, c0, tiles);
-  else
-    k_mbd_adj_pair_oz<5><<<(c1 - c0) * tiles, 288, 0, s>>>(w, p, c0, tiles);
 }
 
 // v_{m+1} = D (T W) with shared-memory staging (cp.async, two stages of 32 K), 64 x 48 outputs

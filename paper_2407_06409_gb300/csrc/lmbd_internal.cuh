@@ -283,8 +283,6 @@ void launch_mbd_adj_pair(const Work& w, const DevParams& p, int c0, int c1, int 
 void launch_mbd_adj_blend(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
 void launch_forces_out(const Work& w, double* forces, cudaStream_t s);
 void launch_slice_t(const Work& w, int c0, int c1, int st, cudaStream_t s);
-void launch_chain_oz(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
-                     cudaStream_t s);
 void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
                       cudaStream_t s);
 // W = D v_m digit planes for chain step m (one block per central atom)
@@ -301,8 +299,6 @@ void launch_slice_pq(const Work& w, int c0, int c1, int digits, cudaStream_t s);
 bool launch_pair_tc(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits, cudaStream_t s);
 void launch_mbd_adj_pair_oz2(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
                              cudaStream_t s);
-void launch_mbd_adj_pair_oz(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int digits,
-                            cudaStream_t s);
 
 // Raise the dynamic shared-memory limit of a kernel to at least `bytes` (never lowers it: the
 // limit is process-wide, and lowering it while another host thread launches the same kernel

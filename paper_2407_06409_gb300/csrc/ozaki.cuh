@@ -1,26 +1,28 @@
 // FP64 matrix products on the bf16 tensor cores by exact integer slicing.
 //
-// GB300 runs FP64 at 1/70 of FP32, while bf16 mma.sync delivers ~600 TFLOP/s.  A product
-// C = A B of FP64 matrices is evaluated from integer digit planes (the slicing scheme of
-// Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix multiplication by
-// using fast routines of matrix multiplication", and its tensor-core use by Mukunoki et al.):
+// GB300 runs FP64 at 1/70 of FP32, while its bf16 tensor cores are two orders of magnitude
+// faster still.  A product C = A B of FP64 matrices is evaluated from integer digit planes (the
+// slicing scheme of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication", and its tensor-core use by
+// Mukunoki et al.):
 //   * every row of A (column of B) is scaled by a power of two 2^e so that |a| < 2^e;
 //   * the scaled value is truncated to 7 S bits and split into S signed 7-bit digits,
 //       a = 2^e sum_k d_k 2^{-7k},  |d_k| <= 127  (exact in bf16);
-//   * digit planes are multiplied with bf16 mma.sync and FP32 accumulation; every product
-//     d_k d_l is an integer below 2^14, and the K dimension is accumulated in chunks of at
-//     most 256 terms, so one digit pair sums to less than 2^22;
+//   * digit planes are multiplied on the tensor cores (tcgen05.mma, tc_sliced.cuh, or the
+//     warp-level mma.sync below) with FP32 accumulation; every product d_k d_l is an integer
+//     below 2^14, and the K dimension is accumulated in chunks of at most OZ_KCHUNK = 256
+//     terms, so one digit pair sums to less than 2^22;
 //   * products with the same digit order m = k + l share one FP32 accumulator: with at most
 //     four pairs per order below m = 6 every partial sum stays below 2^24 and is exact;
 //     higher orders can round, at a level below 2^-52 of the leading term.  Pairs with
-//     m > S + 1 are dropped, and after each K chunk the groups are added in FP64:
-//       c += 2^{e_row + e_col} sum_m 2^{-7m} acc_m.
+//     m > S - 1 are dropped; after each K chunk the orders are recombined exactly as 64-bit
+//     integers, Y += sum_m acc_m 2^{7 (S - 1 - m)}, and the result is scaled once in FP64:
+//       c = 2^{e_row + e_col - 7 (S + 1)} Y.
 // The result differs from the FP64 product by at most ~S 2^{-7S} sum |a||b| (normwise);
 // the digit count S is chosen per product from the accuracy its consumer needs.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
-
 
 // Exponent e with |v| < 2^e for the largest |v| (biased exponent of v, 0 for zero).
 __device__ __forceinline__ int oz_biased_exp(double v) {
@@ -29,6 +31,10 @@ __device__ __forceinline__ int oz_biased_exp(double v) {
 
 // Scale exponent from the largest biased exponent of a row/column: |v| < 2^(ex - 1022).
 __device__ __forceinline__ int oz_scale_exp(int max_biased) { return max_biased == 0 ? -1022 : max_biased - 1022; }
+
+// K chunk over which one digit order is accumulated in FP32 before the exact integer
+// recombination (every partial sum of the low orders stays an integer below 2^24).
+#define OZ_KCHUNK 256
 
 __device__ __forceinline__ unsigned short oz_bf16_bits(int d) {
   __nv_bfloat16 h = __float2bfloat16_rn((float)d);
@@ -71,56 +77,6 @@ __device__ __forceinline__ void oz_mma(float* d, const uint32_t* a, const uint32
 }
 
 __device__ __forceinline__ uint32_t oz_ld32(const unsigned short* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-// One warp computes a 16 x 16 output tile (two m16n8 tiles) of sum_j A[r][j] B[c][j] over
-// j in [kb, ke) (multiples of 16, ke - kb <= 256) from S digit planes of A (row-major, ld lda,
-// plane stride pa) and of B (row-major by output column, ld ldb, plane stride pb).
-// acc[m][nt][4] receives the digit-order groups m = k + l (0-based digits, k + l <= S - 1).
-#define OZ_KCHUNK 256
-template <int S>
-__device__ __forceinline__ void oz_warp_tile(const unsigned short* A, long long lda, long long pa,
-                                             const unsigned short* B, long long ldb, long long pb, int kb,
-                                             int ke, float (&acc)[S][2][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int m = 0; m < S; ++m)
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[m][nt][v] = 0.f;
-  for (int k0 = kb; k0 < ke; k0 += 16) {
-    uint32_t a[S][4], b[S][2][2];
-#pragma unroll
-    for (int k = 0; k < S; ++k) {
-      const unsigned short* Ak = A + k * pa + k0 + 2 * t;
-      a[k][0] = oz_ld32(Ak + g * lda);
-      a[k][1] = oz_ld32(Ak + (g + 8) * lda);
-      a[k][2] = oz_ld32(Ak + g * lda + 8);
-      a[k][3] = oz_ld32(Ak + (g + 8) * lda + 8);
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const unsigned short* Bk = B + k * pb + (nt * 8 + g) * ldb + k0 + 2 * t;
-        b[k][nt][0] = oz_ld32(Bk);
-        b[k][nt][1] = oz_ld32(Bk + 8);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < S; ++k)
-#pragma unroll
-      for (int l = 0; l < S - k; ++l)
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) oz_mma(acc[k + l][nt], a[k], b[l][nt]);
-  }
-}
-
-// FP64 value of output (row, col) of a tile: 2^(er + ec) sum_m 2^{-7(m+2)} acc_m.
-template <int S>
-__device__ __forceinline__ double oz_combine(const float (&acc)[S][2][4], int nt, int v, int er, int ec) {
-  double y = 0.0;
-#pragma unroll
-  for (int m = S - 1; m >= 0; --m) y += (double)acc[m][nt][v] * oz_pow2(er + ec - 7 * (m + 2));
-  return y;
-}
 
 // ---------------------------------------------------------------------------------------
 // shared-memory staged variant

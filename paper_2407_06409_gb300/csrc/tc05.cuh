@@ -93,10 +93,6 @@ __device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// Make this thread's generic-proxy shared-memory writes (cp.async included) visible to the
-// tensor core's asynchronous-proxy reads.
-__device__ __forceinline__ void tc_fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 // Eight consecutive FP32 columns of this thread's TMEM lane (32x32b shape), waited on in the
 // same statement so that no use of the registers can move ahead of the load.
 __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
@@ -110,16 +106,6 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-__device__ __forceinline__ void tc_cp_async16(uint32_t sdst, const void* gsrc, int bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sdst), "l"(gsrc), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void tc_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void tc_cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void tc_cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Arrive once on the mbarrier and add `bytes` to the transaction count it waits for.
 __device__ __forceinline__ void tc_mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
