@@ -109,6 +109,7 @@ bool tc_encode_map(CUtensorMap* map, const void* base, long long inner, long lon
 bool launch_chain_tc(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
                      cudaStream_t s) {
   if (c1 <= c0) return true;
+  if (digits != 5 && digits != 6) return false;
   launch_slice_w(w, p, m, c0, c1, digits, s);
   const int tiles = (3 * max_ns + TCS_M - 1) / TCS_M;
   // the wave's T planes start at row trow0 of the rebased pointer; its W planes at centre wc0

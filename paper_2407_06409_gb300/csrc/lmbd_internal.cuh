@@ -288,7 +288,7 @@ void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, 
 // W = D v_m digit planes for chain step m (one block per central atom)
 void launch_slice_w(const Work& w, const DevParams& p, int m, int c0, int c1, int digits, cudaStream_t s);
 // chain step on the fifth-generation tensor cores (tcgen05, TMEM accumulators), digits 5 or 6
-// (returns false when a tensor map cannot be encoded)
+// (digits 5 or 6; returns false for another digit count or when a tensor map cannot be encoded)
 bool launch_chain_tc(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,
                      cudaStream_t s);
 size_t chain_tc_smem(int digits);
