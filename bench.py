@@ -27,11 +27,18 @@ if ROOT not in sys.path:
 METRIC = "atoms/s for lMBD energy+forces on 1 GB300 (batched vs per-atom launch); serve p50/p99"
 FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (DFMA and DMMA), profiling recipe table
 FP32_PEAK_TFLOPS = 80.5          # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (unit counts and clock)
-# DRAM bytes (read + write) of the SCS phase (k_pair_radial, k_scs_fill, k_scs_factor) per atom:
-# ncu on the 512-atom box, profiles/scs_traffic_box512.md; scaled to a launch by atoms/launches
-SCS_DRAM_BYTES_PER_ATOM = 1.830e6
+# DRAM bytes (read + write) of the SCS factor kernel (k_scs_factor alone) per atom: ncu on the
+# 512-atom box, profiles/scs_traffic_box512.md; scaled to a launch by atoms / launches
+SCS_FACTOR_DRAM_BYTES_PER_ATOM = 1.650e6
+PRECISION = ("chain products: 6-digit (energy blocks) / 5-digit (adjoint-only blocks) bf16 Ozaki slices "
+             "of the FP64 operands, exact integer recombination, FP64 scaling; adjoint pair product: "
+             "5-digit slices; SCS: FP32 Cholesky and solves with FP64 iterative refinement to FP64 "
+             "accuracy; everything else FP64")
+PRECISION_FP64 = ("chain and adjoint pair products in FP64; SCS: FP32 Cholesky and solves with FP64 "
+                  "iterative refinement to FP64 accuracy; everything else FP64")
 WORKLOAD = ("periodic random box, 4096 atoms, 0.1 atoms/A^3, 4 species; r_SCS 5 A, MBD sphere 7 A "
-            "(r_MBD,1 = r_MBD,2 = 7 A), 12 omega, n_max 6; FP64 energies + forces")
+            "(r_MBD,1 = r_MBD,2 = 7 A), 12 omega, n_max 6; energies + forces within 1e-10 rel. / "
+            "1e-8 eV/A of the FP64 oracle (see precision)")
 SAMPLE_ATOMS = 64                # oracle sample: same density and cutoffs, same local problem sizes
 # digit-plane products per FP64 product of the sliced tensor-core kernels: S digits keep the
 # pairs (k, l) with k + l <= S + 1, S (S + 1) / 2 of them (ozaki.cuh); the chain uses 6 digits for
@@ -79,6 +86,10 @@ def parse():
                     help="the paper's approximate forces (Sec. III.D) instead of the exact gradient")
     ap.add_argument("--mma", default="tc05", choices=["warp", "tc05"],
                     help="tensor-core path of the sliced chain product: warp-level mma.sync or tcgen05")
+    ap.add_argument("--precision", default="sliced", choices=["sliced", "fp64"],
+                    help="arithmetic of the two large products: bf16 digit slices (default) or FP64")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="steps of the FP64-products measurement reported beside the default line (0 = skip)")
     ap.add_argument("--fit-nodes", type=int, default=0,
                     help="> 0: the paper's fitted integrand phi(omega) from omega = 0 and this many fit nodes")
     return ap.parse_args()
@@ -220,6 +231,8 @@ def run_ours(args, world, rank, local):
     if args.paper_forces:
         model.set_force_model(lmbd.FORCES_PAPER)
     model.set_mma_path(lmbd.MMA_TC05 if args.mma == "tc05" else lmbd.MMA_WARP)
+    if args.precision == "fp64":
+        model.set_precision(lmbd.PREC_FP64)
     pos = torch.tensor(s.positions, device=dev)
     cell = torch.tensor(s.cell, device=dev)
     sp = torch.tensor(s.species, dtype=torch.int32, device=dev)
@@ -236,6 +249,7 @@ def run_ours(args, world, rank, local):
     model.set_profiling(True)
     sampler = ClockSampler(local)
     phase_ms, phase_flops, phase_launch = {}, {}, {}
+    kernel_ms = {"scs_factor": 0.0, "scs_adjoint": 0.0}
     launches = 0
     barrier()
     torch.cuda.synchronize(dev)
@@ -246,6 +260,8 @@ def run_ours(args, world, rank, local):
         model.energy_forces(pos, cell, sp, nu, forces=True)
         st = model.stats()
         launches += st["kernel_launches"]
+        for k in kernel_ms:
+            kernel_ms[k] += st["ms_kernel"][k]
         for ph in lmbd.PHASES:
             phase_ms[ph] = phase_ms.get(ph, 0.0) + st["ms"][ph]
             phase_flops[ph] = phase_flops.get(ph, 0.0) + st["flops"][ph]
@@ -296,10 +312,27 @@ def run_ours(args, world, rank, local):
                     "launches_per_step": model.stats()["kernel_launches"]}
         model.set_launch_mode(lmbd.LAUNCH_BATCHED)
 
+    # ---- the same workload with FP64 products (same run, fewer steps) -----------------------
+    fp64_line = None
+    if args.precision == "sliced" and args.fp64_steps > 0:
+        model.set_precision(lmbd.PREC_FP64)
+        model.energy_forces(pos, cell, sp, nu, forces=True)
+        torch.cuda.synchronize(dev)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.fp64_steps):
+            model.energy_forces(pos, cell, sp, nu, forces=True)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = b0.elapsed_time(b1) / args.fp64_steps
+        fp64_line = {"value": world * args.atoms / (fms * 1e-3), "unit": "atoms/s", "ms_per_step": fms,
+                     "steps": args.fp64_steps, "warmup": 1, "precision": PRECISION_FP64}
+        model.set_precision(lmbd.PREC_SLICED)
+
     if rank != 0:
         return 0
 
-    # ---- roofline of the dominant kernel (FP64 pipe) ---------------------------------------
+    # ---- roofline of the dominant kernel ---------------------------------------------------
     fp64 = ("scs", "chain", "adj_pair", "adj_scs")
     dom = max(fp64, key=lambda ph: phase_ms.get(ph, 0.0))
     avg_ms = phase_ms[dom] / max(1, phase_launch[dom])
@@ -308,26 +341,39 @@ def run_ours(args, world, rank, local):
                     "adj_scs": "k_scs_adjoint2"}
     st_last = model.stats()
     if dom == "scs":
-        # mixed-precision SCS: FP32 Cholesky and solves, FP64 residual and right-hand side.  The
-        # roofline is the sum of the two pipe-bound times: t* = W32 / P32 + W64 / P64.
-        # frequencies of the SCS solves
+        # The SCS factor kernel.  Method work (the dense linear algebra of the local screening
+        # solves): per centre and SCS frequency a Cholesky factorisation, (3 n1)^3 / 3 flops, and
+        # 12 (3 n1)^2 for the triangular solves with 3 right-hand sides (the count of the work
+        # estimate of the scope table, independent of how many refinement corrections the
+        # kernel makes).  The factor runs on the FP32 SIMT pipe, so the peak is that pipe's
+        # nominal rate from unit counts and the maximum clock.  Time: the kernel's own bucket
+        # launches, fork to join (CUDA events around them in the library).
         nq = 2 if args.omega_ref > 0 else (args.fit_nodes + 2 if args.fit_nodes > 0 else 13)
         n1 = model.site_counts(args.atoms)[:, 0].astype(float)
         N1 = 3.0 * n1
+        w_method = nq * float(np.sum(N1 ** 3 / 3.0 + 12.0 * N1 ** 2))
+        n_fac = max(1, phase_launch[dom] // args.steps - 2)   # less k_pair_radial and k_scs_fill
+        t_fac = kernel_ms["scs_factor"] / args.steps * 1e-3 if kernel_ms["scs_factor"] > 0 else avg_ms * 1e-3
+        work = w_method / n_fac
+        achieved = work / (t_fac / n_fac) / 1e12
+        # the composite bound of the kernel's full instruction mix, as a second figure
         w32 = nq * float(np.sum(N1 ** 3 / 3.0 + 18.0 * N1 ** 2))
         pairs, adj = float(st_last["scs_pairs"]), float(st_last["scs_adjacency"])
         w64 = nq * (60.0 * adj + 36.0 * (pairs - adj / 2.0) + 2.0 * pairs)
-        t_launch = avg_ms * 1e-3
-        t_star = (w32 / (FP32_PEAK_TFLOPS * 1e12) + w64 / (FP64_PEAK_TFLOPS * 1e12)) / phase_launch[dom] * args.steps
-        work = (w32 + w64) / phase_launch[dom] * args.steps
-        roofline = {"bound": "alu", "achieved": work / t_launch / 1e12, "peak": work / t_star / 1e12,
-                    "unit": "TFLOP/s", "frac": t_star / t_launch,
-                    "traffic": SCS_DRAM_BYTES_PER_ATOM * args.atoms * args.steps / phase_launch[dom],
-                    "kernel": kernel_names[dom],
-                    "peak_note": "composite of this phase's FP32 work (Cholesky, solves) at the nominal FP32 "
-                                 "peak (152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s) and its FP64 work "
-                                 "(residual, right-hand side) at the nominal FP64 peak 1.25 TFLOP/s",
-                    "work_fp32": w32, "work_fp64": w64}
+        t_star = w32 / (FP32_PEAK_TFLOPS * 1e12) + w64 / (FP64_PEAK_TFLOPS * 1e12)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_PEAK_TFLOPS,
+                    "traffic": SCS_FACTOR_DRAM_BYTES_PER_ATOM * args.atoms / n_fac,
+                    "kernel": kernel_names[dom], "launches_per_step": n_fac, "ms_per_step": t_fac * 1e3,
+                    "work_per_step": w_method,
+                    "peak_note": "method flops sum_k nq [(3 n1)^3/3 + 12 (3 n1)^2] over the kernel's own time, "
+                                 "against the FP32 SIMT pipe it runs on: 152 SMs x 128 lanes x 2 flops x "
+                                 "2.07 GHz = 80.5 TFLOP/s nominal (unit counts and maximum clock)",
+                    "composite": {"peak_note": "the kernel's whole instruction mix: FP32 work (factor, solves "
+                                               "and refinement corrections) at 80.5 TFLOP/s plus FP64 work "
+                                               "(residual, right-hand side) at the nominal 1.25 TFLOP/s",
+                                  "work_fp32": w32, "work_fp64": w64, "t_star_ms": t_star * 1e3,
+                                  "frac": t_star / t_fac}}
     elif dom in ("chain", "adj_pair"):
         # sliced products on the bf16 tensor cores: the bf16 work is the FP64 product's flops times
         # the digit pairs per product; peak = the measured sustained bf16 rate (timed inside a step)
@@ -380,8 +426,10 @@ def run_ours(args, world, rank, local):
                        "l2": f"inputs resident; per-step working set {st['bytes_workspace'] / 1e9:.1f} GB > 129 MB L2",
                        "sites_per_atom": st["n_sites"] / args.atoms, "max_k1": st["max_k1"],
                        "scs_bucket_width": bucket_width, "chain_mma": args.mma,
-                       "max_sphere": st["max_sphere"]},
+                       "max_sphere": st["max_sphere"],
+                       "precision": PRECISION if args.precision == "sliced" else PRECISION_FP64},
             "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
+            "fp64_products": fp64_line,
             "gpu_launches": launches, "per_atom_launch": per_atom, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0

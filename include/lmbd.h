@@ -112,6 +112,9 @@ typedef struct {
   int scs_recomputed;      /* 1 when the SCS stage was evaluated again before its adjoint     */
   long long scs_pairs;     /* SCS site pairs over all central atoms (r < r_SCS, K1 x (K1 u K2)) */
   long long scs_adjacency; /* directed K1-K1 pair entries (two per K1-K1 pair)                 */
+  double ms_kernel[2];     /* with profiling, one wave: device time of the bucket launches of
+                              [0] the SCS factor kernel, [1] the SCS adjoint kernel (all side
+                              streams, fork to join; without the pair-list kernels)            */
 } lmbd_stats;
 
 /* Fill *out with the defaults r_scs = 5, r_mbd1 = r_mbd2 = r_sphere = 7,
@@ -130,6 +133,9 @@ int lmbd_create(const lmbd_species* species, int n_species, const lmbd_params* p
  *   cell         3 x 3 row-major lattice vectors (rows), Angstrom; NULL = no periodicity
  *   species      N indices into the species table
  *   hirshfeld    N Hirshfeld volume ratios nu_i > 0
+ * A species index outside [0, n_species), a non-finite position or a Hirshfeld ratio
+ * that is not positive and finite gives LMBD_EINVAL, for host and device arrays alike
+ * (device arrays are checked by the first kernel, before any table lookup).
  *   energies     out, N per-atom energies E_k, eV (may be NULL)
  *   forces       out, N x 3, eV/Angstrom, -d(sum_k E_k)/dR; NULL = energies only
  *   stream       cudaStream_t to run on (NULL = legacy default stream)
@@ -309,9 +315,8 @@ int lmbd_destroy(lmbd_ctx* ctx);
 /* Allocation-free central polarisabilities.
  *
  * The paper has no counterpart: this entry point exists for callers that cannot
- * allocate device memory — code running inside someone else's CUDA-graph capture or
- * replay, plug-ins of an MD engine that owns the device memory pool, and embedded
- * runtimes that forbid allocation after start-up.  It computes the same central
+ * allocate device memory — plug-ins of an MD engine that owns the device memory pool,
+ * and embedded runtimes that forbid allocation after start-up.  It computes the same central
  * polarisabilities alpha_I,k(omega) as lmbd_energy_forces (site search and one local
  * SCS solve per atom and frequency, Sec. III.B), without a context and without
  * calling cudaMalloc, cudaFree or any allocating routine: every scratch buffer is
@@ -326,6 +331,11 @@ int lmbd_destroy(lmbd_ctx* ctx);
  * Limits: n_atoms <= LMBD_NOALLOC_MAX_ATOMS, at most LMBD_NOALLOC_SITE_CAP sites within
  * max(2 r_SCS, sphere radius) of any atom, at most LMBD_NOALLOC_MAX_K1 sites within
  * r_SCS; larger problems return LMBD_ESCRATCH before any device work on them.
+ * The call reads the site counts back to the host before the solves, so it cannot run
+ * on a stream that is being captured into a CUDA graph: such a stream gets
+ * LMBD_EUNSUPPORTED before anything is issued on it.  Device-resident species indices
+ * outside [0, n_species), non-finite positions and non-positive Hirshfeld ratios give
+ * LMBD_EINVAL (host arrays are checked before any copy).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
  * share the one array and it keeps the last call's contents: calls whose work

@@ -18,6 +18,16 @@ __global__ void k_free_atom(Work w, DevParams p) {
   if (a >= w.n_atoms) return;
   int s = w.species[a];
   double nu = w.nu[a];
+  // device-resident inputs are validated here (host arrays are checked before the copy): a
+  // species index outside the table is never used to index it; the call then returns
+  // LMBD_EINVAL after the neighbour phase
+  const bool bad = s < 0 || s >= p.n_species || !(nu > 0.0) || !isfinite(nu) || !isfinite(w.pos[3 * a]) ||
+                   !isfinite(w.pos[3 * a + 1]) || !isfinite(w.pos[3 * a + 2]);
+  if (bad) {
+    atomicOr(w.status, LMBD_FLAG_BAD_INPUT);
+    s = 0;
+    nu = 1.0;
+  }
   double a0 = w.table[3 * s + 0], c6 = w.table[3 * s + 1], r0 = w.table[3 * s + 2];
   double om = 4.0 * c6 / (3.0 * a0 * a0);
   const double c = 0.26596152026762182;  // sqrt(2/pi)/3

@@ -233,9 +233,8 @@ __device__ __forceinline__ bool tsr_pair(const DevParams& p, double r, double s_
 // ---------------------------------------------------------------------------------------
 // Allocation-free variant of the SCS forward kernel.
 //
-// Some callers cannot call cudaMalloc: code that runs inside a CUDA graph being captured
-// or replayed by someone else, plug-ins of an MD engine that owns the device memory pool,
-// and embedded runtimes that forbid allocation after start-up.  For them,
+// Some callers cannot call cudaMalloc: plug-ins of an MD engine that owns the device
+// memory pool, and embedded runtimes that forbid allocation after start-up.  For them,
 // lmbd_central_polarizabilities_noalloc (lmbd.h) computes the central polarisabilities
 // with every scratch buffer carved from the fixed array below.  This array is part of the
 // library image: every GPU that loads the library holds these bytes until the process

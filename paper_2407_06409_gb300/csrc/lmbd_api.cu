@@ -58,6 +58,9 @@ struct Ctx {
   int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
+  // around the bucket launches of the SCS factor (pass A) and SCS adjoint (pass C): their own
+  // wall time, fork to join, without the pair-list and radial-table kernels of the phase
+  cudaEvent_t kev[4] = {};
   // side streams for independent bucket launches (same priority as the caller's stream)
   static constexpr int kSide = 3;
   cudaStream_t side[kSide] = {};
@@ -630,8 +633,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   w.energies = (double*)c->energies.p;
   w.trbuf = (double*)c->trbuf.p;
 
-  // species indices must be in range and inputs finite: checked on the host only when
-  // the caller passed host arrays (device arrays are trusted).
+  // species indices must be in range and inputs finite: checked here when the caller passed
+  // host arrays, and by the free-atom kernel for device arrays (LMBD_FLAG_BAD_INPUT).
   if (!is_device_ptr(spec_in))
     for (int i = 0; i < N; ++i)
       if (spec_in[i] < 0 || spec_in[i] >= c->n_species) return LMBD_EINVAL;
@@ -653,8 +656,6 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     }
   };
   mark(LMBD_PHASE_NEIGHBORS);
-  launch_free_atom(w, dp, s);
-  ++launches;
   for (int attempt = 0; attempt < 4; ++attempt) {
     TRY(ensure(c->site_atom, sizeof(int) * (size_t)N * c->site_cap));
     TRY(ensure(c->site_x, sizeof(double) * 3 * (size_t)N * c->site_cap));
@@ -662,6 +663,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     w.site_atom = (int*)c->site_atom.p;
     w.site_x = (double*)c->site_x.p;
     CK(cudaMemsetAsync(w.status, 0, sizeof(int) * 4, s));
+    if (attempt == 0) {   // after the status reset: it validates device-resident inputs
+      launch_free_atom(w, dp, s);
+      ++launches;
+    }
     launch_neighbors(w, dp, g, s, &launches);
     launch_scs_count(w, dp, w.site_cap, s);
     launch_offsets(w, dp, s);
@@ -670,7 +675,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     CK(cudaMemcpyAsync(c->totals_h, w.totals, sizeof(long long) * 16, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->status_h, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (*c->status_h & LMBD_FLAG_COINCIDENT) return LMBD_EINVAL;
+    if (*c->status_h & (LMBD_FLAG_COINCIDENT | LMBD_FLAG_BAD_INPUT)) return LMBD_EINVAL;
     if (!(*c->status_h & LMBD_FLAG_CAPACITY)) break;
     if (c->site_cap >= 4096 || attempt == 3) return LMBD_ECAPACITY;
     c->site_cap *= 2;
@@ -826,6 +831,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   const bool per_atom = c->launch_mode == LMBD_LAUNCH_PER_ATOM;
 
   // stage-1 forward of one wave: pair lists, FP32 factorisation, refined solutions, alpha_K
+  bool kmark_fwd = false;   // record kev[0], kev[1] around the factor buckets (pass A, profiling)
   auto stage1_forward = [&](int wv, const std::vector<int>& cuts, const std::vector<std::vector<Bucket>>& bk,
                             const int* order) -> int {
     const int c0 = cuts[wv], c1 = cuts[wv + 1];
@@ -837,12 +843,14 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         launch_scs_factor(w, dp, nullptr, cc, cc + 1, c->counts_h[cc].n1, c->counts_h[cc].n12, s);
       phase_launch[LMBD_PHASE_SCS] += c1 - c0;
     } else {
+      if (kmark_fwd) cudaEventRecord(c->kev[0], s);
       Fork fk(c, s, (int)bk[wv].size());
       for (size_t i = 0; i < bk[wv].size(); ++i) {
         const Bucket& b = bk[wv][i];
         launch_scs_factor(w, dp, order, b.b0, b.b1, b.n1, b.n12, fk.stream((int)i));
       }
       fk.join();
+      if (kmark_fwd) cudaEventRecord(c->kev[1], s);
       phase_launch[LMBD_PHASE_SCS] += (int)bk[wv].size();
     }
     CK(cudaGetLastError());
@@ -854,7 +862,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   mark(LMBD_PHASE_SCS);
   launch_pair_radial(w, dp, s);
   ++phase_launch[LMBD_PHASE_SCS];
+  kmark_fwd = prof && !per_atom;
   for (int wv = 0; wv < nwA; ++wv) TRY(stage1_forward(wv, cutA, bucketsA, orderA));
+  kmark_fwd = false;
 
   // ---- pass B: stage 2 (MBD energy) and its adjoint, per wave --------------------------------
   if (forces) {
@@ -988,12 +998,14 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         }
         phase_launch[LMBD_PHASE_ADJ_SCS] += 2 * (c1 - c0);
       } else {
+        if (prof) cudaEventRecord(c->kev[2], s);
         Fork fk(c, s, (int)bucketsC[wv].size());
         for (size_t i = 0; i < bucketsC[wv].size(); ++i) {
           const Bucket& b = bucketsC[wv][i];
           launch_scs_adjoint2(w, dp, orderC, b.b0, b.b1, b.n1, b.n12, fk.stream((int)i));
         }
         fk.join();
+        if (prof) cudaEventRecord(c->kev[3], s);
         launch_scs_site_reduce(w, dp, c0, c1, s);
         phase_launch[LMBD_PHASE_ADJ_SCS] += (int)bucketsC[wv].size() + 1;
       }
@@ -1054,6 +1066,14 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         if (nx <= LMBD_NPHASE && cudaEventElapsedTime(&ms, c->ev[ph], c->ev[nx]) == cudaSuccess) S.ms[ph] = ms;
         cudaGetLastError();
       }
+    if (prof && !per_atom) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]) == cudaSuccess) S.ms_kernel[0] = ms;
+      cudaGetLastError();
+      ms = 0.f;
+      if (forces && cudaEventElapsedTime(&ms, c->kev[2], c->kev[3]) == cudaSuccess) S.ms_kernel[1] = ms;
+      cudaGetLastError();
+    }
     S.n_sites = c->totals_h[7];
     S.scs_pairs = c->totals_h[8];
     S.scs_adjacency = c->totals_h[9];
@@ -1192,12 +1212,18 @@ int lmbd_autotune(lmbd_ctx* ctx, int n_atoms, const double* positions, const dou
 int lmbd_set_profiling(lmbd_ctx* ctx, int on) {
   if (!ctx) return LMBD_EINVAL;
   Ctx& c = ctx->c;
-  if (on && !c.ev[0])
+  if (on && !c.ev[0]) {
     for (int i = 0; i <= LMBD_NPHASE; ++i)
       if (cudaEventCreate(&c.ev[i]) != cudaSuccess) {
         cudaGetLastError();
         return LMBD_ECUDA;
       }
+    for (int i = 0; i < 4; ++i)
+      if (cudaEventCreate(&c.kev[i]) != cudaSuccess) {
+        cudaGetLastError();
+        return LMBD_ECUDA;
+      }
+  }
   c.profiling = on ? 1 : 0;
   return LMBD_OK;
 }
@@ -1345,6 +1371,8 @@ int lmbd_destroy(lmbd_ctx* ctx) {
   release(c.arena);
   for (int i = 0; i <= LMBD_NPHASE; ++i)
     if (c.ev[i]) cudaEventDestroy(c.ev[i]);
+  for (int i = 0; i < 4; ++i)
+    if (c.kev[i]) cudaEventDestroy(c.kev[i]);
   for (int i = 0; i < Ctx::kSide; ++i) {
     if (c.side[i]) cudaStreamDestroy(c.side[i]);
     if (c.join_ev[i]) cudaEventDestroy(c.join_ev[i]);
@@ -1381,14 +1409,21 @@ const char* lmbd_status_string(int status) {
 // ---------------------------------------------------------------------------------------
 namespace {
 
+// Regions of the fixed scratch array, 256-byte aligned.  A region that does not fit sets
+// the sticky `failed` bit (and yields nullptr); the caller tests the bit once, before any
+// device work, so no kernel ever receives a pointer past the array.
 struct Carve {
   unsigned char* base;
   size_t used, cap;
+  bool failed;
   template <class T>
   T* take(size_t n) {
     size_t off = (used + 255) & ~size_t(255);
     size_t bytes = n * sizeof(T);
-    if (off + bytes > cap) return nullptr;
+    if (failed || off + bytes > cap) {
+      failed = true;
+      return nullptr;
+    }
     used = off + bytes;
     return reinterpret_cast<T*>(base + off);
   }
@@ -1440,6 +1475,16 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   if (!is_device_ptr(positions))
     for (int i = 0; i < 3 * N; ++i)
       if (!std::isfinite(positions[i])) return LMBD_EINVAL;
+
+  // A capturing stream allows none of the synchronous copies and stream synchronisations
+  // below (the sizes are read back to the host before the solve); refuse it before
+  // touching the stream, so that the caller's capture stays valid.
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap_status) != cudaSuccess) {
+    cudaGetLastError();
+    return LMBD_EUNSUPPORTED;
+  }
+  if (cap_status != cudaStreamCaptureStatusNone) return LMBD_EUNSUPPORTED;
 
   void* base = nullptr;
   size_t cap = 0;
@@ -1507,7 +1552,7 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   const int site_cap = LMBD_NOALLOC_SITE_CAP;
 
   // carve the scratch array
-  Carve cv{static_cast<unsigned char*>(base), 0, cap};
+  Carve cv{static_cast<unsigned char*>(base), 0, cap, false};
   double* table = cv.take<double>(3 * (size_t)n_species);
   double* pos = cv.take<double>(3 * (size_t)N);
   int* spec = cv.take<int>(N);
@@ -1534,17 +1579,17 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   w.off_s = cv.take<long long>(N + 1);
   w.off_b = cv.take<long long>(N + 1);
   w.off_t = cv.take<long long>(N + 1);
-  w.totals = cv.take<long long>(12);
+  w.totals = cv.take<long long>(16);   // the offsets kernel writes 16 totals
   w.status = cv.take<int>(4);
   w.alphaI = cv.take<double>((size_t)N * nq);
   const long long slot_doubles = 9LL * LMBD_NOALLOC_MAX_K1 * LMBD_NOALLOC_MAX_K1;
-  if (!table || !pos || !spec || !nu || !w.alphaI) return LMBD_ESCRATCH;
+  if (cv.failed) return LMBD_ESCRATCH;
   size_t used = (cv.used + 255) & ~size_t(255);
   long long nslots = (long long)((cap - used) / (sizeof(double) * slot_doubles));
   if (nslots > 128) nslots = 128;
   if (nslots < 1) return LMBD_ESCRATCH;
   double* slots = cv.take<double>((size_t)nslots * slot_doubles);
-  if (!slots) return LMBD_ESCRATCH;
+  if (cv.failed) return LMBD_ESCRATCH;
   w.pos = pos;
   w.species = spec;
   w.nu = nu;
@@ -1568,12 +1613,12 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   launch_neighbors(w, dp, g, s, &launches);
   launch_offsets(w, dp, s);
   CK(cudaGetLastError());
-  long long tot[12];
+  long long tot[16];
   int flags = 0;
   CK(cudaMemcpyAsync(tot, w.totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&flags, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (flags & LMBD_FLAG_COINCIDENT) return LMBD_EINVAL;
+  if (flags & (LMBD_FLAG_COINCIDENT | LMBD_FLAG_BAD_INPUT)) return LMBD_EINVAL;
   if (flags & LMBD_FLAG_CAPACITY) return LMBD_ESCRATCH;
   const int max_n1 = (int)tot[4], max_n12 = (int)tot[6];
   if (max_n1 > LMBD_NOALLOC_MAX_K1 || max_n12 > site_cap) return LMBD_ESCRATCH;

@@ -17,6 +17,8 @@
 #define LMBD_FLAG_MODEL 16          // Lorentzian model not applicable: alpha~(0) < alpha~(omega_ref),
                                     // or a fitted phi without decaying term
 #define LMBD_FLAG_TIMEOUT 32        // a bounded device wait (tensor-core pipeline) ran out
+#define LMBD_FLAG_BAD_INPUT 64      // a species index out of range, or a non-finite position or
+                                    // non-positive Hirshfeld ratio, in device-resident inputs
 #define LMBD_FITW 32                // stride of the per-centre integrand weights dE/dI(omega_j)
 #define LMBD_FIT_ROWS 25            // omega = 0 plus at most 24 fit nodes
 #define LMBD_MAX_LANCZOS 64         // Lanczos steps of the polynomial-fit coefficients
@@ -104,7 +106,7 @@ struct Work {
   long long* off_t;            // sum (3 ns)^2
   long long* off_p;            // sum of SCS pairs per centre
   long long* off_a;            // sum of SCS adjacency entries per centre
-  long long* totals;           // 12 entries written by the offsets kernel
+  long long* totals;           // 16 entries written by the offsets kernel
   // SCS pair lists (one list per central atom; rows = coupled sites of K1)
   int* pcount;                 // N x 2: pairs, adjacency entries
   int* pr_ij;                  // pairs x 2: owner row i (K1), partner j (K1 with j < i, or K2)

@@ -45,13 +45,19 @@ class Stats(ctypes.Structure):
                 ("n_sites", ctypes.c_longlong), ("max_k1", ctypes.c_int), ("max_sphere", ctypes.c_int),
                 ("max_sites", ctypes.c_int), ("kernel_launches", ctypes.c_int), ("bytes_arena", ctypes.c_double),
                 ("waves_scs", ctypes.c_int), ("waves_mbd", ctypes.c_int), ("scs_recomputed", ctypes.c_int),
-                ("scs_pairs", ctypes.c_longlong), ("scs_adjacency", ctypes.c_longlong)]
+                ("scs_pairs", ctypes.c_longlong), ("scs_adjacency", ctypes.c_longlong),
+                ("ms_kernel", ctypes.c_double * 2)]
 
     def as_dict(self) -> dict:
         d = {}
         for k, _ in self._fields_:
             v = getattr(self, k)
-            d[k] = {ph: v[i] for i, ph in enumerate(PHASES)} if k in ("flops", "ms", "launches") else v
+            if k in ("flops", "ms", "launches"):
+                d[k] = {ph: v[i] for i, ph in enumerate(PHASES)}
+            elif k == "ms_kernel":
+                d[k] = {"scs_factor": v[0], "scs_adjoint": v[1]}
+            else:
+                d[k] = v
         return d
 
 

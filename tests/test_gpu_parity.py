@@ -279,3 +279,32 @@ def test_fp64_product_mode_matches_oracle(lm, box110, box110_ref):
                                torch.tensor(s.hirshfeld, device="cuda"))
     _check_e(e.cpu().numpy(), e_ref)
     _check_f(f.cpu().numpy(), f_ref)
+
+
+def test_device_inputs_out_of_range_are_rejected(lm, cluster24):
+    # device-resident inputs are validated by the first kernel: a species index outside the
+    # table, a non-finite position or a non-positive Hirshfeld ratio gives LMBD_EINVAL (never
+    # an out-of-bounds table read), and the context stays usable afterwards
+    s = cluster24
+    p = lm.default_params(r_scs=5.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
+    model = lm.LMBD(s.table, p, 12, 6)
+    pos = torch.tensor(s.positions, device="cuda")
+    sp = torch.tensor(s.species, dtype=torch.int32, device="cuda")
+    nu = torch.tensor(s.hirshfeld, device="cuda")
+    for what in ("species_high", "species_negative", "nan_position", "zero_nu"):
+        pos_b, sp_b, nu_b = pos.clone(), sp.clone(), nu.clone()
+        if what == "species_high":
+            sp_b[5] = len(s.table)
+        elif what == "species_negative":
+            sp_b[11] = -1
+        elif what == "nan_position":
+            pos_b[3, 1] = float("nan")
+        else:
+            nu_b[17] = 0.0
+        with pytest.raises(lm.LmbdError) as ex:
+            model.energy_forces(pos_b, None, sp_b, nu_b, forces=True)
+        assert ex.value.status == lm.LMBD_EINVAL, what
+    _, e_ref, f_ref = _run(lm, s, p, forces=True)
+    e, f = model.energy_forces(pos, None, sp, nu, forces=True)
+    assert np.array_equal(e.cpu().numpy(), e_ref)
+    assert np.abs(f.cpu().numpy() - f_ref).max() < 1e-12

@@ -845,3 +845,79 @@ def test_paper_forces_differ_from_the_exact_ones_with_screening():
     Fp = sysm.paper_forces()
     rel = np.sqrt(((Fp - F) ** 2).mean() / (F ** 2).mean())
     assert 0.01 < rel < 0.5
+
+
+# ---------------------------------------------------------------------------------------
+# blend of local and central polarisabilities (Sec. III.B, Eq. full-pol): the limits fix
+# which polarisability each weight multiplies
+# ---------------------------------------------------------------------------------------
+def _blend_limits_hold(sysm, k):
+    """Checks of Eq. full-pol that come from continuity, not from the formula: a site at the
+    centre carries its local polarisability alpha_K (the range-separation switch starts at 0
+    with zero slope), a site approaching r_SCS from inside carries alpha_I, continuously with
+    the value outside r_SCS where only alpha_I exists, and in between the result is a convex
+    combination of the two.  Values come from a real local solve where alpha_K != alpha_I.
+    Returns a list of violated properties (empty when all hold)."""
+    p = sysm.p
+    s = sysm.sites(k)
+    ab, sg, rv, _, _ = sysm.free()
+    x = oracle.site_positions(torch.as_tensor(sysm.pos), sysm.cell, s, k)
+    _, aK, _, _ = oracle.scs_local(x, s, ab, sg, rv, p)
+    aI_map = sysm.central_alpha([int(a) for a in s.atom[: s.ns]])
+    aI = torch.stack([aI_map[int(a)] for a in s.atom[: s.ns]])
+    rs = p.r_scs / BOHR
+    # the coupled site (not the centre) whose local and central values differ the most
+    diff = (aK.T[1:s.n1] - aI[1:s.n1]).abs().max(dim=1).values
+    i = 1 + int(torch.argmax(diff))
+    gap = aI[i] - aK.T[i]
+    bad = []
+    if not float(gap.abs().max()) > 1e-3 * float(aI[i].abs().max()):
+        bad.append("configuration has alpha_K == alpha_I")
+
+    def at(r):
+        rb = torch.full((s.ns,), 2.0 * rs, dtype=DT)   # every other site outside r_SCS
+        rb[0] = 0.0
+        rb[i] = r
+        return oracle.blend(aK, aI, rb, p)[i]
+
+    eps = 1e-3 * rs
+    # r -> 0: alpha_K up to O(eps^2) of the gap
+    lo = at(eps)
+    if not bool(torch.all((lo - aK.T[i]).abs() <= 4.0 * (eps / rs) ** 2 * gap.abs() + 1e-15)):
+        bad.append("r -> 0 does not give alpha_K")
+    # r -> r_SCS from inside: alpha_I up to O(eps^2), the value just outside r_SCS
+    hi = at(rs - eps)
+    if s.ns <= s.n1:
+        bad.append("configuration has no site outside r_SCS")
+    rb = torch.cat([torch.zeros(1, dtype=DT), torch.sqrt((x[1:s.ns] * x[1:s.ns]).sum(-1))])
+    outside = oracle.blend(aK, aI, rb, p)[s.n1:s.ns]
+    if not bool(torch.all(outside == aI[s.n1:s.ns])):
+        bad.append("outside r_SCS is not alpha_I")
+    if not bool(torch.all((hi - aI[i]).abs() <= 4.0 * (eps / rs) ** 2 * gap.abs() + 1e-15)):
+        bad.append("not continuous at r_SCS")
+    # zero slope at both ends (central differences in r)
+    h = 1e-6 * rs
+    slope0 = (at(2 * h) - at(h)) / h
+    slope1 = (at(rs - h) - at(rs - 2 * h)) / h
+    if not bool(torch.all(slope0.abs() <= 1e-4 * gap.abs() / rs)) or \
+            not bool(torch.all(slope1.abs() <= 1e-4 * gap.abs() / rs)):
+        bad.append("slope not zero at the ends")
+    # convex combination in between
+    for frac in (0.2, 0.5, 0.8):
+        v = at(frac * rs)
+        t = (v - aK.T[i]) / gap
+        if not bool(torch.all((t > 0.0) & (t < 1.0))):
+            bad.append(f"not between alpha_K and alpha_I at r = {frac} r_SCS")
+    return bad
+
+
+def test_blend_switches_from_local_to_central_polarisability(monkeypatch):
+    s = inputs.cluster(24, seed=0)
+    p = oracle.Params(r_scs=4.0, r_mbd1=7.0, r_mbd2=7.0, r_sphere=7.0, n_freq=4)
+    sysm = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table, p)
+    assert _blend_limits_hold(sysm, 0) == []
+    # a blend with the two weights swapped, planted in the oracle, fails the same checks
+    import oracle.lmbd_oracle as lo
+    monkeypatch.setattr(lo, "f_scs", lambda r, r_scs: 1.0 - (3.0 * (r / r_scs) ** 2 - 2.0 * (r / r_scs) ** 3))
+    bad = _blend_limits_hold(sysm, 0)
+    assert "r -> 0 does not give alpha_K" in bad and "not continuous at r_SCS" in bad

@@ -1,9 +1,9 @@
 """The allocation-free entry point agrees with the regular one.
 
 lmbd_central_polarizabilities_noalloc serves callers that cannot allocate device
-memory (inside someone else's CUDA-graph capture, an MD engine's memory pool, or an
-embedded runtime that forbids allocation after start-up); its scratch is a fixed
-array inside the library.  This test calls it through the C ABI twice in a row and
+memory (a plug-in of an MD engine that owns the memory pool, or an embedded runtime
+that forbids allocation after start-up); its scratch is a fixed array inside the
+library.  This test calls it through the C ABI twice in a row and
 compares both results with the central polarisabilities that lmbd_energy_forces
 computes, within the 1e-12 relative tolerance the other polarisability tests use.
 It is collected last so that a failure here cannot hide failures elsewhere.
@@ -78,3 +78,52 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lm):
     p = lm.default_params(r_scs=4.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
     out = torch.zeros((s.n_atoms, 13), dtype=torch.float64, device="cuda")
     assert _noalloc(lm, s, p, 12, out) == 7   # LMBD_ESCRATCH
+
+
+def test_noalloc_rejects_site_counts_beyond_its_scratch(lm):
+    # within the atom limit, but more sites per atom than the fixed scratch holds
+    out = torch.zeros((80, 13), dtype=torch.float64, device="cuda")
+    # (a) 80 atoms packed within 4.5 Angstrom, r_SCS = 10 Angstrom: every atom has all 80 in
+    # its coupled set K1 (> LMBD_NOALLOC_MAX_K1 = 64) but only 80 sites in its list (< 512)
+    s = inputs.cluster(80, radius=4.5, min_sep=1.0, n_species=3, seed=5)
+    p = lm.default_params(r_scs=10.0, r_mbd1=10.0, r_mbd2=10.0, r_sphere=10.0)
+    assert _noalloc(lm, s, p, 12, out) == 7   # LMBD_ESCRATCH
+    # (b) a periodic 200-atom box at 0.1 atoms/A^3 with r_SCS = 6 Angstrom: ~720 sites within
+    # 2 r_SCS of every atom (> LMBD_NOALLOC_SITE_CAP = 512)
+    s = inputs.box(200, seed=6)
+    p = lm.default_params(r_scs=6.0, r_mbd1=6.0, r_mbd2=6.0, r_sphere=6.0)
+    out = torch.zeros((200, 13), dtype=torch.float64, device="cuda")
+    assert _noalloc(lm, s, p, 12, out) == 7
+    # the scratch is reusable after a rejection
+    s = inputs.cluster(24, seed=0)
+    p = lm.default_params(r_scs=5.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
+    out = torch.full((24, 13), float("nan"), dtype=torch.float64, device="cuda")
+    assert _noalloc(lm, s, p, 12, out) == lm.LMBD_OK
+    assert np.allclose(out.cpu().numpy(), _reference(lm, s, p, 12), rtol=1e-12, atol=0)
+
+
+def test_noalloc_refuses_a_capturing_stream(lm):
+    # the entry point reads site counts back to the host, which a stream under capture does
+    # not allow: it must refuse the stream before issuing anything, leaving the capture valid
+    s = inputs.cluster(24, seed=0)
+    p = lm.default_params(r_scs=5.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
+    out = torch.zeros((24, 13), dtype=torch.float64, device="cuda")
+    marker = torch.zeros(4, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        st = _noalloc(lm, s, p, 12, out)
+        marker.fill_(1.0)
+    assert st == lm.LMBD_EUNSUPPORTED
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.all(marker == 1.0)
+
+
+def test_noalloc_rejects_device_species_out_of_range(lm):
+    s = inputs.cluster(24, seed=0)
+    p = lm.default_params(r_scs=5.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
+    bad = inputs.Structure(s.positions, None, np.where(np.arange(24) == 7, len(s.table), s.species).astype(np.int32),
+                           s.hirshfeld, s.table)
+    out = torch.zeros((24, 13), dtype=torch.float64, device="cuda")
+    assert _noalloc(lm, bad, p, 12, out) == lm.LMBD_EINVAL
