@@ -579,6 +579,25 @@ def local_energy(T, alpha_tilde, weight, p: Params):
     return e
 
 
+def spectral_ratios(T, alpha_tilde, p: Params) -> list[float]:
+    """Proxy of the polarisation catastrophe (Sec. III.A: the series of Eq. E_k converges only
+    when the eigenvalues of G lie inside (-1, 1)): for every integrand frequency, with
+    M = floor(n_max / 2), the ratio |G^M e_k|^2 / |G^(M-1) e_k|^2 of the Frobenius norms of the
+    centre's columns of G^M and G^(M-1), from explicit matrix powers.  As M grows it tends to
+    the largest lambda^2 that the centre's block sees.  Empty when M < 2."""
+    M = (p.series_order or 0) // 2
+    if M < 2:
+        return []
+    out = []
+    for q in range(1, alpha_tilde.shape[1]):
+        dq = torch.sqrt(alpha_tilde[:, q]).repeat_interleave(3)
+        G = dq[:, None] * T * dq[None, :]
+        Gm1 = torch.linalg.matrix_power(G, M - 1)[:, :3]
+        Gm = G @ Gm1
+        out.append(float((Gm * Gm).sum() / (Gm1 * Gm1).sum()))
+    return out
+
+
 # ----------------------------------------------------------------------------------------
 # drivers
 # ----------------------------------------------------------------------------------------
@@ -636,6 +655,30 @@ class System:
             # Lorentzian model: alpha~ at the quadrature nodes from its values at 0 and omega_ref
             at = lorentzian(at[:, 0], at[:, 1], self.p.omega_ref, self.omega)
         return local_energy(T, at, self.weight, self.p) * HARTREE_EV
+
+    def spectral_ratios_of_centre(self, k, alpha_I) -> list[float]:
+        """spectral_ratios of centre k's sphere at the integrand frequencies."""
+        ab, sg, rv, a0, r0 = self.free()
+        s = self.sites(k)
+        P = torch.as_tensor(self.pos)
+        x = site_positions(P, self.cell, s, k)
+        _, aK, _, _ = scs_local(x, s, ab, sg, rv, self.p)
+        ns = s.ns
+        aI = torch.stack([alpha_I[int(a)] for a in s.atom[:ns]])
+        rb = torch.cat([torch.zeros(1, dtype=_DT), torch.sqrt((x[1:ns] * x[1:ns]).sum(-1))])
+        at = blend(aK, aI, rb, self.p)
+        T = t_lr(x[:ns], at[:, 0], a0[s.atom[:ns]], r0[s.atom[:ns]], self.p)
+        if self.p.omega_ref is not None:
+            at = lorentzian(at[:, 0], at[:, 1], self.p.omega_ref, self.omega)
+        return spectral_ratios(T, at, self.p)
+
+    def spectral_flags(self, centres=None) -> int:
+        """Number of (centre, integrand frequency) terms whose spectral ratio is >= 1."""
+        centres = list(range(self.n)) if centres is None else [int(c) for c in centres]
+        need = sorted({int(a) for k in centres for a in self.sites(k).atom[: self.sites(k).ns]})
+        with torch.no_grad():
+            aI = self.central_alpha(need)
+            return sum(sum(1 for r in self.spectral_ratios_of_centre(k, aI) if r >= 1.0) for k in centres)
 
     def energies(self, centres=None) -> np.ndarray:
         """Per-atom energies E_k in eV for the listed centres (default all)."""

@@ -921,3 +921,57 @@ def test_blend_switches_from_local_to_central_polarisability(monkeypatch):
     monkeypatch.setattr(lo, "f_scs", lambda r, r_scs: 1.0 - (3.0 * (r / r_scs) ** 2 - 2.0 * (r / r_scs) ** 3))
     bad = _blend_limits_hold(sysm, 0)
     assert "r -> 0 does not give alpha_K" in bad and "not continuous at r_SCS" in bad
+
+
+# ---------------------------------------------------------------------------------------
+# spectral proxy of the polarisation catastrophe (Sec. III.A: the series needs the eigenvalues
+# of G inside (-1, 1))
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [4, 6])
+def test_spectral_ratio_of_a_dimer_is_the_closed_form(order):
+    # identical dimer without screening: G = [[0, x T'], [x T', 0]] with T' r^3 of eigenvalues
+    # 2, -1, -1, so G has eigenvalues +-x tau and e_k sees each with weight 1/2:
+    # |G^M e_k|^2 = sum_tau (x tau)^(2M), ratio = x^2 (4^M + 2) / (4^(M-1) + 2), x = alpha f / r^3
+    table = np.array([[20.0, 300.0, 1.5]])
+    nu = np.array([1.0, 1.0])
+    M = order // 2
+    for r_ang in (1.5, 1.8, 2.4):
+        p = oracle.Params(r_scs=0.5, r_mbd1=10, r_mbd2=10, r_sphere=10, series_order=order, n_freq=6)
+        so = _dimer(r_ang, table, np.array([0, 0]), nu, p)
+        with torch.no_grad():
+            aI = so.central_alpha([0, 1])
+            got = so.spectral_ratios_of_centre(0, aI)
+        a0, w0, R = _lorentz(table, 0, 1.0)
+        r = r_ang / BOHR
+        f = 1 / (1 + math.exp(-6 * (r / (0.83 * 2 * R) - 1)))
+        om, _ = oracle.quadrature(6, 0.6)
+        for q, o in enumerate(om):
+            x = a0 / (1 + (o / w0) ** 2) * f / r ** 3
+            exact = x * x * (4.0 ** M + 2) / (4.0 ** (M - 1) + 2)
+            assert abs(got[q] / exact - 1) < 1e-12, (r_ang, q, got[q], exact)
+
+
+def test_spectral_ratio_is_a_weighted_mean_of_the_squared_eigenvalues():
+    # the ratio |G^M e_k|^2 / |G^(M-1) e_k|^2 weighs lambda^2 by lambda^(2M-2) |projection|^2:
+    # it never exceeds the largest lambda^2 (so a flag means an eigenvalue of magnitude >= 1)
+    # and it tends to it as M grows (eigenvalues from the library eigensolver)
+    rng = np.random.default_rng(3)
+    n = 7
+    A = rng.normal(size=(3 * n, 3 * n))
+    T = torch.tensor(A + A.T, dtype=DT)
+    for i in range(n):
+        T[3 * i:3 * i + 3, 3 * i:3 * i + 3] = 0.0
+    alpha = torch.tensor(rng.uniform(0.2, 1.0, size=(n, 3)), dtype=DT)
+    for order in (4, 6, 10):
+        rat = oracle.spectral_ratios(T, alpha, oracle.Params(series_order=order))
+        for q in range(1, 3):
+            d = torch.sqrt(alpha[:, q]).repeat_interleave(3)
+            lam = torch.linalg.eigvalsh(d[:, None] * T * d[None, :])
+            assert rat[q - 1] <= float((lam ** 2).max()) * (1 + 1e-12)
+    T = T / 6.0                      # keep G^200 finite
+    rat = oracle.spectral_ratios(T, alpha, oracle.Params(series_order=400))
+    for q in range(1, 3):
+        d = torch.sqrt(alpha[:, q]).repeat_interleave(3)
+        lam = torch.linalg.eigvalsh(d[:, None] * T * d[None, :])
+        assert abs(rat[q - 1] / float((lam ** 2).max()) - 1) < 1e-6
+    assert oracle.spectral_ratios(T, alpha, oracle.Params(series_order=3)) == []
