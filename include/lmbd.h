@@ -44,7 +44,7 @@ extern "C" {
 #define LMBD_OK            0
 #define LMBD_EINVAL        1  /* bad argument: sizes, NaN input, coincident atoms, bad cutoffs   */
 #define LMBD_ENOMEM        2  /* device allocation failed                                         */
-#define LMBD_NOT_SPD       3  /* a screening matrix B_K had a non-positive Cholesky pivot        */
+#define LMBD_NOT_SPD       3  /* a screening matrix B_K is singular: zero pivot in the LU fallback */
 #define LMBD_ECUDA         4  /* a CUDA runtime call failed                                       */
 #define LMBD_ECAPACITY     5  /* more sites around one atom than the kernels support             */
 #define LMBD_EUNSUPPORTED  6  /* option not supported (e.g. series order out of range)           */
@@ -52,6 +52,9 @@ extern "C" {
 #define LMBD_EMODEL        8  /* frequency or integrand model not applicable (see below)        */
 #define LMBD_ETIMEOUT      9  /* a bounded wait inside a tensor-core kernel ran out; the kernel
                                  drained its own copies, freed its tensor memory and returned   */
+#define LMBD_CATASTROPHE  10  /* diagnostic, only with lmbd_set_spectral_check(ctx, 1): the
+                                 spectral proxy of G reached 1 for some centre and frequency
+                                 (polarisation catastrophe, Sec. III.A); outputs were written  */
 
 #define LMBD_MAX_FREQ      64 /* maximum number of quadrature frequencies                        */
 #define LMBD_MAX_ORDER     10 /* maximum series order n_max                                      */
@@ -115,6 +118,13 @@ typedef struct {
   double ms_kernel[2];     /* with profiling, one wave: device time of the bucket launches of
                               [0] the SCS factor kernel, [1] the SCS adjoint kernel (all side
                               streams, fork to join; without the pair-list kernels)            */
+  long long scs_lu_systems; /* (centre, frequency) screening systems solved by the LU fallback:
+                              the FP32 Cholesky met a non-positive pivot (B_K indefinite) or
+                              its FP64 refinement did not converge                              */
+  long long spectral_flags; /* (centre, frequency) terms whose spectral proxy reached 1: with
+                              M = floor(n_max / 2) >= 2, |G^M e_k|^2 >= |G^(M-1) e_k|^2 (the
+                              k-block traces Tr[G^2M]_kk and Tr[G^(2M-2)]_kk); never set when
+                              n_max < 4                                                       */
 } lmbd_stats;
 
 /* Fill *out with the defaults r_scs = 5, r_mbd1 = r_mbd2 = r_sphere = 7,
@@ -240,6 +250,14 @@ int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes);
  *   LMBD_ECAPACITY in this mode.  Returns LMBD_EINVAL for m outside 0..LMBD_MAX_LANCZOS. */
 #define LMBD_MAX_LANCZOS 64
 int lmbd_set_series_fit(lmbd_ctx* ctx, int lanczos_steps);
+
+/* Spectral check (Sec. III.A: the truncated series and ln(1 - G) need the eigenvalues of
+ * G = sqrt(A) T_LR sqrt(A) inside (-1, 1); beyond, the polarisation catastrophe).  Every call
+ * counts the (centre, frequency) terms whose proxy |G^M e_k|^2 / |G^(M-1) e_k|^2 (M =
+ * floor(n_max / 2) >= 2) reaches 1 in lmbd_stats.spectral_flags.  fail = 0 (default): the call
+ * returns LMBD_OK regardless; fail = 1: it returns LMBD_CATASTROPHE when the count is not zero
+ * (outputs still written).  Returns LMBD_EINVAL for another value.                          */
+int lmbd_set_spectral_check(lmbd_ctx* ctx, int fail);
 
 /* Force model (Sec. III.D).
  * LMBD_FORCES_EXACT (default): forces = -d(sum_k w_k E_k)/dR, the exact gradient of the

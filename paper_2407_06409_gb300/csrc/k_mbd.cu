@@ -777,11 +777,19 @@ __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0)
   if (tid < p.n_freq) {
     int q = tid;
     double e = 0.0;
+    double tr_even[LMBD_MAX_ORDER_P1];
     for (int n = 2; n <= p.order; ++n) {
       double tr = red[n][3 * q] + red[n][3 * q + 1] + red[n][3 * q + 2];
       w.trbuf[((long long)c * (LMBD_MAX_ORDER_P1)) * 64 + n * 64 + q] = tr;
       e += series_c(w, p, c, q, n) * tr;
+      tr_even[n] = tr;
     }
+    // spectral proxy of the polarisation catastrophe (Sec. III.A: the series needs the
+    // eigenvalues of G inside (-1, 1)): with M = floor(n_max / 2) >= 2, the traces
+    // Tr[G^2M]_kk = |G^M e_k|^2 and Tr[G^(2M-2)]_kk = |G^(M-1) e_k|^2; their ratio tends to the
+    // largest lambda^2 that the centre's block sees, and a ratio >= 1 is flagged
+    const int M = p.order / 2;
+    if (M >= 2 && tr_even[2 * M] >= tr_even[2 * M - 2]) atomicAdd(w.status + 1, 1);
     ival[q] = e;
     epart[q] = e * p.cweight[q + 1];
   }

@@ -736,6 +736,61 @@ __global__ void __launch_bounds__(128) k_pair_radial(Work w, DevParams p) {
 }
 
 // ---------------------------------------------------------------------------------------
+// pieces shared by the Cholesky kernels and the LU fallback
+// ---------------------------------------------------------------------------------------
+// alpha_bar of every site at SCS frequency q, and 1/alpha_bar of the coupled sites
+__device__ __forceinline__ void scs2_load_abar(const Work& w, const DevParams& p, int c, int q, int n1, int n12, Scs2Smem& sm) {
+  const long long sbase = (long long)c * w.site_cap;
+  for (int s = threadIdx.x; s < n12; s += blockDim.x) {
+    int a = w.site_atom[sbase + s];
+    const double ab = w.abar[(long long)a * p.nqs + q];
+    sm.ab[s] = ab;
+    if (s < n1) sm.iab[s] = 1.0 / ab;
+  }
+}
+
+// right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j (Eq. local_pol; FP64, fixed order);
+// one thread per (coupled site i, column c): column c of T_SR,ij is F A0 e_c + F B0 r r_c.
+// rhs is N1 x 3 row-major (row 3 i + alpha).
+__device__ __forceinline__ void scs2_build_rhs(const Work& w, const DevParams& p, int n1, long long offp, long long rbase, int q,
+                               const double* ab, double* rhs) {
+  for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
+    const int i = e / 3, c = e % 3;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, ad = 0.0;
+    const int b = w.prow_k2[rbase + i], en = w.prow[rbase + i + 1];
+    for (int t = b; t < en; ++t) {
+      const long long pq = offp + t;
+      const int j = w.pr_ij[2 * pq + 1];
+      const double* g = w.pr_geo + 8 * pq;
+      const double* rad = w.pr_rad + 2 * (pq * p.nqs + q);
+      const double abj = ab[j];
+      ad += abj * rad[0];
+      const double wb = abj * rad[1] * g[c];
+      a0 += wb * g[0];
+      a1 += wb * g[1];
+      a2 += wb * g[2];
+    }
+    double* y = rhs + 9 * i;
+    y[c] = (c == 0 ? 1.0 : 0.0) - a0 - (c == 0 ? ad : 0.0);
+    y[3 + c] = (c == 1 ? 1.0 : 0.0) - a1 - (c == 1 ? ad : 0.0);
+    y[6 + c] = (c == 2 ? 1.0 : 0.0) - a2 - (c == 2 ? ad : 0.0);
+  }
+}
+
+// X (N1 x 3), alpha_K,i = Tr(X_i)/3 and alpha_I,c = alpha_K,0 of one (centre, frequency)
+__device__ __forceinline__ void scs2_store_solution(const Work& w, const DevParams& p, int c, int q, int n1, const double* x) {
+  const int N1 = 3 * n1;
+  const long long offk1 = w.off_k1[c];
+  double* X = w.xsol + offk1 * p.nqs * 9 + (long long)q * N1 * 3;
+  for (int e = threadIdx.x; e < N1 * 3; e += blockDim.x) X[e] = x[e];
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+    double a = (x[9 * i + 0] + x[9 * i + 4] + x[9 * i + 8]) / 3.0;
+    w.alphaK[(offk1 + i) * p.nqs + q] = a;
+    if (i == 0) w.alphaI[(long long)c * p.nqs + q] = a;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // forward: one block per (central atom, frequency)
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, const int* order, int c0, int max_n1,
@@ -753,12 +808,7 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
   const int np = w.prow[rbase + n1];
   __shared__ int bad, fail;
   if (tid == 0) { bad = 0; fail = 0; }
-  for (int s = tid; s < n12; s += blockDim.x) {
-    int a = w.site_atom[sbase + s];
-    const double ab = w.abar[(long long)a * p.nqs + q];
-    sm.ab[s] = ab;
-    if (s < n1) sm.iab[s] = 1.0 / ab;
-  }
+  scs2_load_abar(w, p, c, q, n1, n12, sm);
   const long long nA = (long long)N1 * (N1 + 1) / 2;
   for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = 0.f;
   __syncthreads();
@@ -815,78 +865,35 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
     for (int al = 0; al < 3; ++al) sm.A[packed_idx(3 * i + al, 3 * i + al)] = (float)sm.iab[i];
   __threadfence_block();
   __syncthreads();
-  // right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j (FP64, fixed order); one thread
-  // per (coupled site i, column c): column c of T_SR,ij is F A0 e_c + F B0 r r_c
-  for (int e = tid; e < 3 * n1; e += blockDim.x) {
-    const int i = e / 3, c = e % 3;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, ad = 0.0;
-    const int b = w.prow_k2[rbase + i], en = w.prow[rbase + i + 1];
-    for (int t = b; t < en; ++t) {
-      const long long pq = offp + t;
-      const int j = w.pr_ij[2 * pq + 1];
-      const double* g = w.pr_geo + 8 * pq;
-      const double* rad = w.pr_rad + 2 * (pq * p.nqs + q);
-      const double abj = sm.ab[j];
-      ad += abj * rad[0];
-      const double wb = abj * rad[1] * g[c];
-      a0 += wb * g[0];
-      a1 += wb * g[1];
-      a2 += wb * g[2];
-    }
-    double* y = sm.rhs + 9 * i;
-    y[c] = (c == 0 ? 1.0 : 0.0) - a0 - (c == 0 ? ad : 0.0);
-    y[3 + c] = (c == 1 ? 1.0 : 0.0) - a1 - (c == 1 ? ad : 0.0);
-    y[6 + c] = (c == 2 ? 1.0 : 0.0) - a2 - (c == 2 ? ad : 0.0);
-  }
+  scs2_build_rhs(w, p, n1, offp, rbase, q, sm.ab, sm.rhs);
   __syncthreads();
   chol32_packed(sm.A, N1, &bad, sm.sinv, sm.binv);
-  scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail);
-  // outputs: X, alpha_K, alpha_I and the FP32 factor for the adjoint
-  const long long offk1 = w.off_k1[c];
-  double* X = w.xsol + offk1 * p.nqs * 9 + (long long)q * N1 * 3;
-  for (int e = tid; e < N1 * 3; e += blockDim.x) X[e] = sm.x[e];
-  for (int i = tid; i < n1; i += blockDim.x) {
-    double a = (sm.x[9 * i + 0] + sm.x[9 * i + 4] + sm.x[9 * i + 8]) / 3.0;
-    w.alphaK[(offk1 + i) * p.nqs + q] = a;
-    if (i == 0) w.alphaI[(long long)c * p.nqs + q] = a;
+  // a non-positive pivot (B_K not positive definite: Sec. III.A, polarisation catastrophe) or
+  // a refinement that does not converge sends the system to the LU fallback (k_scs_lu_forward)
+  if (!bad) scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail);
+  __syncthreads();
+  if (bad || fail) {
+    if (tid == 0) {
+      w.fb_flag[(long long)c * p.nqs + q] = 1;
+      const int e = atomicAdd(w.fb, 1);
+      w.fb[1 + e] = c * p.nqs + q;
+    }
+    return;
   }
+  if (tid == 0) w.fb_flag[(long long)c * p.nqs + q] = 0;
+  // outputs: X, alpha_K, alpha_I and the FP32 factor for the adjoint
+  scs2_store_solution(w, p, c, q, n1, sm.x);
   float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
   for (long long e = tid; e < nA; e += blockDim.x) Lg[e] = sm.A[e];
-  if (tid == 0 && (bad || fail)) atomicOr(w.status, bad ? LMBD_FLAG_NOT_SPD : LMBD_FLAG_NOT_CONVERGED);
 }
 
-// ---------------------------------------------------------------------------------------
-// adjoint: one block per (central atom, frequency)
-// ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, const int* order, int c0, int max_n1,
-                                                  int max_n12) {
-  extern __shared__ unsigned char smem_raw[];
-  const int c = order ? order[c0 + blockIdx.x / p.nqs] : c0 + blockIdx.x / p.nqs;
-  const int q = blockIdx.x % p.nqs;
-  if (c >= w.n_atoms) return;
-  const Counts cn = w.counts[c];
-  const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
-  Scs2Smem sm = scs2_carve(smem_raw, max_n1, max_n12, true);
-  const int tid = threadIdx.x;
-  const long long sbase = (long long)c * w.site_cap;
-  const long long offp = w.off_p[c], offa = w.off_a[c], rbase = w.off_k1[c] + c, offk1 = w.off_k1[c];
-  const int np = w.prow[rbase + n1];
-  __shared__ int fail;
-  if (tid == 0) fail = 0;
-  for (int s = tid; s < n12; s += blockDim.x) {
-    int a = w.site_atom[sbase + s];
-    const double ab = w.abar[(long long)a * p.nqs + q];
-    sm.ab[s] = ab;
-    if (s < n1) sm.iab[s] = 1.0 / ab;
-  }
-  const long long nA = (long long)N1 * (N1 + 1) / 2;
-  const float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
-  for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = Lg[e];
-  for (int i = tid; i < N1; i += blockDim.x) sm.sinv[i] = 1.f / Lg[packed_idx(i, i)];
-  __syncthreads();
-  blockinv32(sm.A, N1, sm.sinv, sm.binv);
+// Adjoint right-hand side dL/dX of one (centre, frequency) into sm.rhs (dL/dX_i = delta/3 times
+// dL/dalpha_K,i, plus dL/dalpha_I,c on the centre's block), and the forward solution X into sm.xs.
+__device__ __forceinline__ void scs2_load_adjoint_rhs(const Work& w, const DevParams& p, int c, int q, int n1, Scs2Smem& sm) {
+  const int N1 = 3 * n1;
+  const long long offk1 = w.off_k1[c];
   const double* X = w.xsol + offk1 * p.nqs * 9 + (long long)q * N1 * 3;
-  for (int e = tid; e < N1 * 3; e += blockDim.x) {
+  for (int e = threadIdx.x; e < N1 * 3; e += blockDim.x) {
     sm.xs[e] = X[e];
     int row = e / 3, col = e % 3, i = row / 3, al = row % 3;
     double gval = 0.0;
@@ -897,14 +904,20 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
     }
     sm.rhs[e] = gval;
   }
-  __syncthreads();
-  scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail);    // sm.x <- lambda
-  __syncthreads();
-  // pair contractions: <M, dT_SR/dr> with M = -(lambda_i X_j^T + lambda_j X_i^T) (K1 pairs)
-  // or M = -alpha_bar_j lambda_i (K2 pairs), symmetrised; g = dL/dr_j = -dL/dr_i per pair,
-  // staged in global scratch (L2-resident) for the per-site gather.  The contraction runs in
-  // float-float arithmetic (ff.cuh, ~2^-46 relative) on the FP32 pipe: lambda and X are
-  // converted once per site, geometry and radial terms come converted from the tables.
+}
+
+// Adjoint contraction of one (centre, frequency) given lambda = B^-1 dL/dX in sm.x and the
+// forward solution X in sm.xs (both N1 x 3, FP64): per pair <M, dT_SR/dr> with
+// M = -(lambda_i X_j^T + lambda_j X_i^T) (K1 pairs) or M = -alpha_bar_j lambda_i (K2 pairs),
+// symmetrised; g = dL/dr_j = -dL/dr_i per pair, staged in global scratch (L2-resident), then
+// summed per site in a fixed order.  The contraction runs in float-float arithmetic (ff.cuh,
+// ~2^-46 relative) on the FP32 pipe: lambda and X are converted once per site, geometry and
+// radial terms come converted from the tables.  sm.rhs and sm.xs are overwritten.
+__device__ __forceinline__ void scs2_adjoint_contract(const Work& w, const DevParams& p, int c, int q, int n1, int n12, Scs2Smem& sm) {
+  const int N1 = 3 * n1, tid = threadIdx.x;
+  const long long sbase = (long long)c * w.site_cap;
+  const long long offp = w.off_p[c], offa = w.off_a[c], rbase = w.off_k1[c] + c;
+  const int np = w.prow[rbase + n1];
   ff* lf = reinterpret_cast<ff*>(sm.rhs);   // lambda, 9 n1 (rhs is no longer needed)
   ff* xf = reinterpret_cast<ff*>(sm.xs);    // X, 9 n1 (in place: one element per thread)
   for (int e = tid; e < N1 * 3; e += blockDim.x) {
@@ -1002,7 +1015,223 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
     sgq[(long long)s * p.nqs * 3 + 1] = gy;
     sgq[(long long)s * p.nqs * 3 + 2] = gz;
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint: one block per (central atom, frequency)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, const int* order, int c0, int max_n1,
+                                                  int max_n12) {
+  extern __shared__ unsigned char smem_raw[];
+  const int c = order ? order[c0 + blockIdx.x / p.nqs] : c0 + blockIdx.x / p.nqs;
+  const int q = blockIdx.x % p.nqs;
+  if (c >= w.n_atoms) return;
+  if (w.fb_flag[(long long)c * p.nqs + q]) return;   // solved by the LU fallback (k_scs_lu_adjoint)
+  const Counts cn = w.counts[c];
+  const int n1 = cn.n1, n12 = cn.n12, N1 = 3 * n1;
+  Scs2Smem sm = scs2_carve(smem_raw, max_n1, max_n12, true);
+  const int tid = threadIdx.x;
+  const long long offp = w.off_p[c], offa = w.off_a[c], rbase = w.off_k1[c] + c;
+  __shared__ int fail;
+  if (tid == 0) fail = 0;
+  scs2_load_abar(w, p, c, q, n1, n12, sm);
+  const long long nA = (long long)N1 * (N1 + 1) / 2;
+  const float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
+  for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = Lg[e];
+  for (int i = tid; i < N1; i += blockDim.x) sm.sinv[i] = 1.f / Lg[packed_idx(i, i)];
+  __syncthreads();
+  blockinv32(sm.A, N1, sm.sinv, sm.binv);
+  scs2_load_adjoint_rhs(w, p, c, q, n1, sm);
+  __syncthreads();
+  scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail);    // sm.x <- lambda
+  __syncthreads();
+  scs2_adjoint_contract(w, p, c, q, n1, n12, sm);
   if (tid == 0 && fail) atomicOr(w.status, LMBD_FLAG_NOT_CONVERGED);
+}
+
+// ---------------------------------------------------------------------------------------
+// LU fallback for screening matrices that are not positive definite (Sec. III.A: the
+// polarisation catastrophe makes B_K indefinite) or on which the FP32-factor refinement does
+// not converge.  Such systems are rare; each is solved in FP64 by Gaussian elimination with
+// partial pivoting (row interchanges), the same factorisation a library dense solve uses, on
+// the dense B_K assembled from the pair list into a per-block slot of global memory.  A pivot
+// that is exactly zero (B_K singular) sets LMBD_FLAG_NOT_SPD.
+// ---------------------------------------------------------------------------------------
+// dense B_K (N1 x N1 row-major, FP64) of one (centre, frequency): diag(1/alpha_bar) plus the
+// T_SR blocks of the K1 pairs (symmetric 3 x 3 blocks, F A0 delta + F B0 r r^T)
+__device__ void scs2_dense_b(const Work& w, const DevParams& p, int c, int q, int n1, const Scs2Smem& sm, double* A) {
+  const int N1 = 3 * n1;
+  const long long offp = w.off_p[c], rbase = w.off_k1[c] + c;
+  const int np = w.prow[rbase + n1];
+  for (long long e = threadIdx.x; e < (long long)N1 * N1; e += blockDim.x) A[e] = 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n1; i += blockDim.x)
+    for (int al = 0; al < 3; ++al) A[(long long)(3 * i + al) * N1 + 3 * i + al] = sm.iab[i];
+  for (int t = threadIdx.x; t < np; t += blockDim.x) {
+    const long long pq = offp + t;
+    const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
+    if (j >= n1) continue;
+    const double* g = w.pr_geo + 8 * pq;
+    const double* rad = w.pr_rad + 2 * (pq * p.nqs + q);
+    for (int al = 0; al < 3; ++al)
+      for (int be = 0; be < 3; ++be) {
+        const double v = rad[1] * g[al] * g[be] + (al == be ? rad[0] : 0.0);
+        A[(long long)(3 * i + al) * N1 + 3 * j + be] = v;
+        A[(long long)(3 * j + be) * N1 + 3 * i + al] = v;
+      }
+  }
+  __syncthreads();
+}
+
+// In-place LU with partial pivoting of the N1 x N1 matrix A (global memory), whole block:
+// P A = L U, L unit lower (below the diagonal), U upper; piv[k] = row swapped with row k.
+// Returns (uniformly) false if a pivot is zero or not finite.
+__device__ bool lu_factor_dense(double* A, int n, int* piv, double* redv, int* redi) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ int ok_s, p_s;
+  if (tid == 0) ok_s = 1;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // pivot: the largest |A[i][k]|, i >= k (ties to the lowest row)
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < n; i += blockDim.x) {
+      const double v = fabs(A[(long long)i * n + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = redv[0];
+      int ix = redi[0];
+      for (int u = 1; u < nw; ++u)
+        if (redv[u] > b || (redv[u] == b && redi[u] < ix)) { b = redv[u]; ix = redi[u]; }
+      p_s = ix;
+      piv[k] = ix;
+      if (!(b > 0.0) || !isfinite(b)) ok_s = 0;
+    }
+    __syncthreads();
+    if (!ok_s) return false;
+    const int pr = p_s;
+    if (pr != k)
+      for (int j = tid; j < n; j += blockDim.x) {
+        const double t = A[(long long)k * n + j];
+        A[(long long)k * n + j] = A[(long long)pr * n + j];
+        A[(long long)pr * n + j] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / A[(long long)k * n + k];
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) A[(long long)i * n + k] *= inv;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (long long e = tid; e < (long long)m * m; e += blockDim.x) {
+      const int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+      A[(long long)i * n + j] -= A[(long long)i * n + k] * A[(long long)k * n + j];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// b (n x 3 row-major, shared memory) <- A^-1 b with the factors of lu_factor_dense; warps 0..2
+// take one column each (row sums split over the lanes)
+__device__ void lu_solve3_dense(const double* A, int n, const int* piv, double* b) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp < 3) {
+    const int c = warp;
+    if (lane == 0)
+      for (int k = 0; k < n; ++k)
+        if (piv[k] != k) {
+          const double t = b[3 * k + c];
+          b[3 * k + c] = b[3 * piv[k] + c];
+          b[3 * piv[k] + c] = t;
+        }
+    __syncwarp();
+    for (int i = 0; i < n; ++i) {
+      double sacc = 0.0;
+      for (int j = lane; j < i; j += 32) sacc += A[(long long)i * n + j] * b[3 * j + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) b[3 * i + c] -= sacc;
+      __syncwarp();
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double sacc = 0.0;
+      for (int j = i + 1 + lane; j < n; j += 32) sacc += A[(long long)i * n + j] * b[3 * j + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) b[3 * i + c] = (b[3 * i + c] - sacc) / A[(long long)i * n + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// Forward LU fallback: persistent over the listed (centre, frequency) systems, one dense slot
+// of lu_slot doubles per block.
+__global__ void __launch_bounds__(256) k_scs_lu_forward(Work w, DevParams p, int max_n1, int max_n12, int tally) {
+  extern __shared__ unsigned char smem_raw[];
+  Scs2Smem sm = scs2_carve(smem_raw, max_n1, max_n12, true);
+  int* piv = reinterpret_cast<int*>(sm.A);
+  int* redi = reinterpret_cast<int*>(sm.y);
+  double* A = w.lu + (long long)blockIdx.x * w.lu_slot;
+  const int count = w.fb[0];
+  if (tally && blockIdx.x == 0 && threadIdx.x == 0 && count > 0) atomicAdd(w.status + 2, count);
+  for (int e = blockIdx.x; e < count; e += gridDim.x) {
+    const int id = w.fb[1 + e], c = id / p.nqs, q = id % p.nqs;
+    const int n1 = w.counts[c].n1, n12 = w.counts[c].n12, N1 = 3 * n1;
+    const long long offp = w.off_p[c], rbase = w.off_k1[c] + c;
+    scs2_load_abar(w, p, c, q, n1, n12, sm);
+    __syncthreads();
+    scs2_build_rhs(w, p, n1, offp, rbase, q, sm.ab, sm.x);
+    scs2_dense_b(w, p, c, q, n1, sm, A);
+    if (!lu_factor_dense(A, N1, piv, sm.red, redi)) {
+      if (threadIdx.x == 0) atomicOr(w.status, LMBD_FLAG_NOT_SPD);
+      __syncthreads();
+      continue;
+    }
+    lu_solve3_dense(A, N1, piv, sm.x);
+    scs2_store_solution(w, p, c, q, n1, sm.x);
+    __syncthreads();
+  }
+}
+
+// Adjoint LU fallback for the listed systems of centres [c0, c1): B_K is factored again (it is
+// symmetric, so lambda = B_K^-T dL/dX = B_K^-1 dL/dX), then the same pair contraction as the
+// Cholesky path.
+__global__ void __launch_bounds__(256) k_scs_lu_adjoint(Work w, DevParams p, int c0, int c1, int max_n1,
+                                                         int max_n12) {
+  extern __shared__ unsigned char smem_raw[];
+  Scs2Smem sm = scs2_carve(smem_raw, max_n1, max_n12, true);
+  int* piv = reinterpret_cast<int*>(sm.A);
+  int* redi = reinterpret_cast<int*>(sm.y);
+  double* A = w.lu + (long long)blockIdx.x * w.lu_slot;
+  const int count = w.fb[0];
+  for (int e = blockIdx.x; e < count; e += gridDim.x) {
+    const int id = w.fb[1 + e], c = id / p.nqs, q = id % p.nqs;
+    if (c < c0 || c >= c1) continue;
+    const int n1 = w.counts[c].n1, n12 = w.counts[c].n12, N1 = 3 * n1;
+    scs2_load_abar(w, p, c, q, n1, n12, sm);
+    __syncthreads();
+    scs2_dense_b(w, p, c, q, n1, sm, A);
+    if (!lu_factor_dense(A, N1, piv, sm.red, redi)) {
+      if (threadIdx.x == 0) atomicOr(w.status, LMBD_FLAG_NOT_SPD);
+      __syncthreads();
+      continue;
+    }
+    scs2_load_adjoint_rhs(w, p, c, q, n1, sm);
+    for (int u = threadIdx.x; u < 3 * N1; u += blockDim.x) sm.x[u] = sm.rhs[u];
+    __syncthreads();
+    lu_solve3_dense(A, N1, piv, sm.x);
+    scs2_adjoint_contract(w, p, c, q, n1, n12, sm);
+    __syncthreads();
+  }
 }
 
 // Sum of the per-frequency site gradients of the SCS adjoint, scattered to atoms.
@@ -1068,6 +1297,22 @@ void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, in
   size_t sm = scs2_smem_bytes(max_n1, max_n12, true);
   raise_smem_limit((const void*)k_scs_adjoint2, sm);
   k_scs_adjoint2<<<(c1 - c0) * p.nqs, 256, sm, s>>>(w, p, order, c0, max_n1, max_n12);
+}
+
+// LU fallback launches: a fixed grid of lu_blocks persistent blocks (one dense slot each);
+// with an empty list every block exits at once.
+void launch_scs_lu_forward(const Work& w, const DevParams& p, int lu_blocks, int max_n1, int max_n12, int tally,
+                           cudaStream_t s) {
+  size_t sm = scs2_smem_bytes(max_n1, max_n12, true);
+  raise_smem_limit((const void*)k_scs_lu_forward, sm);
+  k_scs_lu_forward<<<lu_blocks, 256, sm, s>>>(w, p, max_n1, max_n12, tally);
+}
+
+void launch_scs_lu_adjoint(const Work& w, const DevParams& p, int lu_blocks, int c0, int c1, int max_n1,
+                           int max_n12, cudaStream_t s) {
+  size_t sm = scs2_smem_bytes(max_n1, max_n12, true);
+  raise_smem_limit((const void*)k_scs_lu_adjoint, sm);
+  k_scs_lu_adjoint<<<lu_blocks, 256, sm, s>>>(w, p, c0, c1, max_n1, max_n12);
 }
 
 void launch_scs_site_reduce(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {

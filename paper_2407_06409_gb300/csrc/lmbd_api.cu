@@ -56,6 +56,7 @@ struct Ctx {
   int lanczos = 0;                 // polynomial-fit coefficients (lmbd_set_series_fit): steps
   int paper_forces = 0;            // force model (lmbd_set_force_model)
   int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
+  int spectral_fail = 0;           // lmbd_set_spectral_check: return LMBD_CATASTROPHE when flagged
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
   // around the bucket launches of the SCS factor (pass A) and SCS adjoint (pass C): their own
@@ -75,7 +76,7 @@ struct Ctx {
   DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
   DevBuf site_atom, site_x, counts, offs, totals, status, pcount;
   DevBuf alphaK, alphaI, energies, trbuf, wexp, alphaK_bar, alphaI_bar, gacc, rad_ab, rad_ff;
-  DevBuf order1_d, order3_d, fitw, cfit, lam, gl64;
+  DevBuf order1_d, order3_d, fitw, cfit, lam, gl64, fb, fb_flag, lu;
   DevBuf arena;
   std::vector<Counts> counts_h;
   std::vector<long long> offs_h;
@@ -86,7 +87,8 @@ struct Ctx {
     DevBuf* l[] = {&table_d, &pos_d, &species_d, &nu_d, &weights_d, &out_e_d, &out_f_d, &abar, &sig, &rvdw,
                    &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
-                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw, &cfit, &lam, &gl64};
+                   &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw, &cfit, &lam, &gl64,
+                   &fb, &fb_flag, &lu};
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
   size_t whole_bytes() const {
@@ -581,6 +583,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   TRY(ensure(c->alphaI, sizeof(double) * N * nq));
   TRY(ensure(c->energies, sizeof(double) * N));
   TRY(ensure(c->trbuf, sizeof(double) * (size_t)N * LMBD_MAX_ORDER_P1 * 64));
+  TRY(ensure(c->fb, sizeof(int) * (1 + (size_t)N * nq)));
+  TRY(ensure(c->fb_flag, sizeof(int) * (size_t)N * nq));
 
   // site capacity from the density (sites within r_list), grown on overflow
   {
@@ -632,6 +636,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   w.alphaI = (double*)c->alphaI.p;
   w.energies = (double*)c->energies.p;
   w.trbuf = (double*)c->trbuf.p;
+  w.fb = (int*)c->fb.p;
+  w.fb_flag = (int*)c->fb_flag.p;
 
   // species indices must be in range and inputs finite: checked here when the caller passed
   // host arrays, and by the free-atom kernel for device arrays (LMBD_FLAG_BAD_INPUT).
@@ -686,6 +692,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   // kernel shared-memory capacities (per-centre systems live in shared memory)
   if (max_n1 > 96 || max_ns > 1024 || max_n12 > 4096) return LMBD_ECAPACITY;
   if (scs2_adjoint_smem(max_n1, max_n12) > 227 * 1024) return LMBD_ECAPACITY;
+  // dense FP64 slots of the LU fallback, one per persistent block
+  const int lu_blocks = 32;
+  w.lu_slot = 9LL * max_n1 * max_n1;
+  TRY(ensure(c->lu, sizeof(double) * (size_t)lu_blocks * (size_t)w.lu_slot));
+  w.lu = (double*)c->lu.p;
   c->counts_h.resize(N);
   c->offs_h.resize((size_t)O_COUNT * (N + 1));
   CK(cudaMemcpyAsync(c->counts_h.data(), w.counts, sizeof(Counts) * N, cudaMemcpyDeviceToHost, s));
@@ -832,10 +843,12 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
 
   // stage-1 forward of one wave: pair lists, FP32 factorisation, refined solutions, alpha_K
   bool kmark_fwd = false;   // record kev[0], kev[1] around the factor buckets (pass A, profiling)
+  bool tally_lu = true;     // count LU-fallback systems in pass A only (pass C may recompute)
   auto stage1_forward = [&](int wv, const std::vector<int>& cuts, const std::vector<std::vector<Bucket>>& bk,
                             const int* order) -> int {
     const int c0 = cuts[wv], c1 = cuts[wv + 1];
     L.stage1(o, c0, c1, arena, &w);
+    CK(cudaMemsetAsync(w.fb, 0, sizeof(int), s));   // LU-fallback list of this wave
     launch_scs_fill(w, dp, c0, c1, max_n12, max_n1, s);
     ++phase_launch[LMBD_PHASE_SCS];
     if (per_atom) {
@@ -853,6 +866,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       if (kmark_fwd) cudaEventRecord(c->kev[1], s);
       phase_launch[LMBD_PHASE_SCS] += (int)bk[wv].size();
     }
+    launch_scs_lu_forward(w, dp, lu_blocks, max_n1, max_n12, tally_lu ? 1 : 0, s);
+    ++phase_launch[LMBD_PHASE_SCS];
     CK(cudaGetLastError());
     return LMBD_OK;
   };
@@ -981,6 +996,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   }
 
   // ---- pass C: SCS adjoint (needs dL/d alpha_I of every centre, complete after pass B) --------
+  tally_lu = false;
   if (forces) {
     mark(LMBD_PHASE_ADJ_SCS);
     for (int wv = 0; wv < nwC; ++wv) {
@@ -992,11 +1008,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       }
       L.scs_adjoint(o, c0, c1, arena + x_at, &w);
       if (per_atom) {
-        for (int cc = c0; cc < c1; ++cc) {
+        for (int cc = c0; cc < c1; ++cc)
           launch_scs_adjoint2(w, dp, nullptr, cc, cc + 1, c->counts_h[cc].n1, c->counts_h[cc].n12, s);
-          launch_scs_site_reduce(w, dp, cc, cc + 1, s);
-        }
-        phase_launch[LMBD_PHASE_ADJ_SCS] += 2 * (c1 - c0);
+        launch_scs_lu_adjoint(w, dp, lu_blocks, c0, c1, max_n1, max_n12, s);
+        for (int cc = c0; cc < c1; ++cc) launch_scs_site_reduce(w, dp, cc, cc + 1, s);
+        phase_launch[LMBD_PHASE_ADJ_SCS] += 2 * (c1 - c0) + 1;
       } else {
         if (prof) cudaEventRecord(c->kev[2], s);
         Fork fk(c, s, (int)bucketsC[wv].size());
@@ -1006,8 +1022,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         }
         fk.join();
         if (prof) cudaEventRecord(c->kev[3], s);
+        launch_scs_lu_adjoint(w, dp, lu_blocks, c0, c1, max_n1, max_n12, s);
         launch_scs_site_reduce(w, dp, c0, c1, s);
-        phase_launch[LMBD_PHASE_ADJ_SCS] += (int)bucketsC[wv].size() + 1;
+        phase_launch[LMBD_PHASE_ADJ_SCS] += (int)bucketsC[wv].size() + 2;
       }
       CK(cudaGetLastError());
     }
@@ -1036,7 +1053,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     if (!dev) CK(cudaMemcpyAsync(f_out, dst, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s));
   }
   mark(LMBD_NPHASE);
-  CK(cudaMemcpyAsync(c->status_h, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->status_h, w.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
 
@@ -1074,6 +1091,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       if (forces && cudaEventElapsedTime(&ms, c->kev[2], c->kev[3]) == cudaSuccess) S.ms_kernel[1] = ms;
       cudaGetLastError();
     }
+    S.scs_lu_systems = c->status_h[2];
+    S.spectral_flags = c->status_h[1];
     S.n_sites = c->totals_h[7];
     S.scs_pairs = c->totals_h[8];
     S.scs_adjacency = c->totals_h[9];
@@ -1088,6 +1107,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   if (*c->status_h & LMBD_FLAG_TIMEOUT) return LMBD_ETIMEOUT;
   if (*c->status_h & (LMBD_FLAG_NOT_SPD | LMBD_FLAG_NOT_CONVERGED)) return LMBD_NOT_SPD;
   if (*c->status_h & LMBD_FLAG_MODEL) return LMBD_EMODEL;
+  if (c->spectral_fail && c->status_h[1] > 0) return LMBD_CATASTROPHE;
   return LMBD_OK;
 }
 
@@ -1225,6 +1245,12 @@ int lmbd_set_profiling(lmbd_ctx* ctx, int on) {
       }
   }
   c.profiling = on ? 1 : 0;
+  return LMBD_OK;
+}
+
+int lmbd_set_spectral_check(lmbd_ctx* ctx, int fail) {
+  if (!ctx || (fail != 0 && fail != 1)) return LMBD_EINVAL;
+  ctx->c.spectral_fail = fail;
   return LMBD_OK;
 }
 
@@ -1389,13 +1415,14 @@ const char* lmbd_status_string(int status) {
     case LMBD_OK: return "ok";
     case LMBD_EINVAL: return "invalid argument";
     case LMBD_ENOMEM: return "device allocation failed";
-    case LMBD_NOT_SPD: return "screening matrix not positive definite";
+    case LMBD_NOT_SPD: return "screening matrix singular (zero pivot in the LU fallback)";
     case LMBD_ECUDA: return "CUDA runtime error";
     case LMBD_ECAPACITY: return "too many sites around one atom for the kernels";
     case LMBD_EUNSUPPORTED: return "unsupported option";
     case LMBD_ESCRATCH: return "problem exceeds the fixed scratch of the allocation-free entry point";
     case LMBD_EMODEL: return "Lorentzian frequency model not applicable: a polarisability rises between 0 and omega_ref";
     case LMBD_ETIMEOUT: return "a bounded device wait in a tensor-core kernel ran out";
+    case LMBD_CATASTROPHE: return "spectral proxy of G reached 1 for some centre and frequency (polarisation catastrophe); outputs were written";
     default: return "unknown status";
   }
 }

@@ -17,6 +17,8 @@
 #define LMBD_FLAG_MODEL 16          // Lorentzian model not applicable: alpha~(0) < alpha~(omega_ref),
                                     // or a fitted phi without decaying term
 #define LMBD_FLAG_TIMEOUT 32        // a bounded device wait (tensor-core pipeline) ran out
+// status[0]: the flags above; status[1]: (centre, frequency) terms whose spectral proxy reached
+// 1 (energy kernel); status[2]: SCS systems solved by the LU fallback (forward pass)
 #define LMBD_FLAG_BAD_INPUT 64      // a species index out of range, or a non-finite position or
                                     // non-positive Hirshfeld ratio, in device-resident inputs
 #define LMBD_FITW 32                // stride of the per-centre integrand weights dE/dI(omega_j)
@@ -128,6 +130,14 @@ struct Work {
   double* sgq;                 // N x site_cap x nq x 3: SCS-adjoint site gradients per frequency
   double* gstage;              // sum pairs x nq x 3: SCS-adjoint pair gradients (scratch)
   float* lfac;                 // packed FP32 Cholesky factors, off_b
+  // LU fallback of the SCS solves (systems whose FP32 Cholesky pivot is not positive or whose
+  // refinement does not converge): fb[0] = count, fb[1 + e] = c * nqs + q; fb_flag[c * nqs + q]
+  // = 1 for such a system (its FP32 factor is not used); lu: per-block dense slots of lu_slot
+  // doubles ((3 max n1)^2)
+  int* fb;
+  int* fb_flag;
+  double* lu;
+  long long lu_slot;
   // sliced tensor-core products (ozaki.cuh)
   long long* off_tq;           // sum Mpad Kpad (T digit plane sizes)
   long long* off_tr;           // sum Mpad (T rows)
@@ -268,6 +278,10 @@ void launch_scs_factor(const Work& w, const DevParams& p, const int* order, int 
 void launch_scs_adjoint2(const Work& w, const DevParams& p, const int* order, int c0, int c1, int max_n1,
                          int max_n12, cudaStream_t s);
 void launch_scs_site_reduce(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
+void launch_scs_lu_forward(const Work& w, const DevParams& p, int lu_blocks, int max_n1, int max_n12, int tally,
+                           cudaStream_t s);
+void launch_scs_lu_adjoint(const Work& w, const DevParams& p, int lu_blocks, int c0, int c1, int max_n1,
+                           int max_n12, cudaStream_t s);
 size_t scs2_forward_smem(int max_n1, int max_n12);
 size_t scs2_adjoint_smem(int max_n1, int max_n12);
 void launch_mbd_prepare_sized(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblmbd.so")
 
 LMBD_OK, LMBD_EINVAL, LMBD_ENOMEM, LMBD_NOT_SPD, LMBD_ECUDA, LMBD_ECAPACITY, LMBD_EUNSUPPORTED = range(7)
-LMBD_ESCRATCH, LMBD_EMODEL, LMBD_ETIMEOUT = 7, 8, 9
+LMBD_ESCRATCH, LMBD_EMODEL, LMBD_ETIMEOUT, LMBD_CATASTROPHE = 7, 8, 9, 10
 FREQ_QUADRATURE, FREQ_LORENTZIAN = 0, 1
 FORCES_EXACT, FORCES_PAPER = 0, 1
 LAUNCH_BATCHED, LAUNCH_PER_ATOM = 0, 1
@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
                 ("max_sites", ctypes.c_int), ("kernel_launches", ctypes.c_int), ("bytes_arena", ctypes.c_double),
                 ("waves_scs", ctypes.c_int), ("waves_mbd", ctypes.c_int), ("scs_recomputed", ctypes.c_int),
                 ("scs_pairs", ctypes.c_longlong), ("scs_adjacency", ctypes.c_longlong),
-                ("ms_kernel", ctypes.c_double * 2)]
+                ("ms_kernel", ctypes.c_double * 2), ("scs_lu_systems", ctypes.c_longlong),
+                ("spectral_flags", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -95,6 +96,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_integrand_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_series_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_force_model.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_spectral_check.argtypes = [_P, ctypes.c_int]
         L.lmbd_autotune.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]
         L.lmbd_release_workspace.argtypes = [_P]
         L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
@@ -105,7 +107,8 @@ def lib() -> ctypes.CDLL:
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_mma_path", "lmbd_set_wait_budget", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
-                  "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_autotune",
+                  "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_set_spectral_check",
+                  "lmbd_autotune",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
                   "lmbd_get_quadrature", "lmbd_get_stats", "lmbd_destroy"):
@@ -217,6 +220,10 @@ class LMBD:
         ln(1 - lambda) on the m-step Lanczos estimate of G's spectral interval (Sec. III.A)."""
         _check(lib().lmbd_set_series_fit(self._h, int(lanczos_steps)), "lmbd_set_series_fit")
 
+    def set_spectral_check(self, fail: bool) -> None:
+        """True: calls whose spectral proxy reached 1 return LMBD_CATASTROPHE (outputs written)."""
+        _check(lib().lmbd_set_spectral_check(self._h, 1 if fail else 0), "lmbd_set_spectral_check")
+
     def set_force_model(self, model: int) -> None:
         """FORCES_EXACT (gradient of the energies) or FORCES_PAPER (Sec. III.D approximations)."""
         _check(lib().lmbd_set_force_model(self._h, int(model)), "lmbd_set_force_model")
@@ -241,7 +248,7 @@ class LMBD:
         _check(lib().lmbd_set_profiling(self._h, 1 if on else 0), "lmbd_set_profiling")
 
     def energy_forces(self, positions, cell, species, hirshfeld, forces: bool = True, weights=None,
-                      stream=None, allow_not_spd: bool = False):
+                      stream=None, allow_not_spd: bool = False, allow_catastrophe: bool = False):
         """Per-atom energies (eV) and forces (eV/Angstrom) as torch tensors.
 
         Outputs live on the device of ``positions`` (CPU tensors / numpy -> CPU).
@@ -262,7 +269,8 @@ class LMBD:
             self._h, n, pp, cp, sp, hp, wp, ctypes.c_void_p(e.data_ptr()),
             ctypes.c_void_p(f.data_ptr()) if f is not None else None, st)
         self.last_status = status
-        if not (status == LMBD_OK or (allow_not_spd and status == LMBD_NOT_SPD)):
+        if not (status == LMBD_OK or (allow_not_spd and status == LMBD_NOT_SPD)
+                or (allow_catastrophe and status == LMBD_CATASTROPHE)):
             raise LmbdError(status, "lmbd_energy_forces")
         del k1, k2, k3, k4, k5
         return e, f

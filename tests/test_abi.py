@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(libpath):
     assert not missing, missing
     lib.lmbd_status_string.restype = ctypes.c_char_p
     assert lib.lmbd_status_string(0) == b"ok"
-    assert lib.lmbd_status_string(3) == b"screening matrix not positive definite"
+    assert lib.lmbd_status_string(3) == b"screening matrix singular (zero pivot in the LU fallback)"
 
 
 def test_binding_loads_and_rejects_bad_arguments(libpath):

@@ -234,23 +234,84 @@ def test_dimer_matches_oracle_and_coincident_atoms_rejected(lm):
     assert ex.value.status == lm.LMBD_EINVAL
 
 
-def test_non_positive_definite_screening_is_reported(lm):
-    # a tight collinear chain of strongly polarisable atoms: the oracle's B_K has a
-    # negative eigenvalue (polarisation catastrophe, Sec. III.A), so Cholesky must fail
-    table = np.array([[80.0, 30.0, 3.0]])
-    pos = np.zeros((6, 3))
-    pos[:, 2] = 1.5 * np.arange(6)
+def _indefinite_chain():
+    """A periodic chain of strongly polarisable atoms 1.4 Angstrom apart (jittered): at omega = 0
+    every atom's screening matrix B_K has a negative eigenvalue (polarisation catastrophe,
+    Sec. III.A), so the FP32 Cholesky meets a non-positive pivot, while every screened
+    polarisability stays positive and the energies are finite."""
+    n = 6
+    rng = np.random.default_rng(7)
+    pos = np.zeros((n, 3))
+    pos[:, 2] = 1.4 * np.arange(n)
+    pos[:, 0], pos[:, 1] = 1.0, 2.0
+    pos += rng.normal(scale=0.03, size=pos.shape)
+    cell = np.diag([20.0, 20.0, 1.4 * n])
+    table = np.array([[90.0, 30.0, 3.0]])
+    return inputs.Structure(pos, cell, np.zeros(n, dtype=np.int32), np.ones(n), table)
+
+
+def test_indefinite_screening_is_solved_by_the_lu_fallback(lm):
+    s = _indefinite_chain()
     p = lm.default_params(r_scs=4.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
-    so = oracle.System(pos, None, np.zeros(6, int), np.ones(6), table, _oracle_params(p, 4, 4))
+    so = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, _oracle_params(p, 4, 4))
     ab, sg, rv, _, _ = so.free()
-    st = so.sites(2)
-    x = oracle.site_positions(torch.as_tensor(pos), None, st, 2)
-    B = oracle.scs_local(x, st, ab, sg, rv, so.p)[2]
-    assert torch.linalg.eigvalsh(B[0]).min().item() < 0
-    model = lm.LMBD(table, p, 4, 4)
-    e, _ = model.energy_forces(pos, None, np.zeros(6, dtype=np.int32), np.ones(6), forces=False,
-                               allow_not_spd=True)
-    assert model.last_status == lm.LMBD_NOT_SPD
+    for k in range(s.n_atoms):
+        st = so.sites(k)
+        x = oracle.site_positions(torch.as_tensor(s.positions), s.cell, st, k)
+        B = oracle.scs_local(x, st, ab, sg, rv, so.p)[2]
+        assert torch.linalg.eigvalsh(B[0]).min().item() < 0          # indefinite at omega = 0
+        assert torch.linalg.eigvalsh(B[1:]).min().item() > 0         # definite elsewhere
+    e_ref, f_ref = so.energies_forces()
+    model, e, f = _run(lm, s, p, n_freq=4, order=4, forces=True)
+    assert model.stats()["scs_lu_systems"] == s.n_atoms              # one per atom, at omega = 0
+    _check_e(e, e_ref)
+    _check_f(f, f_ref)
+    a_ref = np.stack([v.numpy() for v in so.central_alpha(range(s.n_atoms)).values()])
+    a = model.central_polarizabilities(s.n_atoms).numpy()
+    assert np.allclose(a, a_ref, rtol=1e-12, atol=0)
+    # the same through the one-launch-per-atom form
+    m2 = lm.LMBD(s.table, p, 4, 4)
+    m2.set_launch_mode(lm.LAUNCH_PER_ATOM)
+    e2, f2 = m2.energy_forces(torch.tensor(s.positions, device="cuda"), torch.tensor(s.cell, device="cuda"),
+                              torch.tensor(s.species, device="cuda"), torch.tensor(s.hirshfeld, device="cuda"))
+    _check_e(e2.cpu().numpy(), e_ref)
+    _check_f(f2.cpu().numpy(), f_ref)
+
+
+def _strongly_coupled_cluster():
+    s = inputs.cluster(10, radius=3.0, min_sep=1.3, n_species=2, seed=2)
+    table = np.array([[30.0, 300.0, 1.6], [24.0, 250.0, 1.5]])
+    return inputs.Structure(s.positions, None, (s.species % 2).astype(np.int32), np.ones(10), table)
+
+
+def test_spectral_flags_match_the_oracle(lm):
+    # terms (centre, frequency) whose proxy |G^3 e_k|^2 / |G^2 e_k|^2 reaches 1 (Sec. III.A):
+    # an integer decided in FP64 on both sides, away from ties (every ratio differs from 1 by
+    # more than 5 %), so the counts agree exactly
+    s = _strongly_coupled_cluster()
+    p = lm.default_params(r_scs=2.5, r_mbd1=6.0, r_mbd2=6.0, r_sphere=6.0)
+    so = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table, _oracle_params(p, 6, 6))
+    with torch.no_grad():
+        aI = so.central_alpha(range(s.n_atoms))
+        ratios = np.array([so.spectral_ratios_of_centre(k, aI) for k in range(s.n_atoms)])
+    assert np.min(np.abs(ratios - 1)) > 0.05
+    n_ref = int((ratios >= 1).sum())
+    assert 0 < n_ref < ratios.size
+    model, e, _ = _run(lm, s, p, n_freq=6, order=6, forces=False)
+    assert model.stats()["spectral_flags"] == n_ref
+    _check_e(e, so.energies())
+    # with the check switched on the call reports it and still writes the energies
+    model.set_spectral_check(True)
+    e2, _ = model.energy_forces(torch.tensor(s.positions, device="cuda"), None,
+                                torch.tensor(s.species, device="cuda"), torch.tensor(s.hirshfeld, device="cuda"),
+                                forces=False, allow_catastrophe=True)
+    assert model.last_status == lm.LMBD_CATASTROPHE
+    assert np.array_equal(e2.cpu().numpy(), e)
+    # a benign structure raises no flag
+    c = inputs.cluster(24, seed=0)
+    pc = lm.default_params(r_scs=5.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
+    mc, _, _ = _run(lm, c, pc, forces=False)
+    assert mc.stats()["spectral_flags"] == 0 and mc.stats()["scs_lu_systems"] == 0
 
 
 def test_autograd_function(lm, box110):
