@@ -225,7 +225,8 @@ __global__ void k_sites(Work w, DevParams p, const Grid* __restrict__ gp, int c0
       }
   __syncthreads();
   int n = cnt;
-  if (n > cap) {
+  const bool overflow = n > cap;
+  if (overflow) {
     if (threadIdx.x == 0) atomicOr(w.status, LMBD_FLAG_CAPACITY);
     n = cap;
   }
@@ -275,8 +276,9 @@ __global__ void k_sites(Work w, DevParams p, const Grid* __restrict__ gp, int c0
   __syncthreads();
   if (threadIdx.x == 0) {
     w.counts[k] = Counts{c1, cs, c12, n};
-    // the central atom must be the unique site at distance zero
-    if (n < 1 || at[0] != k || key[0] != 0.0 || (n > 1 && key[1] == 0.0))
+    // the central atom must be the unique site at distance zero (a truncated list, reported
+    // as a capacity overflow, need not hold the centre)
+    if (!overflow && (n < 1 || at[0] != k || key[0] != 0.0 || (n > 1 && key[1] == 0.0)))
       atomicOr(w.status, LMBD_FLAG_COINCIDENT);
   }
 }

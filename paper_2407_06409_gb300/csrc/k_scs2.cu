@@ -511,7 +511,7 @@ struct Scs2Smem {
   double* rhs;    // N1 x 3 (FP64 right-hand side d or dL/dX)
   double* x;      // N1 x 3 (FP64 solution X or lambda)
   double* xs;     // N1 x 3 (adjoint: X of the forward solve)
-  double* ab;     // n12 (alpha_bar at this frequency)
+  ff* abf;        // n12 (alpha_bar at this frequency, float-float)
   double* iab;    // n1 (1 / alpha_bar of the coupled sites)
   double* red;    // 64
 };
@@ -538,68 +538,18 @@ __device__ inline Scs2Smem scs2_carve(unsigned char* base, int max_n1, int max_n
   double* d = (double*)(base + fl * sizeof(float));
   s.rhs = d;
   s.x = s.rhs + 3 * N1;
-  s.ab = s.x + 3 * N1;
-  s.iab = s.ab + max_n12;
+  s.abf = reinterpret_cast<ff*>(s.x + 3 * N1);      // one ff per site: 8 bytes, as a double
+  s.iab = reinterpret_cast<double*>(s.abf + max_n12);
   s.red = s.iab + max_n1;
   s.xs = adjoint ? s.red + 64 : nullptr;
   return s;
 }
 
-// y = (float)(rhs - B x) with B = diag(1/alpha_bar) + sum over the K1 pairs of T_SR.  One
-// thread per (coupled site i, right-hand side c) sums its adjacency row in a fixed order in
-// FP64, T_p x_j = F A0 x_j + F B0 r (r . x_j), then rounds the residual to FP32.
-__device__ void scs2_residual(const Work& w, const DevParams& p, int n1, long long offp, long long offa,
-                              long long rbase, int q, Scs2Smem& sm) {
-  for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
-    const int i = e / 3, c = e % 3;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    const int b = w.arow[rbase + i], en = w.arow[rbase + i + 1];
-    // four entries per step: all loads first (independent), then the arithmetic in order
-    for (int t = b; t < en; t += 4) {
-      int jj[4], pp[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool ok = t + u < en;
-        jj[u] = ok ? w.adj[2 * (offa + t + u)] : 0;
-        pp[u] = ok ? w.adj[2 * (offa + t + u) + 1] : -1;
-      }
-      double gx[4], gy[4], gz[4], fa[4], fb[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (pp[u] >= 0) {
-          const double* g = w.pr_geo + 8 * (offp + pp[u]);
-          const double* rad = w.pr_rad + 2 * ((offp + pp[u]) * p.nqs + q);
-          gx[u] = g[0]; gy[u] = g[1]; gz[u] = g[2]; fa[u] = rad[0]; fb[u] = rad[1];
-        } else {
-          gx[u] = gy[u] = gz[u] = fa[u] = fb[u] = 0.0;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const double* xj = sm.x + 9 * jj[u];
-        const double x0 = xj[c], x1 = xj[3 + c], x2 = xj[6 + c];
-        const double bu = fb[u] * (gx[u] * x0 + gy[u] * x1 + gz[u] * x2);
-        a0 += fa[u] * x0 + bu * gx[u];
-        a1 += fa[u] * x1 + bu * gy[u];
-        a2 += fa[u] * x2 + bu * gz[u];
-      }
-    }
-    const double ia = sm.iab[i];
-    const double r0 = sm.rhs[9 * i + c] - ia * sm.x[9 * i + c] - a0;
-    const double r1 = sm.rhs[9 * i + 3 + c] - ia * sm.x[9 * i + 3 + c] - a1;
-    const double r2 = sm.rhs[9 * i + 6 + c] - ia * sm.x[9 * i + 6 + c] - a2;
-    sm.rhs[9 * i + c] = r0;
-    sm.rhs[9 * i + 3 + c] = r1;
-    sm.rhs[9 * i + 6 + c] = r2;
-    sm.y[9 * i + c] = (float)r0;
-    sm.y[9 * i + 3 + c] = (float)r1;
-    sm.y[9 * i + 6 + c] = (float)r2;
-  }
-}
-
-// rhs <- rhs - B delta for the FP32 correction delta in y, in float-float arithmetic: the
-// residual of x + delta without forming B x again in FP64 (delta is ~1e-7 of x, so 2^-46
-// relative accuracy in B delta keeps the residual exact to FP64 rounding).
+// rhs <- rhs - B y for the FP32 vector y, in float-float arithmetic on the FP32 pipe (B from the
+// float-float tables: 1/alpha_bar on the diagonal, F A0 delta + F B0 r r^T per K1 pair).  Called
+// with the FP32 solution x0 = y it forms the residual d - B x0 (error ~2^-46 |B| |x0|, so the
+// refined solution carries a relative error ~cond(B) 2^-46); called with a correction delta
+// (~1e-7 of x) it updates the residual of x + delta to FP64 rounding.
 __device__ void scs2_residual_update(const Work& w, const DevParams& p, int n1, long long offp, long long offa,
                                      long long rbase, int q, Scs2Smem& sm) {
   for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
@@ -638,8 +588,11 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
   solve32_packed(sm.A, N1, sm.binv, sm.y, sm.z);
   for (int e = tid; e < 3 * N1; e += blockDim.x) sm.x[e] = (double)sm.y[e];
   __syncthreads();
-  // the residual d - B x once in FP64 (kept in rhs), then updated by -B delta per correction
-  scs2_residual(w, p, n1, offp, offa, rbase, q, sm);
+  // the residual d - B x0 of the FP32 solution x0 = y, in float-float arithmetic on the FP32
+  // pipe (kept in rhs), then updated by -B delta per correction the same way
+  scs2_residual_update(w, p, n1, offp, offa, rbase, q, sm);
+  __syncthreads();
+  for (int e = tid; e < 3 * N1; e += blockDim.x) sm.y[e] = (float)sm.rhs[e];
   __syncthreads();
   double prev = 0.0;
   int it = 0;
@@ -744,36 +697,92 @@ __device__ __forceinline__ void scs2_load_abar(const Work& w, const DevParams& p
   for (int s = threadIdx.x; s < n12; s += blockDim.x) {
     int a = w.site_atom[sbase + s];
     const double ab = w.abar[(long long)a * p.nqs + q];
-    sm.ab[s] = ab;
+    sm.abf[s] = ff_from_double(ab);
     if (s < n1) sm.iab[s] = 1.0 / ab;
   }
 }
 
-// right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j (Eq. local_pol; FP64, fixed order);
-// one thread per (coupled site i, column c): column c of T_SR,ij is F A0 e_c + F B0 r r_c.
-// rhs is N1 x 3 row-major (row 3 i + alpha).
-__device__ __forceinline__ void scs2_build_rhs(const Work& w, const DevParams& p, int n1, long long offp, long long rbase, int q,
-                               const double* ab, double* rhs) {
+// right-hand side d_i = 1 - sum_{j in K2} T_SR,ij alpha_bar_j (Eq. local_pol) in float-float
+// arithmetic on the FP32 pipe (fixed order, ~2^-46 relative), rounded to FP64; one thread per
+// (coupled site i, column c): column c of T_SR,ij is F A0 e_c + F B0 r r_c.  rhs is N1 x 3
+// row-major (row 3 i + alpha).  Needs the float-float radial terms of this frequency.
+__device__ __forceinline__ void scs2_build_rhs(const Work& w, const DevParams& p, int n1, long long offp,
+                                               long long rbase, int q, const ff* abf, double* rhs) {
   for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
     const int i = e / 3, c = e % 3;
+    ff a0 = ff_make(0.f, 0.f), a1 = a0, a2 = a0, ad = a0;
+    const int b = w.prow_k2[rbase + i], en = w.prow[rbase + i + 1];
+    for (int t = b; t < en; ++t) {
+      const long long pq = offp + t;
+      const int j = w.pr_ij[2 * pq + 1];
+      const float2* gf = w.pr_gff + 6 * pq;
+      const float2* rf = w.pr_rad_ff + 2 * (pq * p.nqs + q);
+      const ff rx = ff_make(gf[0].x, gf[0].y), ry = ff_make(gf[1].x, gf[1].y), rz = ff_make(gf[2].x, gf[2].y);
+      const ff rc = c == 0 ? rx : (c == 1 ? ry : rz);
+      const ff abj = abf[j];
+      ad = ff_fma(abj, ff_make(rf[0].x, rf[0].y), ad);
+      const ff wb = ff_mul(ff_mul(abj, ff_make(rf[1].x, rf[1].y)), rc);
+      a0 = ff_fma(wb, rx, a0);
+      a1 = ff_fma(wb, ry, a1);
+      a2 = ff_fma(wb, rz, a2);
+    }
+    if (c == 0) a0 = ff_add(a0, ad);
+    if (c == 1) a1 = ff_add(a1, ad);
+    if (c == 2) a2 = ff_add(a2, ad);
+    double* y = rhs + 9 * i;
+    y[c] = (c == 0 ? 1.0 : 0.0) - ff_to_double(a0);
+    y[3 + c] = (c == 1 ? 1.0 : 0.0) - ff_to_double(a1);
+    y[6 + c] = (c == 2 ? 1.0 : 0.0) - ff_to_double(a2);
+  }
+}
+
+// FP64 damped radial terms F A0, F B0 of pair pq at SCS frequency q (LU fallback): from the
+// atom-pair table, or evaluated when the pair has no table entry
+__device__ __forceinline__ void pair_rad64(const Work& w, const DevParams& p, int c, int q, long long pq, double& fa,
+                                           double& fb) {
+  const double* g = w.pr_geo + 8 * pq;
+  const int gi = w.pr_g[pq];
+  double A0, B0;
+  if (gi >= 0) {
+    const double* ra = w.rad_ab + 2 * ((long long)gi * p.nqs + q);
+    A0 = ra[0];
+    B0 = ra[1];
+  } else {
+    const long long sbase = (long long)c * w.site_cap;
+    const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
+    const double si = w.sig[(long long)w.site_atom[sbase + i] * p.nqs + q];
+    const double sj = w.sig[(long long)w.site_atom[sbase + j] * p.nqs + q];
+    double dA0, dB0;
+    tsr_radial_fast(g[3], g[6], si * si + sj * sj, A0, B0, dA0, dB0);
+  }
+  fa = g[4] * A0;
+  fb = g[4] * B0;
+}
+
+// the right-hand side of Eq. local_pol in FP64 (LU fallback), alpha_bar from global memory
+__device__ void scs2_build_rhs64(const Work& w, const DevParams& p, int c, int n1, int q, double* rhs) {
+  const long long offp = w.off_p[c], rbase = w.off_k1[c] + c, sbase = (long long)c * w.site_cap;
+  for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
+    const int i = e / 3, cc = e % 3;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, ad = 0.0;
     const int b = w.prow_k2[rbase + i], en = w.prow[rbase + i + 1];
     for (int t = b; t < en; ++t) {
       const long long pq = offp + t;
       const int j = w.pr_ij[2 * pq + 1];
       const double* g = w.pr_geo + 8 * pq;
-      const double* rad = w.pr_rad + 2 * (pq * p.nqs + q);
-      const double abj = ab[j];
-      ad += abj * rad[0];
-      const double wb = abj * rad[1] * g[c];
+      double fa, fb;
+      pair_rad64(w, p, c, q, pq, fa, fb);
+      const double abj = w.abar[(long long)w.site_atom[sbase + j] * p.nqs + q];
+      ad += abj * fa;
+      const double wb = abj * fb * g[cc];
       a0 += wb * g[0];
       a1 += wb * g[1];
       a2 += wb * g[2];
     }
     double* y = rhs + 9 * i;
-    y[c] = (c == 0 ? 1.0 : 0.0) - a0 - (c == 0 ? ad : 0.0);
-    y[3 + c] = (c == 1 ? 1.0 : 0.0) - a1 - (c == 1 ? ad : 0.0);
-    y[6 + c] = (c == 2 ? 1.0 : 0.0) - a2 - (c == 2 ? ad : 0.0);
+    y[cc] = (cc == 0 ? 1.0 : 0.0) - a0 - (cc == 0 ? ad : 0.0);
+    y[3 + cc] = (cc == 1 ? 1.0 : 0.0) - a1 - (cc == 1 ? ad : 0.0);
+    y[6 + cc] = (cc == 2 ? 1.0 : 0.0) - a2 - (cc == 2 ? ad : 0.0);
   }
 }
 
@@ -812,51 +821,36 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
   const long long nA = (long long)N1 * (N1 + 1) / 2;
   for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = 0.f;
   __syncthreads();
-  // damped radial terms F A0, F B0 of every pair at this frequency (FP64, from the atom-pair
-  // table), and the K1 blocks of B in FP32
+  // damped radial terms F A0, F B0 of every pair at this frequency in float-float (F times the
+  // atom-pair table entry, on the FP32 pipe), stored for the residuals and the adjoint, and the
+  // K1 blocks of B in FP32 (the factor needs FP32 values only)
   for (int t = tid; t < np; t += blockDim.x) {
     const long long pq = offp + t;
     const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
-    const double* g = w.pr_geo + 8 * pq;
     const int gi = w.pr_g[pq];
-    double A0, B0;
+    const float2* gf = w.pr_gff + 6 * pq;
+    ff fa, fb;
     if (gi >= 0) {
-      const double* ra = w.rad_ab + 2 * ((long long)gi * p.nqs + q);
-      A0 = ra[0];
-      B0 = ra[1];
-    } else {
-      double dA0, dB0;
-      const double si = w.sig[(long long)w.site_atom[sbase + i] * p.nqs + q];
-      const double sj = w.sig[(long long)w.site_atom[sbase + j] * p.nqs + q];
-      tsr_radial_fast(g[3], g[6], si * si + sj * sj, A0, B0, dA0, dB0);
+      const float2* ra = w.rad_ff + 4 * ((long long)gi * p.nqs + q);
+      const ff F = ff_make(gf[3].x, gf[3].y);
+      fa = ff_mul(F, ff_make(ra[0].x, ra[0].y));
+      fb = ff_mul(F, ff_make(ra[1].x, ra[1].y));
+    } else {   // no table entry (a distance that ties r_SCS to rounding): evaluate in FP64
+      double da, db;
+      pair_rad64(w, p, c, q, pq, da, db);
+      fa = ff_from_double(da);
+      fb = ff_from_double(db);
     }
-    double* rad = w.pr_rad + 2 * (pq * p.nqs + q);
-    rad[0] = g[4] * A0;
-    rad[1] = g[4] * B0;
-    {
-      float2* rf = w.pr_rad_ff + 2 * (pq * p.nqs + q);
-      ff fa, fb;
-      if (gi >= 0) {   // from the float-float tables, on the FP32 pipe
-        const float2* ra = w.rad_ff + 4 * ((long long)gi * p.nqs + q);
-        const float2 Fg = w.pr_gff[6 * pq + 3];
-        const ff F = ff_make(Fg.x, Fg.y);
-        fa = ff_mul(F, ff_make(ra[0].x, ra[0].y));
-        fb = ff_mul(F, ff_make(ra[1].x, ra[1].y));
-      } else {
-        fa = ff_from_double(rad[0]);
-        fb = ff_from_double(rad[1]);
-      }
-      rf[0] = make_float2(fa.hi, fa.lo);
-      rf[1] = make_float2(fb.hi, fb.lo);
-    }
+    float2* rf = w.pr_rad_ff + 2 * (pq * p.nqs + q);
+    rf[0] = make_float2(fa.hi, fa.lo);
+    rf[1] = make_float2(fb.hi, fb.lo);
     if (j < n1) {
-      const double a = g[4] * A0, b = g[4] * B0;
-      const double rr[3] = {g[0], g[1], g[2]};
+      const float rr[3] = {gf[0].x, gf[1].x, gf[2].x};
 #pragma unroll
       for (int al = 0; al < 3; ++al) {
         float* row = sm.A + packed_idx(3 * i + al, 3 * j);
 #pragma unroll
-        for (int be = 0; be < 3; ++be) row[be] = (float)(b * rr[al] * rr[be] + (al == be ? a : 0.0));
+        for (int be = 0; be < 3; ++be) row[be] = fb.hi * rr[al] * rr[be] + (al == be ? fa.hi : 0.f);
       }
     }
   }
@@ -865,7 +859,7 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
     for (int al = 0; al < 3; ++al) sm.A[packed_idx(3 * i + al, 3 * i + al)] = (float)sm.iab[i];
   __threadfence_block();
   __syncthreads();
-  scs2_build_rhs(w, p, n1, offp, rbase, q, sm.ab, sm.rhs);
+  scs2_build_rhs(w, p, n1, offp, rbase, q, sm.abf, sm.rhs);
   __syncthreads();
   chol32_packed(sm.A, N1, &bad, sm.sinv, sm.binv);
   // a non-positive pivot (B_K not positive definite: Sec. III.A, polarisation catastrophe) or
@@ -956,7 +950,7 @@ __device__ __forceinline__ void scs2_adjoint_contract(const Work& w, const DevPa
       M[4] = ff_scale(ff_add(Mf[0][2], Mf[2][0]), 0.5f);
       M[5] = ff_scale(ff_add(Mf[1][2], Mf[2][1]), 0.5f);
     } else {
-      const ff aj = ff_neg(ff_from_double(sm.ab[j]));
+      const ff aj = ff_neg(sm.abf[j]);
       M[0] = ff_mul(aj, li[0]); M[1] = ff_mul(aj, li[4]); M[2] = ff_mul(aj, li[8]);
       M[3] = ff_scale(ff_mul(aj, ff_add(li[1], li[3])), 0.5f);
       M[4] = ff_scale(ff_mul(aj, ff_add(li[2], li[6])), 0.5f);
@@ -1072,10 +1066,11 @@ __device__ void scs2_dense_b(const Work& w, const DevParams& p, int c, int q, in
     const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
     if (j >= n1) continue;
     const double* g = w.pr_geo + 8 * pq;
-    const double* rad = w.pr_rad + 2 * (pq * p.nqs + q);
+    double fa, fb;
+    pair_rad64(w, p, c, q, pq, fa, fb);
     for (int al = 0; al < 3; ++al)
       for (int be = 0; be < 3; ++be) {
-        const double v = rad[1] * g[al] * g[be] + (al == be ? rad[0] : 0.0);
+        const double v = fb * g[al] * g[be] + (al == be ? fa : 0.0);
         A[(long long)(3 * i + al) * N1 + 3 * j + be] = v;
         A[(long long)(3 * j + be) * N1 + 3 * i + al] = v;
       }
@@ -1189,7 +1184,7 @@ __global__ void __launch_bounds__(256) k_scs_lu_forward(Work w, DevParams p, int
     const long long offp = w.off_p[c], rbase = w.off_k1[c] + c;
     scs2_load_abar(w, p, c, q, n1, n12, sm);
     __syncthreads();
-    scs2_build_rhs(w, p, n1, offp, rbase, q, sm.ab, sm.x);
+    scs2_build_rhs64(w, p, c, n1, q, sm.x);
     scs2_dense_b(w, p, c, q, n1, sm, A);
     if (!lu_factor_dense(A, N1, piv, sm.red, redi)) {
       if (threadIdx.x == 0) atomicOr(w.status, LMBD_FLAG_NOT_SPD);

@@ -251,7 +251,6 @@ struct Layout {
     float* lfac = cv.take<float>(o.span(O_B, c0, c1), o.at(O_B, c0));
     int* pr_ij = cv.take<int>(2 * (np + 1), 2 * p0);
     double* pr_geo = cv.take<double>(8 * (np + 1), 8 * p0);
-    double* pr_rad = cv.take<double>(2LL * nqs * (np + 1), 2LL * nqs * p0);
     float2* pr_rad_ff = cv.take<float2>(2LL * nqs * (np + 1), 2LL * nqs * p0);
     int* pr_g = cv.take<int>(np + 1, p0);
     float2* pr_gff = cv.take<float2>(6 * (np + 1), 6 * p0);
@@ -266,7 +265,6 @@ struct Layout {
       w->lfac = lfac;
       w->pr_ij = pr_ij;
       w->pr_geo = pr_geo;
-      w->pr_rad = pr_rad;
       w->pr_rad_ff = pr_rad_ff;
       w->pr_g = pr_g;
       w->pr_gff = pr_gff;
@@ -1645,8 +1643,9 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   CK(cudaMemcpyAsync(tot, w.totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&flags, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (flags & (LMBD_FLAG_COINCIDENT | LMBD_FLAG_BAD_INPUT)) return LMBD_EINVAL;
+  if (flags & LMBD_FLAG_BAD_INPUT) return LMBD_EINVAL;
   if (flags & LMBD_FLAG_CAPACITY) return LMBD_ESCRATCH;
+  if (flags & LMBD_FLAG_COINCIDENT) return LMBD_EINVAL;
   const int max_n1 = (int)tot[4], max_n12 = (int)tot[6];
   if (max_n1 > LMBD_NOALLOC_MAX_K1 || max_n12 > site_cap) return LMBD_ESCRATCH;
   launch_scs_central_noalloc(w, dp, slots, slot_doubles, (int)nslots, max_n12, max_n1, s);

@@ -113,7 +113,6 @@ struct Work {
   int* pcount;                 // N x 2: pairs, adjacency entries
   int* pr_ij;                  // pairs x 2: owner row i (K1), partner j (K1 with j < i, or K2)
   double* pr_geo;              // pairs x 8: r = x_j - x_i (3), |r|, F, dF/dr, 1/|r|, unused
-  double* pr_rad;              // pairs x nq x 2: F A0, F B0 per frequency (written by the factor kernel)
   float2* pr_rad_ff;           // pairs x nq x 2: F A0, F B0 as float-float (residual updates)
   int* pr_g;                   // pairs: index of the pair in the atom-pair radial table, -1 = none
   // radial terms of T_SR per atom pair and frequency, independent of the central atom: entry

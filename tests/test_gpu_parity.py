@@ -369,3 +369,32 @@ def test_device_inputs_out_of_range_are_rejected(lm, cluster24):
     e, f = model.energy_forces(pos, None, sp, nu, forces=True)
     assert np.array_equal(e.cpu().numpy(), e_ref)
     assert np.abs(f.cpu().numpy() - f_ref).max() < 1e-12
+
+
+def test_site_capacity_grows_for_a_dense_clump(lm):
+    # the first site-list capacity comes from the mean density; a dense clump in a dilute
+    # periodic box overflows it, and the call must grow the lists and finish (a truncated
+    # list is a capacity overflow, not a coincident-atom error)
+    rng = np.random.default_rng(11)
+    clump = inputs.cluster(200, radius=6.0, min_sep=1.1, n_species=2, seed=11)
+    far = rng.uniform(12.0, 38.0, size=(40, 3))
+    pos = np.concatenate([clump.positions + 6.0, far])
+    keep = [0]
+    for i in range(1, len(pos)):
+        d = pos[keep] - pos[i]
+        d -= 40.0 * np.round(d / 40.0)
+        if np.min(np.sum(d * d, axis=1)) > 1.21:
+            keep.append(i)
+    pos = pos[keep]
+    n = len(pos)
+    s = inputs.Structure(pos, np.diag([40.0, 40.0, 40.0]), (np.arange(n) % 2).astype(np.int32),
+                         rng.uniform(0.6, 1.0, n), clump.table)
+    p = lm.default_params(r_scs=4.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
+    model, e, _ = _run(lm, s, p, n_freq=6, order=4, forces=False)
+    st = model.stats()
+    so = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, _oracle_params(p, 6, 4))
+    counts = model.site_counts(n)
+    assert st["max_sites"] >= counts[:, 3].max()
+    for k in (0, 1, 60, n - 1):
+        assert so.sites(k).n1 == counts[k, 0] and so.sites(k).ns == counts[k, 1]
+    _check_e(e[[0, 1, 60, n - 1]], so.energies([0, 1, 60, n - 1]))
