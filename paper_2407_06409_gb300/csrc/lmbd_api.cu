@@ -1501,16 +1501,6 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
     for (int i = 0; i < 3 * N; ++i)
       if (!std::isfinite(positions[i])) return LMBD_EINVAL;
 
-  // A capturing stream allows none of the synchronous copies and stream synchronisations
-  // below (the sizes are read back to the host before the solve); refuse it before
-  // touching the stream, so that the caller's capture stays valid.
-  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cap_status) != cudaSuccess) {
-    cudaGetLastError();
-    return LMBD_EUNSUPPORTED;
-  }
-  if (cap_status != cudaStreamCaptureStatusNone) return LMBD_EUNSUPPORTED;
-
   void* base = nullptr;
   size_t cap = 0;
   if (noalloc_scratch(&base, &cap) != 0) return LMBD_ECUDA;
@@ -1667,6 +1657,15 @@ extern "C" int lmbd_central_polarizabilities_noalloc(const lmbd_species* species
   if (!species_params || !params || n_species <= 0 || n_species > 64 || n_freq < 1 || n_freq > LMBD_MAX_FREQ ||
       n_atoms < 0)
     return LMBD_EINVAL;
+  // A capturing stream allows none of the synchronous copies and stream synchronisations of
+  // this call (the sizes are read back to the host before the solve); refuse it before any
+  // other CUDA call, so that the caller's capture stays valid.
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap_status) != cudaSuccess) {
+    cudaGetLastError();
+    return LMBD_EUNSUPPORTED;
+  }
+  if (cap_status != cudaStreamCaptureStatusNone) return LMBD_EUNSUPPORTED;
   if (n_atoms > LMBD_NOALLOC_MAX_ATOMS) return LMBD_ESCRATCH;
   if (n_atoms == 0) return LMBD_OK;
   if (!positions || !species || !hirshfeld || !alpha_central) return LMBD_EINVAL;

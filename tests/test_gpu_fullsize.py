@@ -1,9 +1,11 @@
 """Parity at the benchmark sizes, in the launch configuration bench.py times.
 
 * 4096-atom periodic box (0.1 atoms/A^3, r_SCS 5 A, sphere 7 A, 12 frequencies, n_max 6),
-  batched launch, sliced tensor-core products: per-atom energies of sampled atoms against the
-  oracle, and the full gradient of one sampled local energy E_k (forces with one-hot weights)
-  against the oracle's autograd gradient.
+  autotuned SCS buckets, batched launch, sliced tensor-core products: per-atom energies of
+  sampled centres against the oracle (the extremes of |K1| and of the sphere, one centre per
+  distinct |K1|, the smallest ragged tensor-core tile tails, random ones), and the full gradients
+  of four single local energies E_k (forces with one-hot weights) against the oracle's autograd
+  gradients (the four oracle gradients in a spawn process pool, oracle_pool).
 * 512-atom box with 0.05 A jitter: adjoint forces against central finite differences of the
   GPU energies (h = 1e-4 A, FP64 products so that rounding noise stays far below 1e-8 eV/A),
   sliced against FP64 products, and weighted forces against the oracle.
@@ -13,6 +15,7 @@ import pytest
 import torch
 
 import oracle
+import oracle_pool
 from paper_2407_06409_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -45,36 +48,86 @@ def box4096():
     return inputs.box(4096, seed=0)
 
 
-def test_box4096_sampled_energies(lm, box4096):
+@pytest.fixture(scope="module")
+def box4096_run(lm, box4096):
+    """The bench configuration: autotuned SCS buckets, batched launch, tcgen05 sliced products."""
     s = box4096
     p = lm.default_params()
     model = lm.LMBD(s.table, p, 12, 6)
+    width = model.autotune(*_dev(s))
     e, f = model.energy_forces(*_dev(s), forces=True)
-    e = e.cpu().numpy()
-    assert np.all(np.isfinite(e)) and np.all(np.isfinite(f.cpu().numpy()))
-    so = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, _op(p))
-    sample = [0, 1777, 4095]
-    ref = so.energies(sample)
-    rel = np.abs(e[sample] - ref) / np.abs(ref)
-    assert np.all(rel < E_RTOL), rel
-    # translation invariance of the total force
-    assert np.abs(f.cpu().numpy().sum(0)).max() < 1e-9
+    counts = model.site_counts(s.n_atoms)
+    return model, width, e.cpu().numpy(), f.cpu().numpy(), counts
 
 
-def test_box4096_gradient_of_one_local_energy(lm, box4096):
+def _sample_centres(s, counts, rng, radius=6.0):
+    """Centres that reach the kernels' edge cases: the largest and smallest |K1| (SCS shared
+    memory and bucket limits) and sphere (the last, ragged 128-row tcgen05 tile), and, among the
+    centres within `radius` of the largest-|K1| centre (so that their spheres share most of the
+    central polarisabilities the oracle must evaluate): one centre per distinct |K1| (bucket
+    edges of any width), the smallest ragged tails of the 128-row tiles (3 n_s mod 128) and
+    random ones."""
+    n1, ns = counts[:, 0], counts[:, 1]
+    tail = (3 * ns) % 128
+    tail[tail == 0] = 128
+    k0 = int(np.argmax(n1))
+    d = s.positions - s.positions[k0]
+    box = np.diag(s.cell)
+    d -= box * np.round(d / box)
+    near = np.flatnonzero(np.sqrt((d * d).sum(1)) < radius)
+    pick = [k0, int(np.argmax(ns)), int(np.argmin(n1)), int(np.argmin(ns))]
+    for v in np.unique(n1[near]):
+        pick.append(int(near[np.flatnonzero(n1[near] == v)[0]]))
+    pick += [int(i) for i in near[np.argsort(tail[near], kind="stable")[:4]]]
+    pick += [int(i) for i in rng.choice(near, 6, replace=False)]
+    out = []
+    for c in pick:
+        if c not in out:
+            out.append(c)
+    return out
+
+
+def test_box4096_sampled_energies(lm, box4096, box4096_run):
     s = box4096
     p = lm.default_params()
-    k = 2048
-    w = np.zeros(s.n_atoms)
-    w[k] = 1.0
-    model = lm.LMBD(s.table, p, 12, 6)
-    _, f = model.energy_forces(*_dev(s), forces=True, weights=torch.tensor(w, device="cuda"))
-    f = f.cpu().numpy()
+    model, width, e, f, counts = box4096_run
+    assert np.all(np.isfinite(e)) and np.all(np.isfinite(f))
+    centres = _sample_centres(s, counts, np.random.default_rng(5))
+    assert len(centres) >= 32, len(centres)
     so = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, _op(p))
-    _, f_ref = so.energies_forces(centres=[k], weights=[1.0])
-    assert np.abs(f - f_ref).max() < F_ATOL
-    # -dE_k/dR is local: atoms beyond sphere + 2 r_SCS (17 A) feel nothing
-    assert np.count_nonzero(np.abs(f).max(1) > 0) < s.n_atoms
+    # the oracle's own site enumeration agrees with the device lists for every sampled centre
+    for c in centres:
+        st = so.sites(c)
+        assert (st.n1, st.ns, st.n12) == tuple(int(v) for v in counts[c, :3])
+    ref = so.energies(centres)
+    rel = np.abs(e[centres] - ref) / np.abs(ref)
+    assert np.all(rel < E_RTOL), (rel.max(), centres[int(np.argmax(rel))])
+    # translation invariance of the total force
+    assert np.abs(f.sum(0)).max() < 1e-9
+
+
+def test_box4096_gradients_of_extreme_local_energies(lm, box4096, box4096_run):
+    # one-hot weights: the full gradient of single local energies E_k, for the centres with the
+    # largest |K1|, the largest sphere, the smallest ragged tile tail and a middle one
+    s = box4096
+    p = lm.default_params()
+    model, width, _, _, counts = box4096_run
+    n1, ns = counts[:, 0], counts[:, 1]
+    tail = (3 * ns) % 128
+    tail[tail == 0] = 128
+    centres = []
+    for c in (int(np.argmax(n1)), int(np.argmax(ns)), int(np.argmin(tail)), 2048):
+        if c not in centres:
+            centres.append(c)
+    refs = oracle_pool.gradients(s, _op(p), centres)
+    for k, f_ref in zip(centres, refs):
+        w = np.zeros(s.n_atoms)
+        w[k] = 1.0
+        _, f = model.energy_forces(*_dev(s), forces=True, weights=torch.tensor(w, device="cuda"))
+        f = f.cpu().numpy()
+        assert np.abs(f - f_ref).max() < F_ATOL, k
+        # -dE_k/dR is local: atoms beyond sphere + 2 r_SCS (17 A) feel nothing
+        assert np.count_nonzero(np.abs(f).max(1) > 0) < s.n_atoms
 
 
 @pytest.fixture(scope="module")

@@ -109,10 +109,17 @@ def test_noalloc_refuses_a_capturing_stream(lm):
     p = lm.default_params(r_scs=5.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
     out = torch.zeros((24, 13), dtype=torch.float64, device="cuda")
     marker = torch.zeros(4, dtype=torch.float64, device="cuda")
+    sp = (lm.Species * len(s.table))(*[lm.Species(*row) for row in s.table])
+    pos = torch.tensor(s.positions, device="cuda")
+    spec = torch.tensor(s.species, dtype=torch.int32, device="cuda")
+    nu = torch.tensor(s.hirshfeld, device="cuda")
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        st = _noalloc(lm, s, p, 12, out)
+        # inputs were made before the capture: nothing but the call itself is captured here
+        st = lm.lib().lmbd_central_polarizabilities_noalloc(
+            sp, len(s.table), ctypes.byref(p), 12, s.n_atoms, pos.data_ptr(), None, spec.data_ptr(),
+            nu.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
         marker.fill_(1.0)
     assert st == lm.LMBD_EUNSUPPORTED
     g.replay()
