@@ -251,6 +251,23 @@ int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes);
 #define LMBD_MAX_LANCZOS 64
 int lmbd_set_series_fit(lmbd_ctx* ctx, int lanczos_steps);
 
+/* Log mode (Sec. III.A, Eq. series-expansion: the n_max -> infinity limit of the series, the
+ * k-block trace of ln(1 - G) that the truncated series and the polynomial fit approximate).
+ * lanczos_steps = 0 (default): the truncated series.  lanczos_steps = m (1..LMBD_MAX_LANCZOS):
+ * for every central atom, frequency of the integrand and direction alpha of the centre's
+ * three rows, m steps of the Lanczos recurrence on G = D T_LR D (FP64, no reorthogonalisation)
+ * from the unit vector e_alpha give a tridiagonal J; its eigenvalues theta_i and the first
+ * components z_i of its eigenvectors (implicit QL) form the Gauss rule
+ * e_alpha^T ln(1 - G) e_alpha ~ sum_i z_i^2 ln(1 - theta_i), exact once the Krylov space is
+ * exhausted (the recurrence stops when beta falls below 1e-13 of the largest coefficient) and
+ * converging geometrically in m otherwise; the three directions sum to [ln(1 - G)]_kk, which
+ * replaces the series in the integrand (quadrature or fitted integrand, either frequency
+ * model).  Energies only: a call with forces returns LMBD_EUNSUPPORTED; combined with
+ * lmbd_set_series_fit it returns LMBD_EINVAL; a sphere beyond 341 sites returns
+ * LMBD_ECAPACITY.  An eigenvalue theta >= 1 (polarisation catastrophe) gives a NaN energy.
+ * Returns LMBD_EINVAL for m outside 0..LMBD_MAX_LANCZOS.                                    */
+int lmbd_set_log_mode(lmbd_ctx* ctx, int lanczos_steps);
+
 /* Spectral check (Sec. III.A: the truncated series and ln(1 - G) need the eigenvalues of
  * G = sqrt(A) T_LR sqrt(A) inside (-1, 1); beyond, the polarisation catastrophe).  Every call
  * counts the (centre, frequency) terms whose proxy |G^M e_k|^2 / |G^(M-1) e_k|^2 (M =

@@ -280,7 +280,73 @@ __device__ double lz_eig(const double* a, const double* b, int m, int which) {
   return 0.5 * (lo + hi);
 }
 
-__global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int c0, int q0, int qc, int L3) {
+// Eigenvalues and first eigenvector components of the symmetric tridiagonal matrix (a, b) of
+// order m, in place: on return a[i] = theta_i and z[i] = first component of eigenvector i (z
+// enters as e_1).  Implicit QL iteration with Wilkinson-type shifts (the tridiagonal QL
+// algorithm of Bowdler, Martin, Reinsch and Wilkinson, 1968); only the first row of the
+// eigenvector matrix is carried along, as in the Golub-Welsch construction of Gauss rules.
+// b[m - 1] is used as scratch.  Returns false if an eigenvalue took more than 60 sweeps.
+__device__ bool tridiag_ql_first_row(double* a, double* b, double* z, int m) {
+  for (int i = 0; i < m; ++i) z[i] = i == 0 ? 1.0 : 0.0;
+  if (m <= 1) return true;
+  b[m - 1] = 0.0;
+  for (int l = 0; l < m; ++l) {
+    int iter = 0;
+    while (true) {
+      int mm = l;
+      for (; mm < m - 1; ++mm) {
+        const double dd = fabs(a[mm]) + fabs(a[mm + 1]);
+        if (fabs(b[mm]) <= 1e-17 * dd) break;
+      }
+      if (mm == l) break;
+      if (++iter > 60) return false;
+      // shift from the 2 x 2 block at the top of the unreduced part
+      double g = (a[l + 1] - a[l]) / (2.0 * b[l]);
+      double r = hypot(g, 1.0);
+      g = a[mm] - a[l] + b[l] / (g + (g >= 0.0 ? r : -r));
+      double sn = 1.0, cs = 1.0, pp = 0.0;
+      int i = mm - 1;
+      bool early = false;
+      for (; i >= l; --i) {
+        const double f = sn * b[i], bb = cs * b[i];
+        r = hypot(f, g);
+        b[i + 1] = r;
+        if (r == 0.0) {   // the rotation splits the matrix: deflate and restart this l
+          a[i + 1] -= pp;
+          b[mm] = 0.0;
+          early = true;
+          break;
+        }
+        sn = f / r;
+        cs = g / r;
+        g = a[i + 1] - pp;
+        r = (a[i] - g) * sn + 2.0 * cs * bb;
+        pp = sn * r;
+        a[i + 1] = g + pp;
+        g = cs * r - bb;
+        const double zt = z[i + 1];
+        z[i + 1] = sn * z[i] + cs * zt;
+        z[i] = cs * z[i] - sn * zt;
+      }
+      if (early) continue;
+      a[l] -= pp;
+      b[l] = g;
+      b[mm] = 0.0;
+    }
+  }
+  return true;
+}
+
+// Lanczos recurrences on G(omega) = D T_LR D for every frequency of this pass (frequencies
+// q0 ..), nd start vectors per frequency (vector v <-> frequency q0 + v / nd, direction v % nd):
+//  * nd = 1 (polynomial-fit coefficients, Sec. III.A): SplitMix64 start vector, the extreme
+//    Ritz values go to w.lam;
+//  * nd = 3 (log mode): start vectors e_alpha, the centre's three rows; the Gauss rule of the
+//    tridiagonal matrix J (Ritz values theta_i, squared first components z_i^2) gives
+//    e_alpha^T ln(1 - G) e_alpha ~ sum_i z_i^2 ln(1 - theta_i) (exact once the Krylov space is
+//    exhausted, b = 0), and the three directions sum to the k-block trace of ln(1 - G)
+//    (Eq. series-expansion, the n_max -> infinity limit), stored per frequency in trbuf row 0.
+__global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int c0, int q0, int qc, int L3, int nd) {
   extern __shared__ double lzs[];
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
@@ -296,26 +362,30 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int
   const int tid = threadIdx.x;
   const double* T = w.tlr + w.off_t[c];
   const long long offs = w.off_s[c];
-  const int m = min(p.lanczos, N);
-  // start vector u / |u| for every frequency
+  const bool logm = nd == 3;
+  const int m = min(logm ? p.logmode : p.lanczos, N);
+  // start vectors: u / |u| for every frequency, or e_alpha
   double part[LZ_QC];
   double tot[LZ_QC];
   for (int q = 0; q < LZ_QC; ++q) part[q] = 0.0;
-  for (int r = 0; r < LZ_RPT; ++r) {
-    const int i = tid + r * LZ_THREADS;
-    if (i < N) {
-      const double u = splitmix_unit((unsigned long long)i);
-      part[0] += u * u;
+  double inv = 1.0;
+  if (!logm) {
+    for (int r = 0; r < LZ_RPT; ++r) {
+      const int i = tid + r * LZ_THREADS;
+      if (i < N) {
+        const double u = splitmix_unit((unsigned long long)i);
+        part[0] += u * u;
+      }
     }
+    lz_block_sum(part, 1, red, tot);
+    inv = 1.0 / sqrt(tot[0]);
   }
-  lz_block_sum(part, 1, red, tot);
-  const double inv = 1.0 / sqrt(tot[0]);
   for (int r = 0; r < LZ_RPT; ++r) {
     const int i = tid + r * LZ_THREADS;
     if (i < N) {
-      const double u = splitmix_unit((unsigned long long)i) * inv;
+      const double u = logm ? 0.0 : splitmix_unit((unsigned long long)i) * inv;
       for (int q = 0; q < qc; ++q) {
-        V[i * qc + q] = u;
+        V[i * qc + q] = logm ? (i == q % 3 ? 1.0 : 0.0) : u;
         Vp[i * qc + q] = 0.0;
       }
     }
@@ -329,7 +399,7 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int
     // X = D V
     for (int e = tid; e < N * qc; e += LZ_THREADS) {
       const int i = e / qc, q = e % qc;
-      X[e] = w.dsq[(offs + i / 3) * p.nq + q0 + q + 1] * V[e];
+      X[e] = w.dsq[(offs + i / 3) * p.nq + q0 + q / nd + 1] * V[e];
     }
     __syncthreads();
     // Y = D (T X): T symmetric, so thread i reads column i of row k (coalesced)
@@ -361,7 +431,7 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int
 #pragma unroll
         for (int q = 0; q < LZ_QC; ++q)
           if (q < qc) {
-            y[r][q] *= w.dsq[(offs + i / 3) * p.nq + q0 + q + 1];
+            y[r][q] *= w.dsq[(offs + i / 3) * p.nq + q0 + q / nd + 1];
             part[q] += V[i * qc + q] * y[r][q];
           }
       }
@@ -389,7 +459,13 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int
     if (tid < qc && mq[tid] == j) {           // frequency still running: record step j
       al[tid * LMBD_MAX_LANCZOS + j] = alpha[tid];
       mq[tid] = j + 1;
-      if (j < m - 1 && beta[tid] != 0.0) {
+      // log mode: a beta below 1e-13 of the largest recurrence coefficient so far means the
+      // Krylov space is exhausted to rounding (the Gauss rule is then exact)
+      double scale = 0.0;
+      if (logm)
+        for (int u = 0; u <= j; ++u)
+          scale = fmax(scale, fabs(al[tid * LMBD_MAX_LANCZOS + u]) + (u < j ? be[tid * LMBD_MAX_LANCZOS + u] : 0.0));
+      if (j < m - 1 && beta[tid] != 0.0 && !(logm && beta[tid] <= 1e-13 * scale)) {
         be[tid * LMBD_MAX_LANCZOS + j] = beta[tid];
       } else {
         mq[tid] = -(j + 1);                   // finished with j + 1 steps
@@ -415,14 +491,39 @@ __global__ void __launch_bounds__(LZ_THREADS) k_lanczos(Work w, DevParams p, int
     for (int q = 0; q < qc; ++q) running |= mq[q] > 0;
     if (!running) break;
   }
-  // extremes of the tridiagonal matrices
+  if (!logm) {
+    // extremes of the tridiagonal matrices
+    if (tid < qc) {
+      const int mm = mq[tid] < 0 ? -mq[tid] : mq[tid];
+      const double* a = al + tid * LMBD_MAX_LANCZOS;
+      const double* b = be + tid * LMBD_MAX_LANCZOS;
+      double* out = w.lam + ((long long)c * p.n_freq + q0 + tid) * 2;
+      out[0] = lz_eig(a, b, mm, 0);
+      out[1] = lz_eig(a, b, mm, mm - 1);
+    }
+    return;
+  }
+  // log mode: Gauss rule of every tridiagonal, then the sum over the three directions
+  double* lq = red;                               // qc partial traces (red is free now)
+  __syncthreads();
   if (tid < qc) {
     const int mm = mq[tid] < 0 ? -mq[tid] : mq[tid];
-    const double* a = al + tid * LMBD_MAX_LANCZOS;
-    const double* b = be + tid * LMBD_MAX_LANCZOS;
-    double* out = w.lam + ((long long)c * p.n_freq + q0 + tid) * 2;
-    out[0] = lz_eig(a, b, mm, 0);
-    out[1] = lz_eig(a, b, mm, mm - 1);
+    double* a = al + tid * LMBD_MAX_LANCZOS;
+    double* b = be + tid * LMBD_MAX_LANCZOS;
+    double* z = X + (size_t)tid * L3;   // X is free after the recurrence; mm <= N <= L3
+    double t = 0.0;
+    if (!tridiag_ql_first_row(a, b, z, mm)) {
+      atomicOr(w.status, LMBD_FLAG_MODEL);
+      t = nan("");
+    } else {
+      for (int i = 0; i < mm; ++i) t += z[i] * z[i] * log1p(-a[i]);
+    }
+    lq[tid] = t;
+  }
+  __syncthreads();
+  if (tid < qc / 3) {
+    const double t = lq[3 * tid] + lq[3 * tid + 1] + lq[3 * tid + 2];
+    w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + q0 + tid] = t;
   }
 }
 
@@ -492,23 +593,34 @@ __global__ void __launch_bounds__(128) k_series_fit(Work w, DevParams p, int c0,
   }
 }
 
-bool launch_series_coefficients(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {
-  if (c1 <= c0) return true;
+// Lanczos passes over the frequencies: nd vectors per frequency, three L3 x (vectors) arrays in
+// shared memory next to the recurrence coefficients; frequencies of one pass share T_LR reads.
+static bool launch_lanczos(const Work& w, const DevParams& p, int c0, int c1, int max_ns, int nd, cudaStream_t s) {
   const int L3 = 3 * max_ns;
   if (L3 > LZ_THREADS * LZ_RPT) return false;
-  // frequencies per pass: three L3 x qc vectors in shared memory next to the recurrence
-  const size_t per_q = sizeof(double) * (3 * (size_t)L3 + 2 * LMBD_MAX_LANCZOS + LZ_THREADS / 32);
-  int qc = (int)((200 * 1024) / per_q);
-  qc = std::max(1, std::min(std::min(qc, LZ_QC), p.n_freq));
-  for (int q0 = 0; q0 < p.n_freq; q0 += qc) {
-    const int n = std::min(qc, p.n_freq - q0);
-    const size_t sm = per_q * n;
+  const size_t per_v = sizeof(double) * (3 * (size_t)L3 + 2 * LMBD_MAX_LANCZOS + LZ_THREADS / 32);
+  int qf = (int)((200 * 1024) / (per_v * nd));       // frequencies per pass
+  qf = std::max(1, std::min(std::min(qf, LZ_QC / nd), p.n_freq));
+  for (int q0 = 0; q0 < p.n_freq; q0 += qf) {
+    const int n = std::min(qf, p.n_freq - q0);
+    const size_t sm = per_v * n * nd;
     raise_smem_limit((const void*)k_lanczos, sm);
-    k_lanczos<<<c1 - c0, LZ_THREADS, sm, s>>>(w, p, c0, q0, n, L3);
+    k_lanczos<<<c1 - c0, LZ_THREADS, sm, s>>>(w, p, c0, q0, n * nd, L3, nd);
   }
+  return true;
+}
+
+bool launch_series_coefficients(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {
+  if (c1 <= c0) return true;
+  if (!launch_lanczos(w, p, c0, c1, max_ns, 1, s)) return false;
   const long long items = (long long)(c1 - c0) * p.n_freq;
   k_series_fit<<<(unsigned)((items + 127) / 128), 128, 0, s>>>(w, p, c0, c1);
   return true;
+}
+
+bool launch_log_mode(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {
+  if (c1 <= c0) return true;
+  return launch_lanczos(w, p, c0, c1, max_ns, 3, s);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -757,7 +869,7 @@ __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0)
   const long long offs = w.off_s[c];
   const int ncv = 3 * p.n_freq;
   const int tid = threadIdx.x;
-  for (int col = tid; col < ncv; col += blockDim.x) {
+  for (int col = tid; col < ncv && !p.logmode; col += blockDim.x) {
     double acc[LMBD_MAX_ORDER_P1];
 #pragma unroll
     for (int n = 0; n < LMBD_MAX_ORDER_P1; ++n) acc[n] = 0.0;
@@ -774,7 +886,11 @@ __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0)
   __syncthreads();
   __shared__ double epart[64];
   __shared__ double ival[64];
-  if (tid < p.n_freq) {
+  if (tid < p.n_freq && p.logmode) {   // log mode: the k-block trace of ln(1 - G) per frequency
+    const double e = w.trbuf[((long long)c * (LMBD_MAX_ORDER_P1)) * 64 + tid];
+    ival[tid] = e;
+    epart[tid] = e * p.cweight[tid + 1];
+  } else if (tid < p.n_freq) {
     int q = tid;
     double e = 0.0;
     double tr_even[LMBD_MAX_ORDER_P1];

@@ -54,6 +54,7 @@ struct Ctx {
   int fit_nodes = 0;               // integrand model (lmbd_set_integrand_fit): 0 = quadrature
   std::vector<double> fit_omega;   // omega = 0, then the fit nodes
   int lanczos = 0;                 // polynomial-fit coefficients (lmbd_set_series_fit): steps
+  int logmode = 0;                 // log mode (lmbd_set_log_mode): Lanczos steps, 0 = series
   int paper_forces = 0;            // force model (lmbd_set_force_model)
   int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
   int spectral_fail = 0;           // lmbd_set_spectral_check: return LMBD_CATASTROPHE when flagged
@@ -511,6 +512,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   }
   dp.lorentz = c->lorentz;
   dp.lanczos = c->lanczos;
+  dp.logmode = c->logmode;
+  if (c->logmode && forces) return LMBD_EUNSUPPORTED;   // the log mode gives energies only
+  if (c->logmode && c->lanczos) return LMBD_EINVAL;
   for (int n = 1; n < LMBD_MAX_ORDER_P1; ++n) dp.cn[n] = -1.0 / n;
   dp.paper = c->paper_forces && forces;
   dp.tc_wait = c->tc_wait > 0 ? c->tc_wait : (1LL << 32);
@@ -708,7 +712,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   const int ncol = 3 * nf * (c->order - 2);
   // sliced tensor-core products: digits per product (see ozaki.cuh and the design notes)
   const bool sliced = c->precision == LMBD_PREC_SLICED;
-  const bool sliced_chain = sliced && ncv <= 48;
+  const bool sliced_chain = sliced && ncv <= 48 && !c->logmode;
   const bool tc05 = c->mma_path == LMBD_MMA_TC05;
   const int ST = 6, DIG_E = 6, DIG_A = 5, DIG_P = 5;
   TRY(ensure(c->alphaK, sizeof(double) * (size_t)sum_n1 * nq));
@@ -906,7 +910,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
           if (!launch_series_coefficients(w, dp, cc, cc + 1, max_ns, s)) return LMBD_ECAPACITY;
           phase_launch[LMBD_PHASE_PREPARE] += 2;
         }
-        for (int m = 1; m < nvec; ++m) {
+        if (dp.logmode && !launch_log_mode(w, dp, cc, cc + 1, max_ns, s)) return LMBD_ECAPACITY;
+        for (int m = 1; m < (dp.logmode ? 1 : nvec); ++m) {
           const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
           if (sliced_chain && tc05) {
             if (!launch_chain_tc(chain_work(dg), dp, m, cc, cc + 1, max_ns, dg, ST, s)) return LMBD_ECUDA;
@@ -919,7 +924,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         launch_mbd_energy(w, dp, cc, cc + 1, s);
       }
       phase_launch[LMBD_PHASE_PREPARE] += c1 - c0;
-      phase_launch[LMBD_PHASE_CHAIN] += (c1 - c0) * (nvec - 1);
+      phase_launch[LMBD_PHASE_CHAIN] += (c1 - c0) * (dp.logmode ? 1 : nvec - 1);
       phase_launch[LMBD_PHASE_ENERGY] += c1 - c0;
     } else {
       mark(LMBD_PHASE_PREPARE);
@@ -930,7 +935,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         phase_launch[LMBD_PHASE_PREPARE] += 2;
       }
       mark(LMBD_PHASE_CHAIN);
-      for (int m = 1; m < nvec; ++m) {
+      // log mode: Lanczos Gauss rules of ln(1 - G) in place of the Krylov chain
+      if (dp.logmode && !launch_log_mode(w, dp, c0, c1, max_ns, s)) return LMBD_ECAPACITY;
+      for (int m = 1; m < (dp.logmode ? 1 : nvec); ++m) {
         const int dg = m + 1 <= (c->order + 1) / 2 ? DIG_E : DIG_A;
         if (sliced_chain && tc05) {
           if (!launch_chain_tc(chain_work(dg), dp, m, c0, c1, max_ns, dg, ST, s)) return LMBD_ECUDA;
@@ -943,7 +950,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       mark(LMBD_PHASE_ENERGY);
       launch_mbd_energy(w, dp, c0, c1, s);
       phase_launch[LMBD_PHASE_PREPARE] += 1;
-      phase_launch[LMBD_PHASE_CHAIN] += nvec - 1;
+      phase_launch[LMBD_PHASE_CHAIN] += dp.logmode ? 1 : nvec - 1;
       phase_launch[LMBD_PHASE_ENERGY] += 1;
     }
     CK(cudaGetLastError());
@@ -1062,7 +1069,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     for (int i = 0; i < N; ++i) {
       double n1 = 3.0 * hc[i].n1, n = 3.0 * hc[i].ns;
       S.flops[LMBD_PHASE_SCS] += dp.nqs * (n1 * n1 * n1 / 3.0 + 6.0 * n1 * n1);
-      S.flops[LMBD_PHASE_CHAIN] += (nvec - 1) * 2.0 * n * n * ncv;
+      S.flops[LMBD_PHASE_CHAIN] += dp.logmode ? 3.0 * dp.logmode * 2.0 * n * n * nf : (nvec - 1) * 2.0 * n * n * ncv;
       if (forces) {
         S.flops[LMBD_PHASE_ADJ_PAIR] += 2.0 * (n * (n + 48.0) / 2.0) * ncol;   // lower tiles of P Q^T
         S.flops[LMBD_PHASE_ADJ_SCS] += dp.nqs * 6.0 * n1 * n1;
@@ -1306,6 +1313,12 @@ int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes) {
 int lmbd_set_force_model(lmbd_ctx* ctx, int model) {
   if (!ctx || (model != LMBD_FORCES_EXACT && model != LMBD_FORCES_PAPER)) return LMBD_EINVAL;
   ctx->c.paper_forces = model == LMBD_FORCES_PAPER;
+  return LMBD_OK;
+}
+
+int lmbd_set_log_mode(lmbd_ctx* ctx, int lanczos_steps) {
+  if (!ctx || lanczos_steps < 0 || lanczos_steps > LMBD_MAX_LANCZOS) return LMBD_EINVAL;
+  ctx->c.logmode = lanczos_steps;
   return LMBD_OK;
 }
 

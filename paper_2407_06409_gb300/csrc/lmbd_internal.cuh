@@ -48,6 +48,9 @@ struct DevParams {
   int n_phi;
   // polynomial-fit series coefficients (Sec. III.A): Lanczos steps, 0 = c_n = -1/n
   int lanczos;
+  // log mode (Sec. III.A, the n_max -> infinity limit): Lanczos steps of the Gauss rules of
+  // [ln(1 - G)]_kk, 0 = the truncated series
+  int logmode;
   double cn[LMBD_MAX_ORDER_P1];   // -1/n (Eq. E_k), so that kernels need no FP64 division
   // force model: 0 = exact gradient of sum_k w_k E_k, 1 = the paper's approximate forces
   // (Sec. III.D: F_k = -dE^{k,tot}/dr_k, alpha_I held, central row and column only for n >= 3)
@@ -288,6 +291,7 @@ void launch_mbd_chain_sized(const Work& w, const DevParams& p, int m, int c0, in
 void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
 // polynomial-fit coefficients: Lanczos interval of every (centre, frequency), then the fit;
 // returns false when the sphere is too large for the kernel (3 max_ns > 1024)
+bool launch_log_mode(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 bool launch_series_coefficients(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 // seeds of the paper's approximate forces (replace the series and pair-matrix adjoint)
 void launch_paper_force_seeds(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);

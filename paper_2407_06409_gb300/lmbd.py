@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_series_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_force_model.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_spectral_check.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_log_mode.argtypes = [_P, ctypes.c_int]
         L.lmbd_autotune.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]
         L.lmbd_release_workspace.argtypes = [_P]
         L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
@@ -108,6 +109,7 @@ def lib() -> ctypes.CDLL:
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_mma_path", "lmbd_set_wait_budget", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
                   "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_set_spectral_check",
+                  "lmbd_set_log_mode",
                   "lmbd_autotune",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
@@ -219,6 +221,10 @@ class LMBD:
         """0: c_n = -1/n.  m > 0: c_n per centre and frequency from the least-squares fit of
         ln(1 - lambda) on the m-step Lanczos estimate of G's spectral interval (Sec. III.A)."""
         _check(lib().lmbd_set_series_fit(self._h, int(lanczos_steps)), "lmbd_set_series_fit")
+
+    def set_log_mode(self, lanczos_steps: int) -> None:
+        """0: truncated series; m > 0: [ln(1 - G)]_kk from m-step Lanczos Gauss rules (energies only)."""
+        _check(lib().lmbd_set_log_mode(self._h, int(lanczos_steps)), "lmbd_set_log_mode")
 
     def set_spectral_check(self, fail: bool) -> None:
         """True: calls whose spectral proxy reached 1 return LMBD_CATASTROPHE (outputs written)."""
