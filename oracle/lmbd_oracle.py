@@ -243,6 +243,47 @@ def phi_integral(a, b, omega: np.ndarray, weight: np.ndarray) -> torch.Tensor:
     return (torch.as_tensor(weight, dtype=_DT) * a / den).sum() / (2.0 * math.pi)
 
 
+def theta_orders(m: int) -> tuple[int, int]:
+    """Orders (M, K) of the force-integrand fit from m fit nodes: M = K = min(floor(m/2), 5),
+    so that the M + K + 1 coefficients need at most the m + 1 samples (omega = 0 and the nodes)."""
+    k = min(m // 2, 5)
+    return k, k
+
+
+def theta_fit(R: np.ndarray, nodes: np.ndarray, M: int, K: int) -> tuple[np.ndarray, np.ndarray]:
+    """Coefficients of the force-integrand fit of Sec. III.D,
+    theta(omega) = sum_{j=0}^{M} u_j (-omega)^j / (1 + sum_{l=1}^{K} v_l omega^(2l)), u, v >= 0
+    (the paper prints the exponent of the denominator as 2n; read as 2l), fitted to the ratios
+    R_i = F(nu_i) / F(0) of the force integrand at the sample frequencies nu_i (nu_0 = 0): the
+    denominator is multiplied out, sum_j u_j (-nu_i)^j - R_i sum_l v_l nu_i^(2l) = R_i, and the
+    system is solved by non-negative least squares (Lawson-Hanson on unit-norm columns, as for
+    phi); the coefficients are the plain least-squares solution on the final passive set."""
+    nu = np.asarray(nodes, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    cols = [(-nu) ** j for j in range(M + 1)] + [-R * nu ** (2 * l) for l in range(1, K + 1)]
+    A = np.stack(cols, axis=1)
+    sc = np.sqrt((A * A).sum(0))
+    sc[sc == 0.0] = 1.0
+    passive, _ = nnls_passive(A / sc, R)
+    x = np.zeros(M + 1 + K)
+    if passive:
+        x[passive] = np.linalg.lstsq(A[:, passive] / sc[passive], R, rcond=None)[0] / sc[passive]
+    u, v = x[:M + 1], x[M + 1:]
+    ju = max([j for j in range(M + 1) if u[j] > 0.0], default=-1)
+    lv = max([l for l in range(1, K + 1) if v[l - 1] > 0.0], default=0)
+    if ju >= 0 and 2 * lv < ju + 2:
+        raise ValueError("fitted force integrand is not integrable")
+    return u, v
+
+
+def theta_integral(u, v, omega: np.ndarray, weight: np.ndarray) -> float:
+    """Integral over [0, inf) of theta(omega) / (2 pi) by the given quadrature."""
+    om = np.asarray(omega, dtype=np.float64)
+    num = sum(u[j] * (-om) ** j for j in range(len(u)))
+    den = 1.0 + sum(v[l - 1] * om ** (2 * l) for l in range(1, len(v) + 1))
+    return float((np.asarray(weight) * num / den).sum() / (2.0 * math.pi))
+
+
 # ----------------------------------------------------------------------------------------
 # polynomial-fit series coefficients (Sec. III.A, Eqs. diagonal_appr, eigendecomp,
 # polynomial-fit)
@@ -760,11 +801,14 @@ def paper_forces(sysm: "System", centres=None) -> np.ndarray:
     """The paper's approximate forces (Sec. III.D) in eV/Angstrom: for every atom k,
     F_k = -dE^{k,tot}/dr_k of its own sphere (every image of k in the sphere moves with it),
     with alpha_I held fixed (Eq. full-pol-grad) and the central-atom approximation for n >= 3
-    (Eq. cent-appr).  The frequency integral is the quadrature (the paper's fitted force
-    integrand theta(omega) is not used)."""
+    (Eq. cent-appr).  The frequency integral is the quadrature; with fit_nodes set it is the
+    paper's fitted force integrand instead: the force integrand F_k(nu_i) (the same derivative of
+    the bare integrand at one frequency) at omega = 0 and the fit nodes, per Cartesian component
+    the fit theta of the ratios F(nu_i) / F(0) (theta_fit), and F_k = F_k(0) times the integral
+    of theta / (2 pi) (the integrand of Eq. mbd-forces-sym with its frequency dependence fitted)."""
     p = sysm.p
-    if p.series_order is None or p.fit_nodes:
-        raise ValueError("paper forces need the truncated series and the quadrature integral")
+    if p.series_order is None:
+        raise ValueError("paper forces need the truncated series")
     centres = list(range(sysm.n)) if centres is None else [int(c) for c in centres]
     need = sorted({int(a) for k in centres for a in sysm.sites(k).atom[: sysm.sites(k).ns]})
     P0 = torch.as_tensor(sysm.pos)
@@ -784,9 +828,30 @@ def paper_forces(sysm: "System", centres=None) -> np.ndarray:
         T = t_lr(x[:ns], at[:, 0], a0[s.atom[:ns]], r0[s.atom[:ns]], p)
         if p.omega_ref is not None:
             at = lorentzian(at[:, 0], at[:, 1], p.omega_ref, sysm.omega)
-        e = _paper_total(T, at, sysm.weight, p) * HARTREE_EV
-        g = torch.autograd.grad(e, P)[0]
-        F[k] = -g[k].numpy()
+        if not p.fit_nodes:
+            e = _paper_total(T, at, sysm.weight, p) * HARTREE_EV
+            g = torch.autograd.grad(e, P)[0]
+            F[k] = -g[k].numpy()
+            continue
+        # force integrand at each sample frequency (columns 1.. of alpha~): the bare integrand
+        # (weight 2 pi at that column only), differentiated like the quadrature form
+        nq = at.shape[1]
+        Fs = []
+        for q in range(1, nq):
+            wq = torch.zeros(nq, dtype=_DT)
+            wq[q] = 2.0 * math.pi
+            e = _paper_total(T, at, wq, p) * HARTREE_EV
+            g = torch.autograd.grad(e, P, retain_graph=q < nq - 1)[0]
+            Fs.append(-g[k].numpy())
+        Fs = np.array(Fs)                                  # (samples, 3)
+        nodes = fit_node_frequencies(p.fit_nodes, p.omega_scale)
+        M, K = theta_orders(p.fit_nodes)
+        om, w = quadrature(p.n_freq, p.omega_scale)
+        for gam in range(3):
+            if Fs[0, gam] == 0.0:
+                continue
+            u, v = theta_fit(Fs[:, gam] / Fs[0, gam], nodes, M, K)
+            F[k, gam] = Fs[0, gam] * theta_integral(u, v, om, w)
     return F
 
 

@@ -975,3 +975,45 @@ def test_spectral_ratio_is_a_weighted_mean_of_the_squared_eigenvalues():
         lam = torch.linalg.eigvalsh(d[:, None] * T * d[None, :])
         assert abs(rat[q - 1] / float((lam ** 2).max()) - 1) < 1e-6
     assert oracle.spectral_ratios(T, alpha, oracle.Params(series_order=3)) == []
+
+
+# ---------------------------------------------------------------------------------------
+# fitted force integrand of Sec. III.D: theta(omega) with a sign-changing numerator
+# ---------------------------------------------------------------------------------------
+def test_theta_fit_recovers_a_sign_changing_rational_integrand():
+    # theta = (1 - 2 w + 0.5 w^2) / (1 + 0.7 w^2 + 0.3 w^4 + 0.05 w^6) changes sign twice
+    # (roots 2 -+ sqrt 2); sampled at omega = 0 and six fit nodes it is recovered exactly
+    u_true, v_true = np.array([1.0, 2.0, 0.5, 0.0]), np.array([0.7, 0.3, 0.05])
+    nodes = oracle.fit_node_frequencies(6, 0.6)
+    M, K = oracle.theta_orders(6)
+    assert (M, K) == (3, 3)
+
+    def theta(om, u, v):
+        num = sum(u[j] * (-om) ** j for j in range(len(u)))
+        return num / (1.0 + sum(v[l - 1] * om ** (2 * l) for l in range(1, len(v) + 1)))
+
+    R = theta(nodes, u_true, v_true)
+    assert R.min() < 0 < R.max()
+    u, v = oracle.theta_fit(R, nodes, M, K)
+    assert np.allclose(u, u_true, atol=1e-9) and np.allclose(v, v_true, atol=1e-9)
+    # its integral by the quadrature against adaptive integration of the true function
+    from scipy.integrate import quad
+    om, w = oracle.quadrature(64, 0.6)
+    exact = quad(lambda x: theta(x, u_true, v_true), 0, np.inf, limit=200)[0] / (2 * math.pi)
+    assert abs(oracle.theta_integral(u, v, om, w) / exact - 1) < 1e-8
+    # a numerator growing as fast as the denominator is not integrable: refused
+    with pytest.raises(ValueError):
+        oracle.theta_fit(theta(nodes, np.array([1.0, 0.0, 0.0, 1.0]), np.array([0.5, 0.0, 0.0])), nodes, 3, 1)
+
+
+def test_paper_forces_with_fitted_integrand_are_exact_for_a_dimer():
+    # without screening the dimer's force integrand is alpha_1(omega) alpha_2(omega) times a
+    # constant, 1 / ((1 + (w/w1)^2)(1 + (w/w2)^2)): in the theta family (u_0, v_1, v_2), so the
+    # fitted force equals the quadrature of the exact integrand, i.e. the quadrature paper force
+    table = np.array([[6.0, 20.0, 3.2], [10.0, 44.0, 3.8]])
+    nu = np.array([0.8, 0.93])
+    p = oracle.Params(r_scs=1.0, r_mbd1=10, r_mbd2=10, r_sphere=10, series_order=2, n_freq=40)
+    f_quad = _dimer(3.4, table, np.array([0, 1]), nu, p).paper_forces()
+    f_fit = _dimer(3.4, table, np.array([0, 1]), nu, oracle.with_params(p, fit_nodes=6)).paper_forces()
+    assert np.abs(f_quad).max() > 1e-6
+    assert np.allclose(f_fit, f_quad, rtol=1e-9, atol=1e-14)
