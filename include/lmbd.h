@@ -283,10 +283,16 @@ int lmbd_set_spectral_check(lmbd_ctx* ctx, int fail);
  *   energy of atom k's own sphere (Eq. E_k_tot, full traces, every image of k in the sphere
  *   moving with it), with the central polarisabilities held fixed (Eq. full-pol-grad), the full
  *   derivative in the n = 2 term and, for n >= 3, the derivative of G kept only in the row and
- *   column of the central atom (Eq. cent-appr).  The frequency integral is the quadrature (the
- *   paper's fitted force integrand theta(omega) is not used), so the mode cannot be combined
- *   with lmbd_set_integrand_fit (LMBD_EINVAL at the call).  Energies are unchanged; with
- *   per-atom weights (lmbd_energy_forces_weighted) E^{k,tot} is multiplied by w_k. */
+ *   column of the central atom (Eq. cent-appr).  The frequency integral is the quadrature; with
+ *   lmbd_set_integrand_fit(m) it is the paper's fitted force integrand instead: the force
+ *   integrand F(nu_j) of every atom and component at omega = 0 and the m fit nodes (one pass of
+ *   the reverse sweep per sample, so m + 1 passes), the fit theta(omega) =
+ *   sum_{i<=M} u_i (-omega)^i / (1 + sum_{l<=K} v_l omega^(2l)), u, v >= 0, M = K = min(m/2, 5),
+ *   to the ratios F(nu_j) / F(0) by non-negative least squares (a fit whose numerator does not
+ *   grow two orders slower than its denominator is repeated with M lowered by one, until theta
+ *   decays at least as omega^-2), and F = F(0) times the integral of theta / (2 pi) by the n_freq-point
+ *   quadrature (LMBD_EMODEL if no fitted theta of some component is integrable).  Energies are unchanged; with per-atom weights (lmbd_energy_forces_weighted)
+ *   E^{k,tot} is multiplied by w_k. */
 #define LMBD_FORCES_EXACT 0
 #define LMBD_FORCES_PAPER 1
 int lmbd_set_force_model(lmbd_ctx* ctx, int model);

@@ -257,23 +257,28 @@ def theta_fit(R: np.ndarray, nodes: np.ndarray, M: int, K: int) -> tuple[np.ndar
     R_i = F(nu_i) / F(0) of the force integrand at the sample frequencies nu_i (nu_0 = 0): the
     denominator is multiplied out, sum_j u_j (-nu_i)^j - R_i sum_l v_l nu_i^(2l) = R_i, and the
     system is solved by non-negative least squares (Lawson-Hanson on unit-norm columns, as for
-    phi); the coefficients are the plain least-squares solution on the final passive set."""
+    phi); the coefficients are the plain least-squares solution on the final passive set.  The
+    integral over [0, inf) needs the numerator to grow two orders slower than the denominator:
+    when the fitted theta does not (the NNLS may leave the highest v at zero), the numerator
+    order M is lowered by one and the fit repeated (a reading; the paper leaves M and K open).
+    Returns (u, v) with len(u) = M + 1 of the original M (trailing zeros if lowered)."""
     nu = np.asarray(nodes, dtype=np.float64)
     R = np.asarray(R, dtype=np.float64)
-    cols = [(-nu) ** j for j in range(M + 1)] + [-R * nu ** (2 * l) for l in range(1, K + 1)]
-    A = np.stack(cols, axis=1)
-    sc = np.sqrt((A * A).sum(0))
-    sc[sc == 0.0] = 1.0
-    passive, _ = nnls_passive(A / sc, R)
-    x = np.zeros(M + 1 + K)
-    if passive:
-        x[passive] = np.linalg.lstsq(A[:, passive] / sc[passive], R, rcond=None)[0] / sc[passive]
-    u, v = x[:M + 1], x[M + 1:]
-    ju = max([j for j in range(M + 1) if u[j] > 0.0], default=-1)
-    lv = max([l for l in range(1, K + 1) if v[l - 1] > 0.0], default=0)
-    if ju >= 0 and 2 * lv < ju + 2:
-        raise ValueError("fitted force integrand is not integrable")
-    return u, v
+    for Mc in range(M, -1, -1):
+        cols = [(-nu) ** j for j in range(Mc + 1)] + [-R * nu ** (2 * l) for l in range(1, K + 1)]
+        A = np.stack(cols, axis=1)
+        sc = np.sqrt((A * A).sum(0))
+        sc[sc == 0.0] = 1.0
+        passive, _ = nnls_passive(A / sc, R)
+        x = np.zeros(Mc + 1 + K)
+        if passive:
+            x[passive] = np.linalg.lstsq(A[:, passive] / sc[passive], R, rcond=None)[0] / sc[passive]
+        u, v = x[:Mc + 1], x[Mc + 1:]
+        ju = max([j for j in range(Mc + 1) if u[j] > 0.0], default=-1)
+        lv = max([l for l in range(1, K + 1) if v[l - 1] > 0.0], default=0)
+        if ju < 0 or 2 * lv >= ju + 2:
+            return np.concatenate([u, np.zeros(M - Mc)]), v
+    raise ValueError("fitted force integrand is not integrable")
 
 
 def theta_integral(u, v, omega: np.ndarray, weight: np.ndarray) -> float:

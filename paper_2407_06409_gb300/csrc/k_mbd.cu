@@ -753,6 +753,100 @@ __device__ void fit_nnls(FitScratch& S, int J, int C, int* passive, double* x) {
   }
 }
 
+// Fitted force integrand of Sec. III.D.  For every atom and Cartesian component, the force
+// integrand F(nu_j) of the paper's forces at the J sample frequencies (nu_0 = 0, then the fit
+// nodes) gives the ratios R_j = F(nu_j) / F(0); theta(omega) = sum_{i<=M} u_i (-omega)^i /
+// (1 + sum_{l<=K} v_l omega^(2l)) with u, v >= 0 is fitted to the multiplied-out equations
+// sum_i u_i (-nu_j)^i - R_j sum_l v_l nu_j^(2l) = R_j by the Lawson-Hanson NNLS above (unit-norm
+// columns), and the force is F(0) times the quadrature of theta / (2 pi).  A fit whose numerator
+// does not grow two orders slower than its denominator is repeated with the numerator order
+// lowered by one; if none is integrable, LMBD_FLAG_MODEL.  One thread per component, its NNLS
+// workspace in shared memory.
+__global__ void __launch_bounds__(16) k_theta_fit(int n, const double* __restrict__ F, ThetaParams tp, double* out,
+                                                  int* status) {
+  extern __shared__ unsigned char theta_smem[];
+  FitScratch& S = reinterpret_cast<FitScratch*>(theta_smem)[threadIdx.x];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 3 * n) return;
+  const int J = tp.J, K = tp.K;
+  const double F0 = F[e];
+  if (F0 == 0.0) {
+    out[e] = 0.0;
+    return;
+  }
+  // numerator order lowered until the fitted theta decays at least as omega^-2
+  double x[LMBD_MAX_ORDER_P1];
+  int M = tp.M;
+  bool ok = false;
+  for (; M >= 0 && !ok; --M) {
+    const int C = M + 1 + K;
+    for (int j = 0; j < J; ++j) {
+      const double R = F[(long long)j * 3 * n + e] / F0;
+      const double nu = tp.nu[j], nu2 = nu * nu;
+      double pw = 1.0;
+      for (int i = 0; i <= M; ++i) {
+        S.A[i][j] = pw;
+        pw *= -nu;
+      }
+      pw = 1.0;
+      for (int l = 1; l <= K; ++l) {
+        pw *= nu2;
+        S.A[M + l][j] = -R * pw;
+      }
+      S.y[j] = R;
+    }
+    for (int c = 0; c < C; ++c) {
+      double t = 0.0;
+      for (int j = 0; j < J; ++j) t += S.A[c][j] * S.A[c][j];
+      t = sqrt(t);
+      S.sc[c] = t > 0.0 ? t : 1.0;
+      for (int j = 0; j < J; ++j) S.A[c][j] /= S.sc[c];
+    }
+    int passive[LMBD_MAX_ORDER_P1];
+    double xs[LMBD_MAX_ORDER_P1];
+    fit_nnls(S, J, C, passive, xs);
+    int ju = -1, lv = 0;
+    for (int c = 0; c < C; ++c) {
+      x[c] = xs[c] / S.sc[c];
+      if (x[c] > 0.0) {
+        if (c <= M) ju = c;
+        else lv = c - M;
+      }
+    }
+    ok = ju < 0 || 2 * lv >= ju + 2;
+    if (ok) break;
+  }
+  if (!ok) {
+    atomicOr(status, LMBD_FLAG_MODEL);
+    out[e] = 0.0;
+    return;
+  }
+  double integral = 0.0;
+  for (int i = 0; i < tp.nphi; ++i) {
+    const double om = tp.om[i], om2 = om * om;
+    double num = 0.0, pw = 1.0;
+    for (int c = 0; c <= M; ++c) {
+      num += x[c] * pw;
+      pw *= -om;
+    }
+    double den = 1.0;
+    pw = 1.0;
+    for (int l = 1; l <= K; ++l) {
+      pw *= om2;
+      den += x[M + l] * pw;
+    }
+    integral += tp.wt[i] * num / den;
+  }
+  out[e] = F0 * integral;
+}
+
+void launch_theta_fit(int n, const double* F, const ThetaParams& tp, double* out, int* status, cudaStream_t s) {
+  if (n <= 0) return;
+  const size_t sm = 16 * sizeof(FitScratch);
+  raise_smem_limit((const void*)k_theta_fit, sm);
+  k_theta_fit<<<(3 * n + 15) / 16, 16, sm, s>>>(n, F, tp, out, status);
+}
+
 // Energy of one centre from its integrand values I[0..J-1] (Hartree), and dE/dI_j into dI.
 __device__ double fit_energy(FitScratch& S, const double* I, const DevParams& p, double* dI, int* status) {
   const int J = p.n_freq, C = p.order + 1;

@@ -58,6 +58,8 @@ struct Ctx {
   int paper_forces = 0;            // force model (lmbd_set_force_model)
   int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
   int spectral_fail = 0;           // lmbd_set_spectral_check: return LMBD_CATASTROPHE when flagged
+  int theta_sample = -1;           // paper forces with the fitted integrand: the sample of this pass
+  DevBuf theta_f, theta_out;       // force integrands at the samples (J x N x 3); fitted forces
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
   // around the bucket launches of the SCS factor (pass A) and SCS adjoint (pass C): their own
@@ -89,7 +91,7 @@ struct Ctx {
                    &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
                    &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw, &cfit, &lam, &gl64,
-                   &fb, &fb_flag, &lu};
+                   &fb, &fb_flag, &lu, &theta_f, &theta_out};
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
   size_t whole_bytes() const {
@@ -518,7 +520,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   for (int n = 1; n < LMBD_MAX_ORDER_P1; ++n) dp.cn[n] = -1.0 / n;
   dp.paper = c->paper_forces && forces;
   dp.tc_wait = c->tc_wait > 0 ? c->tc_wait : (1LL << 32);
-  if (dp.paper && c->fit_nodes) return LMBD_EINVAL;   // the paper fits its force integrand separately
+  // the paper's forces with the fitted integrand run once per sample frequency (run_theta): the
+  // frequency weights of that pass select the bare integrand at that sample
+  if (dp.paper && c->fit_nodes && c->theta_sample < 0) return LMBD_EINVAL;
+  if (dp.paper && c->fit_nodes)
+    for (int q = 0; q < nf; ++q) dp.cweight[q + 1] = q == c->theta_sample ? LMBD_HARTREE : 0.0;
   dp.omega_ref = c->omega_ref;
   dp.nqs = c->lorentz ? 2 : nq;
   for (int q = 0; q < dp.nqs; ++q) dp.omega_s[q] = c->lorentz ? (q == 0 ? 0.0 : c->omega_ref) : dp.omega[q];
@@ -1181,13 +1187,58 @@ int lmbd_create(const lmbd_species* species, int n_species, const lmbd_params* p
   return LMBD_OK;
 }
 
+// The paper's forces with the fitted integrand (Sec. III.D): one pass per sample frequency
+// (omega = 0 and the fit nodes), each returning the force integrand at that sample, then the
+// theta fit per atom and component.  The energies (fitted integrand phi) come from the first pass.
+int run_theta(Ctx* c, int N, const double* pos, const double* cell, const int* spec, const double* nu,
+              const double* w_in, double* e_out, double* f_out, cudaStream_t s) {
+  const int J = c->fit_nodes + 1;
+  if (N == 0) return run(c, N, pos, cell, spec, nu, w_in, e_out, f_out, s);
+  TRY(ensure(c->theta_f, sizeof(double) * 3 * (size_t)N * J));
+  TRY(ensure(c->theta_out, sizeof(double) * 3 * (size_t)N));
+  double* Fj = (double*)c->theta_f.p;
+  int st = LMBD_OK;
+  for (int j = 0; j < J && st == LMBD_OK; ++j) {
+    c->theta_sample = j;
+    st = run(c, N, pos, cell, spec, nu, w_in, j == 0 ? e_out : nullptr, Fj + (size_t)j * 3 * N, s);
+  }
+  c->theta_sample = -1;
+  if (st != LMBD_OK) return st;
+  ThetaParams tp{};
+  tp.J = J;
+  tp.M = tp.K = std::min(c->fit_nodes / 2, 5);
+  tp.nphi = c->n_freq;
+  tp.nu[0] = 0.0;
+  for (int j = 1; j < J; ++j) tp.nu[j] = c->fit_omega[j];
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < c->n_freq; ++i) {
+    tp.om[i] = c->omega[i];
+    tp.wt[i] = c->weight[i] / (2.0 * pi);
+  }
+  int* status = (int*)c->status.p;
+  CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  const bool dev = is_device_ptr(f_out);
+  double* dst = dev ? f_out : (double*)c->theta_out.p;
+  launch_theta_fit(N, Fj, tp, dst, status, s);
+  CK(cudaGetLastError());
+  if (!dev) CK(cudaMemcpyAsync(f_out, dst, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->status_h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*c->status_h & LMBD_FLAG_MODEL) return LMBD_EMODEL;
+  return LMBD_OK;
+}
+
 int lmbd_energy_forces_weighted(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell,
                                 const int* species, const double* hirshfeld, const double* energy_weights,
                                 double* energies, double* forces, void* stream) {
   if (!ctx || n_atoms < 0) return LMBD_EINVAL;
   if (n_atoms > 0 && (!positions || !species || !hirshfeld)) return LMBD_EINVAL;
-  int st = run(&ctx->c, n_atoms, positions, cell, species, hirshfeld, energy_weights, energies, forces,
-               (cudaStream_t)stream);
+  Ctx& c = ctx->c;
+  int st = forces && c.paper_forces && c.fit_nodes
+               ? run_theta(&c, n_atoms, positions, cell, species, hirshfeld, energy_weights, energies, forces,
+                           (cudaStream_t)stream)
+               : run(&c, n_atoms, positions, cell, species, hirshfeld, energy_weights, energies, forces,
+                     (cudaStream_t)stream);
   if (st != LMBD_OK) cudaGetLastError();
   return st;
 }

@@ -292,6 +292,15 @@ void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaSt
 // polynomial-fit coefficients: Lanczos interval of every (centre, frequency), then the fit;
 // returns false when the sphere is too large for the kernel (3 max_ns > 1024)
 bool launch_log_mode(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
+// fitted force integrand (Sec. III.D): sample frequencies nu[0..J) (nu_0 = 0), orders M, K of
+// theta, and the n_phi-point quadrature of its integral (om, wt = w / 2 pi)
+struct ThetaParams {
+  int J, M, K, nphi;
+  double nu[LMBD_FIT_ROWS];
+  double om[LMBD_MAXQ - 1];
+  double wt[LMBD_MAXQ - 1];
+};
+void launch_theta_fit(int n, const double* F, const ThetaParams& tp, double* out, int* status, cudaStream_t s);
 bool launch_series_coefficients(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 // seeds of the paper's approximate forces (replace the series and pair-matrix adjoint)
 void launch_paper_force_seeds(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);

@@ -3,7 +3,8 @@
 F_k = -dE^{k,tot}/dr_k of atom k's own sphere with alpha_I held and, for n >= 3, the
 derivative kept in the central row and column only (Eqs. full-pol-grad, mbd-forces,
 cent-appr); within 1e-8 eV/Angstrom of the oracle, alone and with the Lorentzian model and the
-polynomial-fit coefficients.  Energies are those of the exact mode.
+polynomial-fit coefficients, and with the fitted force integrand theta(omega) of Sec. III.D.
+Energies are those of the exact mode.
 """
 import numpy as np
 import pytest
@@ -86,10 +87,32 @@ def test_force_model_settings(lm):
     with pytest.raises(lm.LmbdError) as err:
         model.set_force_model(2)
     assert err.value.status == lm.LMBD_EINVAL
+
+
+@pytest.mark.parametrize("omega_ref", [None, 4.0])
+def test_paper_forces_with_fitted_force_integrand(lm, omega_ref):
+    # the paper's fast path end to end (Sec. III.C-D): fitted energy integrand phi and fitted
+    # force integrand theta (one reverse pass per sample frequency, then the theta fit)
+    s = inputs.cluster(24, seed=0)
+    p = lm.default_params(r_scs=5.0, r_mbd1=5.0, r_mbd2=5.0, r_sphere=5.0)
+    model = lm.LMBD(s.table, p, 12, 6)
+    model.set_integrand_fit(6)
+    kw = dict(fit_nodes=6)
+    if omega_ref is not None:
+        model.set_frequency_model(lm.FREQ_LORENTZIAN, omega_ref)
+        kw["omega_ref"] = omega_ref
+    e_x, _ = model.energy_forces(*_dev(s), forces=False)
     model.set_force_model(lm.FORCES_PAPER)
-    model.set_integrand_fit(6)                  # the paper fits its force integrand separately
-    with pytest.raises(lm.LmbdError) as err:
-        model.energy_forces(*_dev(s), forces=True)
-    assert err.value.status == lm.LMBD_EINVAL
-    e, _ = model.energy_forces(*_dev(s), forces=False)   # energies alone are fine
-    assert torch.isfinite(e).all()
+    e, f = model.energy_forces(*_dev(s), forces=True)
+    assert torch.equal(e, e_x)
+    so = oracle.System(s.positions, None, s.species, s.hirshfeld, s.table, _op(p, **kw))
+    f_ref = so.paper_forces()
+    assert np.abs(f.cpu().numpy() - f_ref).max() < 1e-8
+    # close to, but not the same as, the quadrature of the force integrand
+    mq = lm.LMBD(s.table, p, 12, 6)
+    mq.set_force_model(lm.FORCES_PAPER)
+    if omega_ref is not None:
+        mq.set_frequency_model(lm.FREQ_LORENTZIAN, omega_ref)
+    _, fq = mq.energy_forces(*_dev(s), forces=True)
+    d = (f - fq).abs().max().item()
+    assert 1e-8 < d < 0.1 * fq.abs().max().item()

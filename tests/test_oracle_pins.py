@@ -1001,9 +1001,16 @@ def test_theta_fit_recovers_a_sign_changing_rational_integrand():
     om, w = oracle.quadrature(64, 0.6)
     exact = quad(lambda x: theta(x, u_true, v_true), 0, np.inf, limit=200)[0] / (2 * math.pi)
     assert abs(oracle.theta_integral(u, v, om, w) / exact - 1) < 1e-8
-    # a numerator growing as fast as the denominator is not integrable: refused
+    # whatever the data, a returned fit decays at least as omega^-2 (numerator orders that would
+    # outgrow a one-term denominator are lowered until it does)
+    for R in (theta(nodes, np.array([1.0, 0.0, 0.0, 1.0]), np.array([0.5])), 1.0 / (1.0 + nodes ** 2)):
+        u, v = oracle.theta_fit(R, nodes, 3, 1)
+        ju = max([j for j in range(4) if u[j] > 0], default=-1)
+        lv = max([l for l in range(1, 2) if v[l - 1] > 0], default=0)
+        assert ju < 0 or 2 * lv >= ju + 2
+    # an integrand that grows with omega has no integrable fit at all: refused
     with pytest.raises(ValueError):
-        oracle.theta_fit(theta(nodes, np.array([1.0, 0.0, 0.0, 1.0]), np.array([0.5, 0.0, 0.0])), nodes, 3, 1)
+        oracle.theta_fit(1.0 + nodes ** 2, nodes, 3, 1)
 
 
 def test_paper_forces_with_fitted_integrand_are_exact_for_a_dimer():
