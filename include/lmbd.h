@@ -121,6 +121,8 @@ typedef struct {
   long long scs_lu_systems; /* (centre, frequency) screening systems solved by the LU fallback:
                               the FP32 Cholesky met a non-positive pivot (B_K indefinite) or
                               its FP64 refinement did not converge                              */
+  int sites_refreshed;     /* 1 if the call refreshed resident site lists (lmbd_set_verlet_skin)
+                              instead of building them                                         */
   long long spectral_flags; /* (centre, frequency) terms whose spectral proxy reached 1: with
                               M = floor(n_max / 2) >= 2, |G^M e_k|^2 >= |G^(M-1) e_k|^2 (the
                               k-block traces Tr[G^2M]_kk and Tr[G^(2M-2)]_kk); never set when
@@ -250,6 +252,20 @@ int lmbd_set_integrand_fit(lmbd_ctx* ctx, int n_fit_nodes);
  *   LMBD_ECAPACITY in this mode.  Returns LMBD_EINVAL for m outside 0..LMBD_MAX_LANCZOS. */
 #define LMBD_MAX_LANCZOS 64
 int lmbd_set_series_fit(lmbd_ctx* ctx, int lanczos_steps);
+
+/* Resident site lists for trajectories (MD frames of one structure).  skin (Angstrom) > 0: the
+ * site lists hold every atom image within the list radius max(2 r_SCS, sphere) + skin of the
+ * frame they were built for, and stay on the device with that frame's positions.  A later call
+ * with the same atom count, cell and species whose atoms have all moved by less than skin / 2
+ * (positions as given, not wrapped) refreshes them instead of searching again: each stored
+ * candidate's displacement is recomputed from the new positions, and the candidates are sorted
+ * and counted again.  The sites within the list radius, their order and their bits are those of a
+ * fresh search, so results are those of a call without a skin (the Verlet-list argument: an atom
+ * now within the radius was within radius + skin).  Any other call searches again and becomes
+ * the new reference.  lmbd_stats.sites_refreshed tells which happened.  skin = 0 (default)
+ * turns it off.  The skin widens the lists (and their memory) by ((r + skin) / r)^3.  Returns
+ * LMBD_EINVAL for a negative or non-finite skin.                                             */
+int lmbd_set_verlet_skin(lmbd_ctx* ctx, double skin);
 
 /* Log mode (Sec. III.A, Eq. series-expansion: the n_max -> infinity limit of the series, the
  * k-block trace of ln(1 - G) that the truncated series and the polynomial fit approximate).

@@ -86,6 +86,41 @@ __global__ void k_bbox(Work w, Grid* g, double r_list) {
   }
 }
 
+// Fractional coordinates f in [0, 1) of atom a, its wrapped position wpos = f C and the lattice
+// translation wrap = floor(frac) with pos = wpos + wrap C (periodic structures).
+__device__ __forceinline__ void wrap_position(const Work& w, const Grid& g, int a, const double* x, double* f) {
+  for (int d = 0; d < 3; ++d) {
+    double v = x[0] * g.inv[0 * 3 + d] + x[1] * g.inv[1 * 3 + d] + x[2] * g.inv[2 * 3 + d];
+    double fl = floor(v);
+    v -= fl;
+    if (v >= 1.0) {
+      v = 0.0;
+      fl += 1.0;
+    }
+    f[d] = v;
+    w.wrap[3 * a + d] = (int)fl;
+  }
+  for (int d = 0; d < 3; ++d)
+    w.wpos[3 * a + d] = f[0] * g.cell[0 * 3 + d] + f[1] * g.cell[1 * 3 + d] + f[2] * g.cell[2 * 3 + d];
+}
+
+// Wrapped positions only (site lists refreshed from a resident candidate list).
+__global__ void k_wrap(Work w, const Grid* __restrict__ gp) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= w.n_atoms) return;
+  const Grid& g = *gp;
+  double x[3] = {w.pos[3 * a], w.pos[3 * a + 1], w.pos[3 * a + 2]};
+  if (g.periodic) {
+    double f[3];
+    wrap_position(w, g, a, x, f);
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      w.wpos[3 * a + d] = x[d];
+      w.wrap[3 * a + d] = 0;
+    }
+  }
+}
+
 __global__ void k_bin(Work w, const Grid* __restrict__ gp) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= w.n_atoms) return;
@@ -94,21 +129,17 @@ __global__ void k_bin(Work w, const Grid* __restrict__ gp) {
   int ci[3];
   if (g.periodic) {
     double f[3];
+    wrap_position(w, g, a, x, f);
     for (int d = 0; d < 3; ++d) {
-      double v = x[0] * g.inv[0 * 3 + d] + x[1] * g.inv[1 * 3 + d] + x[2] * g.inv[2 * 3 + d];
-      v -= floor(v);
-      if (v >= 1.0) v = 0.0;
-      f[d] = v;
-      int c = (int)(v * g.nc[d]);
+      int c = (int)(f[d] * g.nc[d]);
       ci[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
     }
-    for (int d = 0; d < 3; ++d)
-      w.wpos[3 * a + d] = f[0] * g.cell[0 * 3 + d] + f[1] * g.cell[1 * 3 + d] + f[2] * g.cell[2 * 3 + d];
   } else {
     for (int d = 0; d < 3; ++d) {
       int c = (int)((x[d] - g.origin[d]) / g.h[d]);
       ci[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
       w.wpos[3 * a + d] = x[d];
+      w.wrap[3 * a + d] = 0;
     }
   }
   int cell = (ci[0] * g.nc[1] + ci[1]) * g.nc[2] + ci[2];
@@ -165,12 +196,95 @@ __device__ __forceinline__ bool site_less(double ra, int aa, const double* xa, d
   return xa[2] < xb[2];
 }
 
+// Displacement d (Angstrom) of the image img of atom j from the centre at wrapped position xk,
+// and its square, with every operation rounded separately (no contraction): the build and the
+// refresh of the site lists produce the same bits.
+__device__ __forceinline__ double site_disp(const Work& w, const Grid& g, int j, const int* img, const double* xk,
+                                            double* d) {
+  for (int e = 0; e < 3; ++e) {
+    double sh = 0.0;
+    if (g.periodic)
+      sh = __dadd_rn(__dadd_rn(__dmul_rn((double)img[0], g.cell[0 * 3 + e]), __dmul_rn((double)img[1], g.cell[1 * 3 + e])),
+                     __dmul_rn((double)img[2], g.cell[2 * 3 + e]));
+    d[e] = __dsub_rn(__dadd_rn(w.wpos[3 * j + e], sh), xk[e]);
+  }
+  return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+// Sort the n candidates of centre k (shared memory: key r^2, atom, displacement, image) by
+// (r^2, atom, displacement) and store them with the prefix counts; overflow beyond cap was
+// flagged by the caller.
+__device__ void sites_sort_store(Work& w, const DevParams& p, int k, int n, int cnt, double* key, double* dx, int* at,
+                                 int* im) {
+  const int cap = w.site_cap;
+  const bool overflow = cnt > cap;
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = n + threadIdx.x; i < P; i += blockDim.x) {
+    key[i] = 1e300;
+    at[i] = 0x7fffffff;
+    dx[3 * i] = dx[3 * i + 1] = dx[3 * i + 2] = 0.0;
+    im[3 * i] = im[3 * i + 1] = im[3 * i + 2] = 0;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+        int lo = 2 * i - (i & (stride - 1));
+        int hi = lo + stride;
+        bool up = ((lo & size) == 0);
+        bool less = site_less(key[hi], at[hi], dx + 3 * hi, key[lo], at[lo], dx + 3 * lo);
+        if (less == up) {
+          double tk = key[lo]; key[lo] = key[hi]; key[hi] = tk;
+          int ta = at[lo]; at[lo] = at[hi]; at[hi] = ta;
+          for (int d = 0; d < 3; ++d) {
+            double t = dx[3 * lo + d]; dx[3 * lo + d] = dx[3 * hi + d]; dx[3 * hi + d] = t;
+            int ti = im[3 * lo + d]; im[3 * lo + d] = im[3 * hi + d]; im[3 * hi + d] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // write out and count the prefixes
+  __shared__ int c1, cs, c12;
+  if (threadIdx.x == 0) { c1 = 0; cs = 0; c12 = 0; }
+  __syncthreads();
+  long long base = (long long)k * cap;
+  const double ib = 1.0 / LMBD_BOHR;
+  int l1 = 0, ls = 0, l12 = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r2 = key[i];
+    const int j = at[i];
+    w.site_atom[base + i] = j;
+    w.site_x[3 * (base + i) + 0] = dx[3 * i + 0] * ib;
+    w.site_x[3 * (base + i) + 1] = dx[3 * i + 1] * ib;
+    w.site_x[3 * (base + i) + 2] = dx[3 * i + 2] * ib;
+    // lattice image relative to the unwrapped positions: pos_j + n C - pos_k
+    for (int d = 0; d < 3; ++d) w.site_img[3 * (base + i) + d] = im[3 * i + d] - w.wrap[3 * j + d] + w.wrap[3 * k + d];
+    l1 += r2 < p.r2_scs_ang;
+    ls += r2 < p.r2_sphere_ang;
+    l12 += r2 < p.r2_scs2_ang;
+  }
+  atomicAdd(&c1, l1);
+  atomicAdd(&cs, ls);
+  atomicAdd(&c12, l12);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    w.counts[k] = Counts{c1, cs, c12, n};
+    // the central atom must be the unique site at distance zero (a truncated list, reported
+    // as a capacity overflow, need not hold the centre)
+    if (!overflow && (n < 1 || at[0] != k || key[0] != 0.0 || (n > 1 && key[1] == 0.0)))
+      atomicOr(w.status, LMBD_FLAG_COINCIDENT);
+  }
+}
+
 __global__ void k_sites(Work w, DevParams p, const Grid* __restrict__ gp, int c0) {
   extern __shared__ unsigned char smem[];
   const int cap = w.site_cap;                 // power of two
   double* key = (double*)smem;                // cap
   double* dx = key + cap;                     // cap x 3
   int* at = (int*)(dx + 3 * cap);             // cap
+  int* im = at + cap;                         // cap x 3 image shifts of the wrapped positions
   __shared__ int cnt;
   const Grid& g = *gp;
   int k = c0 + blockIdx.x;
@@ -199,88 +313,100 @@ __global__ void k_sites(Work w, DevParams p, const Grid* __restrict__ gp, int c0
           }
         }
         if (!ok) continue;
-        double sh[3] = {0.0, 0.0, 0.0};
-        if (g.periodic)
-          for (int d = 0; d < 3; ++d)
-            sh[d] = img[0] * g.cell[0 * 3 + d] + img[1] * g.cell[1 * 3 + d] + img[2] * g.cell[2 * 3 + d];
         int cell = (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
         int b = w.cell_start[cell], e = w.cell_start[cell + 1];
         for (int t = b + threadIdx.x; t < e; t += blockDim.x) {
           int j = w.cell_atoms[t];
-          double d0 = w.wpos[3 * j + 0] + sh[0] - xk[0];
-          double d1 = w.wpos[3 * j + 1] + sh[1] - xk[1];
-          double d2 = w.wpos[3 * j + 2] + sh[2] - xk[2];
-          double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+          double d[3];
+          const double r2 = site_disp(w, g, j, img, xk, d);
           if (r2 < p.r2_list_ang) {
             int slot = atomicAdd(&cnt, 1);
             if (slot < cap) {
               key[slot] = r2;
               at[slot] = j;
-              dx[3 * slot + 0] = d0;
-              dx[3 * slot + 1] = d1;
-              dx[3 * slot + 2] = d2;
+              dx[3 * slot + 0] = d[0];
+              dx[3 * slot + 1] = d[1];
+              dx[3 * slot + 2] = d[2];
+              im[3 * slot + 0] = img[0];
+              im[3 * slot + 1] = img[1];
+              im[3 * slot + 2] = img[2];
             }
           }
         }
       }
   __syncthreads();
   int n = cnt;
-  const bool overflow = n > cap;
-  if (overflow) {
+  if (n > cap) {
     if (threadIdx.x == 0) atomicOr(w.status, LMBD_FLAG_CAPACITY);
     n = cap;
   }
-  int P = 1;
-  while (P < n) P <<= 1;
-  for (int i = n + threadIdx.x; i < P; i += blockDim.x) {
-    key[i] = 1e300;
-    at[i] = 0x7fffffff;
-    dx[3 * i] = dx[3 * i + 1] = dx[3 * i + 2] = 0.0;
-  }
-  __syncthreads();
-  for (int size = 2; size <= P; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
-        int lo = 2 * i - (i & (stride - 1));
-        int hi = lo + stride;
-        bool up = ((lo & size) == 0);
-        bool less = site_less(key[hi], at[hi], dx + 3 * hi, key[lo], at[lo], dx + 3 * lo);
-        if (less == up) {
-          double tk = key[lo]; key[lo] = key[hi]; key[hi] = tk;
-          int ta = at[lo]; at[lo] = at[hi]; at[hi] = ta;
-          for (int d = 0; d < 3; ++d) { double t = dx[3 * lo + d]; dx[3 * lo + d] = dx[3 * hi + d]; dx[3 * hi + d] = t; }
-        }
-      }
-      __syncthreads();
-    }
-  // write out and count the prefixes
-  __shared__ int c1, cs, c12;
-  if (threadIdx.x == 0) { c1 = 0; cs = 0; c12 = 0; }
-  __syncthreads();
-  long long base = (long long)k * cap;
-  const double ib = 1.0 / LMBD_BOHR;
-  int l1 = 0, ls = 0, l12 = 0;
+  sites_sort_store(w, p, k, n, cnt, key, dx, at, im);
+}
+
+// Refresh of resident site lists (trajectory frames within half a Verlet skin of the frame the
+// lists were built for): every stored candidate, an atom and its lattice image relative to the
+// unwrapped positions, gets its displacement recomputed from the current positions with the
+// build's arithmetic, and the candidates are sorted and counted again.  The candidates hold
+// every site within the list radius + skin of the build frame, so every site now within the
+// list radius; the sites within it come out in the order, and with the bits, of a fresh build.
+__global__ void k_sites_refresh(Work w, DevParams p, const Grid* __restrict__ gp) {
+  extern __shared__ unsigned char smem[];
+  const int cap = w.site_cap;
+  double* key = (double*)smem;
+  double* dx = key + cap;
+  int* at = (int*)(dx + 3 * cap);
+  int* im = at + cap;
+  const Grid& g = *gp;
+  const int k = blockIdx.x;
+  if (k >= w.n_atoms) return;
+  const int n = w.counts[k].nt;
+  const long long base = (long long)k * cap;
+  const double xk[3] = {w.wpos[3 * k], w.wpos[3 * k + 1], w.wpos[3 * k + 2]};
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double r2 = key[i];
-    w.site_atom[base + i] = at[i];
-    w.site_x[3 * (base + i) + 0] = dx[3 * i + 0] * ib;
-    w.site_x[3 * (base + i) + 1] = dx[3 * i + 1] * ib;
-    w.site_x[3 * (base + i) + 2] = dx[3 * i + 2] * ib;
-    l1 += r2 < p.r2_scs_ang;
-    ls += r2 < p.r2_sphere_ang;
-    l12 += r2 < p.r2_scs2_ang;
+    const int j = w.site_atom[base + i];
+    int img[3];
+    for (int d = 0; d < 3; ++d) img[d] = w.site_img[3 * (base + i) + d] + w.wrap[3 * j + d] - w.wrap[3 * k + d];
+    double d3[3];
+    key[i] = site_disp(w, g, j, img, xk, d3);
+    at[i] = j;
+    for (int d = 0; d < 3; ++d) {
+      dx[3 * i + d] = d3[d];
+      im[3 * i + d] = img[d];
+    }
   }
-  atomicAdd(&c1, l1);
-  atomicAdd(&cs, ls);
-  atomicAdd(&c12, l12);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    w.counts[k] = Counts{c1, cs, c12, n};
-    // the central atom must be the unique site at distance zero (a truncated list, reported
-    // as a capacity overflow, need not hold the centre)
-    if (!overflow && (n < 1 || at[0] != k || key[0] != 0.0 || (n > 1 && key[1] == 0.0)))
-      atomicOr(w.status, LMBD_FLAG_COINCIDENT);
+  sites_sort_store(w, p, k, n, n, key, dx, at, im);
+}
+
+// Largest displacement of any atom from the reference frame, and a species change: flag 1 if
+// some atom moved by half the skin or more (or changed species).
+__global__ void k_skin_check(Work w, const double* __restrict__ ref_pos, const int* __restrict__ ref_spec,
+                             double half_skin2, int* flag) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= w.n_atoms) return;
+  double d2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double t = w.pos[3 * a + d] - ref_pos[3 * a + d];
+    d2 += t * t;
   }
+  if (!(d2 < half_skin2) || w.species[a] != ref_spec[a]) atomicOr(flag, 1);
+}
+
+void launch_skin_check(const Work& w, const double* ref_pos, const int* ref_spec, double half_skin2, int* flag,
+                       cudaStream_t s) {
+  if (w.n_atoms == 0) return;
+  k_skin_check<<<(w.n_atoms + 127) / 128, 128, 0, s>>>(w, ref_pos, ref_spec, half_skin2, flag);
+}
+
+void launch_sites_refresh(const Work& w, const DevParams& p, const Grid& g, cudaStream_t s, int* launches) {
+  if (w.n_atoms == 0) return;
+  Grid* gdev = w.grid;
+  cudaMemcpyAsync(gdev, &g, sizeof(Grid), cudaMemcpyHostToDevice, s);
+  k_wrap<<<(w.n_atoms + 127) / 128, 128, 0, s>>>(w, gdev);
+  const size_t sm = (size_t)w.site_cap * (8 + 24 + 4 + 12);
+  raise_smem_limit((const void*)k_sites_refresh, sm);
+  k_sites_refresh<<<w.n_atoms, 256, sm, s>>>(w, p, gdev);
+  *launches += 2;
 }
 
 void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStream_t s, int* launches) {
@@ -296,7 +422,7 @@ void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStre
   k_bin<<<nb, 128, 0, s>>>(w, gdev);
   k_cell_scan<<<1, 1024, 0, s>>>(w, gdev);
   k_scatter<<<nb, 128, 0, s>>>(w);
-  size_t sm = (size_t)w.site_cap * (8 + 24 + 4);
+  size_t sm = (size_t)w.site_cap * (8 + 24 + 4 + 12);
   raise_smem_limit((const void*)k_sites, sm);
   k_sites<<<w.n_atoms, 256, sm, s>>>(w, p, gdev, 0);
   *launches += 4;

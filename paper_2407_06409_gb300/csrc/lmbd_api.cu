@@ -59,6 +59,13 @@ struct Ctx {
   int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
   int spectral_fail = 0;           // lmbd_set_spectral_check: return LMBD_CATASTROPHE when flagged
   int theta_sample = -1;           // paper forces with the fitted integrand: the sample of this pass
+  // resident site lists (lmbd_set_verlet_skin): candidates within the list radius + skin of the
+  // reference frame, refreshed while no atom has moved by half the skin
+  double skin = 0.0;
+  bool ref_valid = false;
+  int ref_n = 0, ref_periodic = 0;
+  double ref_cell[9] = {};
+  DevBuf ref_pos, ref_spec;
   DevBuf theta_f, theta_out;       // force integrands at the samples (J x N x 3); fitted forces
   int last_nqs = 0;                // columns of the central polarisabilities of the last call
   cudaEvent_t ev[LMBD_NPHASE + 1] = {};
@@ -77,7 +84,7 @@ struct Ctx {
   // device buffers: whole-structure arrays, then one arena for the per-wave workspaces
   DevBuf table_d, pos_d, species_d, nu_d, weights_d, out_e_d, out_f_d;
   DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
-  DevBuf site_atom, site_x, counts, offs, totals, status, pcount;
+  DevBuf site_atom, site_x, site_img, wrap, counts, offs, totals, status, pcount;
   DevBuf alphaK, alphaI, energies, trbuf, wexp, alphaK_bar, alphaI_bar, gacc, rad_ab, rad_ff;
   DevBuf order1_d, order3_d, fitw, cfit, lam, gl64, fb, fb_flag, lu;
   DevBuf arena;
@@ -91,7 +98,7 @@ struct Ctx {
                    &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
                    &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw, &cfit, &lam, &gl64,
-                   &fb, &fb_flag, &lu, &theta_f, &theta_out};
+                   &fb, &fb_flag, &lu, &theta_f, &theta_out, &site_img, &wrap, &ref_pos, &ref_spec};
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
   size_t whole_bytes() const {
@@ -476,7 +483,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   DevParams dp{};
   const double ib = 1.0 / LMBD_BOHR;
   const double rsph = sphere_radius(P);
-  const double rlist = fmax(2.0 * P.r_scs, rsph);
+  // with resident site lists the lists hold every site within the list radius + skin
+  const double rlist = fmax(2.0 * P.r_scs, rsph) + c->skin;
   dp.r_scs = P.r_scs * ib;
   dp.r_mbd1 = P.r_mbd1 * ib;
   dp.r_mbd2 = P.r_mbd2 * ib;
@@ -582,6 +590,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   TRY(ensure(c->cell_count, sizeof(int) * ncells));
   TRY(ensure(c->cell_start, sizeof(int) * (ncells + 1)));
   TRY(ensure(c->cell_atoms, sizeof(int) * N));
+  TRY(ensure(c->wrap, sizeof(int) * 3 * (size_t)N));
   TRY(ensure(c->grid, sizeof(Grid)));
   TRY(ensure(c->counts, sizeof(Counts) * N));
   TRY(ensure(c->offs, sizeof(long long) * O_COUNT * (size_t)(N + 1)));
@@ -624,6 +633,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   w.cell_count = (int*)c->cell_count.p;
   w.cell_start = (int*)c->cell_start.p;
   w.cell_atoms = (int*)c->cell_atoms.p;
+  w.wrap = (int*)c->wrap.p;
   w.ncells = ncells;
   w.grid = (Grid*)c->grid.p;
   w.counts = (Counts*)c->counts.p;
@@ -670,18 +680,38 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     }
   };
   mark(LMBD_PHASE_NEIGHBORS);
+  // resident site lists: a frame of the same structure (atom count, cell, species) whose atoms
+  // all moved by less than half the skin since the lists were built refreshes them in place
+  bool refresh = false;
+  if (c->skin > 0.0 && c->ref_valid && c->ref_n == N && c->ref_periodic == (cell ? 1 : 0) &&
+      (!cell || memcmp(c->ref_cell, g.cell, sizeof(c->ref_cell)) == 0) && c->site_atom.p) {
+    w.site_cap = c->site_cap;
+    CK(cudaMemsetAsync(w.status, 0, sizeof(int) * 4, s));
+    launch_skin_check(w, (const double*)c->ref_pos.p, (const int*)c->ref_spec.p, 0.25 * c->skin * c->skin,
+                      w.status + 3, s);
+    CK(cudaMemcpyAsync(c->status_h, w.status + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    refresh = *c->status_h == 0;
+    ++launches;
+  }
+  if (!refresh) c->ref_valid = false;   // the lists are rebuilt below; valid again on success
   for (int attempt = 0; attempt < 4; ++attempt) {
     TRY(ensure(c->site_atom, sizeof(int) * (size_t)N * c->site_cap));
     TRY(ensure(c->site_x, sizeof(double) * 3 * (size_t)N * c->site_cap));
+    TRY(ensure(c->site_img, sizeof(int) * 3 * (size_t)N * c->site_cap));
     w.site_cap = c->site_cap;
     w.site_atom = (int*)c->site_atom.p;
     w.site_x = (double*)c->site_x.p;
+    w.site_img = (int*)c->site_img.p;
     CK(cudaMemsetAsync(w.status, 0, sizeof(int) * 4, s));
     if (attempt == 0) {   // after the status reset: it validates device-resident inputs
       launch_free_atom(w, dp, s);
       ++launches;
     }
-    launch_neighbors(w, dp, g, s, &launches);
+    if (refresh)
+      launch_sites_refresh(w, dp, g, s, &launches);
+    else
+      launch_neighbors(w, dp, g, s, &launches);
     launch_scs_count(w, dp, w.site_cap, s);
     launch_offsets(w, dp, s);
     launches += 2;
@@ -689,12 +719,27 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     CK(cudaMemcpyAsync(c->totals_h, w.totals, sizeof(long long) * 16, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->status_h, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (*c->status_h & (LMBD_FLAG_COINCIDENT | LMBD_FLAG_BAD_INPUT)) return LMBD_EINVAL;
-    if (!(*c->status_h & LMBD_FLAG_CAPACITY)) break;
+    if (*c->status_h & LMBD_FLAG_BAD_INPUT) return LMBD_EINVAL;
+    if (!(*c->status_h & LMBD_FLAG_CAPACITY)) {
+      if (*c->status_h & LMBD_FLAG_COINCIDENT) return LMBD_EINVAL;
+      break;
+    }
+    refresh = false;   // a grown capacity needs a full build
     if (c->site_cap >= 4096 || attempt == 3) return LMBD_ECAPACITY;
     c->site_cap *= 2;
   }
   phase_launch[LMBD_PHASE_NEIGHBORS] = launches;
+  c->stats.sites_refreshed = refresh ? 1 : 0;
+  if (c->skin > 0.0 && !refresh) {   // the lists were built for this frame: it is the reference
+    TRY(ensure(c->ref_pos, sizeof(double) * 3 * (size_t)N));
+    TRY(ensure(c->ref_spec, sizeof(int) * (size_t)N));
+    CK(cudaMemcpyAsync(c->ref_pos.p, w.pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->ref_spec.p, w.species, sizeof(int) * N, cudaMemcpyDeviceToDevice, s));
+    c->ref_valid = true;
+    c->ref_n = N;
+    c->ref_periodic = cell ? 1 : 0;
+    memcpy(c->ref_cell, g.cell, sizeof(c->ref_cell));
+  }
   const long long sum_n1 = c->totals_h[0];
   const int max_n1 = (int)c->totals_h[4], max_ns = (int)c->totals_h[5], max_n12 = (int)c->totals_h[6];
   // kernel shared-memory capacities (per-centre systems live in shared memory)
@@ -1367,6 +1412,13 @@ int lmbd_set_force_model(lmbd_ctx* ctx, int model) {
   return LMBD_OK;
 }
 
+int lmbd_set_verlet_skin(lmbd_ctx* ctx, double skin) {
+  if (!ctx || !(skin >= 0.0) || !std::isfinite(skin)) return LMBD_EINVAL;
+  ctx->c.skin = skin;
+  ctx->c.ref_valid = false;
+  return LMBD_OK;
+}
+
 int lmbd_set_log_mode(lmbd_ctx* ctx, int lanczos_steps) {
   if (!ctx || lanczos_steps < 0 || lanczos_steps > LMBD_MAX_LANCZOS) return LMBD_EINVAL;
   ctx->c.logmode = lanczos_steps;
@@ -1392,6 +1444,7 @@ int lmbd_release_workspace(lmbd_ctx* ctx) {
     if (c.whole_bufs[i] != &c.table_d) release(*c.whole_bufs[i]);
   release(c.arena);
   c.last_n = 0;
+  c.ref_valid = false;
   return LMBD_OK;
 }
 
@@ -1651,6 +1704,8 @@ int noalloc_central(const lmbd_species* species_params, int n_species, const lmb
   w.cell_atoms = cv.take<int>(N);
   w.ncells = ncells;
   w.grid = cv.take<Grid>(1);
+  w.wrap = cv.take<int>(3 * (size_t)N);
+  w.site_img = cv.take<int>(3 * (size_t)N * site_cap);
   w.site_atom = cv.take<int>((size_t)N * site_cap);
   w.site_x = cv.take<double>(3 * (size_t)N * site_cap);
   w.counts = cv.take<Counts>(N);

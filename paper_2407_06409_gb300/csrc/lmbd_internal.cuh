@@ -101,6 +101,9 @@ struct Work {
   int* cell_atoms;             // N
   int ncells;
   Grid* grid;                  // device copy of the search grid
+  int* wrap;                   // N x 3 lattice translation of each atom: pos = wpos + wrap C
+  int* site_img;               // N x site_cap x 3 lattice image of each site relative to the
+                               // unwrapped positions (site = pos_j + img C - pos_k)
   int* site_atom;              // N x site_cap
   double* site_x;              // N x site_cap x 3, displacement from the centre (bohr)
   Counts* counts;              // N
@@ -270,6 +273,9 @@ __device__ __forceinline__ void atomic_add3(double* p, double a, double b, doubl
 // ---------------------------------------------------------------------------------------
 // Each launcher enqueues its kernels on stream s for central atoms [c0, c1).
 void launch_free_atom(const Work& w, const DevParams& p, cudaStream_t s);
+void launch_sites_refresh(const Work& w, const DevParams& p, const Grid& g, cudaStream_t s, int* launches);
+void launch_skin_check(const Work& w, const double* ref_pos, const int* ref_spec, double half_skin2, int* flag,
+                       cudaStream_t s);
 void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStream_t s, int* launches);
 void launch_offsets(const Work& w, const DevParams& p, cudaStream_t s);
 void launch_scs_count(const Work& w, const DevParams& p, int max_n12, cudaStream_t s);

@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("waves_scs", ctypes.c_int), ("waves_mbd", ctypes.c_int), ("scs_recomputed", ctypes.c_int),
                 ("scs_pairs", ctypes.c_longlong), ("scs_adjacency", ctypes.c_longlong),
                 ("ms_kernel", ctypes.c_double * 2), ("scs_lu_systems", ctypes.c_longlong),
-                ("spectral_flags", ctypes.c_longlong)]
+                ("sites_refreshed", ctypes.c_int), ("spectral_flags", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_force_model.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_spectral_check.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_log_mode.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_verlet_skin.argtypes = [_P, ctypes.c_double]
         L.lmbd_autotune.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]
         L.lmbd_release_workspace.argtypes = [_P]
         L.lmbd_held_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
@@ -109,7 +110,7 @@ def lib() -> ctypes.CDLL:
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_mma_path", "lmbd_set_wait_budget", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
                   "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_set_spectral_check",
-                  "lmbd_set_log_mode",
+                  "lmbd_set_log_mode", "lmbd_set_verlet_skin",
                   "lmbd_autotune",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
@@ -221,6 +222,10 @@ class LMBD:
         """0: c_n = -1/n.  m > 0: c_n per centre and frequency from the least-squares fit of
         ln(1 - lambda) on the m-step Lanczos estimate of G's spectral interval (Sec. III.A)."""
         _check(lib().lmbd_set_series_fit(self._h, int(lanczos_steps)), "lmbd_set_series_fit")
+
+    def set_verlet_skin(self, skin: float) -> None:
+        """Resident site lists across frames of one structure (Angstrom; 0 = search every call)."""
+        _check(lib().lmbd_set_verlet_skin(self._h, float(skin)), "lmbd_set_verlet_skin")
 
     def set_log_mode(self, lanczos_steps: int) -> None:
         """0: truncated series; m > 0: [ln(1 - G)]_kk from m-step Lanczos Gauss rules (energies only)."""

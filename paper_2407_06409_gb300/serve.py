@@ -11,7 +11,9 @@ slots give back the memory they hold (least recently used first) before a reques
 to waves, and admission looks past a request that does not fit to the next ones in
 arrival order (a bounded window).  An MD frame goes to the slot that last
 served its trajectory when that slot is free: the workspaces there are sized for the
-structure and stay resident, so the frame runs without device allocation.
+structure and stay resident, so the frame runs without device allocation, and the slot's site
+lists (built with a Verlet skin) are refreshed in place instead of searched again while no atom
+has moved by half the skin.
 
 Timing is host wall-clock: latency = completion - arrival.
 """
@@ -66,6 +68,7 @@ class Result:
     affinity: bool
     waves: tuple[int, int] = (1, 1)
     error: str | None = None
+    sites_refreshed: bool = False   # the slot's resident site lists were refreshed, not rebuilt
 
     @property
     def latency(self) -> float:
@@ -76,10 +79,12 @@ class LmbdEngine:
     """One library context on its own CUDA stream (lower number = higher priority)."""
 
     def __init__(self, table, params=None, n_freq: int = 12, series_order: int = 6, forces: bool = True,
-                 priority: int = 0):
+                 priority: int = 0, skin: float = 0.5):
         import torch
         from . import lmbd
         self.model = lmbd.LMBD(table, params, n_freq, series_order)
+        # site lists stay resident across frames of the trajectory this slot serves
+        self.model.set_verlet_skin(skin)
         self.stream = torch.cuda.Stream(priority=priority)
         self.forces = forces
 
@@ -272,7 +277,8 @@ class Server:
                     self.fp.observe(item.structure.n_atoms, st)
                 results[item.rid] = Result(item.rid, item.structure.n_atoms, e, f, arrival, admitted, done,
                                            slot.index, budget, affinity,
-                                           (st.get("waves_scs", 1), st.get("waves_mbd", 1)), err)
+                                           (st.get("waves_scs", 1), st.get("waves_mbd", 1)), err,
+                                           bool(st.get("sites_refreshed", 0)))
                 self._cv.notify_all()
 
     def serve(self, items: list, realtime: bool = True) -> list[Result]:
@@ -329,6 +335,7 @@ def summarize(results: list[Result], large_atoms: int | None = None) -> dict:
     return {**extra, 
         "requests": len(results),
         "errors": sum(r.error is not None for r in results),
+        "sites_refreshed": sum(r.sites_refreshed for r in results),
         "atoms": int(atoms),
         "p50_s": float(np.percentile(lat, 50)),
         "p99_s": float(np.percentile(lat, 99)),

@@ -70,3 +70,35 @@ def test_realtime_serving_reports_latency(lm):
     assert s["atoms_per_s"] > 0
     for e in engines:
         e.close()
+
+
+def test_resident_site_lists_across_md_frames(lm):
+    # frames of one trajectory on one context with a Verlet skin: while no atom has moved by
+    # half the skin the site lists are refreshed in place (one atom even crosses the periodic
+    # boundary), and every frame's energies equal, bit for bit, those of a fresh context
+    base = inputs.box(300, seed=21)
+    box = float(base.cell[0, 0])
+    pos0 = base.positions.copy()
+    pos0[0, 0] = box - 0.004                      # at the boundary: the jitter moves it across
+    rng = np.random.default_rng(5)
+    frames = [pos0]
+    for _ in range(3):
+        f = frames[-1] + rng.normal(scale=0.02, size=pos0.shape) * 0.5
+        frames.append(f)
+    frames[1][0, 0] = box + 0.004                 # crossed (positions are not wrapped)
+    frames.append(frames[-1] + 0.2 * rng.normal(size=pos0.shape))   # a large move: search again
+    p = lm.default_params()
+    res = lm.LMBD(base.table, p, 12, 6)
+    res.set_verlet_skin(0.5)
+    refreshed = []
+    for f in frames:
+        s = inputs.Structure(f, base.cell, base.species, base.hirshfeld, base.table)
+        e, fo = res.energy_forces(f, base.cell, base.species, base.hirshfeld, forces=True)
+        refreshed.append(res.stats()["sites_refreshed"])
+        fresh = lm.LMBD(base.table, p, 12, 6)
+        e0, f0 = fresh.energy_forces(f, base.cell, base.species, base.hirshfeld, forces=True)
+        assert np.array_equal(res.site_counts(s.n_atoms)[:, :3], fresh.site_counts(s.n_atoms)[:, :3])
+        assert torch.equal(e, e0)
+        assert (fo - f0).abs().max().item() < 1e-12
+        fresh.close()
+    assert refreshed == [0, 1, 1, 1, 0]
