@@ -91,7 +91,8 @@ struct Ctx {
   std::vector<Counts> counts_h;
   std::vector<long long> offs_h;
   std::vector<int> order1_h, order3_h;
-  DevBuf* whole_bufs[48] = {};
+  static constexpr int kMaxWhole = 64;
+  DevBuf* whole_bufs[kMaxWhole] = {};
   int n_whole = 0;
   Ctx() {
     DevBuf* l[] = {&table_d, &pos_d, &species_d, &nu_d, &weights_d, &out_e_d, &out_f_d, &abar, &sig, &rvdw,
@@ -99,6 +100,7 @@ struct Ctx {
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
                    &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw, &cfit, &lam, &gl64,
                    &fb, &fb_flag, &lu, &theta_f, &theta_out, &site_img, &wrap, &ref_pos, &ref_spec};
+    static_assert(sizeof(l) / sizeof(l[0]) <= kMaxWhole, "whole-structure buffer list exceeds its array");
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
   size_t whole_bytes() const {
