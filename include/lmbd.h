@@ -123,6 +123,8 @@ typedef struct {
                               its FP64 refinement did not converge                              */
   int sites_refreshed;     /* 1 if the call refreshed resident site lists (lmbd_set_verlet_skin)
                               instead of building them                                         */
+  int reused_forward;      /* 1 if lmbd_forces_kept ran the reverse sweep on the kept forward
+                              state instead of a whole call                                    */
   long long spectral_flags; /* (centre, frequency) terms whose spectral proxy reached 1: with
                               M = floor(n_max / 2) >= 2, |G^M e_k|^2 >= |G^(M-1) e_k|^2 (the
                               k-block traces Tr[G^2M]_kk and Tr[G^(2M-2)]_kk); never set when
@@ -163,6 +165,25 @@ int lmbd_energy_forces_weighted(lmbd_ctx* ctx, int n_atoms, const double* positi
                                 const double* cell, const int* species,
                                 const double* hirshfeld, const double* energy_weights,
                                 double* energies, double* forces, void* stream);
+
+/* Energies now, forces later (a reverse-mode autograd: forward, then backward with the upstream
+ * gradient as weights).  lmbd_energy_keep computes the energies like lmbd_energy_forces without
+ * forces, but lays the workspaces out for forces and keeps the forward state (site lists, SCS
+ * factors and solutions, T_LR, Krylov blocks, pair coefficients) on the device.
+ * lmbd_forces_kept then gives forces = -d(sum_k w_k E_k)/dR for weights w (NULL = ones) by the
+ * reverse sweep alone on that state (the adjoint of Sec. III.D's derivative pieces, exact), when
+ * the state is there: the context's last call was lmbd_energy_keep for the same atom count, its
+ * state fitted the device as one wave (see lmbd_set_memory_budget), and the positions and species
+ * are the same (compared on the device; the cell and Hirshfeld ratios must be the same too: the
+ * caller's promise).  Otherwise, or after another call on the context, lmbd_forces_kept makes a
+ * whole lmbd_energy_forces_weighted call: the forces are right either way, and
+ * lmbd_stats.reused_forward tells which happened.  The kept state serves one reverse sweep.
+ * Arguments as lmbd_energy_forces_weighted; energies of lmbd_forces_kept are not written.      */
+int lmbd_energy_keep(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell,
+                     const int* species, const double* hirshfeld, double* energies, void* stream);
+int lmbd_forces_kept(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell,
+                     const int* species, const double* hirshfeld, const double* energy_weights,
+                     double* forces, void* stream);
 
 /* Launch mode: LMBD_LAUNCH_BATCHED (default) processes all atoms in each
  * kernel launch; LMBD_LAUNCH_PER_ATOM launches every per-atom kernel once per

@@ -33,6 +33,8 @@ void raise_smem_limit(const void* func, size_t bytes) {
 
 namespace {
 
+constexpr int LMBD_ESTALE = -1;   // internal: the kept forward state does not match the inputs
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -58,6 +60,11 @@ struct Ctx {
   int paper_forces = 0;            // force model (lmbd_set_force_model)
   int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
   int spectral_fail = 0;           // lmbd_set_spectral_check: return LMBD_CATASTROPHE when flagged
+  // forward state kept for a reverse sweep (lmbd_energy_keep / lmbd_forces_kept)
+  int split = 0;
+  bool kept_valid = false;
+  int kept_n = 0;
+  DevBuf kept_pos, kept_spec;
   int theta_sample = -1;           // paper forces with the fitted integrand: the sample of this pass
   // resident site lists (lmbd_set_verlet_skin): candidates within the list radius + skin of the
   // reference frame, refreshed while no atom has moved by half the skin
@@ -99,7 +106,7 @@ struct Ctx {
                    &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
                    &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw, &cfit, &lam, &gl64,
-                   &fb, &fb_flag, &lu, &theta_f, &theta_out, &site_img, &wrap, &ref_pos, &ref_spec};
+                   &fb, &fb_flag, &lu, &theta_f, &theta_out, &site_img, &wrap, &ref_pos, &ref_spec, &kept_pos, &kept_spec};
     static_assert(sizeof(l) / sizeof(l[0]) <= kMaxWhole, "whole-structure buffer list exceeds its array");
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
@@ -471,7 +478,13 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   // the fit nodes of the fitted integrand
   const int nf = c->fit_nodes ? c->fit_nodes + 1 : c->n_freq;
   const int nq = nf + 1;
-  const bool forces = f_out != nullptr;
+  // split: 0 a whole call; 1 (lmbd_energy_keep) the forward passes with the layout of a forces
+  // call, the state kept for a later reverse sweep; 2 (lmbd_forces_kept) the reverse sweep alone
+  // on that state, for the same inputs
+  const int split = c->split;
+  const bool reverse_only = split == 2;
+  const bool forces = f_out != nullptr || split == 1;
+  if (!reverse_only) c->kept_valid = false;   // the forward state is about to be overwritten
   int launches = 0;
 
   // ---- inputs ---------------------------------------------------------------------------
@@ -682,10 +695,21 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     }
   };
   mark(LMBD_PHASE_NEIGHBORS);
+  if (reverse_only) {   // the kept forward state must belong to these positions and species
+    w.site_cap = c->site_cap;
+    w.site_atom = (int*)c->site_atom.p;
+    w.site_x = (double*)c->site_x.p;
+    w.site_img = (int*)c->site_img.p;
+    CK(cudaMemsetAsync(w.status, 0, sizeof(int) * 4, s));
+    launch_skin_check(w, (const double*)c->kept_pos.p, (const int*)c->kept_spec.p, 1e-300, w.status + 3, s);
+    CK(cudaMemcpyAsync(c->status_h, w.status + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*c->status_h != 0) return LMBD_ESTALE;
+  }
   // resident site lists: a frame of the same structure (atom count, cell, species) whose atoms
   // all moved by less than half the skin since the lists were built refreshes them in place
   bool refresh = false;
-  if (c->skin > 0.0 && c->ref_valid && c->ref_n == N && c->ref_periodic == (cell ? 1 : 0) &&
+  if (!reverse_only && c->skin > 0.0 && c->ref_valid && c->ref_n == N && c->ref_periodic == (cell ? 1 : 0) &&
       (!cell || memcmp(c->ref_cell, g.cell, sizeof(c->ref_cell)) == 0) && c->site_atom.p) {
     w.site_cap = c->site_cap;
     CK(cudaMemsetAsync(w.status, 0, sizeof(int) * 4, s));
@@ -696,8 +720,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     refresh = *c->status_h == 0;
     ++launches;
   }
-  if (!refresh) c->ref_valid = false;   // the lists are rebuilt below; valid again on success
-  for (int attempt = 0; attempt < 4; ++attempt) {
+  if (!refresh && !reverse_only) c->ref_valid = false;   // rebuilt below; valid again on success
+  for (int attempt = 0; attempt < 4 && !reverse_only; ++attempt) {
     TRY(ensure(c->site_atom, sizeof(int) * (size_t)N * c->site_cap));
     TRY(ensure(c->site_x, sizeof(double) * 3 * (size_t)N * c->site_cap));
     TRY(ensure(c->site_img, sizeof(int) * 3 * (size_t)N * c->site_cap));
@@ -732,7 +756,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   }
   phase_launch[LMBD_PHASE_NEIGHBORS] = launches;
   c->stats.sites_refreshed = refresh ? 1 : 0;
-  if (c->skin > 0.0 && !refresh) {   // the lists were built for this frame: it is the reference
+  if (c->skin > 0.0 && !refresh && !reverse_only) {   // the lists were built for this frame: it is the reference
     TRY(ensure(c->ref_pos, sizeof(double) * 3 * (size_t)N));
     TRY(ensure(c->ref_spec, sizeof(int) * (size_t)N));
     CK(cudaMemcpyAsync(c->ref_pos.p, w.pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
@@ -752,11 +776,13 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   w.lu_slot = 9LL * max_n1 * max_n1;
   TRY(ensure(c->lu, sizeof(double) * (size_t)lu_blocks * (size_t)w.lu_slot));
   w.lu = (double*)c->lu.p;
-  c->counts_h.resize(N);
-  c->offs_h.resize((size_t)O_COUNT * (N + 1));
-  CK(cudaMemcpyAsync(c->counts_h.data(), w.counts, sizeof(Counts) * N, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(c->offs_h.data(), ob, sizeof(long long) * O_COUNT * (N + 1), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  if (!reverse_only) {   // the reverse sweep reuses the host copies of the kept forward call
+    c->counts_h.resize(N);
+    c->offs_h.resize((size_t)O_COUNT * (N + 1));
+    CK(cudaMemcpyAsync(c->counts_h.data(), w.counts, sizeof(Counts) * N, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->offs_h.data(), ob, sizeof(long long) * O_COUNT * (N + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
   const Offs o{c->offs_h.data(), N};
 
   // ---- whole-structure arrays -------------------------------------------------------------
@@ -848,7 +874,11 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       for (size_t i = 0; i + 1 < cuts.size(); ++i) m = std::max(m, (size_t)f(cuts[i], cuts[i + 1]));
       return m;
     };
-    if (S1all + std::max(S2all, X1all) <= avail) {
+    if (reverse_only) {   // the kept forward call ran as one wave with resident stage-1 arrays
+      cutA = cutC = cut2 = {0, N};
+      R1 = S1all;
+      arena_need = 0;
+    } else if (S1all + std::max(S2all, X1all) <= avail) {
       cutA = cutC = cut2 = {0, N};
       R1 = S1all;
       arena_need = S1all + std::max(S2all, X1all);
@@ -868,7 +898,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       cutC = cutA;
       arena_need = std::max(maxw(cutA, s1_and_x), maxw(cut2, s2));
     }
-    if (c->arena.bytes < arena_need || (c->mem_budget && c->arena.bytes > avail)) {
+    if (!reverse_only && (c->arena.bytes < arena_need || (c->mem_budget && c->arena.bytes > avail))) {
       release(c->arena);
       size_t want = std::min(arena_need + arena_need / 8, std::max(avail, arena_need));
       if (cudaMalloc(&c->arena.p, want) != cudaSuccess) {
@@ -933,7 +963,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   launch_pair_radial(w, dp, s);
   ++phase_launch[LMBD_PHASE_SCS];
   kmark_fwd = prof && !per_atom;
-  for (int wv = 0; wv < nwA; ++wv) TRY(stage1_forward(wv, cutA, bucketsA, orderA));
+  for (int wv = 0; wv < nwA && !reverse_only; ++wv) TRY(stage1_forward(wv, cutA, bucketsA, orderA));
   kmark_fwd = false;
 
   // ---- pass B: stage 2 (MBD energy) and its adjoint, per wave --------------------------------
@@ -955,6 +985,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
                                                     (uintptr_t)shift * sizeof(unsigned short));
       return wm;
     };
+    if (!reverse_only) {   // the forward of stage 2 (kept state in a reverse sweep)
     if (per_atom) {
       for (int cc = c0; cc < c1; ++cc) {
         launch_mbd_prepare_sized(w, dp, cc, cc + 1, max_ns, s);
@@ -1006,8 +1037,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       phase_launch[LMBD_PHASE_CHAIN] += dp.logmode ? 1 : nvec - 1;
       phase_launch[LMBD_PHASE_ENERGY] += 1;
     }
+    }   // !reverse_only
     CK(cudaGetLastError());
-    if (!forces) continue;
+    if (!forces || split == 1) continue;   // energies only, or the forward state kept
     CK(cudaMemsetAsync(w.rbar + o.at(O_S, c0), 0, sizeof(double) * o.span(O_S, c0, c1), s));
     if (per_atom) {
       for (int cc = c0; cc < c1; ++cc) {
@@ -1055,7 +1087,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
 
   // ---- pass C: SCS adjoint (needs dL/d alpha_I of every centre, complete after pass B) --------
   tally_lu = false;
-  if (forces) {
+  if (forces && split != 1) {
     mark(LMBD_PHASE_ADJ_SCS);
     for (int wv = 0; wv < nwC; ++wv) {
       const int c0 = cutC[wv], c1 = cutC[wv + 1];
@@ -1099,7 +1131,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     bool dev = is_device_ptr(e_out);
     CK(cudaMemcpyAsync(e_out, w.energies, sizeof(double) * N, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   }
-  if (forces) {
+  if (forces && f_out) {
     bool dev = is_device_ptr(f_out);
     double* dst = f_out;
     if (!dev) {
@@ -1111,6 +1143,12 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     if (!dev) CK(cudaMemcpyAsync(f_out, dst, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s));
   }
   mark(LMBD_NPHASE);
+  if (split == 1 && one_wave && persist && !per_atom) {   // inputs of the kept forward state
+    TRY(ensure(c->kept_pos, sizeof(double) * 3 * (size_t)N));
+    TRY(ensure(c->kept_spec, sizeof(int) * (size_t)N));
+    CK(cudaMemcpyAsync(c->kept_pos.p, w.pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->kept_spec.p, w.species, sizeof(int) * N, cudaMemcpyDeviceToDevice, s));
+  }
   CK(cudaMemcpyAsync(c->status_h, w.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
@@ -1150,6 +1188,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       cudaGetLastError();
     }
     S.scs_lu_systems = c->status_h[2];
+    S.reused_forward = reverse_only ? 1 : 0;
     S.spectral_flags = c->status_h[1];
     S.n_sites = c->totals_h[7];
     S.scs_pairs = c->totals_h[8];
@@ -1165,6 +1204,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   if (*c->status_h & LMBD_FLAG_TIMEOUT) return LMBD_ETIMEOUT;
   if (*c->status_h & (LMBD_FLAG_NOT_SPD | LMBD_FLAG_NOT_CONVERGED)) return LMBD_NOT_SPD;
   if (*c->status_h & LMBD_FLAG_MODEL) return LMBD_EMODEL;
+  if (split == 1 && one_wave && persist && !per_atom) {
+    c->kept_valid = true;
+    c->kept_n = N;
+  }
   if (c->spectral_fail && c->status_h[1] > 0) return LMBD_CATASTROPHE;
   return LMBD_OK;
 }
@@ -1288,6 +1331,45 @@ int lmbd_energy_forces_weighted(lmbd_ctx* ctx, int n_atoms, const double* positi
                      (cudaStream_t)stream);
   if (st != LMBD_OK) cudaGetLastError();
   return st;
+}
+
+int lmbd_energy_keep(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell, const int* species,
+                     const double* hirshfeld, double* energies, void* stream) {
+  if (!ctx || n_atoms < 0) return LMBD_EINVAL;
+  if (n_atoms > 0 && (!positions || !species || !hirshfeld)) return LMBD_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.paper_forces && c.fit_nodes) {   // the fitted force integrand needs its own passes
+    c.kept_valid = false;
+    return lmbd_energy_forces(ctx, n_atoms, positions, cell, species, hirshfeld, energies, nullptr, stream);
+  }
+  c.split = c.logmode || c.launch_mode == LMBD_LAUNCH_PER_ATOM ? 0 : 1;
+  int st = run(&c, n_atoms, positions, cell, species, hirshfeld, nullptr, energies, nullptr, (cudaStream_t)stream);
+  c.split = 0;
+  if (st != LMBD_OK) {
+    c.kept_valid = false;
+    cudaGetLastError();
+  }
+  return st;
+}
+
+int lmbd_forces_kept(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell, const int* species,
+                     const double* hirshfeld, const double* energy_weights, double* forces, void* stream) {
+  if (!ctx || n_atoms < 0 || (n_atoms > 0 && !forces)) return LMBD_EINVAL;
+  if (n_atoms > 0 && (!positions || !species || !hirshfeld)) return LMBD_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.kept_valid && c.kept_n == n_atoms && n_atoms > 0) {
+    c.split = 2;
+    int st = run(&c, n_atoms, positions, cell, species, hirshfeld, energy_weights, nullptr, forces,
+                 (cudaStream_t)stream);
+    c.split = 0;
+    c.kept_valid = false;   // the reverse sweep overwrites the stage-2 arrays
+    if (st != LMBD_ESTALE) {
+      if (st != LMBD_OK) cudaGetLastError();
+      return st;
+    }
+  }
+  return lmbd_energy_forces_weighted(ctx, n_atoms, positions, cell, species, hirshfeld, energy_weights, nullptr,
+                                     forces, stream);
 }
 
 int lmbd_energy_forces(lmbd_ctx* ctx, int n_atoms, const double* positions, const double* cell,
@@ -1447,6 +1529,7 @@ int lmbd_release_workspace(lmbd_ctx* ctx) {
   release(c.arena);
   c.last_n = 0;
   c.ref_valid = false;
+  c.kept_valid = false;
   return LMBD_OK;
 }
 

@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("waves_scs", ctypes.c_int), ("waves_mbd", ctypes.c_int), ("scs_recomputed", ctypes.c_int),
                 ("scs_pairs", ctypes.c_longlong), ("scs_adjacency", ctypes.c_longlong),
                 ("ms_kernel", ctypes.c_double * 2), ("scs_lu_systems", ctypes.c_longlong),
-                ("sites_refreshed", ctypes.c_int), ("spectral_flags", ctypes.c_longlong)]
+                ("sites_refreshed", ctypes.c_int), ("reused_forward", ctypes.c_int),
+                ("spectral_flags", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -86,6 +87,8 @@ def lib() -> ctypes.CDLL:
                                   ctypes.c_int, ctypes.POINTER(_P)]
         L.lmbd_energy_forces.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
         L.lmbd_energy_forces_weighted.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]
+        L.lmbd_energy_keep.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+        L.lmbd_forces_kept.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
         L.lmbd_set_launch_mode.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_profiling.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_precision.argtypes = [_P, ctypes.c_int]
@@ -108,6 +111,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_get_stats.argtypes = [_P, ctypes.POINTER(Stats)]
         L.lmbd_destroy.argtypes = [_P]
         for f in ("lmbd_default_params", "lmbd_create", "lmbd_energy_forces", "lmbd_energy_forces_weighted",
+                  "lmbd_energy_keep", "lmbd_forces_kept",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_mma_path", "lmbd_set_wait_budget", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
                   "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_set_spectral_check",
                   "lmbd_set_log_mode", "lmbd_set_verlet_skin",
@@ -286,6 +290,42 @@ class LMBD:
         del k1, k2, k3, k4, k5
         return e, f
 
+    def energy_keep(self, positions, cell, species, hirshfeld, stream=None):
+        """Energies (lmbd_energy_keep), keeping the forward state for forces_kept."""
+        torch = _torch()
+        dev = positions.device if isinstance(positions, torch.Tensor) else torch.device("cpu")
+        n = int(positions.shape[0])
+        pp, k1 = _as_arg(positions, torch.float64)
+        cp, k2 = _as_arg(cell, torch.float64)
+        sp, k3 = _as_arg(species, torch.int32)
+        hp, k4 = _as_arg(hirshfeld, torch.float64)
+        e = torch.empty(n, dtype=torch.float64, device=dev)
+        st = _stream_ptr(stream, dev)
+        status = lib().lmbd_energy_keep(self._h, n, pp, cp, sp, hp, ctypes.c_void_p(e.data_ptr()), st)
+        self.last_status = status
+        _check(status, "lmbd_energy_keep")
+        del k1, k2, k3, k4
+        return e
+
+    def forces_kept(self, positions, cell, species, hirshfeld, weights=None, stream=None):
+        """-d(sum_k w_k E_k)/dR (lmbd_forces_kept): the reverse sweep on the kept forward state
+        when it matches these inputs, else a whole call."""
+        torch = _torch()
+        dev = positions.device if isinstance(positions, torch.Tensor) else torch.device("cpu")
+        n = int(positions.shape[0])
+        pp, k1 = _as_arg(positions, torch.float64)
+        cp, k2 = _as_arg(cell, torch.float64)
+        sp, k3 = _as_arg(species, torch.int32)
+        hp, k4 = _as_arg(hirshfeld, torch.float64)
+        wp, k5 = _as_arg(weights, torch.float64)
+        f = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        st = _stream_ptr(stream, dev)
+        status = lib().lmbd_forces_kept(self._h, n, pp, cp, sp, hp, wp, ctypes.c_void_p(f.data_ptr()), st)
+        self.last_status = status
+        _check(status, "lmbd_forces_kept")
+        del k1, k2, k3, k4, k5
+        return f
+
     def autotune(self, positions, cell, species, hirshfeld, forces: bool = True, stream=None) -> int:
         """Pick the SCS bucket width for this kind of structure (lmbd_autotune); returns it."""
         torch = _torch()
@@ -336,13 +376,15 @@ def _make_energy_function():
     class LmbdEnergy(torch.autograd.Function):
         """Per-atom lMBD energies with the hand-written adjoint as backward.
 
-        forward(positions, model, cell, species, hirshfeld) -> E (N); backward uses
-        the library's weighted forces: dL/dR = -F(w = dL/dE).
+        forward(positions, model, cell, species, hirshfeld) -> E (N) with the forward state kept
+        on the device; backward runs the library's reverse sweep on it for weights w = dL/dE:
+        dL/dR = -F(w).
         """
 
         @staticmethod
         def forward(ctx, positions, model, cell, species, hirshfeld):
-            e, _ = model.energy_forces(positions, cell, species, hirshfeld, forces=False)
+            # the library keeps the forward state (factors, T_LR, Krylov blocks) for the backward
+            e = model.energy_keep(positions.detach(), cell, species, hirshfeld)
             ctx.model = model
             ctx.save_for_backward(positions)
             ctx.extra = (cell, species, hirshfeld)
@@ -352,8 +394,8 @@ def _make_energy_function():
         def backward(ctx, grad_e):
             (positions,) = ctx.saved_tensors
             cell, species, hirshfeld = ctx.extra
-            _, f = ctx.model.energy_forces(positions, cell, species, hirshfeld, forces=True,
-                                           weights=grad_e.contiguous())
+            # the reverse sweep alone on the kept state (a whole call if it is gone)
+            f = ctx.model.forces_kept(positions.detach(), cell, species, hirshfeld, weights=grad_e.contiguous())
             return -f, None, None, None, None
 
     return LmbdEnergy

@@ -325,8 +325,36 @@ def test_autograd_function(lm, box110):
     e = lm.lmbd_energy(pos, model, cell, sp, nu)
     w = torch.linspace(-1, 2, s.n_atoms, device="cuda", dtype=torch.float64)
     (g,) = torch.autograd.grad((e * w).sum(), pos)
+    assert model.stats()["reused_forward"] == 1       # backward ran the reverse sweep alone
     _, f = model.energy_forces(pos.detach(), cell, sp, nu, forces=True, weights=w)
     assert (g + f).abs().max().item() < 1e-13
+    e2, _ = model.energy_forces(pos.detach(), cell, sp, nu, forces=False)
+    assert torch.equal(e.detach(), e2)
+
+
+def test_kept_forward_state_falls_back_when_stale(lm, box110):
+    s = box110
+    model = lm.LMBD(s.table, lm.default_params(), 12, 6)
+    pos = torch.tensor(s.positions, device="cuda")
+    cell = torch.tensor(s.cell, device="cuda")
+    sp = torch.tensor(s.species, dtype=torch.int32, device="cuda")
+    nu = torch.tensor(s.hirshfeld, device="cuda")
+    w = torch.linspace(0.5, 1.5, s.n_atoms, device="cuda", dtype=torch.float64)
+    _, f_ref = model.energy_forces(pos, cell, sp, nu, forces=True, weights=w)
+    model.energy_keep(pos, cell, sp, nu)
+    f = model.forces_kept(pos, cell, sp, nu, weights=w)
+    assert model.stats()["reused_forward"] == 1 and (f - f_ref).abs().max().item() < 1e-12
+    # the kept state serves one reverse sweep: a second one is a whole call, same forces
+    f2 = model.forces_kept(pos, cell, sp, nu, weights=w)
+    assert model.stats()["reused_forward"] == 0 and (f2 - f_ref).abs().max().item() < 1e-12
+    # other positions than the kept ones: a whole call for the new positions
+    model.energy_keep(pos, cell, sp, nu)
+    moved = pos.clone()
+    moved[3, 1] += 0.01
+    _, f_moved = model.energy_forces(moved, cell, sp, nu, forces=True, weights=w)
+    model.energy_keep(pos, cell, sp, nu)
+    f3 = model.forces_kept(moved, cell, sp, nu, weights=w)
+    assert model.stats()["reused_forward"] == 0 and (f3 - f_moved).abs().max().item() < 1e-12
 
 
 def test_fp64_product_mode_matches_oracle(lm, box110, box110_ref):
