@@ -963,6 +963,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   launch_pair_radial(w, dp, s);
   ++phase_launch[LMBD_PHASE_SCS];
   kmark_fwd = prof && !per_atom;
+  if (reverse_only)   // the kept stage-1 arrays: their pointers, no work
+    L.stage1(o, cutA[0], cutA[1], arena, &w);
   for (int wv = 0; wv < nwA && !reverse_only; ++wv) TRY(stage1_forward(wv, cutA, bucketsA, orderA));
   kmark_fwd = false;
 
