@@ -19,6 +19,7 @@
 
 #include "../../include/lmbd.h"
 #include "lmbd_internal.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 void raise_smem_limit(const void* func, size_t bytes) {
   static std::mutex mtx;
@@ -34,6 +35,19 @@ void raise_smem_limit(const void* func, size_t bytes) {
 namespace {
 
 constexpr int LMBD_ESTALE = -1;   // internal: the kept forward state does not match the inputs
+
+// One NVTX range open at a time (the current phase of a call); closed when the call returns.
+struct NvtxPhase {
+  bool open = false;
+  void enter(const char* name) {
+    if (open) nvtxRangePop();
+    open = name != nullptr;
+    if (open) nvtxRangePushA(name);
+  }
+  ~NvtxPhase() {
+    if (open) nvtxRangePop();
+  }
+};
 
 struct DevBuf {
   void* p = nullptr;
@@ -688,7 +702,15 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   bool prof = prof_req;   // per-phase events only when every stage runs as one wave
   int phase_launch[LMBD_NPHASE] = {};
   bool marked[LMBD_NPHASE + 1] = {};
+  // phase boundaries: CUDA events when profiling, and an NVTX range per phase (host-side
+  // annotations that a profiler attaches to the launches; nearly free without one)
+  static const char* const kPhaseName[LMBD_NPHASE] = {"lmbd neighbours", "lmbd SCS", "lmbd prepare",
+                                                      "lmbd chain", "lmbd energy", "lmbd adjoint series",
+                                                      "lmbd adjoint pair", "lmbd adjoint blend",
+                                                      "lmbd SCS adjoint", "lmbd output"};
+  NvtxPhase nvtx;
   auto mark = [&](int ph) {
+    nvtx.enter(ph < LMBD_NPHASE ? kPhaseName[ph] : nullptr);
     if (prof) {
       cudaEventRecord(c->ev[ph], s);
       marked[ph] = true;
@@ -942,12 +964,14 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       phase_launch[LMBD_PHASE_SCS] += c1 - c0;
     } else {
       if (kmark_fwd) cudaEventRecord(c->kev[0], s);
+      nvtxRangePushA("lmbd SCS factor buckets");
       Fork fk(c, s, (int)bk[wv].size());
       for (size_t i = 0; i < bk[wv].size(); ++i) {
         const Bucket& b = bk[wv][i];
         launch_scs_factor(w, dp, order, b.b0, b.b1, b.n1, b.n12, fk.stream((int)i));
       }
       fk.join();
+      nvtxRangePop();
       if (kmark_fwd) cudaEventRecord(c->kev[1], s);
       phase_launch[LMBD_PHASE_SCS] += (int)bk[wv].size();
     }
@@ -1107,12 +1131,14 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         phase_launch[LMBD_PHASE_ADJ_SCS] += 2 * (c1 - c0) + 1;
       } else {
         if (prof) cudaEventRecord(c->kev[2], s);
+        nvtxRangePushA("lmbd SCS adjoint buckets");
         Fork fk(c, s, (int)bucketsC[wv].size());
         for (size_t i = 0; i < bucketsC[wv].size(); ++i) {
           const Bucket& b = bucketsC[wv][i];
           launch_scs_adjoint2(w, dp, orderC, b.b0, b.b1, b.n1, b.n12, fk.stream((int)i));
         }
         fk.join();
+        nvtxRangePop();
         if (prof) cudaEventRecord(c->kev[3], s);
         launch_scs_lu_adjoint(w, dp, lu_blocks, c0, c1, max_n1, max_n12, s);
         launch_scs_site_reduce(w, dp, c0, c1, s);
