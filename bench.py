@@ -28,8 +28,8 @@ METRIC = "atoms/s for lMBD energy+forces on 1 GB300 (batched vs per-atom launch)
 FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (DFMA and DMMA), profiling recipe table
 FP32_PEAK_TFLOPS = 80.5          # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (unit counts and clock)
 # DRAM bytes (read + write) of the SCS factor kernel (k_scs_factor alone) per atom: ncu on the
-# 512-atom box, profiles/scs_traffic_box512.md; scaled to a launch by atoms / launches
-SCS_FACTOR_DRAM_BYTES_PER_ATOM = 1.650e6
+# 512-atom box, profiles/ncu_scs_factor_box512.md; scaled to a launch by atoms / launches
+SCS_FACTOR_DRAM_BYTES_PER_ATOM = 1.189e6
 PRECISION = ("chain products: 6-digit (energy blocks) / 5-digit (adjoint-only blocks) bf16 Ozaki slices "
              "of the FP64 operands, exact integer recombination, FP64 scaling; adjoint pair product: "
              "5-digit slices; SCS: FP32 Cholesky and solves with FP64 iterative refinement to FP64 "
