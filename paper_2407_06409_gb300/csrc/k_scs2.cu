@@ -422,81 +422,59 @@ __device__ void blockinv32(const float* A, int n, const float* sinv, float* binv
   }
 }
 
-// y (n x 3, FP32, shared) <- (L L^T)^-1 y with binv the inverses of the 16 x 16 diagonal
-// blocks; z (n x 3) is scratch.  Per block row: the off-diagonal part as 16 rows x 16 partial
-// sums (it updates only this block's right-hand side), then one parallel product with the
-// block inverse written to the other buffer, so two barriers per block row suffice.
-__device__ void solve32_packed(const float* L, int n, const float* binv, float* y, float* z) {
-  const int tid = threadIdx.x;
-  const int r = tid >> 4, s = tid & 15;
-  // forward: z = L^-1 y
-  for (int b0 = 0; b0 < n; b0 += CB) {
-    const int bb = min(CB, n - b0);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    if (r < bb) {
-      const float* row = L + packed_idx(b0 + r, 0);
-      for (int k = s; k < b0; k += 16) {
-        const float l = row[k];
-        a0 += l * z[3 * k];
-        a1 += l * z[3 * k + 1];
-        a2 += l * z[3 * k + 2];
+
+// y (n x 3, FP32, shared) <- (L L^T)^-1 y with binv the inverses of the 16 x 16 diagonal blocks,
+// a blocked substitution with one warp per right-hand side column: warps 0..2 each solve their
+// column with warp-level
+// synchronisation only (a block row: half-warp partial sums of its 16 rows over the solved part,
+// combined across the halves with a shuffle, then the product with the inverse diagonal block by
+// shuffles), so the substitution needs no block barrier; z (n x 3) is scratch.  The caller's
+// writes to y must be visible (a block barrier before); the result is visible after the final one.
+__device__ void solve32_warp(const float* L, int n, const float* binv, float* y, float* z) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 3) {
+    const int c = warp, r = lane & 15, h = lane >> 4;
+    // forward: z = L^-1 y
+    for (int b0 = 0; b0 < n; b0 += CB) {
+      const int bb = min(CB, n - b0);
+      const float* inv = binv + (b0 / CB) * CBP;
+      float t = 0.f;
+      if (r < bb) {
+        const float* row = L + packed_idx(b0 + r, 0);
+        for (int k = h; k < b0; k += 2) t += row[k] * z[3 * k + c];
       }
-    }
+      t += __shfl_xor_sync(0xffffffffu, t, 16);
+      const float v = r < bb ? y[3 * (b0 + r) + c] - t : 0.f;
+      float acc = 0.f;
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      a0 += __shfl_down_sync(0xffffffffu, a0, o, 16);
-      a1 += __shfl_down_sync(0xffffffffu, a1, o, 16);
-      a2 += __shfl_down_sync(0xffffffffu, a2, o, 16);
-    }
-    if (s == 0 && r < bb) {
-      y[3 * (b0 + r)] -= a0;
-      y[3 * (b0 + r) + 1] -= a1;
-      y[3 * (b0 + r) + 2] -= a2;
-    }
-    __syncthreads();
-    const float* inv = binv + (b0 / CB) * CBP;
-    if (tid < 3 * bb) {
-      const int i = tid / 3, c = tid % 3;
-      float v = 0.f;
-      for (int u = 0; u <= i; ++u) v += inv[pidx16(i, u)] * y[3 * (b0 + u) + c];
-      z[3 * b0 + tid] = v;
-    }
-    __syncthreads();
-  }
-  // backward: y = L^-T z
-  const int nblk = (n + CB - 1) / CB;
-  for (int blk = nblk - 1; blk >= 0; --blk) {
-    const int b0 = blk * CB, bb = min(CB, n - b0), b1 = b0 + bb;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    if (r < bb) {
-      for (int k = b1 + s; k < n; k += 16) {
-        const float l = L[packed_idx(k, b0 + r)];
-        a0 += l * y[3 * k];
-        a1 += l * y[3 * k + 1];
-        a2 += l * y[3 * k + 2];
+      for (int u = 0; u < CB; ++u) {
+        const float vu = __shfl_sync(0xffffffffu, v, u);
+        if (u <= r && r < bb) acc += inv[pidx16(r, u)] * vu;
       }
+      if (h == 0 && r < bb) z[3 * (b0 + r) + c] = acc;
+      __syncwarp();
     }
+    // backward: y = L^-T z
+    const int nblk = (n + CB - 1) / CB;
+    for (int blk = nblk - 1; blk >= 0; --blk) {
+      const int b0 = blk * CB, bb = min(CB, n - b0), b1 = b0 + bb;
+      const float* inv = binv + blk * CBP;
+      float t = 0.f;
+      if (r < bb)
+        for (int k = b1 + h; k < n; k += 2) t += L[packed_idx(k, b0 + r)] * y[3 * k + c];
+      t += __shfl_xor_sync(0xffffffffu, t, 16);
+      const float v = r < bb ? z[3 * (b0 + r) + c] - t : 0.f;
+      float acc = 0.f;
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      a0 += __shfl_down_sync(0xffffffffu, a0, o, 16);
-      a1 += __shfl_down_sync(0xffffffffu, a1, o, 16);
-      a2 += __shfl_down_sync(0xffffffffu, a2, o, 16);
+      for (int u = 0; u < CB; ++u) {
+        const float vu = __shfl_sync(0xffffffffu, v, u);
+        if (u >= r && u < bb) acc += inv[pidx16(u, r)] * vu;
+      }
+      if (h == 0 && r < bb) y[3 * (b0 + r) + c] = acc;
+      __syncwarp();
     }
-    if (s == 0 && r < bb) {
-      z[3 * (b0 + r)] -= a0;
-      z[3 * (b0 + r) + 1] -= a1;
-      z[3 * (b0 + r) + 2] -= a2;
-    }
-    __syncthreads();
-    const float* inv = binv + blk * CBP;
-    if (tid < 3 * bb) {
-      const int i = tid / 3, c = tid % 3;
-      float v = 0.f;
-      for (int u = i; u < bb; ++u) v += inv[pidx16(u, i)] * z[3 * (b0 + u) + c];
-      y[3 * b0 + tid] = v;
-    }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -585,7 +563,7 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
   const int N1 = 3 * n1, tid = threadIdx.x;
   for (int e = tid; e < 3 * N1; e += blockDim.x) sm.y[e] = (float)sm.rhs[e];
   __syncthreads();
-  solve32_packed(sm.A, N1, sm.binv, sm.y, sm.z);
+  solve32_warp(sm.A, N1, sm.binv, sm.y, sm.z);
   for (int e = tid; e < 3 * N1; e += blockDim.x) sm.x[e] = (double)sm.y[e];
   __syncthreads();
   // the residual d - B x0 of the FP32 solution x0 = y, in float-float arithmetic on the FP32
@@ -597,7 +575,7 @@ __device__ int scs2_refine(const Work& w, const DevParams& p, int n1, long long 
   double prev = 0.0;
   int it = 0;
   for (; it < 12; ++it) {
-    solve32_packed(sm.A, N1, sm.binv, sm.y, sm.z);
+    solve32_warp(sm.A, N1, sm.binv, sm.y, sm.z);
     double dmax = 0.0, xmax = 0.0;
     for (int e = tid; e < 3 * N1; e += blockDim.x) {
       double dlt = (double)sm.y[e];
