@@ -530,28 +530,46 @@ __device__ inline Scs2Smem scs2_carve(unsigned char* base, int max_n1, int max_n
 // (~1e-7 of x) it updates the residual of x + delta to FP64 rounding.
 __device__ void scs2_residual_update(const Work& w, const DevParams& p, int n1, long long offp, long long offa,
                                      long long rbase, int q, Scs2Smem& sm) {
-  for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
-    const int i = e / 3, c = e % 3;
-    const ff ia = ff_from_double(sm.iab[i]);
-    ff a0 = ff_scale(ia, sm.y[9 * i + c]), a1 = ff_scale(ia, sm.y[9 * i + 3 + c]),
-       a2 = ff_scale(ia, sm.y[9 * i + 6 + c]);
-    const int b = w.arow[rbase + i], en = w.arow[rbase + i + 1];
-    for (int t = b; t < en; ++t) {
-      const int j = w.adj[2 * (offa + t)];
-      const long long pq = offp + w.adj[2 * (offa + t) + 1];
-      const float2* gf = w.pr_gff + 6 * pq;
-      const float2* rf = w.pr_rad_ff + 2 * (pq * p.nqs + q);
-      const ff rx = ff_make(gf[0].x, gf[0].y), ry = ff_make(gf[1].x, gf[1].y), rz = ff_make(gf[2].x, gf[2].y);
-      const ff fa = ff_make(rf[0].x, rf[0].y), fb = ff_make(rf[1].x, rf[1].y);
-      const float d0 = sm.y[9 * j + c], d1 = sm.y[9 * j + 3 + c], d2 = sm.y[9 * j + 6 + c];
-      const ff bu = ff_mul(fb, ff_add(ff_add(ff_scale(rx, d0), ff_scale(ry, d1)), ff_scale(rz, d2)));
-      a0 = ff_add(a0, ff_add(ff_scale(fa, d0), ff_mul(bu, rx)));
-      a1 = ff_add(a1, ff_add(ff_scale(fa, d1), ff_mul(bu, ry)));
-      a2 = ff_add(a2, ff_add(ff_scale(fa, d2), ff_mul(bu, rz)));
+  // two threads per (coupled site i, right-hand side c), neighbouring lanes, each summing half of
+  // the adjacency row; the halves are combined with a shuffle in a fixed order
+  const int items = 6 * n1;
+  for (int base = 0; base < items; base += blockDim.x) {
+    const int e = base + threadIdx.x;
+    const bool act = e < items;
+    const int i = act ? e / 6 : 0, c = act ? (e >> 1) % 3 : 0, half = e & 1;
+    ff a0 = ff_make(0.f, 0.f), a1 = a0, a2 = a0;
+    if (act) {
+      if (half == 0) {
+        const ff ia = ff_from_double(sm.iab[i]);
+        a0 = ff_scale(ia, sm.y[9 * i + c]);
+        a1 = ff_scale(ia, sm.y[9 * i + 3 + c]);
+        a2 = ff_scale(ia, sm.y[9 * i + 6 + c]);
+      }
+      const int b0 = w.arow[rbase + i], en0 = w.arow[rbase + i + 1];
+      const int mid = b0 + (en0 - b0 + 1) / 2;
+      const int b = half == 0 ? b0 : mid, en = half == 0 ? mid : en0;
+      for (int t = b; t < en; ++t) {
+        const int j = w.adj[2 * (offa + t)];
+        const long long pq = offp + w.adj[2 * (offa + t) + 1];
+        const float2* gf = w.pr_gff + 6 * pq;
+        const float2* rf = w.pr_rad_ff + 2 * (pq * p.nqs + q);
+        const ff rx = ff_make(gf[0].x, gf[0].y), ry = ff_make(gf[1].x, gf[1].y), rz = ff_make(gf[2].x, gf[2].y);
+        const ff fa = ff_make(rf[0].x, rf[0].y), fb = ff_make(rf[1].x, rf[1].y);
+        const float d0 = sm.y[9 * j + c], d1 = sm.y[9 * j + 3 + c], d2 = sm.y[9 * j + 6 + c];
+        const ff bu = ff_mul(fb, ff_add(ff_add(ff_scale(rx, d0), ff_scale(ry, d1)), ff_scale(rz, d2)));
+        a0 = ff_add(a0, ff_add(ff_scale(fa, d0), ff_mul(bu, rx)));
+        a1 = ff_add(a1, ff_add(ff_scale(fa, d1), ff_mul(bu, ry)));
+        a2 = ff_add(a2, ff_add(ff_scale(fa, d2), ff_mul(bu, rz)));
+      }
     }
-    sm.rhs[9 * i + c] -= ff_to_double(a0);
-    sm.rhs[9 * i + 3 + c] -= ff_to_double(a1);
-    sm.rhs[9 * i + 6 + c] -= ff_to_double(a2);
+    const ff o0 = ff_make(__shfl_xor_sync(0xffffffffu, a0.hi, 1), __shfl_xor_sync(0xffffffffu, a0.lo, 1));
+    const ff o1 = ff_make(__shfl_xor_sync(0xffffffffu, a1.hi, 1), __shfl_xor_sync(0xffffffffu, a1.lo, 1));
+    const ff o2 = ff_make(__shfl_xor_sync(0xffffffffu, a2.hi, 1), __shfl_xor_sync(0xffffffffu, a2.lo, 1));
+    if (act && half == 0) {
+      sm.rhs[9 * i + c] -= ff_to_double(ff_add(a0, o0));
+      sm.rhs[9 * i + 3 + c] -= ff_to_double(ff_add(a1, o1));
+      sm.rhs[9 * i + 6 + c] -= ff_to_double(ff_add(a2, o2));
+    }
   }
 }
 
