@@ -1024,3 +1024,45 @@ def test_paper_forces_with_fitted_integrand_are_exact_for_a_dimer():
     f_fit = _dimer(3.4, table, np.array([0, 1]), nu, oracle.with_params(p, fit_nodes=6)).paper_forces()
     assert np.abs(f_quad).max() > 1e-6
     assert np.allclose(f_fit, f_quad, rtol=1e-9, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------------------
+# sparsity of T_LR from the two MBD cutoffs (Sec. III.A, Fig. sparsity): the central row and
+# column couple the sites within r_MBD,1, every other pair only within r_MBD,2
+# ---------------------------------------------------------------------------------------
+def test_t_lr_block_pattern_follows_the_two_cutoffs():
+    s = inputs.box(120, seed=9)
+    p = oracle.Params(r_scs=3.0, r_mbd1=6.0, r_mbd2=2.5, r_sphere=0.0, r_buf=0.5)
+    sysm = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, p)
+    ab, sg, rv, a0, r0 = sysm.free()
+    k = 7
+    st = sysm.sites(k)
+    assert st.ns > 100                                     # sphere r_MBD,1 + r_MBD,2 = 8.5 A
+    x = oracle.site_positions(torch.as_tensor(s.positions), s.cell, st, k)[:st.ns]
+    at0 = torch.full((st.ns,), 8.0, dtype=DT)
+    T = oracle.t_lr(x, at0, a0[st.atom[:st.ns]], r0[st.atom[:st.ns]], p).numpy()
+    nz = np.abs(T.reshape(st.ns, 3, st.ns, 3)).max(axis=(1, 3)) > 0
+    # the rule by brute force over the site pairs, in Angstrom
+    xa = x.numpy() * BOHR
+    d = np.sqrt(((xa[:, None, :] - xa[None, :, :]) ** 2).sum(-1))
+    central = np.zeros_like(nz)
+    central[0, :] = central[:, 0] = True
+    rc = np.where(central, p.r_mbd1, p.r_mbd2)
+    want = (d < rc) & ~np.eye(st.ns, dtype=bool)
+    assert np.array_equal(nz, want)
+    # the central row reaches further than any other: every site within r_MBD,1 (about the
+    # whole K1 shell) against a few neighbours within r_MBD,2
+    assert nz[0].sum() == int(np.sum(st.r_ang[1:st.ns].numpy() < p.r_mbd1))
+    assert nz[0].sum() > 3 * nz[1:].sum(1).max()
+    assert nz.sum() < 0.25 * st.ns * st.ns
+    # the blocks switch off continuously at both cutoffs: inside the buffer of width r_b,
+    # f_LR = 3 u^2 - 2 u^3 <= 3 u^2 with u = (r_c - r) / r_b, the Fermi damping is below 1 and
+    # no element of the bare dipole tensor exceeds 2 / r^3
+    edge = want & (d > rc - p.r_buf)
+    assert edge.sum() > 10
+    blk = np.abs(T.reshape(st.ns, 3, st.ns, 3)).max(axis=(1, 3))
+    u = (rc - d) / p.r_buf
+    bound = 3 * u ** 2 * 2 / (np.maximum(d, 1e-3) / BOHR) ** 3
+    assert np.all(blk[edge] <= bound[edge] * (1 + 1e-12))
+    inner = want & (d < rc - p.r_buf)
+    assert blk[inner].min() > 0
