@@ -129,6 +129,9 @@ typedef struct {
                               M = floor(n_max / 2) >= 2, |G^M e_k|^2 >= |G^(M-1) e_k|^2 (the
                               k-block traces Tr[G^2M]_kk and Tr[G^(2M-2)]_kk); never set when
                               n_max < 4                                                       */
+  long long tlr_pairs;     /* site pairs whose T_LR block the call stored: with
+                              lmbd_set_sparse_tlr(ctx, 1) the coupled pairs, otherwise every
+                              pair of every sphere (sum of ns (ns - 1) / 2)                    */
 } lmbd_stats;
 
 /* Fill *out with the defaults r_scs = 5, r_mbd1 = r_mbd2 = r_sphere = 7,
@@ -312,6 +315,24 @@ int lmbd_set_log_mode(lmbd_ctx* ctx, int lanczos_steps);
  * returns LMBD_OK regardless; fail = 1: it returns LMBD_CATASTROPHE when the count is not zero
  * (outputs still written).  Returns LMBD_EINVAL for another value.                          */
 int lmbd_set_spectral_check(lmbd_ctx* ctx, int fail);
+
+/* Block-sparse T_LR (Sec. III.A, Fig. sparsity: the central row and column of T_LR,K couple
+ * the sites within r_MBD,1 of the central atom, every other pair only the sites within r_MBD,2
+ * of each other, so with r_MBD,2 < r_MBD,1 most blocks of a large sphere are zero).
+ * on = 0 (default): T_LR,K is stored dense per central atom (3 ns x 3 ns) and the Krylov chain
+ *   and the adjoint pair products run over all blocks (lmbd_set_precision selects their
+ *   arithmetic).
+ * on = 1: per central atom only the coupled site pairs are stored (found by an FP32 distance
+ *   test with a relative slack of 2e-4 on rc^2; a listed pair whose FP64 distance is not below
+ *   its cutoff has a zero block, as on the dense path), and the chain steps
+ *   v_{m+1} = D T_LR D v_m and the pair products M_st = P_s Q_t^T run over those pairs alone,
+ *   in float-float arithmetic (pairs of FP32 numbers, about 2^-46 relative per product) with
+ *   FP64 results; lmbd_set_precision does not apply to them.  Spheres up to 4096 sites
+ *   (LMBD_ECAPACITY beyond).  Serves the series energy and the exact forces: a call with log
+ *   mode, polynomial-fit coefficients or the paper's force model returns LMBD_EUNSUPPORTED.
+ *   lmbd_stats.tlr_pairs counts the stored pairs.
+ * Returns LMBD_EINVAL for another value of on.                                               */
+int lmbd_set_sparse_tlr(lmbd_ctx* ctx, int on);
 
 /* Force model (Sec. III.D).
  * LMBD_FORCES_EXACT (default): forces = -d(sum_k w_k E_k)/dR, the exact gradient of the

@@ -17,6 +17,7 @@
 //   dL/dT_st = sum_q D_s D_t (dL/dG)_st, contracted with dT_LR/dr and dT_LR/dS~ per pair.
 #include <algorithm>
 
+#include "ff.cuh"
 #include "lmbd_internal.cuh"
 #include "ozaki.cuh"
 #include "pair_epilogue.cuh"
@@ -35,46 +36,11 @@ __global__ void __launch_bounds__(256) k_mbd_prepare(Work w, DevParams p, int c0
   const int tid = threadIdx.x;
   const long long sbase = (long long)c * w.site_cap;
   const long long offs = w.off_s[c], offk1 = w.off_k1[c];
-  const double rscs = p.r_scs;
   for (int s = tid; s < ns; s += blockDim.x) {
     int a = w.site_atom[sbase + s];
     double x0 = w.site_x[3 * (sbase + s)], x1 = w.site_x[3 * (sbase + s) + 1], x2 = w.site_x[3 * (sbase + s) + 2];
     xs[s] = x0; xs[max_ns + s] = x1; xs[2 * max_ns + s] = x2;
-    double fs = 0.0;
-    if (s < n1 && s > 0) {
-      double u = sqrt(x0 * x0 + x1 * x1 + x2 * x2) / rscs;
-      fs = 3.0 * u * u - 2.0 * u * u * u;
-    }
-    if (!p.lorentz) {
-      for (int q = 0; q < p.nq; ++q) {
-        double aI = w.alphaI[(long long)a * p.nqs + q];
-        double at = aI;
-        if (s < n1) at = (1.0 - fs) * w.alphaK[(offk1 + s) * p.nqs + q] + fs * aI;
-        w.alphaT[(offs + s) * p.nq + q] = at;
-        w.dsq[(offs + s) * p.nq + q] = sqrt(at);
-      }
-    } else {
-      // Lorentzian model (Sec. III.C): the blend at omega = 0 and omega_ref, then
-      // alpha~(omega) = alpha~(0) / (1 + (omega/omega~)^2) with
-      // (omega/omega~)^2 = (omega/omega_ref)^2 (alpha~(0)/alpha~(omega_ref) - 1) (Eq. char-freq)
-      double ab[2];
-      for (int qs = 0; qs < 2; ++qs) {
-        const double aI = w.alphaI[(long long)a * 2 + qs];
-        ab[qs] = (s < n1) ? (1.0 - fs) * w.alphaK[(offk1 + s) * 2 + qs] + fs * aI : aI;
-      }
-      double ratio = ab[0] / ab[1];
-      if (!(ratio >= 1.0)) {   // alpha~ rises with frequency: Eq. char-freq has no real solution
-        atomicOr(w.status, LMBD_FLAG_MODEL);
-        ratio = 1.0;
-      }
-      for (int q = 0; q < p.nq; ++q) {
-        const double u = p.omega[q] / p.omega_ref;
-        const double at = ab[0] / (1.0 + u * u * (ratio - 1.0));
-        w.alphaT[(offs + s) * p.nq + q] = at;
-        w.dsq[(offs + s) * p.nq + q] = sqrt(at);
-      }
-    }
-    rt[s] = w.r0[a] * cbrt(w.alphaT[(offs + s) * p.nq] / w.a0[a]);
+    rt[s] = mbd_blend_site(w, p, s, a, n1, offs, offk1, x0, x1, x2);
   }
   __syncthreads();
   double* T = w.tlr + w.off_t[c];
@@ -90,37 +56,8 @@ __global__ void __launch_bounds__(256) k_mbd_prepare(Work w, DevParams p, int c0
     while ((i + 1) * i / 2 <= e) ++i;
     int j = e - i * (i - 1) / 2;     // i > j
     double rr[3] = {xs[j] - xs[i], xs[max_ns + j] - xs[max_ns + i], xs[2 * max_ns + j] - xs[2 * max_ns + i]};
-    double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
-    double rc = (j == 0) ? p.r_mbd1 : p.r_mbd2;
-    double blk[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    double kc[5] = {0, 0, 0, 0, 0};
-    if (r2 < rc * rc) {
-      double r = sqrt(r2);
-      double flr, dflr, f, dfr, dfs;
-      cutoff_buf(r, rc, p.r_buf, flr, dflr);
-      fermi(r, p.beta * (rt[i] + rt[j]), p.d, f, dfr, dfs);
-      double C = flr * f;
-      double ir = 1.0 / r;
-      double ir2 = ir * ir;
-      double ir3 = ir2 * ir;
-      double ir5 = ir3 * ir2;
-#pragma unroll
-      for (int al = 0; al < 3; ++al)
-#pragma unroll
-        for (int be = 0; be < 3; ++be)
-          blk[al][be] = C * (3.0 * rr[al] * rr[be] * ir5 - (al == be ? ir3 : 0.0));
-      if (w.pcoef) {
-        // d<M, T_LR>/dr = (k1 r.M.r + k2 Tr M) r + k3 M r, d<M, T_LR>/dS~ beta = k4 r.M.r + k5 Tr M
-        // (both pair blocks counted), with C = f_LR f, dC/dr, dC/dS~
-        const double dC = dflr * f + flr * dfr, CS = flr * dfs;
-        const double ir4 = ir2 * ir2, ir6 = ir4 * ir2, ir7 = ir6 * ir;
-        kc[0] = 2.0 * (3.0 * dC * ir6 - 15.0 * C * ir7);
-        kc[1] = 2.0 * (3.0 * C * ir5 - dC * ir4);
-        kc[2] = 12.0 * C * ir5;
-        kc[3] = 6.0 * p.beta * CS * ir5;
-        kc[4] = -2.0 * p.beta * CS * ir3;
-      }
-    }
+    double blk[3][3], kc[5];
+    tlr_pair_block(p, rr, (j == 0) ? p.r_mbd1 : p.r_mbd2, rt[i], rt[j], blk, w.pcoef ? kc : nullptr);
     if (w.pcoef) {
       double* pc = w.pcoef + w.off_t[c] + 8LL * (i * (i - 1) / 2 + j);
       pc[0] = rr[0]; pc[1] = rr[1]; pc[2] = rr[2];
@@ -1084,8 +1021,14 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
           double a = 0.0;
           for (int l = 1; l <= nm - 1 - j; ++l) a += ct[j + l + 1] * V0[(long long)(l - 1) * w.vstride + idx];
           long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
-          w.pmat[o] = ds * Vj[idx];
-          w.qmat[o] = ds * a;
+          if (w.qff) {   // block-sparse T_LR: the pair products run in float-float
+            const ff pv = ff_from_double(ds * Vj[idx]), qv = ff_from_double(ds * a);
+            w.pff[o] = make_float2(pv.hi, pv.lo);
+            w.qff[o] = make_float2(qv.hi, qv.lo);
+          } else {
+            w.pmat[o] = ds * Vj[idx];
+            w.qmat[o] = ds * a;
+          }
         }
     }
   }

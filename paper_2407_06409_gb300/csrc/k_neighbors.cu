@@ -433,18 +433,19 @@ void launch_neighbors(const Work& w, const DevParams& p, const Grid& g, cudaStre
 // totals: [0] sum n1, [1] sum ns, [2] sum nq N1(N1+1)/2 (packed factors, N1 = 3 n1),
 //         [3] sum (3 ns)^2, [4] max n1, [5] max ns, [6] max n12, [7] sum nt,
 //         [8] sum of SCS pairs, [9] sum of SCS adjacency entries, [10] max pairs,
+//         [11] max coupled T_LR pairs (block-sparse T_LR, 0 otherwise),
 //         [12] sum Mpad Kpad, [13] sum Mpad, [14] sum Kpad, [15] sum ns16 (sliced products)
 // ---------------------------------------------------------------------------------------
-#define OFF_T 512
+#define OFF_T 256
 __global__ void k_offsets(Work w, int nq) {
-  __shared__ long long part[10][OFF_T];
-  __shared__ int mx[4][OFF_T];
+  __shared__ long long part[11][OFF_T];
+  __shared__ int mx[5][OFF_T];
   __shared__ long long tot_nt[OFF_T];
   int N = w.n_atoms;
   int per = (N + blockDim.x - 1) / blockDim.x;
   int b = threadIdx.x * per, e = min(N, b + per);
-  long long s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  int m[4] = {0, 0, 0, 0};
+  long long s[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int m[5] = {0, 0, 0, 0, 0};
   long long snt = 0;
   for (int i = b; i < e; ++i) {
     Counts c = w.counts[i];
@@ -461,25 +462,28 @@ __global__ void k_offsets(Work w, int nq) {
     s[7] += Mp;
     s[8] += Kp;
     s[9] += (c.ns + 15) / 16 * 16;
+    const int spn = w.sp_np ? w.sp_np[i] : 0;
+    s[10] += spn;
+    m[4] = max(m[4], spn);
     m[0] = max(m[0], c.n1);
     m[1] = max(m[1], c.ns);
     m[2] = max(m[2], c.n12);
     m[3] = max(m[3], np);
     snt += c.nt;
   }
-  for (int t = 0; t < 10; ++t) part[t][threadIdx.x] = s[t];
-  for (int t = 0; t < 4; ++t) mx[t][threadIdx.x] = m[t];
+  for (int t = 0; t < 11; ++t) part[t][threadIdx.x] = s[t];
+  for (int t = 0; t < 5; ++t) mx[t][threadIdx.x] = m[t];
   tot_nt[threadIdx.x] = snt;
   __syncthreads();
   for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-    long long v[10];
-    for (int t = 0; t < 10; ++t) v[t] = threadIdx.x >= off ? part[t][threadIdx.x - off] : 0;
+    long long v[11];
+    for (int t = 0; t < 11; ++t) v[t] = threadIdx.x >= off ? part[t][threadIdx.x - off] : 0;
     __syncthreads();
-    for (int t = 0; t < 10; ++t) part[t][threadIdx.x] += v[t];
+    for (int t = 0; t < 11; ++t) part[t][threadIdx.x] += v[t];
     __syncthreads();
   }
-  long long run[10];
-  for (int t = 0; t < 10; ++t) run[t] = part[t][threadIdx.x] - s[t];
+  long long run[11];
+  for (int t = 0; t < 11; ++t) run[t] = part[t][threadIdx.x] - s[t];
   for (int i = b; i < e; ++i) {
     Counts c = w.counts[i];
     long long N1 = 3LL * c.n1;
@@ -489,6 +493,7 @@ __global__ void k_offsets(Work w, int nq) {
     w.off_t[i] = run[3];
     if (w.off_p) w.off_p[i] = run[4];
     if (w.off_a) w.off_a[i] = run[5];
+    if (w.off_np) w.off_np[i] = run[10];
     if (w.off_tq) {
       w.off_tq[i] = run[6];
       w.off_tr[i] = run[7];
@@ -506,10 +511,11 @@ __global__ void k_offsets(Work w, int nq) {
     run[3] += 9LL * c.ns * c.ns;
     run[4] += w.pcount ? w.pcount[2 * i] : 0;
     run[5] += w.pcount ? w.pcount[2 * i + 1] : 0;
+    run[10] += w.sp_np ? w.sp_np[i] : 0;
   }
   for (int st = blockDim.x / 2; st > 0; st >>= 1) {
     if (threadIdx.x < st) {
-      for (int t = 0; t < 4; ++t) mx[t][threadIdx.x] = max(mx[t][threadIdx.x], mx[t][threadIdx.x + st]);
+      for (int t = 0; t < 5; ++t) mx[t][threadIdx.x] = max(mx[t][threadIdx.x], mx[t][threadIdx.x + st]);
       tot_nt[threadIdx.x] += tot_nt[threadIdx.x + st];
     }
     __syncthreads();
@@ -521,6 +527,7 @@ __global__ void k_offsets(Work w, int nq) {
     w.off_t[N] = part[3][threadIdx.x];
     if (w.off_p) w.off_p[N] = part[4][threadIdx.x];
     if (w.off_a) w.off_a[N] = part[5][threadIdx.x];
+    if (w.off_np) w.off_np[N] = part[10][threadIdx.x];
     for (int t = 0; t < 4; ++t) w.totals[t] = part[t][threadIdx.x];
     w.totals[8] = part[4][threadIdx.x];
     w.totals[9] = part[5][threadIdx.x];
@@ -538,7 +545,7 @@ __global__ void k_offsets(Work w, int nq) {
     w.totals[6] = mx[2][0];
     w.totals[7] = tot_nt[0];
     w.totals[10] = mx[3][0];
-    w.totals[11] = 0;
+    w.totals[11] = mx[4][0];
   }
 }
 

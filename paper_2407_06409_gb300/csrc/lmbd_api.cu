@@ -74,6 +74,7 @@ struct Ctx {
   int paper_forces = 0;            // force model (lmbd_set_force_model)
   int bucket_width = 6;            // |K1| range of one SCS launch (lmbd_autotune)
   int spectral_fail = 0;           // lmbd_set_spectral_check: return LMBD_CATASTROPHE when flagged
+  int sparse = 0;                  // lmbd_set_sparse_tlr: block-sparse T_LR
   // forward state kept for a reverse sweep (lmbd_energy_keep / lmbd_forces_kept)
   int split = 0;
   bool kept_valid = false;
@@ -107,7 +108,7 @@ struct Ctx {
   DevBuf abar, sig, rvdw, a0, r0, wpos, cell_of, cell_count, cell_start, cell_atoms, grid;
   DevBuf site_atom, site_x, site_img, wrap, counts, offs, totals, status, pcount;
   DevBuf alphaK, alphaI, energies, trbuf, wexp, alphaK_bar, alphaI_bar, gacc, rad_ab, rad_ff;
-  DevBuf order1_d, order3_d, fitw, cfit, lam, gl64, fb, fb_flag, lu;
+  DevBuf order1_d, order3_d, fitw, cfit, lam, gl64, fb, fb_flag, lu, sp_cnt, sp_np;
   DevBuf arena;
   std::vector<Counts> counts_h;
   std::vector<long long> offs_h;
@@ -120,7 +121,8 @@ struct Ctx {
                    &a0, &r0, &wpos, &cell_of, &cell_count, &cell_start, &cell_atoms, &grid, &site_atom,
                    &site_x, &counts, &offs, &totals, &status, &pcount, &alphaK, &alphaI, &energies, &trbuf,
                    &wexp, &alphaK_bar, &alphaI_bar, &gacc, &order1_d, &order3_d, &rad_ab, &rad_ff, &fitw, &cfit, &lam, &gl64,
-                   &fb, &fb_flag, &lu, &theta_f, &theta_out, &site_img, &wrap, &ref_pos, &ref_spec, &kept_pos, &kept_spec};
+                   &fb, &fb_flag, &lu, &theta_f, &theta_out, &site_img, &wrap, &ref_pos, &ref_spec, &kept_pos, &kept_spec,
+                   &sp_cnt, &sp_np};
     static_assert(sizeof(l) / sizeof(l[0]) <= kMaxWhole, "whole-structure buffer list exceeds its array");
     for (DevBuf* b : l) whole_bufs[n_whole++] = b;
   }
@@ -243,7 +245,7 @@ int stage_input(DevBuf& buf, const void* src, size_t bytes, cudaStream_t s, cons
 // Central atoms are processed in contiguous waves [c0, c1) whose per-centre arrays fit the
 // memory budget.  The arrays of a wave live in one arena; every pointer is rebased by the
 // wave's first offset, so kernels index them with the whole-structure offsets unchanged.
-enum { O_K1, O_S, O_B, O_T, O_P, O_A, O_TQ, O_TR, O_KP, O_SP, O_COUNT };
+enum { O_K1, O_S, O_B, O_T, O_P, O_A, O_TQ, O_TR, O_KP, O_SP, O_NP, O_COUNT };
 
 struct Offs {
   const long long* h;
@@ -273,6 +275,7 @@ struct Layout {
   bool forces, sliced_chain, sliced_pair;
   int nqs;   // frequencies of the SCS solves (stage-1 arrays)
   int tk;    // tcgen05 path: row pitch of the T and W digit planes (0: per-centre Kpad)
+  bool sparse;   // block-sparse T_LR: coupled pairs and float-float chain/pair operands
 
   // stage 1 (SCS): pair lists, FP32 factors and solutions of centres [c0, c1)
   size_t stage1(const Offs& o, int c0, int c1, char* base, Work* w) const {
@@ -330,9 +333,10 @@ struct Layout {
     Carver cv{base, 0};
     const long long s0 = o.at(O_S, c0), ns = o.span(O_S, c0, c1);
     const long long t0 = o.at(O_T, c0), nt = o.span(O_T, c0, c1);
+    const long long np0 = o.at(O_NP, c0), npn = o.span(O_NP, c0, c1);
     double* alphaT = cv.take<double>((long long)nq * ns, (long long)nq * s0);
     double* dsq = cv.take<double>((long long)nq * ns, (long long)nq * s0);
-    double* tlr = cv.take<double>(nt, t0);
+    double* tlr = sparse ? nullptr : cv.take<double>(nt, t0);
     double* vkr = cv.take<double>((long long)nvec * ns * 3 * ncv, s0 * 3 * ncv);
     if (w) {
       w->alphaT = alphaT;
@@ -340,6 +344,22 @@ struct Layout {
       w->tlr = tlr;
       w->vkr = vkr;
       w->vstride = ns * 3 * ncv;
+    }
+    if (sparse) {
+      int4* sp_row = cv.take<int4>(ns, s0);
+      int2* sp_ent = cv.take<int2>(2 * npn, 2 * np0);
+      int2* sp_pair = cv.take<int2>(npn, np0);
+      float4* sp_blk = cv.take<float4>(3 * npn, 3 * np0);
+      float2* wffa = cv.take<float2>(ns * 3 * ncv, s0 * 3 * ncv);
+      float2* wffb = cv.take<float2>(ns * 3 * ncv, s0 * 3 * ncv);
+      if (w) {
+        w->sp_row = sp_row;
+        w->sp_ent = sp_ent;
+        w->sp_pair = sp_pair;
+        w->sp_blk = sp_blk;
+        w->wffa = wffa;
+        w->wffb = wffb;
+      }
     }
     if (sliced_chain) {
       // T planes: per centre st planes of Mpad rows, row pitch Kpad (warp-level path) or the
@@ -365,15 +385,20 @@ struct Layout {
     if (forces) {
       const long long nc = ncol > 0 ? ncol : 1;
       double* gbar = cv.take<double>((long long)nq * ns, (long long)nq * s0);
-      double* pmat = cv.take<double>(3 * ns * nc, 3 * s0 * nc);
-      double* qmat = cv.take<double>(3 * ns * nc, 3 * s0 * nc);
+      // P and Q: FP64 for the dense products, float-float for the sparse pair products
+      double* pmat = sparse ? nullptr : cv.take<double>(3 * ns * nc, 3 * s0 * nc);
+      double* qmat = sparse ? nullptr : cv.take<double>(3 * ns * nc, 3 * s0 * nc);
+      float2* pff = sparse ? cv.take<float2>(3 * ns * nc, 3 * s0 * nc) : nullptr;
+      float2* qff = sparse ? cv.take<float2>(3 * ns * nc, 3 * s0 * nc) : nullptr;
       double* x0buf = cv.take<double>(9 * ns, 9 * s0);
-      double* pcoef = cv.take<double>(nt, t0);
+      double* pcoef = sparse ? cv.take<double>(8 * npn, 8 * np0) : cv.take<double>(nt, t0);
       double* rbar = cv.take<double>(ns, s0);
       if (w) {
         w->gbar = gbar;
         w->pmat = pmat;
         w->qmat = qmat;
+        w->pff = pff;
+        w->qff = qff;
         w->x0buf = x0buf;
         w->pcoef = pcoef;
         w->rbar = rbar;
@@ -556,6 +581,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   if (c->logmode && c->lanczos) return LMBD_EINVAL;
   for (int n = 1; n < LMBD_MAX_ORDER_P1; ++n) dp.cn[n] = -1.0 / n;
   dp.paper = c->paper_forces && forces;
+  // the block-sparse T_LR serves the series energy and its exact adjoint; the Lanczos-based
+  // modes and the paper's forces read the dense matrix
+  if (c->sparse && (c->logmode || c->lanczos || dp.paper)) return LMBD_EUNSUPPORTED;
   dp.tc_wait = c->tc_wait > 0 ? c->tc_wait : (1LL << 32);
   // the paper's forces with the fitted integrand run once per sample frequency (run_theta): the
   // frequency weights of that pass select the bare integrand at that sample
@@ -677,6 +705,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   w.off_tr = ob + (size_t)O_TR * (N + 1);
   w.off_kp = ob + (size_t)O_KP * (N + 1);
   w.off_sp = ob + (size_t)O_SP * (N + 1);
+  w.off_np = ob + (size_t)O_NP * (N + 1);
   w.totals = (long long*)c->totals.p;
   w.status = (int*)c->status.p;
   w.pcount = (int*)c->pcount.p;
@@ -760,6 +789,14 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       launch_sites_refresh(w, dp, g, s, &launches);
     else
       launch_neighbors(w, dp, g, s, &launches);
+    if (c->sparse) {   // coupled T_LR partners of every site: the offsets size the pair arrays
+      TRY(ensure(c->sp_cnt, sizeof(int2) * (size_t)N * c->site_cap));
+      TRY(ensure(c->sp_np, sizeof(int) * (size_t)N));
+      w.sp_cnt = (int2*)c->sp_cnt.p;
+      w.sp_np = (int*)c->sp_np.p;
+      launch_sp_count(w, dp, s);
+      ++launches;
+    }
     launch_scs_count(w, dp, w.site_cap, s);
     launch_offsets(w, dp, s);
     launches += 2;
@@ -791,7 +828,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   const long long sum_n1 = c->totals_h[0];
   const int max_n1 = (int)c->totals_h[4], max_ns = (int)c->totals_h[5], max_n12 = (int)c->totals_h[6];
   // kernel shared-memory capacities (per-centre systems live in shared memory)
-  if (max_n1 > 96 || max_ns > 1024 || max_n12 > 4096) return LMBD_ECAPACITY;
+  // (the block-sparse T_LR path keeps no dense 3 ns x 3 ns matrix: spheres up to the site capacity)
+  if (max_n1 > 96 || max_ns > (c->sparse ? 4096 : 1024) || max_n12 > 4096) return LMBD_ECAPACITY;
+  const int max_pairs = (int)c->totals_h[11];
   if (scs2_adjoint_smem(max_n1, max_n12) > 227 * 1024) return LMBD_ECAPACITY;
   // dense FP64 slots of the LU fallback, one per persistent block
   const int lu_blocks = 32;
@@ -813,7 +852,9 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   const int ncol = 3 * nf * (c->order - 2);
   // sliced tensor-core products: digits per product (see ozaki.cuh and the design notes)
   const bool sliced = c->precision == LMBD_PREC_SLICED;
-  const bool sliced_chain = sliced && ncv <= 48 && !c->logmode;
+  const bool sparse = c->sparse != 0;
+  const bool sliced_chain = sliced && ncv <= 48 && !c->logmode && !sparse;
+  const bool sliced_pair = sliced && ncol > 0 && !sparse;
   const bool tc05 = c->mma_path == LMBD_MMA_TC05;
   const int ST = 6, DIG_E = 6, DIG_A = 5, DIG_P = 5;
   TRY(ensure(c->alphaK, sizeof(double) * (size_t)sum_n1 * nq));
@@ -865,7 +906,7 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
 
   // ---- waves under the memory budget --------------------------------------------------------
   const Layout L{nq, ncv, nvec, ncol, (ncol + 15) / 16 * 16, ST, DIG_P, c->site_cap, forces, sliced_chain,
-                 sliced && ncol > 0, dp.nqs, tc05 ? (3 * max_ns + 15) / 16 * 16 : 0};
+                 sliced_pair, dp.nqs, tc05 ? (3 * max_ns + 15) / 16 * 16 : 0, sparse};
   auto s1 = [&](int a, int b) { return L.stage1(o, a, b, nullptr, nullptr); };
   auto s1x = [&](int a, int b) { return forces ? L.scs_adjoint(o, a, b, nullptr, nullptr) : (size_t)0; };
   auto s2 = [&](int a, int b) { return L.stage2(o, a, b, nullptr, nullptr, nullptr); };
@@ -1014,7 +1055,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
     if (!reverse_only) {   // the forward of stage 2 (kept state in a reverse sweep)
     if (per_atom) {
       for (int cc = c0; cc < c1; ++cc) {
-        launch_mbd_prepare_sized(w, dp, cc, cc + 1, max_ns, s);
+        if (sparse)
+          launch_sp_prepare(w, dp, cc, cc + 1, max_ns, s);
+        else
+          launch_mbd_prepare_sized(w, dp, cc, cc + 1, max_ns, s);
         if (sliced_chain) launch_slice_t(w, cc, cc + 1, ST, s);
         if (dp.lanczos) {
           if (!launch_series_coefficients(w, dp, cc, cc + 1, max_ns, s)) return LMBD_ECAPACITY;
@@ -1028,6 +1072,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
           }
           else if (sliced_chain)
             launch_chain_oz2(chain_work(dg), dp, m, cc, cc + 1, max_ns, dg, ST, s);
+          else if (sparse)
+            launch_sp_chain(w, dp, m, cc, cc + 1, max_ns, s);
           else
             launch_mbd_chain_sized(w, dp, m, cc, cc + 1, max_ns, s);
         }
@@ -1038,7 +1084,10 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       phase_launch[LMBD_PHASE_ENERGY] += c1 - c0;
     } else {
       mark(LMBD_PHASE_PREPARE);
-      launch_mbd_prepare_sized(w, dp, c0, c1, max_ns, s);
+      if (sparse)
+        launch_sp_prepare(w, dp, c0, c1, max_ns, s);
+      else
+        launch_mbd_prepare_sized(w, dp, c0, c1, max_ns, s);
       if (sliced_chain) launch_slice_t(w, c0, c1, ST, s);
       if (dp.lanczos) {
         if (!launch_series_coefficients(w, dp, c0, c1, max_ns, s)) return LMBD_ECAPACITY;
@@ -1054,6 +1103,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
         }
         else if (sliced_chain)
           launch_chain_oz2(chain_work(dg), dp, m, c0, c1, max_ns, dg, ST, s);
+        else if (sparse)
+          launch_sp_chain(w, dp, m, c0, c1, max_ns, s);
         else
           launch_mbd_chain_sized(w, dp, m, c0, c1, max_ns, s);
       }
@@ -1073,11 +1124,13 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
           launch_paper_force_seeds(w, dp, cc, cc + 1, max_ns, s);
         } else {
           launch_mbd_adj_series(w, dp, cc, cc + 1, s);
-          if (sliced && ncol > 0 && tc05) {
+          if (sliced_pair && tc05) {
             if (!launch_pair_tc(w, dp, cc, cc + 1, max_ns, DIG_P, s)) return LMBD_ECUDA;
           }
-          else if (sliced && ncol > 0)
+          else if (sliced_pair)
             launch_mbd_adj_pair_oz2(w, dp, cc, cc + 1, max_ns, DIG_P, s);
+          else if (sparse)
+            launch_sp_adj_pair(w, dp, cc, cc + 1, max_pairs, s);
           else
             launch_mbd_adj_pair(w, dp, cc, cc + 1, max_ns, s);
         }
@@ -1094,11 +1147,13 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
       } else {
         launch_mbd_adj_series(w, dp, c0, c1, s);
         mark(LMBD_PHASE_ADJ_PAIR);
-        if (sliced && ncol > 0 && tc05) {
+        if (sliced_pair && tc05) {
           if (!launch_pair_tc(w, dp, c0, c1, max_ns, DIG_P, s)) return LMBD_ECUDA;
         }
-        else if (sliced && ncol > 0)
+        else if (sliced_pair)
           launch_mbd_adj_pair_oz2(w, dp, c0, c1, max_ns, DIG_P, s);
+        else if (sparse)
+          launch_sp_adj_pair(w, dp, c0, c1, max_pairs, s);
         else
           launch_mbd_adj_pair(w, dp, c0, c1, max_ns, s);
       }
@@ -1185,12 +1240,22 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   {
     const std::vector<Counts>& hc = c->counts_h;
     lmbd_stats& S = c->stats;
+    S.tlr_pairs = 0;
     for (int i = 0; i < N; ++i) {
       double n1 = 3.0 * hc[i].n1, n = 3.0 * hc[i].ns;
+      // coupled site pairs of the sparse path, every pair of the sphere on the dense one
+      const double npair = sparse ? (double)(o.at(O_NP, i + 1) - o.at(O_NP, i)) : 0.5 * hc[i].ns * (hc[i].ns - 1.0);
+      S.tlr_pairs += (long long)npair;
       S.flops[LMBD_PHASE_SCS] += dp.nqs * (n1 * n1 * n1 / 3.0 + 6.0 * n1 * n1);
-      S.flops[LMBD_PHASE_CHAIN] += dp.logmode ? 3.0 * dp.logmode * 2.0 * n * n * nf : (nvec - 1) * 2.0 * n * n * ncv;
+      if (sparse)   // 9 multiply-adds per column of every entry (both blocks of a pair)
+        S.flops[LMBD_PHASE_CHAIN] += (nvec - 1) * 2.0 * 9.0 * 2.0 * npair * ncv;
+      else
+        S.flops[LMBD_PHASE_CHAIN] += dp.logmode ? 3.0 * dp.logmode * 2.0 * n * n * nf : (nvec - 1) * 2.0 * n * n * ncv;
       if (forces) {
-        S.flops[LMBD_PHASE_ADJ_PAIR] += 2.0 * (n * (n + 48.0) / 2.0) * ncol;   // lower tiles of P Q^T
+        if (sparse)
+          S.flops[LMBD_PHASE_ADJ_PAIR] += 2.0 * 9.0 * npair * ncol;
+        else
+          S.flops[LMBD_PHASE_ADJ_PAIR] += 2.0 * (n * (n + 48.0) / 2.0) * ncol;   // lower tiles of P Q^T
         S.flops[LMBD_PHASE_ADJ_SCS] += dp.nqs * 6.0 * n1 * n1;
       }
     }
@@ -1230,6 +1295,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
   // a tensor-core kernel that gave up leaves its outputs undefined, which later stages may
   // report as failures of their own: the timeout is the cause
   if (*c->status_h & LMBD_FLAG_TIMEOUT) return LMBD_ETIMEOUT;
+  // the block-sparse fill found other partners than its count: cannot happen for one site list
+  if (*c->status_h & LMBD_FLAG_PATTERN) return LMBD_ECUDA;
   if (*c->status_h & (LMBD_FLAG_NOT_SPD | LMBD_FLAG_NOT_CONVERGED)) return LMBD_NOT_SPD;
   if (*c->status_h & LMBD_FLAG_MODEL) return LMBD_EMODEL;
   if (split == 1 && one_wave && persist && !per_atom) {
@@ -1464,6 +1531,13 @@ int lmbd_set_profiling(lmbd_ctx* ctx, int on) {
 int lmbd_set_spectral_check(lmbd_ctx* ctx, int fail) {
   if (!ctx || (fail != 0 && fail != 1)) return LMBD_EINVAL;
   ctx->c.spectral_fail = fail;
+  return LMBD_OK;
+}
+
+int lmbd_set_sparse_tlr(lmbd_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return LMBD_EINVAL;
+  ctx->c.sparse = on;
+  ctx->c.kept_valid = false;   // a kept forward state has the other layout
   return LMBD_OK;
 }
 

@@ -21,6 +21,7 @@
 // 1 (energy kernel); status[2]: SCS systems solved by the LU fallback (forward pass)
 #define LMBD_FLAG_BAD_INPUT 64      // a species index out of range, or a non-finite position or
                                     // non-positive Hirshfeld ratio, in device-resident inputs
+#define LMBD_FLAG_PATTERN 128     // the block-sparse T_LR fill found other partners than its count
 #define LMBD_FITW 32                // stride of the per-centre integrand weights dE/dI(omega_j)
 #define LMBD_FIT_ROWS 25            // omega = 0 plus at most 24 fit nodes
 #define LMBD_MAX_LANCZOS 64         // Lanczos steps of the polynomial-fit coefficients
@@ -190,6 +191,20 @@ struct Work {
   double* x0buf;               // off_s x 9, central-column term of the pair matrix
   double* pcoef;               // off_t: per site pair (s > t) r (3) and 5 derivative coefficients
   double* rbar;                // dL/d R~ per sphere site, off_s
+  // block-sparse T_LR (Sec. III.A: only the central row and column reach r_MBD,1, every other
+  // pair couples within r_MBD,2): per centre the coupled site pairs (s, t), s > t, in row order,
+  // and for every site s a row of entries (partner t, pair index), partners ascending
+  int2* sp_cnt;                // N x site_cap: coupled partners below / above each site
+  int* sp_np;                  // N: coupled pairs per centre
+  long long* off_np;           // sum of coupled pairs per centre
+  int4* sp_row;                // off_s: first entry, entries, first pair, pairs (partners below)
+  int2* sp_ent;                // 2 off_np: partner site, pair index within the centre
+  int2* sp_pair;               // off_np: (s, t), s > t
+  float4* sp_blk;              // 3 off_np: T_LR,st as float-float (00, 11), (22, 01), (02, 12)
+  float2* wffa;                // off_s x 3 x 3 n_freq: W = D v_m as float-float, m odd
+  float2* wffb;                // the same, m even
+  float2* pff;                 // off_s*3 x ncol: P as float-float (replaces pmat)
+  float2* qff;                 // off_s*3 x ncol: Q as float-float (replaces qmat)
   double* alphaK_bar;          // off_k1 * nq
   double* alphaI_bar;          // N x nq
   double* gacc;                // N x 3, dL/dR in eV/bohr (accumulated)
@@ -261,6 +276,85 @@ __device__ __forceinline__ void tsr_value(double r, double sigma, double& A0, do
   B0 = (ht - 3.0 * g) * ir2 * ir2 * ir;
 }
 
+// Blended polarisabilities of sphere site s of centre c at every frequency (Eq. full-pol, or
+// the Lorentzian model of Sec. III.C), written to alphaT and dsq; returns the SCS-scaled vdW
+// radius R~_s (Eq. scaled-rvdw).  x: the site's displacement from the centre (bohr).
+__device__ __forceinline__ double mbd_blend_site(const Work& w, const DevParams& p, int s, int a, int n1,
+                                                 long long offs, long long offk1, double x0, double x1, double x2) {
+  double fs = 0.0;
+  if (s < n1 && s > 0) {
+    double u = sqrt(x0 * x0 + x1 * x1 + x2 * x2) / p.r_scs;
+    fs = 3.0 * u * u - 2.0 * u * u * u;
+  }
+  if (!p.lorentz) {
+    for (int q = 0; q < p.nq; ++q) {
+      double aI = w.alphaI[(long long)a * p.nqs + q];
+      double at = aI;
+      if (s < n1) at = (1.0 - fs) * w.alphaK[(offk1 + s) * p.nqs + q] + fs * aI;
+      w.alphaT[(offs + s) * p.nq + q] = at;
+      w.dsq[(offs + s) * p.nq + q] = sqrt(at);
+    }
+  } else {
+    // alpha~(omega) = alpha~(0) / (1 + (omega/omega~)^2) with
+    // (omega/omega~)^2 = (omega/omega_ref)^2 (alpha~(0)/alpha~(omega_ref) - 1) (Eq. char-freq)
+    double ab[2];
+    for (int qs = 0; qs < 2; ++qs) {
+      const double aI = w.alphaI[(long long)a * 2 + qs];
+      ab[qs] = (s < n1) ? (1.0 - fs) * w.alphaK[(offk1 + s) * 2 + qs] + fs * aI : aI;
+    }
+    double ratio = ab[0] / ab[1];
+    if (!(ratio >= 1.0)) {   // alpha~ rises with frequency: Eq. char-freq has no real solution
+      atomicOr(w.status, LMBD_FLAG_MODEL);
+      ratio = 1.0;
+    }
+    for (int q = 0; q < p.nq; ++q) {
+      const double u = p.omega[q] / p.omega_ref;
+      const double at = ab[0] / (1.0 + u * u * (ratio - 1.0));
+      w.alphaT[(offs + s) * p.nq + q] = at;
+      w.dsq[(offs + s) * p.nq + q] = sqrt(at);
+    }
+  }
+  return w.r0[a] * cbrt(w.alphaT[(offs + s) * p.nq] / w.a0[a]);
+}
+
+// T_LR block of the site pair at displacement rr = x_t - x_s (bohr) with SCS radii R~_s, R~_t
+// and cutoff rc: blk = f_LR f(r, S~) T(rr) (symmetric, 0 beyond rc), and with kc non-null the
+// derivative coefficients of d<M, T_LR>/dr = (k1 r.M.r + k2 Tr M) r + k3 M r and
+// d<M, T_LR>/dS~ beta = k4 r.M.r + k5 Tr M (both pair blocks counted).
+__device__ __forceinline__ void tlr_pair_block(const DevParams& p, const double (&rr)[3], double rc, double rts,
+                                               double rtt, double (&blk)[3][3], double* kc) {
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int be = 0; be < 3; ++be) blk[al][be] = 0.0;
+  if (kc)
+    for (int i = 0; i < 5; ++i) kc[i] = 0.0;
+  const double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+  if (!(r2 < rc * rc)) return;
+  double r = sqrt(r2);
+  double flr, dflr, f, dfr, dfs;
+  cutoff_buf(r, rc, p.r_buf, flr, dflr);
+  fermi(r, p.beta * (rts + rtt), p.d, f, dfr, dfs);
+  double C = flr * f;
+  double ir = 1.0 / r;
+  double ir2 = ir * ir;
+  double ir3 = ir2 * ir;
+  double ir5 = ir3 * ir2;
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int be = 0; be < 3; ++be) blk[al][be] = C * (3.0 * rr[al] * rr[be] * ir5 - (al == be ? ir3 : 0.0));
+  if (kc) {
+    const double dC = dflr * f + flr * dfr, CS = flr * dfs;
+    const double ir4 = ir2 * ir2, ir6 = ir4 * ir2, ir7 = ir6 * ir;
+    kc[0] = 2.0 * (3.0 * dC * ir6 - 15.0 * C * ir7);
+    kc[1] = 2.0 * (3.0 * C * ir5 - dC * ir4);
+    kc[2] = 12.0 * C * ir5;
+    kc[3] = 6.0 * p.beta * CS * ir5;
+    kc[4] = -2.0 * p.beta * CS * ir3;
+  }
+}
+
 // atomicAdd for doubles is native on sm_60+.
 __device__ __forceinline__ void atomic_add3(double* p, double a, double b, double c) {
   atomicAdd(p, a);
@@ -315,6 +409,13 @@ void launch_mbd_adjoint_sized(const Work& w, const DevParams& p, int c0, int c1,
 void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
 void launch_mbd_adj_pair(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
 void launch_mbd_adj_blend(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s);
+// block-sparse T_LR (k_sparse.cu): coupled partners of every site (before the offsets), then
+// per wave the pattern, blocks and first Krylov block, the float-float chain step and the pair
+// adjoint over the coupled pairs only
+void launch_sp_count(const Work& w, const DevParams& p, cudaStream_t s);
+void launch_sp_prepare(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s);
+void launch_sp_chain(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, cudaStream_t s);
+void launch_sp_adj_pair(const Work& w, const DevParams& p, int c0, int c1, int max_pairs, cudaStream_t s);
 void launch_forces_out(const Work& w, double* forces, cudaStream_t s);
 void launch_slice_t(const Work& w, int c0, int c1, int st, cudaStream_t s);
 void launch_chain_oz2(const Work& w, const DevParams& p, int m, int c0, int c1, int max_ns, int digits, int st,

@@ -5,14 +5,12 @@
 
 // Contribution of the site pair (s, t), s > t, to dL/dr and dL/dR~ from its pair-matrix
 // block acc = M_st (3 x 3, before the central-column term): T_LR,st = f_LR f(r, S~) T(r), with
-// the geometry and derivative coefficients of the pair stored by k_mbd_prepare.  Returns
-// g = dL/dr_t (= -dL/dr_s) in out[0..2] and the SCS-radius seed beta dL/dS~ in out[3]
-// (zeros when the pair does not couple).
-__device__ __forceinline__ void pair_epilogue(const Work& w, long long offs, long long offt, int s, int t, int ns,
-                                              double (&acc)[3][3], double* out) {
+// pc the pair's geometry and derivative coefficients (r (3), k1..k5, written by the prepare
+// kernels).  Returns g = dL/dr_t (= -dL/dr_s) in out[0..2] and the SCS-radius seed
+// beta dL/dS~ in out[3] (zeros when the pair does not couple).
+__device__ __forceinline__ void pair_epilogue_at(const Work& w, long long offs, const double* pc, int s, int t,
+                                                 double (&acc)[3][3], double* out) {
   out[0] = out[1] = out[2] = out[3] = 0.0;
-  if (!(s < ns && t < ns && s > t)) return;
-  const double* pc = w.pcoef + offt + 8LL * (s * (s - 1) / 2 + t);
   const double k3 = pc[5];
   if (k3 == 0.0 && pc[6] == 0.0) return;
   if (t == 0) {
@@ -36,3 +34,12 @@ __device__ __forceinline__ void pair_epilogue(const Work& w, long long offs, lon
   out[3] = pc[6] * rMr + pc[7] * trM;
 }
 
+// The pair (s, t) of the dense pair-coefficient layout (lower triangle, s (s - 1) / 2 + t).
+__device__ __forceinline__ void pair_epilogue(const Work& w, long long offs, long long offt, int s, int t, int ns,
+                                              double (&acc)[3][3], double* out) {
+  if (!(s < ns && t < ns && s > t)) {
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    return;
+  }
+  pair_epilogue_at(w, offs, w.pcoef + offt + 8LL * (s * (s - 1) / 2 + t), s, t, acc, out);
+}

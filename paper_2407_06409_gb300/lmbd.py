@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("scs_pairs", ctypes.c_longlong), ("scs_adjacency", ctypes.c_longlong),
                 ("ms_kernel", ctypes.c_double * 2), ("scs_lu_systems", ctypes.c_longlong),
                 ("sites_refreshed", ctypes.c_int), ("reused_forward", ctypes.c_int),
-                ("spectral_flags", ctypes.c_longlong)]
+                ("spectral_flags", ctypes.c_longlong), ("tlr_pairs", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
         L.lmbd_set_series_fit.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_force_model.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_spectral_check.argtypes = [_P, ctypes.c_int]
+        L.lmbd_set_sparse_tlr.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_log_mode.argtypes = [_P, ctypes.c_int]
         L.lmbd_set_verlet_skin.argtypes = [_P, ctypes.c_double]
         L.lmbd_autotune.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]
@@ -114,7 +115,7 @@ def lib() -> ctypes.CDLL:
                   "lmbd_energy_keep", "lmbd_forces_kept",
                   "lmbd_set_launch_mode", "lmbd_set_profiling", "lmbd_set_precision", "lmbd_set_mma_path", "lmbd_set_wait_budget", "lmbd_set_memory_budget", "lmbd_set_frequency_model",
                   "lmbd_set_integrand_fit", "lmbd_set_series_fit", "lmbd_set_force_model", "lmbd_set_spectral_check",
-                  "lmbd_set_log_mode", "lmbd_set_verlet_skin",
+                  "lmbd_set_log_mode", "lmbd_set_verlet_skin", "lmbd_set_sparse_tlr",
                   "lmbd_autotune",
                   "lmbd_release_workspace", "lmbd_held_bytes",
                   "lmbd_get_central_polarizabilities", "lmbd_get_site_counts",
@@ -234,6 +235,10 @@ class LMBD:
     def set_log_mode(self, lanczos_steps: int) -> None:
         """0: truncated series; m > 0: [ln(1 - G)]_kk from m-step Lanczos Gauss rules (energies only)."""
         _check(lib().lmbd_set_log_mode(self._h, int(lanczos_steps)), "lmbd_set_log_mode")
+
+    def set_sparse_tlr(self, on: bool) -> None:
+        """True: block-sparse T_LR (coupled site pairs only, float-float chain and pair products)."""
+        _check(lib().lmbd_set_sparse_tlr(self._h, 1 if on else 0), "lmbd_set_sparse_tlr")
 
     def set_spectral_check(self, fail: bool) -> None:
         """True: calls whose spectral proxy reached 1 return LMBD_CATASTROPHE (outputs written)."""
