@@ -90,6 +90,8 @@ def parse():
                     help="arithmetic of the two large products: bf16 digit slices (default) or FP64")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the FP64-products measurement reported beside the default line (0 = skip)")
+    ap.add_argument("--sparse-steps", type=int, default=2,
+                    help="timed steps of the block-sparse T_LR comparison (0 = skip it)")
     ap.add_argument("--fit-nodes", type=int, default=0,
                     help="> 0: the paper's fitted integrand phi(omega) from omega = 0 and this many fit nodes")
     return ap.parse_args()
@@ -329,6 +331,11 @@ def run_ours(args, world, rank, local):
                      "steps": args.fp64_steps, "warmup": 1, "precision": PRECISION_FP64}
         model.set_precision(lmbd.PREC_SLICED)
 
+    # ---- block-sparse T_LR: the benchmark cutoffs and a split-cutoff sphere -----------------
+    sparse_line = None
+    if args.sparse_steps > 0 and world == 1:
+        sparse_line = sparse_comparison(args, s, (pos, cell, sp, nu), dev, stream)
+
     if rank != 0:
         return 0
 
@@ -433,10 +440,71 @@ def run_ours(args, world, rank, local):
                        "max_sphere": st["max_sphere"],
                        "precision": PRECISION if args.precision == "sliced" else PRECISION_FP64},
             "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
-            "fp64_products": fp64_line,
+            "fp64_products": fp64_line, "sparse_tlr": sparse_line,
             "gpu_launches": launches, "per_atom_launch": per_atom, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ----------------------------------------------------------------------------------------
+# block-sparse T_LR (Sec. III.A: the secondary cutoff r_MBD,2) against the dense path
+# ----------------------------------------------------------------------------------------
+SPLIT_CUTOFFS = (6.0, 3.0)       # r_MBD,1, r_MBD,2 (A); sphere r_MBD,1 + r_MBD,2 = 9 A
+
+
+def sparse_comparison(args, s, dev_args, dev, stream):
+    """Energy+forces atoms/s of the dense and the block-sparse T_LR paths on the benchmark
+    structure, at the benchmark cutoffs and with split MBD cutoffs (the paper's sphere
+    r_MBD,1 + r_MBD,2), plus the rate of the sparse chain kernel on the FP32 pipe."""
+    import torch
+    from paper_2407_06409_gb300 import lmbd
+
+    def timed(params, sparse):
+        m = lmbd.LMBD(s.table, params, 12, 6)
+        m.set_sparse_tlr(sparse)
+        m.energy_forces(*dev_args, forces=True)
+        torch.cuda.synchronize(dev)
+        m.set_profiling(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        chain_ms = chain_flops = pair_ms = pair_flops = 0.0
+        e0.record(stream)
+        for _ in range(args.sparse_steps):
+            m.energy_forces(*dev_args, forces=True)
+            st = m.stats()
+            chain_ms += st["ms"]["chain"]
+            chain_flops += st["flops"]["chain"]
+            pair_ms += st["ms"]["adj_pair"]
+            pair_flops += st["flops"]["adj_pair"]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.sparse_steps
+        out = {"value": args.atoms / (ms * 1e-3), "unit": "atoms/s", "ms_per_step": ms,
+               "tlr_pairs": st["tlr_pairs"], "max_sphere": st["max_sphere"],
+               "workspace_gb": st["bytes_workspace"] / 1e9}
+        if sparse and chain_ms > 0:
+            # 2 flops per FP64-equivalent multiply-add; a float-float multiply-add is 12 FP32
+            # instructions (1 multiply, 3 FMAs for the exact product and cross terms, 6 for the
+            # two-sum, 2 for the low part) on the 40.3 T instructions/s FP32 pipe
+            for key, ms_k, fl in (("chain", chain_ms, chain_flops), ("adj_pair", pair_ms, pair_flops)):
+                instr = fl / 2.0 * 12.0 / (ms_k * 1e-3)
+                out[key] = {"ms_per_step": ms_k / args.sparse_steps,
+                            "fp64_equiv_tflops": fl / (ms_k * 1e-3) / 1e12,
+                            "fp32_issue_frac": instr / (FP32_PEAK_TFLOPS / 2.0 * 1e12)}
+        del m
+        torch.cuda.empty_cache()
+        return out
+
+    r1, r2 = SPLIT_CUTOFFS
+    res = {"workload_bench": "the benchmark cutoffs (r_MBD,1 = r_MBD,2 = sphere 7 A)",
+           "workload_split": f"the benchmark structure with r_MBD,1 {r1} A, r_MBD,2 {r2} A, sphere "
+                             f"r_MBD,1 + r_MBD,2 = {r1 + r2} A",
+           "steps": args.sparse_steps, "warmup": 1}
+    res["bench_dense"] = timed(lmbd.default_params(), False)
+    res["bench_sparse"] = timed(lmbd.default_params(), True)
+    split = lmbd.default_params(r_mbd1=r1, r_mbd2=r2, r_sphere=0.0)
+    res["split_dense"] = timed(split, False)
+    res["split_sparse"] = timed(split, True)
+    return res
 
 
 # ----------------------------------------------------------------------------------------

@@ -296,103 +296,155 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
 #define CBP (CB * (CB + 1) / 2)   // packed lower triangle of one diagonal-block inverse
 __device__ __forceinline__ int pidx16(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// Right-looking blocked Cholesky: warp 0 factors each 16 x 16 diagonal block (and stores the
-// inverse of that block in binv, packed lower triangle, for the triangular solves), every
-// thread then solves panel rows and updates the trailing lower triangle.  sinv[i] = 1/L_ii.
-__device__ void chol32_packed(float* A, int n, int* bad, float* sinv, float* binv) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  for (int k0 = 0; k0 < n; k0 += CB) {
-    const int kb = min(CB, n - k0);
-    if (tid < 32) {
-      // the 16 x 16 diagonal block in registers, one row per lane (rows beyond kb hold the
-      // identity): right-looking Cholesky with shuffles, then the inverse of the factor, one
-      // column per lane
-      const bool act = lane < kb;
-      float a[CB];
+// The 16 x 16 diagonal block at k0, one warp: right-looking Cholesky in registers (one row per
+// lane, rows beyond the block hold the identity; one reciprocal square root per pivot, so
+// sinv[i] = 1/L_ii is that reciprocal), then the inverse of the factor block, one column per
+// lane, into binv (packed lower triangle).  A non-positive pivot sets *bad.
+__device__ void chol32_diag(float* A, int n, int k0, int* bad, float* sinv, float* binv) {
+  const int lane = threadIdx.x & 31;
+  const int kb = min(CB, n - k0);
+  const bool act = lane < kb;
+  float a[CB];
 #pragma unroll
-      for (int u = 0; u < CB; ++u)
-        a[u] = act ? (u <= lane ? A[packed_idx(k0 + lane, k0 + u)] : 0.f) : (u == lane ? 1.f : 0.f);
-      bool fail = false;
+  for (int u = 0; u < CB; ++u)
+    a[u] = act ? (u <= lane ? A[packed_idx(k0 + lane, k0 + u)] : 0.f) : (u == lane ? 1.f : 0.f);
+  bool fail = false;
+  float il_own = 1.f;
 #pragma unroll
-      for (int t = 0; t < CB; ++t) {
-        float d = __shfl_sync(0xffffffffu, a[t], t);
-        if (t < kb && !(d > 0.f)) {
-          fail = true;
-          d = 1.f;
-        }
-        const float l = sqrtf(d), il = 1.f / l;
-        if (lane == t) a[t] = l;
-        else if (lane > t) a[t] *= il;
+  for (int t = 0; t < CB; ++t) {
+    float d = __shfl_sync(0xffffffffu, a[t], t);
+    if (t < kb && !(d > 0.f)) {
+      fail = true;
+      d = 1.f;
+    }
+    const float il = rsqrtf(d), l = d * il;
+    if (lane == t) {
+      a[t] = l;
+      il_own = il;
+    } else if (lane > t) {
+      a[t] *= il;
+    }
 #pragma unroll
-        for (int j = 1; j < CB; ++j) {
-          if (j > t) {
-            const float ljt = __shfl_sync(0xffffffffu, a[t], j);
-            if (lane >= j) a[j] -= a[t] * ljt;
-          }
-        }
-      }
-      if (fail && lane == 0) *bad = 1;
-      float dl = 1.f;
-#pragma unroll
-      for (int u = 0; u < CB; ++u) {
-        if (act && u <= lane) A[packed_idx(k0 + lane, k0 + u)] = a[u];
-        if (u == lane) dl = a[u];
-      }
-      if (act) sinv[k0 + lane] = 1.f / dl;
-      __syncwarp();
-      // inverse of the factor block: lane c solves L x = e_c, reading L from shared memory
-      // (every lane reads the same element: broadcast)
-      float* inv = binv + (k0 / CB) * CBP;
-      float x[CB];
-#pragma unroll
-      for (int i = 0; i < CB; ++i) {
-        float v = 0.f;
-        if (i < kb) {
-          const float* Li = A + packed_idx(k0 + i, k0);
-          float s = (i == lane) ? 1.f : 0.f;
-#pragma unroll
-          for (int u = 0; u < i; ++u) s -= Li[u] * x[u];
-          v = (i >= lane && act) ? s * sinv[k0 + i] : 0.f;
-        }
-        x[i] = v;
-        if (lane < CB && i >= lane) inv[pidx16(i, lane)] = v;
+    for (int j = 1; j < CB; ++j) {
+      if (j > t) {
+        const float ljt = __shfl_sync(0xffffffffu, a[t], j);
+        if (lane >= j) a[j] -= a[t] * ljt;
       }
     }
-    __syncthreads();
-    const int r0 = k0 + kb;
+  }
+  if (fail && lane == 0) *bad = 1;
+#pragma unroll
+  for (int u = 0; u < CB; ++u)
+    if (act && u <= lane) A[packed_idx(k0 + lane, k0 + u)] = a[u];
+  if (act) sinv[k0 + lane] = il_own;
+  __syncwarp();
+  // inverse of the factor block: lane c solves L x = e_c, reading L from shared memory
+  // (every lane reads the same element: broadcast)
+  float* inv = binv + (k0 / CB) * CBP;
+  float x[CB];
+#pragma unroll
+  for (int i = 0; i < CB; ++i) {
+    float v = 0.f;
+    if (i < kb) {
+      const float* Li = A + packed_idx(k0 + i, k0);
+      float s = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int u = 0; u < i; ++u) s -= Li[u] * x[u];
+      v = (i >= lane && act) ? s * sinv[k0 + i] : 0.f;
+    }
+    x[i] = v;
+    if (lane < CB && i >= lane) inv[pidx16(i, lane)] = v;
+  }
+  __syncwarp();
+}
+
+// named barrier 1 between warp 0 (waits) and warp 1 (arrives): 64 threads
+__device__ __forceinline__ void nbar_sync_w01() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+__device__ __forceinline__ void nbar_arrive_w01() { asm volatile("bar.arrive 1, 64;" ::: "memory"); }
+
+// Right-looking blocked Cholesky of the packed lower triangle (16-wide blocks, 256 threads),
+// with lookahead.  Per block column k: all threads form the panel rows below the diagonal block
+// from the inverse diagonal block (L_ik = A_ik L_kk^-T, independent dot products); then warp 1
+// updates the next diagonal block first and hands it to warp 0 through a named barrier, warp 0
+// factors and inverts it while warps 1..7 update the trailing rows below it, two rows per warp
+// at a time (each panel value a lane loads serves both rows).  Two block barriers per block
+// column; the factor of the next diagonal block is off the path of the trailing update.
+// sinv[i] = 1/L_ii; binv holds the inverses of the diagonal blocks (solve32_warp).
+__device__ __noinline__ void chol32_packed(float* A, int n, int* bad, float* sinv, float* binv) {
+  constexpr int RB = 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  if (warp == 0) chol32_diag(A, n, 0, bad, sinv, binv);
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    const int kb = min(CB, n - k0), r0 = k0 + kb;
+    if (r0 >= n) break;
+    const float* inv = binv + (k0 / CB) * CBP;
     for (int i = r0 + tid; i < n; i += blockDim.x) {
       float* row = A + packed_idx(i, k0);
-      float v[CB];
+      float v[CB], o[CB];
 #pragma unroll
       for (int t = 0; t < CB; ++t) v[t] = t < kb ? row[t] : 0.f;
 #pragma unroll
       for (int t = 0; t < CB; ++t) {
-        if (t < kb) {
-          const float* dt = A + packed_idx(k0 + t, k0);
-          float s = v[t];
+        float sum = 0.f;
 #pragma unroll
-          for (int u = 0; u < t; ++u) s -= v[u] * dt[u];
-          v[t] = s * sinv[k0 + t];
-        }
+        for (int u = 0; u <= t; ++u) sum += v[u] * inv[pidx16(t, u)];
+        o[t] = sum;
       }
 #pragma unroll
       for (int t = 0; t < CB; ++t)
-        if (t < kb) row[t] = v[t];
+        if (t < kb) row[t] = o[t];
     }
     __syncthreads();
-    for (int i = r0 + warp; i < n; i += nw) {
-      const float* li = A + packed_idx(i, k0);
-      float a[CB];
+    const int k1 = r0, kb1 = min(CB, n - k1), r1 = k1 + kb1;
+    if (warp == 0) {
+      nbar_sync_w01();
+      chol32_diag(A, n, k1, bad, sinv, binv);
+    } else {
+      if (warp == 1) {
+        // the next diagonal block: lane l takes row l % 16, the columns of parity l / 16
+        const int i = lane & 15;
+        if (i < kb1) {
+          const float* li = A + packed_idx(k1 + i, k0);
+          float a[CB];
 #pragma unroll
-      for (int t = 0; t < CB; ++t) a[t] = t < kb ? li[t] : 0.f;
-      float* row = A + packed_idx(i, 0);
-      for (int j = r0 + lane; j <= i; j += 32) {
-        const float* lj = A + packed_idx(j, k0);
-        float s = 0.f;
+          for (int t = 0; t < CB; ++t) a[t] = t < kb ? li[t] : 0.f;
+          for (int j = lane >> 4; j <= i; j += 2) {
+            const float* lj = A + packed_idx(k1 + j, k0);
+            float sum = 0.f;
 #pragma unroll
-        for (int t = 0; t < CB; ++t)
-          if (t < kb) s += a[t] * lj[t];
-        row[j] -= s;
+            for (int t = 0; t < CB; ++t)
+              if (t < kb) sum += a[t] * lj[t];
+            A[packed_idx(k1 + i, k1 + j)] -= sum;
+          }
+        }
+        __threadfence_block();
+        nbar_arrive_w01();
+      }
+      for (int i0 = r1 + RB * (warp - 1); i0 < n; i0 += RB * (nw - 1)) {
+        float a[RB][CB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const float* li = A + packed_idx(min(i0 + r, n - 1), k0);
+#pragma unroll
+          for (int t = 0; t < CB; ++t) a[r][t] = t < kb ? li[t] : 0.f;
+        }
+        const int ilast = min(i0 + RB - 1, n - 1);
+        for (int j = k1 + lane; j <= ilast; j += 32) {
+          const float* lj = A + packed_idx(j, k0);
+          float sum[RB];
+#pragma unroll
+          for (int r = 0; r < RB; ++r) sum[r] = 0.f;
+#pragma unroll
+          for (int t = 0; t < CB; ++t) {
+            const float v = t < kb ? lj[t] : 0.f;
+#pragma unroll
+            for (int r = 0; r < RB; ++r) sum[r] += a[r][t] * v;
+          }
+#pragma unroll
+          for (int r = 0; r < RB; ++r)
+            if (j <= i0 + r && i0 + r < n) A[packed_idx(i0 + r, j)] -= sum[r];
+        }
       }
     }
     __syncthreads();
