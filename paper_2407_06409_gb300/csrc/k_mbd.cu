@@ -891,20 +891,23 @@ __device__ double fit_energy(FitScratch& S, const double* I, const DevParams& p,
 // energy: tr_{n,q} = <v_a, v_b>_q (a + b = n) and E_k = sum_q cw_q sum_n (-1/n) tr_{n,q}
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0) {
-  // deterministic: one thread per column sums all rows in order, then a fixed-order
-  // sum over the three columns of each frequency
-  __shared__ double red[LMBD_MAX_ORDER_P1][3 * 64];
+  // deterministic: G = floor(256 / 3 n_freq) row groups per column, thread (g, col) sums the rows
+  // g, g + G, ... in order, then fixed-order sums over the groups and over the three columns of
+  // each frequency
+  __shared__ double red[LMBD_MAX_ORDER_P1][256];
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
   const int ns = w.counts[c].ns, N = 3 * ns;
   const long long offs = w.off_s[c];
   const int ncv = 3 * p.n_freq;
   const int tid = threadIdx.x;
-  for (int col = tid; col < ncv && !p.logmode; col += blockDim.x) {
+  const int G = ncv <= (int)blockDim.x ? (int)blockDim.x / ncv : 1;   // G ncv <= 256
+  for (int it = tid; it < G * ncv && !p.logmode; it += blockDim.x) {
+    const int g = it / ncv, col = it % ncv;
     double acc[LMBD_MAX_ORDER_P1];
 #pragma unroll
     for (int n = 0; n < LMBD_MAX_ORDER_P1; ++n) acc[n] = 0.0;
-    for (int row = 0; row < N; ++row) {
+    for (int row = g; row < N; row += G) {
       for (int n = 2; n <= p.order; ++n) {
         int a = n / 2, b = n - a;
         const double* Va = w.vkr + (long long)(a - 1) * w.vstride + (offs * 3) * ncv;
@@ -912,8 +915,15 @@ __global__ void __launch_bounds__(256) k_mbd_energy(Work w, DevParams p, int c0)
         acc[n] += Va[(long long)row * ncv + col] * Vb[(long long)row * ncv + col];
       }
     }
-    for (int n = 2; n <= p.order; ++n) red[n][col] = acc[n];
+    for (int n = 2; n <= p.order; ++n) red[n][it] = acc[n];
   }
+  __syncthreads();
+  for (int col = tid; col < ncv && !p.logmode; col += blockDim.x)   // own column's slots only
+    for (int n = 2; n <= p.order; ++n) {
+      double sum = red[n][col];
+      for (int g = 1; g < G; ++g) sum += red[n][g * ncv + col];
+      red[n][col] = sum;
+    }
   __syncthreads();
   __shared__ double epart[64];
   __shared__ double ival[64];

@@ -13,7 +13,7 @@
 //   pair     M_st = P_s Q_t^T for the coupled pairs only, then the epilogue of the dense path
 // FP64 runs at about 1/64 of the FP32 rate here, so the chain and pair products use
 // float-float arithmetic (Dekker/Knuth error-free products and sums, about 2^-46 relative per
-// product) on the FP32 pipe; sums leave it as FP64.
+// product) on the FP32 pipe; the Krylov blocks leave it as FP64.
 //
 // Pattern test.  A pair is listed when its FP32 squared distance is below rc^2 (1 + 2e-4); the
 // FP64 block of a listed pair is zero when its FP64 distance is not below rc, as in the dense
@@ -202,6 +202,10 @@ __global__ void __launch_bounds__(SP_THREADS) k_sp_prepare(Work w, DevParams p, 
     const int a = w.site_atom[sbase + s];
     const double x0 = w.site_x[3 * (sbase + s)], x1 = w.site_x[3 * (sbase + s) + 1], x2 = w.site_x[3 * (sbase + s) + 2];
     rt[s] = mbd_blend_site(w, p, s, a, n1, offs, offk1, x0, x1, x2);
+    for (int q = 0; q < p.nq; ++q) {
+      const ff d = ff_from_double(w.dsq[(offs + s) * p.nq + q]);
+      w.dsq_ff[(offs + s) * p.nq + q] = make_float2(d.hi, d.lo);
+    }
     const int2 cnt = w.sp_cnt[sbase + s];
     rs[s] = cnt.x + cnt.y;
     pb[s] = cnt.x;
@@ -338,13 +342,15 @@ __global__ void __launch_bounds__(SP_THREADS) k_sp_chain(Work w, DevParams p, in
       ffmac(a2, b2.z, b2.w, x1);
       ffmac(a2, b1.x, b1.y, x2);
     }
-    const double d = w.dsq[(offs + s) * p.nq + col / 3 + 1];
+    // v = D y and W = D v in float-float; one FP64 sum per output for the FP64 Krylov block
+    const float2 dq = w.dsq_ff[(offs + s) * p.nq + col / 3 + 1];
+    const ff d = ff_make(dq.x, dq.y);
     const ff acc[3] = {a0, a1, a2};
 #pragma unroll
     for (int al = 0; al < 3; ++al) {
-      const double v = d * ((double)acc[al].hi + (double)acc[al].lo);
-      Vout[(long long)(3 * s + al) * ncv + col] = v;
-      const ff wv = ff_from_double(d * v);
+      const ff v = ff_mul(d, ff_quick_two_sum(acc[al].hi, acc[al].lo));
+      Vout[(long long)(3 * s + al) * ncv + col] = (double)v.hi + (double)v.lo;
+      const ff wv = ff_mul(d, v);
       Wout[((offs + s) * 3 + al) * ncv + col] = make_float2(wv.hi, wv.lo);
     }
   }

@@ -352,7 +352,9 @@ struct Layout {
       float4* sp_blk = cv.take<float4>(3 * npn, 3 * np0);
       float2* wffa = cv.take<float2>(ns * 3 * ncv, s0 * 3 * ncv);
       float2* wffb = cv.take<float2>(ns * 3 * ncv, s0 * 3 * ncv);
+      float2* dsq_ff = cv.take<float2>((long long)nq * ns, (long long)nq * s0);
       if (w) {
+        w->dsq_ff = dsq_ff;
         w->sp_row = sp_row;
         w->sp_ent = sp_ent;
         w->sp_pair = sp_pair;
