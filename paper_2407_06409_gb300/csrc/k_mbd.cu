@@ -988,59 +988,68 @@ void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaSt
 //   a_j = sum_{l=1}^{n_max-1-j} c~_{j+l+1} v_l,  P_s = [D_qs v_j[s]],  Q_s = [D_qs a_j[s]]
 //   X0_s = sum_q D_qs D_q0 sum_n c~_n v_{n-1}[s]
 // ---------------------------------------------------------------------------------------
+template <int NM>
 __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c0) {
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
   const int ns = w.counts[c].ns;
   const long long offs = w.off_s[c];
   const int ncv = 3 * p.n_freq;
-  const int nm = p.order;
+  const int nm = NM;
   const double wk = w.weights ? w.weights[c] : 1.0;
   const int tid = threadIdx.x;
   const double* V0 = w.vkr + (offs * 3) * ncv;   // block of v_1, others at +vstride*(m-1)
-  // per (site, frequency) work items
+  // per (site, frequency) work items; for each of the 9 entries of the site's 3 x 3 block at this
+  // frequency the values v_1 .. v_{n_max-1} are read once into registers
   for (int e = tid; e < ns * p.n_freq; e += blockDim.x) {
-    int s = e / p.n_freq, qq = e % p.n_freq, q = qq + 1;
+    const int s = e / p.n_freq, qq = e % p.n_freq, q = qq + 1;
     const double cwq = p.fit ? w.fitw[(long long)c * LMBD_FITW + qq] : p.cweight[q];
-    double ct[LMBD_MAX_ORDER_P1];
-    for (int n = 0; n <= nm; ++n) ct[n] = (n >= 2) ? wk * cwq * series_c(w, p, c, qq, n) : 0.0;
-    // inner products <v_j[s], v_l[s]> for 1 <= j <= l, j + l <= n_max
-    double ga = 0.0;
-    for (int n = 2; n <= nm; ++n) {
-      double sum = 0.0;
-      if (s == 0) sum += w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq];
-      for (int j = 1; j <= n - 1; ++j) {
-        const double* Va = V0 + (long long)(j - 1) * w.vstride;
-        const double* Vb = V0 + (long long)(n - j - 1) * w.vstride;
-        for (int al = 0; al < 3; ++al)
-          for (int be = 0; be < 3; ++be) {
-            long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
-            sum += Va[idx] * Vb[idx];
-          }
+    double ct[NM + 1];
+#pragma unroll
+    for (int n = 0; n <= NM; ++n) ct[n] = (n >= 2) ? wk * cwq * series_c(w, p, c, qq, n) : 0.0;
+    // gs_n = sum_{j=1}^{n-1} <v_j[s], v_{n-j}[s]>: the pairs j < n - j once (doubled), j = n/2 once
+    double go[NM + 1], gd[NM + 1];
+#pragma unroll
+    for (int n = 0; n <= NM; ++n) go[n] = gd[n] = 0.0;
+    const double ds = w.dsq[(offs + s) * p.nq + q];
+#pragma unroll
+    for (int ab = 0; ab < 9; ++ab) {
+      const int al = ab / 3, be = ab % 3;
+      const long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
+      double v[NM];   // v[m] = v_m, m = 1 .. n_max - 1
+#pragma unroll
+      for (int m = 1; m < NM; ++m) v[m] = V0[(long long)(m - 1) * w.vstride + idx];
+#pragma unroll
+      for (int n = 2; n <= NM; ++n) {
+#pragma unroll
+        for (int j = 1; 2 * j < n; ++j) go[n] += v[j] * v[n - j];
+        if (n % 2 == 0) gd[n] += v[n / 2] * v[n / 2];
       }
+      // P and Q columns of this frequency: P_j = D v_j, Q_j = D a_j, a_j = sum_l c~_{j+l+1} v_l
+#pragma unroll
+      for (int j = 1; j <= NM - 2; ++j) {
+        double a = 0.0;
+#pragma unroll
+        for (int l = 1; l <= NM - 1 - j; ++l) a += ct[j + l + 1] * v[l];
+        const long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
+        if (w.qff) {   // block-sparse T_LR: the pair products run in float-float
+          const ff pv = ff_from_double(ds * v[j]), qv = ff_from_double(ds * a);
+          w.pff[o] = make_float2(pv.hi, pv.lo);
+          w.qff[o] = make_float2(qv.hi, qv.lo);
+        } else {
+          w.pmat[o] = ds * v[j];
+          w.qmat[o] = ds * a;
+        }
+      }
+    }
+    double ga = 0.0;
+#pragma unroll
+    for (int n = 2; n <= NM; ++n) {
+      double sum = 2.0 * go[n] + gd[n];
+      if (s == 0) sum += w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq];
       ga += ct[n] * sum;
     }
     w.gbar[(offs + s) * p.nq + q] = ga / w.alphaT[(offs + s) * p.nq + q];
-    // P and Q columns of this frequency
-    const double ds = w.dsq[(offs + s) * p.nq + q];
-    for (int j = 1; j <= nm - 2; ++j) {
-      const double* Vj = V0 + (long long)(j - 1) * w.vstride;
-      for (int al = 0; al < 3; ++al)
-        for (int be = 0; be < 3; ++be) {
-          long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
-          double a = 0.0;
-          for (int l = 1; l <= nm - 1 - j; ++l) a += ct[j + l + 1] * V0[(long long)(l - 1) * w.vstride + idx];
-          long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
-          if (w.qff) {   // block-sparse T_LR: the pair products run in float-float
-            const ff pv = ff_from_double(ds * Vj[idx]), qv = ff_from_double(ds * a);
-            w.pff[o] = make_float2(pv.hi, pv.lo);
-            w.qff[o] = make_float2(qv.hi, qv.lo);
-          } else {
-            w.pmat[o] = ds * Vj[idx];
-            w.qmat[o] = ds * a;
-          }
-        }
-    }
   }
   __syncthreads();
   // X0_s (3 x 3) summed over frequencies
@@ -1383,7 +1392,14 @@ void launch_paper_force_seeds(const Work& w, const DevParams& p, int c0, int c1,
 
 void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {
   if (c1 <= c0) return;
-  k_mbd_adj_site<<<c1 - c0, 256, 0, s>>>(w, p, c0);
+  switch (p.order) {   // series order n_max: 2 .. LMBD_MAX_ORDER_P1 - 1
+#define ADJ_SITE_CASE(N) \
+  case N: k_mbd_adj_site<N><<<c1 - c0, 256, 0, s>>>(w, p, c0); break;
+    ADJ_SITE_CASE(2) ADJ_SITE_CASE(3) ADJ_SITE_CASE(4) ADJ_SITE_CASE(5) ADJ_SITE_CASE(6)
+    ADJ_SITE_CASE(7) ADJ_SITE_CASE(8) ADJ_SITE_CASE(9) ADJ_SITE_CASE(10)
+#undef ADJ_SITE_CASE
+    default: break;
+  }
 }
 
 void launch_mbd_adj_pair(const Work& w, const DevParams& p, int c0, int c1, int max_ns, cudaStream_t s) {

@@ -321,7 +321,11 @@ __device__ __forceinline__ double mbd_blend_site(const Work& w, const DevParams&
 // T_LR block of the site pair at displacement rr = x_t - x_s (bohr) with SCS radii R~_s, R~_t
 // and cutoff rc: blk = f_LR f(r, S~) T(rr) (symmetric, 0 beyond rc), and with kc non-null the
 // derivative coefficients of d<M, T_LR>/dr = (k1 r.M.r + k2 Tr M) r + k3 M r and
-// d<M, T_LR>/dS~ beta = k4 r.M.r + k5 Tr M (both pair blocks counted).
+// d<M, T_LR>/dS~ beta = k4 r.M.r + k5 Tr M (both pair blocks counted).  FP64 throughout; the
+// operation count is kept low because every site pair of every sphere goes through it on the
+// FP64 pipe: 1/r from one reciprocal square root, the Fermi damping (Eq. damping-function) with
+// x = r / S~ as the only division besides 1/(1 + e), its derivatives through 1/r, and the six
+// distinct entries of the symmetric block from two shared factors.
 __device__ __forceinline__ void tlr_pair_block(const DevParams& p, const double (&rr)[3], double rc, double rts,
                                                double rtt, double (&blk)[3][3], double* kc) {
 #pragma unroll
@@ -332,20 +336,29 @@ __device__ __forceinline__ void tlr_pair_block(const DevParams& p, const double 
     for (int i = 0; i < 5; ++i) kc[i] = 0.0;
   const double r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
   if (!(r2 < rc * rc)) return;
-  double r = sqrt(r2);
-  double flr, dflr, f, dfr, dfs;
+  const double ir = rsqrt(r2);
+  const double r = r2 * ir;
+  double flr, dflr;
   cutoff_buf(r, rc, p.r_buf, flr, dflr);
-  fermi(r, p.beta * (rts + rtt), p.d, f, dfr, dfs);
-  double C = flr * f;
-  double ir = 1.0 / r;
-  double ir2 = ir * ir;
-  double ir3 = ir2 * ir;
-  double ir5 = ir3 * ir2;
-#pragma unroll
-  for (int al = 0; al < 3; ++al)
-#pragma unroll
-    for (int be = 0; be < 3; ++be) blk[al][be] = C * (3.0 * rr[al] * rr[be] * ir5 - (al == be ? ir3 : 0.0));
+  // f = 1 / (1 + exp(-d (x - 1))), x = r / S~; df/dr = f (1 - f) d / S~ = f (1 - f) d x / r,
+  // df/dS~ = -x df/dr
+  const double x = r / (p.beta * (rts + rtt));
+  const double e = exp(-p.d * (x - 1.0));
+  const double f = 1.0 / (1.0 + e);
+  const double dfr = f * (1.0 - f) * p.d * x * ir;
+  const double C = flr * f;
+  const double ir2 = ir * ir;
+  const double ir3 = ir2 * ir;
+  const double ir5 = ir3 * ir2;
+  const double a = 3.0 * C * ir5, b = C * ir3;
+  blk[0][0] = a * rr[0] * rr[0] - b;
+  blk[1][1] = a * rr[1] * rr[1] - b;
+  blk[2][2] = a * rr[2] * rr[2] - b;
+  blk[0][1] = blk[1][0] = a * rr[0] * rr[1];
+  blk[0][2] = blk[2][0] = a * rr[0] * rr[2];
+  blk[1][2] = blk[2][1] = a * rr[1] * rr[2];
   if (kc) {
+    const double dfs = -dfr * x;
     const double dC = dflr * f + flr * dfr, CS = flr * dfs;
     const double ir4 = ir2 * ir2, ir6 = ir4 * ir2, ir7 = ir6 * ir;
     kc[0] = 2.0 * (3.0 * dC * ir6 - 15.0 * C * ir7);
