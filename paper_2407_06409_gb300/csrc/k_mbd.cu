@@ -988,7 +988,7 @@ void launch_mbd_energy(const Work& w, const DevParams& p, int c0, int c1, cudaSt
 //   a_j = sum_{l=1}^{n_max-1-j} c~_{j+l+1} v_l,  P_s = [D_qs v_j[s]],  Q_s = [D_qs a_j[s]]
 //   X0_s = sum_q D_qs D_q0 sum_n c~_n v_{n-1}[s]
 // ---------------------------------------------------------------------------------------
-template <int NM>
+template <int NM, bool SPARSE>
 __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c0) {
   const int c = c0 + blockIdx.x;
   if (c >= w.n_atoms) return;
@@ -1007,6 +1007,53 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
     double ct[NM + 1];
 #pragma unroll
     for (int n = 0; n <= NM; ++n) ct[n] = (n >= 2) ? wk * cwq * series_c(w, p, c, qq, n) : 0.0;
+    if (SPARSE) {
+      // block-sparse T_LR: the chain kept W_m = D v_m as float-float, so P_j = W_j,
+      // Q_j = sum_l c~_{j+l+1} W_l and <v_j, v_l> = <W_j, W_l> / alpha~ run on the FP32 pipe
+      const float2* W0 = w.wff + (offs * 3) * ncv;
+      ff ctf[NM + 1], fo[NM + 1], fd[NM + 1];
+#pragma unroll
+      for (int n = 0; n <= NM; ++n) {
+        ctf[n] = ff_from_double(ct[n]);
+        fo[n] = fd[n] = ff_make(0.f, 0.f);
+      }
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) {
+        const int al = ab / 3, be = ab % 3;
+        const long long idx = (long long)(3 * s + al) * ncv + 3 * qq + be;
+        ff v[NM];
+#pragma unroll
+        for (int m = 1; m < NM; ++m) {
+          const float2 t = W0[(long long)(m - 1) * w.vstride + idx];
+          v[m] = ff_make(t.x, t.y);
+        }
+#pragma unroll
+        for (int n = 2; n <= NM; ++n) {
+#pragma unroll
+          for (int j = 1; 2 * j < n; ++j) fo[n] = ff_fma(v[j], v[n - j], fo[n]);
+          if (n % 2 == 0) fd[n] = ff_fma(v[n / 2], v[n / 2], fd[n]);
+        }
+#pragma unroll
+        for (int j = 1; j <= NM - 2; ++j) {
+          ff a = ff_make(0.f, 0.f);
+#pragma unroll
+          for (int l = 1; l <= NM - 1 - j; ++l) a = ff_fma(ctf[j + l + 1], v[l], a);
+          const long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
+          w.pff[o] = make_float2(v[j].hi, v[j].lo);
+          w.qff[o] = make_float2(a.hi, a.lo);
+        }
+      }
+      const double ia = 1.0 / w.alphaT[(offs + s) * p.nq + q];
+      double ga = 0.0;
+#pragma unroll
+      for (int n = 2; n <= NM; ++n) {
+        double sum = ff_to_double(ff_add(ff_add(fo[n], fo[n]), fd[n])) * ia;
+        if (s == 0) sum += w.trbuf[((long long)c * LMBD_MAX_ORDER_P1) * 64 + n * 64 + qq];
+        ga += ct[n] * sum;
+      }
+      w.gbar[(offs + s) * p.nq + q] = ga * ia;
+      continue;
+    }
     // gs_n = sum_{j=1}^{n-1} <v_j[s], v_{n-j}[s]>: the pairs j < n - j once (doubled), j = n/2 once
     double go[NM + 1], gd[NM + 1];
 #pragma unroll
@@ -1032,14 +1079,8 @@ __global__ void __launch_bounds__(256) k_mbd_adj_site(Work w, DevParams p, int c
 #pragma unroll
         for (int l = 1; l <= NM - 1 - j; ++l) a += ct[j + l + 1] * v[l];
         const long long o = (offs * 3 + 3 * s + al) * (long long)w.ncol + (qq * (nm - 2) + (j - 1)) * 3 + be;
-        if (w.qff) {   // block-sparse T_LR: the pair products run in float-float
-          const ff pv = ff_from_double(ds * v[j]), qv = ff_from_double(ds * a);
-          w.pff[o] = make_float2(pv.hi, pv.lo);
-          w.qff[o] = make_float2(qv.hi, qv.lo);
-        } else {
-          w.pmat[o] = ds * v[j];
-          w.qmat[o] = ds * a;
-        }
+        w.pmat[o] = ds * v[j];
+        w.qmat[o] = ds * a;
       }
     }
     double ga = 0.0;
@@ -1393,8 +1434,13 @@ void launch_paper_force_seeds(const Work& w, const DevParams& p, int c0, int c1,
 void launch_mbd_adj_series(const Work& w, const DevParams& p, int c0, int c1, cudaStream_t s) {
   if (c1 <= c0) return;
   switch (p.order) {   // series order n_max: 2 .. LMBD_MAX_ORDER_P1 - 1
-#define ADJ_SITE_CASE(N) \
-  case N: k_mbd_adj_site<N><<<c1 - c0, 256, 0, s>>>(w, p, c0); break;
+#define ADJ_SITE_CASE(N)                                                \
+  case N:                                                               \
+    if (w.wff)                                                          \
+      k_mbd_adj_site<N, true><<<c1 - c0, 256, 0, s>>>(w, p, c0);        \
+    else                                                                \
+      k_mbd_adj_site<N, false><<<c1 - c0, 256, 0, s>>>(w, p, c0);       \
+    break;
     ADJ_SITE_CASE(2) ADJ_SITE_CASE(3) ADJ_SITE_CASE(4) ADJ_SITE_CASE(5) ADJ_SITE_CASE(6)
     ADJ_SITE_CASE(7) ADJ_SITE_CASE(8) ADJ_SITE_CASE(9) ADJ_SITE_CASE(10)
 #undef ADJ_SITE_CASE

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(SP_THREADS) k_sp_prepare(Work w, DevParams p, 
   // v_1 = G e_k = D T_{s0} D_0 (the central partner is the first entry of a row) and W_1 = D v_1
   const int ncv = 3 * p.n_freq;
   double* V1 = w.vkr + (offs * 3) * ncv;
-  float2* W1 = w.wffa + (offs * 3) * ncv;
+  float2* W1 = w.wff + (offs * 3) * ncv;
   for (int e = tid; e < 3 * ns * ncv; e += blockDim.x) {
     const int row = e / ncv, col = e % ncv;
     const int s = row / 3, al = row % 3, q = col / 3 + 1, be = col % 3;
@@ -307,7 +307,7 @@ __device__ __forceinline__ void ffmac(ff& acc, float ah, float al, float2 b) {
 
 // ---------------------------------------------------------------------------------------
 // chain step m: v_{m+1} = D (T W_m), W_{m+1} = D v_{m+1}; rpb sites per block, one thread per
-// (site, column); W_m in wffa for odd m, wffb for even m
+// (site, column); W_m is block m - 1 of wff (all blocks kept for the adjoint)
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(SP_THREADS) k_sp_chain(Work w, DevParams p, int m, int c0, int bpc, int rpb) {
   const int c = c0 + blockIdx.x / bpc;
@@ -317,8 +317,8 @@ __global__ void __launch_bounds__(SP_THREADS) k_sp_chain(Work w, DevParams p, in
   if (s0 >= ns) return;
   const int ncv = 3 * p.n_freq;
   const long long offs = w.off_s[c], pbg = w.off_np[c], eb = 2 * pbg;
-  const float2* Win = (m & 1) ? w.wffa : w.wffb;
-  float2* Wout = (m & 1) ? w.wffb : w.wffa;
+  const float2* Win = w.wff + (long long)(m - 1) * w.vstride;
+  float2* Wout = w.wff + (long long)m * w.vstride;
   double* Vout = w.vkr + (long long)m * w.vstride + (offs * 3) * ncv;
   for (int it = threadIdx.x; it < rpb * ncv; it += blockDim.x) {
     const int s = s0 + it / ncv, col = it % ncv;

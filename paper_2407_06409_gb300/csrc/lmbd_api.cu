@@ -350,8 +350,7 @@ struct Layout {
       int2* sp_ent = cv.take<int2>(2 * npn, 2 * np0);
       int2* sp_pair = cv.take<int2>(npn, np0);
       float4* sp_blk = cv.take<float4>(3 * npn, 3 * np0);
-      float2* wffa = cv.take<float2>(ns * 3 * ncv, s0 * 3 * ncv);
-      float2* wffb = cv.take<float2>(ns * 3 * ncv, s0 * 3 * ncv);
+      float2* wff = cv.take<float2>((long long)nvec * ns * 3 * ncv, s0 * 3 * ncv);
       float2* dsq_ff = cv.take<float2>((long long)nq * ns, (long long)nq * s0);
       if (w) {
         w->dsq_ff = dsq_ff;
@@ -359,8 +358,7 @@ struct Layout {
         w->sp_ent = sp_ent;
         w->sp_pair = sp_pair;
         w->sp_blk = sp_blk;
-        w->wffa = wffa;
-        w->wffb = wffb;
+        w->wff = wff;
       }
     }
     if (sliced_chain) {

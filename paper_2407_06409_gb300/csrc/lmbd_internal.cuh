@@ -201,8 +201,8 @@ struct Work {
   int2* sp_ent;                // 2 off_np: partner site, pair index within the centre
   int2* sp_pair;               // off_np: (s, t), s > t
   float4* sp_blk;              // 3 off_np: T_LR,st as float-float (00, 11), (22, 01), (02, 12)
-  float2* wffa;                // off_s x 3 x 3 n_freq: W = D v_m as float-float, m odd
-  float2* wffb;                // the same, m even
+  float2* wff;                 // nvec blocks of (off_s total * 3) x (3 n_freq): W_m = D v_m as
+                               // float-float, block m - 1 (P_j = W_j and Q of the adjoint)
   float2* dsq_ff;              // off_s x nq: sqrt(alpha~) as float-float
   float2* pff;                 // off_s*3 x ncol: P as float-float (replaces pmat)
   float2* qff;                 // off_s*3 x ncol: Q as float-float (replaces qmat)
