@@ -203,16 +203,21 @@ __global__ void __launch_bounds__(256) k_scs_fill(Work w, DevParams p, int c0, i
     const int i = w.pr_ij[2 * q], j = w.pr_ij[2 * q + 1];
     double rx, ry, rz, r2;
     scs_pair_in(xs, max_n12, i, j, rc2, rx, ry, rz, r2);
-    const double r = sqrt(r2);
+    // 1/r from one reciprocal square root; the Fermi damping (Eq. damping-function) through
+    // x = r / S_vdW, its r-derivative f (1 - f) d / S_vdW as f (1 - f) d x / r
+    const double ir = rsqrt(r2);
+    const double r = r2 * ir;
     const int ai = w.site_atom[sbase + i], aj = w.site_atom[sbase + j];
-    double fsr, dfsr, fin = 1.0, dfin = 0.0, f, dfr, dfs;
+    double fsr, dfsr, fin = 1.0, dfin = 0.0;
     cutoff_buf(r, p.r_scs, p.r_buf, fsr, dfsr);
     if (j >= n1) finner(r, p.r_inner, fin, dfin);
-    fermi(r, p.beta * (w.rvdw[ai] + w.rvdw[aj]), p.d, f, dfr, dfs);
+    const double x = r / (p.beta * (w.rvdw[ai] + w.rvdw[aj]));
+    const double f = 1.0 / (1.0 + exp(-p.d * (x - 1.0)));
+    const double dfr = f * (1.0 - f) * p.d * x * ir;
     const double F = fin * fsr * (1.0 - f);
     const double dF = dfin * fsr * (1.0 - f) + fin * dfsr * (1.0 - f) - fin * fsr * dfr;
     double* g = w.pr_geo + 8 * q;
-    g[0] = rx; g[1] = ry; g[2] = rz; g[3] = r; g[4] = F; g[5] = dF; g[6] = 1.0 / r; g[7] = 0.0;
+    g[0] = rx; g[1] = ry; g[2] = rz; g[3] = r; g[4] = F; g[5] = dF; g[6] = ir; g[7] = 0.0;
     float2* gf = w.pr_gff + 6 * q;
 #pragma unroll
     for (int u = 0; u < 7; ++u) {
