@@ -245,3 +245,38 @@ def test_sparse_sphere_beyond_the_dense_capacity(lm):
         assert abs(fd - f[a, g]) < F_ATOL + 1e-6 * abs(f[a, g]), (a, g, fd, f[a, g])
         checked += 1
     assert checked >= 2
+
+
+# ---------------------------------------------------------------------------------------
+# the bench line's split-cutoff workload at full size: the 4096-atom benchmark box with
+# r_MBD,1 = 6, r_MBD,2 = 3 A (sphere 9 A, ~300 sites), every atom against the dense path with
+# FP64 products, sampled centres and one one-hot gradient against the oracle
+# ---------------------------------------------------------------------------------------
+def test_box4096_split_cutoffs_sparse(lm):
+    s = inputs.box(4096, seed=0)
+    p = lm.default_params(r_mbd1=6.0, r_mbd2=3.0, r_sphere=0.0)
+    args = _dev(s)
+    msp = _model(lm, s, p, sparse=True)
+    esp, fsp = msp.energy_forces(*args)
+    counts = msp.site_counts(s.n_atoms)
+    e64, f64 = _model(lm, s, p, sparse=False, fp64=True).energy_forces(*args)
+    assert ((esp - e64).abs() / e64.abs()).max().item() < 1e-11
+    assert (fsp - f64).abs().max().item() < 1e-9
+    # oracle centres: the largest |K1| and sphere, and centres within 4 A of the former (their
+    # spheres share most of the central polarisabilities the oracle must solve for)
+    n1, ns = counts[:, 0], counts[:, 1]
+    k0 = int(np.argmax(n1))
+    d = s.positions - s.positions[k0]
+    box = np.diag(s.cell)
+    d -= box * np.round(d / box)
+    near = np.argsort((d * d).sum(1))[1:6]
+    centres = [k0, int(np.argmax(ns))] + [int(c) for c in near if int(c) != int(np.argmax(ns))]
+    so = oracle.System(s.positions, s.cell, s.species, s.hirshfeld, s.table, _op(p))
+    e_ref = so.energies(centres)
+    rel = np.abs(esp.cpu().numpy()[centres] - e_ref) / np.abs(e_ref)
+    assert np.all(rel < E_RTOL), (rel.max(), centres[int(np.argmax(rel))])
+    w = np.zeros(s.n_atoms)
+    w[k0] = 1.0
+    _, f_ref = so.energies_forces(centres=[k0], weights=np.array([1.0]))
+    _, f = msp.energy_forces(*args, forces=True, weights=torch.tensor(w, device="cuda"))
+    assert np.abs(f.cpu().numpy() - f_ref).max() < F_ATOL
