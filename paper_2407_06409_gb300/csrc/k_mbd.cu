@@ -1489,7 +1489,9 @@ void launch_forces_out(const Work& w, double* forces, cudaStream_t s) {
 __device__ __forceinline__ int oz_mpad(int n) { return (n + 63) / 64 * 64; }
 __device__ __forceinline__ int oz_kpad(int n) { return (n + 15) / 16 * 16; }
 
-// T_LR digit planes and row exponents (one block per central atom, one warp per row).
+// T_LR digit planes and row exponents (one block per central atom, one warp per row).  Rows of
+// at most 32 SLT_REG entries are read once into registers; longer rows are read twice.
+#define SLT_REG 18
 template <int st>
 __global__ void __launch_bounds__(256) k_slice_t(Work w, int c0) {
   const int c = c0 + blockIdx.x;
@@ -1501,6 +1503,30 @@ __global__ void __launch_bounds__(256) k_slice_t(Work w, int c0) {
   unsigned short* base = w.tk > 0 ? w.tdig + w.off_tr[c] * st * w.tk : w.tdig + w.off_tq[c] * st;
   const long long plane = (long long)Mpad * ld;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (N <= 32 * SLT_REG) {
+    // one read of T: the row stays in registers between its exponent and its digits
+    for (int row = warp; row < Mpad; row += nw) {
+      double v[SLT_REG];
+      int mx = 0;
+#pragma unroll
+      for (int k = 0; k < SLT_REG; ++k) {
+        const int j = lane + 32 * k;
+        v[k] = (row < N && j < N) ? T[(long long)row * N + j] : 0.0;
+        mx = max(mx, oz_biased_exp(v[k]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const int e = oz_scale_exp(mx);
+      if (lane == 0) w.texp[w.off_tr[c] + row] = e;
+#pragma unroll
+      for (int k = 0; k < SLT_REG; ++k) {
+        const int j = lane + 32 * k;
+        if (j < ld) oz_store_digits<st>(base + (long long)row * ld + j, plane, v[k], e);
+      }
+      for (int j = lane + 32 * SLT_REG; j < ld; j += 32) oz_store_digits<st>(base + (long long)row * ld + j, plane, 0.0, e);
+    }
+    return;
+  }
   for (int row = warp; row < Mpad; row += nw) {
     int mx = 0;
     if (row < N)
@@ -1548,7 +1574,9 @@ __global__ void __launch_bounds__(256) k_slice_w(Work w, DevParams p, int m, int
   }
 }
 
-// P and Q digit planes and row exponents (blockIdx.y = 0: P, 1: Q).
+// P and Q digit planes and row exponents (blockIdx.y = 0: P, 1: Q); rows of at most 32 SLP_REG
+// columns are read once into registers.
+#define SLP_REG 6
 template <int sp>
 __global__ void __launch_bounds__(256) k_slice_pq(Work w, int c0) {
   const int c = c0 + blockIdx.x;
@@ -1561,6 +1589,30 @@ __global__ void __launch_bounds__(256) k_slice_pq(Work w, int c0) {
   int* ex = (blockIdx.y == 0 ? w.pexp : w.qexp) + w.off_sp[c] * 3;
   const long long plane = (long long)R * Kp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (ncol <= 32 * SLP_REG) {
+    // one read of P or Q: the row stays in registers between its exponent and its digits
+    for (int row = warp; row < R; row += nw) {
+      double v[SLP_REG];
+      int mx = 0;
+#pragma unroll
+      for (int k = 0; k < SLP_REG; ++k) {
+        const int j = lane + 32 * k;
+        v[k] = (row < rows && j < ncol) ? src[(long long)row * ncol + j] : 0.0;
+        mx = max(mx, oz_biased_exp(v[k]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const int e = oz_scale_exp(mx);
+      if (lane == 0) ex[row] = e;
+#pragma unroll
+      for (int k = 0; k < SLP_REG; ++k) {
+        const int j = lane + 32 * k;
+        if (j < Kp) oz_store_digits<sp>(base + (long long)row * Kp + j, plane, v[k], e);
+      }
+      for (int j = lane + 32 * SLP_REG; j < Kp; j += 32) oz_store_digits<sp>(base + (long long)row * Kp + j, plane, 0.0, e);
+    }
+    return;
+  }
   for (int row = warp; row < R; row += nw) {
     int mx = 0;
     if (row < rows)
