@@ -456,30 +456,6 @@ __device__ __noinline__ void chol32_packed(float* A, int n, int* bad, float* sin
   }
 }
 
-// Inverses of the 16 x 16 diagonal blocks of a stored factor (one warp per block, one lane
-// per column), as chol32_packed produces them.
-__device__ void blockinv32(const float* A, int n, const float* sinv, float* binv) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nblk = (n + CB - 1) / CB;
-  for (int blk = warp; blk < nblk; blk += nw) {
-    const int k0 = blk * CB, kb = min(CB, n - k0);
-    float* inv = binv + blk * CBP;
-    if (lane < CB) {
-      const int cc = lane;
-      for (int i = cc; i < CB; ++i) {
-        float v = 0.f;
-        if (i < kb && cc < kb) {
-          float s = (i == cc) ? 1.f : 0.f;
-          for (int u = cc; u < i; ++u) s -= A[packed_idx(k0 + i, k0 + u)] * inv[pidx16(u, cc)];
-          v = s * sinv[k0 + i];
-        }
-        inv[pidx16(i, cc)] = v;
-      }
-    }
-  }
-}
-
-
 // y (n x 3, FP32, shared) <- (L L^T)^-1 y with binv the inverses of the 16 x 16 diagonal blocks,
 // a blocked substitution with one warp per right-hand side column: warps 0..2 each solve their
 // column with warp-level
@@ -941,6 +917,9 @@ __global__ void __launch_bounds__(256, 3) k_scs_factor(Work w, DevParams p, cons
   scs2_store_solution(w, p, c, q, n1, sm.x);
   float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
   for (long long e = tid; e < nA; e += blockDim.x) Lg[e] = sm.A[e];
+  // the inverses of the diagonal blocks as well, so that the adjoint need not form them again
+  float* Bg = w.binvg + ((long long)c * p.nqs + q) * w.binv_slot;
+  for (int e = tid; e < (N1 + CB - 1) / CB * CBP; e += blockDim.x) Bg[e] = sm.binv[e];
 }
 
 // Adjoint right-hand side dL/dX of one (centre, frequency) into sm.rhs (dL/dX_i = delta/3 times
@@ -982,7 +961,8 @@ __device__ __forceinline__ void scs2_adjoint_contract(const Work& w, const DevPa
     xf[e] = ff_from_double(xv);
   }
   __syncthreads();
-  double* gst = w.gstage + (offp * p.nqs + (long long)q * np) * 3;
+  // pair gradients as float-float (the per-site sums below stay on the FP32 pipe)
+  float2* gst = reinterpret_cast<float2*>(w.gstage) + (offp * p.nqs + (long long)q * np) * 3;
   for (int t = tid; t < np; t += blockDim.x) {
     const long long pq = offp + t;
     const int i = w.pr_ij[2 * pq], j = w.pr_ij[2 * pq + 1];
@@ -1043,33 +1023,36 @@ __device__ __forceinline__ void scs2_adjoint_contract(const Work& w, const DevPa
     const ff inner = ff_fma(dB0, rMr, ff_mul(dA0, trM));
     const ff radial = ff_mul(ff_fma(F, inner, ff_mul(dF, phi)), ir);
     const ff tang = ff_scale(ff_mul(F, B0), 2.0f);
-    gst[3 * t] = ff_to_double(ff_fma(tang, Mr[0], ff_mul(radial, rr[0])));
-    gst[3 * t + 1] = ff_to_double(ff_fma(tang, Mr[1], ff_mul(radial, rr[1])));
-    gst[3 * t + 2] = ff_to_double(ff_fma(tang, Mr[2], ff_mul(radial, rr[2])));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const ff g = ff_fma(tang, Mr[d], ff_mul(radial, rr[d]));
+      gst[3 * t + d] = make_float2(g.hi, g.lo);
+    }
   }
   __syncthreads();
   // per site (fixed order): owner of its row's pairs (-g), partner of K1 pairs owned by later
   // rows (+g, from the adjacency row) and of K2 pairs (+g, from the reverse list)
   double* sgq = w.sgq + (sbase * p.nqs + q) * 3;
+  auto gld = [&](long long k) { const float2 v = gst[k]; return ff_make(v.x, v.y); };
   for (int s = tid; s < n12; s += blockDim.x) {
-    double gx = 0.0, gy = 0.0, gz = 0.0;
+    ff gx = ff_make(0.f, 0.f), gy = gx, gz = gx;
     if (s < n1) {
       for (int t = w.prow[rbase + s]; t < w.prow[rbase + s + 1]; ++t) {
-        gx -= gst[3 * t]; gy -= gst[3 * t + 1]; gz -= gst[3 * t + 2];
+        gx = ff_sub(gx, gld(3 * t)); gy = ff_sub(gy, gld(3 * t + 1)); gz = ff_sub(gz, gld(3 * t + 2));
       }
       for (int t = w.arow[rbase + s]; t < w.arow[rbase + s + 1]; ++t) {
         const int j = w.adj[2 * (offa + t)], pp = w.adj[2 * (offa + t) + 1];
-        if (j > s) { gx += gst[3 * pp]; gy += gst[3 * pp + 1]; gz += gst[3 * pp + 2]; }
+        if (j > s) { gx = ff_add(gx, gld(3 * pp)); gy = ff_add(gy, gld(3 * pp + 1)); gz = ff_add(gz, gld(3 * pp + 2)); }
       }
     } else {
       for (int t = w.k2ptr[sbase + s]; t < w.k2ptr[sbase + s + 1]; ++t) {
         const int pp = w.k2rev[offp + t];
-        gx += gst[3 * pp]; gy += gst[3 * pp + 1]; gz += gst[3 * pp + 2];
+        gx = ff_add(gx, gld(3 * pp)); gy = ff_add(gy, gld(3 * pp + 1)); gz = ff_add(gz, gld(3 * pp + 2));
       }
     }
-    sgq[(long long)s * p.nqs * 3] = gx;
-    sgq[(long long)s * p.nqs * 3 + 1] = gy;
-    sgq[(long long)s * p.nqs * 3 + 2] = gz;
+    sgq[(long long)s * p.nqs * 3] = ff_to_double(gx);
+    sgq[(long long)s * p.nqs * 3 + 1] = ff_to_double(gy);
+    sgq[(long long)s * p.nqs * 3 + 2] = ff_to_double(gz);
   }
 }
 
@@ -1094,9 +1077,10 @@ __global__ void __launch_bounds__(256, 3) k_scs_adjoint2(Work w, DevParams p, co
   const long long nA = (long long)N1 * (N1 + 1) / 2;
   const float* Lg = w.lfac + w.off_b[c] + (long long)q * nA;
   for (long long e = tid; e < nA; e += blockDim.x) sm.A[e] = Lg[e];
-  for (int i = tid; i < N1; i += blockDim.x) sm.sinv[i] = 1.f / Lg[packed_idx(i, i)];
+  // the inverses of the diagonal blocks, as the factor kernel formed them (the solves need no more)
+  const float* Bg = w.binvg + ((long long)c * p.nqs + q) * w.binv_slot;
+  for (int e = tid; e < (N1 + CB - 1) / CB * CBP; e += blockDim.x) sm.binv[e] = Bg[e];
   __syncthreads();
-  blockinv32(sm.A, N1, sm.sinv, sm.binv);
   scs2_load_adjoint_rhs(w, p, c, q, n1, sm);
   __syncthreads();
   scs2_refine(w, p, n1, offp, offa, rbase, q, sm, &fail, 9.313225746154785e-10);   // lambda, 2^-30

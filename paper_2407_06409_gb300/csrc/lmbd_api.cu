@@ -276,6 +276,7 @@ struct Layout {
   int nqs;   // frequencies of the SCS solves (stage-1 arrays)
   int tk;    // tcgen05 path: row pitch of the T and W digit planes (0: per-centre Kpad)
   bool sparse;   // block-sparse T_LR: coupled pairs and float-float chain/pair operands
+  int binv_slot; // floats of the diagonal-block inverses of one SCS system (largest |K1|)
 
   // stage 1 (SCS): pair lists, FP32 factors and solutions of centres [c0, c1)
   size_t stage1(const Offs& o, int c0, int c1, char* base, Work* w) const {
@@ -285,6 +286,7 @@ struct Layout {
     const long long k0 = o.at(O_K1, c0), nk = o.span(O_K1, c0, c1);
     const long long n = c1 - c0;
     float* lfac = cv.take<float>(o.span(O_B, c0, c1), o.at(O_B, c0));
+    float* binvg = cv.take<float>((long long)binv_slot * nqs * n, (long long)binv_slot * nqs * c0);
     int* pr_ij = cv.take<int>(2 * (np + 1), 2 * p0);
     double* pr_geo = cv.take<double>(8 * (np + 1), 8 * p0);
     float2* pr_rad_ff = cv.take<float2>(2LL * nqs * (np + 1), 2LL * nqs * p0);
@@ -299,6 +301,8 @@ struct Layout {
     double* xsol = cv.take<double>(9LL * nqs * nk, 9LL * nqs * k0);
     if (w) {
       w->lfac = lfac;
+      w->binvg = binvg;
+      w->binv_slot = binv_slot;
       w->pr_ij = pr_ij;
       w->pr_geo = pr_geo;
       w->pr_rad_ff = pr_rad_ff;
@@ -906,7 +910,8 @@ int run(Ctx* c, int N, const double* pos_in, const double* cell, const int* spec
 
   // ---- waves under the memory budget --------------------------------------------------------
   const Layout L{nq, ncv, nvec, ncol, (ncol + 15) / 16 * 16, ST, DIG_P, c->site_cap, forces, sliced_chain,
-                 sliced_pair, dp.nqs, tc05 ? (3 * max_ns + 15) / 16 * 16 : 0, sparse};
+                 sliced_pair, dp.nqs, tc05 ? (3 * max_ns + 15) / 16 * 16 : 0, sparse,
+                 (3 * max_n1 + 15) / 16 * 136};
   auto s1 = [&](int a, int b) { return L.stage1(o, a, b, nullptr, nullptr); };
   auto s1x = [&](int a, int b) { return forces ? L.scs_adjoint(o, a, b, nullptr, nullptr) : (size_t)0; };
   auto s2 = [&](int a, int b) { return L.stage2(o, a, b, nullptr, nullptr, nullptr); };

@@ -134,8 +134,12 @@ struct Work {
   int* k2ptr;                  // N x site_cap: first reverse-list entry of each K2 site
   int* k2rev;                  // per centre (off_p): pair indices grouped by K2 partner
   double* sgq;                 // N x site_cap x nq x 3: SCS-adjoint site gradients per frequency
-  double* gstage;              // sum pairs x nq x 3: SCS-adjoint pair gradients (scratch)
+  double* gstage;              // sum pairs x nq x 3: SCS-adjoint pair gradients (scratch; 8-byte
+                               // entries, written and read as float-float pairs)
   float* lfac;                 // packed FP32 Cholesky factors, off_b
+  float* binvg;                // inverses of their 16 x 16 diagonal blocks, binv_slot floats per
+                               // (centre, SCS frequency), indexed by the global centre
+  int binv_slot;
   // LU fallback of the SCS solves (systems whose FP32 Cholesky pivot is not positive or whose
   // refinement does not converge): fb[0] = count, fb[1 + e] = c * nqs + q; fb_flag[c * nqs + q]
   // = 1 for such a system (its FP32 factor is not used); lu: per-block dense slots of lu_slot
